@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-free finite element operator action on GB300.
+
+Default workload: Laplacian and Helmholtz (k^2 = 1) actions of scalar Q_p,
+p = 1..6, on a 64^3 hexahedral mesh with vertices perturbed by up to 0.1h,
+p+1 Gauss points per direction, sum-factorised, FP64, input uniform in
+[-1, 1) (the Section 4 operator-action experiment on the hex mesh).  One
+step applies all 12 operators once; the metric is the operator action rate
+in GDoF/s (global dofs processed per second, summed over the operators).
+
+--impl reference times the FP64 CPU oracle on the host cores instead, on a
+bounded sample (a box of cells cut from the same mesh) per operator.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import fe_inputs as fi  # noqa: E402
+
+# FP64 pipe of GB300: 152 SMs x 2 DFMA lanes/clk x 2 flop x 2070 MHz (max SM clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# DRAM traffic per launch of the dominant kernel from one ncu capture, valid only
+# while the kernel source is unchanged (sha1 of hex_kernels.cuh).
+NCU_TRAFFIC = {}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mfa", "reference"], default="mfa")
+    ap.add_argument("--nx", type=int, default=64)
+    ap.add_argument("--degrees", default="1,2,3,4,5,6")
+    ap.add_argument("--forms", default="laplace,helmholtz")
+    ap.add_argument("--scatter", choices=["atomic", "colour"], default="atomic")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+FORM_IDS = {"mass": 0, "laplace": 1, "helmholtz": 2}
+
+
+def workload_name(args):
+    return "hex%d^3-perturbed0.1h-Q%s-%s-fp64" % (args.nx, args.degrees.replace(",", ""), args.forms.replace(",", "+"))
+
+
+def build_cases(args):
+    degrees = [int(p) for p in args.degrees.split(",")]
+    forms = args.forms.split(",")
+    mesh = fi.hex_box_mesh(args.nx, perturb=0.1, seed=1)
+    cases = []
+    for p in degrees:
+        cell_node, nnode = fi.hex_node_map(args.nx, p)
+        x = fi.uniform_vector(nnode, seed=1)
+        for f in forms:
+            cases.append(dict(form=f, p=p, cell_node=cell_node, nnode=nnode, x=x))
+    return mesh, cases
+
+
+def kernel_hash():
+    src = os.path.join(ROOT, "paper_1903_08243_gb300", "csrc", "hex_kernels.cuh")
+    return hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allreduce_max(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline / reference arm)
+
+def sub_box(mesh, cell_node, nx, b):
+    """The first b^3 box of cells of the structured mesh, with compact node numbering."""
+    k, j, i = np.meshgrid(np.arange(b), np.arange(b), np.arange(b), indexing="ij")
+    cells = (i + nx * (j + nx * k)).ravel()
+    cv, cn = mesh.cell_vert[cells], cell_node[cells]
+    nodes, inv = np.unique(cn, return_inverse=True)
+    return cv, inv.reshape(cn.shape).astype(np.int32), nodes.size, cells.size
+
+
+SAMPLE_BOX = {1: 16, 2: 10, 3: 7, 4: 5, 5: 4, 6: 3, 7: 3, 8: 2}
+
+
+def oracle_rate(mesh, cases, nx, repeats=1):
+    """Extrapolated full-mesh apply time per operator from timing the oracle on a sub-box."""
+    import oracle
+
+    ncell = nx ** 3
+    out = []
+    for c in cases:
+        b = min(SAMPLE_BOX.get(c["p"], 2), nx)
+        cv, cn, nn, nsub = sub_box(mesh, c["cell_node"], nx, b)
+        pb = oracle.Problem(oracle.HEX, mesh.coords, cv, c["p"], cn, nn, FORM_IDS[c["form"]], k2=1.0)
+        xs = fi.uniform_vector(nn, seed=5)
+        best = None
+        for _ in range(repeats):
+            t0 = time.perf_counter()
+            pb.apply(xs)
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        out.append(dict(form=c["form"], p=c["p"], sample_cells=nsub, sample_s=best, full_s=best * ncell / nsub,
+                        ndof=c["nnode"]))
+    return out
+
+
+def reference_arm(args, world, rank):
+    if rank != 0:
+        return
+    mesh, cases = build_cases(args)
+    for _ in range(args.warmup):
+        oracle_rate(mesh, cases[:1], args.nx)
+    times, samples = [], None
+    for _ in range(args.steps):
+        r = oracle_rate(mesh, cases, args.nx)
+        samples = r
+        times.append(sum(o["full_s"] for o in r))
+    ndof = sum(c["nnode"] for c in cases)
+    step_s = statistics.mean(times)
+    value = ndof / step_s / 1e9
+    sample_desc = "per operator a box of cells (%s) of the %d^3 mesh; full-mesh time extrapolated by cell count" % (
+        ", ".join("Q%d %s: %d cells" % (o["p"], o["form"], o["sample_cells"]) for o in samples), args.nx)
+    line = {
+        "impl": "reference", "metric": "operator-action GDoF/s", "value": value, "unit": "GDoF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args), "mesh": "%d^3 hex, interior vertices perturbed U[-0.1h,0.1h]" % args.nx,
+                   "quadrature": "p+1 Gauss points per direction", "input": "x ~ U[-1,1) seed 1"},
+        "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": sample_desc},
+        "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def gpu_arm(args, world, rank, local):
+    import torch
+
+    from paper_1903_08243_gb300 import build as libbuild
+
+    libbuild.build()
+    import paper_1903_08243_gb300 as mfa
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = mfa.Context(local, stream)
+    mesh, cases = build_cases(args)
+    m = mfa.Mesh(ctx, mfa.MFA_CELL_HEX8, mesh.coords, mesh.cell_vert)
+    scatter = mfa.MFA_SCATTER_ATOMIC if args.scatter == "atomic" else mfa.MFA_SCATTER_COLOUR
+    spaces, ops = {}, []
+    for c in cases:
+        if c["p"] not in spaces:
+            spaces[c["p"]] = mfa.Space(m, c["p"], 1, c["cell_node"], c["nnode"])
+        form = mfa.Form(spaces[c["p"]], FORM_IDS[c["form"]], k2=1.0, scatter=scatter)
+        x = torch.from_numpy(c["x"]).to("cuda")
+        y = torch.empty_like(x)
+        info = form.info()
+        ops.append(dict(case=c, form=form, x=x, y=y, info=info))
+    ctx.sync()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
+    launches_per_step = sum(o["info"].ncolours if o["info"].scatter == mfa.MFA_SCATTER_COLOUR else 1 for o in ops)
+
+    def step(events=None):
+        for i, o in enumerate(ops):
+            if events is not None:
+                events[i][0].record(stream)
+            mfa.mfa_apply(ctx.h, o["form"].h, o["x"], o["y"], False)
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    ctx.sync()
+    ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in ops]
+          for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))  # L2 flush between steps, outside the per-operator events
+        step(ev[k])
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall
+    time.sleep(0.3)
+    clocks = sampler.stop()
+    ctx.sync()
+    per_op_ms = [statistics.mean(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
+                 for i in range(len(ops))]
+    step_ms = sum(per_op_ms)
+    step_ms = allreduce_max(world, step_ms)
+    ndof_step = sum(o["case"]["nnode"] for o in ops)
+    value = world * ndof_step / (step_ms / 1e3) / 1e9
+
+    # dominant kernel roofline (FP64 pipe)
+    i_dom = int(np.argmax(per_op_ms))
+    dom = ops[i_dom]
+    achieved = dom["info"].flops / (per_op_ms[i_dom] / 1e3) / 1e12
+    kh = kernel_hash()
+    traffic = NCU_TRAFFIC.get((kh, dom["case"]["form"], dom["case"]["p"]))
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": "hex_apply_kernel<n=%d,nq=%d,%s>" % (dom["case"]["p"] + 1, dom["case"]["p"] + 1,
+                                                                 dom["case"]["form"]),
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (FP64 pipe; recipe unit counts)",
+                "algorithmic_flops_per_launch": dom["info"].flops, "kernel_sha1": kh}
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if args.e2e_steps > 0:
+        hx = [torch.from_numpy(o["case"]["x"]).pin_memory() for o in ops]
+        hy = [torch.empty_like(h).pin_memory() for h in hx]
+        for i, o in enumerate(ops):  # warm the staging buffers
+            mfa.mfa_apply_host(ctx.h, o["form"].h, hx[i], hy[i])
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for i, o in enumerate(ops):
+                mfa.mfa_apply_host(ctx.h, o["form"].h, hx[i], hy[i])
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        dt = allreduce_max(world, dt)
+        e2e = {"value": world * ndof_step / dt / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * ndof_step,
+               "d2h_bytes_per_step": 8 * ndof_step, "ms_per_step": dt * 1e3, "path": "mfa_apply_host, pinned host buffers"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_rate(mesh, cases, args.nx)
+        full_s = sum(o["full_s"] for o in r)
+        cpu = {"value": ndof_step / full_s / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+               "sample": "per operator a box of cells of the %d^3 mesh (%s), timed once; full-mesh time "
+                         "extrapolated by cell count" % (args.nx, ", ".join("Q%d %s %d cells %.2fs" % (
+                             o["p"], o["form"], o["sample_cells"], o["sample_s"]) for o in r))}
+
+    per_op = []
+    for o, ms in zip(ops, per_op_ms):
+        per_op.append({"form": o["case"]["form"], "p": o["case"]["p"], "ndof": o["case"]["nnode"], "ms": ms,
+                       "gdof_s": o["case"]["nnode"] / ms / 1e6, "gflop_s": o["info"].flops / ms / 1e6,
+                       "frac_fp64": o["info"].flops / ms / 1e9 / FP64_PEAK_TFLOPS})
+    if rank == 0:
+        line = {
+            "metric": "operator-action GDoF/s", "value": value, "unit": "GDoF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args), "mesh": "%d^3 hex, interior vertices perturbed U[-0.1h,0.1h], seed 1" % args.nx,
+                       "degrees": [int(p) for p in args.degrees.split(",")], "forms": args.forms.split(","),
+                       "quadrature": "p+1 Gauss points per direction", "geometry": "stored FP64 G per point",
+                       "scatter": args.scatter, "input": "x ~ U[-1,1) seed 1", "ndof_per_step": ndof_step,
+                       "l2": "flushed between steps (256 MiB write outside the timed events)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches_per_step * args.steps, "wall_s_timed_region": t_wall, "per_operator": per_op,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+    else:
+        gpu_arm(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

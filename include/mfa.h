@@ -1,0 +1,175 @@
+/*
+ * mfa.h -- matrix-free finite element operator action on GB300 (sm_103a).
+ *
+ * The library evaluates y = A(x): the global assembly of a linear (residual)
+ * form L(x; v) over every cell of a tetrahedral or hexahedral mesh, as in
+ * Section 2 of arXiv 1903.08243 ("A study of vectorization for matrix-free
+ * finite element methods").  One apply is the parloop of Section 2.2,
+ *
+ *     parloop(kernel, cells, y(cell2dof, INC), coords(cell2vert, R), x(cell2dof, R)),
+ *
+ * i.e. for every cell: gather the vertex coordinates through the
+ * cell->vertex map and the dofs through the cell->node map, evaluate the
+ * local element kernel at the quadrature points (Section 2.1, Listing 2), and
+ * add the local result into y through the cell->node map (Listing 3).  The
+ * element kernels are the operators of the paper's Supplementary material:
+ * mass, Helmholtz, (vector) Laplacian, linear elasticity and hyperelasticity
+ * (residual and its Gateaux derivative).
+ *
+ * Conventions
+ *  - Every function returns an mfa_status; 0 is success.  Nothing aborts.
+ *    mfa_last_error() returns a message for the calling thread's last failure.
+ *  - Handles are created and owned by the library; destroy them with the
+ *    matching *_destroy call (a NULL handle is accepted and ignored).
+ *  - Host arrays passed to *_upload / *_create are copied; the caller keeps
+ *    ownership and may free them on return.
+ *  - Vectors passed to mfa_apply are device pointers owned by the caller
+ *    (e.g. PyTorch tensors), FP64, contiguous, 8-byte aligned.  Work is
+ *    enqueued on the context's stream and is asynchronous with respect to the
+ *    host; mfa_sync() waits for it and reports errors found by kernels.
+ *  - Reference tetrahedron: vertices (0,0,0), (1,0,0), (0,1,0), (0,0,1).
+ *    Reference hexahedron: [0,1]^3, local vertex a + 2b + 4c at corner (a,b,c).
+ *  - P2 local nodes: 0..3 vertices, 4..9 midpoints of edges (0,1), (0,2),
+ *    (0,3), (1,2), (1,3), (2,3).  Q_p local node i + n*j + n*n*k (n = p + 1)
+ *    sits at the tensor product of the Gauss-Lobatto-Legendre points.
+ *  - A vector field with ncomp = 3 stores dof 3*node + c.
+ */
+#ifndef MFA_H
+#define MFA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MFA_VERSION 1
+
+#if defined(__GNUC__)
+#define MFA_API __attribute__((visibility("default")))
+#else
+#define MFA_API
+#endif
+
+typedef enum {
+  MFA_OK = 0,
+  MFA_ERR_ARG = 1,           /* null pointer, bad size, bad enum value            */
+  MFA_ERR_RANGE = 2,         /* a map entry outside [0, n)                          */
+  MFA_ERR_UNSUPPORTED = 3,   /* degree / cell / form / precision combination        */
+  MFA_ERR_CUDA = 4,          /* a CUDA runtime call failed                          */
+  MFA_ERR_OOM = 5,           /* device or host allocation failed                    */
+  MFA_ERR_TIMEOUT = 6,       /* a bounded device wait ran out                       */
+  MFA_ERR_NOT_CONVERGED = 7, /* an iterative solver reached maxit                   */
+  MFA_ERR_BREAKDOWN = 8,     /* CG breakdown: p.Ap <= 0 or a non-finite scalar      */
+  MFA_ERR_DOMAIN = 9         /* a kernel met det J <= 0 or a deformation with J <= 0 */
+} mfa_status;
+
+enum { MFA_CELL_TET4 = 4, MFA_CELL_HEX8 = 8 };
+
+/* Forms of the Supplementary material (bilinear forms taken by their action). */
+enum {
+  MFA_FORM_MASS = 0,       /* y_i = int phi_i u                                       */
+  MFA_FORM_LAPLACE = 1,    /* y_i = int grad phi_i : grad u   (vector Laplacian if ncomp=3) */
+  MFA_FORM_HELMHOLTZ = 2,  /* y_i = int grad phi_i . grad u + k2 phi_i u              */
+  MFA_FORM_ELASTICITY = 3, /* y_i = int sigma(u) : eps(phi_i), sigma = 2 mu eps + lambda tr(eps) I */
+  MFA_FORM_HYPER_RES = 4,  /* y_i = int P(F) : grad phi_i - b . phi_i, F = I + grad x  */
+  MFA_FORM_HYPER_JAC = 5   /* y_i = int dP(F; grad x) : grad phi_i, F = I + grad u (coefficient) */
+};
+
+enum { MFA_LAW_SVK = 0, MFA_LAW_NEOHOOKE = 1 };
+enum { MFA_PREC_FP64 = 0, MFA_PREC_FP32 = 1, MFA_PREC_BF16 = 2 };
+enum { MFA_SCATTER_AUTO = 0, MFA_SCATTER_COLOUR = 1, MFA_SCATTER_ATOMIC = 2 };
+
+typedef struct {
+  int32_t kind;            /* MFA_FORM_*                                               */
+  int32_t law;             /* MFA_LAW_* (hyperelastic forms)                           */
+  int32_t qdeg;            /* 0 = default.  Hex: Gauss points per direction (default p+1).
+                              Tet: degree of the rule (default 2p; hyperelastic 4).     */
+  int32_t precision;       /* MFA_PREC_*                                               */
+  int32_t scatter;         /* MFA_SCATTER_*                                            */
+  int32_t cells_per_block; /* 0 = automatic                                            */
+  double k2;               /* Helmholtz coefficient (paper: 1)                          */
+  double lambda, mu;       /* Lame parameters (elasticity, hyperelasticity)             */
+  double b[3];             /* body force of the hyperelastic residual                   */
+} mfa_form_params;
+
+typedef struct {
+  int64_t ncell, ndof;
+  int32_t nloc;            /* local nodes per cell                                      */
+  int32_t nq;              /* quadrature points per cell used by the kernel              */
+  int32_t ncolours;        /* colours of the deterministic scatter (0 if not built)     */
+  int32_t scatter;         /* scatter actually used                                      */
+  double flops;            /* algorithmic FP operations of one apply                     */
+  double bytes;            /* algorithmic DRAM bytes of one apply                        */
+  double setup_ms;         /* host+device time spent in mfa_form_create                  */
+} mfa_form_info;
+
+typedef struct mfa_ctx mfa_ctx;
+typedef struct mfa_mesh mfa_mesh;
+typedef struct mfa_space mfa_space;
+typedef struct mfa_form mfa_form;
+
+/* Message of the calling thread's most recent failure ("" if none). */
+MFA_API const char *mfa_last_error(void);
+MFA_API int mfa_version(void);
+
+/* Context bound to CUDA `device`; `stream` is a borrowed cudaStream_t (NULL =
+ * the legacy default stream).  The stream must outlive the context. */
+MFA_API int mfa_create(mfa_ctx **ctx, int device, void *stream);
+MFA_API int mfa_set_stream(mfa_ctx *ctx, void *stream);
+MFA_API int mfa_destroy(mfa_ctx *ctx);
+
+/* Mesh: coords [nvert][3] (host, FP64), cell_vert [ncell][cell_type] (host,
+ * int32).  Returns MFA_ERR_RANGE if a vertex index is outside [0, nvert).
+ * Section 2.2: `coords(cell2vert, R)`. */
+MFA_API int mfa_mesh_upload(mfa_ctx *ctx, int cell_type, int64_t ncell, int64_t nvert, const double *coords,
+                    const int32_t *cell_vert, mfa_mesh **out);
+MFA_API int mfa_mesh_destroy(mfa_mesh *mesh);
+
+/* Continuous Lagrange space of `degree` (P1/P2 on tets, Q1..Q8 on hexes) with
+ * ncomp in {1, 3}.  cell_node [ncell][nloc] (host, int32) is the cell->node
+ * map of Section 2.2 (`cell2dof`); entries must lie in [0, nnode) and be
+ * distinct within a cell.  The mesh must outlive the space. */
+MFA_API int mfa_space_create(mfa_ctx *ctx, mfa_mesh *mesh, int degree, int ncomp, const int32_t *cell_node,
+                     int64_t nnode, mfa_space **out);
+MFA_API int mfa_space_ndof(const mfa_space *space, int64_t *ndof);
+MFA_API int mfa_space_destroy(mfa_space *space);
+
+/* Build a form on a space: quadrature tables, geometric factors (hex: stored
+ * per quadrature point in FP64), and the cell colouring if the scatter is
+ * coloured.  Synchronous.  The space must outlive the form. */
+MFA_API int mfa_form_create(mfa_ctx *ctx, mfa_space *space, const mfa_form_params *params, mfa_form **out);
+/* HYPER_JAC: linearisation point u (device, FP64, ndof entries, borrowed: it
+ * must stay valid while the form is applied). */
+MFA_API int mfa_form_set_coefficient(mfa_form *form, const double *u);
+MFA_API int mfa_form_get_info(const mfa_form *form, mfa_form_info *info);
+MFA_API int mfa_form_destroy(mfa_form *form);
+
+/* y = A(x) (accumulate = 0) or y += A(x) (accumulate = 1).  x, y: device,
+ * ndof FP64 entries, must not overlap.  Asynchronous on the context stream.
+ * Section 2.2 global assembly with the Section 2.1 local kernel. */
+MFA_API int mfa_apply(mfa_ctx *ctx, mfa_form *form, const double *x, double *y, int accumulate);
+/* Same with host buffers: copies x to the device, applies, copies y back and
+ * waits.  The device staging buffers are owned by the form. */
+MFA_API int mfa_apply_host(mfa_ctx *ctx, mfa_form *form, const double *x_host, double *y_host);
+/* Wait for the context stream; MFA_ERR_DOMAIN if a kernel flagged det J <= 0
+ * or a deformation with J <= 0 since the last mfa_sync (the flag is cleared). */
+MFA_API int mfa_sync(mfa_ctx *ctx);
+
+/* d_i = A_ii (linear forms): the matrix-free diagonal, assembled per cell
+ * from the same quadrature as mfa_apply.  d: device, ndof FP64. */
+MFA_API int mfa_diagonal(mfa_ctx *ctx, mfa_form *form, double *d);
+
+/* Conjugate gradients on a symmetric positive-definite linear form in FP64.
+ * precond: MFA_PC_NONE or MFA_PC_JACOBI.  b, x: device (x is the initial guess
+ * on entry and the solution on exit).  Stops when ||r||_2 <= rtol ||b||_2.
+ * Returns MFA_ERR_NOT_CONVERGED at maxit, MFA_ERR_BREAKDOWN on p.Ap <= 0 or a
+ * non-finite scalar.  iters and relres (nullable) receive the outcome. */
+enum { MFA_PC_NONE = 0, MFA_PC_JACOBI = 1 };
+MFA_API int mfa_cg(mfa_ctx *ctx, mfa_form *form, int precond, const double *b, double *x, double rtol, int maxit,
+           int *iters, double *relres);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFA_H */

@@ -1,0 +1,327 @@
+"""Python binding of libmfa: matrix-free finite element operator action on GB300.
+
+Argument marshalling only.  Every step of the operator action runs in the
+CUDA kernels of ``libmfa.so`` behind the C ABI of ``include/mfa.h``; this
+module converts numpy arrays and torch CUDA tensors into pointers and status
+codes into exceptions.  There is no CPU fallback: if the library is missing
+the import fails.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmfa.so")
+
+# ---- constants mirrored from include/mfa.h
+MFA_OK, MFA_ERR_ARG, MFA_ERR_RANGE, MFA_ERR_UNSUPPORTED, MFA_ERR_CUDA = 0, 1, 2, 3, 4
+MFA_ERR_OOM, MFA_ERR_TIMEOUT, MFA_ERR_NOT_CONVERGED, MFA_ERR_BREAKDOWN, MFA_ERR_DOMAIN = 5, 6, 7, 8, 9
+MFA_CELL_TET4, MFA_CELL_HEX8 = 4, 8
+MFA_FORM_MASS, MFA_FORM_LAPLACE, MFA_FORM_HELMHOLTZ = 0, 1, 2
+MFA_FORM_ELASTICITY, MFA_FORM_HYPER_RES, MFA_FORM_HYPER_JAC = 3, 4, 5
+MFA_LAW_SVK, MFA_LAW_NEOHOOKE = 0, 1
+MFA_PREC_FP64, MFA_PREC_FP32, MFA_PREC_BF16 = 0, 1, 2
+MFA_SCATTER_AUTO, MFA_SCATTER_COLOUR, MFA_SCATTER_ATOMIC = 0, 1, 2
+MFA_PC_NONE, MFA_PC_JACOBI = 0, 1
+
+
+class MfaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("mfa status %d: %s" % (code, msg))
+        self.code = code
+
+
+class mfa_form_params(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("law", ctypes.c_int32),
+        ("qdeg", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("scatter", ctypes.c_int32),
+        ("cells_per_block", ctypes.c_int32),
+        ("k2", ctypes.c_double),
+        ("lam", ctypes.c_double),
+        ("mu", ctypes.c_double),
+        ("b", ctypes.c_double * 3),
+    ]
+
+
+class mfa_form_info(ctypes.Structure):
+    _fields_ = [
+        ("ncell", ctypes.c_int64),
+        ("ndof", ctypes.c_int64),
+        ("nloc", ctypes.c_int32),
+        ("nq", ctypes.c_int32),
+        ("ncolours", ctypes.c_int32),
+        ("scatter", ctypes.c_int32),
+        ("flops", ctypes.c_double),
+        ("bytes", ctypes.c_double),
+        ("setup_ms", ctypes.c_double),
+    ]
+
+
+_lib = None
+_VP, _I, _I64, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+_PP = ctypes.POINTER(ctypes.c_void_p)
+_SIGS = {
+    "mfa_last_error": ([], ctypes.c_char_p),
+    "mfa_version": ([], _I),
+    "mfa_create": ([_PP, _I, _VP], _I),
+    "mfa_set_stream": ([_VP, _VP], _I),
+    "mfa_destroy": ([_VP], _I),
+    "mfa_mesh_upload": ([_VP, _I, _I64, _I64, _VP, _VP, _PP], _I),
+    "mfa_mesh_destroy": ([_VP], _I),
+    "mfa_space_create": ([_VP, _VP, _I, _I, _VP, _I64, _PP], _I),
+    "mfa_space_ndof": ([_VP, ctypes.POINTER(_I64)], _I),
+    "mfa_space_destroy": ([_VP], _I),
+    "mfa_form_create": ([_VP, _VP, ctypes.POINTER(mfa_form_params), _PP], _I),
+    "mfa_form_set_coefficient": ([_VP, _VP], _I),
+    "mfa_form_get_info": ([_VP, ctypes.POINTER(mfa_form_info)], _I),
+    "mfa_form_destroy": ([_VP], _I),
+    "mfa_apply": ([_VP, _VP, _VP, _VP, _I], _I),
+    "mfa_apply_host": ([_VP, _VP, _VP, _VP], _I),
+    "mfa_sync": ([_VP], _I),
+    "mfa_diagonal": ([_VP, _VP, _VP], _I),
+    "mfa_cg": ([_VP, _VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
+}
+
+
+def lib():
+    """Load libmfa.so (built by ``build()``); raises if it is absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libmfa.so not found at %s: run paper_1903_08243_gb300.build.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != MFA_OK:
+        raise MfaError(rc, lib().mfa_last_error().decode())
+
+
+def _ptr(a):
+    """Address of a numpy array or a torch tensor."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- the C ABI under the same names (status codes become MfaError)
+
+def mfa_create(device=0, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().mfa_create(ctypes.byref(h), device, _stream_handle(stream)))
+    return h
+
+
+def mfa_set_stream(ctx, stream):
+    _check(lib().mfa_set_stream(ctx, _stream_handle(stream)))
+
+
+def mfa_destroy(ctx):
+    _check(lib().mfa_destroy(ctx))
+
+
+def mfa_mesh_upload(ctx, cell_type, coords, cell_vert):
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    cell_vert = np.ascontiguousarray(cell_vert, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(lib().mfa_mesh_upload(ctx, cell_type, cell_vert.shape[0], coords.shape[0], _ptr(coords), _ptr(cell_vert),
+                                 ctypes.byref(h)))
+    return h
+
+
+def mfa_mesh_destroy(mesh):
+    _check(lib().mfa_mesh_destroy(mesh))
+
+
+def mfa_space_create(ctx, mesh, degree, ncomp, cell_node, nnode):
+    cell_node = np.ascontiguousarray(cell_node, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(lib().mfa_space_create(ctx, mesh, degree, ncomp, _ptr(cell_node), nnode, ctypes.byref(h)))
+    return h
+
+
+def mfa_space_ndof(space):
+    n = ctypes.c_int64()
+    _check(lib().mfa_space_ndof(space, ctypes.byref(n)))
+    return n.value
+
+
+def mfa_space_destroy(space):
+    _check(lib().mfa_space_destroy(space))
+
+
+def mfa_form_create(ctx, space, params):
+    h = ctypes.c_void_p()
+    _check(lib().mfa_form_create(ctx, space, ctypes.byref(params), ctypes.byref(h)))
+    return h
+
+
+def mfa_form_set_coefficient(form, u):
+    _check(lib().mfa_form_set_coefficient(form, _ptr(u)))
+
+
+def mfa_form_get_info(form):
+    info = mfa_form_info()
+    _check(lib().mfa_form_get_info(form, ctypes.byref(info)))
+    return info
+
+
+def mfa_form_destroy(form):
+    _check(lib().mfa_form_destroy(form))
+
+
+def mfa_apply(ctx, form, x, y, accumulate=False):
+    _check(lib().mfa_apply(ctx, form, _ptr(x), _ptr(y), int(accumulate)))
+
+
+def mfa_apply_host(ctx, form, x_host, y_host):
+    _check(lib().mfa_apply_host(ctx, form, _ptr(x_host), _ptr(y_host)))
+
+
+def mfa_sync(ctx):
+    _check(lib().mfa_sync(ctx))
+
+
+def mfa_diagonal(ctx, form, d):
+    _check(lib().mfa_diagonal(ctx, form, _ptr(d)))
+
+
+def mfa_cg(ctx, form, precond, b, x, rtol, maxit):
+    """Returns (status, iterations, relative residual); raises on errors other than non-convergence."""
+    it, rel = ctypes.c_int(), ctypes.c_double()
+    rc = lib().mfa_cg(ctx, form, precond, _ptr(b), _ptr(x), rtol, maxit, ctypes.byref(it), ctypes.byref(rel))
+    if rc not in (MFA_OK, MFA_ERR_NOT_CONVERGED):
+        _check(rc)
+    return rc, it.value, rel.value
+
+
+# ---- small owning wrappers (destroy in reverse order of creation)
+
+class Context:
+    def __init__(self, device=0, stream=None):
+        self.h = mfa_create(device, stream)
+
+    def sync(self):
+        mfa_sync(self.h)
+
+    def close(self):
+        if self.h:
+            mfa_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh:
+    def __init__(self, ctx, cell_type, coords, cell_vert):
+        self.ctx = ctx
+        self.cell_type = cell_type
+        self.ncell = int(np.asarray(cell_vert).shape[0])
+        self.nvert = int(np.asarray(coords).shape[0])
+        self.h = mfa_mesh_upload(ctx.h, cell_type, coords, cell_vert)
+
+    def __del__(self):
+        try:
+            if self.h:
+                mfa_mesh_destroy(self.h)
+        except Exception:
+            pass
+
+
+class Space:
+    def __init__(self, mesh, degree, ncomp, cell_node, nnode):
+        self.mesh = mesh
+        self.degree, self.ncomp, self.nnode = degree, ncomp, int(nnode)
+        self.h = mfa_space_create(mesh.ctx.h, mesh.h, degree, ncomp, cell_node, nnode)
+        self.ndof = mfa_space_ndof(self.h)
+
+    def __del__(self):
+        try:
+            if self.h:
+                mfa_space_destroy(self.h)
+        except Exception:
+            pass
+
+
+def form_params(kind, law=MFA_LAW_SVK, qdeg=0, precision=MFA_PREC_FP64, scatter=MFA_SCATTER_AUTO, k2=1.0,
+                lam=1.0, mu=1.0, b=(0.0, 0.0, 0.0)):
+    p = mfa_form_params()
+    p.kind, p.law, p.qdeg, p.precision, p.scatter, p.cells_per_block = kind, law, qdeg, precision, scatter, 0
+    p.k2, p.lam, p.mu = k2, lam, mu
+    p.b[0], p.b[1], p.b[2] = b
+    return p
+
+
+class Form:
+    def __init__(self, space, kind, **kw):
+        self.space = space
+        self.ctx = space.mesh.ctx
+        self.params = form_params(kind, **kw)
+        self.h = mfa_form_create(self.ctx.h, space.h, self.params)
+        self._coef = None
+
+    def info(self):
+        return mfa_form_get_info(self.h)
+
+    def set_coefficient(self, u):
+        self._coef = u  # keep the borrowed buffer alive
+        mfa_form_set_coefficient(self.h, u)
+
+    def apply(self, x, y=None, accumulate=False):
+        if y is None:
+            import torch
+
+            y = torch.empty_like(x)
+        mfa_apply(self.ctx.h, self.h, x, y, accumulate)
+        return y
+
+    def apply_host(self, x_host, y_host=None):
+        x_host = np.ascontiguousarray(x_host, dtype=np.float64)
+        if y_host is None:
+            y_host = np.empty_like(x_host)
+        mfa_apply_host(self.ctx.h, self.h, x_host, y_host)
+        return y_host
+
+    def diagonal(self, d=None):
+        if d is None:
+            import torch
+
+            d = torch.empty(self.space.ndof, dtype=torch.float64, device="cuda")
+        mfa_diagonal(self.ctx.h, self.h, d)
+        return d
+
+    def cg(self, b, x, precond=MFA_PC_JACOBI, rtol=1e-8, maxit=10000):
+        return mfa_cg(self.ctx.h, self.h, precond, b, x, rtol, maxit)
+
+    def __del__(self):
+        try:
+            if self.h:
+                mfa_form_destroy(self.h)
+        except Exception:
+            pass

@@ -1,0 +1,592 @@
+// C-ABI entry points of the mfa library (declared in include/mfa.h).
+//
+// The handles mirror the parloop of Section 2.2 of arXiv 1903.08243: a mesh
+// holds `coords` and `cell2vert`, a space holds `cell2dof`, a form holds the
+// element kernel's tables and stored geometry, and mfa_apply runs the global
+// assembly loop on the GPU.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mfa_internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define MFA_CUDA(call)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) return fail(MFA_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));  \
+  } while (0)
+
+int cuda_alloc(void** p, size_t bytes, const char* what) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(MFA_ERR_OOM, "cudaMalloc(%zu) for %s: out of device memory", bytes, what);
+  }
+  if (e != cudaSuccess) return fail(MFA_ERR_CUDA, "cudaMalloc for %s: %s", what, cudaGetErrorString(e));
+  return MFA_OK;
+}
+
+int nloc_of(int cell_type, int degree) {
+  if (cell_type == MFA_CELL_TET4) return degree == 1 ? 4 : (degree == 2 ? 10 : -1);
+  if (cell_type == MFA_CELL_HEX8 && degree >= 1 && degree <= 8) return (degree + 1) * (degree + 1) * (degree + 1);
+  return -1;
+}
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Algorithmic FP operations of one apply (an FMA counts 2), following the
+// kernels' arithmetic, which is the operation count of the definitions after
+// sum factorisation (hex) or per-point evaluation (tet).
+void count_work(mfa_form* f) {
+  const mfa_space* sp = f->space;
+  const int64_t ncell = sp->mesh->ncell;
+  const int64_t ndof = sp->nnode * sp->ncomp;
+  const int kind = f->p.kind;
+  double per_cell = 0.0, bytes = 0.0;
+  if (sp->mesh->cell_type == MFA_CELL_HEX8) {
+    const double n = sp->degree + 1, q = f->nq1;
+    const double sweeps = 2.0 * (q * n * n * n + q * q * n * n + q * q * q * n);  // one direction set
+    per_cell = 2.0 * sweeps + n * n * n;                                            // B, B^T and the scatter add
+    if (kind != MFA_FORM_MASS) per_cell += 12.0 * q * q * q * q + 15.0 * q * q * q;  // D, D^T, G g
+    if (kind != MFA_FORM_LAPLACE) per_cell += q * q * q;                            // c0 w|J| u
+    bytes = ncell * (4.0 * n * n * n + 8.0 * mfa::hex_geom_entries(kind) * q * q * q);
+  } else {
+    const double nl = sp->nloc, nc = sp->ncomp, nq = f->nq;
+    double per_q = 0.0;
+    const bool value = kind == MFA_FORM_MASS || kind == MFA_FORM_HELMHOLTZ;
+    const bool grad = kind != MFA_FORM_MASS;
+    if (value) per_q += 2.0 * nl * nc + 2.0 * nl * nc + 2.0 * nc;  // interpolate, integrate, scale
+    if (grad) per_q += 6.0 * nl * nc + 6.0 * nl * nc;              // reference gradient in and out
+    if (kind <= MFA_FORM_HELMHOLTZ && grad) per_q += nc * (15.0 + 18.0);
+    if (kind == MFA_FORM_ELASTICITY) per_q += 45.0 + 23.0 + 54.0;
+    if (kind == MFA_FORM_HYPER_RES) per_q += 45.0 + 54.0 + (f->p.law == MFA_LAW_SVK ? 100.0 : 60.0) + 6.0;
+    if (kind == MFA_FORM_HYPER_JAC) per_q += 45.0 + 45.0 + 6.0 * nl * 3 + 54.0 + (f->p.law == MFA_LAW_SVK ? 190.0 : 170.0);
+    per_cell = nq * per_q + 60.0 + nl * nc;  // affine geometry + scatter adds
+    bytes = ncell * (4.0 * nl + 16.0) + 24.0 * sp->mesh->nvert;
+    if (kind == MFA_FORM_HYPER_JAC) bytes += 8.0 * ndof;
+  }
+  bytes += 16.0 * ndof;  // x read once, y written once
+  if (f->scatter == MFA_SCATTER_COLOUR) bytes += 4.0 * ncell;
+  f->flops = per_cell * ncell;
+  f->bytes = bytes;
+}
+
+int build_colouring(mfa_space* sp) {
+  if (sp->d_colour_cells) return MFA_OK;
+  const int64_t ncell = sp->mesh->ncell;
+  std::vector<int32_t> map((size_t)ncell * sp->nloc);
+  MFA_CUDA(cudaMemcpy(map.data(), sp->d_cell_node, map.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  std::vector<int32_t> order;
+  std::vector<int64_t> offsets;
+  const int ncol = mfa::greedy_colour(ncell, sp->nloc, map.data(), sp->nnode, order, offsets);
+  if (ncol <= 0) return fail(MFA_ERR_UNSUPPORTED, "greedy colouring needs more than 64 colours");
+  int rc = cuda_alloc((void**)&sp->d_colour_cells, order.size() * sizeof(int32_t), "colour lists");
+  if (rc) return rc;
+  MFA_CUDA(cudaMemcpy(sp->d_colour_cells, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  sp->ncolours = ncol;
+  sp->colour_offsets = offsets;
+  return MFA_OK;
+}
+
+int hex_tables(mfa_form* f) {
+  const int n = f->space->degree + 1, q = f->nq1;
+  double gll[mfa::kMaxN], xg[mfa::kMaxN], wg[mfa::kMaxN];
+  mfa::gll01(n, gll);
+  mfa::gauss_legendre01(q, xg, wg);
+  mfa::lagrange_matrix(n, gll, q, xg, f->hex.B);
+  mfa::collocation_derivative(q, xg, f->hex.D);
+  for (int i = 0; i < q; ++i) {
+    f->hex.x1[i] = xg[i];
+    f->hex.w1[i] = wg[i];
+  }
+  return MFA_OK;
+}
+
+// Tet rule: polynomial integrands of degree <= qdeg are integrated exactly by
+// any exact rule, so the kernel takes the cheapest exact one it has; other
+// integrands (neo-Hookean, under-integration) use the conical-product rule
+// of degree qdeg, which defines the result.
+int tet_tables(mfa_form* f) {
+  const int p = f->space->degree, kind = f->p.kind;
+  int qdeg = f->p.qdeg;
+  if (qdeg <= 0) qdeg = (kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC) ? 4 : 2 * p;
+  int poly = -1;  // integrand degree on affine cells (-1: not polynomial)
+  if (kind == MFA_FORM_MASS || kind == MFA_FORM_HELMHOLTZ) poly = 2 * p;
+  if (kind == MFA_FORM_LAPLACE || kind == MFA_FORM_ELASTICITY) poly = 2 * (p - 1);
+  if ((kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC) && f->p.law == MFA_LAW_SVK) poly = 4 * (p - 1);
+  double pts[mfa::kTetMaxQ * 3];
+  int nq;
+  if (poly >= 0 && poly <= qdeg && poly <= 2) {
+    nq = mfa::tet_rule_4pt_deg2(pts, f->tet.w);
+  } else {
+    const int deg = (poly >= 0 && poly <= qdeg) ? poly : qdeg;
+    const int m = (deg + 2) / 2;
+    if (m * m * m > mfa::kTetMaxQ) return fail(MFA_ERR_UNSUPPORTED, "tet rule of degree %d needs %d points", deg, m * m * m);
+    nq = mfa::tet_rule_collapsed(deg, pts, f->tet.w);
+    if (nq != 27) return fail(MFA_ERR_UNSUPPORTED, "tet kernels are built for 4- and 27-point rules (got %d)", nq);
+  }
+  f->tet.nq = nq;
+  const int nl = f->space->nloc;
+  for (int i = 0; i < nq; ++i) mfa::tet_basis(p, pts + 3 * i, f->tet.phi + i * nl, f->tet.dphi + i * nl * 3);
+  f->nq = nq;
+  return MFA_OK;
+}
+
+mfa::TetApplyArgs tet_args(mfa_form* f, const double* x, double* y) {
+  mfa::TetApplyArgs a{};
+  a.x = x;
+  a.y = y;
+  a.coords = f->space->mesh->d_coords;
+  a.cell_vert = f->space->mesh->d_cell_vert;
+  a.cell_node = f->space->d_cell_node;
+  a.ucoef = f->d_coef;
+  a.cell_list = nullptr;
+  a.count = f->space->mesh->ncell;
+  a.k2 = f->p.k2;
+  a.lambda = f->p.lambda;
+  a.mu = f->p.mu;
+  a.b0 = f->p.b[0];
+  a.b1 = f->p.b[1];
+  a.b2 = f->p.b[2];
+  a.err = f->ctx->d_err;
+  return a;
+}
+
+int launch_apply(mfa_form* f, const double* x, double* y) {
+  mfa_space* sp = f->space;
+  mfa_ctx* ctx = f->ctx;
+  const bool colour = f->scatter == MFA_SCATTER_COLOUR;
+  const int ncol = colour ? sp->ncolours : 1;
+  for (int k = 0; k < ncol; ++k) {
+    const int32_t* list = colour ? sp->d_colour_cells + sp->colour_offsets[k] : nullptr;
+    const int64_t count = colour ? sp->colour_offsets[k + 1] - sp->colour_offsets[k] : sp->mesh->ncell;
+    cudaError_t e;
+    if (sp->mesh->cell_type == MFA_CELL_HEX8) {
+      mfa::HexApplyArgs a{x, y, sp->d_cell_node, f->d_geom, list, count, ctx->d_err};
+      e = mfa::hex_apply_launch(sp->degree + 1, f->nq1, f->p.kind, colour, f->hex, a, ctx->sm_count, ctx->stream);
+    } else {
+      mfa::TetApplyArgs a = tet_args(f, x, y);
+      a.cell_list = list;
+      a.count = count;
+      e = mfa::tet_apply_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, f->tet, a, ctx->sm_count,
+                                ctx->stream);
+    }
+    if (e != cudaSuccess) return fail(MFA_ERR_CUDA, "apply kernel launch: %s", cudaGetErrorString(e));
+  }
+  return MFA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mfa_last_error(void) { return g_err; }
+int mfa_version(void) { return MFA_VERSION; }
+
+int mfa_create(mfa_ctx** out, int device, void* stream) {
+  if (!out) return fail(MFA_ERR_ARG, "mfa_create: out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  MFA_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(MFA_ERR_ARG, "mfa_create: device %d of %d", device, ndev);
+  MFA_CUDA(cudaSetDevice(device));
+  mfa_ctx* c = new (std::nothrow) mfa_ctx();
+  if (!c) return fail(MFA_ERR_OOM, "mfa_create: host allocation");
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  int rc = e == cudaSuccess ? MFA_OK : fail(MFA_ERR_CUDA, "SM count: %s", cudaGetErrorString(e));
+  if (!rc) rc = cuda_alloc((void**)&c->d_err, sizeof(int), "error flag");
+  if (!rc) rc = cuda_alloc((void**)&c->d_scratch, sizeof(double) * (mfa::dot_partials() + 8), "dot scratch");
+  if (!rc && cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) rc = fail(MFA_ERR_CUDA, "memset error flag");
+  if (rc) {
+    mfa_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return MFA_OK;
+}
+
+int mfa_set_stream(mfa_ctx* ctx, void* stream) {
+  if (!ctx) return fail(MFA_ERR_ARG, "mfa_set_stream: ctx is NULL");
+  ctx->stream = (cudaStream_t)stream;
+  return MFA_OK;
+}
+
+int mfa_destroy(mfa_ctx* ctx) {
+  if (!ctx) return MFA_OK;
+  cudaSetDevice(ctx->device);
+  cudaFree(ctx->d_err);
+  cudaFree(ctx->d_scratch);
+  delete ctx;
+  return MFA_OK;
+}
+
+int mfa_mesh_upload(mfa_ctx* ctx, int cell_type, int64_t ncell, int64_t nvert, const double* coords,
+                    const int32_t* cell_vert, mfa_mesh** out) {
+  if (!ctx || !out || !coords || !cell_vert) return fail(MFA_ERR_ARG, "mfa_mesh_upload: NULL argument");
+  *out = nullptr;
+  if (cell_type != MFA_CELL_TET4 && cell_type != MFA_CELL_HEX8)
+    return fail(MFA_ERR_ARG, "mfa_mesh_upload: cell_type %d", cell_type);
+  if (ncell < 0 || nvert <= 0 || nvert > INT32_MAX || ncell > INT32_MAX)
+    return fail(MFA_ERR_ARG, "mfa_mesh_upload: ncell %lld nvert %lld", (long long)ncell, (long long)nvert);
+  for (int64_t i = 0; i < ncell * cell_type; ++i)
+    if (cell_vert[i] < 0 || cell_vert[i] >= nvert)
+      return fail(MFA_ERR_RANGE, "mfa_mesh_upload: cell_vert[%lld] = %d outside [0, %lld)", (long long)i,
+                  cell_vert[i], (long long)nvert);
+  MFA_CUDA(cudaSetDevice(ctx->device));
+  mfa_mesh* m = new (std::nothrow) mfa_mesh();
+  if (!m) return fail(MFA_ERR_OOM, "mfa_mesh_upload: host allocation");
+  m->ctx = ctx;
+  m->cell_type = cell_type;
+  m->ncell = ncell;
+  m->nvert = nvert;
+  int rc = cuda_alloc((void**)&m->d_coords, sizeof(double) * 3 * nvert, "coords");
+  if (!rc) rc = cuda_alloc((void**)&m->d_cell_vert, sizeof(int32_t) * cell_type * ncell, "cell_vert");
+  if (!rc && cudaMemcpy(m->d_coords, coords, sizeof(double) * 3 * nvert, cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = fail(MFA_ERR_CUDA, "mfa_mesh_upload: copy coords");
+  if (!rc && ncell > 0 &&
+      cudaMemcpy(m->d_cell_vert, cell_vert, sizeof(int32_t) * cell_type * ncell, cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = fail(MFA_ERR_CUDA, "mfa_mesh_upload: copy cell_vert");
+  if (rc) {
+    mfa_mesh_destroy(m);
+    return rc;
+  }
+  *out = m;
+  return MFA_OK;
+}
+
+int mfa_mesh_destroy(mfa_mesh* m) {
+  if (!m) return MFA_OK;
+  cudaSetDevice(m->ctx->device);
+  cudaFree(m->d_coords);
+  cudaFree(m->d_cell_vert);
+  delete m;
+  return MFA_OK;
+}
+
+int mfa_space_create(mfa_ctx* ctx, mfa_mesh* mesh, int degree, int ncomp, const int32_t* cell_node, int64_t nnode,
+                     mfa_space** out) {
+  if (!ctx || !mesh || !out || !cell_node) return fail(MFA_ERR_ARG, "mfa_space_create: NULL argument");
+  *out = nullptr;
+  const int nl = nloc_of(mesh->cell_type, degree);
+  if (nl < 0) return fail(MFA_ERR_UNSUPPORTED, "mfa_space_create: degree %d on cell type %d", degree, mesh->cell_type);
+  if (ncomp != 1 && ncomp != 3) return fail(MFA_ERR_ARG, "mfa_space_create: ncomp %d", ncomp);
+  if (nnode <= 0 || nnode * ncomp > INT32_MAX) return fail(MFA_ERR_ARG, "mfa_space_create: nnode %lld", (long long)nnode);
+  {
+    std::vector<int64_t> stamp(nnode, -1);
+    for (int64_t c = 0; c < mesh->ncell; ++c)
+      for (int a = 0; a < nl; ++a) {
+        const int32_t v = cell_node[c * nl + a];
+        if (v < 0 || v >= nnode)
+          return fail(MFA_ERR_RANGE, "mfa_space_create: cell_node[%lld][%d] = %d outside [0, %lld)", (long long)c, a, v,
+                      (long long)nnode);
+        if (stamp[v] == c)
+          return fail(MFA_ERR_ARG, "mfa_space_create: node %d repeated in cell %lld", v, (long long)c);
+        stamp[v] = c;
+      }
+  }
+  MFA_CUDA(cudaSetDevice(ctx->device));
+  mfa_space* s = new (std::nothrow) mfa_space();
+  if (!s) return fail(MFA_ERR_OOM, "mfa_space_create: host allocation");
+  s->ctx = ctx;
+  s->mesh = mesh;
+  s->degree = degree;
+  s->ncomp = ncomp;
+  s->nloc = nl;
+  s->nnode = nnode;
+  const size_t bytes = sizeof(int32_t) * nl * mesh->ncell;
+  int rc = cuda_alloc((void**)&s->d_cell_node, bytes, "cell_node");
+  if (!rc && bytes && cudaMemcpy(s->d_cell_node, cell_node, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = fail(MFA_ERR_CUDA, "mfa_space_create: copy cell_node");
+  if (rc) {
+    mfa_space_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return MFA_OK;
+}
+
+int mfa_space_ndof(const mfa_space* s, int64_t* ndof) {
+  if (!s || !ndof) return fail(MFA_ERR_ARG, "mfa_space_ndof: NULL argument");
+  *ndof = s->nnode * s->ncomp;
+  return MFA_OK;
+}
+
+int mfa_space_destroy(mfa_space* s) {
+  if (!s) return MFA_OK;
+  cudaSetDevice(s->ctx->device);
+  cudaFree(s->d_cell_node);
+  cudaFree(s->d_colour_cells);
+  delete s;
+  return MFA_OK;
+}
+
+int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa_form** out) {
+  if (!ctx || !sp || !prm || !out) return fail(MFA_ERR_ARG, "mfa_form_create: NULL argument");
+  *out = nullptr;
+  const double t0 = now_ms();
+  const int kind = prm->kind, ct = sp->mesh->cell_type;
+  if (kind < MFA_FORM_MASS || kind > MFA_FORM_HYPER_JAC) return fail(MFA_ERR_ARG, "mfa_form_create: kind %d", kind);
+  if (prm->scatter < MFA_SCATTER_AUTO || prm->scatter > MFA_SCATTER_ATOMIC)
+    return fail(MFA_ERR_ARG, "mfa_form_create: scatter %d", prm->scatter);
+  if (prm->law != MFA_LAW_SVK && prm->law != MFA_LAW_NEOHOOKE) return fail(MFA_ERR_ARG, "mfa_form_create: law %d", prm->law);
+  if (prm->precision != MFA_PREC_FP64)
+    return fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: precision %d (this build: FP64)", prm->precision);
+  if (kind >= MFA_FORM_ELASTICITY && sp->ncomp != 3)
+    return fail(MFA_ERR_ARG, "mfa_form_create: form %d needs a 3-component space", kind);
+  if (ct == MFA_CELL_HEX8 && (sp->ncomp != 1 || kind > MFA_FORM_HELMHOLTZ))
+    return fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: hex kernels cover scalar mass/Laplace/Helmholtz");
+  if (ct == MFA_CELL_TET4) {
+    const bool ok = (sp->degree == 1 && sp->ncomp == 1 && kind <= MFA_FORM_HELMHOLTZ) ||
+                    (sp->degree == 2 && sp->ncomp == 1 && kind <= MFA_FORM_HELMHOLTZ) ||
+                    (sp->degree == 2 && sp->ncomp == 3 && kind >= MFA_FORM_LAPLACE && kind != MFA_FORM_HELMHOLTZ);
+    if (!ok) return fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: form %d on P%d x %d", kind, sp->degree, sp->ncomp);
+  }
+  MFA_CUDA(cudaSetDevice(ctx->device));
+  mfa_form* f = new (std::nothrow) mfa_form();
+  if (!f) return fail(MFA_ERR_OOM, "mfa_form_create: host allocation");
+  f->ctx = ctx;
+  f->space = sp;
+  f->p = *prm;
+  f->scatter = prm->scatter == MFA_SCATTER_COLOUR ? MFA_SCATTER_COLOUR : MFA_SCATTER_ATOMIC;
+  int rc = MFA_OK;
+  if (ct == MFA_CELL_HEX8) {
+    const int n = sp->degree + 1;
+    f->nq1 = prm->qdeg > 0 ? prm->qdeg : n;
+    if (!(f->nq1 == n || (f->nq1 == n + 1 && n <= 7)) || n > 9)
+      rc = fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: Q%d with %d Gauss points per direction", sp->degree, f->nq1);
+    if (!rc) rc = hex_tables(f);
+    f->nq = f->nq1 * f->nq1 * f->nq1;
+    if (!rc) {
+      const int ng = mfa::hex_geom_entries(kind);
+      rc = cuda_alloc((void**)&f->d_geom, sizeof(double) * ng * f->nq * sp->mesh->ncell, "geometric factors");
+      const double c0 = kind == MFA_FORM_HELMHOLTZ ? prm->k2 : 1.0;
+      if (!rc) {
+        cudaError_t e = mfa::hex_geometry_launch(f->nq1, kind, c0, f->hex, sp->mesh->d_coords, sp->mesh->d_cell_vert,
+                                                 sp->mesh->ncell, f->d_geom, ctx->d_err, ctx->stream);
+        if (e != cudaSuccess) rc = fail(MFA_ERR_CUDA, "geometry kernel: %s", cudaGetErrorString(e));
+      }
+      if (!rc) rc = mfa_sync(ctx);
+    }
+  } else {
+    rc = tet_tables(f);
+  }
+  if (!rc && f->scatter == MFA_SCATTER_COLOUR) rc = build_colouring(sp);
+  if (rc) {
+    mfa_form_destroy(f);
+    return rc;
+  }
+  count_work(f);
+  f->setup_ms = now_ms() - t0;
+  *out = f;
+  return MFA_OK;
+}
+
+int mfa_form_set_coefficient(mfa_form* f, const double* u) {
+  if (!f || !u) return fail(MFA_ERR_ARG, "mfa_form_set_coefficient: NULL argument");
+  f->d_coef = u;
+  return MFA_OK;
+}
+
+int mfa_form_get_info(const mfa_form* f, mfa_form_info* info) {
+  if (!f || !info) return fail(MFA_ERR_ARG, "mfa_form_get_info: NULL argument");
+  info->ncell = f->space->mesh->ncell;
+  info->ndof = f->space->nnode * f->space->ncomp;
+  info->nloc = f->space->nloc;
+  info->nq = f->nq;
+  info->ncolours = f->space->ncolours;
+  info->scatter = f->scatter;
+  info->flops = f->flops;
+  info->bytes = f->bytes;
+  info->setup_ms = f->setup_ms;
+  return MFA_OK;
+}
+
+int mfa_form_destroy(mfa_form* f) {
+  if (!f) return MFA_OK;
+  cudaSetDevice(f->ctx->device);
+  cudaFree(f->d_geom);
+  cudaFree(f->d_stage_x);
+  cudaFree(f->d_stage_y);
+  delete f;
+  return MFA_OK;
+}
+
+int mfa_apply(mfa_ctx* ctx, mfa_form* f, const double* x, double* y, int accumulate) {
+  if (!ctx || !f || !x || !y) return fail(MFA_ERR_ARG, "mfa_apply: NULL argument");
+  if (f->ctx != ctx) return fail(MFA_ERR_ARG, "mfa_apply: form belongs to another context");
+  if ((const void*)x == (const void*)y) return fail(MFA_ERR_ARG, "mfa_apply: x and y alias");
+  if (f->p.kind == MFA_FORM_HYPER_JAC && !f->d_coef)
+    return fail(MFA_ERR_ARG, "mfa_apply: HYPER_JAC needs mfa_form_set_coefficient");
+  MFA_CUDA(cudaSetDevice(ctx->device));
+  const int64_t ndof = f->space->nnode * f->space->ncomp;
+  if (!accumulate) MFA_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * ndof, ctx->stream));
+  return launch_apply(f, x, y);
+}
+
+int mfa_apply_host(mfa_ctx* ctx, mfa_form* f, const double* xh, double* yh) {
+  if (!ctx || !f || !xh || !yh) return fail(MFA_ERR_ARG, "mfa_apply_host: NULL argument");
+  MFA_CUDA(cudaSetDevice(ctx->device));
+  const int64_t ndof = f->space->nnode * f->space->ncomp;
+  int rc = MFA_OK;
+  if (!f->d_stage_x) rc = cuda_alloc((void**)&f->d_stage_x, sizeof(double) * ndof, "staging x");
+  if (!rc && !f->d_stage_y) rc = cuda_alloc((void**)&f->d_stage_y, sizeof(double) * ndof, "staging y");
+  if (rc) return rc;
+  MFA_CUDA(cudaMemcpyAsync(f->d_stage_x, xh, sizeof(double) * ndof, cudaMemcpyHostToDevice, ctx->stream));
+  rc = mfa_apply(ctx, f, f->d_stage_x, f->d_stage_y, 0);
+  if (rc) return rc;
+  MFA_CUDA(cudaMemcpyAsync(yh, f->d_stage_y, sizeof(double) * ndof, cudaMemcpyDeviceToHost, ctx->stream));
+  return mfa_sync(ctx);
+}
+
+int mfa_sync(mfa_ctx* ctx) {
+  if (!ctx) return fail(MFA_ERR_ARG, "mfa_sync: ctx is NULL");
+  MFA_CUDA(cudaSetDevice(ctx->device));
+  MFA_CUDA(cudaStreamSynchronize(ctx->stream));
+  int flag = 0;
+  MFA_CUDA(cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    MFA_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    return fail(MFA_ERR_DOMAIN, "kernel reported %s%s", (flag & 1) ? "det J == 0 or non-finite " : "",
+                (flag & 2) ? "deformation with J <= 0" : "");
+  }
+  return MFA_OK;
+}
+
+int mfa_diagonal(mfa_ctx* ctx, mfa_form* f, double* d) {
+  if (!ctx || !f || !d) return fail(MFA_ERR_ARG, "mfa_diagonal: NULL argument");
+  if (f->p.kind == MFA_FORM_HYPER_RES || f->p.kind == MFA_FORM_HYPER_JAC)
+    return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: linear forms only");
+  MFA_CUDA(cudaSetDevice(ctx->device));
+  mfa_space* sp = f->space;
+  const int64_t ndof = sp->nnode * sp->ncomp;
+  MFA_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * ndof, ctx->stream));
+  cudaError_t e;
+  if (sp->mesh->cell_type == MFA_CELL_HEX8) {
+    e = mfa::hex_diagonal_launch(sp->degree + 1, f->nq1, f->p.kind, f->hex, sp->d_cell_node, f->d_geom,
+                                 sp->mesh->ncell, d, ctx->sm_count, ctx->stream);
+  } else {
+    mfa::TetApplyArgs a = tet_args(f, nullptr, nullptr);
+    e = mfa::tet_diagonal_launch(sp->degree, sp->ncomp, f->p.kind, f->tet, a, d, ctx->stream);
+  }
+  if (e != cudaSuccess) return fail(MFA_ERR_CUDA, "diagonal kernel: %s", cudaGetErrorString(e));
+  return MFA_OK;
+}
+
+int mfa_cg(mfa_ctx* ctx, mfa_form* f, int precond, const double* b, double* x, double rtol, int maxit, int* iters,
+           double* relres) {
+  if (!ctx || !f || !b || !x) return fail(MFA_ERR_ARG, "mfa_cg: NULL argument");
+  if (precond != MFA_PC_NONE && precond != MFA_PC_JACOBI) return fail(MFA_ERR_ARG, "mfa_cg: precond %d", precond);
+  if (f->p.kind > MFA_FORM_ELASTICITY && f->p.kind != MFA_FORM_HYPER_JAC)
+    return fail(MFA_ERR_ARG, "mfa_cg: the residual form is not linear");
+  if (!(rtol > 0.0) || maxit < 0) return fail(MFA_ERR_ARG, "mfa_cg: rtol %g maxit %d", rtol, maxit);
+  MFA_CUDA(cudaSetDevice(ctx->device));
+  const int64_t n = f->space->nnode * f->space->ncomp;
+  cudaStream_t s = ctx->stream;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *dinv = nullptr;
+  int rc = cuda_alloc((void**)&r, n * 8, "cg r");
+  if (!rc) rc = cuda_alloc((void**)&z, n * 8, "cg z");
+  if (!rc) rc = cuda_alloc((void**)&p, n * 8, "cg p");
+  if (!rc) rc = cuda_alloc((void**)&q, n * 8, "cg q");
+  if (!rc && precond == MFA_PC_JACOBI) rc = cuda_alloc((void**)&dinv, n * 8, "cg diag");
+  double* partial = ctx->d_scratch;
+  double* dres = ctx->d_scratch + mfa::dot_partials();
+  auto dot = [&](const double* u, const double* v, double* out) -> int {
+    cudaError_t e = mfa::dot_launch(u, v, n, partial, dres, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dres, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? MFA_OK : fail(MFA_ERR_CUDA, "mfa_cg dot: %s", cudaGetErrorString(e));
+  };
+  auto precondition = [&](const double* in, double* outv) -> int {
+    cudaError_t e = precond == MFA_PC_JACOBI ? mfa::pointwise_mul_launch(dinv, in, outv, n, s)
+                                             : cudaMemcpyAsync(outv, in, n * 8, cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? MFA_OK : fail(MFA_ERR_CUDA, "mfa_cg precondition: %s", cudaGetErrorString(e));
+  };
+  int it = 0;
+  double bnorm = 0.0, rr = 0.0, rz = 0.0, res = 0.0;
+  if (!rc && precond == MFA_PC_JACOBI) {
+    rc = mfa_diagonal(ctx, f, dinv);
+    if (!rc && mfa::reciprocal_launch(dinv, dinv, n, s) != cudaSuccess) rc = fail(MFA_ERR_CUDA, "mfa_cg: reciprocal");
+  }
+  if (!rc) rc = dot(b, b, &bnorm);
+  if (!rc) {
+    bnorm = std::sqrt(bnorm);
+    rc = mfa_apply(ctx, f, x, r, 0);  // r = b - A x
+  }
+  if (!rc && mfa::axpby_launch(1.0, b, -1.0, r, n, s) != cudaSuccess) rc = fail(MFA_ERR_CUDA, "mfa_cg: axpby");
+  if (!rc) rc = dot(r, r, &rr);
+  if (!rc) rc = precondition(r, z);
+  if (!rc) rc = dot(r, z, &rz);
+  if (!rc && cudaMemcpyAsync(p, z, n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) rc = fail(MFA_ERR_CUDA, "copy");
+  res = bnorm > 0.0 ? std::sqrt(rr) / bnorm : std::sqrt(rr);
+  while (!rc && res > rtol && it < maxit) {
+    double pq = 0.0;
+    rc = mfa_apply(ctx, f, p, q, 0);
+    if (!rc) rc = dot(p, q, &pq);
+    if (rc) break;
+    if (!(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(rz)) {
+      rc = fail(MFA_ERR_BREAKDOWN, "mfa_cg: breakdown at iteration %d (p.Ap = %g)", it, pq);
+      break;
+    }
+    const double alpha = rz / pq;
+    if (mfa::axpby_launch(alpha, p, 1.0, x, n, s) != cudaSuccess ||
+        mfa::axpby_launch(-alpha, q, 1.0, r, n, s) != cudaSuccess) {
+      rc = fail(MFA_ERR_CUDA, "mfa_cg: update");
+      break;
+    }
+    rc = dot(r, r, &rr);
+    ++it;
+    if (rc) break;
+    if (!std::isfinite(rr)) {
+      rc = fail(MFA_ERR_BREAKDOWN, "mfa_cg: non-finite residual at iteration %d", it);
+      break;
+    }
+    res = bnorm > 0.0 ? std::sqrt(rr) / bnorm : std::sqrt(rr);
+    if (res <= rtol) break;
+    double rz_new = 0.0;
+    rc = precondition(r, z);
+    if (!rc) rc = dot(r, z, &rz_new);
+    if (rc) break;
+    const double beta = rz_new / rz;
+    rz = rz_new;
+    if (mfa::axpby_launch(1.0, z, beta, p, n, s) != cudaSuccess) {
+      rc = fail(MFA_ERR_CUDA, "mfa_cg: direction update");
+      break;
+    }
+  }
+  if (!rc) {
+    int r2 = mfa_sync(ctx);
+    if (r2) rc = r2;
+  }
+  if (!rc && res > rtol) rc = fail(MFA_ERR_NOT_CONVERGED, "mfa_cg: relative residual %g after %d iterations", res, it);
+  if (iters) *iters = it;
+  if (relres) *relres = res;
+  cudaFree(r);
+  cudaFree(z);
+  cudaFree(p);
+  cudaFree(q);
+  cudaFree(dinv);
+  return rc;
+}
+
+}  // extern "C"

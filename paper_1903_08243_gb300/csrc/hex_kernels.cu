@@ -1,0 +1,161 @@
+// Hexahedral kernels: geometry precompute and dispatch of the sum-factorised
+// action (see hex_kernels.cuh for the algorithm).
+#include "hex_kernels.cuh"
+
+namespace mfa {
+
+int hex_geom_entries(int kind) {
+  return kind == MFA_FORM_MASS ? 1 : (kind == MFA_FORM_LAPLACE ? 6 : 7);
+}
+
+namespace {
+
+// Per Gauss point of a trilinear cell: J = sum_v X_v (grad_ref N_v)^T, then
+// G = w|det J| J^{-1} J^{-T} (6 entries) and c0 w|det J| (Sections 2.1 and
+// 4.1: the Jacobian of a bilinear/trilinear map is evaluated at every
+// quadrature point).  Computed once in FP64 and stored [cell][entry][q].
+__global__ void hex_geometry_kernel(const __grid_constant__ HexTables tb, int nq1, int ng, double c0, const double* __restrict__ coords,
+                                    const int32_t* __restrict__ cell_vert, int64_t ncell, double* __restrict__ geom,
+                                    int* err) {
+  const int pq = nq1 * nq1 * nq1;
+  const int64_t total = ncell * pq;
+  for (int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gid < total;
+       gid += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = gid / pq;
+    const int q = (int)(gid - cell * pq);
+    const int qi = q % nq1, qj = (q / nq1) % nq1, qk = q / (nq1 * nq1);
+    const double xi[3] = {tb.x1[qi], tb.x1[qj], tb.x1[qk]};
+    const double w = tb.w1[qi] * tb.w1[qj] * tb.w1[qk];
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int v = 0; v < 8; ++v) {
+      const int32_t vid = cell_vert[cell * 8 + v];
+      const int bits[3] = {v & 1, (v >> 1) & 1, (v >> 2) & 1};
+      double f[3], df[3];
+      for (int d = 0; d < 3; ++d) {
+        f[d] = bits[d] ? xi[d] : 1.0 - xi[d];
+        df[d] = bits[d] ? 1.0 : -1.0;
+      }
+      const double dN[3] = {df[0] * f[1] * f[2], f[0] * df[1] * f[2], f[0] * f[1] * df[2]};
+      for (int d = 0; d < 3; ++d) {
+        const double X = coords[3 * (int64_t)vid + d];
+        for (int e = 0; e < 3; ++e) J[d][e] += X * dN[e];
+      }
+    }
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    if (!(det != 0.0) || !isfinite(det)) {
+      atomicOr(err, 1);
+      for (int e = 0; e < ng; ++e) geom[(cell * ng + e) * pq + q] = 0.0;
+      continue;
+    }
+    // inverse by the adjugate: Ji[i][j] = cof[j][i] / det
+    double Ji[3][3];
+    Ji[0][0] = c00 / det;
+    Ji[1][0] = c01 / det;
+    Ji[2][0] = c02 / det;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    const double wdet = w * fabs(det);
+    double* out = geom + cell * ng * pq + q;
+    if (ng == 1) {
+      out[0] = c0 * wdet;
+      continue;
+    }
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    for (int e = 0; e < 6; ++e) {
+      const int r = ia[e], c = ib[e];
+      out[e * pq] = wdet * (Ji[r][0] * Ji[c][0] + Ji[r][1] * Ji[c][1] + Ji[r][2] * Ji[c][2]);
+    }
+    if (ng == 7) out[6 * pq] = c0 * wdet;
+  }
+}
+
+}  // namespace
+
+cudaError_t hex_geometry_launch(int nq, int kind, double c0, const HexTables& tb, const double* coords,
+                                const int32_t* cell_vert, int64_t ncell, double* geom, int* err, cudaStream_t s) {
+  const int64_t total = ncell * nq * nq * nq;
+  if (total == 0) return cudaSuccess;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 65535 * 8) blocks = 65535 * 8;
+  hex_geometry_kernel<<<(unsigned)blocks, 256, 0, s>>>(tb, nq, hex_geom_entries(kind), c0, coords, cell_vert, ncell,
+                                                       geom, err);
+  return cudaGetLastError();
+}
+
+#define MFA_HEX_CASE(NN, NQQ)                                                                         \
+  if (n == NN && nq == NQQ) {                                                                         \
+    switch (kind) {                                                                                   \
+      case MFA_FORM_MASS:                                                                             \
+        return colour ? hexk::launch_apply<NN, NQQ, MFA_FORM_MASS, true>(tb, a, sm_count, s)          \
+                      : hexk::launch_apply<NN, NQQ, MFA_FORM_MASS, false>(tb, a, sm_count, s);        \
+      case MFA_FORM_LAPLACE:                                                                          \
+        return colour ? hexk::launch_apply<NN, NQQ, MFA_FORM_LAPLACE, true>(tb, a, sm_count, s)       \
+                      : hexk::launch_apply<NN, NQQ, MFA_FORM_LAPLACE, false>(tb, a, sm_count, s);     \
+      case MFA_FORM_HELMHOLTZ:                                                                        \
+        return colour ? hexk::launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, true>(tb, a, sm_count, s)     \
+                      : hexk::launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, false>(tb, a, sm_count, s);   \
+      default:                                                                                        \
+        return cudaErrorInvalidValue;                                                                 \
+    }                                                                                                 \
+  }
+
+cudaError_t hex_apply_launch(int n, int nq, int kind, bool colour, const HexTables& tb, const HexApplyArgs& a,
+                             int sm_count, cudaStream_t s) {
+  MFA_HEX_CASE(2, 2)
+  MFA_HEX_CASE(3, 3)
+  MFA_HEX_CASE(4, 4)
+  MFA_HEX_CASE(5, 5)
+  MFA_HEX_CASE(6, 6)
+  MFA_HEX_CASE(7, 7)
+  MFA_HEX_CASE(8, 8)
+  MFA_HEX_CASE(9, 9)
+  MFA_HEX_CASE(2, 3)
+  MFA_HEX_CASE(3, 4)
+  MFA_HEX_CASE(4, 5)
+  MFA_HEX_CASE(5, 6)
+  MFA_HEX_CASE(6, 7)
+  MFA_HEX_CASE(7, 8)
+  return cudaErrorInvalidValue;
+}
+
+#define MFA_HEX_DIAG_CASE(NN, NQQ)                                                                    \
+  if (n == NN && nq == NQQ) {                                                                         \
+    switch (kind) {                                                                                   \
+      case MFA_FORM_MASS:                                                                             \
+        return hexk::launch_diag<NN, NQQ, MFA_FORM_MASS>(tb, cell_node, geom, ncell, d, sm_count, s); \
+      case MFA_FORM_LAPLACE:                                                                          \
+        return hexk::launch_diag<NN, NQQ, MFA_FORM_LAPLACE>(tb, cell_node, geom, ncell, d, sm_count, s); \
+      case MFA_FORM_HELMHOLTZ:                                                                        \
+        return hexk::launch_diag<NN, NQQ, MFA_FORM_HELMHOLTZ>(tb, cell_node, geom, ncell, d, sm_count, s); \
+      default:                                                                                        \
+        return cudaErrorInvalidValue;                                                                 \
+    }                                                                                                 \
+  }
+
+cudaError_t hex_diagonal_launch(int n, int nq, int kind, const HexTables& tb, const int32_t* cell_node,
+                                const double* geom, int64_t ncell, double* d, int sm_count, cudaStream_t s) {
+  MFA_HEX_DIAG_CASE(2, 2)
+  MFA_HEX_DIAG_CASE(3, 3)
+  MFA_HEX_DIAG_CASE(4, 4)
+  MFA_HEX_DIAG_CASE(5, 5)
+  MFA_HEX_DIAG_CASE(6, 6)
+  MFA_HEX_DIAG_CASE(7, 7)
+  MFA_HEX_DIAG_CASE(8, 8)
+  MFA_HEX_DIAG_CASE(9, 9)
+  MFA_HEX_DIAG_CASE(2, 3)
+  MFA_HEX_DIAG_CASE(3, 4)
+  MFA_HEX_DIAG_CASE(4, 5)
+  MFA_HEX_DIAG_CASE(5, 6)
+  MFA_HEX_DIAG_CASE(6, 7)
+  MFA_HEX_DIAG_CASE(7, 8)
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace mfa

@@ -1,0 +1,302 @@
+// Sum-factorised FP64 operator action on Q_p hexahedra (mass, Laplacian,
+// Helmholtz), one CUDA thread per tensor point of a cell.
+//
+// Local assembly (Section 2.1 of arXiv 1903.08243) on a tensor-product cell
+// factorises into 1D contractions (the sum factorisation TSFC applies to
+// tensor-product elements, Sections 3 and 4.2.4):
+//   u_q   = (B x B x B) u                  values at Gauss points, 3 sweeps
+//   g_d   = D_d u_q                        collocation derivatives, 3 sweeps
+//   f     = G(q) g  (+ c0 w|J| u_q)        pointwise physics with stored geometry
+//   r     = sum_d D_d^T f_d (+ mass term)  3 transposed sweeps
+//   y_loc = (B^T x B^T x B^T) r            3 transposed sweeps
+// B is the GLL-node basis at the Gauss points and D the derivative of the
+// Lagrange basis on the Gauss points, so that D B equals the derivative of
+// the node basis at the Gauss points.
+//
+// The FP64 pipe of GB300 issues 2 DFMA lanes per clock per SM, about 1/64 of
+// the FP32 rate; every other instruction class (loads, shared memory,
+// integer) is nearly free by comparison.  So the kernel minimises FP64
+// operations: geometry is precomputed once in FP64 and read per point
+// (56 B per point against ~70 DFMA), and the 12 n^4 DFMA of the contractions
+// are the only FP64 work besides ~10 per point for the physics.
+//
+// Cross-element batching (Section 3.1) maps to CB cells per thread block,
+// each cell a slab of n^3 threads; blocks loop persistently over batches.
+#pragma once
+
+#include "mfa_internal.h"
+
+namespace mfa {
+namespace hexk {
+
+constexpr int ceil32(int x) { return (x + 31) / 32 * 32; }
+
+template <int N, int NQ>
+struct Shape {
+  static constexpr int PN = N * N * N;
+  static constexpr int PQ = NQ * NQ * NQ;
+  static constexpr int M = N > NQ ? N : NQ;
+  static constexpr int P = M * M * M;
+  static constexpr int CB = P <= 128 ? 256 / P : 1;  // cells per block
+  static constexpr int T = ceil32(CB * P);           // threads per block
+  static constexpr int SMEM = (NQ * N + NQ * NQ + 2 * CB * P + 3 * CB * PQ) * 8;
+};
+
+template <int KIND>
+__host__ __device__ constexpr int geom_entries() {
+  return KIND == MFA_FORM_MASS ? 1 : (KIND == MFA_FORM_LAPLACE ? 6 : 7);
+}
+
+template <int N, int NQ, int KIND, bool COLOUR>
+__global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_kernel(const __grid_constant__ HexTables tb, const HexApplyArgs a) {
+  using S = Shape<N, NQ>;
+  constexpr int P = S::P, PN = S::PN, PQ = S::PQ, CB = S::CB;
+  constexpr int NG = geom_entries<KIND>();
+  extern __shared__ double smem[];
+  double* sB = smem;              // [NQ][N]
+  double* sD = sB + NQ * N;       // [NQ][NQ]
+  double* bufA = sD + NQ * NQ;    // [CB][P]
+  double* bufB = bufA + CB * P;   // [CB][P]
+  double* F = bufB + CB * P;      // [3][CB][PQ]
+  const int t = threadIdx.x;
+  for (int i = t; i < NQ * N; i += blockDim.x) sB[i] = tb.B[i];
+  for (int i = t; i < NQ * NQ; i += blockDim.x) sD[i] = tb.D[i];
+
+  const int cl = t / P;  // cell slot of this thread
+  const int pt = t - cl * P;
+  double* A = bufA + cl * P;
+  double* Bf = bufB + cl * P;
+  double* F0 = F + cl * PQ;
+  double* F1 = F0 + CB * PQ;
+  double* F2 = F1 + CB * PQ;
+  const int64_t nbatch = (a.count + CB - 1) / CB;
+
+  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
+    const int64_t idx = batch * CB + cl;
+    const bool valid = (cl < CB) && (idx < a.count);
+    int64_t cell = 0;
+    if (valid) cell = a.cell_list ? (int64_t)__ldg(a.cell_list + idx) : idx;
+
+    // gather x through the cell->node map; keep the node for the scatter
+    int32_t node = 0;
+    if (valid && pt < PN) {
+      node = __ldg(a.cell_node + cell * PN + pt);
+      A[pt] = __ldg(a.x + node);
+    }
+    // stored geometric factors of this point (consumed after three sweeps)
+    double g[NG];
+    if (valid && pt < PQ) {
+#pragma unroll
+      for (int e = 0; e < NG; ++e) g[e] = __ldg(a.geom + (cell * NG + e) * PQ + pt);
+    }
+    __syncthreads();
+
+    // B in x: (NQ, N, N) <- (N, N, N)
+    if (valid && pt < NQ * N * N) {
+      const int i = pt % NQ, jk = pt / NQ;
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < N; ++m) s = fma(sB[i * N + m], A[m + N * jk], s);
+      Bf[pt] = s;
+    }
+    __syncthreads();
+    // B in y: (NQ, NQ, N) <- (NQ, N, N)
+    if (valid && pt < NQ * NQ * N) {
+      const int i = pt % NQ, j = (pt / NQ) % NQ, k = pt / (NQ * NQ);
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < N; ++m) s = fma(sB[j * N + m], Bf[i + NQ * (m + N * k)], s);
+      A[pt] = s;
+    }
+    __syncthreads();
+    // B in z: (NQ, NQ, NQ) <- (NQ, NQ, N)
+    if (valid && pt < PQ) {
+      const int ij = pt % (NQ * NQ), k = pt / (NQ * NQ);
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < N; ++m) s = fma(sB[k * N + m], A[ij + NQ * NQ * m], s);
+      Bf[pt] = s;
+    }
+    __syncthreads();
+
+    if constexpr (KIND == MFA_FORM_MASS) {
+      if (valid && pt < PQ) A[pt] = g[0] * Bf[pt];
+    } else {
+      double v0 = 0.0;
+      if (valid && pt < PQ) {
+        const int i = pt % NQ, j = (pt / NQ) % NQ, k = pt / (NQ * NQ);
+        double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+#pragma unroll
+        for (int m = 0; m < NQ; ++m) {
+          d0 = fma(sD[i * NQ + m], Bf[m + NQ * (j + NQ * k)], d0);
+          d1 = fma(sD[j * NQ + m], Bf[i + NQ * (m + NQ * k)], d1);
+          d2 = fma(sD[k * NQ + m], Bf[i + NQ * (j + NQ * m)], d2);
+        }
+        // G = w|J| J^{-1} J^{-T}: (00, 11, 22, 01, 02, 12)
+        F0[pt] = fma(g[0], d0, fma(g[3], d1, g[4] * d2));
+        F1[pt] = fma(g[3], d0, fma(g[1], d1, g[5] * d2));
+        F2[pt] = fma(g[4], d0, fma(g[5], d1, g[2] * d2));
+        if constexpr (KIND == MFA_FORM_HELMHOLTZ) v0 = g[6] * Bf[pt];
+      }
+      __syncthreads();
+      if (valid && pt < PQ) {
+        const int i = pt % NQ, j = (pt / NQ) % NQ, k = pt / (NQ * NQ);
+        double r = v0;
+#pragma unroll
+        for (int m = 0; m < NQ; ++m) {
+          r = fma(sD[m * NQ + i], F0[m + NQ * (j + NQ * k)], r);
+          r = fma(sD[m * NQ + j], F1[i + NQ * (m + NQ * k)], r);
+          r = fma(sD[m * NQ + k], F2[i + NQ * (j + NQ * m)], r);
+        }
+        A[pt] = r;
+      }
+    }
+    __syncthreads();
+
+    // B^T in z: (NQ, NQ, N) <- (NQ, NQ, NQ)
+    if (valid && pt < NQ * NQ * N) {
+      const int ij = pt % (NQ * NQ), c = pt / (NQ * NQ);
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < NQ; ++m) s = fma(sB[m * N + c], A[ij + NQ * NQ * m], s);
+      Bf[pt] = s;
+    }
+    __syncthreads();
+    // B^T in y: (NQ, N, N) <- (NQ, NQ, N)
+    if (valid && pt < NQ * N * N) {
+      const int i = pt % NQ, b = (pt / NQ) % N, c = pt / (NQ * N);
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < NQ; ++m) s = fma(sB[m * N + b], Bf[i + NQ * (m + NQ * c)], s);
+      A[pt] = s;
+    }
+    __syncthreads();
+    // B^T in x and scatter-add: (N, N, N) <- (NQ, N, N)
+    if (valid && pt < PN) {
+      const int i = pt % N, bc = pt / N;
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < NQ; ++m) s = fma(sB[m * N + i], A[m + NQ * bc], s);
+      if constexpr (COLOUR) {
+        a.y[node] += s;  // no other cell of this colour touches `node`
+      } else {
+        atomicAdd(a.y + node, s);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int N, int NQ, int KIND, bool COLOUR>
+cudaError_t launch_apply(const HexTables& tb, const HexApplyArgs& a, int sm_count, cudaStream_t s) {
+  using S = Shape<N, NQ>;
+  auto kern = hex_apply_kernel<N, NQ, KIND, COLOUR>;
+  static int blocks_per_sm = -1;
+  if (blocks_per_sm < 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, S::T, S::SMEM);
+    if (e != cudaSuccess) return e;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  const int64_t nbatch = (a.count + S::CB - 1) / S::CB;
+  if (nbatch == 0) return cudaSuccess;
+  const int64_t grid = nbatch < (int64_t)sm_count * blocks_per_sm ? nbatch : (int64_t)sm_count * blocks_per_sm;
+  kern<<<(unsigned)grid, S::T, S::SMEM, s>>>(tb, a);
+  return cudaGetLastError();
+}
+
+// Matrix-free diagonal d_i = sum_K A_K[i][i] (for Jacobi preconditioning).
+// With phi_i = l_a(x) l_b(y) l_c(z) and stored G, the diagonal is a sum of 7
+// tensor terms, sum_q G_t(q) U_t[q_x][a] V_t[q_y][b] W_t[q_z][c], each
+// contracted by three 1D sweeps (z, then y, then x) over the Gauss points.
+template <int N, int NQ, int KIND>
+__global__ void __launch_bounds__(Shape<N, NQ>::T) hex_diag_kernel(const __grid_constant__ HexTables tb,
+                                                                   const int32_t* __restrict__ cell_node,
+                                                                   const double* __restrict__ geom, int64_t ncell,
+                                                                   double* __restrict__ d) {
+  using S = Shape<N, NQ>;
+  constexpr int P = S::P, PN = S::PN, PQ = S::PQ, CB = S::CB;
+  constexpr int NG = geom_entries<KIND>();
+  extern __shared__ double smem[];
+  double* B2 = smem;             // [NQ][N] B*B
+  double* DB2 = B2 + NQ * N;     // [NQ][N] (D B)*(D B)
+  double* X = DB2 + NQ * N;      // [NQ][N] (D B)*B
+  double* bufA = X + NQ * N;     // [CB][P]
+  double* bufB = bufA + CB * P;  // [CB][P]
+  const int t = threadIdx.x;
+  for (int e = t; e < NQ * N; e += blockDim.x) {
+    const int q = e / N, a = e % N;
+    double db = 0.0;
+    for (int r = 0; r < NQ; ++r) db += tb.D[q * NQ + r] * tb.B[r * N + a];
+    const double b = tb.B[q * N + a];
+    B2[e] = b * b;
+    DB2[e] = db * db;
+    X[e] = db * b;
+  }
+  const int cl = t / P, pt = t - cl * P;
+  double* A = bufA + cl * P;
+  double* Bf = bufB + cl * P;
+  const int64_t nbatch = (ncell + CB - 1) / CB;
+  // term t: geometry entry, factor for x, y, z (0: B2, 1: DB2, 2: X), multiplier
+  constexpr int nterm = KIND == MFA_FORM_MASS ? 1 : (KIND == MFA_FORM_LAPLACE ? 6 : 7);
+  const int tg[7] = {0, 1, 2, 3, 4, 5, 6};
+  const int fx[7] = {1, 0, 0, 2, 2, 0, 0}, fy[7] = {0, 1, 0, 2, 0, 2, 0}, fz[7] = {0, 0, 1, 0, 2, 2, 0};
+  const double mult[7] = {1, 1, 1, 2, 2, 2, 1};
+  __syncthreads();
+  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
+    const int64_t cell = batch * CB + cl;
+    const bool valid = (cl < CB) && (cell < ncell);
+    double acc = 0.0;
+    for (int term = 0; term < nterm; ++term) {
+      const int ge = KIND == MFA_FORM_MASS ? 0 : tg[term];
+      const int ix = KIND == MFA_FORM_MASS ? 0 : fx[term], iy = KIND == MFA_FORM_MASS ? 0 : fy[term],
+                iz = KIND == MFA_FORM_MASS ? 0 : fz[term];
+      const double* U = ix == 0 ? B2 : (ix == 1 ? DB2 : X);
+      const double* V = iy == 0 ? B2 : (iy == 1 ? DB2 : X);
+      const double* W = iz == 0 ? B2 : (iz == 1 ? DB2 : X);
+      if (valid && pt < PQ) A[pt] = mult[term] * geom[(cell * NG + ge) * PQ + pt];
+      __syncthreads();
+      if (valid && pt < NQ * NQ * N) {  // z: (NQ, NQ, N) <- (NQ, NQ, NQ)
+        const int ij = pt % (NQ * NQ), c = pt / (NQ * NQ);
+        double s = 0.0;
+        for (int m = 0; m < NQ; ++m) s = fma(W[m * N + c], A[ij + NQ * NQ * m], s);
+        Bf[pt] = s;
+      }
+      __syncthreads();
+      if (valid && pt < NQ * N * N) {  // y: (NQ, N, N) <- (NQ, NQ, N)
+        const int i = pt % NQ, b = (pt / NQ) % N, c = pt / (NQ * N);
+        double s = 0.0;
+        for (int m = 0; m < NQ; ++m) s = fma(V[m * N + b], Bf[i + NQ * (m + NQ * c)], s);
+        A[pt] = s;
+      }
+      __syncthreads();
+      if (valid && pt < PN) {  // x: (N, N, N) <- (NQ, N, N)
+        const int i = pt % N, bc = pt / N;
+        double s = 0.0;
+        for (int m = 0; m < NQ; ++m) s = fma(U[m * N + i], A[m + NQ * bc], s);
+        acc += s;
+      }
+      __syncthreads();
+    }
+    if (valid && pt < PN) atomicAdd(d + cell_node[cell * PN + pt], acc);
+  }
+}
+
+template <int N, int NQ, int KIND>
+cudaError_t launch_diag(const HexTables& tb, const int32_t* cell_node, const double* geom, int64_t ncell, double* d,
+                        int sm_count, cudaStream_t s) {
+  using S = Shape<N, NQ>;
+  auto kern = hex_diag_kernel<N, NQ, KIND>;
+  const int smem = (3 * NQ * N + 2 * S::CB * S::P) * 8;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t nbatch = (ncell + S::CB - 1) / S::CB;
+  if (nbatch == 0) return cudaSuccess;
+  const int64_t grid = nbatch < (int64_t)sm_count * 4 ? nbatch : (int64_t)sm_count * 4;
+  kern<<<(unsigned)grid, S::T, smem, s>>>(tb, cell_node, geom, ncell, d);
+  return cudaGetLastError();
+}
+
+}  // namespace hexk
+}  // namespace mfa

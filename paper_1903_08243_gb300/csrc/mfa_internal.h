@@ -1,0 +1,145 @@
+// Internal declarations of the mfa library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mfa.h"
+
+namespace mfa {
+
+constexpr int kMaxN = 10;  // nodes or quadrature points per direction (Q_p, p <= 8; p+2 points)
+
+// ---------------------------------------------------------------- tables.cpp
+// Quadrature rules and 1D/3D basis tabulations built on the host in FP64.
+void gauss_jacobi01(int n, int alpha, double* x, double* w);  // weight (1-x)^alpha on [0,1]
+void gauss_legendre01(int n, double* x, double* w);
+void gll01(int n, double* x);
+// Lagrange basis on `nodes` (n) evaluated at `pts` (m): L[q*n + a] = l_a(pts[q]).
+void lagrange_matrix(int n, const double* nodes, int m, const double* pts, double* L);
+// Collocation derivative on `pts` (m points): D[q*m + r] = l_r'(pts[q]).
+void collocation_derivative(int m, const double* pts, double* D);
+// Reference-tet rules.  Returns the number of points.
+int tet_rule_4pt_deg2(double* pts, double* w);  // degree-2, symmetric 4-point
+int tet_rule_collapsed(int degree, double* pts, double* w);  // conical product, m = ceil((deg+1)/2)
+// P1 / P2 basis on the reference tet (closed forms in barycentric coordinates).
+void tet_basis(int p, const double* xi, double* phi, double* dphi);
+
+// ---------------------------------------------------------------- colour.cpp
+// Greedy first-fit colouring: cells sharing a node get different colours.
+// Returns the number of colours (0 on failure); `order` lists cells grouped by
+// colour and `offsets` has ncolours + 1 entries.
+int greedy_colour(int64_t ncell, int nloc, const int32_t* cell_node, int64_t nnode,
+                  std::vector<int32_t>& order, std::vector<int64_t>& offsets);
+
+// ---------------------------------------------------------------- hex kernels
+struct HexTables {
+  double B[kMaxN * kMaxN];   // [nq][n]: basis at Gauss points
+  double D[kMaxN * kMaxN];   // [nq][nq]: collocation derivative at Gauss points
+  double w1[kMaxN];          // 1D Gauss weights on [0,1]
+  double x1[kMaxN];          // 1D Gauss points on [0,1]
+};
+
+struct HexApplyArgs {
+  const double* x;
+  double* y;
+  const int32_t* cell_node;  // [ncell][n^3]
+  const double* geom;        // [ncell][ng][nq^3]
+  const int32_t* cell_list;  // cells to process (nullptr: 0..count-1)
+  int64_t count;             // number of cells to process
+  int* err;
+};
+
+// Launch the sum-factorised FP64 action for cells [list].  Returns a cudaError_t.
+cudaError_t hex_apply_launch(int n, int nq, int kind, bool colour, const HexTables& tb, const HexApplyArgs& a,
+                             int sm_count, cudaStream_t s);
+cudaError_t hex_geometry_launch(int nq, int kind, double c0, const HexTables& tb, const double* coords,
+                                const int32_t* cell_vert, int64_t ncell, double* geom, int* err, cudaStream_t s);
+cudaError_t hex_diagonal_launch(int n, int nq, int kind, const HexTables& tb, const int32_t* cell_node,
+                                const double* geom, int64_t ncell, double* d, int sm_count, cudaStream_t s);
+int hex_geom_entries(int kind);  // stored FP64 values per quadrature point
+
+// ---------------------------------------------------------------- tet kernels
+constexpr int kTetMaxQ = 27;
+struct TetTables {
+  int nq;
+  double w[kTetMaxQ];
+  double phi[kTetMaxQ * 10];      // [q][a]
+  double dphi[kTetMaxQ * 10 * 3]; // [q][a][d] reference gradients
+};
+
+struct TetApplyArgs {
+  const double* x;
+  double* y;
+  const double* coords;
+  const int32_t* cell_vert;
+  const int32_t* cell_node;
+  const double* ucoef;       // HYPER_JAC linearisation point
+  const int32_t* cell_list;
+  int64_t count;
+  double k2, lambda, mu, b0, b1, b2;
+  int* err;
+};
+
+cudaError_t tet_apply_launch(int p, int ncomp, int kind, int law, bool colour, const TetTables& tb,
+                             const TetApplyArgs& a, int sm_count, cudaStream_t s);
+cudaError_t tet_diagonal_launch(int p, int ncomp, int kind, const TetTables& tb, const TetApplyArgs& a,
+                                double* d, cudaStream_t s);
+
+// ---------------------------------------------------------------- blas
+cudaError_t dot_launch(const double* a, const double* b, int64_t n, double* partial, double* out, cudaStream_t s);
+cudaError_t axpby_launch(double alpha, const double* x, double beta, double* y, int64_t n, cudaStream_t s);
+cudaError_t pointwise_mul_launch(const double* a, const double* b, double* out, int64_t n, cudaStream_t s);
+cudaError_t reciprocal_launch(const double* a, double* out, int64_t n, cudaStream_t s);
+int dot_partials();
+
+}  // namespace mfa
+
+// ---------------------------------------------------------------- handle types
+struct mfa_ctx {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  int* d_err = nullptr;          // kernel error flags (bit 0: det J <= 0, bit 1: J <= 0)
+  double* d_scratch = nullptr;   // reduction scratch (partials + result)
+};
+
+struct mfa_mesh {
+  mfa_ctx* ctx = nullptr;
+  int cell_type = 0;
+  int64_t ncell = 0, nvert = 0;
+  double* d_coords = nullptr;
+  int32_t* d_cell_vert = nullptr;
+};
+
+struct mfa_space {
+  mfa_ctx* ctx = nullptr;
+  mfa_mesh* mesh = nullptr;
+  int degree = 0, ncomp = 1, nloc = 0;
+  int64_t nnode = 0;
+  int32_t* d_cell_node = nullptr;
+  std::vector<int32_t> h_cell_node;  // kept for colouring
+  // colouring (built on first coloured form)
+  int ncolours = 0;
+  std::vector<int64_t> colour_offsets;
+  int32_t* d_colour_cells = nullptr;
+};
+
+struct mfa_form {
+  mfa_ctx* ctx = nullptr;
+  mfa_space* space = nullptr;
+  mfa_form_params p{};
+  int nq1 = 0;                   // hex: points per direction
+  int nq = 0;                    // points per cell
+  int scatter = MFA_SCATTER_ATOMIC;
+  mfa::HexTables hex{};
+  mfa::TetTables tet{};
+  double* d_geom = nullptr;
+  const double* d_coef = nullptr;
+  double* d_stage_x = nullptr;   // mfa_apply_host staging
+  double* d_stage_y = nullptr;
+  double flops = 0.0, bytes = 0.0, setup_ms = 0.0;
+};

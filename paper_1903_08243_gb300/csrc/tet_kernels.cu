@@ -1,0 +1,420 @@
+// Tetrahedral kernels: P1/P2 Lagrange on affine cells, one CUDA thread per
+// cell.
+//
+// This is the GPU form of the paper's cross-element vectorisation (Section
+// 3.1): the loop over cells is split across lanes, each lane runs the whole
+// local kernel of one cell (Listing 2) and every lane executes the same
+// instruction stream, with the quadrature and basis tables shared by all
+// lanes (uniform loads from the constant bank).  The Jacobian is constant on
+// an affine cell and computed once per cell (Listing 2, lines 8-20).
+//
+// Forms (Supplementary material): mass, Laplacian, Helmholtz (P1/P2 scalar,
+// P2 vector Laplacian), linear elasticity, and the hyperelastic residual and
+// Jacobian action for St Venant-Kirchhoff and compressible neo-Hookean laws.
+#include "mfa_internal.h"
+
+namespace mfa {
+namespace {
+
+struct M3 {
+  double m[3][3];
+};
+
+__device__ __forceinline__ double det3(const double A[3][3], double cof[3][3]) {
+  cof[0][0] = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+  cof[0][1] = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+  cof[0][2] = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+  cof[1][0] = A[0][2] * A[2][1] - A[0][1] * A[2][2];
+  cof[1][1] = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+  cof[1][2] = A[0][1] * A[2][0] - A[0][0] * A[2][1];
+  cof[2][0] = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+  cof[2][1] = A[0][2] * A[1][0] - A[0][0] * A[1][2];
+  cof[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+  return A[0][0] * cof[0][0] + A[0][1] * cof[0][1] + A[0][2] * cof[0][2];
+}
+
+// Stress fluxes f1[c][j] multiplying d(phi_a)/dx_j for test component c.
+template <int KIND, int LAW>
+__device__ __forceinline__ bool physics(const double gu[3][3], const double gc[3][3], double lam, double mu,
+                                        double f1[3][3]) {
+  if constexpr (KIND == MFA_FORM_ELASTICITY) {
+    const double tr = gu[0][0] + gu[1][1] + gu[2][2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) f1[i][j] = mu * (gu[i][j] + gu[j][i]) + (i == j ? lam * tr : 0.0);
+    return true;
+  } else if constexpr (KIND == MFA_FORM_HYPER_RES) {
+    double F[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) F[i][j] = gu[i][j] + (i == j ? 1.0 : 0.0);
+    if constexpr (LAW == MFA_LAW_SVK) {
+      // S = lambda tr(E) I + 2 mu E, E = (F^T F - I)/2, P = F S
+      double E[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+          const double c = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
+          E[i][j] = 0.5 * (c - (i == j ? 1.0 : 0.0));
+          E[j][i] = E[i][j];
+        }
+      const double tr = E[0][0] + E[1][1] + E[2][2];
+      double S[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) S[i][j] = 2.0 * mu * E[i][j] + (i == j ? lam * tr : 0.0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) f1[i][j] = F[i][0] * S[0][j] + F[i][1] * S[1][j] + F[i][2] * S[2][j];
+      return true;
+    } else {
+      // P = mu F + (lambda ln J - mu) F^{-T},  F^{-T} = cof(F) / J
+      double cof[3][3];
+      const double J = det3(F, cof);
+      if (!(J > 0.0)) return false;
+      const double s = (lam * log(J) - mu) / J;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) f1[i][j] = mu * F[i][j] + s * cof[i][j];
+      return true;
+    }
+  } else {  // MFA_FORM_HYPER_JAC: f1 = dP(F; dF), F = I + gc, dF = gu
+    double F[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) F[i][j] = gc[i][j] + (i == j ? 1.0 : 0.0);
+    if constexpr (LAW == MFA_LAW_SVK) {
+      // dP = dF S + F dS, dE = sym(F^T dF), dS = lambda tr(dE) I + 2 mu dE
+      double E[3][3], dE[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+          const double c = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
+          const double d = F[0][i] * gu[0][j] + F[1][i] * gu[1][j] + F[2][i] * gu[2][j] + F[0][j] * gu[0][i] +
+                           F[1][j] * gu[1][i] + F[2][j] * gu[2][i];
+          E[i][j] = 0.5 * (c - (i == j ? 1.0 : 0.0));
+          E[j][i] = E[i][j];
+          dE[i][j] = 0.5 * d;
+          dE[j][i] = dE[i][j];
+        }
+      const double tr = E[0][0] + E[1][1] + E[2][2];
+      const double dtr = dE[0][0] + dE[1][1] + dE[2][2];
+      double S[3][3], dS[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          S[i][j] = 2.0 * mu * E[i][j] + (i == j ? lam * tr : 0.0);
+          dS[i][j] = 2.0 * mu * dE[i][j] + (i == j ? lam * dtr : 0.0);
+        }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          f1[i][j] = gu[i][0] * S[0][j] + gu[i][1] * S[1][j] + gu[i][2] * S[2][j] + F[i][0] * dS[0][j] +
+                     F[i][1] * dS[1][j] + F[i][2] * dS[2][j];
+      return true;
+    } else {
+      // dP = mu dF + (mu - lambda ln J) A dF^T A + lambda (A : dF) A,  A = F^{-T}
+      double cof[3][3];
+      const double J = det3(F, cof);
+      if (!(J > 0.0)) return false;
+      const double iJ = 1.0 / J;
+      double A[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) A[i][j] = cof[i][j] * iJ;
+      double AdFt[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) AdFt[i][j] = A[i][0] * gu[j][0] + A[i][1] * gu[j][1] + A[i][2] * gu[j][2];
+      double tr = 0.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) tr += A[i][j] * gu[i][j];
+      const double c2 = mu - lam * log(J), c3 = lam * tr;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          f1[i][j] = mu * gu[i][j] + c2 * (AdFt[i][0] * A[0][j] + AdFt[i][1] * A[1][j] + AdFt[i][2] * A[2][j]) +
+                     c3 * A[i][j];
+      return true;
+    }
+  }
+}
+
+template <int P, int NC, int KIND, int LAW, int NQ, bool COLOUR>
+__global__ void __launch_bounds__(128) tet_apply_kernel(const __grid_constant__ TetTables tb, const TetApplyArgs a) {
+  constexpr int NL = P == 1 ? 4 : 10;
+  constexpr bool kValue = (KIND == MFA_FORM_MASS || KIND == MFA_FORM_HELMHOLTZ);
+  constexpr bool kGrad = (KIND != MFA_FORM_MASS);
+  constexpr bool kVector = (KIND >= MFA_FORM_ELASTICITY);
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < a.count;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = a.cell_list ? (int64_t)__ldg(a.cell_list + idx) : idx;
+    // affine geometry: J[d][e] = X_{e+1}[d] - X_0[d]
+    double X0[3], J[3][3];
+    {
+      const int32_t v0 = __ldg(a.cell_vert + 4 * cell);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) X0[d] = __ldg(a.coords + 3 * (int64_t)v0 + d);
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        const int32_t ve = __ldg(a.cell_vert + 4 * cell + e + 1);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) J[d][e] = __ldg(a.coords + 3 * (int64_t)ve + d) - X0[d];
+      }
+    }
+    double cof[3][3];
+    const double det = det3(J, cof);
+    if (!(det != 0.0) || !isfinite(det)) {
+      atomicOr(a.err, 1);
+      continue;
+    }
+    const double idet = 1.0 / det;
+    double Ji[3][3];  // J^{-1}[e][j] = cof[j][e] / det
+#pragma unroll
+    for (int e = 0; e < 3; ++e)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Ji[e][j] = cof[j][e] * idet;
+    const double adet = fabs(det);
+
+    int32_t node[NL];
+    double xl[NL][NC], yl[NL][NC];
+#pragma unroll
+    for (int i = 0; i < NL; ++i) {
+      node[i] = __ldg(a.cell_node + NL * cell + i);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        xl[i][c] = __ldg(a.x + (int64_t)NC * node[i] + c);
+        yl[i][c] = 0.0;
+      }
+    }
+    bool ok = true;
+#pragma unroll 1
+    for (int q = 0; q < NQ; ++q) {
+      const double wd = tb.w[q] * adet;
+      const double* phi = tb.phi + q * NL;
+      const double* dphi = tb.dphi + q * NL * 3;
+      double u[NC];
+      double gr[NC][3];  // reference gradient d u_c / d xi_e
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        u[c] = 0.0;
+        gr[c][0] = gr[c][1] = gr[c][2] = 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < NL; ++i)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          if constexpr (kValue) u[c] = fma(phi[i], xl[i][c], u[c]);
+          if constexpr (kGrad) {
+            gr[c][0] = fma(xl[i][c], dphi[3 * i + 0], gr[c][0]);
+            gr[c][1] = fma(xl[i][c], dphi[3 * i + 1], gr[c][1]);
+            gr[c][2] = fma(xl[i][c], dphi[3 * i + 2], gr[c][2]);
+          }
+        }
+      // h[c][e] = wd * sum_j f1[c][j] Ji[e][j]: the test-gradient flux pulled back to the reference cell
+      double h[NC][3];
+      double f0[NC];
+      if constexpr (!kVector) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          f0[c] = 0.0;
+          if constexpr (kValue) f0[c] = wd * (KIND == MFA_FORM_HELMHOLTZ ? a.k2 : 1.0) * u[c];
+          if constexpr (kGrad) {
+            double gx[3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) gx[j] = gr[c][0] * Ji[0][j] + gr[c][1] * Ji[1][j] + gr[c][2] * Ji[2][j];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) h[c][e] = wd * (gx[0] * Ji[e][0] + gx[1] * Ji[e][1] + gx[2] * Ji[e][2]);
+          }
+        }
+      } else {
+        double gu[3][3], gc[3][3], f1[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) gu[c][j] = gr[c][0] * Ji[0][j] + gr[c][1] * Ji[1][j] + gr[c][2] * Ji[2][j];
+        if constexpr (KIND == MFA_FORM_HYPER_JAC) {
+          double gcr[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+          for (int i = 0; i < NL; ++i) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const double uc = __ldg(a.ucoef + 3 * (int64_t)node[i] + c);
+              gcr[c][0] = fma(uc, dphi[3 * i + 0], gcr[c][0]);
+              gcr[c][1] = fma(uc, dphi[3 * i + 1], gcr[c][1]);
+              gcr[c][2] = fma(uc, dphi[3 * i + 2], gcr[c][2]);
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) gc[c][j] = gcr[c][0] * Ji[0][j] + gcr[c][1] * Ji[1][j] + gcr[c][2] * Ji[2][j];
+        }
+        ok = ok && physics<KIND, LAW>(gu, gc, a.lambda, a.mu, f1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+          for (int e = 0; e < 3; ++e) h[c][e] = wd * (f1[c][0] * Ji[e][0] + f1[c][1] * Ji[e][1] + f1[c][2] * Ji[e][2]);
+          f0[c] = 0.0;
+        }
+        if constexpr (KIND == MFA_FORM_HYPER_RES) {
+          f0[0] = -wd * a.b0;
+          f0[1] = -wd * a.b1;
+          f0[2] = -wd * a.b2;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NL; ++i)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          double s = yl[i][c];
+          if constexpr (kValue || KIND == MFA_FORM_HYPER_RES) s = fma(f0[c], phi[i], s);
+          if constexpr (kGrad) {
+            s = fma(h[c][0], dphi[3 * i + 0], s);
+            s = fma(h[c][1], dphi[3 * i + 1], s);
+            s = fma(h[c][2], dphi[3 * i + 2], s);
+          }
+          yl[i][c] = s;
+        }
+    }
+    if (!ok) atomicOr(a.err, 2);
+#pragma unroll
+    for (int i = 0; i < NL; ++i)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        double* dst = a.y + (int64_t)NC * node[i] + c;
+        if constexpr (COLOUR) *dst += yl[i][c];
+        else atomicAdd(dst, yl[i][c]);
+      }
+  }
+}
+
+template <int P, int NC, int KIND, int LAW, int NQ, bool COLOUR>
+cudaError_t launch(const TetTables& tb, const TetApplyArgs& a, int sm_count, cudaStream_t s) {
+  if (a.count == 0) return cudaSuccess;
+  auto kern = tet_apply_kernel<P, NC, KIND, LAW, NQ, COLOUR>;
+  static int bps = -1;
+  if (bps < 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 128, 0);
+    if (e != cudaSuccess) return e;
+    if (bps < 1) bps = 1;
+  }
+  int64_t blocks = (a.count + 127) / 128;
+  const int64_t cap = (int64_t)sm_count * bps;
+  if (blocks > cap) blocks = cap;
+  kern<<<(unsigned)blocks, 128, 0, s>>>(tb, a);
+  return cudaGetLastError();
+}
+
+template <int P, int NC, int KIND, int LAW, int NQ>
+cudaError_t launch2(bool colour, const TetTables& tb, const TetApplyArgs& a, int sm_count, cudaStream_t s) {
+  return colour ? launch<P, NC, KIND, LAW, NQ, true>(tb, a, sm_count, s)
+                : launch<P, NC, KIND, LAW, NQ, false>(tb, a, sm_count, s);
+}
+
+// Diagonal of the linear forms, per local dof and cell:
+//   scalar:      sum_q w|J| (c0 phi_a^2 + |grad phi_a|^2)
+//   vector Lap.: sum_q w|J| |grad phi_a|^2
+//   elasticity:  sum_q w|J| (mu |grad phi_a|^2 + (mu + lambda) (d_c phi_a)^2)
+template <int NL, int NC>
+__global__ void tet_diag_kernel(const __grid_constant__ TetTables tb, const TetApplyArgs a, int kind, double* d) {
+  for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < a.count;
+       cell += (int64_t)gridDim.x * blockDim.x) {
+    double X0[3], J[3][3];
+    const int32_t v0 = a.cell_vert[4 * cell];
+    for (int k = 0; k < 3; ++k) X0[k] = a.coords[3 * (int64_t)v0 + k];
+    for (int e = 0; e < 3; ++e) {
+      const int32_t ve = a.cell_vert[4 * cell + e + 1];
+      for (int k = 0; k < 3; ++k) J[k][e] = a.coords[3 * (int64_t)ve + k] - X0[k];
+    }
+    double cof[3][3];
+    const double det = det3(J, cof);
+    if (!(det != 0.0) || !isfinite(det)) {
+      atomicOr(a.err, 1);
+      continue;
+    }
+    const double adet = fabs(det);
+    double c0 = kind == MFA_FORM_MASS ? 1.0 : (kind == MFA_FORM_HELMHOLTZ ? a.k2 : 0.0);
+    const bool grad = kind != MFA_FORM_MASS;
+    for (int i = 0; i < NL; ++i) {
+      double acc[NC];
+      for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+      for (int q = 0; q < tb.nq; ++q) {
+        const double wd = tb.w[q] * adet;
+        const double ph = tb.phi[q * NL + i];
+        double g[3];
+        for (int j = 0; j < 3; ++j)
+          g[j] = (tb.dphi[(q * NL + i) * 3 + 0] * cof[j][0] + tb.dphi[(q * NL + i) * 3 + 1] * cof[j][1] +
+                  tb.dphi[(q * NL + i) * 3 + 2] * cof[j][2]) / det;
+        const double gg = grad ? g[0] * g[0] + g[1] * g[1] + g[2] * g[2] : 0.0;
+        for (int c = 0; c < NC; ++c) {
+          if (kind == MFA_FORM_ELASTICITY) acc[c] += wd * (a.mu * gg + (a.mu + a.lambda) * g[c] * g[c]);
+          else acc[c] += wd * (c0 * ph * ph + gg);
+        }
+      }
+      const int32_t node = a.cell_node[NL * cell + i];
+      for (int c = 0; c < NC; ++c) atomicAdd(d + (int64_t)NC * node + c, acc[c]);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t tet_diagonal_launch(int p, int ncomp, int kind, const TetTables& tb, const TetApplyArgs& a, double* d,
+                                cudaStream_t s) {
+  if (a.count == 0) return cudaSuccess;
+  int64_t blocks = (a.count + 127) / 128;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (p == 1 && ncomp == 1) tet_diag_kernel<4, 1><<<(unsigned)blocks, 128, 0, s>>>(tb, a, kind, d);
+  else if (p == 2 && ncomp == 1) tet_diag_kernel<10, 1><<<(unsigned)blocks, 128, 0, s>>>(tb, a, kind, d);
+  else if (p == 2 && ncomp == 3) tet_diag_kernel<10, 3><<<(unsigned)blocks, 128, 0, s>>>(tb, a, kind, d);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t tet_apply_launch(int p, int ncomp, int kind, int law, bool colour, const TetTables& tb,
+                             const TetApplyArgs& a, int sm_count, cudaStream_t s) {
+  const int nq = tb.nq;
+  if (p == 1 && ncomp == 1 && nq == 4) {
+    switch (kind) {
+      case MFA_FORM_MASS: return launch2<1, 1, MFA_FORM_MASS, 0, 4>(colour, tb, a, sm_count, s);
+      case MFA_FORM_LAPLACE: return launch2<1, 1, MFA_FORM_LAPLACE, 0, 4>(colour, tb, a, sm_count, s);
+      case MFA_FORM_HELMHOLTZ: return launch2<1, 1, MFA_FORM_HELMHOLTZ, 0, 4>(colour, tb, a, sm_count, s);
+    }
+  }
+  if (p == 2 && ncomp == 1) {
+    if (kind == MFA_FORM_MASS && nq == 27) return launch2<2, 1, MFA_FORM_MASS, 0, 27>(colour, tb, a, sm_count, s);
+    if (kind == MFA_FORM_LAPLACE && nq == 4) return launch2<2, 1, MFA_FORM_LAPLACE, 0, 4>(colour, tb, a, sm_count, s);
+    if (kind == MFA_FORM_HELMHOLTZ && nq == 27)
+      return launch2<2, 1, MFA_FORM_HELMHOLTZ, 0, 27>(colour, tb, a, sm_count, s);
+  }
+  if (p == 2 && ncomp == 3) {
+    if (kind == MFA_FORM_LAPLACE && nq == 4) return launch2<2, 3, MFA_FORM_LAPLACE, 0, 4>(colour, tb, a, sm_count, s);
+    if (kind == MFA_FORM_ELASTICITY && nq == 4)
+      return launch2<2, 3, MFA_FORM_ELASTICITY, 0, 4>(colour, tb, a, sm_count, s);
+    if (kind == MFA_FORM_HYPER_RES && nq == 27)
+      return law == MFA_LAW_SVK ? launch2<2, 3, MFA_FORM_HYPER_RES, MFA_LAW_SVK, 27>(colour, tb, a, sm_count, s)
+                                : launch2<2, 3, MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE, 27>(colour, tb, a, sm_count, s);
+    if (kind == MFA_FORM_HYPER_JAC && nq == 27)
+      return law == MFA_LAW_SVK ? launch2<2, 3, MFA_FORM_HYPER_JAC, MFA_LAW_SVK, 27>(colour, tb, a, sm_count, s)
+                                : launch2<2, 3, MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE, 27>(colour, tb, a, sm_count, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace mfa

@@ -1,0 +1,51 @@
+"""Shared problem builders: one set of seeded inputs, handed to both the oracle and the library."""
+import numpy as np
+
+import fe_inputs as fi
+import oracle
+
+KIND_NAMES = {"mass": 0, "laplace": 1, "helmholtz": 2, "elasticity": 3, "hyper_res": 4, "hyper_jac": 5}
+
+
+def hex_case(nx, p, perturb=0.1, seed=1, shuffle=False):
+    mesh = fi.hex_box_mesh(nx, perturb=perturb, seed=seed)
+    cell_node, nnode = fi.hex_node_map(nx, p)
+    cv = mesh.cell_vert
+    if shuffle:
+        cv, cell_node, _ = fi.shuffle_mesh(cv, cell_node, nnode, seed=seed + 100)
+    return dict(cell_type=8, coords=mesh.coords, cell_vert=cv, degree=p, cell_node=cell_node, nnode=nnode, ncomp=1,
+                nodes=None)
+
+
+def tet_case(nx, p, ncomp=1, perturb=0.0, seed=0, shuffle=False):
+    mesh = fi.kuhn_tet_mesh(nx, perturb=perturb, seed=seed)
+    if p == 1:
+        cn, nnode, nodes = mesh.cell_vert, mesh.nvert, mesh.coords
+    else:
+        cn, nnode, edges = fi.p2_node_map(mesh.cell_vert, mesh.nvert)
+        nodes = fi.p2_node_coords(mesh.coords, edges)
+    cv = mesh.cell_vert
+    if shuffle:
+        cv, cn, perm = fi.shuffle_mesh(cv, cn, nnode, seed=seed + 100)
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(perm.size)
+        nodes = nodes[inv]
+    return dict(cell_type=4, coords=mesh.coords, cell_vert=cv, degree=p, cell_node=cn, nnode=nnode, ncomp=ncomp,
+                nodes=nodes)
+
+
+def oracle_problem(case, kind, qdeg=None, **kw):
+    if qdeg is None:
+        if case["cell_type"] == 8:
+            qdeg = case["degree"] + 1
+        else:
+            qdeg = 4 if kind in ("hyper_res", "hyper_jac") else 2 * case["degree"]
+    return oracle.Problem(case["cell_type"], case["coords"], case["cell_vert"], case["degree"], case["cell_node"],
+                          case["nnode"], KIND_NAMES[kind], ncomp=case["ncomp"], qdeg=qdeg, **kw)
+
+
+def cells_touching(cell_node, dofs, ncomp=1):
+    """Cells whose map contains any node of the given dofs (for sampled full-size parity)."""
+    nodes = np.unique(np.asarray(dofs) // ncomp)
+    mask = np.isin(cell_node, nodes).any(axis=1)
+    return np.nonzero(mask)[0]

@@ -1,0 +1,304 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerance (FP64 paths): relative L2 error <= 1e-12 and max-abs error <= 1e-12
+times max|y_ref|.  Both sides integrate the same forms with rules that are
+exact for the polynomial integrands (or the same conical-product rule for
+neo-Hookean), so they agree to rounding; reordering of FP64 sums over
+~10^2-10^3 terms per entry stays many orders below the bound.
+"""
+import numpy as np
+import pytest
+
+import fe_inputs as fi
+import oracle
+from tests.problems import KIND_NAMES, cells_touching, hex_case, oracle_problem, tet_case
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1903_08243_gb300 as mfa  # noqa: E402
+
+TOL = 1e-12
+SCATTER = {"atomic": mfa.MFA_SCATTER_ATOMIC, "colour": mfa.MFA_SCATTER_COLOUR}
+LAWS = {"svk": mfa.MFA_LAW_SVK, "nh": mfa.MFA_LAW_NEOHOOKE}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch.cuda.set_device(0)
+    c = mfa.Context(0, torch.cuda.current_stream())
+    yield c
+
+
+def gpu_form(ctx, case, kind, **kw):
+    m = mfa.Mesh(ctx, case["cell_type"], case["coords"], case["cell_vert"])
+    sp = mfa.Space(m, case["degree"], case["ncomp"], case["cell_node"], case["nnode"])
+    return mfa.Form(sp, KIND_NAMES[kind], **kw)
+
+
+def compare(y, ref, tol=TOL):
+    y = np.asarray(y)
+    rel = np.linalg.norm(y - ref) / max(np.linalg.norm(ref), 1e-300)
+    mx = np.abs(y - ref).max() / max(np.abs(ref).max(), 1e-300)
+    assert rel <= tol and mx <= tol, (rel, mx)
+    return rel
+
+
+def run(ctx, form, x):
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    y = form.apply(xd)
+    ctx.sync()
+    return y.cpu().numpy()
+
+
+# ------------------------------------------------------------------ hexahedra
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("kind", ["mass", "laplace", "helmholtz"])
+@pytest.mark.parametrize("scatter", ["atomic", "colour"])
+def test_hex_parity(ctx, p, kind, scatter):
+    nx = {1: 7, 2: 5, 3: 5, 4: 3, 5: 3, 6: 3, 7: 2, 8: 2}[p]  # several blocks and a ragged last batch
+    case = hex_case(nx, p)
+    x = fi.uniform_vector(case["nnode"], seed=11)
+    ref = oracle_problem(case, kind, k2=0.75).apply(x)
+    form = gpu_form(ctx, case, kind, k2=0.75, scatter=SCATTER[scatter])
+    compare(run(ctx, form, x), ref)
+
+
+@pytest.mark.parametrize("p", [1, 3, 6])
+def test_hex_paper_quadrature_p_plus_2(ctx, p):
+    """Table 2 uses p+2 Gauss points per direction on hexahedra."""
+    case = hex_case(3, p)
+    x = fi.uniform_vector(case["nnode"], seed=12)
+    ref = oracle_problem(case, "helmholtz", qdeg=p + 2).apply(x)
+    form = gpu_form(ctx, case, "helmholtz", qdeg=p + 2)
+    compare(run(ctx, form, x), ref)
+
+
+def test_hex_shuffled_numbering(ctx):
+    case = hex_case(4, 3, shuffle=True)
+    x = fi.uniform_vector(case["nnode"], seed=13)
+    ref = oracle_problem(case, "laplace").apply(x)
+    for sc in SCATTER.values():
+        compare(run(ctx, gpu_form(ctx, case, "laplace", scatter=sc), x), ref)
+
+
+def test_colour_scatter_is_bitwise_deterministic(ctx):
+    case = hex_case(6, 3)
+    x = fi.uniform_vector(case["nnode"], seed=14)
+    form = gpu_form(ctx, case, "helmholtz", scatter=mfa.MFA_SCATTER_COLOUR)
+    assert form.info().ncolours == 8
+    y1, y2 = run(ctx, form, x), run(ctx, form, x)
+    assert np.array_equal(y1.view(np.uint64), y2.view(np.uint64))
+
+
+def test_hex_accumulate_and_host_apply(ctx):
+    case = hex_case(4, 2)
+    x = fi.uniform_vector(case["nnode"], seed=15)
+    ref = oracle_problem(case, "mass").apply(x)
+    form = gpu_form(ctx, case, "mass")
+    compare(form.apply_host(x), ref)
+    xd = torch.from_numpy(x).cuda()
+    y = torch.ones_like(xd)
+    form.apply(xd, y, accumulate=True)
+    ctx.sync()
+    compare(y.cpu().numpy(), ref + 1.0)
+
+
+@pytest.mark.parametrize("p", [1, 4])
+def test_hex_full_size_sampled(ctx, p):
+    """64^3 perturbed hex mesh (the benchmark size): sampled dofs against the oracle, cell by cell."""
+    case = hex_case(64, p)
+    x = fi.uniform_vector(case["nnode"], seed=1)
+    form = gpu_form(ctx, case, "helmholtz")
+    y = run(ctx, form, x)
+    rng = np.random.default_rng(p)
+    dofs = rng.choice(case["nnode"], size=64, replace=False)
+    cells = cells_touching(case["cell_node"], dofs)
+    ref = oracle_problem(case, "helmholtz").apply(x, cells=cells)
+    compare(y[dofs], ref[dofs])
+    # the action of the constant field sums to the domain volume (k2 = 1)
+    one = run(ctx, form, np.ones(case["nnode"]))
+    assert abs(one.sum() - 1.0) < 1e-11
+
+
+def test_empty_mesh(ctx):
+    case = hex_case(2, 2)
+    case["cell_vert"] = case["cell_vert"][:0]
+    case["cell_node"] = case["cell_node"][:0]
+    form = gpu_form(ctx, case, "helmholtz")
+    y = run(ctx, form, np.ones(case["nnode"]))
+    assert np.all(y == 0)
+
+
+# ------------------------------------------------------------------ tetrahedra
+
+TET_CASES = [
+    (1, 1, "mass", {}), (1, 1, "laplace", {}), (1, 1, "helmholtz", {"k2": 0.5}),
+    (2, 1, "mass", {}), (2, 1, "laplace", {}), (2, 1, "helmholtz", {"k2": 2.0}),
+    (2, 3, "laplace", {}), (2, 3, "elasticity", {"lam": 1.0, "mu": 1.0}),
+    (2, 3, "elasticity", {"lam": 0.0, "mu": 0.5}),  # the paper's int eps(u):eps(v)
+]
+
+
+@pytest.mark.parametrize("p,ncomp,kind,kw", TET_CASES)
+@pytest.mark.parametrize("scatter", ["atomic", "colour"])
+def test_tet_linear_forms(ctx, p, ncomp, kind, kw, scatter):
+    case = tet_case(5, p, ncomp=ncomp, perturb=0.15, seed=3)
+    x = fi.uniform_vector(case["nnode"] * ncomp, seed=21)
+    ref = oracle_problem(case, kind, **kw).apply(x)
+    form = gpu_form(ctx, case, kind, scatter=SCATTER[scatter], **kw)
+    compare(run(ctx, form, x), ref)
+
+
+@pytest.mark.parametrize("law", ["svk", "nh"])
+@pytest.mark.parametrize("scatter", ["atomic", "colour"])
+def test_tet_hyperelastic_residual(ctx, law, scatter):
+    case = tet_case(4, 2, ncomp=3, perturb=0.15, seed=4)
+    u = fi.sinusoid_displacement(case["nodes"], seed=2).ravel()
+    b = (0.1, -0.2, 0.05)
+    ref = oracle_problem(case, "hyper_res", law=LAWS[law], b=b).apply(u)
+    form = gpu_form(ctx, case, "hyper_res", law=LAWS[law], b=b, scatter=SCATTER[scatter])
+    compare(run(ctx, form, u), ref)
+
+
+@pytest.mark.parametrize("law", ["svk", "nh"])
+def test_tet_hyperelastic_jacobian(ctx, law):
+    case = tet_case(4, 2, ncomp=3, perturb=0.15, seed=5)
+    u = fi.sinusoid_displacement(case["nodes"], seed=3).ravel()
+    du = fi.uniform_vector(u.size, seed=22)
+    ref = oracle_problem(case, "hyper_jac", law=LAWS[law], ucoef=u).apply(du)
+    form = gpu_form(ctx, case, "hyper_jac", law=LAWS[law])
+    ud = torch.from_numpy(u).cuda()
+    form.set_coefficient(ud)
+    compare(run(ctx, form, du), ref)
+
+
+def test_tet_p1_mass_config0_full(ctx):
+    """The 8^3 x 6 Kuhn mesh, P1 mass, in full."""
+    case = tet_case(8, 1)
+    x = fi.uniform_vector(case["nnode"], seed=0)
+    ref = oracle_problem(case, "mass").apply(x)
+    for sc in SCATTER.values():
+        compare(run(ctx, gpu_form(ctx, case, "mass", scatter=sc), x), ref)
+
+
+def test_tet_p2_elasticity_and_nh_full_size_sampled(ctx):
+    """48^3 x 6 Kuhn mesh, vector P2: sampled dofs against the oracle, cell by cell."""
+    case = tet_case(48, 2, ncomp=3)
+    u = fi.sinusoid_displacement(case["nodes"], seed=2).ravel()
+    rng = np.random.default_rng(9)
+    dofs = rng.choice(u.size, size=48, replace=False)
+    cells = cells_touching(case["cell_node"], dofs, ncomp=3)
+    for kind, kw in [("elasticity", {}), ("hyper_res", {"law": mfa.MFA_LAW_NEOHOOKE})]:
+        okw = {"law": oracle.NEOHOOKE} if kw else {}
+        y = run(ctx, gpu_form(ctx, case, kind, **kw), u)
+        ref = oracle_problem(case, kind, **okw).apply(u, cells=cells)
+        compare(y[dofs], ref[dofs])
+
+
+def test_tet_shuffled(ctx):
+    case = tet_case(4, 2, ncomp=3, perturb=0.1, seed=6, shuffle=True)
+    x = fi.uniform_vector(case["nnode"] * 3, seed=23)
+    ref = oracle_problem(case, "elasticity").apply(x)
+    compare(run(ctx, gpu_form(ctx, case, "elasticity"), x), ref)
+
+
+# ------------------------------------------------------------------ diagonal and CG
+
+@pytest.mark.parametrize("which", ["hex-helm", "hex-lap", "hex-mass", "tet-p1-helm", "tet-p2-elast"])
+def test_diagonal(ctx, which):
+    if which.startswith("hex"):
+        case = hex_case(2, 3)
+        kind = {"helm": "helmholtz", "lap": "laplace", "mass": "mass"}[which.split("-")[1]]
+        kw = {"k2": 0.6} if kind == "helmholtz" else {}
+    elif which == "tet-p1-helm":
+        case, kind, kw = tet_case(2, 1, perturb=0.2, seed=7), "helmholtz", {"k2": 0.6}
+    else:
+        case, kind, kw = tet_case(2, 2, ncomp=3, perturb=0.2, seed=7), "elasticity", {"lam": 1.3, "mu": 0.7}
+    ref = np.diag(oracle_problem(case, kind, **kw).dense())
+    form = gpu_form(ctx, case, kind, **kw)
+    d = form.diagonal()
+    ctx.sync()
+    compare(d.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("precond", [mfa.MFA_PC_NONE, mfa.MFA_PC_JACOBI])
+def test_cg_matches_dense_solve(ctx, precond):
+    case = hex_case(3, 2)
+    A = oracle_problem(case, "helmholtz").dense()
+    b = fi.uniform_vector(case["nnode"], seed=30)
+    xs = np.linalg.solve(A, b)
+    form = gpu_form(ctx, case, "helmholtz")
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    rc, it, rel = form.cg(bd, xd, precond=precond, rtol=1e-12, maxit=500)
+    assert rc == mfa.MFA_OK and rel <= 1e-12
+    np.testing.assert_allclose(xd.cpu().numpy(), xs, rtol=0, atol=1e-9 * np.abs(xs).max())
+
+
+def test_cg_not_converged_status(ctx):
+    case = hex_case(3, 2)
+    form = gpu_form(ctx, case, "helmholtz")
+    bd = torch.from_numpy(fi.uniform_vector(case["nnode"], seed=31)).cuda()
+    rc, it, rel = form.cg(bd, torch.zeros_like(bd), precond=mfa.MFA_PC_NONE, rtol=1e-14, maxit=3)
+    assert rc == mfa.MFA_ERR_NOT_CONVERGED and it == 3
+
+
+def test_cg_breakdown_on_nan(ctx):
+    case = hex_case(2, 1)
+    form = gpu_form(ctx, case, "helmholtz")
+    b = np.ones(case["nnode"])
+    b[3] = np.nan
+    bd = torch.from_numpy(b).cuda()
+    with pytest.raises(mfa.MfaError) as e:
+        form.cg(bd, torch.zeros_like(bd), rtol=1e-8, maxit=10)
+    assert e.value.code == mfa.MFA_ERR_BREAKDOWN
+
+
+# ------------------------------------------------------------------ errors found on the host or by kernels
+
+def test_range_errors(ctx):
+    case = hex_case(2, 1)
+    bad = case["cell_vert"].copy()
+    bad[1, 3] = case["coords"].shape[0]
+    with pytest.raises(mfa.MfaError) as e:
+        mfa.Mesh(ctx, 8, case["coords"], bad)
+    assert e.value.code == mfa.MFA_ERR_RANGE
+    m = mfa.Mesh(ctx, 8, case["coords"], case["cell_vert"])
+    cn = case["cell_node"].copy()
+    cn[0, 0] = -1
+    with pytest.raises(mfa.MfaError) as e:
+        mfa.Space(m, 1, 1, cn, case["nnode"])
+    assert e.value.code == mfa.MFA_ERR_RANGE
+    cn = case["cell_node"].copy()
+    cn[0, 1] = cn[0, 0]
+    with pytest.raises(mfa.MfaError) as e:
+        mfa.Space(m, 1, 1, cn, case["nnode"])
+    assert e.value.code == mfa.MFA_ERR_ARG
+
+
+def test_unsupported_combinations(ctx):
+    case = hex_case(2, 1)
+    m = mfa.Mesh(ctx, 8, case["coords"], case["cell_vert"])
+    sp = mfa.Space(m, 1, 1, case["cell_node"], case["nnode"])
+    with pytest.raises(mfa.MfaError) as e:
+        mfa.Form(sp, mfa.MFA_FORM_ELASTICITY)
+    assert e.value.code == mfa.MFA_ERR_ARG
+    with pytest.raises(mfa.MfaError) as e:
+        mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ, qdeg=7)
+    assert e.value.code == mfa.MFA_ERR_UNSUPPORTED
+
+
+def test_neohookean_inverted_element_reports_domain_error(ctx):
+    case = tet_case(2, 2, ncomp=3)
+    u = -3.0 * case["nodes"].ravel()  # F = -2 I: det F < 0 everywhere
+    form = gpu_form(ctx, case, "hyper_res", law=mfa.MFA_LAW_NEOHOOKE)
+    form.apply(torch.from_numpy(u).cuda())
+    with pytest.raises(mfa.MfaError) as e:
+        ctx.sync()
+    assert e.value.code == mfa.MFA_ERR_DOMAIN
+    ctx.sync()  # the flag was cleared
