@@ -539,6 +539,8 @@ int mfa_cg(mfa_ctx* ctx, mfa_form* f, int precond, const double* b, double* x, d
   if (!rc) rc = dot(r, z, &rz);
   if (!rc && cudaMemcpyAsync(p, z, n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) rc = fail(MFA_ERR_CUDA, "copy");
   res = bnorm > 0.0 ? std::sqrt(rr) / bnorm : std::sqrt(rr);
+  if (!rc && (!std::isfinite(bnorm) || !std::isfinite(rr) || !std::isfinite(rz)))
+    rc = fail(MFA_ERR_BREAKDOWN, "mfa_cg: non-finite right-hand side or initial residual");
   while (!rc && res > rtol && it < maxit) {
     double pq = 0.0;
     rc = mfa_apply(ctx, f, p, q, 0);
