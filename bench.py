@@ -31,7 +31,9 @@ import fe_inputs as fi  # noqa: E402
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM traffic per launch of the dominant kernel from one ncu capture, valid only
 # while the kernel source is unchanged (sha1 of hex_kernels.cuh).
-NCU_TRAFFIC = {}
+# 32^3 capture (868.2 MB per launch) scaled by the cell count to the 64^3 launch;
+# see profiles/hex_apply_q6_helmholtz_hex32.md.
+NCU_TRAFFIC = {("d6756fc2c236", "helmholtz", 6): 8 * 868.18e6}
 
 
 def parse_args():
@@ -165,17 +167,21 @@ def sub_box(mesh, cell_node, nx, b):
     return cv, inv.reshape(cn.shape).astype(np.int32), nodes.size, cells.size
 
 
-SAMPLE_BOX = {1: 16, 2: 10, 3: 7, 4: 5, 5: 4, 6: 3, 7: 3, 8: 2}
+# Sub-box edge per degree: ~1-2.5 s of oracle work per operator for the
+# baseline (about 15 s for the 12 operators), ~0.1 s per operator and step
+# for the reference arm.
+SAMPLE_BOX_BASELINE = {1: 64, 2: 40, 3: 28, 4: 20, 5: 14, 6: 12, 7: 8, 8: 6}
+SAMPLE_BOX_STEP = {1: 24, 2: 14, 3: 10, 4: 8, 5: 6, 6: 5, 7: 4, 8: 3}
 
 
-def oracle_rate(mesh, cases, nx, repeats=1):
+def oracle_rate(mesh, cases, nx, repeats=1, boxes=SAMPLE_BOX_STEP):
     """Extrapolated full-mesh apply time per operator from timing the oracle on a sub-box."""
     import oracle
 
     ncell = nx ** 3
     out = []
     for c in cases:
-        b = min(SAMPLE_BOX.get(c["p"], 2), nx)
+        b = min(boxes.get(c["p"], 2), nx)
         cv, cn, nn, nsub = sub_box(mesh, c["cell_node"], nx, b)
         pb = oracle.Problem(oracle.HEX, mesh.coords, cv, c["p"], cn, nn, FORM_IDS[c["form"]], k2=1.0)
         xs = fi.uniform_vector(nn, seed=5)
@@ -315,7 +321,7 @@ def gpu_arm(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = oracle_rate(mesh, cases, args.nx)
+        r = oracle_rate(mesh, cases, args.nx, boxes=SAMPLE_BOX_BASELINE)
         full_s = sum(o["full_s"] for o in r)
         cpu = {"value": ndof_step / full_s / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
                "sample": "per operator a box of cells of the %d^3 mesh (%s), timed once; full-mesh time "
