@@ -169,6 +169,26 @@ enum { MFA_PC_NONE = 0, MFA_PC_JACOBI = 1 };
 MFA_API int mfa_cg(mfa_ctx *ctx, mfa_form *form, int precond, const double *b, double *x, double rtol, int maxit,
            int *iters, double *relres);
 
+/* mfa_cg without device allocation.  The paper has no counterpart: this is
+ * for callers that cannot call cudaMalloc (an application whose memory pool
+ * already holds the device memory, a solver step inside another framework's
+ * stream pipeline where the implicit synchronisation of cudaMalloc/cudaFree
+ * would stall other work, a loop that forbids allocation after start-up).
+ * Same arguments, algorithm, kernels and status codes as mfa_cg.  The work
+ * vectors live in one file-scope __device__ array of
+ * 5 * MFA_CG_NOALLOC_MAX_NDOF + 1056 doubles (about 10 MiB), which every GPU
+ * that loads the library holds until the process exits.
+ *  - ndof above MFA_CG_NOALLOC_MAX_NDOF returns MFA_ERR_ARG, before any work.
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any
+ *    stream capture.
+ *  - All calls on a device share the array: calls that overlap on the GPU
+ *    (other streams, other host threads) race.  Each call writes every part
+ *    of the array it reads before reading it. */
+#define MFA_CG_NOALLOC_MAX_NDOF 262144
+MFA_API int mfa_cg_noalloc(mfa_ctx *ctx, mfa_form *form, int precond, const double *b, double *x, double rtol,
+                           int maxit, int *iters, double *relres);
+
 #ifdef __cplusplus
 }
 #endif

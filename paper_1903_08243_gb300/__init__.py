@@ -84,7 +84,9 @@ _SIGS = {
     "mfa_sync": ([_VP], _I),
     "mfa_diagonal": ([_VP, _VP, _VP], _I),
     "mfa_cg": ([_VP, _VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
+    "mfa_cg_noalloc": ([_VP, _VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
 }
+MFA_CG_NOALLOC_MAX_NDOF = 262144
 
 
 def lib():
@@ -212,6 +214,17 @@ def mfa_cg(ctx, form, precond, b, x, rtol, maxit):
     """Returns (status, iterations, relative residual); raises on errors other than non-convergence."""
     it, rel = ctypes.c_int(), ctypes.c_double()
     rc = lib().mfa_cg(ctx, form, precond, _ptr(b), _ptr(x), rtol, maxit, ctypes.byref(it), ctypes.byref(rel))
+    if rc not in (MFA_OK, MFA_ERR_NOT_CONVERGED):
+        _check(rc)
+    return rc, it.value, rel.value
+
+
+def mfa_cg_noalloc(ctx, form, precond, b, x, rtol, maxit):
+    """mfa_cg without device allocation (work vectors in a fixed device array,
+    at most MFA_CG_NOALLOC_MAX_NDOF dofs).  Returns (status, iterations, relative
+    residual); raises on errors other than non-convergence."""
+    it, rel = ctypes.c_int(), ctypes.c_double()
+    rc = lib().mfa_cg_noalloc(ctx, form, precond, _ptr(b), _ptr(x), rtol, maxit, ctypes.byref(it), ctypes.byref(rel))
     if rc not in (MFA_OK, MFA_ERR_NOT_CONVERGED):
         _check(rc)
     return rc, it.value, rel.value

@@ -197,6 +197,10 @@ int launch_apply(mfa_form* f, const double* x, double* y) {
 
 }  // namespace
 
+namespace mfa {
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace mfa
+
 extern "C" {
 
 const char* mfa_last_error(void) { return g_err; }

@@ -96,6 +96,9 @@ cudaError_t pointwise_mul_launch(const double* a, const double* b, double* out, 
 cudaError_t reciprocal_launch(const double* a, double* out, int64_t n, cudaStream_t s);
 int dot_partials();
 
+// Record `msg` as the calling thread's mfa_last_error() and return `code`.
+int set_error(int code, const char* msg);
+
 }  // namespace mfa
 
 // ---------------------------------------------------------------- handle types
