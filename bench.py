@@ -33,7 +33,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # while the kernel source is unchanged (sha1 of hex_kernels.cuh).
 # 32^3 capture (868.2 MB per launch) scaled by the cell count to the 64^3 launch;
 # see profiles/hex_apply_q6_helmholtz_hex32.md.
-NCU_TRAFFIC = {("d6756fc2c236", "helmholtz", 6): 8 * 868.18e6}
+NCU_TRAFFIC = {("d6756fc2c236", "Q6 helmholtz"): 8 * 868.18e6}
 
 
 def parse_args():
@@ -42,7 +42,11 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mfa", "reference"], default="mfa")
-    ap.add_argument("--nx", type=int, default=64)
+    ap.add_argument("--workload", choices=["hex", "tet-p1-mass", "tet-p2"], default="hex",
+                    help="hex: 64^3 Q1-Q6 Laplace+Helmholtz; tet-p1-mass: 8^3x6 P1 mass; "
+                         "tet-p2: 48^3x6 vector P2 elasticity + neo-Hookean residual")
+    ap.add_argument("--nx", type=int, default=None)
+    ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
     ap.add_argument("--degrees", default="1,2,3,4,5,6")
     ap.add_argument("--forms", default="laplace,helmholtz")
     ap.add_argument("--scatter", choices=["atomic", "colour"], default="atomic")
@@ -51,24 +55,50 @@ def parse_args():
     return ap.parse_args()
 
 
-FORM_IDS = {"mass": 0, "laplace": 1, "helmholtz": 2}
+FORM_IDS = {"mass": 0, "laplace": 1, "helmholtz": 2, "elasticity": 3, "hyper_res": 4, "hyper_jac": 5}
 
 
 def workload_name(args):
-    return "hex%d^3-perturbed0.1h-Q%s-%s-fp64" % (args.nx, args.degrees.replace(",", ""), args.forms.replace(",", "+"))
+    if args.workload == "hex":
+        return "hex%d^3-perturbed0.1h-Q%s-%s-fp64" % (args.nx, args.degrees.replace(",", ""),
+                                                      args.forms.replace(",", "+"))
+    if args.workload == "tet-p1-mass":
+        return "tet-kuhn%d^3x6-P1-mass-fp64" % args.nx
+    return "tet-kuhn%d^3x6-P2vec-elasticity+neohookean-residual-fp64" % args.nx
 
 
 def build_cases(args):
-    degrees = [int(p) for p in args.degrees.split(",")]
-    forms = args.forms.split(",")
-    mesh = fi.hex_box_mesh(args.nx, perturb=0.1, seed=1)
+    """Operators of one step.  Each case holds the seeded inputs shared by the GPU and the oracle."""
+    if args.nx is None:
+        args.nx = {"hex": 64, "tet-p1-mass": 8, "tet-p2": 48}[args.workload]
     cases = []
-    for p in degrees:
-        cell_node, nnode = fi.hex_node_map(args.nx, p)
-        x = fi.uniform_vector(nnode, seed=1)
-        for f in forms:
-            cases.append(dict(form=f, p=p, cell_node=cell_node, nnode=nnode, x=x))
-    return mesh, cases
+    if args.workload == "hex":
+        mesh = fi.hex_box_mesh(args.nx, perturb=0.1, seed=1)
+        for p in [int(p) for p in args.degrees.split(",")]:
+            cell_node, nnode = fi.hex_node_map(args.nx, p)
+            x = fi.uniform_vector(nnode, seed=1)
+            for f in args.forms.split(","):
+                cases.append(dict(name="Q%d %s" % (p, f), cell_type=8, mesh=mesh, p=p, ncomp=1, form=f,
+                                  cell_node=cell_node, nnode=nnode, x=x, kw=dict(k2=1.0), okw=dict(k2=1.0),
+                                  qdeg=p + 1))
+    elif args.workload == "tet-p1-mass":
+        mesh = fi.kuhn_tet_mesh(args.nx)
+        x = fi.uniform_vector(mesh.nvert, seed=0)
+        cases.append(dict(name="P1 mass", cell_type=4, mesh=mesh, p=1, ncomp=1, form="mass",
+                          cell_node=mesh.cell_vert, nnode=mesh.nvert, x=x, kw={}, okw={}, qdeg=2))
+    else:
+        mesh = fi.kuhn_tet_mesh(args.nx)
+        cn, nnode, edges = fi.p2_node_map(mesh.cell_vert, mesh.nvert)
+        u = fi.sinusoid_displacement(fi.p2_node_coords(mesh.coords, edges), seed=2).ravel()
+        cases.append(dict(name="P2 elasticity", cell_type=4, mesh=mesh, p=2, ncomp=3, form="elasticity",
+                          cell_node=cn, nnode=nnode, x=u, kw=dict(lam=1.0, mu=1.0), okw=dict(lam=1.0, mu=1.0),
+                          qdeg=4))
+        cases.append(dict(name="P2 neo-Hookean residual", cell_type=4, mesh=mesh, p=2, ncomp=3, form="hyper_res",
+                          cell_node=cn, nnode=nnode, x=u, kw=dict(lam=1.0, mu=1.0, law=1),
+                          okw=dict(lam=1.0, mu=1.0, law=1), qdeg=4))
+    for c in cases:
+        c["ndof"] = c["nnode"] * c["ncomp"]
+    return cases
 
 
 def kernel_hash():
@@ -158,66 +188,66 @@ def allreduce_max(world, v):
 
 # ------------------------------------------------------------------ CPU oracle (baseline / reference arm)
 
-def sub_box(mesh, cell_node, nx, b):
-    """The first b^3 box of cells of the structured mesh, with compact node numbering."""
-    k, j, i = np.meshgrid(np.arange(b), np.arange(b), np.arange(b), indexing="ij")
-    cells = (i + nx * (j + nx * k)).ravel()
-    cv, cn = mesh.cell_vert[cells], cell_node[cells]
+def sub_mesh(case, ncell_sample):
+    """The first cells of the mesh (a slab of boxes), with compact node numbering."""
+    cells = np.arange(min(ncell_sample, case["mesh"].ncell))
+    cv, cn = case["mesh"].cell_vert[cells], case["cell_node"][cells]
     nodes, inv = np.unique(cn, return_inverse=True)
-    return cv, inv.reshape(cn.shape).astype(np.int32), nodes.size, cells.size
+    return cv, inv.reshape(cn.shape).astype(np.int32), nodes, cells.size
 
 
-# Sub-box edge per degree: ~1-2.5 s of oracle work per operator for the
-# baseline (about 15 s for the 12 operators), ~0.1 s per operator and step
-# for the reference arm.
-SAMPLE_BOX_BASELINE = {1: 64, 2: 40, 3: 28, 4: 20, 5: 14, 6: 12, 7: 8, 8: 6}
-SAMPLE_BOX_STEP = {1: 24, 2: 14, 3: 10, 4: 8, 5: 6, 6: 5, 7: 4, 8: 3}
+# Cells per oracle sample: about 1-2.5 s of oracle work per operator for the
+# baseline, about 0.1 s per operator and step for the reference arm.
+SAMPLE_BASELINE = {("hex", 1): 262144, ("hex", 2): 64000, ("hex", 3): 21952, ("hex", 4): 8000, ("hex", 5): 2744,
+                   ("hex", 6): 1728, ("hex", 7): 512, ("hex", 8): 216, ("tet", 1): 3072, ("tet", 2): 200000}
+SAMPLE_STEP = {("hex", 1): 13824, ("hex", 2): 2744, ("hex", 3): 1000, ("hex", 4): 512, ("hex", 5): 216,
+               ("hex", 6): 125, ("hex", 7): 64, ("hex", 8): 27, ("tet", 1): 3072, ("tet", 2): 6000}
 
 
-def oracle_rate(mesh, cases, nx, repeats=1, boxes=SAMPLE_BOX_STEP):
-    """Extrapolated full-mesh apply time per operator from timing the oracle on a sub-box."""
+def oracle_rate(cases, repeats=1, samples=SAMPLE_STEP):
+    """Extrapolated full-mesh oracle time per operator from timing it on a sub-mesh."""
     import oracle
 
-    ncell = nx ** 3
     out = []
     for c in cases:
-        b = min(boxes.get(c["p"], 2), nx)
-        cv, cn, nn, nsub = sub_box(mesh, c["cell_node"], nx, b)
-        pb = oracle.Problem(oracle.HEX, mesh.coords, cv, c["p"], cn, nn, FORM_IDS[c["form"]], k2=1.0)
-        xs = fi.uniform_vector(nn, seed=5)
+        ncell = c["mesh"].ncell
+        key = ("hex" if c["cell_type"] == 8 else "tet", c["p"])
+        cv, cn, nodes, nsub = sub_mesh(c, samples.get(key, 64))
+        coef = None
+        xs = c["x"].reshape(-1, c["ncomp"])[nodes].ravel()
+        pb = oracle.Problem(c["cell_type"], c["mesh"].coords, cv, c["p"], cn, nodes.size, FORM_IDS[c["form"]],
+                            ncomp=c["ncomp"], qdeg=c["qdeg"], ucoef=coef, **c["okw"])
         best = None
         for _ in range(repeats):
             t0 = time.perf_counter()
             pb.apply(xs)
             dt = time.perf_counter() - t0
             best = dt if best is None else min(best, dt)
-        out.append(dict(form=c["form"], p=c["p"], sample_cells=nsub, sample_s=best, full_s=best * ncell / nsub,
-                        ndof=c["nnode"]))
+        out.append(dict(name=c["name"], sample_cells=nsub, sample_s=best, full_s=best * ncell / nsub, ndof=c["ndof"]))
     return out
 
 
 def reference_arm(args, world, rank):
     if rank != 0:
         return
-    mesh, cases = build_cases(args)
+    cases = build_cases(args)
     for _ in range(args.warmup):
-        oracle_rate(mesh, cases[:1], args.nx)
+        oracle_rate(cases[:1])
     times, samples = [], None
     for _ in range(args.steps):
-        r = oracle_rate(mesh, cases, args.nx)
+        r = oracle_rate(cases)
         samples = r
         times.append(sum(o["full_s"] for o in r))
-    ndof = sum(c["nnode"] for c in cases)
+    ndof = sum(c["ndof"] for c in cases)
     step_s = statistics.mean(times)
     value = ndof / step_s / 1e9
-    sample_desc = "per operator a box of cells (%s) of the %d^3 mesh; full-mesh time extrapolated by cell count" % (
-        ", ".join("Q%d %s: %d cells" % (o["p"], o["form"], o["sample_cells"]) for o in samples), args.nx)
+    sample_desc = "per operator the first cells of the mesh (%s); full-mesh time extrapolated by cell count" % (
+        ", ".join("%s: %d cells" % (o["name"], o["sample_cells"]) for o in samples))
     line = {
         "impl": "reference", "metric": "operator-action GDoF/s", "value": value, "unit": "GDoF/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args), "mesh": "%d^3 hex, interior vertices perturbed U[-0.1h,0.1h]" % args.nx,
-                   "quadrature": "p+1 Gauss points per direction", "input": "x ~ U[-1,1) seed 1"},
+        "config": {"workload": workload_name(args), "operators": [c["name"] for c in cases]},
         "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": sample_desc},
         "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -237,33 +267,66 @@ def gpu_arm(args, world, rank, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     ctx = mfa.Context(local, stream)
-    mesh, cases = build_cases(args)
-    m = mfa.Mesh(ctx, mfa.MFA_CELL_HEX8, mesh.coords, mesh.cell_vert)
+    cases = build_cases(args)
     scatter = mfa.MFA_SCATTER_ATOMIC if args.scatter == "atomic" else mfa.MFA_SCATTER_COLOUR
-    spaces, ops = {}, []
+    meshes, spaces, ops = {}, {}, []
     for c in cases:
-        if c["p"] not in spaces:
-            spaces[c["p"]] = mfa.Space(m, c["p"], 1, c["cell_node"], c["nnode"])
-        form = mfa.Form(spaces[c["p"]], FORM_IDS[c["form"]], k2=1.0, scatter=scatter)
+        mk = id(c["mesh"])
+        if mk not in meshes:
+            meshes[mk] = mfa.Mesh(ctx, c["cell_type"], c["mesh"].coords, c["mesh"].cell_vert)
+        sk = (mk, c["p"], c["ncomp"])
+        if sk not in spaces:
+            spaces[sk] = mfa.Space(meshes[mk], c["p"], c["ncomp"], c["cell_node"], c["nnode"])
+        form = mfa.Form(spaces[sk], FORM_IDS[c["form"]], scatter=scatter, qdeg=c["qdeg"] if c["cell_type"] == 8 else 0,
+                        **c["kw"])
         x = torch.from_numpy(c["x"]).to("cuda")
         y = torch.empty_like(x)
-        info = form.info()
-        ops.append(dict(case=c, form=form, x=x, y=y, info=info))
+        ops.append(dict(case=c, form=form, x=x, y=y, info=form.info()))
     ctx.sync()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
     launches_per_step = sum(o["info"].ncolours if o["info"].scatter == mfa.MFA_SCATTER_COLOUR else 1 for o in ops)
 
-    def step(events=None):
+    def step(events=None, s=None):
+        s = s or stream
         for i, o in enumerate(ops):
             if events is not None:
-                events[i][0].record(stream)
+                events[i][0].record(s)
             mfa.mfa_apply(ctx.h, o["form"].h, o["x"], o["y"], False)
+            if events is not None:
+                events[i][1].record(s)
+
+    graphs = None
+    if args.graph:
+        # one graph per operator so that events can bracket each replay
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        mfa.mfa_set_stream(ctx.h, side)
+        with torch.cuda.stream(side):
+            step(s=side)
+        side.synchronize()
+        graphs = []
+        for o in ops:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=side):
+                mfa.mfa_apply(ctx.h, o["form"].h, o["x"], o["y"], False)
+            graphs.append(g)
+        mfa.mfa_set_stream(ctx.h, stream)
+        torch.cuda.synchronize()
+
+    def run_step(events=None):
+        if graphs is None:
+            step(events)
+            return
+        for i, g in enumerate(graphs):
+            if events is not None:
+                events[i][0].record(stream)
+            g.replay()
             if events is not None:
                 events[i][1].record(stream)
 
     for _ in range(args.warmup):
         flush.fill_(1.0)
-        step()
+        run_step()
     ctx.sync()
     ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in ops]
           for _ in range(args.steps)]
@@ -275,7 +338,7 @@ def gpu_arm(args, world, rank, local):
     t_wall = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(float(k))  # L2 flush between steps, outside the per-operator events
-        step(ev[k])
+        run_step(ev[k])
     torch.cuda.synchronize()
     barrier(world)
     t_wall = time.perf_counter() - t_wall
@@ -284,9 +347,8 @@ def gpu_arm(args, world, rank, local):
     ctx.sync()
     per_op_ms = [statistics.mean(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
                  for i in range(len(ops))]
-    step_ms = sum(per_op_ms)
-    step_ms = allreduce_max(world, step_ms)
-    ndof_step = sum(o["case"]["nnode"] for o in ops)
+    step_ms = allreduce_max(world, sum(per_op_ms))
+    ndof_step = sum(o["case"]["ndof"] for o in ops)
     value = world * ndof_step / (step_ms / 1e3) / 1e9
 
     # dominant kernel roofline (FP64 pipe)
@@ -294,13 +356,12 @@ def gpu_arm(args, world, rank, local):
     dom = ops[i_dom]
     achieved = dom["info"].flops / (per_op_ms[i_dom] / 1e3) / 1e12
     kh = kernel_hash()
-    traffic = NCU_TRAFFIC.get((kh, dom["case"]["form"], dom["case"]["p"]))
+    traffic = NCU_TRAFFIC.get((kh, dom["case"]["name"])) if dom["case"]["cell_type"] == 8 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "hex_apply_kernel<n=%d,nq=%d,%s>" % (dom["case"]["p"] + 1, dom["case"]["p"] + 1,
-                                                                 dom["case"]["form"]),
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "operator": dom["case"]["name"],
                 "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (FP64 pipe; recipe unit counts)",
-                "algorithmic_flops_per_launch": dom["info"].flops, "kernel_sha1": kh}
+                "algorithmic_flops_per_launch": dom["info"].flops, "algorithmic_bytes_per_launch": dom["info"].bytes,
+                "kernel_sha1": kh if dom["case"]["cell_type"] == 8 else None}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
@@ -321,29 +382,37 @@ def gpu_arm(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = oracle_rate(mesh, cases, args.nx, boxes=SAMPLE_BOX_BASELINE)
+        r = oracle_rate(cases, samples=SAMPLE_BASELINE)
         full_s = sum(o["full_s"] for o in r)
         cpu = {"value": ndof_step / full_s / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
-               "sample": "per operator a box of cells of the %d^3 mesh (%s), timed once; full-mesh time "
-                         "extrapolated by cell count" % (args.nx, ", ".join("Q%d %s %d cells %.2fs" % (
-                             o["p"], o["form"], o["sample_cells"], o["sample_s"]) for o in r))}
+               "sample": "per operator the first cells of the mesh (%s), timed once; full-mesh time extrapolated "
+                         "by cell count" % ", ".join("%s %d cells %.2fs" % (o["name"], o["sample_cells"], o["sample_s"])
+                                                     for o in r)}
 
     per_op = []
     for o, ms in zip(ops, per_op_ms):
-        per_op.append({"form": o["case"]["form"], "p": o["case"]["p"], "ndof": o["case"]["nnode"], "ms": ms,
-                       "gdof_s": o["case"]["nnode"] / ms / 1e6, "gflop_s": o["info"].flops / ms / 1e6,
-                       "frac_fp64": o["info"].flops / ms / 1e9 / FP64_PEAK_TFLOPS})
+        per_op.append({"operator": o["case"]["name"], "ndof": o["case"]["ndof"], "ms": ms,
+                       "gdof_s": o["case"]["ndof"] / ms / 1e6, "gflop_s": o["info"].flops / ms / 1e6,
+                       "frac_fp64": o["info"].flops / ms / 1e9 / FP64_PEAK_TFLOPS, "ncolours": o["info"].ncolours})
     if rank == 0:
+        cfg = {"workload": workload_name(args), "operators": [c["name"] for c in cases], "scatter": args.scatter,
+               "ndof_per_step": ndof_step, "graph_replay": bool(args.graph),
+               "l2": "flushed between steps (256 MiB write outside the timed events)",
+               "parallelism": "replicas" if world > 1 else "single"}
+        if args.workload == "hex":
+            cfg.update({"mesh": "%d^3 hex, interior vertices perturbed U[-0.1h,0.1h], seed 1" % args.nx,
+                        "quadrature": "p+1 Gauss points per direction", "geometry": "stored FP64 G per point",
+                        "input": "x ~ U[-1,1) seed 1"})
+        elif args.workload == "tet-p1-mass":
+            cfg.update({"mesh": "%d^3 boxes x 6 Kuhn tets" % args.nx, "quadrature": "degree 2",
+                        "input": "x ~ U[-1,1) seed 0"})
+        else:
+            cfg.update({"mesh": "%d^3 boxes x 6 Kuhn tets" % args.nx, "quadrature": "degree 4",
+                        "lambda": 1.0, "mu": 1.0, "input": "sinusoid displacement, 8 terms, amplitude 0.05, seed 2"})
         line = {
             "metric": "operator-action GDoF/s", "value": value, "unit": "GDoF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args), "mesh": "%d^3 hex, interior vertices perturbed U[-0.1h,0.1h], seed 1" % args.nx,
-                       "degrees": [int(p) for p in args.degrees.split(",")], "forms": args.forms.split(","),
-                       "quadrature": "p+1 Gauss points per direction", "geometry": "stored FP64 G per point",
-                       "scatter": args.scatter, "input": "x ~ U[-1,1) seed 1", "ndof_per_step": ndof_step,
-                       "l2": "flushed between steps (256 MiB write outside the timed events)",
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches_per_step * args.steps, "wall_s_timed_region": t_wall, "per_operator": per_op,
         }

@@ -77,6 +77,11 @@ enum {
 };
 
 enum { MFA_LAW_SVK = 0, MFA_LAW_NEOHOOKE = 1 };
+/* Arithmetic of the element kernel.  FP64: everything in double.  FP32: float
+ * arithmetic with geometric factors computed in FP64 and stored as float.
+ * BF16: x, the geometric factors and the 1D tables rounded to bfloat16, float
+ * arithmetic and accumulation.  x and y stay FP64 in memory for all three.
+ * FP32/BF16 cover hexahedral forms with p+1 points per direction. */
 enum { MFA_PREC_FP64 = 0, MFA_PREC_FP32 = 1, MFA_PREC_BF16 = 2 };
 enum { MFA_SCATTER_AUTO = 0, MFA_SCATTER_COLOUR = 1, MFA_SCATTER_ATOMIC = 2 };
 

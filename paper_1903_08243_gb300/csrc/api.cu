@@ -68,7 +68,8 @@ void count_work(mfa_form* f) {
     per_cell = 2.0 * sweeps + n * n * n;                                            // B, B^T and the scatter add
     if (kind != MFA_FORM_MASS) per_cell += 12.0 * q * q * q * q + 15.0 * q * q * q;  // D, D^T, G g
     if (kind != MFA_FORM_LAPLACE) per_cell += q * q * q;                            // c0 w|J| u
-    bytes = ncell * (4.0 * n * n * n + 8.0 * mfa::hex_geom_entries(kind) * q * q * q);
+    const double esz = f->p.precision == MFA_PREC_FP64 ? 8.0 : (f->p.precision == MFA_PREC_FP32 ? 4.0 : 2.0);
+    bytes = ncell * (4.0 * n * n * n + esz * mfa::hex_geom_entries(kind) * q * q * q);
   } else {
     const double nl = sp->nloc, nc = sp->ncomp, nq = f->nq;
     double per_q = 0.0;
@@ -182,7 +183,8 @@ int launch_apply(mfa_form* f, const double* x, double* y) {
     cudaError_t e;
     if (sp->mesh->cell_type == MFA_CELL_HEX8) {
       mfa::HexApplyArgs a{x, y, sp->d_cell_node, f->d_geom, list, count, ctx->d_err};
-      e = mfa::hex_apply_launch(sp->degree + 1, f->nq1, f->p.kind, colour, f->hex, a, ctx->sm_count, ctx->stream);
+      e = mfa::hex_apply_launch(sp->degree + 1, f->nq1, f->p.kind, f->p.precision, colour, f->hex, a, ctx->sm_count,
+                                ctx->stream);
     } else {
       mfa::TetApplyArgs a = tet_args(f, x, y);
       a.cell_list = list;
@@ -354,8 +356,10 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
   if (prm->scatter < MFA_SCATTER_AUTO || prm->scatter > MFA_SCATTER_ATOMIC)
     return fail(MFA_ERR_ARG, "mfa_form_create: scatter %d", prm->scatter);
   if (prm->law != MFA_LAW_SVK && prm->law != MFA_LAW_NEOHOOKE) return fail(MFA_ERR_ARG, "mfa_form_create: law %d", prm->law);
-  if (prm->precision != MFA_PREC_FP64)
-    return fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: precision %d (this build: FP64)", prm->precision);
+  if (prm->precision < MFA_PREC_FP64 || prm->precision > MFA_PREC_BF16)
+    return fail(MFA_ERR_ARG, "mfa_form_create: precision %d", prm->precision);
+  if (prm->precision != MFA_PREC_FP64 && (ct != MFA_CELL_HEX8 || (prm->qdeg > 0 && prm->qdeg != sp->degree + 1)))
+    return fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: FP32/BF16 cover hex forms with p+1 points per direction");
   if (kind >= MFA_FORM_ELASTICITY && sp->ncomp != 3)
     return fail(MFA_ERR_ARG, "mfa_form_create: form %d needs a 3-component space", kind);
   if (ct == MFA_CELL_HEX8 && (sp->ncomp != 1 || kind > MFA_FORM_HELMHOLTZ))
@@ -383,11 +387,13 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
     f->nq = f->nq1 * f->nq1 * f->nq1;
     if (!rc) {
       const int ng = mfa::hex_geom_entries(kind);
-      rc = cuda_alloc((void**)&f->d_geom, sizeof(double) * ng * f->nq * sp->mesh->ncell, "geometric factors");
+      const size_t esz = prm->precision == MFA_PREC_FP64 ? 8 : (prm->precision == MFA_PREC_FP32 ? 4 : 2);
+      rc = cuda_alloc((void**)&f->d_geom, esz * ng * f->nq * sp->mesh->ncell, "geometric factors");
       const double c0 = kind == MFA_FORM_HELMHOLTZ ? prm->k2 : 1.0;
       if (!rc) {
-        cudaError_t e = mfa::hex_geometry_launch(f->nq1, kind, c0, f->hex, sp->mesh->d_coords, sp->mesh->d_cell_vert,
-                                                 sp->mesh->ncell, f->d_geom, ctx->d_err, ctx->stream);
+        cudaError_t e = mfa::hex_geometry_launch(f->nq1, kind, prm->precision, c0, f->hex, sp->mesh->d_coords,
+                                                 sp->mesh->d_cell_vert, sp->mesh->ncell, f->d_geom, ctx->d_err,
+                                                 ctx->stream);
         if (e != cudaSuccess) rc = fail(MFA_ERR_CUDA, "geometry kernel: %s", cudaGetErrorString(e));
       }
       if (!rc) rc = mfa_sync(ctx);
@@ -487,7 +493,9 @@ int mfa_diagonal(mfa_ctx* ctx, mfa_form* f, double* d) {
   MFA_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * ndof, ctx->stream));
   cudaError_t e;
   if (sp->mesh->cell_type == MFA_CELL_HEX8) {
-    e = mfa::hex_diagonal_launch(sp->degree + 1, f->nq1, f->p.kind, f->hex, sp->d_cell_node, f->d_geom,
+    if (f->p.precision != MFA_PREC_FP64) return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: FP64 forms only");
+    e = mfa::hex_diagonal_launch(sp->degree + 1, f->nq1, f->p.kind, f->hex, sp->d_cell_node,
+                                 static_cast<const double*>(f->d_geom),
                                  sp->mesh->ncell, d, ctx->sm_count, ctx->stream);
   } else {
     mfa::TetApplyArgs a = tet_args(f, nullptr, nullptr);

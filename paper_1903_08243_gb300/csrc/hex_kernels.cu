@@ -14,9 +14,19 @@ namespace {
 // G = w|det J| J^{-1} J^{-T} (6 entries) and c0 w|det J| (Sections 2.1 and
 // 4.1: the Jacobian of a bilinear/trilinear map is evaluated at every
 // quadrature point).  Computed once in FP64 and stored [cell][entry][q].
-__global__ void hex_geometry_kernel(const __grid_constant__ HexTables tb, int nq1, int ng, double c0, const double* __restrict__ coords,
-                                    const int32_t* __restrict__ cell_vert, int64_t ncell, double* __restrict__ geom,
-                                    int* err) {
+template <typename TG>
+__device__ __forceinline__ void store_geo(TG* p, double v);
+template <>
+__device__ __forceinline__ void store_geo<double>(double* p, double v) { *p = v; }
+template <>
+__device__ __forceinline__ void store_geo<float>(float* p, double v) { *p = (float)v; }
+template <>
+__device__ __forceinline__ void store_geo<__nv_bfloat16>(__nv_bfloat16* p, double v) { *p = __double2bfloat16(v); }
+
+template <typename TG>
+__global__ void hex_geometry_kernel(const __grid_constant__ HexTables tb, int nq1, int ng, double c0,
+                                    const double* __restrict__ coords, const int32_t* __restrict__ cell_vert,
+                                    int64_t ncell, TG* __restrict__ geom, int* err) {
   const int pq = nq1 * nq1 * nq1;
   const int64_t total = ncell * pq;
   for (int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gid < total;
@@ -47,7 +57,7 @@ __global__ void hex_geometry_kernel(const __grid_constant__ HexTables tb, int nq
     const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
     if (!(det != 0.0) || !isfinite(det)) {
       atomicOr(err, 1);
-      for (int e = 0; e < ng; ++e) geom[(cell * ng + e) * pq + q] = 0.0;
+      for (int e = 0; e < ng; ++e) store_geo(geom + (cell * ng + e) * pq + q, 0.0);
       continue;
     }
     // inverse by the adjugate: Ji[i][j] = cof[j][i] / det
@@ -62,66 +72,59 @@ __global__ void hex_geometry_kernel(const __grid_constant__ HexTables tb, int nq
     Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
     Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
     const double wdet = w * fabs(det);
-    double* out = geom + cell * ng * pq + q;
+    TG* out = geom + cell * ng * pq + q;
     if (ng == 1) {
-      out[0] = c0 * wdet;
+      store_geo(out, c0 * wdet);
       continue;
     }
     const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
     for (int e = 0; e < 6; ++e) {
       const int r = ia[e], c = ib[e];
-      out[e * pq] = wdet * (Ji[r][0] * Ji[c][0] + Ji[r][1] * Ji[c][1] + Ji[r][2] * Ji[c][2]);
+      store_geo(out + e * pq, wdet * (Ji[r][0] * Ji[c][0] + Ji[r][1] * Ji[c][1] + Ji[r][2] * Ji[c][2]));
     }
-    if (ng == 7) out[6 * pq] = c0 * wdet;
+    if (ng == 7) store_geo(out + 6 * pq, c0 * wdet);
   }
 }
 
 }  // namespace
 
-cudaError_t hex_geometry_launch(int nq, int kind, double c0, const HexTables& tb, const double* coords,
-                                const int32_t* cell_vert, int64_t ncell, double* geom, int* err, cudaStream_t s) {
+cudaError_t hex_geometry_launch(int nq, int kind, int prec, double c0, const HexTables& tb, const double* coords,
+                                const int32_t* cell_vert, int64_t ncell, void* geom, int* err, cudaStream_t s) {
   const int64_t total = ncell * nq * nq * nq;
   if (total == 0) return cudaSuccess;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 65535 * 8) blocks = 65535 * 8;
-  hex_geometry_kernel<<<(unsigned)blocks, 256, 0, s>>>(tb, nq, hex_geom_entries(kind), c0, coords, cell_vert, ncell,
-                                                       geom, err);
+  const int ng = hex_geom_entries(kind);
+  if (prec == MFA_PREC_FP64)
+    hex_geometry_kernel<double><<<(unsigned)blocks, 256, 0, s>>>(tb, nq, ng, c0, coords, cell_vert, ncell,
+                                                                 static_cast<double*>(geom), err);
+  else if (prec == MFA_PREC_FP32)
+    hex_geometry_kernel<float><<<(unsigned)blocks, 256, 0, s>>>(tb, nq, ng, c0, coords, cell_vert, ncell,
+                                                                static_cast<float*>(geom), err);
+  else
+    hex_geometry_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, s>>>(tb, nq, ng, c0, coords, cell_vert, ncell,
+                                                                        static_cast<__nv_bfloat16*>(geom), err);
   return cudaGetLastError();
 }
 
-#define MFA_HEX_CASE(NN, NQQ)                                                                         \
-  if (n == NN && nq == NQQ) {                                                                         \
-    switch (kind) {                                                                                   \
-      case MFA_FORM_MASS:                                                                             \
-        return colour ? hexk::launch_apply<NN, NQQ, MFA_FORM_MASS, true>(tb, a, sm_count, s)          \
-                      : hexk::launch_apply<NN, NQQ, MFA_FORM_MASS, false>(tb, a, sm_count, s);        \
-      case MFA_FORM_LAPLACE:                                                                          \
-        return colour ? hexk::launch_apply<NN, NQQ, MFA_FORM_LAPLACE, true>(tb, a, sm_count, s)       \
-                      : hexk::launch_apply<NN, NQQ, MFA_FORM_LAPLACE, false>(tb, a, sm_count, s);     \
-      case MFA_FORM_HELMHOLTZ:                                                                        \
-        return colour ? hexk::launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, true>(tb, a, sm_count, s)     \
-                      : hexk::launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, false>(tb, a, sm_count, s);   \
-      default:                                                                                        \
-        return cudaErrorInvalidValue;                                                                 \
-    }                                                                                                 \
-  }
-
-cudaError_t hex_apply_launch(int n, int nq, int kind, bool colour, const HexTables& tb, const HexApplyArgs& a,
-                             int sm_count, cudaStream_t s) {
-  MFA_HEX_CASE(2, 2)
-  MFA_HEX_CASE(3, 3)
-  MFA_HEX_CASE(4, 4)
-  MFA_HEX_CASE(5, 5)
-  MFA_HEX_CASE(6, 6)
-  MFA_HEX_CASE(7, 7)
-  MFA_HEX_CASE(8, 8)
-  MFA_HEX_CASE(9, 9)
-  MFA_HEX_CASE(2, 3)
-  MFA_HEX_CASE(3, 4)
-  MFA_HEX_CASE(4, 5)
-  MFA_HEX_CASE(5, 6)
-  MFA_HEX_CASE(6, 7)
-  MFA_HEX_CASE(7, 8)
+cudaError_t hex_apply_launch(int n, int nq, int kind, int prec, bool colour, const HexTables& tb,
+                             const HexApplyArgs& a, int sm_count, cudaStream_t s) {
+  if (prec != MFA_PREC_FP64) return hex_apply_launch_mixed(n, nq, kind, prec, colour, tb, a, sm_count, s);
+  using namespace hexk;
+  MFA_HEX_KIND_CASES(2, 2, MFA_PREC_FP64)
+  MFA_HEX_KIND_CASES(3, 3, MFA_PREC_FP64)
+  MFA_HEX_KIND_CASES(4, 4, MFA_PREC_FP64)
+  MFA_HEX_KIND_CASES(5, 5, MFA_PREC_FP64)
+  MFA_HEX_KIND_CASES(6, 6, MFA_PREC_FP64)
+  MFA_HEX_KIND_CASES(7, 7, MFA_PREC_FP64)
+  MFA_HEX_KIND_CASES(8, 8, MFA_PREC_FP64)
+  MFA_HEX_KIND_CASES(9, 9, MFA_PREC_FP64)
+  MFA_HEX_KIND_CASES(2, 3, MFA_PREC_FP64)
+  MFA_HEX_KIND_CASES(3, 4, MFA_PREC_FP64)
+  MFA_HEX_KIND_CASES(4, 5, MFA_PREC_FP64)
+  MFA_HEX_KIND_CASES(5, 6, MFA_PREC_FP64)
+  MFA_HEX_KIND_CASES(6, 7, MFA_PREC_FP64)
+  MFA_HEX_KIND_CASES(7, 8, MFA_PREC_FP64)
   return cudaErrorInvalidValue;
 }
 

@@ -24,14 +24,45 @@
 // each cell a slab of n^3 threads; blocks loop persistently over batches.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "mfa_internal.h"
 
 namespace mfa {
 namespace hexk {
 
+// Arithmetic and storage types of one precision variant.  FP64: everything
+// in double.  FP32: float arithmetic, geometric factors stored as float.
+// BF16: the streamed operands (x and the geometric factors) and the 1D
+// tables are rounded to bfloat16, arithmetic and accumulation are float.
+// The geometric factors are always computed in FP64 and only then rounded.
+template <int PREC>
+struct Prec;
+template <>
+struct Prec<MFA_PREC_FP64> {
+  using T = double;
+  using TG = double;
+  static __device__ __forceinline__ T in(double v) { return v; }
+  static __device__ __forceinline__ T geo(const TG* p) { return __ldg(p); }
+};
+template <>
+struct Prec<MFA_PREC_FP32> {
+  using T = float;
+  using TG = float;
+  static __device__ __forceinline__ T in(double v) { return (float)v; }
+  static __device__ __forceinline__ T geo(const TG* p) { return __ldg(p); }
+};
+template <>
+struct Prec<MFA_PREC_BF16> {
+  using T = float;
+  using TG = __nv_bfloat16;
+  static __device__ __forceinline__ T in(double v) { return __bfloat162float(__double2bfloat16(v)); }
+  static __device__ __forceinline__ T geo(const TG* p) { return __bfloat162float(*p); }
+};
+
 constexpr int ceil32(int x) { return (x + 31) / 32 * 32; }
 
-template <int N, int NQ>
+template <int N, int NQ, int ELEM = 8>
 struct Shape {
   static constexpr int PN = N * N * N;
   static constexpr int PQ = NQ * NQ * NQ;
@@ -39,7 +70,7 @@ struct Shape {
   static constexpr int P = M * M * M;
   static constexpr int CB = P <= 128 ? 256 / P : 1;  // cells per block
   static constexpr int T = ceil32(CB * P);           // threads per block
-  static constexpr int SMEM = (NQ * N + NQ * NQ + 2 * CB * P + 3 * CB * PQ) * 8;
+  static constexpr int SMEM = (NQ * N + NQ * NQ + 2 * CB * P + 3 * CB * PQ) * ELEM;
 };
 
 template <int KIND>
@@ -47,28 +78,33 @@ __host__ __device__ constexpr int geom_entries() {
   return KIND == MFA_FORM_MASS ? 1 : (KIND == MFA_FORM_LAPLACE ? 6 : 7);
 }
 
-template <int N, int NQ, int KIND, bool COLOUR>
-__global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_kernel(const __grid_constant__ HexTables tb, const HexApplyArgs a) {
+template <int N, int NQ, int KIND, bool COLOUR, int PREC>
+__global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_kernel(const __grid_constant__ HexTables tb,
+                                                                    const HexApplyArgs a) {
   using S = Shape<N, NQ>;
+  using T = typename Prec<PREC>::T;
+  using TG = typename Prec<PREC>::TG;
   constexpr int P = S::P, PN = S::PN, PQ = S::PQ, CB = S::CB;
   constexpr int NG = geom_entries<KIND>();
-  extern __shared__ double smem[];
-  double* sB = smem;              // [NQ][N]
-  double* sD = sB + NQ * N;       // [NQ][NQ]
-  double* bufA = sD + NQ * NQ;    // [CB][P]
-  double* bufB = bufA + CB * P;   // [CB][P]
-  double* F = bufB + CB * P;      // [3][CB][PQ]
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  T* sB = smem;              // [NQ][N]
+  T* sD = sB + NQ * N;       // [NQ][NQ]
+  T* bufA = sD + NQ * NQ;    // [CB][P]
+  T* bufB = bufA + CB * P;   // [CB][P]
+  T* F = bufB + CB * P;      // [3][CB][PQ]
+  const TG* geom = static_cast<const TG*>(a.geom);
   const int t = threadIdx.x;
-  for (int i = t; i < NQ * N; i += blockDim.x) sB[i] = tb.B[i];
-  for (int i = t; i < NQ * NQ; i += blockDim.x) sD[i] = tb.D[i];
+  for (int i = t; i < NQ * N; i += blockDim.x) sB[i] = Prec<PREC>::in(tb.B[i]);
+  for (int i = t; i < NQ * NQ; i += blockDim.x) sD[i] = Prec<PREC>::in(tb.D[i]);
 
   const int cl = t / P;  // cell slot of this thread
   const int pt = t - cl * P;
-  double* A = bufA + cl * P;
-  double* Bf = bufB + cl * P;
-  double* F0 = F + cl * PQ;
-  double* F1 = F0 + CB * PQ;
-  double* F2 = F1 + CB * PQ;
+  T* A = bufA + cl * P;
+  T* Bf = bufB + cl * P;
+  T* F0 = F + cl * PQ;
+  T* F1 = F0 + CB * PQ;
+  T* F2 = F1 + CB * PQ;
   const int64_t nbatch = (a.count + CB - 1) / CB;
 
   for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
@@ -81,20 +117,20 @@ __global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_kernel(const __grid
     int32_t node = 0;
     if (valid && pt < PN) {
       node = __ldg(a.cell_node + cell * PN + pt);
-      A[pt] = __ldg(a.x + node);
+      A[pt] = Prec<PREC>::in(__ldg(a.x + node));
     }
     // stored geometric factors of this point (consumed after three sweeps)
-    double g[NG];
+    T g[NG];
     if (valid && pt < PQ) {
 #pragma unroll
-      for (int e = 0; e < NG; ++e) g[e] = __ldg(a.geom + (cell * NG + e) * PQ + pt);
+      for (int e = 0; e < NG; ++e) g[e] = Prec<PREC>::geo(geom + (cell * NG + e) * PQ + pt);
     }
     __syncthreads();
 
     // B in x: (NQ, N, N) <- (N, N, N)
     if (valid && pt < NQ * N * N) {
       const int i = pt % NQ, jk = pt / NQ;
-      double s = 0.0;
+      T s = 0;
 #pragma unroll
       for (int m = 0; m < N; ++m) s = fma(sB[i * N + m], A[m + N * jk], s);
       Bf[pt] = s;
@@ -103,7 +139,7 @@ __global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_kernel(const __grid
     // B in y: (NQ, NQ, N) <- (NQ, N, N)
     if (valid && pt < NQ * NQ * N) {
       const int i = pt % NQ, j = (pt / NQ) % NQ, k = pt / (NQ * NQ);
-      double s = 0.0;
+      T s = 0;
 #pragma unroll
       for (int m = 0; m < N; ++m) s = fma(sB[j * N + m], Bf[i + NQ * (m + N * k)], s);
       A[pt] = s;
@@ -112,7 +148,7 @@ __global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_kernel(const __grid
     // B in z: (NQ, NQ, NQ) <- (NQ, NQ, N)
     if (valid && pt < PQ) {
       const int ij = pt % (NQ * NQ), k = pt / (NQ * NQ);
-      double s = 0.0;
+      T s = 0;
 #pragma unroll
       for (int m = 0; m < N; ++m) s = fma(sB[k * N + m], A[ij + NQ * NQ * m], s);
       Bf[pt] = s;
@@ -122,10 +158,10 @@ __global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_kernel(const __grid
     if constexpr (KIND == MFA_FORM_MASS) {
       if (valid && pt < PQ) A[pt] = g[0] * Bf[pt];
     } else {
-      double v0 = 0.0;
+      T v0 = 0;
       if (valid && pt < PQ) {
         const int i = pt % NQ, j = (pt / NQ) % NQ, k = pt / (NQ * NQ);
-        double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+        T d0 = 0, d1 = 0, d2 = 0;
 #pragma unroll
         for (int m = 0; m < NQ; ++m) {
           d0 = fma(sD[i * NQ + m], Bf[m + NQ * (j + NQ * k)], d0);
@@ -141,7 +177,7 @@ __global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_kernel(const __grid
       __syncthreads();
       if (valid && pt < PQ) {
         const int i = pt % NQ, j = (pt / NQ) % NQ, k = pt / (NQ * NQ);
-        double r = v0;
+        T r = v0;
 #pragma unroll
         for (int m = 0; m < NQ; ++m) {
           r = fma(sD[m * NQ + i], F0[m + NQ * (j + NQ * k)], r);
@@ -156,7 +192,7 @@ __global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_kernel(const __grid
     // B^T in z: (NQ, NQ, N) <- (NQ, NQ, NQ)
     if (valid && pt < NQ * NQ * N) {
       const int ij = pt % (NQ * NQ), c = pt / (NQ * NQ);
-      double s = 0.0;
+      T s = 0;
 #pragma unroll
       for (int m = 0; m < NQ; ++m) s = fma(sB[m * N + c], A[ij + NQ * NQ * m], s);
       Bf[pt] = s;
@@ -165,7 +201,7 @@ __global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_kernel(const __grid
     // B^T in y: (NQ, N, N) <- (NQ, NQ, N)
     if (valid && pt < NQ * N * N) {
       const int i = pt % NQ, b = (pt / NQ) % N, c = pt / (NQ * N);
-      double s = 0.0;
+      T s = 0;
 #pragma unroll
       for (int m = 0; m < NQ; ++m) s = fma(sB[m * N + b], Bf[i + NQ * (m + NQ * c)], s);
       A[pt] = s;
@@ -174,23 +210,23 @@ __global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_kernel(const __grid
     // B^T in x and scatter-add: (N, N, N) <- (NQ, N, N)
     if (valid && pt < PN) {
       const int i = pt % N, bc = pt / N;
-      double s = 0.0;
+      T s = 0;
 #pragma unroll
       for (int m = 0; m < NQ; ++m) s = fma(sB[m * N + i], A[m + NQ * bc], s);
       if constexpr (COLOUR) {
-        a.y[node] += s;  // no other cell of this colour touches `node`
+        a.y[node] += (double)s;  // no other cell of this colour touches `node`
       } else {
-        atomicAdd(a.y + node, s);
+        atomicAdd(a.y + node, (double)s);
       }
     }
     __syncthreads();
   }
 }
 
-template <int N, int NQ, int KIND, bool COLOUR>
+template <int N, int NQ, int KIND, bool COLOUR, int PREC>
 cudaError_t launch_apply(const HexTables& tb, const HexApplyArgs& a, int sm_count, cudaStream_t s) {
-  using S = Shape<N, NQ>;
-  auto kern = hex_apply_kernel<N, NQ, KIND, COLOUR>;
+  using S = Shape<N, NQ, (int)sizeof(typename Prec<PREC>::T)>;
+  auto kern = hex_apply_kernel<N, NQ, KIND, COLOUR, PREC>;
   static int blocks_per_sm = -1;
   if (blocks_per_sm < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
@@ -205,6 +241,24 @@ cudaError_t launch_apply(const HexTables& tb, const HexApplyArgs& a, int sm_coun
   kern<<<(unsigned)grid, S::T, S::SMEM, s>>>(tb, a);
   return cudaGetLastError();
 }
+
+// Dispatch over the supported (n, nq) pairs for one precision.
+#define MFA_HEX_KIND_CASES(NN, NQQ, PREC)                                                              \
+  if (n == NN && nq == NQQ) {                                                                          \
+    switch (kind) {                                                                                    \
+      case MFA_FORM_MASS:                                                                              \
+        return colour ? launch_apply<NN, NQQ, MFA_FORM_MASS, true, PREC>(tb, a, sm_count, s)           \
+                      : launch_apply<NN, NQQ, MFA_FORM_MASS, false, PREC>(tb, a, sm_count, s);         \
+      case MFA_FORM_LAPLACE:                                                                           \
+        return colour ? launch_apply<NN, NQQ, MFA_FORM_LAPLACE, true, PREC>(tb, a, sm_count, s)        \
+                      : launch_apply<NN, NQQ, MFA_FORM_LAPLACE, false, PREC>(tb, a, sm_count, s);      \
+      case MFA_FORM_HELMHOLTZ:                                                                         \
+        return colour ? launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, true, PREC>(tb, a, sm_count, s)      \
+                      : launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, false, PREC>(tb, a, sm_count, s);    \
+      default:                                                                                         \
+        return cudaErrorInvalidValue;                                                                  \
+    }                                                                                                  \
+  }
 
 // Matrix-free diagonal d_i = sum_K A_K[i][i] (for Jacobi preconditioning).
 // With phi_i = l_a(x) l_b(y) l_c(z) and stored G, the diagonal is a sum of 7

@@ -47,17 +47,19 @@ struct HexApplyArgs {
   const double* x;
   double* y;
   const int32_t* cell_node;  // [ncell][n^3]
-  const double* geom;        // [ncell][ng][nq^3]
+  const void* geom;          // [ncell][ng][nq^3], double / float / bfloat16 by precision
   const int32_t* cell_list;  // cells to process (nullptr: 0..count-1)
   int64_t count;             // number of cells to process
   int* err;
 };
 
 // Launch the sum-factorised FP64 action for cells [list].  Returns a cudaError_t.
-cudaError_t hex_apply_launch(int n, int nq, int kind, bool colour, const HexTables& tb, const HexApplyArgs& a,
-                             int sm_count, cudaStream_t s);
-cudaError_t hex_geometry_launch(int nq, int kind, double c0, const HexTables& tb, const double* coords,
-                                const int32_t* cell_vert, int64_t ncell, double* geom, int* err, cudaStream_t s);
+cudaError_t hex_apply_launch(int n, int nq, int kind, int prec, bool colour, const HexTables& tb,
+                             const HexApplyArgs& a, int sm_count, cudaStream_t s);
+cudaError_t hex_apply_launch_mixed(int n, int nq, int kind, int prec, bool colour, const HexTables& tb,
+                                   const HexApplyArgs& a, int sm_count, cudaStream_t s);
+cudaError_t hex_geometry_launch(int nq, int kind, int prec, double c0, const HexTables& tb, const double* coords,
+                                const int32_t* cell_vert, int64_t ncell, void* geom, int* err, cudaStream_t s);
 cudaError_t hex_diagonal_launch(int n, int nq, int kind, const HexTables& tb, const int32_t* cell_node,
                                 const double* geom, int64_t ncell, double* d, int sm_count, cudaStream_t s);
 int hex_geom_entries(int kind);  // stored FP64 values per quadrature point
@@ -140,7 +142,7 @@ struct mfa_form {
   int scatter = MFA_SCATTER_ATOMIC;
   mfa::HexTables hex{};
   mfa::TetTables tet{};
-  double* d_geom = nullptr;
+  void* d_geom = nullptr;
   const double* d_coef = nullptr;
   double* d_stage_x = nullptr;   // mfa_apply_host staging
   double* d_stage_y = nullptr;

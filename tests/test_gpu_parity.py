@@ -68,6 +68,34 @@ def test_hex_parity(ctx, p, kind, scatter):
     compare(run(ctx, form, x), ref)
 
 
+PREC = {"fp32": (mfa.MFA_PREC_FP32, 1e-5), "bf16": (mfa.MFA_PREC_BF16, 1e-2)}
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("kind", ["mass", "laplace", "helmholtz"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_hex_mixed_precision_against_fp64_oracle(ctx, p, kind, prec):
+    """FP32 arithmetic within 1e-5, BF16 operands with FP32 accumulation within 1e-2 (relative L2)."""
+    nx = {1: 7, 2: 5, 3: 5, 4: 3, 5: 3, 6: 3, 7: 2, 8: 2}[p]
+    case = hex_case(nx, p)
+    x = fi.uniform_vector(case["nnode"], seed=16)
+    ref = oracle_problem(case, kind, k2=1.0).apply(x)
+    code, tol = PREC[prec]
+    form = gpu_form(ctx, case, kind, k2=1.0, precision=code)
+    y = run(ctx, form, x)
+    rel = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    assert rel <= tol, rel
+    if prec == "fp32":
+        assert rel > 1e-12  # really computed in reduced precision
+
+
+def test_mixed_precision_rejected_where_not_built(ctx):
+    case = tet_case(2, 1)
+    with pytest.raises(mfa.MfaError) as e:
+        gpu_form(ctx, case, "mass", precision=mfa.MFA_PREC_FP32)
+    assert e.value.code == mfa.MFA_ERR_UNSUPPORTED
+
+
 @pytest.mark.parametrize("p", [1, 3, 6])
 def test_hex_paper_quadrature_p_plus_2(ctx, p):
     """Table 2 uses p+2 Gauss points per direction on hexahedra."""
