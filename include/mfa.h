@@ -174,6 +174,28 @@ enum { MFA_PC_NONE = 0, MFA_PC_JACOBI = 1 };
 MFA_API int mfa_cg(mfa_ctx *ctx, mfa_form *form, int precond, const double *b, double *x, double rtol, int maxit,
            int *iters, double *relres);
 
+/* Many operators in one call (spec batching; the paper applies one
+ * operator per parloop).  y_k = A_k(x_k) for k < n; each y_k is overwritten.
+ * Hexahedral forms with the atomic scatter and p+1 points are grouped by
+ * (degree, kind, precision) and each group runs as one persistent launch over
+ * all its forms' cells; other forms get their own launch.  Synchronous: the
+ * call returns when every y_k is complete.  x_k, y_k: device, FP64. */
+MFA_API int mfa_apply_batched(mfa_ctx *ctx, int n, mfa_form *const *forms, const double *const *xs,
+                              double *const *ys);
+
+/* The same batch built once and recorded into a CUDA graph (zeroing of every
+ * y_k, then the grouped and single launches).  mfa_batch_apply replays it
+ * asynchronously on the context stream as one graph launch.  The forms and
+ * vectors are borrowed and must outlive the batch; mfa_batch_create runs the
+ * batch once eagerly and waits.  mfa_batch_info reports the number of grouped
+ * launches and of single-form launches. */
+typedef struct mfa_batch mfa_batch;
+MFA_API int mfa_batch_create(mfa_ctx *ctx, int n, mfa_form *const *forms, const double *const *xs, double *const *ys,
+                             mfa_batch **out);
+MFA_API int mfa_batch_apply(mfa_ctx *ctx, mfa_batch *batch);
+MFA_API int mfa_batch_info(const mfa_batch *batch, int *ngroups, int *nsingles);
+MFA_API int mfa_batch_destroy(mfa_batch *batch);
+
 /* mfa_cg without device allocation.  The paper has no counterpart: this is
  * for callers that cannot call cudaMalloc (an application whose memory pool
  * already holds the device memory, a solver step inside another framework's

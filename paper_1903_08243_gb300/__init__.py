@@ -84,6 +84,11 @@ _SIGS = {
     "mfa_sync": ([_VP], _I),
     "mfa_diagonal": ([_VP, _VP, _VP], _I),
     "mfa_cg": ([_VP, _VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
+    "mfa_apply_batched": ([_VP, _I, _VP, _VP, _VP], _I),
+    "mfa_batch_create": ([_VP, _I, _VP, _VP, _VP, _PP], _I),
+    "mfa_batch_apply": ([_VP, _VP], _I),
+    "mfa_batch_info": ([_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "mfa_batch_destroy": ([_VP], _I),
     "mfa_cg_noalloc": ([_VP, _VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
 }
 MFA_CG_NOALLOC_MAX_NDOF = 262144
@@ -217,6 +222,39 @@ def mfa_cg(ctx, form, precond, b, x, rtol, maxit):
     if rc not in (MFA_OK, MFA_ERR_NOT_CONVERGED):
         _check(rc)
     return rc, it.value, rel.value
+
+
+def _ptr_array(items, ctype=ctypes.c_void_p):
+    arr = (ctype * max(1, len(items)))()
+    for i, it in enumerate(items):
+        arr[i] = it if isinstance(it, int) or it is None else (it.value if isinstance(it, ctypes.c_void_p) else _ptr(it))
+    return arr
+
+
+def mfa_apply_batched(ctx, forms, xs, ys):
+    fa = _ptr_array([f.value for f in forms])
+    _check(lib().mfa_apply_batched(ctx, len(forms), fa, _ptr_array(xs), _ptr_array(ys)))
+
+
+def mfa_batch_create(ctx, forms, xs, ys):
+    h = ctypes.c_void_p()
+    fa = _ptr_array([f.value for f in forms])
+    _check(lib().mfa_batch_create(ctx, len(forms), fa, _ptr_array(xs), _ptr_array(ys), ctypes.byref(h)))
+    return h
+
+
+def mfa_batch_apply(ctx, batch):
+    _check(lib().mfa_batch_apply(ctx, batch))
+
+
+def mfa_batch_info(batch):
+    g, s = ctypes.c_int(), ctypes.c_int()
+    _check(lib().mfa_batch_info(batch, ctypes.byref(g), ctypes.byref(s)))
+    return g.value, s.value
+
+
+def mfa_batch_destroy(batch):
+    _check(lib().mfa_batch_destroy(batch))
 
 
 def mfa_cg_noalloc(ctx, form, precond, b, x, rtol, maxit):

@@ -172,7 +172,12 @@ mfa::TetApplyArgs tet_args(mfa_form* f, const double* x, double* y) {
   return a;
 }
 
-int launch_apply(mfa_form* f, const double* x, double* y) {
+}  // namespace
+
+namespace mfa {
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+int apply_form(mfa_form* f, const double* x, double* y, cudaStream_t stream) {
   mfa_space* sp = f->space;
   mfa_ctx* ctx = f->ctx;
   const bool colour = f->scatter == MFA_SCATTER_COLOUR;
@@ -184,23 +189,19 @@ int launch_apply(mfa_form* f, const double* x, double* y) {
     if (sp->mesh->cell_type == MFA_CELL_HEX8) {
       mfa::HexApplyArgs a{x, y, sp->d_cell_node, f->d_geom, list, count, ctx->d_err};
       e = mfa::hex_apply_launch(sp->degree + 1, f->nq1, f->p.kind, f->p.precision, colour, f->hex, a, ctx->sm_count,
-                                ctx->stream);
+                                stream);
     } else {
       mfa::TetApplyArgs a = tet_args(f, x, y);
       a.cell_list = list;
       a.count = count;
       e = mfa::tet_apply_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, f->tet, a, ctx->sm_count,
-                                ctx->stream);
+                                stream);
     }
     if (e != cudaSuccess) return fail(MFA_ERR_CUDA, "apply kernel launch: %s", cudaGetErrorString(e));
   }
   return MFA_OK;
 }
 
-}  // namespace
-
-namespace mfa {
-int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 }  // namespace mfa
 
 extern "C" {
@@ -451,7 +452,7 @@ int mfa_apply(mfa_ctx* ctx, mfa_form* f, const double* x, double* y, int accumul
   MFA_CUDA(cudaSetDevice(ctx->device));
   const int64_t ndof = f->space->nnode * f->space->ncomp;
   if (!accumulate) MFA_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * ndof, ctx->stream));
-  return launch_apply(f, x, y);
+  return mfa::apply_form(f, x, y, ctx->stream);
 }
 
 int mfa_apply_host(mfa_ctx* ctx, mfa_form* f, const double* xh, double* yh) {

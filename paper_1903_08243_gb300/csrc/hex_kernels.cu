@@ -4,6 +4,12 @@
 
 namespace mfa {
 
+int hex_cells_per_block(int n, int nq) {
+  const int m = n > nq ? n : nq;
+  const int p = m * m * m;
+  return p <= 128 ? 256 / p : 1;  // hexk::Shape<N, NQ>::CB
+}
+
 int hex_geom_entries(int kind) {
   return kind == MFA_FORM_MASS ? 1 : (kind == MFA_FORM_LAPLACE ? 6 : 7);
 }
@@ -125,6 +131,21 @@ cudaError_t hex_apply_launch(int n, int nq, int kind, int prec, bool colour, con
   MFA_HEX_KIND_CASES(5, 6, MFA_PREC_FP64)
   MFA_HEX_KIND_CASES(6, 7, MFA_PREC_FP64)
   MFA_HEX_KIND_CASES(7, 8, MFA_PREC_FP64)
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t hex_group_launch(int n, int kind, int prec, const HexTables& tb, const HexApplyArgs* items,
+                             const int64_t* first, int nitems, int64_t total, int sm_count, cudaStream_t s) {
+  if (prec != MFA_PREC_FP64) return hex_group_launch_mixed(n, kind, prec, tb, items, first, nitems, total, sm_count, s);
+  using namespace hexk;
+  MFA_HEX_GROUP_CASES(2, MFA_PREC_FP64)
+  MFA_HEX_GROUP_CASES(3, MFA_PREC_FP64)
+  MFA_HEX_GROUP_CASES(4, MFA_PREC_FP64)
+  MFA_HEX_GROUP_CASES(5, MFA_PREC_FP64)
+  MFA_HEX_GROUP_CASES(6, MFA_PREC_FP64)
+  MFA_HEX_GROUP_CASES(7, MFA_PREC_FP64)
+  MFA_HEX_GROUP_CASES(8, MFA_PREC_FP64)
+  MFA_HEX_GROUP_CASES(9, MFA_PREC_FP64)
   return cudaErrorInvalidValue;
 }
 

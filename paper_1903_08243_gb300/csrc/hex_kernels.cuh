@@ -78,36 +78,59 @@ __host__ __device__ constexpr int geom_entries() {
   return KIND == MFA_FORM_MASS ? 1 : (KIND == MFA_FORM_LAPLACE ? 6 : 7);
 }
 
+// Shared-memory working set of one block (types by precision).
+template <int N, int NQ, int PREC>
+struct Smem {
+  using S = Shape<N, NQ>;
+  using T = typename Prec<PREC>::T;
+  T* sB;  // [NQ][N]
+  T* sD;  // [NQ][NQ]
+  T* A;   // this thread's cell slot of buffer A
+  T* Bf;  // this thread's cell slot of buffer B
+  T* F0;
+  T* F1;
+  T* F2;
+  int cl, pt;
+  __device__ __forceinline__ void init(unsigned char* raw, const HexTables& tb) {
+    constexpr int P = S::P, PQ = S::PQ, CB = S::CB;
+    T* smem = reinterpret_cast<T*>(raw);
+    sB = smem;
+    sD = sB + NQ * N;
+    T* bufA = sD + NQ * NQ;
+    T* bufB = bufA + CB * P;
+    T* F = bufB + CB * P;
+    const int t = threadIdx.x;
+    for (int i = t; i < NQ * N; i += blockDim.x) sB[i] = Prec<PREC>::in(tb.B[i]);
+    for (int i = t; i < NQ * NQ; i += blockDim.x) sD[i] = Prec<PREC>::in(tb.D[i]);
+    cl = t / P;
+    pt = t - cl * P;
+    A = bufA + cl * P;
+    Bf = bufB + cl * P;
+    F0 = F + cl * PQ;
+    F1 = F0 + CB * PQ;
+    F2 = F1 + CB * PQ;
+  }
+};
+
+// One batch of CB cells of one form: gather, sum-factorised local kernel,
+// scatter.  Every thread of the block calls it (it contains barriers).
 template <int N, int NQ, int KIND, bool COLOUR, int PREC>
-__global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_kernel(const __grid_constant__ HexTables tb,
-                                                                    const HexApplyArgs a) {
+__device__ __forceinline__ void hex_cell_batch(const HexApplyArgs& a, int64_t batch, const Smem<N, NQ, PREC>& sm) {
   using S = Shape<N, NQ>;
   using T = typename Prec<PREC>::T;
   using TG = typename Prec<PREC>::TG;
-  constexpr int P = S::P, PN = S::PN, PQ = S::PQ, CB = S::CB;
+  constexpr int PN = S::PN, PQ = S::PQ, CB = S::CB;
   constexpr int NG = geom_entries<KIND>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* smem = reinterpret_cast<T*>(smem_raw);
-  T* sB = smem;              // [NQ][N]
-  T* sD = sB + NQ * N;       // [NQ][NQ]
-  T* bufA = sD + NQ * NQ;    // [CB][P]
-  T* bufB = bufA + CB * P;   // [CB][P]
-  T* F = bufB + CB * P;      // [3][CB][PQ]
   const TG* geom = static_cast<const TG*>(a.geom);
-  const int t = threadIdx.x;
-  for (int i = t; i < NQ * N; i += blockDim.x) sB[i] = Prec<PREC>::in(tb.B[i]);
-  for (int i = t; i < NQ * NQ; i += blockDim.x) sD[i] = Prec<PREC>::in(tb.D[i]);
-
-  const int cl = t / P;  // cell slot of this thread
-  const int pt = t - cl * P;
-  T* A = bufA + cl * P;
-  T* Bf = bufB + cl * P;
-  T* F0 = F + cl * PQ;
-  T* F1 = F0 + CB * PQ;
-  T* F2 = F1 + CB * PQ;
-  const int64_t nbatch = (a.count + CB - 1) / CB;
-
-  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
+  const T* sB = sm.sB;
+  const T* sD = sm.sD;
+  T* A = sm.A;
+  T* Bf = sm.Bf;
+  T* F0 = sm.F0;
+  T* F1 = sm.F1;
+  T* F2 = sm.F2;
+  const int cl = sm.cl, pt = sm.pt;
+  {
     const int64_t idx = batch * CB + cl;
     const bool valid = (cl < CB) && (idx < a.count);
     int64_t cell = 0;
@@ -224,6 +247,36 @@ __global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_kernel(const __grid
 }
 
 template <int N, int NQ, int KIND, bool COLOUR, int PREC>
+__global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_kernel(const __grid_constant__ HexTables tb,
+                                                                    const HexApplyArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<N, NQ, PREC> sm;
+  sm.init(smem_raw, tb);
+  const int64_t nbatch = (a.count + Shape<N, NQ>::CB - 1) / Shape<N, NQ>::CB;
+  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) hex_cell_batch<N, NQ, KIND, COLOUR, PREC>(a, batch, sm);
+}
+
+// Many forms of one (n, nq, kind, precision) class in one persistent launch:
+// the global batch index runs over all forms' batches (prefix sums in
+// `first`), so blocks move from one operator to the next without a launch.
+template <int N, int NQ, int KIND, int PREC>
+__global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_group_kernel(const __grid_constant__ HexTables tb,
+                                                                          const HexApplyArgs* __restrict__ items,
+                                                                          const int64_t* __restrict__ first,
+                                                                          int nitems) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<N, NQ, PREC> sm;
+  sm.init(smem_raw, tb);
+  const int64_t total = first[nitems];
+  int k = 0;
+  for (int64_t gb = blockIdx.x; gb < total; gb += gridDim.x) {
+    while (k + 1 < nitems && gb >= first[k + 1]) ++k;  // batches only increase within a block
+    const HexApplyArgs a = items[k];
+    hex_cell_batch<N, NQ, KIND, false, PREC>(a, gb - first[k], sm);
+  }
+}
+
+template <int N, int NQ, int KIND, bool COLOUR, int PREC>
 cudaError_t launch_apply(const HexTables& tb, const HexApplyArgs& a, int sm_count, cudaStream_t s) {
   using S = Shape<N, NQ, (int)sizeof(typename Prec<PREC>::T)>;
   auto kern = hex_apply_kernel<N, NQ, KIND, COLOUR, PREC>;
@@ -241,6 +294,39 @@ cudaError_t launch_apply(const HexTables& tb, const HexApplyArgs& a, int sm_coun
   kern<<<(unsigned)grid, S::T, S::SMEM, s>>>(tb, a);
   return cudaGetLastError();
 }
+
+template <int N, int NQ, int KIND, int PREC>
+cudaError_t launch_group(const HexTables& tb, const HexApplyArgs* items, const int64_t* first, int nitems,
+                         int64_t total_batches, int sm_count, cudaStream_t s) {
+  using S = Shape<N, NQ, (int)sizeof(typename Prec<PREC>::T)>;
+  auto kern = hex_apply_group_kernel<N, NQ, KIND, PREC>;
+  static int blocks_per_sm = -1;
+  if (blocks_per_sm < 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, S::T, S::SMEM);
+    if (e != cudaSuccess) return e;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  if (total_batches == 0) return cudaSuccess;
+  const int64_t cap = (int64_t)sm_count * blocks_per_sm;
+  kern<<<(unsigned)(total_batches < cap ? total_batches : cap), S::T, S::SMEM, s>>>(tb, items, first, nitems);
+  return cudaGetLastError();
+}
+
+#define MFA_HEX_GROUP_CASES(NN, PREC)                                                                   \
+  if (n == NN) {                                                                                       \
+    switch (kind) {                                                                                    \
+      case MFA_FORM_MASS:                                                                              \
+        return launch_group<NN, NN, MFA_FORM_MASS, PREC>(tb, items, first, nitems, total, sm_count, s); \
+      case MFA_FORM_LAPLACE:                                                                           \
+        return launch_group<NN, NN, MFA_FORM_LAPLACE, PREC>(tb, items, first, nitems, total, sm_count, s); \
+      case MFA_FORM_HELMHOLTZ:                                                                         \
+        return launch_group<NN, NN, MFA_FORM_HELMHOLTZ, PREC>(tb, items, first, nitems, total, sm_count, s); \
+      default:                                                                                         \
+        return cudaErrorInvalidValue;                                                                  \
+    }                                                                                                  \
+  }
 
 // Dispatch over the supported (n, nq) pairs for one precision.
 #define MFA_HEX_KIND_CASES(NN, NQQ, PREC)                                                              \

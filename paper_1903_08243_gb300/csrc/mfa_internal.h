@@ -58,6 +58,12 @@ cudaError_t hex_apply_launch(int n, int nq, int kind, int prec, bool colour, con
                              const HexApplyArgs& a, int sm_count, cudaStream_t s);
 cudaError_t hex_apply_launch_mixed(int n, int nq, int kind, int prec, bool colour, const HexTables& tb,
                                    const HexApplyArgs& a, int sm_count, cudaStream_t s);
+// One persistent launch over many forms of the same (n, n, kind, precision).
+cudaError_t hex_group_launch(int n, int kind, int prec, const HexTables& tb, const HexApplyArgs* items,
+                             const int64_t* first, int nitems, int64_t total, int sm_count, cudaStream_t s);
+cudaError_t hex_group_launch_mixed(int n, int kind, int prec, const HexTables& tb, const HexApplyArgs* items,
+                                   const int64_t* first, int nitems, int64_t total, int sm_count, cudaStream_t s);
+int hex_cells_per_block(int n, int nq);
 cudaError_t hex_geometry_launch(int nq, int kind, int prec, double c0, const HexTables& tb, const double* coords,
                                 const int32_t* cell_vert, int64_t ncell, void* geom, int* err, cudaStream_t s);
 cudaError_t hex_diagonal_launch(int n, int nq, int kind, const HexTables& tb, const int32_t* cell_node,
@@ -100,6 +106,8 @@ int dot_partials();
 
 // Record `msg` as the calling thread's mfa_last_error() and return `code`.
 int set_error(int code, const char* msg);
+// Enqueue one form's action on `s` (y must already hold zeros or the sum to add to).
+int apply_form(mfa_form* f, const double* x, double* y, cudaStream_t s);
 
 }  // namespace mfa
 

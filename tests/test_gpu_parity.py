@@ -330,3 +330,68 @@ def test_neohookean_inverted_element_reports_domain_error(ctx):
         ctx.sync()
     assert e.value.code == mfa.MFA_ERR_DOMAIN
     ctx.sync()  # the flag was cleared
+
+
+# ------------------------------------------------------------------ batched operators
+
+def _batch_inputs(ctx):
+    rng = np.random.default_rng(77)
+    forms, xs, refs = [], [], []
+    specs = [(1, "helmholtz", "fp64"), (2, "laplace", "fp64"), (2, "laplace", "fp64"), (3, "mass", "fp32"),
+             (3, "helmholtz", "fp32"), (4, "helmholtz", "bf16"), (2, "helmholtz", "fp32"), (8, "helmholtz", "fp64")]
+    keep = []
+    for i, (p, kind, prec) in enumerate(specs):
+        nx = int(rng.integers(2, 5))
+        case = hex_case(nx, p, seed=100 + i)
+        code = {"fp64": mfa.MFA_PREC_FP64, "fp32": mfa.MFA_PREC_FP32, "bf16": mfa.MFA_PREC_BF16}[prec]
+        f = gpu_form(ctx, case, kind, k2=1.0, precision=code)
+        x = fi.uniform_vector(case["nnode"], seed=200 + i)
+        forms.append(f)
+        xs.append(torch.from_numpy(x).cuda())
+        refs.append((oracle_problem(case, kind, k2=1.0).apply(x), {"fp64": 1e-12, "fp32": 1e-5, "bf16": 1e-2}[prec]))
+        keep.append(case)
+    # two forms that cannot be grouped: a tetrahedral one and a coloured one
+    tcase = tet_case(3, 2, ncomp=3, perturb=0.1, seed=9)
+    f = gpu_form(ctx, tcase, "elasticity")
+    x = fi.uniform_vector(tcase["nnode"] * 3, seed=300)
+    forms.append(f)
+    xs.append(torch.from_numpy(x).cuda())
+    refs.append((oracle_problem(tcase, "elasticity").apply(x), 1e-12))
+    hcase = hex_case(3, 2, seed=5)
+    f = gpu_form(ctx, hcase, "helmholtz", scatter=mfa.MFA_SCATTER_COLOUR)
+    x = fi.uniform_vector(hcase["nnode"], seed=301)
+    forms.append(f)
+    xs.append(torch.from_numpy(x).cuda())
+    refs.append((oracle_problem(hcase, "helmholtz").apply(x), 1e-12))
+    return forms, xs, refs
+
+
+def _check_batch(ys, refs):
+    for y, (ref, tol) in zip(ys, refs):
+        yv = y.cpu().numpy()
+        rel = np.linalg.norm(yv - ref) / np.linalg.norm(ref)
+        assert rel <= tol, (rel, tol)
+
+
+def test_apply_batched(ctx):
+    forms, xs, refs = _batch_inputs(ctx)
+    ys = [torch.full_like(x, 7.0) for x in xs]  # overwritten, not accumulated
+    mfa.mfa_apply_batched(ctx.h, [f.h for f in forms], xs, ys)
+    _check_batch(ys, refs)
+
+
+def test_batch_graph_replay(ctx):
+    forms, xs, refs = _batch_inputs(ctx)
+    ys = [torch.empty_like(x) for x in xs]
+    b = mfa.mfa_batch_create(ctx.h, [f.h for f in forms], xs, ys)
+    try:
+        ngroups, nsingles = mfa.mfa_batch_info(b)
+        assert nsingles == 2 and ngroups == 7  # (1,H,64) (2,L,64) (3,M,32) (3,H,32) (4,H,16) (2,H,32) (8,H,64)
+        for y in ys:
+            y.fill_(-1.0)
+        for _ in range(2):
+            mfa.mfa_batch_apply(ctx.h, b)
+        ctx.sync()
+        _check_batch(ys, refs)
+    finally:
+        mfa.mfa_batch_destroy(b)
