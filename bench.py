@@ -42,9 +42,17 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mfa", "reference"], default="mfa")
-    ap.add_argument("--workload", choices=["hex", "tet-p1-mass", "tet-p2"], default="hex",
+    ap.add_argument("--workload", choices=["hex", "tet-p1-mass", "tet-p2", "batched", "pcg"], default="hex",
                     help="hex: 64^3 Q1-Q6 Laplace+Helmholtz; tet-p1-mass: 8^3x6 P1 mass; "
-                         "tet-p2: 48^3x6 vector P2 elasticity + neo-Hookean residual")
+                         "tet-p2: 48^3x6 vector P2 elasticity + neo-Hookean residual; "
+                         "batched: 64 hex Helmholtz operators (degrees 1-8, 8^3-48^3) in one graph; "
+                         "pcg: Q4 64^3 Helmholtz solves to 1e-8, FP64 Jacobi-PCG vs mixed-precision FCG")
+    ap.add_argument("--nrhs", type=int, default=2, help="pcg: right-hand sides timed")
+    ap.add_argument("--inner", type=int, default=16, help="pcg: inner FP32 Jacobi-PCG steps per outer step")
+    ap.add_argument("--inner-precision", choices=["fp32", "bf16", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp32",
+                    help="arithmetic of the batched workload")
+    ap.add_argument("--nops", type=int, default=64)
     ap.add_argument("--nx", type=int, default=None)
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
     ap.add_argument("--degrees", default="1,2,3,4,5,6")
@@ -419,10 +427,185 @@ def gpu_arm(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def batched_specs(nops, seed=3):
+    """Operator list of the batched workload: degree ~ U{1..8}, cells per side ~ U{8..48}."""
+    deg = fi.randint(seed, 0xDE6, nops, 1, 8)
+    side = fi.randint(seed, 0x51DE, nops, 8, 48)
+    return [(int(p), int(n)) for p, n in zip(deg, side)]
+
+
+def batched_arm(args, world, rank, local):
+    import torch
+
+    from paper_1903_08243_gb300 import build as libbuild
+
+    libbuild.build()
+    import paper_1903_08243_gb300 as mfa
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = mfa.Context(local, stream)
+    prec = {"fp64": mfa.MFA_PREC_FP64, "fp32": mfa.MFA_PREC_FP32, "bf16": mfa.MFA_PREC_BF16}[args.precision]
+    specs = batched_specs(args.nops)
+    keep, forms, ref_forms, xs, ys, yrefs, infos = [], [], [], [], [], [], []
+    for i, (p, n) in enumerate(specs):
+        mesh = fi.hex_box_mesh(n, perturb=0.1, seed=1000 + i)
+        cell_node, nnode = fi.hex_node_map(n, p)
+        m = mfa.Mesh(ctx, mfa.MFA_CELL_HEX8, mesh.coords, mesh.cell_vert)
+        sp = mfa.Space(m, p, 1, cell_node, nnode)
+        f = mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ, k2=1.0, precision=prec)
+        x = torch.from_numpy(fi.uniform_vector(nnode, seed=2000 + i)).cuda()
+        keep.append((m, sp))
+        forms.append(f)
+        xs.append(x)
+        ys.append(torch.empty_like(x))
+        infos.append(f.info())
+        if prec != mfa.MFA_PREC_FP64:
+            ref_forms.append(mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ, k2=1.0, precision=mfa.MFA_PREC_FP64))
+            yrefs.append(torch.empty_like(x))
+    ctx.sync()
+    batch = mfa.mfa_batch_create(ctx.h, [f.h for f in forms], xs, ys)
+    ngroups, nsingles = mfa.mfa_batch_info(batch)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        mfa.mfa_batch_apply(ctx.h, batch)
+    ctx.sync()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        mfa.mfa_batch_apply(ctx.h, batch)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall
+    time.sleep(0.3)
+    clocks = sampler.stop()
+    ctx.sync()
+    step_ms = allreduce_max(world, statistics.mean(a.elapsed_time(b) for a, b in ev))
+    ndof = sum(i.ndof for i in infos)
+    value = world * ndof / (step_ms / 1e3) / 1e9
+    errors = []
+    if ref_forms:
+        for f, x, y, yr in zip(ref_forms, xs, ys, yrefs):
+            f.apply(x, yr)
+        ctx.sync()
+        for y, yr in zip(ys, yrefs):
+            errors.append(float(torch.linalg.norm(y - yr) / torch.linalg.norm(yr)))
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    total_bytes = sum(i.bytes for i in infos)
+    total_flops = sum(i.flops for i in infos)
+    if prec == mfa.MFA_PREC_FP64:
+        achieved = total_flops / (step_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None}
+    else:
+        achieved = total_bytes / (step_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": None,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+    roofline.update({"scope": "whole batch graph (all grouped launches) per replay",
+                     "algorithmic_bytes_per_step": total_bytes, "algorithmic_flops_per_step": total_flops})
+    if rank == 0:
+        line = {
+            "metric": "operator-action GDoF/s", "value": value, "unit": "GDoF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16 operands, f32 accumulate"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": "batched-%d-hex-helmholtz-%s" % (args.nops, args.precision),
+                       "operators": "%d Helmholtz (k2=1) operators, degree ~ U{1..8}, n^3 perturbed hexes with n ~ U{8..48}, seed 3" % args.nops,
+                       "degrees": [p for p, _ in specs], "sides": [n for _, n in specs], "ndof_per_step": ndof,
+                       "launch": "one CUDA graph replay: %d grouped persistent launches + %d single launches" % (ngroups, nsingles),
+                       "l2": "flushed between steps (256 MiB write outside the timed events)"},
+            "roofline": roofline, "clocks": clocks, "gpu_launches": (ngroups + nsingles) * args.steps,
+            "error_vs_fp64": {"max": max(errors), "mean": statistics.mean(errors)} if errors else None,
+            "wall_s_timed_region": t_wall, "cpu_baseline": None, "e2e": None,
+        }
+        print(json.dumps(line), flush=True)
+    mfa.mfa_batch_destroy(batch)
+
+
+def pcg_arm(args, world, rank, local):
+    """Time to ||b - A x|| <= 1e-8 ||b||: FP64 Jacobi-PCG against FP64-outer / FP32-inner flexible CG."""
+    import torch
+
+    from paper_1903_08243_gb300 import build as libbuild
+
+    libbuild.build()
+    import paper_1903_08243_gb300 as mfa
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = mfa.Context(local, stream)
+    nx, p = (args.nx or 64), 4
+    mesh = fi.hex_box_mesh(nx, perturb=0.1, seed=1)
+    cell_node, nnode = fi.hex_node_map(nx, p)
+    m = mfa.Mesh(ctx, mfa.MFA_CELL_HEX8, mesh.coords, mesh.cell_vert)
+    sp = mfa.Space(m, p, 1, cell_node, nnode)
+    A64 = mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ, k2=1.0)
+    iprec = {"fp64": mfa.MFA_PREC_FP64, "fp32": mfa.MFA_PREC_FP32, "bf16": mfa.MFA_PREC_BF16}[args.inner_precision]
+    A32 = mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ, k2=1.0, precision=iprec)
+    M64 = mfa.Form(sp, mfa.MFA_FORM_MASS)
+    rtol = 1e-8
+    rows = []
+    sampler = ClockSampler(local)
+    sampler.start()
+    for r in range(args.nrhs + 1):  # the first solve of each method warms up and is not reported
+        f = torch.from_numpy(fi.grf_lattice(nx * p + 1, seed=400 + r)).cuda()
+        b = M64.apply(f)  # b = M f_h
+        ctx.sync()
+        res = {}
+        for name in ("jacobi_pcg_fp64", "fcg_mixed"):
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if name == "jacobi_pcg_fp64":
+                rc, it, rel = mfa.mfa_cg(ctx.h, A64.h, mfa.MFA_PC_JACOBI, b, x, rtol, 20000)
+                inner = 0
+            else:
+                rc, it, inner, rel = mfa.mfa_fcg_mixed(ctx.h, A64.h, A32.h, args.inner, b, x, rtol, 5000)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            true_rel = float(torch.linalg.norm(b - A64.apply(x)) / torch.linalg.norm(b))
+            res[name] = {"seconds": dt, "iterations": it, "inner_iterations": inner, "relres": rel,
+                         "true_relres": true_rel, "status": rc}
+        if r > 0:
+            rows.append(res)
+    clocks = sampler.stop()
+    tj = statistics.mean(r["jacobi_pcg_fp64"]["seconds"] for r in rows)
+    tm = statistics.mean(r["fcg_mixed"]["seconds"] for r in rows)
+    if rank == 0:
+        line = {
+            "metric": "PCG time-to-1e-8", "value": tm, "unit": "s", "n_gpus": world, "steps": args.nrhs,
+            "warmup": 1, "ms_per_step": tm * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 outer / %s inner" % args.inner_precision, "data": "synthetic",
+            "config": {"workload": "pcg-hex%d^3-Q4-helmholtz-grf" % nx, "ndof": nnode,
+                       "rhs": "b = M f_h, f a Gaussian random field (256 random Fourier features, correlation length 0.1) on the node lattice, seeds 401..",
+                       "stop": "FP64 ||b - A x||_2 <= 1e-8 ||b||_2 from x = 0",
+                       "mixed": "flexible CG (FP64 operator) preconditioned by %d steps of Jacobi-PCG with the %s operator" % (args.inner, args.inner_precision)},
+            "jacobi_pcg_fp64_seconds": tj, "speedup_vs_jacobi_pcg_fp64": tj / tm, "solves": rows, "clocks": clocks,
+            "roofline": None, "cpu_baseline": None, "e2e": None,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
-    if args.impl == "reference":
+    if args.workload == "batched" and args.impl != "reference":
+        batched_arm(args, world, rank, local)
+    elif args.workload == "pcg" and args.impl != "reference":
+        pcg_arm(args, world, rank, local)
+    elif args.impl == "reference":
         reference_arm(args, world, rank)
     else:
         gpu_arm(args, world, rank, local)

@@ -19,7 +19,7 @@ from .mesh import (
     shuffle_mesh,
     p2_node_coords,
 )
-from .fields import sinusoid_displacement, uniform_vector, grf_fourier_features
+from .fields import sinusoid_displacement, uniform_vector, grf_fourier_features, grf_lattice
 
 __all__ = [
     "splitmix64",
@@ -36,4 +36,5 @@ __all__ = [
     "sinusoid_displacement",
     "uniform_vector",
     "grf_fourier_features",
+    "grf_lattice",
 ]

@@ -60,3 +60,24 @@ def grf_fourier_features(points, seed, corr_len=0.1, nfeat=1024):
         for j in range(s, e):
             out += np.cos(points @ omega[j] + b[j])
     return np.sqrt(2.0 / nfeat) * out
+
+
+def grf_lattice(m, seed, corr_len=0.1, nfeat=256):
+    """Gaussian random field on the m^3 equispaced lattice of the unit cube.
+
+    Same random Fourier features as ``grf_fourier_features``; on a tensor
+    lattice cos(w.x + b) is the real part of a product of three 1D complex
+    exponentials, so the field is one complex matrix product:
+    f[k, j, i] = Re sum_f c_f E2[f, k] E1[f, j] E0[f, i].  Returned flat with
+    i fastest (lattice point i + m j + m^2 k).
+    """
+    u1 = uniform(seed, 0x6A1, 3 * nfeat, 0.0, 1.0)
+    u2 = uniform(seed, 0x6A2, 3 * nfeat, 0.0, 1.0)
+    z = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+    omega = (z / corr_len).reshape(nfeat, 3)
+    b = uniform(seed, 0x6A3, nfeat, 0.0, 2.0 * np.pi)
+    t = np.linspace(0.0, 1.0, m)
+    E = [np.exp(1j * np.outer(omega[:, d], t)) for d in range(3)]  # [nfeat][m]
+    c = np.sqrt(2.0 / nfeat) * np.exp(1j * b)
+    T = (c[:, None, None] * E[1][:, :, None] * E[0][:, None, :]).reshape(nfeat, m * m)
+    return np.real(E[2].T @ T).reshape(-1)

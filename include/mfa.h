@@ -174,6 +174,19 @@ enum { MFA_PC_NONE = 0, MFA_PC_JACOBI = 1 };
 MFA_API int mfa_cg(mfa_ctx *ctx, mfa_form *form, int precond, const double *b, double *x, double rtol, int maxit,
            int *iters, double *relres);
 
+/* Mixed-precision flexible CG (spec solver; the paper has no solver).
+ * Outer loop: flexible CG (Notay 2000, one stored direction) in FP64 with the
+ * FP64 form `outer`, so convergence is decided on an FP64 residual
+ * ||b - A x||_2 <= rtol ||b||_2.  Preconditioner: `inner_iters` steps of
+ * Jacobi-PCG with the form `inner` (the same operator on the same space,
+ * typically MFA_PREC_FP32), started from zero; inner_iters = 0 gives
+ * Jacobi-preconditioned FCG.  The Jacobi diagonal comes from `outer`.
+ * b, x: device FP64 (x: initial guess in, solution out).  Allocates its work
+ * vectors (11 of ndof doubles) per call.  Returns MFA_ERR_NOT_CONVERGED at
+ * maxit outer iterations, MFA_ERR_BREAKDOWN on p.Ap <= 0 or non-finite values. */
+MFA_API int mfa_fcg_mixed(mfa_ctx *ctx, mfa_form *outer, mfa_form *inner, int inner_iters, const double *b,
+                          double *x, double rtol, int maxit, int *outer_iters, int *inner_total, double *relres);
+
 /* Many operators in one call (spec batching; the paper applies one
  * operator per parloop).  y_k = A_k(x_k) for k < n; each y_k is overwritten.
  * Hexahedral forms with the atomic scatter and p+1 points are grouped by

@@ -84,6 +84,8 @@ _SIGS = {
     "mfa_sync": ([_VP], _I),
     "mfa_diagonal": ([_VP, _VP, _VP], _I),
     "mfa_cg": ([_VP, _VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
+    "mfa_fcg_mixed": ([_VP, _VP, _VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                       ctypes.POINTER(_D)], _I),
     "mfa_apply_batched": ([_VP, _I, _VP, _VP, _VP], _I),
     "mfa_batch_create": ([_VP, _I, _VP, _VP, _VP, _PP], _I),
     "mfa_batch_apply": ([_VP, _VP], _I),
@@ -222,6 +224,16 @@ def mfa_cg(ctx, form, precond, b, x, rtol, maxit):
     if rc not in (MFA_OK, MFA_ERR_NOT_CONVERGED):
         _check(rc)
     return rc, it.value, rel.value
+
+
+def mfa_fcg_mixed(ctx, outer, inner, inner_iters, b, x, rtol, maxit):
+    """Returns (status, outer iterations, inner iterations, relative residual)."""
+    it, inn, rel = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    rc = lib().mfa_fcg_mixed(ctx, outer, inner, inner_iters, _ptr(b), _ptr(x), rtol, maxit, ctypes.byref(it),
+                             ctypes.byref(inn), ctypes.byref(rel))
+    if rc not in (MFA_OK, MFA_ERR_NOT_CONVERGED):
+        _check(rc)
+    return rc, it.value, inn.value, rel.value
 
 
 def _ptr_array(items, ctype=ctypes.c_void_p):

@@ -64,6 +64,22 @@ __global__ void recip_kernel(const double* __restrict__ a, double* __restrict__ 
     out[i] = 1.0 / a[i];
 }
 
+// y += sign * (num / den) * x with the scalars read on the device.
+__global__ void axpy_ratio_kernel(const double* __restrict__ x, double* __restrict__ y, int64_t n,
+                                  const double* __restrict__ num, const double* __restrict__ den, double sign) {
+  const double a = sign * (*num / *den);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], y[i]);
+}
+
+// p = z + (num / den) * p
+__global__ void xpby_ratio_kernel(const double* __restrict__ z, double* __restrict__ p, int64_t n,
+                                  const double* __restrict__ num, const double* __restrict__ den) {
+  const double beta = *num / *den;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+}
+
 unsigned grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
@@ -90,6 +106,20 @@ cudaError_t axpby_launch(double alpha, const double* x, double beta, double* y, 
 cudaError_t pointwise_mul_launch(const double* a, const double* b, double* out, int64_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   mul_kernel<<<grid_for(n), 256, 0, s>>>(a, b, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t axpy_ratio_launch(const double* x, double* y, int64_t n, const double* num, const double* den, double sign,
+                              cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  axpy_ratio_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n, num, den, sign);
+  return cudaGetLastError();
+}
+
+cudaError_t xpby_ratio_launch(const double* z, double* p, int64_t n, const double* num, const double* den,
+                              cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  xpby_ratio_kernel<<<grid_for(n), 256, 0, s>>>(z, p, n, num, den);
   return cudaGetLastError();
 }
 

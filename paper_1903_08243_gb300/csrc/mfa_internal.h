@@ -102,6 +102,10 @@ cudaError_t dot_launch(const double* a, const double* b, int64_t n, double* part
 cudaError_t axpby_launch(double alpha, const double* x, double beta, double* y, int64_t n, cudaStream_t s);
 cudaError_t pointwise_mul_launch(const double* a, const double* b, double* out, int64_t n, cudaStream_t s);
 cudaError_t reciprocal_launch(const double* a, double* out, int64_t n, cudaStream_t s);
+cudaError_t axpy_ratio_launch(const double* x, double* y, int64_t n, const double* num, const double* den, double sign,
+                              cudaStream_t s);
+cudaError_t xpby_ratio_launch(const double* z, double* p, int64_t n, const double* num, const double* den,
+                              cudaStream_t s);
 int dot_partials();
 
 // Record `msg` as the calling thread's mfa_last_error() and return `code`.

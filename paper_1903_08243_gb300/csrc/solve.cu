@@ -1,0 +1,145 @@
+// Mixed-precision flexible CG.
+//
+// Outer: flexible CG (Notay 2000, one stored direction) in FP64 with the FP64
+// operator, so the residual that decides convergence is an FP64 residual.
+// Preconditioner: `inner_iters` steps of Jacobi-PCG on a reduced-precision
+// form of the same operator, started from zero.  On GB300 the FP32 action
+// costs about 1/18 of the FP64 one (HBM-bound against FP64-pipe-bound), so
+// most of the Krylov work moves to the cheap operator while the outer loop
+// keeps the FP64 accuracy.  The inner loop keeps its scalars on the device:
+// it never waits for the host.
+#include <cmath>
+
+#include "mfa_internal.h"
+
+namespace {
+
+struct Vecs {
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *pp = nullptr, *qp = nullptr;
+  double *ri = nullptr, *zi = nullptr, *pi = nullptr, *qi = nullptr, *dinv = nullptr;
+  double* scal = nullptr;     // device scalars: [0] rz, [1] pq, [2] rz_new
+  double* partial = nullptr;  // dot partials
+};
+
+void free_vecs(Vecs& v) {
+  double* all[] = {v.r, v.z, v.p, v.q, v.pp, v.qp, v.ri, v.zi, v.pi, v.qi, v.dinv, v.scal, v.partial};
+  for (double* a : all) cudaFree(a);
+}
+
+}  // namespace
+
+extern "C" int mfa_fcg_mixed(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, int inner_iters, const double* b,
+                             double* x, double rtol, int maxit, int* outer_iters, int* inner_total, double* relres) {
+  if (!ctx || !outer || !inner || !b || !x) return mfa::set_error(MFA_ERR_ARG, "mfa_fcg_mixed: NULL argument");
+  if (outer->p.precision != MFA_PREC_FP64 || outer->p.kind > MFA_FORM_HELMHOLTZ)
+    return mfa::set_error(MFA_ERR_ARG, "mfa_fcg_mixed: the outer form must be an FP64 mass/Laplace/Helmholtz form");
+  if (inner->space != outer->space || inner->p.kind != outer->p.kind)
+    return mfa::set_error(MFA_ERR_ARG, "mfa_fcg_mixed: the inner form must be the same operator on the same space");
+  if (inner_iters < 0 || maxit < 0 || !(rtol > 0.0)) return mfa::set_error(MFA_ERR_ARG, "mfa_fcg_mixed: bad counts");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return mfa::set_error(MFA_ERR_CUDA, "mfa_fcg_mixed: cudaSetDevice");
+  const int64_t n = outer->space->nnode * outer->space->ncomp;
+  cudaStream_t s = ctx->stream;
+  Vecs v;
+  double** slots[] = {&v.r, &v.z, &v.p, &v.q, &v.pp, &v.qp, &v.ri, &v.zi, &v.pi, &v.qi, &v.dinv};
+  for (double** sl : slots)
+    if (cudaMalloc((void**)sl, sizeof(double) * (n > 0 ? n : 1)) != cudaSuccess) {
+      free_vecs(v);
+      return mfa::set_error(MFA_ERR_OOM, "mfa_fcg_mixed: work vectors");
+    }
+  if (cudaMalloc((void**)&v.scal, sizeof(double) * 8) != cudaSuccess ||
+      cudaMalloc((void**)&v.partial, sizeof(double) * mfa::dot_partials()) != cudaSuccess) {
+    free_vecs(v);
+    return mfa::set_error(MFA_ERR_OOM, "mfa_fcg_mixed: scalars");
+  }
+  int rc = MFA_OK;
+  auto ck = [&](cudaError_t e) {
+    if (e != cudaSuccess && !rc) rc = mfa::set_error(MFA_ERR_CUDA, cudaGetErrorString(e));
+  };
+  auto hdot = [&](const double* a, const double* c, double* out) {
+    ck(mfa::dot_launch(a, c, n, v.partial, v.scal + 4, s));
+    ck(cudaMemcpyAsync(out, v.scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+  };
+  // z = M(r): inner_iters steps of Jacobi-PCG on the inner operator from z = 0
+  auto precondition = [&](const double* r, double* z) {
+    ck(cudaMemsetAsync(z, 0, sizeof(double) * n, s));
+    if (inner_iters == 0) {
+      ck(mfa::pointwise_mul_launch(v.dinv, r, z, n, s));
+      return;
+    }
+    ck(cudaMemcpyAsync(v.ri, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    ck(mfa::pointwise_mul_launch(v.dinv, v.ri, v.zi, n, s));
+    ck(cudaMemcpyAsync(v.pi, v.zi, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    double* rz = v.scal + 0;
+    double* pq = v.scal + 1;
+    double* rzn = v.scal + 2;
+    ck(mfa::dot_launch(v.ri, v.zi, n, v.partial, rz, s));
+    for (int k = 0; k < inner_iters && !rc; ++k) {
+      ck(cudaMemsetAsync(v.qi, 0, sizeof(double) * n, s));
+      if (!rc) rc = mfa::apply_form(inner, v.pi, v.qi, s);
+      ck(mfa::dot_launch(v.pi, v.qi, n, v.partial, pq, s));
+      ck(mfa::axpy_ratio_launch(v.pi, z, n, rz, pq, 1.0, s));
+      ck(mfa::axpy_ratio_launch(v.qi, v.ri, n, rz, pq, -1.0, s));
+      if (k + 1 == inner_iters) break;
+      ck(mfa::pointwise_mul_launch(v.dinv, v.ri, v.zi, n, s));
+      ck(mfa::dot_launch(v.ri, v.zi, n, v.partial, rzn, s));
+      ck(mfa::xpby_ratio_launch(v.zi, v.pi, n, rzn, rz, s));
+      std::swap(rz, rzn);
+    }
+  };
+
+  int it = 0, inner_count = 0;
+  double bnorm = 0.0, rr = 0.0, res = 0.0;
+  rc = mfa_diagonal(ctx, outer, v.dinv);
+  ck(rc ? cudaSuccess : mfa::reciprocal_launch(v.dinv, v.dinv, n, s));
+  if (!rc) hdot(b, b, &bnorm);
+  bnorm = std::sqrt(bnorm);
+  if (!rc) rc = mfa_apply(ctx, outer, x, v.r, 0);
+  ck(rc ? cudaSuccess : mfa::axpby_launch(1.0, b, -1.0, v.r, n, s));
+  if (!rc) hdot(v.r, v.r, &rr);
+  res = bnorm > 0.0 ? std::sqrt(rr) / bnorm : std::sqrt(rr);
+  if (!rc && (!std::isfinite(bnorm) || !std::isfinite(rr)))
+    rc = mfa::set_error(MFA_ERR_BREAKDOWN, "mfa_fcg_mixed: non-finite right-hand side");
+  double pq_prev = 0.0;
+  while (!rc && res > rtol && it < maxit) {
+    precondition(v.r, v.z);
+    inner_count += inner_iters;
+    if (it == 0) {
+      ck(cudaMemcpyAsync(v.p, v.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    } else {
+      // p = z - (z.q_prev / p_prev.q_prev) p_prev: A-orthogonal to the last direction
+      double zq = 0.0;
+      hdot(v.z, v.qp, &zq);
+      ck(mfa::axpby_launch(1.0, v.z, -zq / pq_prev, v.pp, n, s));
+      std::swap(v.p, v.pp);  // v.p now holds the new direction
+    }
+    if (rc) break;
+    rc = mfa_apply(ctx, outer, v.p, v.q, 0);
+    double pq = 0.0, pr = 0.0;
+    if (!rc) hdot(v.p, v.q, &pq);
+    if (!rc) hdot(v.p, v.r, &pr);
+    if (rc) break;
+    if (!(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(pr)) {
+      rc = mfa::set_error(MFA_ERR_BREAKDOWN, "mfa_fcg_mixed: breakdown (p.Ap <= 0 or non-finite)");
+      break;
+    }
+    const double alpha = pr / pq;
+    ck(mfa::axpby_launch(alpha, v.p, 1.0, x, n, s));
+    ck(mfa::axpby_launch(-alpha, v.q, 1.0, v.r, n, s));
+    hdot(v.r, v.r, &rr);
+    ++it;
+    res = bnorm > 0.0 ? std::sqrt(rr) / bnorm : std::sqrt(rr);
+    if (!std::isfinite(res)) rc = mfa::set_error(MFA_ERR_BREAKDOWN, "mfa_fcg_mixed: non-finite residual");
+    // keep this direction for the next orthogonalisation
+    std::swap(v.pp, v.p);
+    std::swap(v.qp, v.q);
+    pq_prev = pq;
+  }
+  if (!rc) rc = mfa_sync(ctx);
+  if (!rc && res > rtol) rc = mfa::set_error(MFA_ERR_NOT_CONVERGED, "mfa_fcg_mixed: not converged");
+  if (outer_iters) *outer_iters = it;
+  if (inner_total) *inner_total = inner_count;
+  if (relres) *relres = res;
+  free_vecs(v);
+  return rc;
+}

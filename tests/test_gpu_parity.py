@@ -268,6 +268,29 @@ def test_cg_matches_dense_solve(ctx, precond):
     np.testing.assert_allclose(xd.cpu().numpy(), xs, rtol=0, atol=1e-8 * np.abs(xs).max())
 
 
+@pytest.mark.parametrize("inner_prec,inner_iters", [("fp64", 0), ("fp32", 6), ("bf16", 4), ("fp64", 10)])
+def test_fcg_mixed_matches_dense_solve(ctx, inner_prec, inner_iters):
+    case = hex_case(4, 2)
+    A = oracle_problem(case, "helmholtz").dense()
+    b = fi.uniform_vector(case["nnode"], seed=32)
+    xs = np.linalg.solve(A, b)
+    m = mfa.Mesh(ctx, 8, case["coords"], case["cell_vert"])
+    sp = mfa.Space(m, 2, 1, case["cell_node"], case["nnode"])
+    outer = mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ)
+    code = {"fp64": mfa.MFA_PREC_FP64, "fp32": mfa.MFA_PREC_FP32, "bf16": mfa.MFA_PREC_BF16}[inner_prec]
+    inner = mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ, precision=code)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    rc, it, inn, rel = mfa.mfa_fcg_mixed(ctx.h, outer.h, inner.h, inner_iters, bd, xd, 1e-11, 400)
+    assert rc == mfa.MFA_OK and rel <= 1e-11
+    x = xd.cpu().numpy()
+    assert np.linalg.norm(b - A @ x) <= 2e-11 * np.linalg.norm(b)  # the FP64 residual, recomputed
+    np.testing.assert_allclose(x, xs, rtol=0, atol=1e-8 * np.abs(xs).max())
+    if inner_iters:
+        rc0, it0, _, _ = mfa.mfa_fcg_mixed(ctx.h, outer.h, inner.h, 0, bd, torch.zeros_like(bd), 1e-11, 400)
+        assert it < it0  # the inner solve cuts outer iterations
+
+
 def test_cg_not_converged_status(ctx):
     case = hex_case(3, 2)
     form = gpu_form(ctx, case, "helmholtz")
