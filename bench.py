@@ -50,8 +50,8 @@ def parse_args():
     ap.add_argument("--nrhs", type=int, default=2, help="pcg: right-hand sides timed")
     ap.add_argument("--inner", type=int, default=16, help="pcg: inner FP32 Jacobi-PCG steps per outer step")
     ap.add_argument("--inner-precision", choices=["fp32", "bf16", "fp64"], default="fp32")
-    ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default="fp32",
-                    help="arithmetic of the batched workload")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default=None,
+                    help="arithmetic (hex and batched workloads; default fp64 for hex, fp32 for batched)")
     ap.add_argument("--nops", type=int, default=64)
     ap.add_argument("--nx", type=int, default=None)
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
@@ -285,8 +285,11 @@ def gpu_arm(args, world, rank, local):
         sk = (mk, c["p"], c["ncomp"])
         if sk not in spaces:
             spaces[sk] = mfa.Space(meshes[mk], c["p"], c["ncomp"], c["cell_node"], c["nnode"])
+        prec = {"fp64": mfa.MFA_PREC_FP64, "fp32": mfa.MFA_PREC_FP32, "bf16": mfa.MFA_PREC_BF16}[args.precision]
+        if c["cell_type"] != 8:
+            prec = mfa.MFA_PREC_FP64
         form = mfa.Form(spaces[sk], FORM_IDS[c["form"]], scatter=scatter, qdeg=c["qdeg"] if c["cell_type"] == 8 else 0,
-                        **c["kw"])
+                        precision=prec, **c["kw"])
         x = torch.from_numpy(c["x"]).to("cuda")
         y = torch.empty_like(x)
         ops.append(dict(case=c, form=form, x=x, y=y, info=form.info()))
@@ -600,6 +603,8 @@ def pcg_arm(args, world, rank, local):
 
 def main():
     args = parse_args()
+    if args.precision is None:
+        args.precision = "fp32" if args.workload == "batched" else "fp64"
     world, rank, local = dist_setup(args)
     if args.workload == "batched" and args.impl != "reference":
         batched_arm(args, world, rank, local)

@@ -154,6 +154,16 @@ MFA_API int mfa_form_destroy(mfa_form *form);
  * ndof FP64 entries, must not overlap.  Asynchronous on the context stream.
  * Section 2.2 global assembly with the Section 2.1 local kernel. */
 MFA_API int mfa_apply(mfa_ctx *ctx, mfa_form *form, const double *x, double *y, int accumulate);
+/* The action of an FP32 or BF16 form on float vectors: x, y device, ndof
+ * floats each.  Halves the vector traffic of mfa_apply and needs no
+ * conversions; otherwise identical. */
+MFA_API int mfa_apply_f32(mfa_ctx *ctx, mfa_form *form, const float *x, float *y, int accumulate);
+/* Element-wise conversion of device vectors between FP64 and FP32, computed
+ * on the integer pipe from the IEEE-754 bit fields: round to nearest, ties to
+ * even; results below the smallest normal float become signed zero, above
+ * the largest float infinity.  Asynchronous on the context stream. */
+MFA_API int mfa_convert_f64_to_f32(mfa_ctx *ctx, const double *x, float *y, int64_t n);
+MFA_API int mfa_convert_f32_to_f64(mfa_ctx *ctx, const float *x, double *y, int64_t n);
 /* Same with host buffers: copies x to the device, applies, copies y back and
  * waits.  The device staging buffers are owned by the form. */
 MFA_API int mfa_apply_host(mfa_ctx *ctx, mfa_form *form, const double *x_host, double *y_host);

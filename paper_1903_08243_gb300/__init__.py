@@ -81,6 +81,9 @@ _SIGS = {
     "mfa_form_destroy": ([_VP], _I),
     "mfa_apply": ([_VP, _VP, _VP, _VP, _I], _I),
     "mfa_apply_host": ([_VP, _VP, _VP, _VP], _I),
+    "mfa_apply_f32": ([_VP, _VP, _VP, _VP, _I], _I),
+    "mfa_convert_f64_to_f32": ([_VP, _VP, _VP, _I64], _I),
+    "mfa_convert_f32_to_f64": ([_VP, _VP, _VP, _I64], _I),
     "mfa_sync": ([_VP], _I),
     "mfa_diagonal": ([_VP, _VP, _VP], _I),
     "mfa_cg": ([_VP, _VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
@@ -203,6 +206,18 @@ def mfa_form_destroy(form):
 
 def mfa_apply(ctx, form, x, y, accumulate=False):
     _check(lib().mfa_apply(ctx, form, _ptr(x), _ptr(y), int(accumulate)))
+
+
+def mfa_apply_f32(ctx, form, x, y, accumulate=False):
+    _check(lib().mfa_apply_f32(ctx, form, _ptr(x), _ptr(y), int(accumulate)))
+
+
+def mfa_convert_f64_to_f32(ctx, x, y):
+    _check(lib().mfa_convert_f64_to_f32(ctx, _ptr(x), _ptr(y), x.numel()))
+
+
+def mfa_convert_f32_to_f64(ctx, x, y):
+    _check(lib().mfa_convert_f32_to_f64(ctx, _ptr(x), _ptr(y), x.numel()))
 
 
 def mfa_apply_host(ctx, form, x_host, y_host):

@@ -359,8 +359,10 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
   if (prm->law != MFA_LAW_SVK && prm->law != MFA_LAW_NEOHOOKE) return fail(MFA_ERR_ARG, "mfa_form_create: law %d", prm->law);
   if (prm->precision < MFA_PREC_FP64 || prm->precision > MFA_PREC_BF16)
     return fail(MFA_ERR_ARG, "mfa_form_create: precision %d", prm->precision);
-  if (prm->precision != MFA_PREC_FP64 && (ct != MFA_CELL_HEX8 || (prm->qdeg > 0 && prm->qdeg != sp->degree + 1)))
-    return fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: FP32/BF16 cover hex forms with p+1 points per direction");
+  if (prm->precision != MFA_PREC_FP64 && (ct != MFA_CELL_HEX8 || (prm->qdeg > 0 && prm->qdeg != sp->degree + 1) ||
+                                          prm->scatter == MFA_SCATTER_COLOUR))
+    return fail(MFA_ERR_UNSUPPORTED,
+                "mfa_form_create: FP32/BF16 cover hex forms with p+1 points per direction and the atomic scatter");
   if (kind >= MFA_FORM_ELASTICITY && sp->ncomp != 3)
     return fail(MFA_ERR_ARG, "mfa_form_create: form %d needs a 3-component space", kind);
   if (ct == MFA_CELL_HEX8 && (sp->ncomp != 1 || kind > MFA_FORM_HELMHOLTZ))
@@ -453,6 +455,35 @@ int mfa_apply(mfa_ctx* ctx, mfa_form* f, const double* x, double* y, int accumul
   const int64_t ndof = f->space->nnode * f->space->ncomp;
   if (!accumulate) MFA_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * ndof, ctx->stream));
   return mfa::apply_form(f, x, y, ctx->stream);
+}
+
+int mfa_apply_f32(mfa_ctx* ctx, mfa_form* f, const float* x, float* y, int accumulate) {
+  if (!ctx || !f || !x || !y) return fail(MFA_ERR_ARG, "mfa_apply_f32: NULL argument");
+  if (f->ctx != ctx) return fail(MFA_ERR_ARG, "mfa_apply_f32: form belongs to another context");
+  if ((const void*)x == (const void*)y) return fail(MFA_ERR_ARG, "mfa_apply_f32: x and y alias");
+  if (f->p.precision == MFA_PREC_FP64) return fail(MFA_ERR_ARG, "mfa_apply_f32: needs an FP32 or BF16 form");
+  MFA_CUDA(cudaSetDevice(ctx->device));
+  mfa_space* sp = f->space;
+  const int64_t ndof = sp->nnode * sp->ncomp;
+  if (!accumulate) MFA_CUDA(cudaMemsetAsync(y, 0, sizeof(float) * ndof, ctx->stream));
+  cudaError_t e = mfa::hex_apply_launch_f32(sp->degree + 1, f->p.kind, f->p.precision, x, y, sp->d_cell_node,
+                                            f->d_geom, sp->mesh->ncell, ctx->sm_count, ctx->stream);
+  if (e != cudaSuccess) return fail(MFA_ERR_CUDA, "mfa_apply_f32: %s", cudaGetErrorString(e));
+  return MFA_OK;
+}
+
+int mfa_convert_f64_to_f32(mfa_ctx* ctx, const double* x, float* y, int64_t n) {
+  if (!ctx || (n > 0 && (!x || !y)) || n < 0) return fail(MFA_ERR_ARG, "mfa_convert_f64_to_f32: bad arguments");
+  MFA_CUDA(cudaSetDevice(ctx->device));
+  cudaError_t e = mfa::convert_d2f_launch(x, y, n, ctx->stream);
+  return e == cudaSuccess ? MFA_OK : fail(MFA_ERR_CUDA, "mfa_convert_f64_to_f32: %s", cudaGetErrorString(e));
+}
+
+int mfa_convert_f32_to_f64(mfa_ctx* ctx, const float* x, double* y, int64_t n) {
+  if (!ctx || (n > 0 && (!x || !y)) || n < 0) return fail(MFA_ERR_ARG, "mfa_convert_f32_to_f64: bad arguments");
+  MFA_CUDA(cudaSetDevice(ctx->device));
+  cudaError_t e = mfa::convert_f2d_launch(x, y, n, ctx->stream);
+  return e == cudaSuccess ? MFA_OK : fail(MFA_ERR_CUDA, "mfa_convert_f32_to_f64: %s", cudaGetErrorString(e));
 }
 
 int mfa_apply_host(mfa_ctx* ctx, mfa_form* f, const double* xh, double* yh) {

@@ -1,6 +1,7 @@
 // FP64 vector kernels for the CG solver: a deterministic two-pass dot product
 // (fixed grid, fixed reduction order, so repeated calls give identical bits),
 // axpby, pointwise product and reciprocal.  All are HBM-bound streams.
+#include "convert.cuh"
 #include "mfa_internal.h"
 
 namespace mfa {
@@ -80,6 +81,84 @@ __global__ void xpby_ratio_kernel(const double* __restrict__ z, double* __restri
     p[i] = fma(beta, p[i], z[i]);
 }
 
+__global__ void d2f_kernel(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = d2f_bits(x[i]);
+}
+
+__global__ void f2d_kernel(const float* __restrict__ x, double* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = f2d_bits(x[i]);
+}
+
+// ---- float-vector kernels of the inner (reduced-precision) Krylov loop.
+// Per-thread sums in float over a few dozen entries, then double across the
+// block and across blocks (dot_final_kernel): deterministic for a fixed grid.
+
+__device__ __forceinline__ void block_partial(double v, double* partial) {
+  __shared__ double ws[kDotThreads / 32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < kDotThreads / 32 ? ws[threadIdx.x] : 0.0;
+    w = warp_sum(w);
+    if (threadIdx.x == 0) partial[blockIdx.x] = w;
+  }
+}
+
+__global__ void __launch_bounds__(kDotThreads) dot32_kernel(const float* __restrict__ a, const float* __restrict__ b,
+                                                            int64_t n, double* __restrict__ partial) {
+  float s = 0.0f;
+  for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kDotThreads)
+    s = fmaf(a[i], b[i], s);
+  block_partial(f2d_bits(s), partial);
+}
+
+// z = d * r, p = z, partial sums of r . z
+__global__ void __launch_bounds__(kDotThreads) jacobi_init32_kernel(const float* __restrict__ d,
+                                                                    const float* __restrict__ r, float* __restrict__ z,
+                                                                    float* __restrict__ p, int64_t n,
+                                                                    double* __restrict__ partial) {
+  float s = 0.0f;
+  for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kDotThreads) {
+    const float zi = d[i] * r[i];
+    z[i] = zi;
+    p[i] = zi;
+    s = fmaf(r[i], zi, s);
+  }
+  block_partial(f2d_bits(s), partial);
+}
+
+// alpha = rz / pq; x += alpha p; r -= alpha q; z = d * r; partial sums of r . z
+__global__ void __launch_bounds__(kDotThreads) cg_update32_kernel(const float* __restrict__ p,
+                                                                  const float* __restrict__ q, float* __restrict__ r,
+                                                                  float* __restrict__ x, const float* __restrict__ d,
+                                                                  float* __restrict__ z, int64_t n,
+                                                                  const double* __restrict__ rz,
+                                                                  const double* __restrict__ pq,
+                                                                  double* __restrict__ partial) {
+  const float alpha = d2f_bits(*rz / *pq);
+  float s = 0.0f;
+  for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kDotThreads) {
+    x[i] = fmaf(alpha, p[i], x[i]);
+    const float ri = fmaf(-alpha, q[i], r[i]);
+    r[i] = ri;
+    const float zi = d[i] * ri;
+    z[i] = zi;
+    s = fmaf(ri, zi, s);
+  }
+  block_partial(f2d_bits(s), partial);
+}
+
+// p = z + (num / den) p
+__global__ void xpby32_kernel(const float* __restrict__ z, float* __restrict__ p, int64_t n,
+                              const double* __restrict__ num, const double* __restrict__ den) {
+  const float beta = d2f_bits(*num / *den);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fmaf(beta, p[i], z[i]);
+}
+
 unsigned grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
@@ -120,6 +199,45 @@ cudaError_t xpby_ratio_launch(const double* z, double* p, int64_t n, const doubl
                               cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   xpby_ratio_kernel<<<grid_for(n), 256, 0, s>>>(z, p, n, num, den);
+  return cudaGetLastError();
+}
+
+cudaError_t convert_d2f_launch(const double* x, float* y, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  d2f_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t convert_f2d_launch(const float* x, double* y, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  f2d_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t dot32_launch(const float* a, const float* b, int64_t n, double* partial, double* out, cudaStream_t s) {
+  dot32_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(a, b, n, partial);
+  dot_final_kernel<<<1, kDotThreads, 0, s>>>(partial, out);
+  return cudaGetLastError();
+}
+
+cudaError_t jacobi_init32_launch(const float* d, const float* r, float* z, float* p, int64_t n, double* partial,
+                                 double* out, cudaStream_t s) {
+  jacobi_init32_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(d, r, z, p, n, partial);
+  dot_final_kernel<<<1, kDotThreads, 0, s>>>(partial, out);
+  return cudaGetLastError();
+}
+
+cudaError_t cg_update32_launch(const float* p, const float* q, float* r, float* x, const float* d, float* z,
+                               int64_t n, const double* rz, const double* pq, double* partial, double* rz_new,
+                               cudaStream_t s) {
+  cg_update32_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(p, q, r, x, d, z, n, rz, pq, partial);
+  dot_final_kernel<<<1, kDotThreads, 0, s>>>(partial, rz_new);
+  return cudaGetLastError();
+}
+
+cudaError_t xpby32_launch(const float* z, float* p, int64_t n, const double* num, const double* den, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  xpby32_kernel<<<grid_for(n), 256, 0, s>>>(z, p, n, num, den);
   return cudaGetLastError();
 }
 

@@ -10,6 +10,11 @@ int hex_cells_per_block(int n, int nq) {
   return p <= 128 ? 256 / p : 1;  // hexk::Shape<N, NQ>::CB
 }
 
+int hex_line_cells_per_block(int n) {
+  const int l = n * n;
+  return 256 / l > 0 ? 256 / l : 1;  // hexl::LShape<N>::CB
+}
+
 int hex_geom_entries(int kind) {
   return kind == MFA_FORM_MASS ? 1 : (kind == MFA_FORM_LAPLACE ? 6 : 7);
 }

@@ -1,0 +1,243 @@
+// Sum-factorised hex action for FP32 arithmetic (FP32 and BF16 variants):
+// one thread per 1D line of a cell, tables in the constant bank.
+//
+// The FP64 kernel (hex_kernels.cuh) is bound by the FP64 pipe and can spend
+// two shared-memory loads per FMA.  In FP32 the same layout is bound by the
+// load/store pipe, so this kernel changes the work split: a thread owns one
+// line of n points in one direction, loads its n inputs once, and forms the
+// n outputs with n^2 FMAs whose table coefficients are compile-time offsets
+// into __constant__ memory (an FMA operand, no load instruction).  The same
+// algorithm as the FP64 kernel: B sweeps in x, y, z; collocation derivatives
+// D_x, D_y, D_z; pointwise G g (+ c0 w|J| u); transposed D and B sweeps;
+// atomic scatter.  Double vectors are converted on the integer pipe.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "convert.cuh"
+#include "mfa_internal.h"
+
+namespace mfa {
+namespace hexl {
+
+__host__ __device__ constexpr int tab_offset(int n) {  // B (n x n) then D (n x n) for n = 2, 3, ...
+  int off = 0;
+  for (int k = 2; k < n; ++k) off += 2 * k * k;
+  return off;
+}
+constexpr int kTabFloats = tab_offset(10);
+
+// One copy per translation unit; filled by upload_tables() of that unit.
+static __constant__ float c_tab[2][kTabFloats];  // [0]: FP32 tables, [1]: tables rounded to bfloat16
+
+constexpr int ceil32(int x) { return (x + 31) / 32 * 32; }
+
+template <int N>
+struct LShape {
+  static constexpr int L = N * N;         // lines per cell and direction
+  static constexpr int P = N * N * N;     // points per cell
+  static constexpr int CB = 256 / L > 0 ? 256 / L : 1;
+  static constexpr int T = ceil32(CB * L);
+  static constexpr int SMEM = 5 * CB * P * 4;
+};
+
+template <int KIND>
+__host__ __device__ constexpr int geom_entries() {
+  return KIND == MFA_FORM_MASS ? 1 : (KIND == MFA_FORM_LAPLACE ? 6 : 7);
+}
+
+// Index of point m on line (a, b) in direction DIR (0: x, 1: y, 2: z).
+template <int N, int DIR>
+__device__ __forceinline__ int at(int a, int b, int m) {
+  if constexpr (DIR == 0) return m + N * (a + N * b);
+  else if constexpr (DIR == 1) return a + N * (m + N * b);
+  else return a + N * (b + N * m);
+}
+
+// out[line] = T[.][.] applied along DIR: out_r = sum_m Tab[r][m] in_m (TRANS: Tab[m][r]).
+template <int N, int DIR, int TAB, bool TRANS, bool ACC, int variant>
+__device__ __forceinline__ void sweep(const float* in, float* out, int a, int b) {
+  constexpr int off = tab_offset(N) + (TAB == 0 ? 0 : N * N);
+  float v[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) v[m] = in[at<N, DIR>(a, b, m)];
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    float s = ACC ? out[at<N, DIR>(a, b, r)] : 0.0f;
+#pragma unroll
+    for (int m = 0; m < N; ++m) s = fmaf(c_tab[variant][off + (TRANS ? m * N + r : r * N + m)], v[m], s);
+    out[at<N, DIR>(a, b, r)] = s;
+  }
+}
+
+template <typename TX>
+__device__ __forceinline__ float load_x(const TX* x, int32_t node, bool bf16) {
+  float v;
+  if constexpr (sizeof(TX) == 8) v = d2f_bits(__ldg(x + node));
+  else v = __ldg(x + node);
+  if (bf16) v = __bfloat162float(__float2bfloat16_rn(v));
+  return v;
+}
+
+template <typename TY>
+__device__ __forceinline__ void add_y(TY* y, int32_t node, float v) {
+  if constexpr (sizeof(TY) == 8) atomicAdd(y + node, f2d_bits(v));
+  else atomicAdd(y + node, v);
+}
+
+struct LineArgs {
+  const void* x;  // double or float
+  void* y;
+  const int32_t* cell_node;
+  const void* geom;  // float or bfloat16
+  int64_t count;
+};
+
+template <int PREC>
+__device__ __forceinline__ float load_g(const void* geom, int64_t i) {
+  if constexpr (PREC == MFA_PREC_BF16) return __bfloat162float(static_cast<const __nv_bfloat16*>(geom)[i]);
+  else return __ldg(static_cast<const float*>(geom) + i);
+}
+
+// One batch of CB consecutive cells.  Contractions run line-parallel (a
+// thread owns one line per direction); the phases that touch global memory
+// (gather, geometric factors, scatter) run point-parallel over the whole
+// batch, so consecutive threads read consecutive map, factor and output
+// addresses.
+template <int N, int KIND, int PREC, typename TX>
+__device__ __forceinline__ void line_batch(const LineArgs& a, int64_t batch, float* smem) {
+  using S = LShape<N>;
+  constexpr int L = S::L, P = S::P, CB = S::CB, T = S::T, NG = geom_entries<KIND>();
+  constexpr int variant = PREC == MFA_PREC_BF16 ? 1 : 0;
+  const int t = threadIdx.x;
+  const int cl = t / L, l = t - cl * L;
+  const int la = l % N, lb = l / N;
+  const int64_t c0 = batch * CB;
+  const int ncb = (int)(a.count - c0 < CB ? a.count - c0 : CB);  // cells in this batch
+  const bool valid = cl < ncb;
+  float* U0 = smem;
+  float* U = U0 + cl * P;
+  float* V = U + CB * P;
+  float* F0 = V + CB * P;
+  float* F1 = F0 + CB * P;
+  float* F2 = F1 + CB * P;
+  const TX* x = static_cast<const TX*>(a.x);
+
+  // gather, point-parallel: point i of the batch is local point i % P of cell c0 + i / P
+  for (int i = t; i < ncb * P; i += T) U0[i] = load_x(x, __ldg(a.cell_node + c0 * P + i), variant == 1);
+  __syncthreads();
+  if (valid) sweep<N, 0, 0, false, false, variant>(U, V, la, lb);  // B in x
+  __syncthreads();
+  if (valid) sweep<N, 1, 0, false, false, variant>(V, U, la, lb);  // B in y
+  __syncthreads();
+  if (valid) sweep<N, 2, 0, false, false, variant>(U, V, la, lb);  // B in z: values at the Gauss points
+  __syncthreads();
+  float* V0 = U0 + CB * P;
+  if constexpr (KIND == MFA_FORM_MASS) {
+    for (int i = t; i < ncb * P; i += T) {
+      const int c = i / P, q = i - c * P;
+      U0[i] = load_g<PREC>(a.geom, (c0 + c) * P + q) * V0[i];
+    }
+  } else {
+    if (valid) {
+      sweep<N, 0, 1, false, false, variant>(V, F0, la, lb);  // D in x
+      sweep<N, 1, 1, false, false, variant>(V, F1, la, lb);  // D in y
+      sweep<N, 2, 1, false, false, variant>(V, F2, la, lb);  // D in z
+    }
+    __syncthreads();
+    float* G0 = V0 + CB * P;
+    float* G1 = G0 + CB * P;
+    float* G2 = G1 + CB * P;
+    for (int i = t; i < ncb * P; i += T) {
+      const int c = i / P, q = i - c * P;
+      const int64_t gb = (c0 + c) * (int64_t)NG * P + q;
+      float g[NG];
+#pragma unroll
+      for (int e = 0; e < NG; ++e) g[e] = load_g<PREC>(a.geom, gb + (int64_t)e * P);
+      const float d0 = G0[i], d1 = G1[i], d2 = G2[i];
+      G0[i] = fmaf(g[0], d0, fmaf(g[3], d1, g[4] * d2));
+      G1[i] = fmaf(g[3], d0, fmaf(g[1], d1, g[5] * d2));
+      G2[i] = fmaf(g[4], d0, fmaf(g[5], d1, g[2] * d2));
+      if constexpr (KIND == MFA_FORM_HELMHOLTZ) U0[i] = g[6] * V0[i];
+      else U0[i] = 0.0f;
+    }
+    __syncthreads();
+    if (valid) sweep<N, 0, 1, true, true, variant>(F0, U, la, lb);  // r = c0 w|J| u + D_x^T f0
+    __syncthreads();
+    if (valid) sweep<N, 1, 1, true, true, variant>(F1, U, la, lb);  // + D_y^T f1
+    __syncthreads();
+    if (valid) sweep<N, 2, 1, true, true, variant>(F2, U, la, lb);  // + D_z^T f2
+  }
+  __syncthreads();
+  if (valid) sweep<N, 2, 0, true, false, variant>(U, V, la, lb);  // B^T in z
+  __syncthreads();
+  if (valid) sweep<N, 1, 0, true, false, variant>(V, U, la, lb);  // B^T in y
+  __syncthreads();
+  if (valid) sweep<N, 0, 0, true, false, variant>(U, V, la, lb);  // B^T in x
+  __syncthreads();
+  // scatter-add, point-parallel
+  for (int i = t; i < ncb * P; i += T) {
+    const int32_t node = __ldg(a.cell_node + c0 * P + i);
+    if constexpr (sizeof(TX) == 8) add_y(static_cast<double*>(a.y), node, V0[i]);
+    else add_y(static_cast<float*>(a.y), node, V0[i]);
+  }
+  __syncthreads();
+}
+
+template <int N, int KIND, int PREC, typename TX>
+__global__ void __launch_bounds__(LShape<N>::T) line_apply_kernel(const LineArgs a) {
+  extern __shared__ __align__(16) float smem_l[];
+  const int64_t nbatch = (a.count + LShape<N>::CB - 1) / LShape<N>::CB;
+  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) line_batch<N, KIND, PREC, TX>(a, batch, smem_l);
+}
+
+template <int N, int KIND, int PREC>
+__global__ void __launch_bounds__(LShape<N>::T) line_group_kernel(const HexApplyArgs* __restrict__ items,
+                                                                  const int64_t* __restrict__ first, int nitems) {
+  extern __shared__ __align__(16) float smem_l[];
+  const int64_t total = first[nitems];
+  int k = 0;
+  for (int64_t gb = blockIdx.x; gb < total; gb += gridDim.x) {
+    while (k + 1 < nitems && gb >= first[k + 1]) ++k;
+    const HexApplyArgs h = items[k];
+    const LineArgs a{h.x, h.y, h.cell_node, h.geom, h.count};
+    line_batch<N, KIND, PREC, double>(a, gb - first[k], smem_l);
+  }
+}
+
+template <typename Kern>
+int occupancy(Kern kern, int threads, int smem) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int b = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem) != cudaSuccess || b < 1) b = 1;
+  return b;
+}
+
+template <int N, int KIND, int PREC, typename TX>
+cudaError_t launch_line(const LineArgs& a, int sm_count, cudaStream_t s) {
+  using S = LShape<N>;
+  auto kern = line_apply_kernel<N, KIND, PREC, TX>;
+  static int bps = -1;
+  if (bps < 0) bps = occupancy(kern, S::T, S::SMEM);
+  const int64_t nbatch = (a.count + S::CB - 1) / S::CB;
+  if (nbatch == 0) return cudaSuccess;
+  const int64_t cap = (int64_t)sm_count * bps;
+  kern<<<(unsigned)(nbatch < cap ? nbatch : cap), S::T, S::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N, int KIND, int PREC>
+cudaError_t launch_line_group(const HexApplyArgs* items, const int64_t* first, int nitems, int64_t total,
+                              int sm_count, cudaStream_t s) {
+  using S = LShape<N>;
+  auto kern = line_group_kernel<N, KIND, PREC>;
+  static int bps = -1;
+  if (bps < 0) bps = occupancy(kern, S::T, S::SMEM);
+  if (total == 0) return cudaSuccess;
+  const int64_t cap = (int64_t)sm_count * bps;
+  kern<<<(unsigned)(total < cap ? total : cap), S::T, S::SMEM, s>>>(items, first, nitems);
+  return cudaGetLastError();
+}
+
+}  // namespace hexl
+}  // namespace mfa

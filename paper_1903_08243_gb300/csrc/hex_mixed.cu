@@ -1,57 +1,37 @@
-// Instantiations of the sum-factorised hex action for the FP32 and BF16
-// variants (compiled separately from the FP64 ones to build in parallel).
-#include "hex_kernels.cuh"
+// Dispatch of the FP32 and BF16 hex action to the line-per-thread kernels
+// (hex_lines.cuh), split over two translation units by degree.
+#include "hex_lines.cuh"
 
 namespace mfa {
 
-cudaError_t hex_apply_launch_mixed(int n, int nq, int kind, int prec, bool colour, const HexTables& tb,
+cudaError_t hex_line_apply_a(int n, int kind, int prec, bool f32vec, const hexl::LineArgs& a, int sm_count,
+                             cudaStream_t s);
+cudaError_t hex_line_apply_b(int n, int kind, int prec, bool f32vec, const hexl::LineArgs& a, int sm_count,
+                             cudaStream_t s);
+cudaError_t hex_line_group_a(int n, int kind, int prec, const HexApplyArgs* items, const int64_t* first, int nitems,
+                             int64_t total, int sm_count, cudaStream_t s);
+cudaError_t hex_line_group_b(int n, int kind, int prec, const HexApplyArgs* items, const int64_t* first, int nitems,
+                             int64_t total, int sm_count, cudaStream_t s);
+
+cudaError_t hex_apply_launch_mixed(int n, int nq, int kind, int prec, bool colour, const HexTables&,
                                    const HexApplyArgs& a, int sm_count, cudaStream_t s) {
-  using namespace hexk;
-  if (prec == MFA_PREC_FP32) {
-    MFA_HEX_KIND_CASES(2, 2, MFA_PREC_FP32)
-    MFA_HEX_KIND_CASES(3, 3, MFA_PREC_FP32)
-    MFA_HEX_KIND_CASES(4, 4, MFA_PREC_FP32)
-    MFA_HEX_KIND_CASES(5, 5, MFA_PREC_FP32)
-    MFA_HEX_KIND_CASES(6, 6, MFA_PREC_FP32)
-    MFA_HEX_KIND_CASES(7, 7, MFA_PREC_FP32)
-    MFA_HEX_KIND_CASES(8, 8, MFA_PREC_FP32)
-    MFA_HEX_KIND_CASES(9, 9, MFA_PREC_FP32)
-  } else if (prec == MFA_PREC_BF16) {
-    MFA_HEX_KIND_CASES(2, 2, MFA_PREC_BF16)
-    MFA_HEX_KIND_CASES(3, 3, MFA_PREC_BF16)
-    MFA_HEX_KIND_CASES(4, 4, MFA_PREC_BF16)
-    MFA_HEX_KIND_CASES(5, 5, MFA_PREC_BF16)
-    MFA_HEX_KIND_CASES(6, 6, MFA_PREC_BF16)
-    MFA_HEX_KIND_CASES(7, 7, MFA_PREC_BF16)
-    MFA_HEX_KIND_CASES(8, 8, MFA_PREC_BF16)
-    MFA_HEX_KIND_CASES(9, 9, MFA_PREC_BF16)
-  }
-  return cudaErrorInvalidValue;
+  if (nq != n || colour || a.cell_list) return cudaErrorInvalidValue;
+  const hexl::LineArgs la{a.x, a.y, a.cell_node, a.geom, a.count};
+  return n <= 5 ? hex_line_apply_a(n, kind, prec, false, la, sm_count, s)
+                : hex_line_apply_b(n, kind, prec, false, la, sm_count, s);
 }
 
-cudaError_t hex_group_launch_mixed(int n, int kind, int prec, const HexTables& tb, const HexApplyArgs* items,
+cudaError_t hex_apply_launch_f32(int n, int kind, int prec, const float* x, float* y, const int32_t* cell_node,
+                                 const void* geom, int64_t count, int sm_count, cudaStream_t s) {
+  const hexl::LineArgs la{x, y, cell_node, geom, count};
+  return n <= 5 ? hex_line_apply_a(n, kind, prec, true, la, sm_count, s)
+                : hex_line_apply_b(n, kind, prec, true, la, sm_count, s);
+}
+
+cudaError_t hex_group_launch_mixed(int n, int kind, int prec, const HexTables&, const HexApplyArgs* items,
                                    const int64_t* first, int nitems, int64_t total, int sm_count, cudaStream_t s) {
-  using namespace hexk;
-  if (prec == MFA_PREC_FP32) {
-    MFA_HEX_GROUP_CASES(2, MFA_PREC_FP32)
-    MFA_HEX_GROUP_CASES(3, MFA_PREC_FP32)
-    MFA_HEX_GROUP_CASES(4, MFA_PREC_FP32)
-    MFA_HEX_GROUP_CASES(5, MFA_PREC_FP32)
-    MFA_HEX_GROUP_CASES(6, MFA_PREC_FP32)
-    MFA_HEX_GROUP_CASES(7, MFA_PREC_FP32)
-    MFA_HEX_GROUP_CASES(8, MFA_PREC_FP32)
-    MFA_HEX_GROUP_CASES(9, MFA_PREC_FP32)
-  } else if (prec == MFA_PREC_BF16) {
-    MFA_HEX_GROUP_CASES(2, MFA_PREC_BF16)
-    MFA_HEX_GROUP_CASES(3, MFA_PREC_BF16)
-    MFA_HEX_GROUP_CASES(4, MFA_PREC_BF16)
-    MFA_HEX_GROUP_CASES(5, MFA_PREC_BF16)
-    MFA_HEX_GROUP_CASES(6, MFA_PREC_BF16)
-    MFA_HEX_GROUP_CASES(7, MFA_PREC_BF16)
-    MFA_HEX_GROUP_CASES(8, MFA_PREC_BF16)
-    MFA_HEX_GROUP_CASES(9, MFA_PREC_BF16)
-  }
-  return cudaErrorInvalidValue;
+  return n <= 5 ? hex_line_group_a(n, kind, prec, items, first, nitems, total, sm_count, s)
+                : hex_line_group_b(n, kind, prec, items, first, nitems, total, sm_count, s);
 }
 
 }  // namespace mfa

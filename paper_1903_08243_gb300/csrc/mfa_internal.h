@@ -64,6 +64,10 @@ cudaError_t hex_group_launch(int n, int kind, int prec, const HexTables& tb, con
 cudaError_t hex_group_launch_mixed(int n, int kind, int prec, const HexTables& tb, const HexApplyArgs* items,
                                    const int64_t* first, int nitems, int64_t total, int sm_count, cudaStream_t s);
 int hex_cells_per_block(int n, int nq);
+int hex_line_cells_per_block(int n);
+// FP32/BF16 action with float vectors.
+cudaError_t hex_apply_launch_f32(int n, int kind, int prec, const float* x, float* y, const int32_t* cell_node,
+                                 const void* geom, int64_t count, int sm_count, cudaStream_t s);
 cudaError_t hex_geometry_launch(int nq, int kind, int prec, double c0, const HexTables& tb, const double* coords,
                                 const int32_t* cell_vert, int64_t ncell, void* geom, int* err, cudaStream_t s);
 cudaError_t hex_diagonal_launch(int n, int nq, int kind, const HexTables& tb, const int32_t* cell_node,
@@ -102,6 +106,15 @@ cudaError_t dot_launch(const double* a, const double* b, int64_t n, double* part
 cudaError_t axpby_launch(double alpha, const double* x, double beta, double* y, int64_t n, cudaStream_t s);
 cudaError_t pointwise_mul_launch(const double* a, const double* b, double* out, int64_t n, cudaStream_t s);
 cudaError_t reciprocal_launch(const double* a, double* out, int64_t n, cudaStream_t s);
+cudaError_t convert_d2f_launch(const double* x, float* y, int64_t n, cudaStream_t s);
+cudaError_t dot32_launch(const float* a, const float* b, int64_t n, double* partial, double* out, cudaStream_t s);
+cudaError_t jacobi_init32_launch(const float* d, const float* r, float* z, float* p, int64_t n, double* partial,
+                                 double* out, cudaStream_t s);
+cudaError_t cg_update32_launch(const float* p, const float* q, float* r, float* x, const float* d, float* z,
+                               int64_t n, const double* rz, const double* pq, double* partial, double* rz_new,
+                               cudaStream_t s);
+cudaError_t xpby32_launch(const float* z, float* p, int64_t n, const double* num, const double* den, cudaStream_t s);
+cudaError_t convert_f2d_launch(const float* x, double* y, int64_t n, cudaStream_t s);
 cudaError_t axpy_ratio_launch(const double* x, double* y, int64_t n, const double* num, const double* den, double sign,
                               cudaStream_t s);
 cudaError_t xpby_ratio_launch(const double* z, double* p, int64_t n, const double* num, const double* den,

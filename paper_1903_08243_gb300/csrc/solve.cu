@@ -7,23 +7,28 @@
 // costs about 1/18 of the FP64 one (HBM-bound against FP64-pipe-bound), so
 // most of the Krylov work moves to the cheap operator while the outer loop
 // keeps the FP64 accuracy.  The inner loop keeps its scalars on the device:
-// it never waits for the host.
+// it never waits for the host.  With an FP32/BF16 inner form the inner loop
+// runs on float vectors with fused update/Jacobi/dot kernels.
 #include <cmath>
+#include <utility>
+#include <vector>
 
 #include "mfa_internal.h"
 
 namespace {
 
 struct Vecs {
-  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *pp = nullptr, *qp = nullptr;
-  double *ri = nullptr, *zi = nullptr, *pi = nullptr, *qi = nullptr, *dinv = nullptr;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *pp = nullptr, *qp = nullptr, *dinv = nullptr;
+  double *ri = nullptr, *zi = nullptr, *pi = nullptr, *qi = nullptr;  // FP64 inner loop (FP64 inner form)
+  float *fr = nullptr, *fz = nullptr, *fp = nullptr, *fq = nullptr, *fx = nullptr, *fd = nullptr;  // float inner loop
   double* scal = nullptr;     // device scalars: [0] rz, [1] pq, [2] rz_new
   double* partial = nullptr;  // dot partials
 };
 
 void free_vecs(Vecs& v) {
-  double* all[] = {v.r, v.z, v.p, v.q, v.pp, v.qp, v.ri, v.zi, v.pi, v.qi, v.dinv, v.scal, v.partial};
-  for (double* a : all) cudaFree(a);
+  void* all[] = {v.r, v.z, v.p, v.q, v.pp, v.qp, v.dinv, v.ri, v.zi, v.pi, v.qi,
+                 v.fr, v.fz, v.fp, v.fq, v.fx, v.fd, v.scal, v.partial};
+  for (void* a : all) cudaFree(a);
 }
 
 }  // namespace
@@ -40,12 +45,22 @@ extern "C" int mfa_fcg_mixed(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, int
   const int64_t n = outer->space->nnode * outer->space->ncomp;
   cudaStream_t s = ctx->stream;
   Vecs v;
-  double** slots[] = {&v.r, &v.z, &v.p, &v.q, &v.pp, &v.qp, &v.ri, &v.zi, &v.pi, &v.qi, &v.dinv};
+  const bool f32 = inner->p.precision != MFA_PREC_FP64;  // inner loop on float vectors
+  std::vector<double**> slots = {&v.r, &v.z, &v.p, &v.q, &v.pp, &v.qp, &v.dinv};
+  if (!f32) slots.insert(slots.end(), {&v.ri, &v.zi, &v.pi, &v.qi});
   for (double** sl : slots)
     if (cudaMalloc((void**)sl, sizeof(double) * (n > 0 ? n : 1)) != cudaSuccess) {
       free_vecs(v);
       return mfa::set_error(MFA_ERR_OOM, "mfa_fcg_mixed: work vectors");
     }
+  if (f32) {
+    float** fslots[] = {&v.fr, &v.fz, &v.fp, &v.fq, &v.fx, &v.fd};
+    for (float** sl : fslots)
+      if (cudaMalloc((void**)sl, sizeof(float) * (n > 0 ? n : 1)) != cudaSuccess) {
+        free_vecs(v);
+        return mfa::set_error(MFA_ERR_OOM, "mfa_fcg_mixed: float work vectors");
+      }
+  }
   if (cudaMalloc((void**)&v.scal, sizeof(double) * 8) != cudaSuccess ||
       cudaMalloc((void**)&v.partial, sizeof(double) * mfa::dot_partials()) != cudaSuccess) {
     free_vecs(v);
@@ -60,8 +75,31 @@ extern "C" int mfa_fcg_mixed(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, int
     ck(cudaMemcpyAsync(out, v.scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
     ck(cudaStreamSynchronize(s));
   };
+  // float inner loop: r, p, q, z, x in float; fused update + Jacobi + dot kernels
+  auto precondition32 = [&](const double* r, double* z) {
+    double* rz = v.scal + 0;
+    double* pq = v.scal + 1;
+    double* rzn = v.scal + 2;
+    ck(mfa::convert_d2f_launch(r, v.fr, n, s));
+    ck(cudaMemsetAsync(v.fx, 0, sizeof(float) * n, s));
+    ck(mfa::jacobi_init32_launch(v.fd, v.fr, v.fz, v.fp, n, v.partial, rz, s));
+    for (int k = 0; k < inner_iters && !rc; ++k) {
+      const int e = mfa_apply_f32(ctx, inner, v.fp, v.fq, 0);
+      if (e && !rc) rc = e;
+      ck(mfa::dot32_launch(v.fp, v.fq, n, v.partial, pq, s));
+      ck(mfa::cg_update32_launch(v.fp, v.fq, v.fr, v.fx, v.fd, v.fz, n, rz, pq, v.partial, rzn, s));
+      if (k + 1 == inner_iters) break;
+      ck(mfa::xpby32_launch(v.fz, v.fp, n, rzn, rz, s));
+      std::swap(rz, rzn);
+    }
+    ck(mfa::convert_f2d_launch(v.fx, z, n, s));
+  };
   // z = M(r): inner_iters steps of Jacobi-PCG on the inner operator from z = 0
   auto precondition = [&](const double* r, double* z) {
+    if (f32 && inner_iters > 0) {
+      precondition32(r, z);
+      return;
+    }
     ck(cudaMemsetAsync(z, 0, sizeof(double) * n, s));
     if (inner_iters == 0) {
       ck(mfa::pointwise_mul_launch(v.dinv, r, z, n, s));
@@ -92,6 +130,7 @@ extern "C" int mfa_fcg_mixed(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, int
   double bnorm = 0.0, rr = 0.0, res = 0.0;
   rc = mfa_diagonal(ctx, outer, v.dinv);
   ck(rc ? cudaSuccess : mfa::reciprocal_launch(v.dinv, v.dinv, n, s));
+  if (f32) ck(rc ? cudaSuccess : mfa::convert_d2f_launch(v.dinv, v.fd, n, s));
   if (!rc) hdot(b, b, &bnorm);
   bnorm = std::sqrt(bnorm);
   if (!rc) rc = mfa_apply(ctx, outer, x, v.r, 0);

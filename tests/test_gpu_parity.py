@@ -89,6 +89,50 @@ def test_hex_mixed_precision_against_fp64_oracle(ctx, p, kind, prec):
         assert rel > 1e-12  # really computed in reduced precision
 
 
+@pytest.mark.parametrize("p", [1, 4, 8])
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_apply_f32_vectors(ctx, p, prec):
+    nx = {1: 7, 4: 3, 8: 2}[p]
+    case = hex_case(nx, p)
+    x = fi.uniform_vector(case["nnode"], seed=17)
+    ref = oracle_problem(case, "helmholtz").apply(x)
+    code, tol = PREC[prec]
+    form = gpu_form(ctx, case, "helmholtz", precision=code)
+    xf = torch.from_numpy(x).cuda().float()
+    yf = torch.empty_like(xf)
+    mfa.mfa_apply_f32(ctx.h, form.h, xf, yf)
+    ctx.sync()
+    y = yf.double().cpu().numpy()
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) <= tol
+    # same result as the double-vector entry point up to the float rounding of the output
+    yd = run(ctx, form, x)
+    assert np.linalg.norm(y - yd) / np.linalg.norm(yd) <= 1e-6
+
+
+def test_integer_pipe_conversions_match_cuda(ctx):
+    rng = np.random.default_rng(3)
+    mant = rng.standard_normal(200000)
+    expo = rng.integers(-120, 120, size=mant.size)
+    x = np.ldexp(mant, expo)
+    x[:8] = [0.0, -0.0, 1.0, -1.0, np.inf, -np.inf, 3.4028234663852886e38, 1.1754943508222875e-38]
+    # ties: exactly halfway between two floats, both parities
+    halfway = np.array([1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24, -(2.0 + 2.0 ** -23)])
+    x = np.concatenate([x, halfway])
+    xd = torch.from_numpy(x).cuda()
+    yf = torch.empty(x.size, dtype=torch.float32, device="cuda")
+    mfa.mfa_convert_f64_to_f32(ctx.h, xd, yf)
+    ctx.sync()
+    ref = xd.float()  # CUDA's own round-to-nearest conversion
+    normal = torch.isfinite(ref) & ((ref.abs() >= 1.1754943508222875e-38) | (ref == 0))
+    assert torch.equal(yf[normal].view(torch.int32), ref[normal].view(torch.int32))
+    assert torch.equal(torch.isinf(yf), torch.isinf(ref))
+    back = torch.empty_like(xd)
+    mfa.mfa_convert_f32_to_f64(ctx.h, yf, back)
+    ctx.sync()
+    fin = torch.isfinite(yf) & ((yf.abs() >= 1.1754943508222875e-38) | (yf == 0))
+    assert torch.equal(back[fin].view(torch.int64), yf[fin].double().view(torch.int64))
+
+
 def test_mixed_precision_rejected_where_not_built(ctx):
     case = tet_case(2, 1)
     with pytest.raises(mfa.MfaError) as e:
