@@ -1,0 +1,155 @@
+"""Cell-partitioned operator action across ranks: one halo exchange per apply.
+
+Global assembly (Section 2.2 of arXiv 1903.08243) sums cell contributions
+into shared dofs.  Partitioning the cells over R ranks leaves each node
+either interior to one rank or shared by several.  Every node is owned by
+the lowest rank that touches it; the other ranks that touch it hold it as a
+ghost.  One distributed apply is then
+
+  1. import: owners send the current x at every ghost node to the ranks that
+     hold the ghost (so each rank sees x on all nodes of its cells),
+  2. local apply on the rank's cells (the GPU kernels in production),
+  3. reverse add: each rank sends its partial sums at ghost nodes to the owner,
+     which adds them, so each owned entry of y is the full global sum.
+
+Scalars of Krylov methods are sums over owned entries, all-reduced.  The
+exchange uses torch.distributed point-to-point messages between neighbouring
+ranks (NCCL between GPUs, gloo on CPU).
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class HaloPlan:
+    rank: int
+    nranks: int
+    cells: np.ndarray            # global ids of this rank's cells
+    local_cell_node: np.ndarray  # [ncell_local][nloc] in local node ids
+    l2g: np.ndarray              # local node -> global node
+    owned: np.ndarray            # bool per local node
+    # per neighbour rank: local ids this rank sends / receives
+    send_import: dict = field(default_factory=dict)  # owned nodes whose x a neighbour needs
+    recv_import: dict = field(default_factory=dict)  # ghost nodes whose x comes from the owner
+    send_reverse: dict = field(default_factory=dict)  # ghost nodes whose partial y goes to the owner
+    recv_reverse: dict = field(default_factory=dict)  # owned nodes receiving partial y from a neighbour
+
+
+def contiguous_partition(ncell, nranks):
+    """Cell ranges [start, end) per rank (z-slabs on a lexicographic structured mesh)."""
+    bounds = np.linspace(0, ncell, nranks + 1).round().astype(np.int64)
+    return [(int(bounds[r]), int(bounds[r + 1])) for r in range(nranks)]
+
+
+def build_plan(cell_node, nnode, nranks, rank, parts=None):
+    """Halo plan of `rank`; every rank computes the same global ownership."""
+    ncell = cell_node.shape[0]
+    parts = parts or contiguous_partition(ncell, nranks)
+    touch_min = np.full(nnode, nranks, dtype=np.int64)  # owner = lowest rank touching the node
+    touched_by = [None] * nranks
+    for r, (s, e) in enumerate(parts):
+        nodes = np.unique(cell_node[s:e])
+        touched_by[r] = nodes
+        touch_min[nodes] = np.minimum(touch_min[nodes], r)
+    s, e = parts[rank]
+    cells = np.arange(s, e, dtype=np.int64)
+    l2g, local = np.unique(cell_node[s:e], return_inverse=True)
+    plan = HaloPlan(rank=rank, nranks=nranks, cells=cells,
+                    local_cell_node=local.reshape(e - s, -1).astype(np.int32), l2g=l2g,
+                    owned=touch_min[l2g] == rank)
+    g2l = {int(g): i for i, g in enumerate(l2g)}
+    for other in range(nranks):
+        if other == rank:
+            continue
+        shared = np.intersect1d(l2g, touched_by[other], assume_unique=True)
+        if shared.size == 0:
+            continue
+        mine = shared[touch_min[shared] == rank]       # I own, `other` holds as ghost
+        theirs = shared[touch_min[shared] == other]    # `other` owns, I hold as ghost
+        if mine.size:
+            ids = np.array([g2l[int(g)] for g in mine], dtype=np.int64)
+            plan.send_import[other] = ids
+            plan.recv_reverse[other] = ids
+        if theirs.size:
+            ids = np.array([g2l[int(g)] for g in theirs], dtype=np.int64)
+            plan.recv_import[other] = ids
+            plan.send_reverse[other] = ids
+    return plan
+
+
+def _exchange(send, recv, values, combine):
+    """Point-to-point exchange: send values[ids] to each peer, combine received data at ids."""
+    import torch
+    import torch.distributed as dist
+
+    reqs, bufs = [], {}
+    for peer, ids in recv.items():
+        buf = torch.empty((len(ids),) + tuple(values.shape[1:]), dtype=values.dtype, device=values.device)
+        bufs[peer] = buf
+        reqs.append(dist.irecv(buf, src=peer))
+    for peer, ids in send.items():
+        reqs.append(dist.isend(values[torch.as_tensor(ids, device=values.device)].contiguous(), dst=peer))
+    for r in reqs:
+        r.wait()
+    for peer, ids in recv.items():
+        idx = torch.as_tensor(ids, device=values.device)
+        combine(values, idx, bufs[peer])
+
+
+def import_ghosts(plan, x_local):
+    """x at ghost nodes <- owner's value."""
+    def put(v, idx, buf):
+        v[idx] = buf
+    _exchange(plan.send_import, plan.recv_import, x_local, put)
+
+
+def reverse_add(plan, y_local):
+    """Owner's y += each neighbour's partial sums at its ghost copies; ghosts then hold the full value."""
+    def add(v, idx, buf):
+        v.index_add_(0, idx, buf)
+    _exchange(plan.send_reverse, plan.recv_reverse, y_local, add)
+    import_ghosts(plan, y_local)  # make ghost copies consistent with the owner
+
+
+def distributed_apply(plan, local_apply, x_local):
+    """y_local = (A x)_local on every local node (owned and ghost), x_local holding owned values."""
+    import_ghosts(plan, x_local)
+    y = local_apply(x_local)
+    reverse_add(plan, y)
+    return y
+
+
+def owned_dot(plan, a, b):
+    import torch
+    import torch.distributed as dist
+
+    mask = torch.as_tensor(plan.owned, device=a.device)
+    s = (a[mask] * b[mask]).sum().reshape(1)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    return float(s.item())
+
+
+def distributed_cg(plan, local_apply, b_local, x_local, diag_local=None, rtol=1e-8, maxit=1000):
+    """Jacobi-preconditioned CG over the partitioned operator (reference logic for N > 1)."""
+    r = b_local - distributed_apply(plan, local_apply, x_local.clone())
+    dinv = None if diag_local is None else 1.0 / diag_local
+    z = r if dinv is None else dinv * r
+    p = z.clone()
+    rz = owned_dot(plan, r, z)
+    bnorm = owned_dot(plan, b_local, b_local) ** 0.5
+    it, res = 0, owned_dot(plan, r, r) ** 0.5 / bnorm
+    while res > rtol and it < maxit:
+        q = distributed_apply(plan, local_apply, p.clone())
+        alpha = rz / owned_dot(plan, p, q)
+        x_local += alpha * p
+        r -= alpha * q
+        it += 1
+        res = owned_dot(plan, r, r) ** 0.5 / bnorm
+        if res <= rtol:
+            break
+        z = r if dinv is None else dinv * r
+        rz_new = owned_dot(plan, r, z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x_local, it, res
