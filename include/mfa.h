@@ -197,6 +197,52 @@ MFA_API int mfa_cg(mfa_ctx *ctx, mfa_form *form, int precond, const double *b, d
 MFA_API int mfa_fcg_mixed(mfa_ctx *ctx, mfa_form *outer, mfa_form *inner, int inner_iters, const double *b,
                           double *x, double rtol, int maxit, int *outer_iters, int *inner_total, double *relres);
 
+/* Learned element-wise preconditioner (spec component; the paper has
+ * no solver).  For a residual r on a scalar Q1-Q4 hexahedral space,
+ *   M(r) = D^{-1} r + sum_K R_K^T ( w_K * s_K * f(R_K r / s_K) ),
+ *   f(z) = W2 relu(W1 z + b1),  s_K = ||R_K r||_2,
+ * R_K gathers the cell's dofs, w_K = 1 / (cells sharing each node), D is the
+ * diagonal of `form` (FP64).  W1 is 128 x nloc, b1 128, W2 nloc x 128; the
+ * forward pass uses BF16 copies of W1 and W2 on the tensor cores with FP32
+ * accumulation.  At creation W1 is seeded uniform in +-1/sqrt(nloc) from
+ * SplitMix64(seed), b1 = W2 = 0, so the untrained M is Jacobi.
+ * Vectors are device float arrays of ndof entries.
+ *  - mfa_precond_apply: z = M(r).
+ *  - mfa_precond_loss_grad: L = (M(r)-e)^T A (M(r)-e) / (e^T A e) with A the
+ *    FP32/BF16 form `aform` on the same space, and (if grad_host != NULL) dL
+ *    in the master layout of mfa_precond_get_weights, without updating.
+ *  - mfa_precond_train: `steps` Adam steps (lr; beta 0.9/0.999) cycling over
+ *    the (r, e) pairs; loss_first / loss_last receive the mean loss over the
+ *    pairs before and after.
+ *  - weights: FP32 master layout W1 [128][128] (columns >= nloc zero),
+ *    b1 [128], W2 [128][128] (rows >= nloc zero): 32896 floats.
+ *  - save/load: a 16-byte header ('MFAP', version 1, nloc, 128) and the weights. */
+typedef struct mfa_precond mfa_precond;
+#define MFA_PRECOND_NPARAMS 32896
+MFA_API int mfa_precond_create(mfa_ctx *ctx, mfa_form *form, uint64_t seed, mfa_precond **out);
+MFA_API int mfa_precond_apply(mfa_ctx *ctx, mfa_precond *pc, const float *r, float *z);
+MFA_API int mfa_precond_loss_grad(mfa_ctx *ctx, mfa_precond *pc, mfa_form *aform, const float *r, const float *e,
+                                  double *loss, float *grad_host);
+MFA_API int mfa_precond_train(mfa_ctx *ctx, mfa_precond *pc, mfa_form *aform, int npairs, const float *const *rs,
+                              const float *const *es, int steps, double lr, double *loss_first, double *loss_last);
+MFA_API int mfa_precond_get_weights(const mfa_precond *pc, float *host);
+MFA_API int mfa_precond_set_weights(mfa_precond *pc, const float *host);
+MFA_API int mfa_precond_save(const mfa_precond *pc, const char *path);
+MFA_API int mfa_precond_load(mfa_precond *pc, const char *path);
+MFA_API int mfa_precond_destroy(mfa_precond *pc);
+
+/* Mixed-precision flexible CG whose inner loop is flexible CG (one stored
+ * direction, float vectors, the FP32/BF16 form `inner`) preconditioned by the
+ * learned M of `pc`; otherwise as mfa_fcg_mixed.  With fallback = 1 the
+ * Jacobi inner loop of mfa_fcg_mixed takes over (a) for the rest of the solve
+ * once the learned one stops reducing the FP64 residual (by less than 20%
+ * over 3 outer steps): *used_fallback = 1; (b) from the initial guess if the
+ * solve breaks down or reaches maxit: *used_fallback = 2.  With fallback = 0
+ * the learned solver's own status is returned and *used_fallback = 0. */
+MFA_API int mfa_fcg_learned(mfa_ctx *ctx, mfa_form *outer, mfa_form *inner, mfa_precond *pc, int inner_iters,
+                            const double *b, double *x, double rtol, int maxit, int fallback, int *outer_iters,
+                            int *inner_total, double *relres, int *used_fallback);
+
 /* Many operators in one call (spec batching; the paper applies one
  * operator per parloop).  y_k = A_k(x_k) for k < n; each y_k is overwritten.
  * Hexahedral forms with the atomic scatter and p+1 points are grouped by

@@ -1,0 +1,60 @@
+"""FP64 oracle of the learned element-wise preconditioner (test infrastructure only).
+
+Not a paper operator: the spec preconditioner for CG over the
+matrix-free operator, restated here in plain numpy:
+
+    M(r) = D^{-1} r + sum_K R_K^T ( w_K * s_K * f(R_K r / s_K) ),
+    f(z) = W2 relu(W1 z + b1),   s_K = ||R_K r||_2   (contribution 0 if s_K = 0),
+
+R_K gathers the cell's local dofs, w_K holds 1 / (number of cells sharing
+each node) at the cell's nodes, D is the operator diagonal.  Training
+minimises L = (M(r) - e)^T A (M(r) - e) / (e^T A e) over (residual, error)
+pairs; `loss_and_grad` returns L and its exact gradient by backpropagation
+through the MLP, the scaling, and the assembly.
+"""
+import numpy as np
+
+
+def multiplicity_weights(cell_node, nnode):
+    mult = np.bincount(cell_node.ravel(), minlength=nnode).astype(np.float64)
+    return 1.0 / np.maximum(mult, 1.0)
+
+
+def apply(r, cell_node, winv, dinv, W1, b1, W2):
+    """M(r) in FP64.  W1 [H][nloc], b1 [H], W2 [nloc][H]."""
+    out = dinv * r
+    R = r[cell_node]                      # [ncell][nloc]
+    s = np.linalg.norm(R, axis=1)         # [ncell]
+    safe = np.where(s > 0, s, 1.0)
+    Z = R / safe[:, None]
+    Hpre = Z @ W1.T + b1
+    H = np.maximum(Hpre, 0.0)
+    O = H @ W2.T                          # [ncell][nloc]
+    contrib = winv[cell_node] * (s[:, None] * O) * (s[:, None] > 0)
+    np.add.at(out, cell_node, contrib)
+    return out
+
+
+def loss_and_grad(r, e, A_apply, cell_node, winv, dinv, W1, b1, W2):
+    """Loss L and (dL/dW1, dL/db1, dL/dW2) for one pair; A_apply(v) = A v."""
+    R = r[cell_node]
+    s = np.linalg.norm(R, axis=1)
+    safe = np.where(s > 0, s, 1.0)
+    Z = R / safe[:, None]
+    Hpre = Z @ W1.T + b1
+    H = np.maximum(Hpre, 0.0)
+    O = H @ W2.T
+    alive = (s > 0)[:, None]
+    M = dinv * r
+    np.add.at(M, cell_node, winv[cell_node] * (s[:, None] * O) * alive)
+    u = M - e
+    Au = A_apply(u)
+    den = e @ A_apply(e)
+    L = (u @ Au) / den
+    g = 2.0 * Au / den                    # dL/du (A symmetric)
+    Delta = winv[cell_node] * g[cell_node] * s[:, None] * alive  # dL/dO
+    dW2 = Delta.T @ H
+    dH = (Delta @ W2) * (Hpre > 0)
+    dW1 = dH.T @ Z
+    db1 = dH.sum(axis=0)
+    return L, dW1, db1, dW2

@@ -89,6 +89,17 @@ _SIGS = {
     "mfa_cg": ([_VP, _VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
     "mfa_fcg_mixed": ([_VP, _VP, _VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
                        ctypes.POINTER(_D)], _I),
+    "mfa_fcg_learned": ([_VP, _VP, _VP, _VP, _I, _VP, _VP, _D, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                         ctypes.POINTER(_D), ctypes.POINTER(_I)], _I),
+    "mfa_precond_create": ([_VP, _VP, ctypes.c_uint64, _PP], _I),
+    "mfa_precond_apply": ([_VP, _VP, _VP, _VP], _I),
+    "mfa_precond_loss_grad": ([_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_D), _VP], _I),
+    "mfa_precond_train": ([_VP, _VP, _VP, _I, _VP, _VP, _I, _D, ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
+    "mfa_precond_get_weights": ([_VP, _VP], _I),
+    "mfa_precond_set_weights": ([_VP, _VP], _I),
+    "mfa_precond_save": ([_VP, ctypes.c_char_p], _I),
+    "mfa_precond_load": ([_VP, ctypes.c_char_p], _I),
+    "mfa_precond_destroy": ([_VP], _I),
     "mfa_apply_batched": ([_VP, _I, _VP, _VP, _VP], _I),
     "mfa_batch_create": ([_VP, _I, _VP, _VP, _VP, _PP], _I),
     "mfa_batch_apply": ([_VP, _VP], _I),
@@ -97,6 +108,7 @@ _SIGS = {
     "mfa_cg_noalloc": ([_VP, _VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
 }
 MFA_CG_NOALLOC_MAX_NDOF = 262144
+MFA_PRECOND_NPARAMS = 32896
 
 
 def lib():
@@ -249,6 +261,81 @@ def mfa_fcg_mixed(ctx, outer, inner, inner_iters, b, x, rtol, maxit):
     if rc not in (MFA_OK, MFA_ERR_NOT_CONVERGED):
         _check(rc)
     return rc, it.value, inn.value, rel.value
+
+
+def mfa_fcg_learned(ctx, outer, inner, pc, inner_iters, b, x, rtol, maxit, fallback=True, raise_on_breakdown=True):
+    """Returns (status, outer iterations, inner iterations, relative residual, used_fallback)."""
+    it, inn, rel, fb = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+    rc = lib().mfa_fcg_learned(ctx, outer, inner, pc, inner_iters, _ptr(b), _ptr(x), rtol, maxit, int(fallback),
+                               ctypes.byref(it), ctypes.byref(inn), ctypes.byref(rel), ctypes.byref(fb))
+    ok = (MFA_OK, MFA_ERR_NOT_CONVERGED) if raise_on_breakdown else (MFA_OK, MFA_ERR_NOT_CONVERGED, MFA_ERR_BREAKDOWN)
+    if rc not in ok:
+        _check(rc)
+    return rc, it.value, inn.value, rel.value, fb.value
+
+
+def mfa_precond_create(ctx, form, seed=0):
+    h = ctypes.c_void_p()
+    _check(lib().mfa_precond_create(ctx, form, seed, ctypes.byref(h)))
+    return h
+
+
+def mfa_precond_apply(ctx, pc, r, z):
+    _check(lib().mfa_precond_apply(ctx, pc, _ptr(r), _ptr(z)))
+
+
+def mfa_precond_loss_grad(ctx, pc, aform, r, e, want_grad=True):
+    loss = ctypes.c_double()
+    g = np.zeros(MFA_PRECOND_NPARAMS, dtype=np.float32) if want_grad else None
+    _check(lib().mfa_precond_loss_grad(ctx, pc, aform, _ptr(r), _ptr(e), ctypes.byref(loss), _ptr(g)))
+    return loss.value, g
+
+
+def mfa_precond_train(ctx, pc, aform, rs, es, steps, lr):
+    first, last = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mfa_precond_train(ctx, pc, aform, len(rs), _ptr_array(rs), _ptr_array(es), steps, lr,
+                                   ctypes.byref(first), ctypes.byref(last)))
+    return first.value, last.value
+
+
+def mfa_precond_get_weights(pc):
+    w = np.zeros(MFA_PRECOND_NPARAMS, dtype=np.float32)
+    _check(lib().mfa_precond_get_weights(pc, _ptr(w)))
+    return w
+
+
+def mfa_precond_set_weights(pc, w):
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    _check(lib().mfa_precond_set_weights(pc, _ptr(w)))
+
+
+def mfa_precond_save(pc, path):
+    _check(lib().mfa_precond_save(pc, str(path).encode()))
+
+
+def mfa_precond_load(pc, path):
+    _check(lib().mfa_precond_load(pc, str(path).encode()))
+
+
+def mfa_precond_destroy(pc):
+    _check(lib().mfa_precond_destroy(pc))
+
+
+def unpack_precond_weights(w, nloc):
+    """(W1 [128][nloc], b1 [128], W2 [nloc][128]) from the master layout."""
+    W1 = w[:128 * 128].reshape(128, 128)[:, :nloc]
+    b1 = w[128 * 128:128 * 128 + 128]
+    W2 = w[128 * 128 + 128:].reshape(128, 128)[:nloc, :]
+    return W1, b1, W2
+
+
+def pack_precond_weights(W1, b1, W2):
+    w = np.zeros(MFA_PRECOND_NPARAMS, dtype=np.float32)
+    nloc = W1.shape[1]
+    w[:128 * 128].reshape(128, 128)[:, :nloc] = W1
+    w[128 * 128:128 * 128 + 128] = b1
+    w[128 * 128 + 128:].reshape(128, 128)[:nloc, :] = W2
+    return w
 
 
 def _ptr_array(items, ctype=ctypes.c_void_p):

@@ -159,6 +159,22 @@ __global__ void xpby32_kernel(const float* __restrict__ z, float* __restrict__ p
     p[i] = fmaf(beta, p[i], z[i]);
 }
 
+// y += sign * (num / den) * x  (float vectors, device scalars)
+__global__ void axpy32_ratio_kernel(const float* __restrict__ x, float* __restrict__ y, int64_t n,
+                                    const double* __restrict__ num, const double* __restrict__ den, float sign) {
+  const float a = sign * d2f_bits(*num / *den);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fmaf(a, x[i], y[i]);
+}
+
+// p = z + sign * (num / den) * p
+__global__ void xpay32_ratio_kernel(const float* __restrict__ z, float* __restrict__ p, int64_t n,
+                                    const double* __restrict__ num, const double* __restrict__ den, float sign) {
+  const float beta = sign * d2f_bits(*num / *den);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fmaf(beta, p[i], z[i]);
+}
+
 unsigned grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
@@ -238,6 +254,20 @@ cudaError_t cg_update32_launch(const float* p, const float* q, float* r, float* 
 cudaError_t xpby32_launch(const float* z, float* p, int64_t n, const double* num, const double* den, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   xpby32_kernel<<<grid_for(n), 256, 0, s>>>(z, p, n, num, den);
+  return cudaGetLastError();
+}
+
+cudaError_t axpy32_ratio_launch(const float* x, float* y, int64_t n, const double* num, const double* den, float sign,
+                                cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  axpy32_ratio_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n, num, den, sign);
+  return cudaGetLastError();
+}
+
+cudaError_t xpay32_ratio_launch(const float* z, float* p, int64_t n, const double* num, const double* den, float sign,
+                                cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  xpay32_ratio_kernel<<<grid_for(n), 256, 0, s>>>(z, p, n, num, den, sign);
   return cudaGetLastError();
 }
 

@@ -123,6 +123,12 @@ int dot_partials();
 
 // Record `msg` as the calling thread's mfa_last_error() and return `code`.
 int set_error(int code, const char* msg);
+// z = M(r) of a learned preconditioner, float vectors, on stream s.
+int precond_apply_f32(mfa_precond* pc, const float* r, float* z, cudaStream_t s);
+cudaError_t axpy32_ratio_launch(const float* x, float* y, int64_t n, const double* num, const double* den, float sign,
+                                cudaStream_t s);
+cudaError_t xpay32_ratio_launch(const float* z, float* p, int64_t n, const double* num, const double* den, float sign,
+                                cudaStream_t s);
 // Enqueue one form's action on `s` (y must already hold zeros or the sum to add to).
 int apply_form(mfa_form* f, const double* x, double* y, cudaStream_t s);
 

@@ -33,15 +33,24 @@ void free_vecs(Vecs& v) {
 
 }  // namespace
 
-extern "C" int mfa_fcg_mixed(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, int inner_iters, const double* b,
-                             double* x, double rtol, int maxit, int* outer_iters, int* inner_total, double* relres) {
-  if (!ctx || !outer || !inner || !b || !x) return mfa::set_error(MFA_ERR_ARG, "mfa_fcg_mixed: NULL argument");
+namespace {
+
+// Flexible CG with one stored direction (Notay 2000) on the FP64 form
+// `outer`; `inner_iters` steps of an inner Krylov loop on `inner` supply the
+// preconditioned residual: Jacobi-PCG (pc == nullptr) or flexible CG with the
+// learned preconditioner.
+int fcg(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, mfa_precond* pc, int inner_iters, const double* b, double* x,
+        double rtol, int maxit, int* outer_iters, int* inner_total, double* relres, bool allow_switch = false,
+        int* switched_at = nullptr) {
+  if (!ctx || !outer || !inner || !b || !x) return mfa::set_error(MFA_ERR_ARG, "mfa_fcg: NULL argument");
   if (outer->p.precision != MFA_PREC_FP64 || outer->p.kind > MFA_FORM_HELMHOLTZ)
-    return mfa::set_error(MFA_ERR_ARG, "mfa_fcg_mixed: the outer form must be an FP64 mass/Laplace/Helmholtz form");
+    return mfa::set_error(MFA_ERR_ARG, "mfa_fcg: the outer form must be an FP64 mass/Laplace/Helmholtz form");
   if (inner->space != outer->space || inner->p.kind != outer->p.kind)
-    return mfa::set_error(MFA_ERR_ARG, "mfa_fcg_mixed: the inner form must be the same operator on the same space");
-  if (inner_iters < 0 || maxit < 0 || !(rtol > 0.0)) return mfa::set_error(MFA_ERR_ARG, "mfa_fcg_mixed: bad counts");
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return mfa::set_error(MFA_ERR_CUDA, "mfa_fcg_mixed: cudaSetDevice");
+    return mfa::set_error(MFA_ERR_ARG, "mfa_fcg: the inner form must be the same operator on the same space");
+  if (pc && inner->p.precision == MFA_PREC_FP64)
+    return mfa::set_error(MFA_ERR_ARG, "mfa_fcg_learned: the inner form must be FP32 or BF16");
+  if (inner_iters < 0 || maxit < 0 || !(rtol > 0.0)) return mfa::set_error(MFA_ERR_ARG, "mfa_fcg: bad counts");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return mfa::set_error(MFA_ERR_CUDA, "mfa_fcg: cudaSetDevice");
   const int64_t n = outer->space->nnode * outer->space->ncomp;
   cudaStream_t s = ctx->stream;
   Vecs v;
@@ -51,20 +60,20 @@ extern "C" int mfa_fcg_mixed(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, int
   for (double** sl : slots)
     if (cudaMalloc((void**)sl, sizeof(double) * (n > 0 ? n : 1)) != cudaSuccess) {
       free_vecs(v);
-      return mfa::set_error(MFA_ERR_OOM, "mfa_fcg_mixed: work vectors");
+      return mfa::set_error(MFA_ERR_OOM, "mfa_fcg: work vectors");
     }
   if (f32) {
     float** fslots[] = {&v.fr, &v.fz, &v.fp, &v.fq, &v.fx, &v.fd};
     for (float** sl : fslots)
       if (cudaMalloc((void**)sl, sizeof(float) * (n > 0 ? n : 1)) != cudaSuccess) {
         free_vecs(v);
-        return mfa::set_error(MFA_ERR_OOM, "mfa_fcg_mixed: float work vectors");
+        return mfa::set_error(MFA_ERR_OOM, "mfa_fcg: float work vectors");
       }
   }
   if (cudaMalloc((void**)&v.scal, sizeof(double) * 8) != cudaSuccess ||
       cudaMalloc((void**)&v.partial, sizeof(double) * mfa::dot_partials()) != cudaSuccess) {
     free_vecs(v);
-    return mfa::set_error(MFA_ERR_OOM, "mfa_fcg_mixed: scalars");
+    return mfa::set_error(MFA_ERR_OOM, "mfa_fcg: scalars");
   }
   int rc = MFA_OK;
   auto ck = [&](cudaError_t e) {
@@ -75,7 +84,7 @@ extern "C" int mfa_fcg_mixed(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, int
     ck(cudaMemcpyAsync(out, v.scal + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
     ck(cudaStreamSynchronize(s));
   };
-  // float inner loop: r, p, q, z, x in float; fused update + Jacobi + dot kernels
+  // float inner loop with Jacobi: fused update + Jacobi + dot kernels
   auto precondition32 = [&](const double* r, double* z) {
     double* rz = v.scal + 0;
     double* pq = v.scal + 1;
@@ -94,8 +103,36 @@ extern "C" int mfa_fcg_mixed(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, int
     }
     ck(mfa::convert_f2d_launch(v.fx, z, n, s));
   };
-  // z = M(r): inner_iters steps of Jacobi-PCG on the inner operator from z = 0
+  // float inner loop with the learned preconditioner: flexible CG, one stored direction
+  auto precondition_learned = [&](const double* r, double* z) {
+    double* pq = v.scal + 0;
+    double* pr = v.scal + 1;
+    double* zq = v.scal + 2;
+    ck(mfa::convert_d2f_launch(r, v.fr, n, s));
+    ck(cudaMemsetAsync(v.fx, 0, sizeof(float) * n, s));
+    if (!rc) rc = mfa::precond_apply_f32(pc, v.fr, v.fz, s);
+    ck(cudaMemcpyAsync(v.fp, v.fz, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+    for (int k = 0; k < inner_iters && !rc; ++k) {
+      const int e = mfa_apply_f32(ctx, inner, v.fp, v.fq, 0);
+      if (e && !rc) rc = e;
+      ck(mfa::dot32_launch(v.fp, v.fq, n, v.partial, pq, s));
+      ck(mfa::dot32_launch(v.fp, v.fr, n, v.partial, pr, s));
+      ck(mfa::axpy32_ratio_launch(v.fp, v.fx, n, pr, pq, 1.0f, s));   // x += (p.r / p.q) p
+      ck(mfa::axpy32_ratio_launch(v.fq, v.fr, n, pr, pq, -1.0f, s));  // r -= (p.r / p.q) q
+      if (k + 1 == inner_iters) break;
+      if (!rc) rc = mfa::precond_apply_f32(pc, v.fr, v.fz, s);
+      ck(mfa::dot32_launch(v.fz, v.fq, n, v.partial, zq, s));
+      ck(mfa::xpay32_ratio_launch(v.fz, v.fp, n, zq, pq, -1.0f, s));  // p = z - (z.q / p.q) p
+    }
+    ck(mfa::convert_f2d_launch(v.fx, z, n, s));
+  };
+  // z = M(r): inner_iters steps of the inner loop from z = 0
+  bool use_learned = pc != nullptr;
   auto precondition = [&](const double* r, double* z) {
+    if (use_learned && inner_iters > 0) {
+      precondition_learned(r, z);
+      return;
+    }
     if (f32 && inner_iters > 0) {
       precondition32(r, z);
       return;
@@ -138,8 +175,10 @@ extern "C" int mfa_fcg_mixed(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, int
   if (!rc) hdot(v.r, v.r, &rr);
   res = bnorm > 0.0 ? std::sqrt(rr) / bnorm : std::sqrt(rr);
   if (!rc && (!std::isfinite(bnorm) || !std::isfinite(rr)))
-    rc = mfa::set_error(MFA_ERR_BREAKDOWN, "mfa_fcg_mixed: non-finite right-hand side");
+    rc = mfa::set_error(MFA_ERR_BREAKDOWN, "mfa_fcg: non-finite right-hand side");
   double pq_prev = 0.0;
+  std::vector<double> hist{res};
+  if (switched_at) *switched_at = 0;
   while (!rc && res > rtol && it < maxit) {
     precondition(v.r, v.z);
     inner_count += inner_iters;
@@ -159,7 +198,7 @@ extern "C" int mfa_fcg_mixed(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, int
     if (!rc) hdot(v.p, v.r, &pr);
     if (rc) break;
     if (!(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(pr)) {
-      rc = mfa::set_error(MFA_ERR_BREAKDOWN, "mfa_fcg_mixed: breakdown (p.Ap <= 0 or non-finite)");
+      rc = mfa::set_error(MFA_ERR_BREAKDOWN, "mfa_fcg: breakdown (p.Ap <= 0 or non-finite)");
       break;
     }
     const double alpha = pr / pq;
@@ -168,17 +207,61 @@ extern "C" int mfa_fcg_mixed(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, int
     hdot(v.r, v.r, &rr);
     ++it;
     res = bnorm > 0.0 ? std::sqrt(rr) / bnorm : std::sqrt(rr);
-    if (!std::isfinite(res)) rc = mfa::set_error(MFA_ERR_BREAKDOWN, "mfa_fcg_mixed: non-finite residual");
+    if (!std::isfinite(res)) rc = mfa::set_error(MFA_ERR_BREAKDOWN, "mfa_fcg: non-finite residual");
     // keep this direction for the next orthogonalisation
     std::swap(v.pp, v.p);
     std::swap(v.qp, v.q);
     pq_prev = pq;
+    hist.push_back(res);
+    // Jacobi fallback inside the solve: a learned inner loop that stops
+    // reducing the FP64 residual (< 20% over 3 outer steps) is replaced by the
+    // Jacobi inner loop for the rest of the solve (flexible CG allows it).
+    if (allow_switch && use_learned && it >= 3 && res > 0.8 * hist[it - 3]) {
+      use_learned = false;
+      if (switched_at) *switched_at = it;
+    }
   }
   if (!rc) rc = mfa_sync(ctx);
-  if (!rc && res > rtol) rc = mfa::set_error(MFA_ERR_NOT_CONVERGED, "mfa_fcg_mixed: not converged");
+  if (!rc && res > rtol) rc = mfa::set_error(MFA_ERR_NOT_CONVERGED, "mfa_fcg: not converged");
   if (outer_iters) *outer_iters = it;
   if (inner_total) *inner_total = inner_count;
   if (relres) *relres = res;
   free_vecs(v);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int mfa_fcg_mixed(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, int inner_iters, const double* b,
+                             double* x, double rtol, int maxit, int* outer_iters, int* inner_total, double* relres) {
+  return fcg(ctx, outer, inner, nullptr, inner_iters, b, x, rtol, maxit, outer_iters, inner_total, relres);
+}
+
+extern "C" int mfa_fcg_learned(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, mfa_precond* pc, int inner_iters,
+                               const double* b, double* x, double rtol, int maxit, int fallback, int* outer_iters,
+                               int* inner_total, double* relres, int* used_fallback) {
+  if (!pc) return mfa::set_error(MFA_ERR_ARG, "mfa_fcg_learned: NULL preconditioner");
+  if (used_fallback) *used_fallback = 0;
+  if (!ctx || !outer || !b || !x) return mfa::set_error(MFA_ERR_ARG, "mfa_fcg_learned: NULL argument");
+  const int64_t n = outer->space->nnode * outer->space->ncomp;
+  double* x0 = nullptr;  // keep the initial guess for the fallback
+  if (cudaMalloc((void**)&x0, sizeof(double) * (n > 0 ? n : 1)) != cudaSuccess)
+    return mfa::set_error(MFA_ERR_OOM, "mfa_fcg_learned: initial guess copy");
+  if (cudaMemcpyAsync(x0, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) {
+    cudaFree(x0);
+    return mfa::set_error(MFA_ERR_CUDA, "mfa_fcg_learned: copy");
+  }
+  int switched = 0;
+  int rc = fcg(ctx, outer, inner, pc, inner_iters, b, x, rtol, maxit, outer_iters, inner_total, relres, fallback != 0,
+               &switched);
+  if (used_fallback) *used_fallback = switched > 0 ? 1 : 0;
+  if (fallback && (rc == MFA_ERR_BREAKDOWN || rc == MFA_ERR_NOT_CONVERGED)) {
+    // Jacobi restart from the same initial guess
+    if (cudaMemcpyAsync(x, x0, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream) == cudaSuccess) {
+      if (used_fallback) *used_fallback = 2;
+      rc = fcg(ctx, outer, inner, nullptr, inner_iters, b, x, rtol, maxit, outer_iters, inner_total, relres);
+    }
+  }
+  cudaFree(x0);
   return rc;
 }

@@ -1,0 +1,67 @@
+"""Pins of the preconditioner oracle: Jacobi reduction, homogeneity, and finite-difference gradients."""
+import numpy as np
+import pytest
+
+import fe_inputs as fi
+from oracle import precond as op
+from tests.problems import hex_case, oracle_problem
+
+
+@pytest.fixture(scope="module")
+def small():
+    case = hex_case(3, 2)
+    pb = oracle_problem(case, "helmholtz")
+    A = pb.dense()
+    n = case["nnode"]
+    nloc = case["cell_node"].shape[1]
+    rng = np.random.default_rng(0)
+    W1 = rng.uniform(-0.3, 0.3, (16, nloc))
+    b1 = rng.uniform(-0.1, 0.1, 16)
+    W2 = rng.uniform(-0.3, 0.3, (nloc, 16)) * 1e-2
+    winv = op.multiplicity_weights(case["cell_node"], n)
+    dinv = 1.0 / np.diag(A)
+    e = fi.uniform_vector(n, seed=5)
+    r = A @ e
+    return case, A, W1, b1, W2, winv, dinv, r, e
+
+
+def test_zero_network_is_jacobi(small):
+    case, A, W1, b1, W2, winv, dinv, r, e = small
+    z = op.apply(r, case["cell_node"], winv, dinv, W1, b1, 0 * W2)
+    np.testing.assert_allclose(z, dinv * r, rtol=0, atol=0)
+
+
+def test_positive_homogeneity(small):
+    case, A, W1, b1, W2, winv, dinv, r, e = small
+    z1 = op.apply(r, case["cell_node"], winv, dinv, W1, b1, W2)
+    z3 = op.apply(3.0 * r, case["cell_node"], winv, dinv, W1, b1, W2)
+    np.testing.assert_allclose(z3, 3.0 * z1, rtol=1e-13, atol=1e-15)
+
+
+def test_partition_of_unity_weights(small):
+    case = small[0]
+    winv = op.multiplicity_weights(case["cell_node"], case["nnode"])
+    acc = np.zeros(case["nnode"])
+    np.add.at(acc, case["cell_node"], winv[case["cell_node"]])
+    np.testing.assert_allclose(acc, 1.0, rtol=1e-15)
+
+
+def test_gradients_match_finite_differences(small):
+    case, A, W1, b1, W2, winv, dinv, r, e = small
+    cn = case["cell_node"]
+    L, dW1, db1, dW2 = op.loss_and_grad(r, e, lambda v: A @ v, cn, winv, dinv, W1, b1, W2)
+    rng = np.random.default_rng(1)
+    for name, P, G in [("W1", W1, dW1), ("b1", b1, db1), ("W2", W2, dW2)]:
+        D = rng.standard_normal(P.shape)
+        eps = 1e-6
+
+        def loss_at(Q):
+            args = {"W1": W1, "b1": b1, "W2": W2}
+            args[name] = Q
+            return op.loss_and_grad(r, e, lambda v: A @ v, cn, winv, dinv, args["W1"], args["b1"], args["W2"])[0]
+
+        fd = (loss_at(P + eps * D) - loss_at(P - eps * D)) / (2 * eps)
+        assert abs(fd - np.sum(G * D)) <= 1e-6 * max(1.0, abs(fd)), (name, fd, np.sum(G * D))
+    # the loss is the relative A-norm error of the preconditioned step
+    z = op.apply(r, cn, winv, dinv, W1, b1, W2)
+    assert abs(L - (z - e) @ A @ (z - e) / (e @ A @ e)) < 1e-13
