@@ -216,10 +216,17 @@ MFA_API int mfa_fcg_mixed(mfa_ctx *ctx, mfa_form *outer, mfa_form *inner, int in
  *    pairs before and after.
  *  - weights: FP32 master layout W1 [128][128] (columns >= nloc zero),
  *    b1 [128], W2 [128][128] (rows >= nloc zero): 32896 floats.
- *  - save/load: a 16-byte header ('MFAP', version 1, nloc, 128) and the weights. */
+ *  - save/load: a 16-byte header ('MFAP', 1 for MLP / 2 for linear, nloc, 128)
+ *    and the weights. */
 typedef struct mfa_precond mfa_precond;
 #define MFA_PRECOND_NPARAMS 32896
-MFA_API int mfa_precond_create(mfa_ctx *ctx, mfa_form *form, uint64_t seed, mfa_precond **out);
+/* MFA_PRECOND_MLP: the network above (nonlinear; used by flexible CG).
+ * MFA_PRECOND_LINEAR: no normalisation, bias or activation, W2 tied to W1^T:
+ *   M(r) = D^{-1} r + sum_K R_K^T w_K W1^T W1 (w_K R_K r),
+ * symmetric positive definite, so the inner loop is standard PCG; W1 starts
+ * at +-0.01/sqrt(nloc) (b1 and W2 stay zero). */
+enum { MFA_PRECOND_MLP = 0, MFA_PRECOND_LINEAR = 1 };
+MFA_API int mfa_precond_create(mfa_ctx *ctx, mfa_form *form, int mode, uint64_t seed, mfa_precond **out);
 MFA_API int mfa_precond_apply(mfa_ctx *ctx, mfa_precond *pc, const float *r, float *z);
 MFA_API int mfa_precond_loss_grad(mfa_ctx *ctx, mfa_precond *pc, mfa_form *aform, const float *r, const float *e,
                                   double *loss, float *grad_host);

@@ -58,3 +58,31 @@ def loss_and_grad(r, e, A_apply, cell_node, winv, dinv, W1, b1, W2):
     dW1 = dH.T @ Z
     db1 = dH.sum(axis=0)
     return L, dW1, db1, dW2
+
+
+# ---- linear (tied, symmetric) variant:
+#   M(r) = D^{-1} r + sum_K R_K^T w_K W1^T W1 (w_K R_K r)
+
+def apply_linear(r, cell_node, winv, dinv, W1):
+    out = dinv * r
+    Z = winv[cell_node] * r[cell_node]
+    O = (Z @ W1.T) @ W1
+    np.add.at(out, cell_node, winv[cell_node] * O)
+    return out
+
+
+def loss_and_grad_linear(r, e, A_apply, cell_node, winv, dinv, W1):
+    """L = (M r - e)^T A (M r - e) / (e^T A e) and dL/dW1 for the linear variant."""
+    Z = winv[cell_node] * r[cell_node]
+    H = Z @ W1.T
+    O = H @ W1
+    M = dinv * r
+    np.add.at(M, cell_node, winv[cell_node] * O)
+    u = M - e
+    Au = A_apply(u)
+    den = e @ A_apply(e)
+    L = (u @ Au) / den
+    g = 2.0 * Au / den
+    Delta = winv[cell_node] * g[cell_node]      # dL/dO
+    dW1 = H.T @ Delta + (Delta @ W1.T).T @ Z     # O = W1^T (W1 z)
+    return L, dW1

@@ -24,6 +24,7 @@ MFA_LAW_SVK, MFA_LAW_NEOHOOKE = 0, 1
 MFA_PREC_FP64, MFA_PREC_FP32, MFA_PREC_BF16 = 0, 1, 2
 MFA_SCATTER_AUTO, MFA_SCATTER_COLOUR, MFA_SCATTER_ATOMIC = 0, 1, 2
 MFA_PC_NONE, MFA_PC_JACOBI = 0, 1
+MFA_PRECOND_MLP, MFA_PRECOND_LINEAR = 0, 1
 
 
 class MfaError(RuntimeError):
@@ -91,7 +92,7 @@ _SIGS = {
                        ctypes.POINTER(_D)], _I),
     "mfa_fcg_learned": ([_VP, _VP, _VP, _VP, _I, _VP, _VP, _D, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
                          ctypes.POINTER(_D), ctypes.POINTER(_I)], _I),
-    "mfa_precond_create": ([_VP, _VP, ctypes.c_uint64, _PP], _I),
+    "mfa_precond_create": ([_VP, _VP, _I, ctypes.c_uint64, _PP], _I),
     "mfa_precond_apply": ([_VP, _VP, _VP, _VP], _I),
     "mfa_precond_loss_grad": ([_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_D), _VP], _I),
     "mfa_precond_train": ([_VP, _VP, _VP, _I, _VP, _VP, _I, _D, ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
@@ -274,9 +275,9 @@ def mfa_fcg_learned(ctx, outer, inner, pc, inner_iters, b, x, rtol, maxit, fallb
     return rc, it.value, inn.value, rel.value, fb.value
 
 
-def mfa_precond_create(ctx, form, seed=0):
+def mfa_precond_create(ctx, form, seed=0, mode=0):
     h = ctypes.c_void_p()
-    _check(lib().mfa_precond_create(ctx, form, seed, ctypes.byref(h)))
+    _check(lib().mfa_precond_create(ctx, form, mode, seed, ctypes.byref(h)))
     return h
 
 

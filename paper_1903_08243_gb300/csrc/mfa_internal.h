@@ -125,6 +125,7 @@ int dot_partials();
 int set_error(int code, const char* msg);
 // z = M(r) of a learned preconditioner, float vectors, on stream s.
 int precond_apply_f32(mfa_precond* pc, const float* r, float* z, cudaStream_t s);
+bool precond_is_linear(const mfa_precond* pc);
 cudaError_t axpy32_ratio_launch(const float* x, float* y, int64_t n, const double* num, const double* den, float sign,
                                 cudaStream_t s);
 cudaError_t xpay32_ratio_launch(const float* z, float* p, int64_t n, const double* num, const double* den, float sign,

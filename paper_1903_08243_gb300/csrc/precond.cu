@@ -8,7 +8,12 @@
 //
 // with R_K the gather of the cell's local dofs, w_K = 1 / (cells sharing the
 // node) and D the operator diagonal.  W2 starts at zero, so the untrained
-// preconditioner is Jacobi.  Training minimises
+// preconditioner is Jacobi.  The linear mode drops the normalisation, the
+// bias and the activation and ties W2 = W1^T:
+//
+//   M(r) = D^{-1} r + sum_K R_K^T w_K W1^T W1 (w_K R_K r),
+//
+// symmetric positive definite, so standard PCG applies.  Training minimises
 // L = (M(r) - e)^T A (M(r) - e) / (e^T A e) over (residual, error) pairs.
 //
 // The per-cell MLP is a pair of dense contractions over a tile of 128 cells:
@@ -145,6 +150,7 @@ struct MlpArgs {
   float* grad;             // master-layout gradient accumulator
   int64_t ncell;
   int nloc;
+  int linear;              // 1: the tied linear variant
 };
 
 __device__ __forceinline__ void load_weights(bf16* W1s, bf16* W2s, float* b1s, const MlpArgs& a) {
@@ -164,10 +170,19 @@ __device__ __forceinline__ void gather_inputs(const MlpArgs& a, int64_t c0, int 
   __syncthreads();
   for (int i = threadIdx.x; i < ncb * nloc; i += kThreads) {
     const int c = i / nloc, k = i - c * nloc;
-    F[c * kK + k] = __ldg(a.r + __ldg(a.cell_node + (c0 + c) * nloc + k));
+    const int32_t node = __ldg(a.cell_node + (c0 + c) * nloc + k);
+    F[c * kK + k] = a.linear ? __ldg(a.winv + node) * __ldg(a.r + node) : __ldg(a.r + node);
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (a.linear) {  // z = w R r, no normalisation
+    for (int c = warp * 16; c < warp * 16 + 16; ++c) {
+      if (lane == 0) scale[c] = 1.0f;
+      for (int k = lane; k < kK; k += 32) Zs[c * kLd + k] = __float2bfloat16_rn(F[c * kK + k]);
+    }
+    __syncthreads();
+    return;
+  }
   for (int c = warp * 16; c < warp * 16 + 16; ++c) {
     float ss = 0.0f;
     for (int k = lane; k < kK; k += 32) ss = fmaf(F[c * kK + k], F[c * kK + k], ss);
@@ -183,7 +198,7 @@ __device__ __forceinline__ void gather_inputs(const MlpArgs& a, int64_t c0, int 
 
 // Hidden layer of this warp's 16 cells: Hs = relu(Z W1^T + b1) in BF16.
 __device__ __forceinline__ void hidden_layer(const bf16* Zs, const bf16* W1s, const float* b1s, bf16* Hs, int r0,
-                                             int lane) {
+                                             int lane, bool linear) {
   float acc[16][4];
 #pragma unroll
   for (int t = 0; t < 16; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.0f;
@@ -192,10 +207,17 @@ __device__ __forceinline__ void hidden_layer(const bf16* Zs, const bf16* W1s, co
 #pragma unroll
   for (int t = 0; t < 16; ++t) {
     const int n = 8 * t + col;
-    Hs[row * kLd + n] = __float2bfloat16_rn(fmaxf(acc[t][0] + b1s[n], 0.0f));
-    Hs[row * kLd + n + 1] = __float2bfloat16_rn(fmaxf(acc[t][1] + b1s[n + 1], 0.0f));
-    Hs[(row + 8) * kLd + n] = __float2bfloat16_rn(fmaxf(acc[t][2] + b1s[n], 0.0f));
-    Hs[(row + 8) * kLd + n + 1] = __float2bfloat16_rn(fmaxf(acc[t][3] + b1s[n + 1], 0.0f));
+    if (linear) {
+      Hs[row * kLd + n] = __float2bfloat16_rn(acc[t][0]);
+      Hs[row * kLd + n + 1] = __float2bfloat16_rn(acc[t][1]);
+      Hs[(row + 8) * kLd + n] = __float2bfloat16_rn(acc[t][2]);
+      Hs[(row + 8) * kLd + n + 1] = __float2bfloat16_rn(acc[t][3]);
+    } else {
+      Hs[row * kLd + n] = __float2bfloat16_rn(fmaxf(acc[t][0] + b1s[n], 0.0f));
+      Hs[row * kLd + n + 1] = __float2bfloat16_rn(fmaxf(acc[t][1] + b1s[n + 1], 0.0f));
+      Hs[(row + 8) * kLd + n] = __float2bfloat16_rn(fmaxf(acc[t][2] + b1s[n], 0.0f));
+      Hs[(row + 8) * kLd + n + 1] = __float2bfloat16_rn(fmaxf(acc[t][3] + b1s[n + 1], 0.0f));
+    }
   }
   __syncwarp();
 }
@@ -216,11 +238,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_forward_kernel(const MlpArgs 
     const int64_t c0 = tile * kTile;
     const int ncb = (int)(a.ncell - c0 < kTile ? a.ncell - c0 : kTile);
     gather_inputs(a, c0, ncb, F, scale, Zs);
-    hidden_layer(Zs, W1s, b1s, Hs, r0, lane);
+    hidden_layer(Zs, W1s, b1s, Hs, r0, lane, a.linear);
     float acc[16][4];
 #pragma unroll
     for (int t = 0; t < 16; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.0f;
-    gemm_awt<16>(acc, Hs, r0, W2s, 0, lane);  // O = H W2^T
+    if (a.linear) gemm_ay<16>(acc, Hs, r0, W1s, 0, lane);  // O = H W1 (tied)
+    else gemm_awt<16>(acc, Hs, r0, W2s, 0, lane);          // O = H W2^T
     const int row = r0 + (lane >> 2), col = (lane & 3) * 2;
 #pragma unroll
     for (int t = 0; t < 16; ++t) {
@@ -265,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_backward_kernel(const MlpArgs
     const int64_t c0 = tile * kTile;
     const int ncb = (int)(a.ncell - c0 < kTile ? a.ncell - c0 : kTile);
     gather_inputs(a, c0, ncb, F, scale, Zs);
-    hidden_layer(Zs, W1s, b1s, Hs, r0, lane);
+    hidden_layer(Zs, W1s, b1s, Hs, r0, lane, a.linear);
     // Delta[c][o] = s_c w[node] dL/du[node]  (dL/dO), zero-padded
     for (int i = threadIdx.x; i < kTile * kLd; i += kThreads) Ds[i] = __float2bfloat16_rn(0.0f);
     __syncthreads();
@@ -275,6 +298,30 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_backward_kernel(const MlpArgs
       Ds[c * kLd + k] = __float2bfloat16_rn(scale[c] * __ldg(a.winv + node) * gs * __ldg(a.g + node));
     }
     __syncthreads();
+    if (a.linear) {
+      // O = W1^T W1 z: dW1 = H^T Delta + (Delta W1^T)^T Z, both reduced over the tile's cells
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        float acc[8][4];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.0f;
+        gemm_awt<8>(acc, Ds, r0, W1s, 64 * half, lane);  // P = Delta W1^T
+        const int row = r0 + (lane >> 2), col = (lane & 3) * 2;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int n = 64 * half + 8 * t + col;
+          dHs[row * kLd + n] = __float2bfloat16_rn(acc[t][0]);
+          dHs[row * kLd + n + 1] = __float2bfloat16_rn(acc[t][1]);
+          dHs[(row + 8) * kLd + n] = __float2bfloat16_rn(acc[t][2]);
+          dHs[(row + 8) * kLd + n + 1] = __float2bfloat16_rn(acc[t][3]);
+        }
+      }
+      __syncthreads();
+      gemm_xty(accW1, Hs, r0, Ds, lane);   // + sum_c h_c delta_c^T
+      gemm_xty(accW1, dHs, r0, Zs, lane);  // + sum_c p_c z_c^T
+      __syncthreads();
+      continue;
+    }
     // dH = (Delta W2) * relu'(.) for this warp's cells, in two halves of 64 columns
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
@@ -322,11 +369,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_backward_kernel(const MlpArgs
 // Adam on the FP32 master weights; refreshes the BF16 copies and clears the
 // gradient.  Entries outside the nloc x kH and kH x nloc blocks stay zero.
 __global__ void adam_kernel(float* w, float* grad, float* m, float* v, bf16* w1, bf16* w2, float* b1, int nloc,
-                            float lr, float beta1, float beta2, float eps, float c1, float c2) {
+                            int linear, float lr, float beta1, float beta2, float eps, float c1, float c2) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kParams; i += gridDim.x * blockDim.x) {
     bool live = true;
     if (i < kB1) live = (i % kK) < nloc;
-    else if (i >= kW2) live = ((i - kW2) / kH) < nloc;
+    else if (i >= kW2) live = !linear && ((i - kW2) / kH) < nloc;
+    else live = !linear;
     float wi = w[i];
     if (live) {
       const float g = grad[i];
@@ -407,6 +455,7 @@ struct mfa_precond {
   double* partial = nullptr;
   int64_t adam_t = 0;
   int fwd_blocks = 0, bwd_blocks = 0;
+  int linear = 0;
 };
 
 namespace {
@@ -425,6 +474,7 @@ MlpArgs mlp_args(mfa_precond* pc, const float* r, float* y, const float* g) {
   a.grad = pc->grad;
   a.ncell = pc->ncell;
   a.nloc = pc->nloc;
+  a.linear = pc->linear;
   return a;
 }
 
@@ -472,8 +522,10 @@ int loss_grad(mfa_precond* pc, mfa_form* aform, const float* r, const float* e, 
 
 extern "C" {
 
-int mfa_precond_create(mfa_ctx* ctx, mfa_form* form, uint64_t seed, mfa_precond** out) {
+int mfa_precond_create(mfa_ctx* ctx, mfa_form* form, int mode, uint64_t seed, mfa_precond** out) {
   if (!ctx || !form || !out) return mfa::set_error(MFA_ERR_ARG, "mfa_precond_create: NULL argument");
+  if (mode != MFA_PRECOND_MLP && mode != MFA_PRECOND_LINEAR)
+    return mfa::set_error(MFA_ERR_ARG, "mfa_precond_create: unknown mode");
   *out = nullptr;
   mfa_space* sp = form->space;
   if (sp->mesh->cell_type != MFA_CELL_HEX8 || sp->ncomp != 1 || form->p.precision != MFA_PREC_FP64 ||
@@ -484,6 +536,7 @@ int mfa_precond_create(mfa_ctx* ctx, mfa_form* form, uint64_t seed, mfa_precond*
   mfa_precond* pc = new mfa_precond();
   pc->ctx = ctx;
   pc->form = form;
+  pc->linear = mode == MFA_PRECOND_LINEAR;
   pc->nloc = sp->nloc;
   pc->ncell = sp->mesh->ncell;
   pc->ndof = sp->nnode;
@@ -516,9 +569,10 @@ int mfa_precond_create(mfa_ctx* ctx, mfa_form* form, uint64_t seed, mfa_precond*
     invert32_kernel<<<grid1(pc->ndof), 256, 0, s>>>(pc->winv, pc->ndof);
     rc = check(cudaGetLastError(), "weights");
   }
-  // W1 ~ U(-1/sqrt(nloc), 1/sqrt(nloc)) from SplitMix64, b1 = 0, W2 = 0: the untrained M is Jacobi
+  // W1 ~ U(-a, a) from SplitMix64 with a = 1/sqrt(nloc) (MLP mode, where b1 = W2 = 0 makes the
+  // untrained M Jacobi) or a = 0.01/sqrt(nloc) (linear mode: a small start next to Jacobi)
   std::vector<float> w(kParams, 0.0f);
-  const float bound = 1.0f / std::sqrt((float)pc->nloc);
+  const float bound = (pc->linear ? 0.01f : 1.0f) / std::sqrt((float)pc->nloc);
   for (int h = 0; h < kH; ++h)
     for (int k = 0; k < pc->nloc; ++k) {
       const uint64_t z = splitmix(seed * 0x100000001B3ull + (uint64_t)(h * kK + k));
@@ -603,8 +657,8 @@ int mfa_precond_train(mfa_ctx* ctx, mfa_precond* pc, mfa_form* aform, int npairs
     ++pc->adam_t;
     const float c1 = 1.0f / (1.0f - std::pow(beta1, (float)pc->adam_t));
     const float c2 = 1.0f / (1.0f - std::pow(beta2, (float)pc->adam_t));
-    adam_kernel<<<64, 256, 0, s>>>(pc->w, pc->grad, pc->m, pc->v, pc->w1, pc->w2, pc->b1, pc->nloc, (float)lr, beta1,
-                                   beta2, eps, c1, c2);
+    adam_kernel<<<64, 256, 0, s>>>(pc->w, pc->grad, pc->m, pc->v, pc->w1, pc->w2, pc->b1, pc->nloc, pc->linear,
+                                   (float)lr, beta1, beta2, eps, c1, c2);
     rc = check(cudaGetLastError(), "adam");
   }
   for (int j = 0; j < npairs && !rc; ++j) {
@@ -628,9 +682,10 @@ int mfa_precond_set_weights(mfa_precond* pc, const float* host) {
   if (!pc || !host) return mfa::set_error(MFA_ERR_ARG, "mfa_precond_set_weights: NULL argument");
   if (cudaSetDevice(pc->ctx->device) != cudaSuccess) return mfa::set_error(MFA_ERR_CUDA, "cudaSetDevice");
   std::vector<float> w(host, host + kParams);
-  for (int i = 0; i < kParams; ++i) {  // keep the padding zero
+  for (int i = 0; i < kParams; ++i) {  // keep the padding (and, in linear mode, b1 and W2) zero
     if (i < kB1 && (i % kK) >= pc->nloc) w[i] = 0.0f;
     if (i >= kW2 && ((i - kW2) / kH) >= pc->nloc) w[i] = 0.0f;
+    if (pc->linear && i >= kB1) w[i] = 0.0f;
   }
   int rc = check(cudaMemcpy(pc->w, w.data(), kParams * 4, cudaMemcpyHostToDevice), "mfa_precond_set_weights");
   if (!rc) {
@@ -647,7 +702,7 @@ int mfa_precond_save(const mfa_precond* pc, const char* path) {
   if (rc) return rc;
   FILE* f = fopen(path, "wb");
   if (!f) return mfa::set_error(MFA_ERR_ARG, "mfa_precond_save: cannot open the file");
-  const int32_t header[4] = {0x4D464150 /* 'MFAP' */, 1 /* version */, pc->nloc, kH};
+  const int32_t header[4] = {0x4D464150 /* 'MFAP' */, 1 + pc->linear /* version 1: MLP, 2: linear */, pc->nloc, kH};
   const bool ok = fwrite(header, sizeof(header), 1, f) == 1 && fwrite(w.data(), 4, kParams, f) == (size_t)kParams;
   fclose(f);
   return ok ? MFA_OK : mfa::set_error(MFA_ERR_ARG, "mfa_precond_save: write failed");
@@ -661,7 +716,7 @@ int mfa_precond_load(mfa_precond* pc, const char* path) {
   std::vector<float> w(kParams);
   const bool ok = fread(header, sizeof(header), 1, f) == 1 && fread(w.data(), 4, kParams, f) == (size_t)kParams;
   fclose(f);
-  if (!ok || header[0] != 0x4D464150 || header[1] != 1 || header[2] != pc->nloc || header[3] != kH)
+  if (!ok || header[0] != 0x4D464150 || header[1] != 1 + pc->linear || header[2] != pc->nloc || header[3] != kH)
     return mfa::set_error(MFA_ERR_ARG, "mfa_precond_load: not a weight file of this preconditioner shape");
   return mfa_precond_set_weights(pc, w.data());
 }
@@ -680,4 +735,5 @@ int mfa_precond_destroy(mfa_precond* pc) {
 
 namespace mfa {
 int precond_apply_f32(mfa_precond* pc, const float* r, float* z, cudaStream_t s) { return forward(pc, r, z, s); }
+bool precond_is_linear(const mfa_precond* pc) { return pc->linear != 0; }
 }  // namespace mfa

@@ -148,3 +148,66 @@ def test_training_reduces_the_loss_and_learned_fcg_converges(ctx, tmp_path):
         assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 2e-10 * np.linalg.norm(b)
     mfa.mfa_precond_destroy(pc)
     mfa.mfa_precond_destroy(pc2)
+
+
+
+# ------------------------------------------------------------------ linear (SPD) variant
+
+def test_linear_precond_forward_and_gradient_match_oracle(ctx):
+    nx, p = 3, 3
+    case = hex_case(nx, p)
+    A = oracle_problem(case, "helmholtz").dense()
+    m = mfa.Mesh(ctx, 8, case["coords"], case["cell_vert"])
+    sp = mfa.Space(m, p, 1, case["cell_node"], case["nnode"])
+    f64 = mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ)
+    f32 = mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ, precision=mfa.MFA_PREC_FP32)
+    pc = mfa.mfa_precond_create(ctx.h, f64.h, 3, mode=mfa.MFA_PRECOND_LINEAR)
+    nloc = (p + 1) ** 3
+    W1 = (0.3 * np.random.default_rng(4).standard_normal((128, nloc))).astype(np.float32)
+    mfa.mfa_precond_set_weights(pc, mfa.pack_precond_weights(W1, np.zeros(128), np.zeros((nloc, 128))))
+    winv = op.multiplicity_weights(case["cell_node"], case["nnode"])
+    dinv = 1.0 / np.diag(A)
+    r = fi.uniform_vector(case["nnode"], seed=8)
+    W1b = bf16_round(W1)
+    ref = op.apply_linear(r, case["cell_node"], winv, dinv, W1b)
+    z = torch.empty(case["nnode"], dtype=torch.float32, device="cuda")
+    mfa.mfa_precond_apply(ctx.h, pc, torch.from_numpy(r).float().cuda(), z)
+    ctx.sync()
+    zg = z.double().cpu().numpy()
+    assert np.linalg.norm(zg - ref) <= 2e-2 * np.linalg.norm(ref - dinv * r)
+    e = fi.uniform_vector(case["nnode"], seed=9)
+    rr = A @ e
+    L, dW1 = op.loss_and_grad_linear(rr, e, lambda v: A @ v, case["cell_node"], winv, dinv, W1b)
+    loss, g = mfa.mfa_precond_loss_grad(ctx.h, pc, f32.h, torch.from_numpy(rr).float().cuda(),
+                                        torch.from_numpy(e).float().cuda())
+    gW1, gb1, gW2 = mfa.unpack_precond_weights(g, nloc)
+    assert abs(loss - L) <= 2e-2 * L
+    cos = (dW1.ravel() @ gW1.ravel()) / (np.linalg.norm(dW1) * np.linalg.norm(gW1))
+    assert cos > 0.999 and np.linalg.norm(gW1 - dW1) <= 5e-2 * np.linalg.norm(dW1)
+    assert not gb1.any() and not gW2.any()
+    mfa.mfa_precond_destroy(pc)
+
+
+def test_linear_learned_pcg_beats_jacobi_inner_loop(ctx):
+    """What training buys: fewer outer iterations than the same solver with the Jacobi inner loop."""
+    nx, p = 4, 3
+    case = hex_case(nx, p)
+    A = oracle_problem(case, "helmholtz").dense()
+    m = mfa.Mesh(ctx, 8, case["coords"], case["cell_vert"])
+    sp = mfa.Space(m, p, 1, case["cell_node"], case["nnode"])
+    f64 = mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ)
+    f32 = mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ, precision=mfa.MFA_PREC_FP32)
+    pc = mfa.mfa_precond_create(ctx.h, f64.h, 5, mode=mfa.MFA_PRECOND_LINEAR)
+    rs, es = _pairs(ctx, A, f64, case["nnode"], nrhs=3, its=(2, 6, 20, 60, 150))
+    first, last = mfa.mfa_precond_train(ctx.h, pc, f32.h, rs, es, 800, 2e-3)
+    assert last < first
+    b = fi.uniform_vector(case["nnode"], seed=78)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    rc, it_l, _, rel, fb = mfa.mfa_fcg_learned(ctx.h, f64.h, f32.h, pc, 4, bd, x, 1e-10, 1000, fallback=False)
+    assert rc == mfa.MFA_OK and rel <= 1e-10
+    assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 2e-10 * np.linalg.norm(b)
+    rc, it_j, _, _ = mfa.mfa_fcg_mixed(ctx.h, f64.h, f32.h, 4, bd, torch.zeros_like(bd), 1e-10, 1000)
+    print("linear learned outer iterations", it_l, "jacobi", it_j, "loss", first, "->", last)
+    assert it_l <= it_j
+    mfa.mfa_precond_destroy(pc)

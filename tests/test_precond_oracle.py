@@ -65,3 +65,25 @@ def test_gradients_match_finite_differences(small):
     # the loss is the relative A-norm error of the preconditioned step
     z = op.apply(r, cn, winv, dinv, W1, b1, W2)
     assert abs(L - (z - e) @ A @ (z - e) / (e @ A @ e)) < 1e-13
+
+
+def test_linear_variant_is_symmetric_positive_definite_and_linear(small):
+    case, A, W1, b1, W2, winv, dinv, r, e = small
+    cn = case["cell_node"]
+    n = case["nnode"]
+    Mmat = np.stack([op.apply_linear(np.eye(n)[j], cn, winv, dinv, W1) for j in range(n)], axis=1)
+    np.testing.assert_allclose(Mmat, Mmat.T, rtol=0, atol=1e-14 * np.abs(Mmat).max())
+    assert np.linalg.eigvalsh(Mmat).min() > 0
+    np.testing.assert_allclose(op.apply_linear(r, cn, winv, dinv, W1), Mmat @ r, rtol=1e-12)
+    np.testing.assert_allclose(op.apply_linear(r, cn, winv, dinv, 0 * W1), dinv * r, rtol=0, atol=0)
+
+
+def test_linear_variant_gradient_matches_finite_differences(small):
+    case, A, W1, b1, W2, winv, dinv, r, e = small
+    cn = case["cell_node"]
+    L, dW1 = op.loss_and_grad_linear(r, e, lambda v: A @ v, cn, winv, dinv, W1)
+    D = np.random.default_rng(2).standard_normal(W1.shape)
+    eps = 1e-6
+    fd = (op.loss_and_grad_linear(r, e, lambda v: A @ v, cn, winv, dinv, W1 + eps * D)[0] -
+          op.loss_and_grad_linear(r, e, lambda v: A @ v, cn, winv, dinv, W1 - eps * D)[0]) / (2 * eps)
+    assert abs(fd - np.sum(dW1 * D)) <= 1e-6 * max(1.0, abs(fd))
