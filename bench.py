@@ -50,6 +50,10 @@ def parse_args():
     ap.add_argument("--nrhs", type=int, default=2, help="pcg: right-hand sides timed")
     ap.add_argument("--inner", type=int, default=16, help="pcg: inner FP32 Jacobi-PCG steps per outer step")
     ap.add_argument("--inner-precision", choices=["fp32", "bf16", "fp64"], default="fp32")
+    ap.add_argument("--train-rhs", type=int, default=3)
+    ap.add_argument("--train-steps", type=int, default=800)
+    ap.add_argument("--train-lr", type=float, default=2e-3)
+    ap.add_argument("--train-data", choices=["grf", "white"], default="white")
     ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default=None,
                     help="arithmetic (hex and batched workloads; default fp64 for hex, fp32 for batched)")
     ap.add_argument("--nops", type=int, default=64)
@@ -538,7 +542,8 @@ def batched_arm(args, world, rank, local):
 
 
 def pcg_arm(args, world, rank, local):
-    """Time to ||b - A x|| <= 1e-8 ||b||: FP64 Jacobi-PCG against FP64-outer / FP32-inner flexible CG."""
+    """Time to ||b - A x|| <= 1e-8 ||b||: FP64 Jacobi-PCG, mixed FCG (FP32 Jacobi inner loop), and mixed
+    FCG with the learned linear preconditioner in the inner loop (training time reported separately)."""
     import torch
 
     from paper_1903_08243_gb300 import build as libbuild
@@ -559,44 +564,90 @@ def pcg_arm(args, world, rank, local):
     A32 = mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ, k2=1.0, precision=iprec)
     M64 = mfa.Form(sp, mfa.MFA_FORM_MASS)
     rtol = 1e-8
+
+    def grf_rhs(seed):
+        f = torch.from_numpy(fi.grf_lattice(nx * p + 1, seed=seed)).cuda()
+        b = M64.apply(f)  # b = M f_h
+        ctx.sync()
+        return b
+
+    # ---- training data: (r, e) pairs from plain CG iterates.  "grf": right-hand sides like the test
+    # ones, reference solution by the mixed solver; "white": manufactured solutions x* ~ U[-1,1) per dof,
+    # b = A x*, whose early plain-CG errors span the whole spectrum (the part a local preconditioner can act on).
+    t0 = time.perf_counter()
+    rs, es = [], []
+    its = (2, 6, 20, 60, 150) if args.train_data == "grf" else (0, 1, 2, 4, 8, 16)
+    for j in range(args.train_rhs):
+        if args.train_data == "grf":
+            b = grf_rhs(300 + j)
+            xs = torch.zeros_like(b)
+            mfa.mfa_fcg_mixed(ctx.h, A64.h, A32.h, args.inner, b, xs, 1e-10, 5000)
+        else:
+            xs = torch.from_numpy(fi.uniform_vector(nnode, seed=300 + j)).cuda()
+            b = A64.apply(xs)
+        for k in its:
+            x = torch.zeros_like(b)
+            mfa.mfa_cg(ctx.h, A32.h, mfa.MFA_PC_NONE, b, x, 1e-30, k)  # k plain CG steps
+            r = b - A64.apply(x)
+            rs.append(r.float())
+            es.append((xs - x).float())
+    ctx.sync()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pc = mfa.mfa_precond_create(ctx.h, A64.h, 5, mode=mfa.MFA_PRECOND_LINEAR)
+    loss_first, loss_last = mfa.mfa_precond_train(ctx.h, pc, A32.h, rs, es, args.train_steps, args.train_lr)
+    ctx.sync()
+    t_train = time.perf_counter() - t0
+    del rs, es
+
     rows = []
     sampler = ClockSampler(local)
     sampler.start()
     for r in range(args.nrhs + 1):  # the first solve of each method warms up and is not reported
-        f = torch.from_numpy(fi.grf_lattice(nx * p + 1, seed=400 + r)).cuda()
-        b = M64.apply(f)  # b = M f_h
-        ctx.sync()
+        b = grf_rhs(400 + r)
         res = {}
-        for name in ("jacobi_pcg_fp64", "fcg_mixed"):
+        for name in ("jacobi_pcg_fp64", "fcg_mixed", "fcg_learned"):
             x = torch.zeros_like(b)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
+            fb = 0
             if name == "jacobi_pcg_fp64":
                 rc, it, rel = mfa.mfa_cg(ctx.h, A64.h, mfa.MFA_PC_JACOBI, b, x, rtol, 20000)
                 inner = 0
-            else:
+            elif name == "fcg_mixed":
                 rc, it, inner, rel = mfa.mfa_fcg_mixed(ctx.h, A64.h, A32.h, args.inner, b, x, rtol, 5000)
+            else:
+                rc, it, inner, rel, fb = mfa.mfa_fcg_learned(ctx.h, A64.h, A32.h, pc, args.inner, b, x, rtol, 5000)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             true_rel = float(torch.linalg.norm(b - A64.apply(x)) / torch.linalg.norm(b))
             res[name] = {"seconds": dt, "iterations": it, "inner_iterations": inner, "relres": rel,
-                         "true_relres": true_rel, "status": rc}
+                         "true_relres": true_rel, "status": rc, "fallback": fb}
         if r > 0:
             rows.append(res)
     clocks = sampler.stop()
+    mfa.mfa_precond_destroy(pc)
     tj = statistics.mean(r["jacobi_pcg_fp64"]["seconds"] for r in rows)
     tm = statistics.mean(r["fcg_mixed"]["seconds"] for r in rows)
+    tl = statistics.mean(r["fcg_learned"]["seconds"] for r in rows)
     if rank == 0:
         line = {
-            "metric": "PCG time-to-1e-8", "value": tm, "unit": "s", "n_gpus": world, "steps": args.nrhs,
-            "warmup": 1, "ms_per_step": tm * 1e3, "higher_is_better": False, "scaling": "weak",
+            "metric": "PCG time-to-1e-8", "value": tl, "unit": "s", "n_gpus": world, "steps": args.nrhs,
+            "warmup": 1, "ms_per_step": tl * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 outer / %s inner" % args.inner_precision, "data": "synthetic",
             "config": {"workload": "pcg-hex%d^3-Q4-helmholtz-grf" % nx, "ndof": nnode,
-                       "rhs": "b = M f_h, f a Gaussian random field (256 random Fourier features, correlation length 0.1) on the node lattice, seeds 401..",
+                       "rhs": "b = M f_h, f a Gaussian random field (256 random Fourier features, correlation length 0.1) "
+                              "on the node lattice; training seeds 300.., test seeds 401..",
                        "stop": "FP64 ||b - A x||_2 <= 1e-8 ||b||_2 from x = 0",
-                       "mixed": "flexible CG (FP64 operator) preconditioned by %d steps of Jacobi-PCG with the %s operator" % (args.inner, args.inner_precision)},
-            "jacobi_pcg_fp64_seconds": tj, "speedup_vs_jacobi_pcg_fp64": tj / tm, "solves": rows, "clocks": clocks,
-            "roofline": None, "cpu_baseline": None, "e2e": None,
+                       "learned": "flexible CG (FP64 operator) preconditioned by %d steps of PCG with the %s operator "
+                                  "and the learned linear element preconditioner" % (args.inner, args.inner_precision),
+                       "training": {"data": args.train_data, "rhs": args.train_rhs, "plain_cg_iterates": list(its),
+                                    "steps": args.train_steps,
+                                    "lr": args.train_lr, "data_seconds": t_data, "train_seconds": t_train,
+                                    "loss_first (Jacobi step)": loss_first, "loss_last": loss_last}},
+            "jacobi_pcg_fp64_seconds": tj, "fcg_mixed_jacobi_seconds": tm, "fcg_learned_seconds": tl,
+            "speedup_vs_jacobi_pcg_fp64": tj / tl, "learned_gain_vs_jacobi_inner": tm / tl, "solves": rows,
+            "clocks": clocks, "roofline": None, "cpu_baseline": None, "e2e": None,
         }
         print(json.dumps(line), flush=True)
 
