@@ -113,8 +113,15 @@ def build_cases(args):
     return cases
 
 
-def kernel_hash():
-    src = os.path.join(ROOT, "paper_1903_08243_gb300", "csrc", "hex_kernels.cuh")
+def kernel_source(p, precision):
+    """Header holding the hex kernel that runs Q_p with p+1 points in this precision."""
+    if precision != "fp64":
+        return "hex_lines.cuh"
+    return "hex_eo.cuh" if 6 <= p <= 8 else "hex_kernels.cuh"
+
+
+def kernel_hash(name="hex_kernels.cuh"):
+    src = os.path.join(ROOT, "paper_1903_08243_gb300", "csrc", name)
     return hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
 
 
@@ -370,13 +377,20 @@ def gpu_arm(args, world, rank, local):
     i_dom = int(np.argmax(per_op_ms))
     dom = ops[i_dom]
     achieved = dom["info"].flops / (per_op_ms[i_dom] / 1e3) / 1e12
-    kh = kernel_hash()
-    traffic = NCU_TRAFFIC.get((kh, dom["case"]["name"])) if dom["case"]["cell_type"] == 8 else None
+    if dom["case"]["cell_type"] == 8:
+        ksrc = kernel_source(dom["case"]["p"], args.precision)
+        kh = kernel_hash(ksrc)
+        kname = {"hex_eo.cuh": "eo_apply_kernel", "hex_lines.cuh": "line_apply_kernel",
+                 "hex_kernels.cuh": "hex_apply_kernel"}[ksrc] + "<n=%d,%s>" % (dom["case"]["p"] + 1, dom["case"]["form"])
+    else:
+        kh, kname = None, "tet_apply_kernel<%s>" % dom["case"]["name"]
+    traffic = NCU_TRAFFIC.get((kh, dom["case"]["name"]))
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "operator": dom["case"]["name"],
+                "kernel": kname,
                 "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (FP64 pipe; recipe unit counts)",
                 "algorithmic_flops_per_launch": dom["info"].flops, "algorithmic_bytes_per_launch": dom["info"].bytes,
-                "kernel_sha1": kh if dom["case"]["cell_type"] == 8 else None}
+                "kernel_sha1": kh}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None

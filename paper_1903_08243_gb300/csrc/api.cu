@@ -62,7 +62,21 @@ void count_work(mfa_form* f) {
   const int64_t ndof = sp->nnode * sp->ncomp;
   const int kind = f->p.kind;
   double per_cell = 0.0, bytes = 0.0;
-  if (sp->mesh->cell_type == MFA_CELL_HEX8) {
+  if (sp->mesh->cell_type == MFA_CELL_HEX8 && mfa::hex_use_eo(sp->degree + 1, f->nq1, f->p.precision)) {
+    // even-odd line products: per line, forming e/o (2h adds), then per mirror pair of outputs
+    // (odd: one multiply) + 2h FMA + 2 adds, and for odd n a middle output
+    const int n = sp->degree + 1, h = n / 2, odd = n & 1;
+    auto line = [&](int sigma, int acc) {
+      double f_ = 2.0 * h + h * (4.0 * h + 2.0 + odd);
+      if (odd) f_ += 2.0 * h + (sigma > 0 ? 1.0 : 0.0);
+      return f_ + (acc ? n : 0);
+    };
+    const double L = (double)n * n, P = (double)n * n * n;
+    per_cell = L * 6.0 * line(1, 0) + P;  // B, B^T and the scatter adds
+    if (kind != MFA_FORM_MASS) per_cell += L * (3.0 * line(-1, 0) + 3.0 * line(-1, 1)) + 15.0 * P;  // D, D^T, G g
+    if (kind != MFA_FORM_LAPLACE) per_cell += P;  // c0 w|J| u
+    bytes = ncell * (4.0 * P + 8.0 * mfa::hex_geom_entries(kind) * P);
+  } else if (sp->mesh->cell_type == MFA_CELL_HEX8) {
     const double n = sp->degree + 1, q = f->nq1;
     const double sweeps = 2.0 * (q * n * n * n + q * q * n * n + q * q * q * n);  // one direction set
     per_cell = 2.0 * sweeps + n * n * n;                                            // B, B^T and the scatter add

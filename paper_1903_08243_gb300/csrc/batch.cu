@@ -76,7 +76,9 @@ int build(mfa_ctx* ctx, int n, mfa_form* const* forms, const double* const* xs, 
     g.kind = std::get<1>(key);
     g.prec = std::get<2>(key);
     g.tb = forms[members[0]]->hex;
-    const int cb = g.prec == MFA_PREC_FP64 ? mfa::hex_cells_per_block(g.n, g.n) : mfa::hex_line_cells_per_block(g.n);
+    const int cb = g.prec != MFA_PREC_FP64          ? mfa::hex_line_cells_per_block(g.n)
+                   : mfa::hex_use_eo(g.n, g.n, g.prec) ? mfa::hex_eo_cells_per_block(g.n)
+                                                       : mfa::hex_cells_per_block(g.n, g.n);
     std::vector<mfa::HexApplyArgs> items;
     std::vector<int64_t> first{0};
     for (int k : members) {

@@ -1,0 +1,211 @@
+// FP64 sum-factorised hex action with even-odd split 1D contractions.
+//
+// The FP64 pipe bounds the hex action on GB300, so the only way to go faster
+// is fewer FP64 instructions.  The GLL nodes and the Gauss points are both
+// symmetric about 1/2, hence the 1D matrices have a mirror symmetry:
+// B[i][j] = B[n-1-i][n-1-j] (centrosymmetric) and D[i][j] = -D[n-1-i][n-1-j]
+// (anti-centrosymmetric), and so do their transposes.  Writing the input of a
+// line as even and odd parts e_j = v_j + v_{n-1-j}, o_j = v_j - v_{n-1-j}
+// (j < n/2), an n x n product splits into two (n/2) x (n/2) products:
+//
+//   pe_i = sum_j E[i][j] e_j (+ S[i][mid] v_mid),  po_i = sum_j O[i][j] o_j,
+//   out_i = pe_i + po_i,  out_{n-1-i} = sigma (pe_i - po_i),
+//
+// with E = (S[i][j] + S[i][n-1-j]) / 2, O = (S[i][j] - S[i][n-1-j]) / 2 and
+// sigma = +1 for B, -1 for D.  For n = 5 this is 21 instead of 25 FP64
+// operations per line, for n = 7 37 instead of 49, for n = 9 57 instead of 81.
+// The sweep order and the pointwise physics are those of hex_kernels.cuh;
+// one thread owns one line per direction, the table entries are
+// compile-time offsets into __constant__ memory (FMA operands), and the
+// gather, the geometric-factor reads and the scatter run point-parallel.
+#pragma once
+
+#include "mfa_internal.h"
+
+namespace mfa {
+namespace hexeo {
+
+// Split table of one n x n matrix: E [h][h], O [h][h], Mc [h] = S[i][mid],
+// Mr [h+1] = (S[mid][j], j < h; S[mid][mid]).
+__host__ __device__ constexpr int split_size(int n) { return 2 * (n / 2) * (n / 2) + (n / 2) + (n / 2) + 1; }
+// Four matrices per n (0: B, 1: B^T, 2: D, 3: D^T), n = 5..9.
+__host__ __device__ constexpr int tab_offset(int n, int mat) {
+  int off = 0;
+  for (int k = 5; k < n; ++k) off += 4 * split_size(k);
+  return off + mat * split_size(n);
+}
+constexpr int kTabDoubles = tab_offset(10, 0);
+
+static __constant__ double c_eo[kTabDoubles];
+
+constexpr int ceil32(int x) { return (x + 31) / 32 * 32; }
+
+template <int N>
+struct EShape {
+  static constexpr int L = N * N;
+  static constexpr int P = N * N * N;
+  static constexpr int CB = 256 / L > 0 ? 256 / L : 1;
+  static constexpr int T = ceil32(CB * L);
+  static constexpr int SMEM = 5 * CB * P * 8;
+};
+
+template <int KIND>
+__host__ __device__ constexpr int geom_entries() {
+  return KIND == MFA_FORM_MASS ? 1 : (KIND == MFA_FORM_LAPLACE ? 6 : 7);
+}
+
+template <int N, int DIR>
+__device__ __forceinline__ int at(int a, int b, int m) {
+  if constexpr (DIR == 0) return m + N * (a + N * b);
+  else if constexpr (DIR == 1) return a + N * (m + N * b);
+  else return a + N * (b + N * m);
+}
+
+// out (+)= S v along direction DIR of line (a, b); MAT selects S, SIGMA its mirror sign.
+template <int N, int DIR, int MAT, int SIGMA, bool ACC>
+__device__ __forceinline__ void eo_sweep(const double* in, double* out, int a, int b) {
+  constexpr int H = N / 2;
+  constexpr bool ODD = (N & 1) != 0;
+  constexpr int base = tab_offset(N, MAT);
+  constexpr int oE = base, oO = base + H * H, oMc = base + 2 * H * H, oMr = oMc + H;
+  double v[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) v[m] = in[at<N, DIR>(a, b, m)];
+  double e[H], o[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    e[j] = v[j] + v[N - 1 - j];
+    o[j] = v[j] - v[N - 1 - j];
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    double pe = 0.0, po = 0.0;
+    if constexpr (ODD) pe = c_eo[oMc + i] * v[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      pe = fma(c_eo[oE + i * H + j], e[j], pe);
+      po = fma(c_eo[oO + i * H + j], o[j], po);
+    }
+    const double lo = pe + po;
+    const double hi = SIGMA > 0 ? pe - po : po - pe;
+    if constexpr (ACC) {
+      out[at<N, DIR>(a, b, i)] += lo;
+      out[at<N, DIR>(a, b, N - 1 - i)] += hi;
+    } else {
+      out[at<N, DIR>(a, b, i)] = lo;
+      out[at<N, DIR>(a, b, N - 1 - i)] = hi;
+    }
+  }
+  if constexpr (ODD) {
+    double s = SIGMA > 0 ? c_eo[oMr + H] * v[H] : 0.0;  // the middle diagonal of D is zero
+#pragma unroll
+    for (int j = 0; j < H; ++j) s = fma(c_eo[oMr + j], SIGMA > 0 ? e[j] : o[j], s);
+    if constexpr (ACC) out[at<N, DIR>(a, b, H)] += s;
+    else out[at<N, DIR>(a, b, H)] = s;
+  }
+}
+
+template <int N, int KIND, bool COLOUR>
+__device__ __forceinline__ void eo_batch(const HexApplyArgs& a, int64_t batch, double* smem) {
+  using S = EShape<N>;
+  constexpr int L = S::L, P = S::P, CB = S::CB, T = S::T, NG = geom_entries<KIND>();
+  const int t = threadIdx.x;
+  const int cl = t / L, l = t - cl * L;
+  const int la = l % N, lb = l / N;
+  const int64_t c0 = batch * CB;
+  const int ncb = (int)(a.count - c0 < CB ? a.count - c0 : CB);
+  const bool valid = cl < ncb;
+  double* U0 = smem;
+  double* V0 = U0 + CB * P;
+  double* G0 = V0 + CB * P;
+  double* G1 = G0 + CB * P;
+  double* G2 = G1 + CB * P;
+  double* U = U0 + cl * P;
+  double* V = V0 + cl * P;
+  double* F0 = G0 + cl * P;
+  double* F1 = G1 + cl * P;
+  double* F2 = G2 + cl * P;
+  const double* geom = static_cast<const double*>(a.geom);
+  auto cell_of = [&](int c) -> int64_t { return a.cell_list ? (int64_t)__ldg(a.cell_list + c0 + c) : c0 + c; };
+
+  for (int i = t; i < ncb * P; i += T) {  // gather, point-parallel
+    const int c = i / P, k = i - c * P;
+    U0[i] = __ldg(a.x + __ldg(a.cell_node + cell_of(c) * P + k));
+  }
+  __syncthreads();
+  if (valid) eo_sweep<N, 0, 0, 1, false>(U, V, la, lb);  // B in x
+  __syncthreads();
+  if (valid) eo_sweep<N, 1, 0, 1, false>(V, U, la, lb);  // B in y
+  __syncthreads();
+  if (valid) eo_sweep<N, 2, 0, 1, false>(U, V, la, lb);  // B in z: values at the Gauss points
+  __syncthreads();
+  if constexpr (KIND == MFA_FORM_MASS) {
+    for (int i = t; i < ncb * P; i += T) {
+      const int c = i / P, q = i - c * P;
+      U0[i] = __ldg(geom + cell_of(c) * P + q) * V0[i];
+    }
+  } else {
+    if (valid) {
+      eo_sweep<N, 0, 2, -1, false>(V, F0, la, lb);  // D in x
+      eo_sweep<N, 1, 2, -1, false>(V, F1, la, lb);  // D in y
+      eo_sweep<N, 2, 2, -1, false>(V, F2, la, lb);  // D in z
+    }
+    __syncthreads();
+    for (int i = t; i < ncb * P; i += T) {  // pointwise physics, point-parallel
+      const int c = i / P, q = i - c * P;
+      const double* gc = geom + cell_of(c) * (int64_t)NG * P + q;
+      double g[NG];
+#pragma unroll
+      for (int e = 0; e < NG; ++e) g[e] = __ldg(gc + (int64_t)e * P);
+      const double d0 = G0[i], d1 = G1[i], d2 = G2[i];
+      G0[i] = fma(g[0], d0, fma(g[3], d1, g[4] * d2));
+      G1[i] = fma(g[3], d0, fma(g[1], d1, g[5] * d2));
+      G2[i] = fma(g[4], d0, fma(g[5], d1, g[2] * d2));
+      if constexpr (KIND == MFA_FORM_HELMHOLTZ) U0[i] = g[6] * V0[i];
+      else U0[i] = 0.0;
+    }
+    __syncthreads();
+    if (valid) eo_sweep<N, 0, 3, -1, true>(F0, U, la, lb);  // + D_x^T f0
+    __syncthreads();
+    if (valid) eo_sweep<N, 1, 3, -1, true>(F1, U, la, lb);  // + D_y^T f1
+    __syncthreads();
+    if (valid) eo_sweep<N, 2, 3, -1, true>(F2, U, la, lb);  // + D_z^T f2
+  }
+  __syncthreads();
+  if (valid) eo_sweep<N, 2, 1, 1, false>(U, V, la, lb);  // B^T in z
+  __syncthreads();
+  if (valid) eo_sweep<N, 1, 1, 1, false>(V, U, la, lb);  // B^T in y
+  __syncthreads();
+  if (valid) eo_sweep<N, 0, 1, 1, false>(U, V, la, lb);  // B^T in x
+  __syncthreads();
+  for (int i = t; i < ncb * P; i += T) {  // scatter-add, point-parallel
+    const int c = i / P, k = i - c * P;
+    const int32_t node = __ldg(a.cell_node + cell_of(c) * P + k);
+    if constexpr (COLOUR) a.y[node] += V0[i];  // no other cell of this colour touches `node`
+    else atomicAdd(a.y + node, V0[i]);
+  }
+  __syncthreads();
+}
+
+template <int N, int KIND, bool COLOUR>
+__global__ void __launch_bounds__(EShape<N>::T) eo_apply_kernel(const HexApplyArgs a) {
+  extern __shared__ __align__(16) double smem_eo[];
+  const int64_t nbatch = (a.count + EShape<N>::CB - 1) / EShape<N>::CB;
+  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) eo_batch<N, KIND, COLOUR>(a, batch, smem_eo);
+}
+
+template <int N, int KIND>
+__global__ void __launch_bounds__(EShape<N>::T) eo_group_kernel(const HexApplyArgs* __restrict__ items,
+                                                                const int64_t* __restrict__ first, int nitems) {
+  extern __shared__ __align__(16) double smem_eo[];
+  const int64_t total = first[nitems];
+  int k = 0;
+  for (int64_t gb = blockIdx.x; gb < total; gb += gridDim.x) {
+    while (k + 1 < nitems && gb >= first[k + 1]) ++k;
+    const HexApplyArgs h = items[k];
+    eo_batch<N, KIND, false>(h, gb - first[k], smem_eo);
+  }
+}
+
+}  // namespace hexeo
+}  // namespace mfa

@@ -121,6 +121,7 @@ cudaError_t hex_geometry_launch(int nq, int kind, int prec, double c0, const Hex
 cudaError_t hex_apply_launch(int n, int nq, int kind, int prec, bool colour, const HexTables& tb,
                              const HexApplyArgs& a, int sm_count, cudaStream_t s) {
   if (prec != MFA_PREC_FP64) return hex_apply_launch_mixed(n, nq, kind, prec, colour, tb, a, sm_count, s);
+  if (hex_use_eo(n, nq, prec)) return hex_eo_apply_launch(n, kind, colour, a, sm_count, s);
   using namespace hexk;
   MFA_HEX_KIND_CASES(2, 2, MFA_PREC_FP64)
   MFA_HEX_KIND_CASES(3, 3, MFA_PREC_FP64)
@@ -142,6 +143,7 @@ cudaError_t hex_apply_launch(int n, int nq, int kind, int prec, bool colour, con
 cudaError_t hex_group_launch(int n, int kind, int prec, const HexTables& tb, const HexApplyArgs* items,
                              const int64_t* first, int nitems, int64_t total, int sm_count, cudaStream_t s) {
   if (prec != MFA_PREC_FP64) return hex_group_launch_mixed(n, kind, prec, tb, items, first, nitems, total, sm_count, s);
+  if (hex_use_eo(n, n, prec)) return hex_eo_group_launch(n, kind, items, first, nitems, total, sm_count, s);
   using namespace hexk;
   MFA_HEX_GROUP_CASES(2, MFA_PREC_FP64)
   MFA_HEX_GROUP_CASES(3, MFA_PREC_FP64)

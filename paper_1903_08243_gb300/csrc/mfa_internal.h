@@ -65,6 +65,16 @@ cudaError_t hex_group_launch_mixed(int n, int kind, int prec, const HexTables& t
                                    const int64_t* first, int nitems, int64_t total, int sm_count, cudaStream_t s);
 int hex_cells_per_block(int n, int nq);
 int hex_line_cells_per_block(int n);
+// FP64 even-odd action for n = 5..9, p+1 points (hex_eo.cuh).
+cudaError_t hex_eo_apply_launch(int n, int kind, bool colour, const HexApplyArgs& a, int sm_count, cudaStream_t s);
+cudaError_t hex_eo_group_launch(int n, int kind, const HexApplyArgs* items, const int64_t* first, int nitems,
+                                int64_t total, int sm_count, cudaStream_t s);
+int hex_eo_cells_per_block(int n);
+// FP64 kernel choice.  The even-odd line kernel issues 16-30% fewer FP64
+// instructions (n = 5..9) but, with n^2 threads per cell, keeps the FP64 pipe
+// busy ~80% of the time against ~93% for the point kernel; measured on GB300
+// it wins from n = 7 (Q6: 14.15 vs 14.86 ms) and loses at n = 5, 6.
+inline bool hex_use_eo(int n, int nq, int prec) { return prec == MFA_PREC_FP64 && nq == n && n >= 7 && n <= 9; }
 // FP32/BF16 action with float vectors.
 cudaError_t hex_apply_launch_f32(int n, int kind, int prec, const float* x, float* y, const int32_t* cell_node,
                                  const void* geom, int64_t count, int sm_count, cudaStream_t s);
