@@ -168,7 +168,8 @@ MFA_API int mfa_convert_f32_to_f64(mfa_ctx *ctx, const float *x, double *y, int6
  * waits.  The device staging buffers are owned by the form. */
 MFA_API int mfa_apply_host(mfa_ctx *ctx, mfa_form *form, const double *x_host, double *y_host);
 /* Wait for the context stream; MFA_ERR_DOMAIN if a kernel flagged det J <= 0
- * or a deformation with J <= 0 since the last mfa_sync (the flag is cleared). */
+ * or a deformation with J <= 0, MFA_ERR_TIMEOUT if a kernel gave up a bounded
+ * wait, since the last mfa_sync (the flag is cleared). */
 MFA_API int mfa_sync(mfa_ctx *ctx);
 
 /* d_i = A_ii (linear forms): the matrix-free diagonal, assembled per cell

@@ -201,7 +201,7 @@ int apply_form(mfa_form* f, const double* x, double* y, cudaStream_t stream) {
     const int64_t count = colour ? sp->colour_offsets[k + 1] - sp->colour_offsets[k] : sp->mesh->ncell;
     cudaError_t e;
     if (sp->mesh->cell_type == MFA_CELL_HEX8) {
-      mfa::HexApplyArgs a{x, y, sp->d_cell_node, f->d_geom, list, count, ctx->d_err};
+      mfa::HexApplyArgs a{x, y, sp->d_cell_node, f->d_geom, list, count, ctx->d_err, f->gstride};
       e = mfa::hex_apply_launch(sp->degree + 1, f->nq1, f->p.kind, f->p.precision, colour, f->hex, a, ctx->sm_count,
                                 stream);
     } else {
@@ -405,12 +405,15 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
     if (!rc) {
       const int ng = mfa::hex_geom_entries(kind);
       const size_t esz = prm->precision == MFA_PREC_FP64 ? 8 : (prm->precision == MFA_PREC_FP32 ? 4 : 2);
-      rc = cuda_alloc((void**)&f->d_geom, esz * ng * f->nq * sp->mesh->ncell, "geometric factors");
+      // FP32/BF16 blocks are padded to 16 bytes per cell: the kernel moves them with bulk copies
+      f->gstride = (int64_t)ng * f->nq;
+      if (prm->precision != MFA_PREC_FP64) f->gstride = (f->gstride * (int64_t)esz + 15) / 16 * 16 / (int64_t)esz;
+      rc = cuda_alloc((void**)&f->d_geom, esz * f->gstride * sp->mesh->ncell, "geometric factors");
       const double c0 = kind == MFA_FORM_HELMHOLTZ ? prm->k2 : 1.0;
       if (!rc) {
         cudaError_t e = mfa::hex_geometry_launch(f->nq1, kind, prm->precision, c0, f->hex, sp->mesh->d_coords,
-                                                 sp->mesh->d_cell_vert, sp->mesh->ncell, f->d_geom, ctx->d_err,
-                                                 ctx->stream);
+                                                 sp->mesh->d_cell_vert, sp->mesh->ncell, f->d_geom, f->gstride,
+                                                 ctx->d_err, ctx->stream);
         if (e != cudaSuccess) rc = fail(MFA_ERR_CUDA, "geometry kernel: %s", cudaGetErrorString(e));
       }
       if (!rc) rc = mfa_sync(ctx);
@@ -481,7 +484,8 @@ int mfa_apply_f32(mfa_ctx* ctx, mfa_form* f, const float* x, float* y, int accum
   const int64_t ndof = sp->nnode * sp->ncomp;
   if (!accumulate) MFA_CUDA(cudaMemsetAsync(y, 0, sizeof(float) * ndof, ctx->stream));
   cudaError_t e = mfa::hex_apply_launch_f32(sp->degree + 1, f->p.kind, f->p.precision, x, y, sp->d_cell_node,
-                                            f->d_geom, sp->mesh->ncell, ctx->sm_count, ctx->stream);
+                                            f->d_geom, sp->mesh->ncell, f->gstride, ctx->d_err, ctx->sm_count,
+                                            ctx->stream);
   if (e != cudaSuccess) return fail(MFA_ERR_CUDA, "mfa_apply_f32: %s", cudaGetErrorString(e));
   return MFA_OK;
 }
@@ -523,6 +527,7 @@ int mfa_sync(mfa_ctx* ctx) {
   MFA_CUDA(cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     MFA_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    if (flag & 4) return fail(MFA_ERR_TIMEOUT, "a kernel gave up waiting for a bulk copy");
     return fail(MFA_ERR_DOMAIN, "kernel reported %s%s", (flag & 1) ? "det J == 0 or non-finite " : "",
                 (flag & 2) ? "deformation with J <= 0" : "");
   }

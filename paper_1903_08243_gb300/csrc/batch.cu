@@ -83,7 +83,8 @@ int build(mfa_ctx* ctx, int n, mfa_form* const* forms, const double* const* xs, 
     std::vector<int64_t> first{0};
     for (int k : members) {
       mfa_form* f = forms[k];
-      mfa::HexApplyArgs a{xs[k], ys[k], f->space->d_cell_node, f->d_geom, nullptr, f->space->mesh->ncell, ctx->d_err};
+      mfa::HexApplyArgs a{xs[k], ys[k], f->space->d_cell_node, f->d_geom,     nullptr,
+                          f->space->mesh->ncell, ctx->d_err, f->gstride};
       items.push_back(a);
       first.push_back(first.back() + (f->space->mesh->ncell + cb - 1) / cb);
     }

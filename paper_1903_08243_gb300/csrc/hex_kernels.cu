@@ -37,7 +37,7 @@ __device__ __forceinline__ void store_geo<__nv_bfloat16>(__nv_bfloat16* p, doubl
 template <typename TG>
 __global__ void hex_geometry_kernel(const __grid_constant__ HexTables tb, int nq1, int ng, double c0,
                                     const double* __restrict__ coords, const int32_t* __restrict__ cell_vert,
-                                    int64_t ncell, TG* __restrict__ geom, int* err) {
+                                    int64_t ncell, TG* __restrict__ geom, int64_t stride, int* err) {
   const int pq = nq1 * nq1 * nq1;
   const int64_t total = ncell * pq;
   for (int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gid < total;
@@ -68,7 +68,7 @@ __global__ void hex_geometry_kernel(const __grid_constant__ HexTables tb, int nq
     const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
     if (!(det != 0.0) || !isfinite(det)) {
       atomicOr(err, 1);
-      for (int e = 0; e < ng; ++e) store_geo(geom + (cell * ng + e) * pq + q, 0.0);
+      for (int e = 0; e < ng; ++e) store_geo(geom + cell * stride + e * pq + q, 0.0);
       continue;
     }
     // inverse by the adjugate: Ji[i][j] = cof[j][i] / det
@@ -83,7 +83,7 @@ __global__ void hex_geometry_kernel(const __grid_constant__ HexTables tb, int nq
     Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
     Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
     const double wdet = w * fabs(det);
-    TG* out = geom + cell * ng * pq + q;
+    TG* out = geom + cell * stride + q;
     if (ng == 1) {
       store_geo(out, c0 * wdet);
       continue;
@@ -100,7 +100,8 @@ __global__ void hex_geometry_kernel(const __grid_constant__ HexTables tb, int nq
 }  // namespace
 
 cudaError_t hex_geometry_launch(int nq, int kind, int prec, double c0, const HexTables& tb, const double* coords,
-                                const int32_t* cell_vert, int64_t ncell, void* geom, int* err, cudaStream_t s) {
+                                const int32_t* cell_vert, int64_t ncell, void* geom, int64_t stride, int* err,
+                                cudaStream_t s) {
   const int64_t total = ncell * nq * nq * nq;
   if (total == 0) return cudaSuccess;
   int64_t blocks = (total + 255) / 256;
@@ -108,13 +109,13 @@ cudaError_t hex_geometry_launch(int nq, int kind, int prec, double c0, const Hex
   const int ng = hex_geom_entries(kind);
   if (prec == MFA_PREC_FP64)
     hex_geometry_kernel<double><<<(unsigned)blocks, 256, 0, s>>>(tb, nq, ng, c0, coords, cell_vert, ncell,
-                                                                 static_cast<double*>(geom), err);
+                                                                 static_cast<double*>(geom), stride, err);
   else if (prec == MFA_PREC_FP32)
     hex_geometry_kernel<float><<<(unsigned)blocks, 256, 0, s>>>(tb, nq, ng, c0, coords, cell_vert, ncell,
-                                                                static_cast<float*>(geom), err);
+                                                                static_cast<float*>(geom), stride, err);
   else
     hex_geometry_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, s>>>(tb, nq, ng, c0, coords, cell_vert, ncell,
-                                                                        static_cast<__nv_bfloat16*>(geom), err);
+                                                                        static_cast<__nv_bfloat16*>(geom), stride, err);
   return cudaGetLastError();
 }
 

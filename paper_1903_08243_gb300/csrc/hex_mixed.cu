@@ -16,14 +16,15 @@ cudaError_t hex_line_group_b(int n, int kind, int prec, const HexApplyArgs* item
 cudaError_t hex_apply_launch_mixed(int n, int nq, int kind, int prec, bool colour, const HexTables&,
                                    const HexApplyArgs& a, int sm_count, cudaStream_t s) {
   if (nq != n || colour || a.cell_list) return cudaErrorInvalidValue;
-  const hexl::LineArgs la{a.x, a.y, a.cell_node, a.geom, a.count};
+  const hexl::LineArgs la{a.x, a.y, a.cell_node, a.geom, a.count, a.geom_stride, a.err};
   return n <= 5 ? hex_line_apply_a(n, kind, prec, false, la, sm_count, s)
                 : hex_line_apply_b(n, kind, prec, false, la, sm_count, s);
 }
 
 cudaError_t hex_apply_launch_f32(int n, int kind, int prec, const float* x, float* y, const int32_t* cell_node,
-                                 const void* geom, int64_t count, int sm_count, cudaStream_t s) {
-  const hexl::LineArgs la{x, y, cell_node, geom, count};
+                                 const void* geom, int64_t count, int64_t gstride, int* err, int sm_count,
+                                 cudaStream_t s) {
+  const hexl::LineArgs la{x, y, cell_node, geom, count, gstride, err};
   return n <= 5 ? hex_line_apply_a(n, kind, prec, true, la, sm_count, s)
                 : hex_line_apply_b(n, kind, prec, true, la, sm_count, s);
 }

@@ -51,6 +51,7 @@ struct HexApplyArgs {
   const int32_t* cell_list;  // cells to process (nullptr: 0..count-1)
   int64_t count;             // number of cells to process
   int* err;
+  int64_t geom_stride;       // elements per cell of geom (ng * nq^3, padded to 16 bytes for FP32/BF16)
 };
 
 // Launch the sum-factorised FP64 action for cells [list].  Returns a cudaError_t.
@@ -77,9 +78,11 @@ int hex_eo_cells_per_block(int n);
 inline bool hex_use_eo(int n, int nq, int prec) { return prec == MFA_PREC_FP64 && nq == n && n >= 7 && n <= 9; }
 // FP32/BF16 action with float vectors.
 cudaError_t hex_apply_launch_f32(int n, int kind, int prec, const float* x, float* y, const int32_t* cell_node,
-                                 const void* geom, int64_t count, int sm_count, cudaStream_t s);
+                                 const void* geom, int64_t count, int64_t gstride, int* err, int sm_count,
+                                 cudaStream_t s);
 cudaError_t hex_geometry_launch(int nq, int kind, int prec, double c0, const HexTables& tb, const double* coords,
-                                const int32_t* cell_vert, int64_t ncell, void* geom, int* err, cudaStream_t s);
+                                const int32_t* cell_vert, int64_t ncell, void* geom, int64_t stride, int* err,
+                                cudaStream_t s);
 cudaError_t hex_diagonal_launch(int n, int nq, int kind, const HexTables& tb, const int32_t* cell_node,
                                 const double* geom, int64_t ncell, double* d, int sm_count, cudaStream_t s);
 int hex_geom_entries(int kind);  // stored FP64 values per quadrature point
@@ -185,6 +188,7 @@ struct mfa_form {
   mfa::HexTables hex{};
   mfa::TetTables tet{};
   void* d_geom = nullptr;
+  int64_t gstride = 0;           // elements per cell of d_geom
   const double* d_coef = nullptr;
   double* d_stage_x = nullptr;   // mfa_apply_host staging
   double* d_stage_y = nullptr;
