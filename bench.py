@@ -383,7 +383,8 @@ def gpu_arm(args, world, rank, local):
         kname = {"hex_eo.cuh": "eo_apply_kernel", "hex_lines.cuh": "line_apply_kernel",
                  "hex_kernels.cuh": "hex_apply_kernel"}[ksrc] + "<n=%d,%s>" % (dom["case"]["p"] + 1, dom["case"]["form"])
     else:
-        kh, kname = None, "tet_apply_kernel<%s>" % dom["case"]["name"]
+        moment = dom["case"]["p"] == 2 and dom["case"]["form"] in ("hyper_res", "hyper_jac")
+        kh, kname = None, ("tet_moment_kernel<%s>" if moment else "tet_apply_kernel<%s>") % dom["case"]["name"]
     traffic = NCU_TRAFFIC.get((kh, dom["case"]["name"]))
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "operator": dom["case"]["name"],

@@ -84,6 +84,18 @@ void count_work(mfa_form* f) {
     if (kind != MFA_FORM_LAPLACE) per_cell += q * q * q;                            // c0 w|J| u
     const double esz = f->p.precision == MFA_PREC_FP64 ? 8.0 : (f->p.precision == MFA_PREC_FP32 ? 4.0 : 2.0);
     bytes = ncell * (4.0 * n * n * n + esz * mfa::hex_geom_entries(kind) * q * q * q);
+  } else if (sp->degree == 2 && sp->ncomp == 3 && f->nq == 27 &&
+             (kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC)) {
+    // moment kernel: per field 10x3x12 FMA moments + 36 mapped entries (900), per point the
+    // gradient(s) (54 each), wd and wd*xi (4), the physics, the moment sums (72); per cell the
+    // map back (180), the outputs (720), the body force (60, residual) and the scatter adds (30).
+    // ln J and one division count as one flop each.
+    const bool res = kind == MFA_FORM_HYPER_RES, svk = f->p.law == MFA_LAW_SVK;
+    const double phys = res ? (svk ? 102.0 : 66.0) : (svk ? 243.0 : 202.0);
+    const double fields = res ? 1.0 : 2.0;
+    per_cell = 60.0 + 900.0 * fields + 27.0 * (54.0 * fields + 76.0 + phys) + 180.0 + 720.0 + (res ? 60.0 : 0.0) + 30.0;
+    bytes = ncell * (4.0 * sp->nloc + 16.0) + 24.0 * sp->mesh->nvert;
+    if (kind == MFA_FORM_HYPER_JAC) bytes += 8.0 * ndof;
   } else {
     const double nl = sp->nloc, nc = sp->ncomp, nq = f->nq;
     double per_q = 0.0;
@@ -162,6 +174,26 @@ int tet_tables(mfa_form* f) {
   f->tet.nq = nq;
   const int nl = f->space->nloc;
   for (int i = 0; i < nq; ++i) mfa::tet_basis(p, pts + 3 * i, f->tet.phi + i * nl, f->tet.dphi + i * nl * 3);
+  for (int i = 0; i < 3 * nq; ++i) f->tet.pts[i] = pts[i];
+  if (p == 2) {  // the P2 reference gradients are linear: alpha = grad(0), beta[.][f] = grad(e_f) - grad(0)
+    double phi0[10], g0[30], phif[10], gf[30];
+    const double origin[3] = {0.0, 0.0, 0.0};
+    mfa::tet_basis(2, origin, phi0, g0);
+    for (int a = 0; a < 10; ++a)
+      for (int e = 0; e < 3; ++e) f->tet.alpha[a * 3 + e] = g0[a * 3 + e];
+    for (int fd = 0; fd < 3; ++fd) {
+      double ef[3] = {0.0, 0.0, 0.0};
+      ef[fd] = 1.0;
+      mfa::tet_basis(2, ef, phif, gf);
+      for (int a = 0; a < 10; ++a)
+        for (int e = 0; e < 3; ++e) f->tet.beta[a * 9 + e * 3 + fd] = gf[a * 3 + e] - g0[a * 3 + e];
+    }
+    for (int a = 0; a < 10; ++a) {
+      double m = 0.0;
+      for (int q = 0; q < nq; ++q) m += f->tet.w[q] * f->tet.phi[q * nl + a];
+      f->tet.mvec[a] = m;
+    }
+  }
   f->nq = nq;
   return MFA_OK;
 }

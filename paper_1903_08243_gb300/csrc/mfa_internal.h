@@ -94,6 +94,11 @@ struct TetTables {
   double w[kTetMaxQ];
   double phi[kTetMaxQ * 10];      // [q][a]
   double dphi[kTetMaxQ * 10 * 3]; // [q][a][d] reference gradients
+  // P2 only: reference gradient of basis a is alpha[a] + beta[a] xi (linear in xi)
+  double pts[kTetMaxQ * 3];       // [q][3] quadrature points
+  double alpha[10 * 3];           // [a][e]
+  double beta[10 * 9];            // [a][e][f]
+  double mvec[10];                // sum_q w_q phi_a(xi_q)
 };
 
 struct TetApplyArgs {
