@@ -61,7 +61,10 @@ def parse_args():
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
     ap.add_argument("--degrees", default="1,2,3,4,5,6")
     ap.add_argument("--forms", default="laplace,helmholtz")
-    ap.add_argument("--scatter", choices=["atomic", "colour"], default="atomic")
+    ap.add_argument("--scatter", choices=["atomic", "colour"], default="atomic",
+                    help="scatter at form creation (the autotuner may change it)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep each form's default launch configuration instead of timing all of them")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     return ap.parse_args()
@@ -113,11 +116,9 @@ def build_cases(args):
     return cases
 
 
-def kernel_source(p, precision):
-    """Header holding the hex kernel that runs Q_p with p+1 points in this precision."""
-    if precision != "fp64":
-        return "hex_lines.cuh"
-    return "hex_eo.cuh" if 6 <= p <= 8 else "hex_kernels.cuh"
+# launch-configuration variant -> (header holding the kernel, kernel name)
+VARIANT_KERNELS = {1: ("hex_kernels.cuh", "hex_apply_kernel"), 2: ("hex_eo.cuh", "eo_apply_kernel"),
+                   3: ("hex_lines.cuh", "line_apply_kernel"), 4: ("hex_lines.cuh", "line_apply_kernel")}
 
 
 def kernel_hash(name="hex_kernels.cuh"):
@@ -305,6 +306,21 @@ def gpu_arm(args, world, rank, local):
         y = torch.empty_like(x)
         ops.append(dict(case=c, form=form, x=x, y=y, info=form.info()))
     ctx.sync()
+    # autotuner: every compiled launch configuration of each form is timed, the fastest kept
+    tune_s = 0.0
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        for o in ops:
+            default_cfg = o["form"].config()
+            tried = o["form"].autotune(o["x"], o["y"], reps=3)
+            default_ms = next(c.ms for c in tried if (c.variant, c.cells_per_block, c.scatter) ==
+                              (default_cfg.variant, default_cfg.cells_per_block, default_cfg.scatter))
+            o["tune"] = dict(o["form"].config().as_dict(), default_ms=default_ms, configs_tried=len(tried))
+            o["info"] = o["form"].info()
+        tune_s = time.perf_counter() - t0
+    for o in ops:
+        o["cfg"] = o["form"].config()
+    ctx.sync()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
     launches_per_step = sum(o["info"].ncolours if o["info"].scatter == mfa.MFA_SCATTER_COLOUR else 1 for o in ops)
 
@@ -378,20 +394,32 @@ def gpu_arm(args, world, rank, local):
     dom = ops[i_dom]
     achieved = dom["info"].flops / (per_op_ms[i_dom] / 1e3) / 1e12
     if dom["case"]["cell_type"] == 8:
-        ksrc = kernel_source(dom["case"]["p"], args.precision)
+        ksrc, kbase = VARIANT_KERNELS[dom["cfg"].variant]
         kh = kernel_hash(ksrc)
-        kname = {"hex_eo.cuh": "eo_apply_kernel", "hex_lines.cuh": "line_apply_kernel",
-                 "hex_kernels.cuh": "hex_apply_kernel"}[ksrc] + "<n=%d,%s>" % (dom["case"]["p"] + 1, dom["case"]["form"])
+        kname = kbase + "<n=%d,%s,cb=%d>" % (dom["case"]["p"] + 1, dom["case"]["form"], dom["cfg"].cells_per_block)
     else:
         moment = dom["case"]["p"] == 2 and dom["case"]["form"] in ("hyper_res", "hyper_jac")
         kh, kname = None, ("tet_moment_kernel<%s>" if moment else "tet_apply_kernel<%s>") % dom["case"]["name"]
     traffic = NCU_TRAFFIC.get((kh, dom["case"]["name"]))
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "operator": dom["case"]["name"],
-                "kernel": kname,
-                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (FP64 pipe; recipe unit counts)",
-                "algorithmic_flops_per_launch": dom["info"].flops, "algorithmic_bytes_per_launch": dom["info"].bytes,
-                "kernel_sha1": kh}
+    if args.workload == "hex" and args.precision != "fp64":
+        # FP32/BF16 contractions: bound by HBM bandwidth (algorithmic bytes of the dominant operator)
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        gbs = dom["info"].bytes / (per_op_ms[i_dom] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                    "traffic": traffic, "operator": dom["case"]["name"], "kernel": kname,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
+                    "algorithmic_bytes_per_launch": dom["info"].bytes, "kernel_sha1": kh}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "operator": dom["case"]["name"],
+                    "kernel": kname,
+                    "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (FP64 pipe; recipe unit counts)",
+                    "algorithmic_flops_per_launch": dom["info"].flops,
+                    "executed_flops_per_launch": dom["info"].flops_executed,
+                    "frac_executed": dom["info"].flops_executed / (per_op_ms[i_dom] / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                    "algorithmic_bytes_per_launch": dom["info"].bytes, "kernel_sha1": kh}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
@@ -423,12 +451,17 @@ def gpu_arm(args, world, rank, local):
     for o, ms in zip(ops, per_op_ms):
         per_op.append({"operator": o["case"]["name"], "ndof": o["case"]["ndof"], "ms": ms,
                        "gdof_s": o["case"]["ndof"] / ms / 1e6, "gflop_s": o["info"].flops / ms / 1e6,
-                       "frac_fp64": o["info"].flops / ms / 1e9 / FP64_PEAK_TFLOPS, "ncolours": o["info"].ncolours})
+                       "frac_fp64": o["info"].flops / ms / 1e9 / FP64_PEAK_TFLOPS,
+                       "frac_fp64_executed": o["info"].flops_executed / ms / 1e9 / FP64_PEAK_TFLOPS,
+                       "ncolours": o["info"].ncolours,
+                       "launch": dict(o["cfg"].as_dict(), ms=None), "tune": o.get("tune")})
     if rank == 0:
         cfg = {"workload": workload_name(args), "operators": [c["name"] for c in cases], "scatter": args.scatter,
                "ndof_per_step": ndof_step, "graph_replay": bool(args.graph),
                "l2": "flushed between steps (256 MiB write outside the timed events)",
-               "parallelism": "replicas" if world > 1 else "single"}
+               "parallelism": "replicas" if world > 1 else "single",
+               "autotune": None if args.no_autotune else "every compiled launch configuration timed (3 reps, "
+                                                          "warm L2) before warm-up; %.2f s" % tune_s}
         if args.workload == "hex":
             cfg.update({"mesh": "%d^3 hex, interior vertices perturbed U[-0.1h,0.1h], seed 1" % args.nx,
                         "quadrature": "p+1 Gauss points per direction", "geometry": "stored FP64 G per point",
@@ -442,7 +475,9 @@ def gpu_arm(args, world, rank, local):
         line = {
             "metric": "operator-action GDoF/s", "value": value, "unit": "GDoF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "scaling": "weak", "vs_baseline": None, "data": "synthetic", "config": cfg,
+            "dtype": {"fp64": "f64", "fp32": "f32 (FP64 vectors)", "bf16": "bf16 operands, f32 accumulation"}[
+                args.precision if args.workload == "hex" else "fp64"],
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches_per_step * args.steps, "wall_s_timed_region": t_wall, "per_operator": per_op,
         }

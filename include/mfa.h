@@ -92,7 +92,8 @@ typedef struct {
                               Tet: degree of the rule (default 2p; hyperelastic 4).     */
   int32_t precision;       /* MFA_PREC_*                                               */
   int32_t scatter;         /* MFA_SCATTER_*                                            */
-  int32_t cells_per_block; /* 0 = automatic                                            */
+  int32_t cells_per_block; /* 0 = automatic; else one of the default variant's choices
+                              (mfa_form_list_configs), MFA_ERR_UNSUPPORTED otherwise   */
   double k2;               /* Helmholtz coefficient (paper: 1)                          */
   double lambda, mu;       /* Lame parameters (elasticity, hyperelasticity)             */
   double b[3];             /* body force of the hyperelastic residual                   */
@@ -104,9 +105,13 @@ typedef struct {
   int32_t nq;              /* quadrature points per cell used by the kernel              */
   int32_t ncolours;        /* colours of the deterministic scatter (0 if not built)     */
   int32_t scatter;         /* scatter actually used                                      */
-  double flops;            /* algorithmic FP operations of one apply                     */
+  double flops;            /* algorithmic FP operations of one apply (hex: collocation sum
+                              factorisation, 24 n^4 + pointwise physics per cell)       */
   double bytes;            /* algorithmic DRAM bytes of one apply                        */
   double setup_ms;         /* host+device time spent in mfa_form_create                  */
+  double flops_executed;   /* FP operations the selected kernel executes: below `flops` for the
+                              even-odd hex variant, which forms the 1D products from half-size
+                              even and odd parts; equal to `flops` otherwise                */
 } mfa_form_info;
 
 typedef struct mfa_ctx mfa_ctx;
@@ -149,6 +154,65 @@ MFA_API int mfa_form_create(mfa_ctx *ctx, mfa_space *space, const mfa_form_param
 MFA_API int mfa_form_set_coefficient(mfa_form *form, const double *u);
 MFA_API int mfa_form_get_info(const mfa_form *form, mfa_form_info *info);
 MFA_API int mfa_form_destroy(mfa_form *form);
+
+/* Launch configuration of a form and its autotuner.  The paper picks its
+ * batch size (cells per SIMD vector) by the hardware's vector width
+ * (Section 4.1); on the GPU the thread-to-data mapping, the number of cells a
+ * thread block processes together and the scatter mode have no single best
+ * value across degrees and forms, so they are chosen per form by timing.
+ * Every configuration computes the same operator: the kernels differ only in
+ * how the work is split, so results agree to rounding (bitwise for the same
+ * variant and cells per block with the colour scatter).
+ *  - variant: MFA_VARIANT_POINT  one thread per tensor point, a slab of n^3
+ *                                threads per hex cell (FP64);
+ *             MFA_VARIANT_EVEN_ODD one thread per 1D line with even-odd split
+ *                                1D products (FP64 hex, n = p+1 = 5..9, p+1 points);
+ *             MFA_VARIANT_LINE   one thread per 1D line, geometric factors read
+ *                                from global memory (FP32/BF16 hex);
+ *             MFA_VARIANT_LINE_STAGED as LINE with the factors staged in shared
+ *                                memory by bulk copies (FP32/BF16 hex);
+ *             MFA_VARIANT_CELL   one thread per cell (tets).
+ *  - cells_per_block: cells one thread block processes together (tets:
+ *    threads per block); 0 in mfa_form_set_config = the variant's default.
+ *  - scatter: MFA_SCATTER_ATOMIC or MFA_SCATTER_COLOUR (FP64 only).
+ *  - ms: mean time of one apply measured by mfa_form_autotune (else 0). */
+enum {
+  MFA_VARIANT_AUTO = 0,
+  MFA_VARIANT_POINT = 1,
+  MFA_VARIANT_EVEN_ODD = 2,
+  MFA_VARIANT_LINE = 3,
+  MFA_VARIANT_LINE_STAGED = 4,
+  MFA_VARIANT_CELL = 5
+};
+typedef struct {
+  int32_t variant;
+  int32_t cells_per_block;
+  int32_t scatter;
+  int32_t reserved;        /* 0 */
+  double ms;
+} mfa_launch_config;
+
+/* All configurations the library has compiled for this form (the default
+ * first).  Writes min(count, max) entries to `out` (may be NULL when max = 0)
+ * and the full count to *count. */
+MFA_API int mfa_form_list_configs(const mfa_form *form, mfa_launch_config *out, int max, int *count);
+/* The configuration mfa_apply uses for this form. */
+MFA_API int mfa_form_get_config(const mfa_form *form, mfa_launch_config *cfg);
+/* Select a configuration; MFA_ERR_UNSUPPORTED if it is not one of
+ * mfa_form_list_configs (MFA_VARIANT_AUTO selects the default).  Choosing the
+ * colour scatter builds the space's colouring on first use (host work and a
+ * device allocation). */
+MFA_API int mfa_form_set_config(mfa_form *form, const mfa_launch_config *cfg);
+/* Time every configuration of the form on the context stream (one untimed
+ * apply, then `reps` >= 1 timed applies each, CUDA events) with y = A x on
+ * the caller's device vectors x and y (y is overwritten), then select the
+ * fastest.  `tried` receives min(count, max_tried) entries with their times,
+ * in mfa_form_list_configs order (may be NULL when max_tried = 0); *ntried
+ * the count.  Synchronises the context stream; do not call during stream
+ * capture.  A configuration whose launch fails is reported with ms = -1 and
+ * skipped; MFA_ERR_CUDA if all fail. */
+MFA_API int mfa_form_autotune(mfa_ctx *ctx, mfa_form *form, const double *x, double *y, int reps,
+                              mfa_launch_config *tried, int max_tried, int *ntried);
 
 /* y = A(x) (accumulate = 0) or y += A(x) (accumulate = 1).  x, y: device,
  * ndof FP64 entries, must not overlap.  Asynchronous on the context stream.

@@ -25,6 +25,9 @@ MFA_PREC_FP64, MFA_PREC_FP32, MFA_PREC_BF16 = 0, 1, 2
 MFA_SCATTER_AUTO, MFA_SCATTER_COLOUR, MFA_SCATTER_ATOMIC = 0, 1, 2
 MFA_PC_NONE, MFA_PC_JACOBI = 0, 1
 MFA_PRECOND_MLP, MFA_PRECOND_LINEAR = 0, 1
+(MFA_VARIANT_AUTO, MFA_VARIANT_POINT, MFA_VARIANT_EVEN_ODD, MFA_VARIANT_LINE, MFA_VARIANT_LINE_STAGED,
+ MFA_VARIANT_CELL) = 0, 1, 2, 3, 4, 5
+VARIANT_NAMES = {1: "point", 2: "even-odd", 3: "line", 4: "line-staged", 5: "cell"}
 
 
 class MfaError(RuntimeError):
@@ -59,7 +62,22 @@ class mfa_form_info(ctypes.Structure):
         ("flops", ctypes.c_double),
         ("bytes", ctypes.c_double),
         ("setup_ms", ctypes.c_double),
+        ("flops_executed", ctypes.c_double),
     ]
+
+
+class mfa_launch_config(ctypes.Structure):
+    _fields_ = [
+        ("variant", ctypes.c_int32),
+        ("cells_per_block", ctypes.c_int32),
+        ("scatter", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {"variant": VARIANT_NAMES.get(self.variant, self.variant), "cells_per_block": self.cells_per_block,
+                "scatter": "colour" if self.scatter == MFA_SCATTER_COLOUR else "atomic", "ms": self.ms}
 
 
 _lib = None
@@ -80,6 +98,10 @@ _SIGS = {
     "mfa_form_set_coefficient": ([_VP, _VP], _I),
     "mfa_form_get_info": ([_VP, ctypes.POINTER(mfa_form_info)], _I),
     "mfa_form_destroy": ([_VP], _I),
+    "mfa_form_list_configs": ([_VP, _VP, _I, ctypes.POINTER(_I)], _I),
+    "mfa_form_get_config": ([_VP, ctypes.POINTER(mfa_launch_config)], _I),
+    "mfa_form_set_config": ([_VP, ctypes.POINTER(mfa_launch_config)], _I),
+    "mfa_form_autotune": ([_VP, _VP, _VP, _VP, _I, _VP, _I, ctypes.POINTER(_I)], _I),
     "mfa_apply": ([_VP, _VP, _VP, _VP, _I], _I),
     "mfa_apply_host": ([_VP, _VP, _VP, _VP], _I),
     "mfa_apply_f32": ([_VP, _VP, _VP, _VP, _I], _I),
@@ -215,6 +237,33 @@ def mfa_form_get_info(form):
 
 def mfa_form_destroy(form):
     _check(lib().mfa_form_destroy(form))
+
+
+def mfa_form_list_configs(form):
+    n = ctypes.c_int()
+    _check(lib().mfa_form_list_configs(form, None, 0, ctypes.byref(n)))
+    arr = (mfa_launch_config * max(n.value, 1))()
+    _check(lib().mfa_form_list_configs(form, arr, n.value, ctypes.byref(n)))
+    return [arr[i] for i in range(n.value)]
+
+
+def mfa_form_get_config(form):
+    c = mfa_launch_config()
+    _check(lib().mfa_form_get_config(form, ctypes.byref(c)))
+    return c
+
+
+def mfa_form_set_config(form, cfg):
+    _check(lib().mfa_form_set_config(form, ctypes.byref(cfg)))
+
+
+def mfa_form_autotune(ctx, form, x, y, reps=3):
+    """Time every configuration, keep the fastest; returns the list with times."""
+    n = ctypes.c_int()
+    _check(lib().mfa_form_list_configs(form, None, 0, ctypes.byref(n)))
+    arr = (mfa_launch_config * max(n.value, 1))()
+    _check(lib().mfa_form_autotune(ctx, form, _ptr(x), _ptr(y), reps, arr, n.value, ctypes.byref(n)))
+    return [arr[i] for i in range(n.value)]
 
 
 def mfa_apply(ctx, form, x, y, accumulate=False):
@@ -436,9 +485,10 @@ class Space:
 
 
 def form_params(kind, law=MFA_LAW_SVK, qdeg=0, precision=MFA_PREC_FP64, scatter=MFA_SCATTER_AUTO, k2=1.0,
-                lam=1.0, mu=1.0, b=(0.0, 0.0, 0.0)):
+                lam=1.0, mu=1.0, b=(0.0, 0.0, 0.0), cells_per_block=0):
     p = mfa_form_params()
-    p.kind, p.law, p.qdeg, p.precision, p.scatter, p.cells_per_block = kind, law, qdeg, precision, scatter, 0
+    p.kind, p.law, p.qdeg, p.precision, p.scatter = kind, law, qdeg, precision, scatter
+    p.cells_per_block = cells_per_block
     p.k2, p.lam, p.mu = k2, lam, mu
     p.b[0], p.b[1], p.b[2] = b
     return p
@@ -454,6 +504,18 @@ class Form:
 
     def info(self):
         return mfa_form_get_info(self.h)
+
+    def configs(self):
+        return mfa_form_list_configs(self.h)
+
+    def config(self):
+        return mfa_form_get_config(self.h)
+
+    def set_config(self, cfg):
+        mfa_form_set_config(self.h, cfg)
+
+    def autotune(self, x, y, reps=3):
+        return mfa_form_autotune(self.ctx.h, self.h, x, y, reps)
 
     def set_coefficient(self, u):
         self._coef = u  # keep the borrowed buffer alive

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "mfa_internal.h"
@@ -62,7 +63,8 @@ void count_work(mfa_form* f) {
   const int64_t ndof = sp->nnode * sp->ncomp;
   const int kind = f->p.kind;
   double per_cell = 0.0, bytes = 0.0;
-  if (sp->mesh->cell_type == MFA_CELL_HEX8 && mfa::hex_use_eo(sp->degree + 1, f->nq1, f->p.precision)) {
+  double exec_cell = -1.0;  // operations the kernel executes, where fewer than the algorithmic count
+  if (sp->mesh->cell_type == MFA_CELL_HEX8 && f->launch.variant == MFA_VARIANT_EVEN_ODD) {
     // even-odd line products: per line, forming e/o (2h adds), then per mirror pair of outputs
     // (odd: one multiply) + 2h FMA + 2 adds, and for odd n a middle output
     const int n = sp->degree + 1, h = n / 2, odd = n & 1;
@@ -72,11 +74,13 @@ void count_work(mfa_form* f) {
       return f_ + (acc ? n : 0);
     };
     const double L = (double)n * n, P = (double)n * n * n;
-    per_cell = L * 6.0 * line(1, 0) + P;  // B, B^T and the scatter adds
-    if (kind != MFA_FORM_MASS) per_cell += L * (3.0 * line(-1, 0) + 3.0 * line(-1, 1)) + 15.0 * P;  // D, D^T, G g
-    if (kind != MFA_FORM_LAPLACE) per_cell += P;  // c0 w|J| u
-    bytes = ncell * (4.0 * P + 8.0 * mfa::hex_geom_entries(kind) * P);
-  } else if (sp->mesh->cell_type == MFA_CELL_HEX8) {
+    exec_cell = L * 6.0 * line(1, 0) + P;  // B, B^T and the scatter adds
+    if (kind != MFA_FORM_MASS) exec_cell += L * (3.0 * line(-1, 0) + 3.0 * line(-1, 1)) + 15.0 * P;  // D, D^T, G g
+    if (kind != MFA_FORM_LAPLACE) exec_cell += P;  // c0 w|J| u
+  }
+  if (sp->mesh->cell_type == MFA_CELL_HEX8) {
+    // algorithmic count of collocation sum factorisation, whatever the kernel variant:
+    // 24 n^4 for n = nq (B, B^T, D, D^T sweeps) + pointwise physics + scatter adds
     const double n = sp->degree + 1, q = f->nq1;
     const double sweeps = 2.0 * (q * n * n * n + q * q * n * n + q * q * q * n);  // one direction set
     per_cell = 2.0 * sweeps + n * n * n;                                            // B, B^T and the scatter add
@@ -114,6 +118,7 @@ void count_work(mfa_form* f) {
   bytes += 16.0 * ndof;  // x read once, y written once
   if (f->scatter == MFA_SCATTER_COLOUR) bytes += 4.0 * ncell;
   f->flops = per_cell * ncell;
+  f->flops_executed = (exec_cell >= 0.0 ? exec_cell : per_cell) * ncell;
   f->bytes = bytes;
 }
 
@@ -234,14 +239,14 @@ int apply_form(mfa_form* f, const double* x, double* y, cudaStream_t stream) {
     cudaError_t e;
     if (sp->mesh->cell_type == MFA_CELL_HEX8) {
       mfa::HexApplyArgs a{x, y, sp->d_cell_node, f->d_geom, list, count, ctx->d_err, f->gstride};
-      e = mfa::hex_apply_launch(sp->degree + 1, f->nq1, f->p.kind, f->p.precision, colour, f->hex, a, ctx->sm_count,
-                                stream);
+      e = mfa::hex_apply_launch(sp->degree + 1, f->nq1, f->p.kind, f->p.precision, colour, f->launch, f->hex, a,
+                                ctx->sm_count, stream);
     } else {
       mfa::TetApplyArgs a = tet_args(f, x, y);
       a.cell_list = list;
       a.count = count;
-      e = mfa::tet_apply_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, f->tet, a, ctx->sm_count,
-                                stream);
+      e = mfa::tet_apply_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, f->launch.cb ? f->launch.cb : 128,
+                                f->tet, a, ctx->sm_count, stream);
     }
     if (e != cudaSuccess) return fail(MFA_ERR_CUDA, "apply kernel launch: %s", cudaGetErrorString(e));
   }
@@ -394,6 +399,54 @@ int mfa_space_destroy(mfa_space* s) {
   return MFA_OK;
 }
 
+// Compiled cells-per-block choices of `variant` for this form (default first).
+static int cb_options(const mfa_form* f, int variant, int* out) {
+  const mfa_space* sp = f->space;
+  const int n = sp->degree + 1, nq = f->p.qdeg > 0 ? f->p.qdeg : n;
+  if (sp->mesh->cell_type != MFA_CELL_HEX8) return variant == MFA_VARIANT_CELL ? mfa::tet_cb_options(out) : 0;
+  if (f->p.precision == MFA_PREC_FP64) {
+    if (variant == MFA_VARIANT_POINT) return mfa::hex_point_cb_options(n, nq, out);
+    if (variant == MFA_VARIANT_EVEN_ODD) return nq == n ? mfa::hex_eo_cb_options(n, out) : 0;
+    return 0;
+  }
+  if (variant == MFA_VARIANT_LINE || variant == MFA_VARIANT_LINE_STAGED) return mfa::hex_line_cb_options(n, out);
+  return 0;
+}
+
+// Every compiled configuration of the form: the creation-time one first, then
+// variant by variant, cells per block in option order, atomic before colour.
+static std::vector<mfa_launch_config> form_configs(const mfa_form* f) {
+  std::vector<mfa_launch_config> all;
+  const bool hex = f->space->mesh->cell_type == MFA_CELL_HEX8;
+  std::vector<int> variants;
+  if (!hex) variants = {MFA_VARIANT_CELL};
+  else if (f->p.precision == MFA_PREC_FP64) variants = {MFA_VARIANT_POINT, MFA_VARIANT_EVEN_ODD};
+  else variants = {MFA_VARIANT_LINE, MFA_VARIANT_LINE_STAGED};
+  const bool colour_ok = f->p.precision == MFA_PREC_FP64;
+  for (int v : variants) {
+    int opts[4];
+    const int nopt = cb_options(f, v, opts);
+    for (int i = 0; i < nopt; ++i)
+      for (int sc = 0; sc < (colour_ok ? 2 : 1); ++sc) {
+        mfa_launch_config c{};
+        c.variant = v;
+        c.cells_per_block = opts[i];
+        c.scatter = sc == 0 ? MFA_SCATTER_ATOMIC : MFA_SCATTER_COLOUR;
+        all.push_back(c);
+      }
+  }
+  // move the creation-time configuration to the front
+  int dopts[4];
+  const int dn = cb_options(f, f->launch.variant, dopts);
+  const int dcb = f->launch.cb ? f->launch.cb : (dn > 0 ? dopts[0] : 0);
+  for (size_t i = 0; i < all.size(); ++i)
+    if (all[i].variant == f->launch.variant && all[i].cells_per_block == dcb && all[i].scatter == f->scatter) {
+      std::rotate(all.begin(), all.begin() + i, all.begin() + i + 1);
+      break;
+    }
+  return all;
+}
+
 int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa_form** out) {
   if (!ctx || !sp || !prm || !out) return fail(MFA_ERR_ARG, "mfa_form_create: NULL argument");
   *out = nullptr;
@@ -426,8 +479,21 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
   f->space = sp;
   f->p = *prm;
   f->scatter = prm->scatter == MFA_SCATTER_COLOUR ? MFA_SCATTER_COLOUR : MFA_SCATTER_ATOMIC;
+  f->launch.variant = ct == MFA_CELL_HEX8 ? mfa::hex_default_variant(sp->degree + 1, prm->qdeg > 0 ? prm->qdeg : sp->degree + 1,
+                                                                     prm->precision)
+                                          : MFA_VARIANT_CELL;
   int rc = MFA_OK;
-  if (ct == MFA_CELL_HEX8) {
+  if (prm->cells_per_block != 0) {
+    int opts[4];
+    const int nopt = cb_options(f, f->launch.variant, opts);
+    bool found = false;
+    for (int i = 0; i < nopt; ++i) found = found || opts[i] == prm->cells_per_block;
+    if (!found)
+      rc = fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: %d cells per block is not compiled for this form",
+                prm->cells_per_block);
+    f->launch.cb = prm->cells_per_block;
+  }
+  if (!rc && ct == MFA_CELL_HEX8) {
     const int n = sp->degree + 1;
     f->nq1 = prm->qdeg > 0 ? prm->qdeg : n;
     if (!(f->nq1 == n || (f->nq1 == n + 1 && n <= 7)) || n > 9)
@@ -450,7 +516,7 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
       }
       if (!rc) rc = mfa_sync(ctx);
     }
-  } else {
+  } else if (!rc) {
     rc = tet_tables(f);
   }
   if (!rc && f->scatter == MFA_SCATTER_COLOUR) rc = build_colouring(sp);
@@ -479,9 +545,124 @@ int mfa_form_get_info(const mfa_form* f, mfa_form_info* info) {
   info->ncolours = f->space->ncolours;
   info->scatter = f->scatter;
   info->flops = f->flops;
+  info->flops_executed = f->flops_executed;
   info->bytes = f->bytes;
   info->setup_ms = f->setup_ms;
   return MFA_OK;
+}
+
+int mfa_form_list_configs(const mfa_form* f, mfa_launch_config* out, int max, int* count) {
+  if (!f || !count || max < 0 || (max > 0 && !out)) return fail(MFA_ERR_ARG, "mfa_form_list_configs: bad argument");
+  const std::vector<mfa_launch_config> all = form_configs(f);
+  for (int i = 0; i < max && i < (int)all.size(); ++i) out[i] = all[i];
+  *count = (int)all.size();
+  return MFA_OK;
+}
+
+int mfa_form_get_config(const mfa_form* f, mfa_launch_config* cfg) {
+  if (!f || !cfg) return fail(MFA_ERR_ARG, "mfa_form_get_config: NULL argument");
+  int opts[4];
+  const int nopt = cb_options(f, f->launch.variant, opts);
+  *cfg = mfa_launch_config{};
+  cfg->variant = f->launch.variant;
+  cfg->cells_per_block = f->launch.cb ? f->launch.cb : (nopt > 0 ? opts[0] : 0);
+  cfg->scatter = f->scatter;
+  cfg->ms = f->tuned_ms;
+  return MFA_OK;
+}
+
+int mfa_form_set_config(mfa_form* f, const mfa_launch_config* cfg) {
+  if (!f || !cfg) return fail(MFA_ERR_ARG, "mfa_form_set_config: NULL argument");
+  mfa_launch_config want = *cfg;
+  const mfa_space* sp = f->space;
+  if (want.variant == MFA_VARIANT_AUTO)
+    want.variant = sp->mesh->cell_type == MFA_CELL_HEX8
+                       ? mfa::hex_default_variant(sp->degree + 1, f->nq1, f->p.precision)
+                       : MFA_VARIANT_CELL;
+  if (want.cells_per_block == 0) {
+    int opts[4];
+    if (cb_options(f, want.variant, opts) > 0) want.cells_per_block = opts[0];
+  }
+  bool found = false;
+  for (const mfa_launch_config& c : form_configs(f))
+    found = found || (c.variant == want.variant && c.cells_per_block == want.cells_per_block && c.scatter == want.scatter);
+  if (!found)
+    return fail(MFA_ERR_UNSUPPORTED, "mfa_form_set_config: variant %d, %d cells per block, scatter %d not compiled",
+                want.variant, want.cells_per_block, want.scatter);
+  if (want.scatter == MFA_SCATTER_COLOUR) {
+    int rc = build_colouring(f->space);
+    if (rc) return rc;
+  }
+  f->launch.variant = want.variant;
+  f->launch.cb = want.cells_per_block;
+  f->scatter = want.scatter;
+  f->tuned_ms = 0.0;
+  count_work(f);
+  return MFA_OK;
+}
+
+int mfa_form_autotune(mfa_ctx* ctx, mfa_form* f, const double* x, double* y, int reps, mfa_launch_config* tried,
+                      int max_tried, int* ntried) {
+  if (!ctx || !f || !x || !y || !ntried || reps < 1 || max_tried < 0 || (max_tried > 0 && !tried))
+    return fail(MFA_ERR_ARG, "mfa_form_autotune: bad argument");
+  if (f->ctx != ctx) return fail(MFA_ERR_ARG, "mfa_form_autotune: form belongs to another context");
+  if ((const void*)x == (const void*)y) return fail(MFA_ERR_ARG, "mfa_form_autotune: x and y alias");
+  if (f->p.kind == MFA_FORM_HYPER_JAC && !f->d_coef)
+    return fail(MFA_ERR_ARG, "mfa_form_autotune: HYPER_JAC needs mfa_form_set_coefficient");
+  MFA_CUDA(cudaSetDevice(ctx->device));
+  std::vector<mfa_launch_config> all = form_configs(f);
+  const mfa::LaunchConfig keep_launch = f->launch;
+  const int keep_scatter = f->scatter;
+  cudaEvent_t ev[2];
+  MFA_CUDA(cudaEventCreate(&ev[0]));
+  if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+    cudaEventDestroy(ev[0]);
+    return fail(MFA_ERR_CUDA, "mfa_form_autotune: cudaEventCreate");
+  }
+  int best = -1, rc = MFA_OK;
+  for (size_t i = 0; i < all.size() && rc == MFA_OK; ++i) {
+    mfa_launch_config& c = all[i];
+    c.ms = -1.0;
+    if (mfa_form_set_config(f, &c) != MFA_OK) continue;  // e.g. colouring needs more than 64 colours
+    // untimed first apply (first-use setup of the variant).  A refused launch
+    // leaves the context intact and skips the configuration; an error seen at
+    // the synchronisation (a device fault or a kernel's error flag) ends the
+    // tuning with that status.
+    int r = mfa_apply(ctx, f, x, y, 0);
+    int s = mfa_sync(ctx);
+    if (s != MFA_OK) {
+      rc = s;
+      break;
+    }
+    if (r != MFA_OK) continue;
+    cudaEventRecord(ev[0], ctx->stream);
+    for (int k = 0; k < reps && r == MFA_OK; ++k) r = mfa_apply(ctx, f, x, y, 0);
+    cudaEventRecord(ev[1], ctx->stream);
+    s = mfa_sync(ctx);
+    if (s != MFA_OK) {
+      rc = s;
+      break;
+    }
+    if (r != MFA_OK) continue;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) continue;
+    c.ms = ms / reps;
+    if (best < 0 || c.ms < all[best].ms) best = (int)i;
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  for (int i = 0; i < max_tried && i < (int)all.size(); ++i) tried[i] = all[i];
+  *ntried = (int)all.size();
+  if (rc == MFA_OK && best < 0) rc = fail(MFA_ERR_CUDA, "mfa_form_autotune: no configuration ran");
+  if (rc != MFA_OK) {
+    f->launch = keep_launch;
+    f->scatter = keep_scatter;
+    count_work(f);
+    return rc;
+  }
+  rc = mfa_form_set_config(f, &all[best]);
+  if (rc == MFA_OK) f->tuned_ms = all[best].ms;
+  return rc;
 }
 
 int mfa_form_destroy(mfa_form* f) {

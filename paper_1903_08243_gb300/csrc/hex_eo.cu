@@ -1,75 +1,10 @@
 // Instantiations and launchers of the even-odd FP64 hex action (hex_eo.cuh).
-#include <mutex>
-#include <vector>
-
 #include "hex_eo.cuh"
 
 namespace mfa {
 namespace {
 
 using namespace hexeo;
-
-std::mutex g_mutex;
-bool g_ready[64] = {false};
-
-// Split tables of B, B^T, D, D^T for n = 5..9 into this unit's constant bank.
-cudaError_t upload_tables() {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (g_ready[dev]) return cudaSuccess;
-  std::vector<double> tab(kTabDoubles, 0.0);
-  for (int n = 5; n <= 9; ++n) {
-    double gll[kMaxN], xg[kMaxN], wg[kMaxN], B[kMaxN * kMaxN], D[kMaxN * kMaxN];
-    gll01(n, gll);
-    gauss_legendre01(n, xg, wg);
-    lagrange_matrix(n, gll, n, xg, B);  // B[q][a]
-    collocation_derivative(n, xg, D);   // D[q][r]
-    const int h = n / 2;
-    for (int mat = 0; mat < 4; ++mat) {
-      auto S = [&](int i, int j) {
-        const double* M = mat < 2 ? B : D;
-        return (mat % 2 == 0) ? M[i * n + j] : M[j * n + i];  // odd mat: transpose
-      };
-      double* o = tab.data() + tab_offset(n, mat);
-      for (int i = 0; i < h; ++i)
-        for (int j = 0; j < h; ++j) {
-          o[i * h + j] = 0.5 * (S(i, j) + S(i, n - 1 - j));              // E
-          o[h * h + i * h + j] = 0.5 * (S(i, j) - S(i, n - 1 - j));      // O
-        }
-      if (n & 1) {
-        for (int i = 0; i < h; ++i) o[2 * h * h + i] = S(i, h);          // Mc
-        for (int j = 0; j <= h; ++j) o[2 * h * h + h + j] = S(h, j);     // Mr
-      }
-    }
-  }
-  e = cudaMemcpyToSymbol(c_eo, tab.data(), sizeof(double) * kTabDoubles);
-  if (e == cudaSuccess) g_ready[dev] = true;
-  return e;
-}
-
-template <typename Kern>
-int occupancy(Kern kern, int threads, int smem) {
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  int b = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem) != cudaSuccess || b < 1) b = 1;
-  return b;
-}
-
-template <int N, int KIND, bool COLOUR>
-cudaError_t launch(const HexApplyArgs& a, int sm_count, cudaStream_t s) {
-  using S = EShape<N>;
-  auto kern = eo_apply_kernel<N, KIND, COLOUR>;
-  static int bps = -1;
-  if (bps < 0) bps = occupancy(kern, S::T, S::SMEM);
-  const int64_t nbatch = (a.count + S::CB - 1) / S::CB;
-  if (nbatch == 0) return cudaSuccess;
-  const int64_t cap = (int64_t)sm_count * bps;
-  kern<<<(unsigned)(nbatch < cap ? nbatch : cap), S::T, S::SMEM, s>>>(a);
-  return cudaGetLastError();
-}
 
 template <int N, int KIND>
 cudaError_t launch_group(const HexApplyArgs* items, const int64_t* first, int nitems, int64_t total, int sm_count,
@@ -112,9 +47,15 @@ cudaError_t dispatch_group(int kind, const HexApplyArgs* items, const int64_t* f
 
 }  // namespace
 
-int hex_eo_cells_per_block(int n) {
-  const int l = n * n;
-  return 256 / l > 0 ? 256 / l : 1;  // hexeo::EShape<N>::CB
+int hex_eo_cells_per_block(int n) { return eo_cb_for(n, 256); }  // hexeo::EShape<N>::CB
+
+// Default (256-thread target), then 128- and 512-thread targets (hex_eo_tune.cu).
+int hex_eo_cb_options(int n, int* out) {
+  if (n < 5 || n > 9) return 0;
+  out[0] = eo_cb_for(n, 256);
+  out[1] = eo_cb_for(n, 128);
+  out[2] = eo_cb_for(n, 512);
+  return 3;
 }
 
 cudaError_t hex_eo_apply_launch(int n, int kind, bool colour, const HexApplyArgs& a, int sm_count, cudaStream_t s) {

@@ -20,6 +20,9 @@
 // gather, the geometric-factor reads and the scatter run point-parallel.
 #pragma once
 
+#include <mutex>
+#include <vector>
+
 #include "mfa_internal.h"
 
 namespace mfa {
@@ -40,11 +43,14 @@ static __constant__ double c_eo[kTabDoubles];
 
 constexpr int ceil32(int x) { return (x + 31) / 32 * 32; }
 
-template <int N>
+// Cells per block for a target block size (the default targets 256 threads).
+constexpr int eo_cb_for(int n, int target) { return cells_for_target(n * n, target); }
+
+template <int N, int CBX = 0>
 struct EShape {
   static constexpr int L = N * N;
   static constexpr int P = N * N * N;
-  static constexpr int CB = 256 / L > 0 ? 256 / L : 1;
+  static constexpr int CB = CBX > 0 ? CBX : eo_cb_for(N, 256);
   static constexpr int T = ceil32(CB * L);
   static constexpr int SMEM = 5 * CB * P * 8;
 };
@@ -105,9 +111,9 @@ __device__ __forceinline__ void eo_sweep(const double* in, double* out, int a, i
   }
 }
 
-template <int N, int KIND, bool COLOUR>
+template <int N, int KIND, bool COLOUR, int CBX = 0>
 __device__ __forceinline__ void eo_batch(const HexApplyArgs& a, int64_t batch, double* smem) {
-  using S = EShape<N>;
+  using S = EShape<N, CBX>;
   constexpr int L = S::L, P = S::P, CB = S::CB, T = S::T, NG = geom_entries<KIND>();
   const int t = threadIdx.x;
   const int cl = t / L, l = t - cl * L;
@@ -187,11 +193,13 @@ __device__ __forceinline__ void eo_batch(const HexApplyArgs& a, int64_t batch, d
   __syncthreads();
 }
 
-template <int N, int KIND, bool COLOUR>
-__global__ void __launch_bounds__(EShape<N>::T) eo_apply_kernel(const HexApplyArgs a) {
+template <int N, int KIND, bool COLOUR, int CBX = 0>
+__global__ void __launch_bounds__(EShape<N, CBX>::T) eo_apply_kernel(const HexApplyArgs a) {
   extern __shared__ __align__(16) double smem_eo[];
-  const int64_t nbatch = (a.count + EShape<N>::CB - 1) / EShape<N>::CB;
-  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) eo_batch<N, KIND, COLOUR>(a, batch, smem_eo);
+  constexpr int CB = EShape<N, CBX>::CB;
+  const int64_t nbatch = (a.count + CB - 1) / CB;
+  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x)
+    eo_batch<N, KIND, COLOUR, CBX>(a, batch, smem_eo);
 }
 
 template <int N, int KIND>
@@ -206,6 +214,72 @@ __global__ void __launch_bounds__(EShape<N>::T) eo_group_kernel(const HexApplyAr
     eo_batch<N, KIND, false>(h, gb - first[k], smem_eo);
   }
 }
+
+namespace {  // one copy per translation unit, like c_eo
+
+template <typename Kern>
+int occupancy(Kern kern, int threads, int smem) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int b = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem) != cudaSuccess || b < 1) b = 1;
+  return b;
+}
+
+template <int N, int KIND, bool COLOUR, int CBX = 0>
+cudaError_t launch(const HexApplyArgs& a, int sm_count, cudaStream_t s) {
+  using S = EShape<N, CBX>;
+  auto kern = eo_apply_kernel<N, KIND, COLOUR, CBX>;
+  static int bps = -1;
+  if (bps < 0) bps = occupancy(kern, S::T, S::SMEM);
+  const int64_t nbatch = (a.count + S::CB - 1) / S::CB;
+  if (nbatch == 0) return cudaSuccess;
+  const int64_t cap = (int64_t)sm_count * bps;
+  kern<<<(unsigned)(nbatch < cap ? nbatch : cap), S::T, S::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+std::mutex g_mutex;
+bool g_ready[64] = {false};
+
+// Split tables of B, B^T, D, D^T for n = 5..9 into this unit's constant bank.
+inline cudaError_t upload_tables() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (g_ready[dev]) return cudaSuccess;
+  std::vector<double> tab(kTabDoubles, 0.0);
+  for (int n = 5; n <= 9; ++n) {
+    double gll[kMaxN], xg[kMaxN], wg[kMaxN], B[kMaxN * kMaxN], D[kMaxN * kMaxN];
+    gll01(n, gll);
+    gauss_legendre01(n, xg, wg);
+    lagrange_matrix(n, gll, n, xg, B);  // B[q][a]
+    collocation_derivative(n, xg, D);   // D[q][r]
+    const int h = n / 2;
+    for (int mat = 0; mat < 4; ++mat) {
+      auto S = [&](int i, int j) {
+        const double* M = mat < 2 ? B : D;
+        return (mat % 2 == 0) ? M[i * n + j] : M[j * n + i];  // odd mat: transpose
+      };
+      double* o = tab.data() + tab_offset(n, mat);
+      for (int i = 0; i < h; ++i)
+        for (int j = 0; j < h; ++j) {
+          o[i * h + j] = 0.5 * (S(i, j) + S(i, n - 1 - j));              // E
+          o[h * h + i * h + j] = 0.5 * (S(i, j) - S(i, n - 1 - j));      // O
+        }
+      if (n & 1) {
+        for (int i = 0; i < h; ++i) o[2 * h * h + i] = S(i, h);          // Mc
+        for (int j = 0; j <= h; ++j) o[2 * h * h + h + j] = S(h, j);     // Mr
+      }
+    }
+  }
+  e = cudaMemcpyToSymbol(c_eo, tab.data(), sizeof(double) * kTabDoubles);
+  if (e == cudaSuccess) g_ready[dev] = true;
+  return e;
+}
+
+}  // namespace
 
 }  // namespace hexeo
 }  // namespace mfa

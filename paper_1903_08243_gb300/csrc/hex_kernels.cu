@@ -119,10 +119,37 @@ cudaError_t hex_geometry_launch(int nq, int kind, int prec, double c0, const Hex
   return cudaGetLastError();
 }
 
-cudaError_t hex_apply_launch(int n, int nq, int kind, int prec, bool colour, const HexTables& tb,
-                             const HexApplyArgs& a, int sm_count, cudaStream_t s) {
-  if (prec != MFA_PREC_FP64) return hex_apply_launch_mixed(n, nq, kind, prec, colour, tb, a, sm_count, s);
-  if (hex_use_eo(n, nq, prec)) return hex_eo_apply_launch(n, kind, colour, a, sm_count, s);
+int hex_default_variant(int n, int nq, int prec) {
+  if (prec == MFA_PREC_BF16) return MFA_VARIANT_LINE_STAGED;
+  if (prec == MFA_PREC_FP32) return MFA_VARIANT_LINE;
+  return hex_use_eo(n, nq, prec) ? MFA_VARIANT_EVEN_ODD : MFA_VARIANT_POINT;
+}
+
+// Default, then half and double the default where the block stays within 512
+// threads (hex_kernels_tune.cu instantiates the extra ones, p+1 points only).
+int hex_point_cb_options(int n, int nq, int* out) {
+  const int m = n > nq ? n : nq, p = m * m * m;
+  const int cb0 = hex_cells_per_block(n, nq);
+  int k = 0;
+  out[k++] = cb0;
+  if (nq != n || n > 6) return k;
+  if (cb0 / 2 >= 1 && cb0 / 2 != cb0) out[k++] = cb0 / 2;
+  if (2 * cb0 * p <= 512) out[k++] = 2 * cb0;
+  return k;
+}
+
+cudaError_t hex_apply_launch(int n, int nq, int kind, int prec, bool colour, const LaunchConfig& lc,
+                             const HexTables& tb, const HexApplyArgs& a, int sm_count, cudaStream_t s) {
+  if (prec != MFA_PREC_FP64) return hex_apply_launch_mixed(n, nq, kind, prec, colour, lc, tb, a, sm_count, s);
+  const int variant = lc.variant == MFA_VARIANT_AUTO ? hex_default_variant(n, nq, prec) : lc.variant;
+  if (variant == MFA_VARIANT_EVEN_ODD) {
+    if (nq != n || n < 5 || n > 9) return cudaErrorInvalidValue;
+    if (lc.cb == 0 || lc.cb == hex_eo_cells_per_block(n)) return hex_eo_apply_launch(n, kind, colour, a, sm_count, s);
+    return hex_eo_apply_launch_cb(n, kind, colour, lc.cb, a, sm_count, s);
+  }
+  if (variant != MFA_VARIANT_POINT) return cudaErrorInvalidValue;
+  if (lc.cb != 0 && lc.cb != hex_cells_per_block(n, nq))
+    return hex_point_launch_cb(n, nq, kind, colour, lc.cb, tb, a, sm_count, s);
   using namespace hexk;
   MFA_HEX_KIND_CASES(2, 2, MFA_PREC_FP64)
   MFA_HEX_KIND_CASES(3, 3, MFA_PREC_FP64)

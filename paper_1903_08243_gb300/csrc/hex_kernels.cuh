@@ -62,13 +62,15 @@ struct Prec<MFA_PREC_BF16> {
 
 constexpr int ceil32(int x) { return (x + 31) / 32 * 32; }
 
-template <int N, int NQ, int ELEM = 8>
+// CBX > 0 overrides the default number of cells per block (autotuner choices).
+template <int N, int NQ, int ELEM = 8, int CBX = 0>
 struct Shape {
   static constexpr int PN = N * N * N;
   static constexpr int PQ = NQ * NQ * NQ;
   static constexpr int M = N > NQ ? N : NQ;
   static constexpr int P = M * M * M;
-  static constexpr int CB = P <= 128 ? 256 / P : 1;  // cells per block
+  static constexpr int CB0 = P <= 128 ? 256 / P : 1;  // default cells per block
+  static constexpr int CB = CBX > 0 ? CBX : CB0;      // cells per block
   static constexpr int T = ceil32(CB * P);           // threads per block
   static constexpr int SMEM = (NQ * N + NQ * NQ + 2 * CB * P + 3 * CB * PQ) * ELEM;
 };
@@ -79,9 +81,9 @@ __host__ __device__ constexpr int geom_entries() {
 }
 
 // Shared-memory working set of one block (types by precision).
-template <int N, int NQ, int PREC>
+template <int N, int NQ, int PREC, int CBX = 0>
 struct Smem {
-  using S = Shape<N, NQ>;
+  using S = Shape<N, NQ, 8, CBX>;
   using T = typename Prec<PREC>::T;
   T* sB;  // [NQ][N]
   T* sD;  // [NQ][NQ]
@@ -114,9 +116,10 @@ struct Smem {
 
 // One batch of CB cells of one form: gather, sum-factorised local kernel,
 // scatter.  Every thread of the block calls it (it contains barriers).
-template <int N, int NQ, int KIND, bool COLOUR, int PREC>
-__device__ __forceinline__ void hex_cell_batch(const HexApplyArgs& a, int64_t batch, const Smem<N, NQ, PREC>& sm) {
-  using S = Shape<N, NQ>;
+template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0>
+__device__ __forceinline__ void hex_cell_batch(const HexApplyArgs& a, int64_t batch,
+                                               const Smem<N, NQ, PREC, CBX>& sm) {
+  using S = Shape<N, NQ, 8, CBX>;
   using T = typename Prec<PREC>::T;
   using TG = typename Prec<PREC>::TG;
   constexpr int PN = S::PN, PQ = S::PQ, CB = S::CB;
@@ -246,14 +249,16 @@ __device__ __forceinline__ void hex_cell_batch(const HexApplyArgs& a, int64_t ba
   }
 }
 
-template <int N, int NQ, int KIND, bool COLOUR, int PREC>
-__global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_kernel(const __grid_constant__ HexTables tb,
-                                                                    const HexApplyArgs a) {
+template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0>
+__global__ void __launch_bounds__(Shape<N, NQ, 8, CBX>::T) hex_apply_kernel(const __grid_constant__ HexTables tb,
+                                                                           const HexApplyArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<N, NQ, PREC> sm;
+  Smem<N, NQ, PREC, CBX> sm;
   sm.init(smem_raw, tb);
-  const int64_t nbatch = (a.count + Shape<N, NQ>::CB - 1) / Shape<N, NQ>::CB;
-  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) hex_cell_batch<N, NQ, KIND, COLOUR, PREC>(a, batch, sm);
+  constexpr int CB = Shape<N, NQ, 8, CBX>::CB;
+  const int64_t nbatch = (a.count + CB - 1) / CB;
+  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x)
+    hex_cell_batch<N, NQ, KIND, COLOUR, PREC, CBX>(a, batch, sm);
 }
 
 // Many forms of one (n, nq, kind, precision) class in one persistent launch:
@@ -276,10 +281,10 @@ __global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_group_kernel(const 
   }
 }
 
-template <int N, int NQ, int KIND, bool COLOUR, int PREC>
+template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0>
 cudaError_t launch_apply(const HexTables& tb, const HexApplyArgs& a, int sm_count, cudaStream_t s) {
-  using S = Shape<N, NQ, (int)sizeof(typename Prec<PREC>::T)>;
-  auto kern = hex_apply_kernel<N, NQ, KIND, COLOUR, PREC>;
+  using S = Shape<N, NQ, (int)sizeof(typename Prec<PREC>::T), CBX>;
+  auto kern = hex_apply_kernel<N, NQ, KIND, COLOUR, PREC, CBX>;
   static int blocks_per_sm = -1;
   if (blocks_per_sm < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
@@ -341,6 +346,24 @@ cudaError_t launch_group(const HexTables& tb, const HexApplyArgs* items, const i
       case MFA_FORM_HELMHOLTZ:                                                                         \
         return colour ? launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, true, PREC>(tb, a, sm_count, s)      \
                       : launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, false, PREC>(tb, a, sm_count, s);    \
+      default:                                                                                         \
+        return cudaErrorInvalidValue;                                                                  \
+    }                                                                                                  \
+  }
+
+// Same, for an explicit number of cells per block CBB (autotuner choices).
+#define MFA_HEX_KIND_CASES_CB(NN, NQQ, CBB, PREC)                                                     \
+  if (n == NN && nq == NQQ && cb == CBB) {                                                             \
+    switch (kind) {                                                                                    \
+      case MFA_FORM_MASS:                                                                              \
+        return colour ? launch_apply<NN, NQQ, MFA_FORM_MASS, true, PREC, CBB>(tb, a, sm_count, s)      \
+                      : launch_apply<NN, NQQ, MFA_FORM_MASS, false, PREC, CBB>(tb, a, sm_count, s);    \
+      case MFA_FORM_LAPLACE:                                                                           \
+        return colour ? launch_apply<NN, NQQ, MFA_FORM_LAPLACE, true, PREC, CBB>(tb, a, sm_count, s)   \
+                      : launch_apply<NN, NQQ, MFA_FORM_LAPLACE, false, PREC, CBB>(tb, a, sm_count, s); \
+      case MFA_FORM_HELMHOLTZ:                                                                         \
+        return colour ? launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, true, PREC, CBB>(tb, a, sm_count, s) \
+                      : launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, false, PREC, CBB>(tb, a, sm_count, s); \
       default:                                                                                         \
         return cudaErrorInvalidValue;                                                                  \
     }                                                                                                  \

@@ -25,7 +25,9 @@
 
 #include <cuda_bf16.h>
 
+#include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "convert.cuh"
 #include "mfa_internal.h"
@@ -45,11 +47,14 @@ static __constant__ float c_tab[2][kTabFloats];  // [0]: FP32 tables, [1]: table
 
 constexpr int ceil32(int x) { return (x + 31) / 32 * 32; }
 
-template <int N>
+// Cells per block for a target block size (the default targets 256 threads).
+constexpr int line_cb_for(int n, int target) { return cells_for_target(n * n, target); }
+
+template <int N, int CBX = 0>
 struct LShape {
   static constexpr int L = N * N;         // lines per cell and direction
   static constexpr int P = N * N * N;     // points per cell
-  static constexpr int CB = 256 / L > 0 ? 256 / L : 1;
+  static constexpr int CB = CBX > 0 ? CBX : line_cb_for(N, 256);
   static constexpr int T = ceil32(CB * L);
   static constexpr int SMEM = 5 * CB * P * 4;
 };
@@ -159,10 +164,12 @@ struct LineArgs {
 template <int PREC>
 using GeoT = typename std::conditional<PREC == MFA_PREC_BF16, __nv_bfloat16, float>::type;
 
-template <int PREC>
+// Factor i of a batch: `p` is the shared-memory stage (SHARED) or global memory.
+template <int PREC, bool SHARED>
 __device__ __forceinline__ float geo_at(const void* p, int64_t i) {
   if constexpr (PREC == MFA_PREC_BF16) return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
-  else return __ldg(static_cast<const float*>(p) + i);
+  else if constexpr (SHARED) return static_cast<const float*>(p)[i];
+  else return __ldg(static_cast<const float*>(p) + i);  // read-only path: global memory only
 }
 
 // Shared staging of one batch's factors, and the barrier state.
@@ -178,10 +185,10 @@ __host__ __device__ constexpr bool staged() {
   return PREC == MFA_PREC_BF16;
 }
 
-template <int N, int KIND, int PREC>
+template <int N, int KIND, int PREC, bool STG = staged<PREC>(), int CBX = 0>
 __device__ __forceinline__ void issue_factors(const LineArgs& a, int64_t batch, Stage& st) {
-  if constexpr (!staged<PREC>()) return;
-  using S = LShape<N>;
+  if constexpr (!STG) return;
+  using S = LShape<N, CBX>;
   const int64_t c0 = batch * S::CB;
   const int ncb = (int)(a.count - c0 < S::CB ? a.count - c0 : S::CB);
   const uint32_t bytes = (uint32_t)(ncb * a.gstride * (int64_t)sizeof(GeoT<PREC>));
@@ -193,10 +200,10 @@ __device__ __forceinline__ void issue_factors(const LineArgs& a, int64_t batch, 
 // (gather, scatter) run point-parallel over the whole batch, so consecutive
 // threads read consecutive map and output addresses; the factors come from
 // the bulk-copied stage.  `next` >= 0: batch (of `an`) to prefetch afterwards.
-template <int N, int KIND, int PREC, typename TX>
+template <int N, int KIND, int PREC, typename TX, bool STG = staged<PREC>(), int CBX = 0>
 __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, float* smem, Stage& st,
                                            const LineArgs* an, int64_t next) {
-  using S = LShape<N>;
+  using S = LShape<N, CBX>;
   constexpr int L = S::L, P = S::P, CB = S::CB, T = S::T, NG = geom_entries<KIND>();
   constexpr int variant = PREC == MFA_PREC_BF16 ? 1 : 0;
   const int t = threadIdx.x;
@@ -229,8 +236,8 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
       sweep<N, 2, 1, false, false, variant>(V, F2, la, lb);  // D in z
     }
   }
-  // this batch's factors: from the stage (BF16) or straight from global memory (FP32)
-  if constexpr (staged<PREC>()) {
+  // this batch's factors: from the stage (bulk copies) or straight from global memory
+  if constexpr (STG) {
     if (!mbar_wait(st.bar, st.phase)) {
       atomicOr(a.err, 4);
       *st.abort = 1;
@@ -238,17 +245,17 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
     st.phase ^= 1u;
   }
   __syncthreads();
-  if constexpr (staged<PREC>()) {
+  if constexpr (STG) {
     if (*st.abort) return false;
   }
   float* V0 = U0 + CB * P;
-  const void* gs = staged<PREC>() ? static_cast<const void*>(st.buf)
+  const void* gs = STG ? static_cast<const void*>(st.buf)
                                   : static_cast<const void*>(static_cast<const GeoT<PREC>*>(a.geom) + c0 * a.gstride);
   const int64_t gsd = a.gstride;
   if constexpr (KIND == MFA_FORM_MASS) {
     for (int i = t; i < ncb * P; i += T) {
       const int c = i / P, q = i - c * P;
-      U0[i] = geo_at<PREC>(gs, c * gsd + q) * V0[i];
+      U0[i] = geo_at<PREC, STG>(gs, c * gsd + q) * V0[i];
     }
   } else {
     float* G0 = V0 + CB * P;
@@ -259,7 +266,7 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
       const int64_t gb = c * gsd + q;
       float g[NG];
 #pragma unroll
-      for (int e = 0; e < NG; ++e) g[e] = geo_at<PREC>(gs, gb + (int64_t)e * P);
+      for (int e = 0; e < NG; ++e) g[e] = geo_at<PREC, STG>(gs, gb + (int64_t)e * P);
       const float d0 = G0[i], d1 = G1[i], d2 = G2[i];
       G0[i] = fmaf(g[0], d0, fmaf(g[3], d1, g[4] * d2));
       G1[i] = fmaf(g[3], d0, fmaf(g[1], d1, g[5] * d2));
@@ -270,7 +277,7 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
   }
   __syncthreads();
   // the stage is free: start the next batch's factors now
-  if (t == 0 && next >= 0) issue_factors<N, KIND, PREC>(*an, next, st);
+  if (t == 0 && next >= 0) issue_factors<N, KIND, PREC, STG, CBX>(*an, next, st);
   if constexpr (KIND != MFA_FORM_MASS) {
     if (valid) sweep<N, 0, 1, true, true, variant>(F0, U, la, lb);  // r = c0 w|J| u + D_x^T f0
     __syncthreads();
@@ -295,47 +302,48 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
   return true;
 }
 
-template <int N, int PREC>
+template <int N, int PREC, int CBX = 0>
 __host__ __device__ constexpr int stage_bytes(int ng) {
-  return LShape<N>::CB * (int)geom_stride(ng, LShape<N>::P, PREC == MFA_PREC_BF16 ? 2 : 4) *
+  return LShape<N, CBX>::CB * (int)geom_stride(ng, LShape<N, CBX>::P, PREC == MFA_PREC_BF16 ? 2 : 4) *
          (PREC == MFA_PREC_BF16 ? 2 : 4);
 }
 
 // The stage starts 128-byte aligned (bulk copies need a 16-byte aligned destination).
-template <int N>
+template <int N, int CBX = 0>
 __host__ __device__ constexpr int stage_offset() {
-  return (LShape<N>::SMEM + 127) / 128 * 128;
+  return (LShape<N, CBX>::SMEM + 127) / 128 * 128;
 }
 
-template <int N, int KIND, int PREC>
+template <int N, int KIND, int PREC, bool STG = staged<PREC>(), int CBX = 0>
 __host__ __device__ constexpr int line_smem() {
-  return staged<PREC>() ? stage_offset<N>() + stage_bytes<N, PREC>(geom_entries<KIND>()) + 16 : LShape<N>::SMEM;
+  return STG ? stage_offset<N, CBX>() + stage_bytes<N, PREC, CBX>(geom_entries<KIND>()) + 16 : LShape<N, CBX>::SMEM;
 }
 
-template <int N, int KIND, int PREC>
+template <int N, int KIND, int PREC, bool STG = staged<PREC>(), int CBX = 0>
 __device__ __forceinline__ void stage_setup(float* smem, Stage& st, int* abort) {
-  st.buf = reinterpret_cast<unsigned char*>(smem) + stage_offset<N>();
-  st.bar = reinterpret_cast<uint64_t*>(st.buf + stage_bytes<N, PREC>(geom_entries<KIND>()));
+  st.buf = reinterpret_cast<unsigned char*>(smem) + stage_offset<N, CBX>();
+  st.bar = reinterpret_cast<uint64_t*>(st.buf + stage_bytes<N, PREC, CBX>(geom_entries<KIND>()));
   st.phase = 0;
   st.abort = abort;
   if (threadIdx.x == 0) {
     *abort = 0;
-    if constexpr (staged<PREC>()) mbar_init(st.bar);
+    if constexpr (STG) mbar_init(st.bar);
   }
   __syncthreads();
 }
 
-template <int N, int KIND, int PREC, typename TX>
-__global__ void __launch_bounds__(LShape<N>::T) line_apply_kernel(const LineArgs a) {
+template <int N, int KIND, int PREC, typename TX, bool STG = staged<PREC>(), int CBX = 0>
+__global__ void __launch_bounds__(LShape<N, CBX>::T) line_apply_kernel(const LineArgs a) {
   extern __shared__ __align__(128) float smem_l[];
   __shared__ int abort_flag;
   Stage st;
-  stage_setup<N, KIND, PREC>(smem_l, st, &abort_flag);
-  const int64_t nbatch = (a.count + LShape<N>::CB - 1) / LShape<N>::CB;
-  if ((int64_t)blockIdx.x < nbatch && threadIdx.x == 0) issue_factors<N, KIND, PREC>(a, blockIdx.x, st);
+  stage_setup<N, KIND, PREC, STG, CBX>(smem_l, st, &abort_flag);
+  constexpr int CB = LShape<N, CBX>::CB;
+  const int64_t nbatch = (a.count + CB - 1) / CB;
+  if ((int64_t)blockIdx.x < nbatch && threadIdx.x == 0) issue_factors<N, KIND, PREC, STG, CBX>(a, blockIdx.x, st);
   for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
     const int64_t next = batch + gridDim.x < nbatch ? batch + gridDim.x : -1;
-    if (!line_batch<N, KIND, PREC, TX>(a, batch, smem_l, st, &a, next)) return;
+    if (!line_batch<N, KIND, PREC, TX, STG, CBX>(a, batch, smem_l, st, &a, next)) return;
   }
 }
 
@@ -379,11 +387,11 @@ int occupancy(Kern kern, int threads, int smem) {
   return b;
 }
 
-template <int N, int KIND, int PREC, typename TX>
+template <int N, int KIND, int PREC, typename TX, bool STG = staged<PREC>(), int CBX = 0>
 cudaError_t launch_line(const LineArgs& a, int sm_count, cudaStream_t s) {
-  using S = LShape<N>;
-  constexpr int smem = line_smem<N, KIND, PREC>();
-  auto kern = line_apply_kernel<N, KIND, PREC, TX>;
+  using S = LShape<N, CBX>;
+  constexpr int smem = line_smem<N, KIND, PREC, STG, CBX>();
+  auto kern = line_apply_kernel<N, KIND, PREC, TX, STG, CBX>;
   static int bps = -1;
   if (bps < 0) bps = occupancy(kern, S::T, smem);
   const int64_t nbatch = (a.count + S::CB - 1) / S::CB;
@@ -406,6 +414,43 @@ cudaError_t launch_line_group(const HexApplyArgs* items, const int64_t* first, i
   kern<<<(unsigned)(total < cap ? total : cap), S::T, smem, s>>>(items, first, nitems);
   return cudaGetLastError();
 }
+
+namespace {  // one copy per translation unit, like c_tab
+
+std::mutex g_tab_mutex;
+bool g_tab_ready[64] = {false};
+
+// B (GLL basis at the Gauss points) and D (collocation derivative at the Gauss
+// points) for every n, in float and rounded to bfloat16, into this unit's
+// constant bank on the current device.
+inline cudaError_t upload_tables() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_tab_mutex);
+  if (g_tab_ready[dev]) return cudaSuccess;
+  std::vector<float> tab(2 * kTabFloats, 0.0f);
+  for (int n = 2; n <= 9; ++n) {
+    double gll[kMaxN], xg[kMaxN], wg[kMaxN], B[kMaxN * kMaxN], D[kMaxN * kMaxN];
+    gll01(n, gll);
+    gauss_legendre01(n, xg, wg);
+    lagrange_matrix(n, gll, n, xg, B);
+    collocation_derivative(n, xg, D);
+    const int off = tab_offset(n);
+    for (int i = 0; i < n * n; ++i) {
+      tab[off + i] = (float)B[i];
+      tab[off + n * n + i] = (float)D[i];
+      tab[kTabFloats + off + i] = __bfloat162float(__double2bfloat16(B[i]));
+      tab[kTabFloats + off + n * n + i] = __bfloat162float(__double2bfloat16(D[i]));
+    }
+  }
+  e = cudaMemcpyToSymbol(c_tab, tab.data(), sizeof(float) * 2 * kTabFloats);
+  if (e == cudaSuccess) g_tab_ready[dev] = true;
+  return e;
+}
+
+}  // namespace
 
 }  // namespace hexl
 }  // namespace mfa

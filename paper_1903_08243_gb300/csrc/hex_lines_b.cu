@@ -1,49 +1,9 @@
 // Instantiations of the line-per-thread FP32/BF16 hex action for n = 6..9
 // (the other degrees live in the sibling translation unit so both compile in parallel).
-#include <mutex>
-#include <vector>
-
 #include "hex_lines.cuh"
 
 namespace mfa {
-namespace {
-
 using namespace hexl;
-
-std::mutex g_tab_mutex;
-bool g_tab_ready[64] = {false};
-
-// B (GLL basis at the Gauss points) and D (collocation derivative at the Gauss
-// points) for every n, in float and rounded to bfloat16, into this unit's
-// constant bank on the current device.
-cudaError_t upload_tables() {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_tab_mutex);
-  if (g_tab_ready[dev]) return cudaSuccess;
-  std::vector<float> tab(2 * kTabFloats, 0.0f);
-  for (int n = 2; n <= 9; ++n) {
-    double gll[kMaxN], xg[kMaxN], wg[kMaxN], B[kMaxN * kMaxN], D[kMaxN * kMaxN];
-    gll01(n, gll);
-    gauss_legendre01(n, xg, wg);
-    lagrange_matrix(n, gll, n, xg, B);
-    collocation_derivative(n, xg, D);
-    const int off = tab_offset(n);
-    for (int i = 0; i < n * n; ++i) {
-      tab[off + i] = (float)B[i];
-      tab[off + n * n + i] = (float)D[i];
-      tab[kTabFloats + off + i] = __bfloat162float(__double2bfloat16(B[i]));
-      tab[kTabFloats + off + n * n + i] = __bfloat162float(__double2bfloat16(D[i]));
-    }
-  }
-  e = cudaMemcpyToSymbol(c_tab, tab.data(), sizeof(float) * 2 * kTabFloats);
-  if (e == cudaSuccess) g_tab_ready[dev] = true;
-  return e;
-}
-
-}  // namespace
 
 cudaError_t hex_line_apply_b(int n, int kind, int prec, bool f32vec, const hexl::LineArgs& a, int sm_count,
                                  cudaStream_t s) {

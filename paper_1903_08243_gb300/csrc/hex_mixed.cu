@@ -13,12 +13,33 @@ cudaError_t hex_line_group_a(int n, int kind, int prec, const HexApplyArgs* item
 cudaError_t hex_line_group_b(int n, int kind, int prec, const HexApplyArgs* items, const int64_t* first, int nitems,
                              int64_t total, int sm_count, cudaStream_t s);
 
-cudaError_t hex_apply_launch_mixed(int n, int nq, int kind, int prec, bool colour, const HexTables&,
-                                   const HexApplyArgs& a, int sm_count, cudaStream_t s) {
+cudaError_t hex_line_tuned_a(int n, int kind, int prec, bool stg, int cb, const hexl::LineArgs& a, int sm_count,
+                             cudaStream_t s);
+cudaError_t hex_line_tuned_b(int n, int kind, int prec, bool stg, int cb, const hexl::LineArgs& a, int sm_count,
+                             cudaStream_t s);
+
+// Default (256-thread target), then the 512-thread target (hex_lines_tune_*.cu).
+int hex_line_cb_options(int n, int* out) {
+  if (n < 2 || n > 9) return 0;
+  out[0] = hexl::line_cb_for(n, 256);
+  out[1] = hexl::line_cb_for(n, 512);
+  return 2;
+}
+
+cudaError_t hex_apply_launch_mixed(int n, int nq, int kind, int prec, bool colour, const LaunchConfig& lc,
+                                   const HexTables&, const HexApplyArgs& a, int sm_count, cudaStream_t s) {
   if (nq != n || colour || a.cell_list) return cudaErrorInvalidValue;
+  const int variant = lc.variant == MFA_VARIANT_AUTO ? hex_default_variant(n, nq, prec) : lc.variant;
+  if (variant != MFA_VARIANT_LINE && variant != MFA_VARIANT_LINE_STAGED) return cudaErrorInvalidValue;
+  const bool stg = variant == MFA_VARIANT_LINE_STAGED;
+  const bool stg_default = prec == MFA_PREC_BF16 ? hexl::staged<MFA_PREC_BF16>() : hexl::staged<MFA_PREC_FP32>();
   const hexl::LineArgs la{a.x, a.y, a.cell_node, a.geom, a.count, a.geom_stride, a.err};
-  return n <= 5 ? hex_line_apply_a(n, kind, prec, false, la, sm_count, s)
-                : hex_line_apply_b(n, kind, prec, false, la, sm_count, s);
+  if (stg == stg_default && (lc.cb == 0 || lc.cb == hexl::line_cb_for(n, 256)))
+    return n <= 5 ? hex_line_apply_a(n, kind, prec, false, la, sm_count, s)
+                  : hex_line_apply_b(n, kind, prec, false, la, sm_count, s);
+  const int cb = lc.cb == 0 ? hexl::line_cb_for(n, 256) : lc.cb;
+  return n <= 5 ? hex_line_tuned_a(n, kind, prec, stg, cb, la, sm_count, s)
+                : hex_line_tuned_b(n, kind, prec, stg, cb, la, sm_count, s);
 }
 
 cudaError_t hex_apply_launch_f32(int n, int kind, int prec, const float* x, float* y, const int32_t* cell_node,

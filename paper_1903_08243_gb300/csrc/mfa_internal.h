@@ -55,10 +55,11 @@ struct HexApplyArgs {
 };
 
 // Launch the sum-factorised FP64 action for cells [list].  Returns a cudaError_t.
-cudaError_t hex_apply_launch(int n, int nq, int kind, int prec, bool colour, const HexTables& tb,
-                             const HexApplyArgs& a, int sm_count, cudaStream_t s);
-cudaError_t hex_apply_launch_mixed(int n, int nq, int kind, int prec, bool colour, const HexTables& tb,
-                                   const HexApplyArgs& a, int sm_count, cudaStream_t s);
+struct LaunchConfig;
+cudaError_t hex_apply_launch(int n, int nq, int kind, int prec, bool colour, const LaunchConfig& lc,
+                             const HexTables& tb, const HexApplyArgs& a, int sm_count, cudaStream_t s);
+cudaError_t hex_apply_launch_mixed(int n, int nq, int kind, int prec, bool colour, const LaunchConfig& lc,
+                                   const HexTables& tb, const HexApplyArgs& a, int sm_count, cudaStream_t s);
 // One persistent launch over many forms of the same (n, n, kind, precision).
 cudaError_t hex_group_launch(int n, int kind, int prec, const HexTables& tb, const HexApplyArgs* items,
                              const int64_t* first, int nitems, int64_t total, int sm_count, cudaStream_t s);
@@ -76,6 +77,27 @@ int hex_eo_cells_per_block(int n);
 // busy ~80% of the time against ~93% for the point kernel; measured on GB300
 // it wins from n = 7 (Q6: 14.15 vs 14.86 ms) and loses at n = 5, 6.
 inline bool hex_use_eo(int n, int nq, int prec) { return prec == MFA_PREC_FP64 && nq == n && n >= 7 && n <= 9; }
+
+// ---------------------------------------------------------------- launch configurations
+// Kernel variant (MFA_VARIANT_*) and cells per block of one apply; cb = 0 is
+// the variant's default.  Only the compiled choices listed by the *_cb_options
+// functions are accepted by the launchers.
+struct LaunchConfig {
+  int variant = MFA_VARIANT_AUTO;
+  int cb = 0;
+};
+// Cells per block of a kernel with `per_cell` threads per cell for a target block size.
+constexpr int cells_for_target(int per_cell, int target) { return target / per_cell > 0 ? target / per_cell : 1; }
+int hex_default_variant(int n, int nq, int prec);
+// Compiled cells-per-block choices, the default first; return the count (<= 4).
+int hex_point_cb_options(int n, int nq, int* out);
+int hex_eo_cb_options(int n, int* out);
+int hex_line_cb_options(int n, int* out);
+int tet_cb_options(int* out);
+cudaError_t hex_point_launch_cb(int n, int nq, int kind, bool colour, int cb, const HexTables& tb,
+                                const HexApplyArgs& a, int sm_count, cudaStream_t s);
+cudaError_t hex_eo_apply_launch_cb(int n, int kind, bool colour, int cb, const HexApplyArgs& a, int sm_count,
+                                   cudaStream_t s);
 // FP32/BF16 action with float vectors.
 cudaError_t hex_apply_launch_f32(int n, int kind, int prec, const float* x, float* y, const int32_t* cell_node,
                                  const void* geom, int64_t count, int64_t gstride, int* err, int sm_count,
@@ -114,7 +136,8 @@ struct TetApplyArgs {
   int* err;
 };
 
-cudaError_t tet_apply_launch(int p, int ncomp, int kind, int law, bool colour, const TetTables& tb,
+// threads: threads (cells) per block, one of tet_cb_options.
+cudaError_t tet_apply_launch(int p, int ncomp, int kind, int law, bool colour, int threads, const TetTables& tb,
                              const TetApplyArgs& a, int sm_count, cudaStream_t s);
 cudaError_t tet_diagonal_launch(int p, int ncomp, int kind, const TetTables& tb, const TetApplyArgs& a,
                                 double* d, cudaStream_t s);
@@ -190,6 +213,8 @@ struct mfa_form {
   int nq1 = 0;                   // hex: points per direction
   int nq = 0;                    // points per cell
   int scatter = MFA_SCATTER_ATOMIC;
+  mfa::LaunchConfig launch{};    // variant and cells per block used by apply_form
+  double tuned_ms = 0.0;         // time of `launch` measured by mfa_form_autotune
   mfa::HexTables hex{};
   mfa::TetTables tet{};
   void* d_geom = nullptr;
@@ -198,4 +223,5 @@ struct mfa_form {
   double* d_stage_x = nullptr;   // mfa_apply_host staging
   double* d_stage_y = nullptr;
   double flops = 0.0, bytes = 0.0, setup_ms = 0.0;
+  double flops_executed = 0.0;
 };

@@ -447,46 +447,46 @@ __global__ void __launch_bounds__(128) tet_moment_kernel(const __grid_constant__
   }
 }
 
-template <int KIND, int LAW>
-cudaError_t launch_moment(bool colour, const TetTables& tb, const TetApplyArgs& a, int sm_count, cudaStream_t s) {
+// Persistent grid of `threads`-thread blocks (one cell per thread), capped at
+// the resident blocks of all SMs; `bps` caches the occupancy per block size.
+template <typename Kern>
+cudaError_t launch_cells(Kern kern, int (&bps)[4], int threads, const TetTables& tb, const TetApplyArgs& a,
+                         int sm_count, cudaStream_t s) {
   if (a.count == 0) return cudaSuccess;
-  auto kern = colour ? tet_moment_kernel<KIND, LAW, true> : tet_moment_kernel<KIND, LAW, false>;
-  static int bps_cache[2] = {-1, -1};  // per scatter variant
-  int& bps = bps_cache[colour ? 1 : 0];
-  if (bps < 0) {
+  if (threads != 32 && threads != 64 && threads != 128) return cudaErrorInvalidValue;
+  int& b = bps[threads / 32 - 1];
+  if (b < 0) {
     int v = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, 128, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, 0);
     if (e != cudaSuccess) return e;
-    bps = v < 1 ? 1 : v;
+    b = v < 1 ? 1 : v;
   }
-  int64_t blocks = (a.count + 127) / 128;
-  const int64_t cap = (int64_t)sm_count * bps;
+  int64_t blocks = (a.count + threads - 1) / threads;
+  const int64_t cap = (int64_t)sm_count * b;
   if (blocks > cap) blocks = cap;
-  kern<<<(unsigned)blocks, 128, 0, s>>>(tb, a);
+  kern<<<(unsigned)blocks, threads, 0, s>>>(tb, a);
   return cudaGetLastError();
+}
+
+template <int KIND, int LAW>
+cudaError_t launch_moment(bool colour, int threads, const TetTables& tb, const TetApplyArgs& a, int sm_count,
+                          cudaStream_t s) {
+  static int bps[2][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}};  // per scatter variant and block size
+  return colour ? launch_cells(tet_moment_kernel<KIND, LAW, true>, bps[1], threads, tb, a, sm_count, s)
+                : launch_cells(tet_moment_kernel<KIND, LAW, false>, bps[0], threads, tb, a, sm_count, s);
 }
 
 template <int P, int NC, int KIND, int LAW, int NQ, bool COLOUR>
-cudaError_t launch(const TetTables& tb, const TetApplyArgs& a, int sm_count, cudaStream_t s) {
-  if (a.count == 0) return cudaSuccess;
-  auto kern = tet_apply_kernel<P, NC, KIND, LAW, NQ, COLOUR>;
-  static int bps = -1;
-  if (bps < 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 128, 0);
-    if (e != cudaSuccess) return e;
-    if (bps < 1) bps = 1;
-  }
-  int64_t blocks = (a.count + 127) / 128;
-  const int64_t cap = (int64_t)sm_count * bps;
-  if (blocks > cap) blocks = cap;
-  kern<<<(unsigned)blocks, 128, 0, s>>>(tb, a);
-  return cudaGetLastError();
+cudaError_t launch(int threads, const TetTables& tb, const TetApplyArgs& a, int sm_count, cudaStream_t s) {
+  static int bps[4] = {-1, -1, -1, -1};
+  return launch_cells(tet_apply_kernel<P, NC, KIND, LAW, NQ, COLOUR>, bps, threads, tb, a, sm_count, s);
 }
 
 template <int P, int NC, int KIND, int LAW, int NQ>
-cudaError_t launch2(bool colour, const TetTables& tb, const TetApplyArgs& a, int sm_count, cudaStream_t s) {
-  return colour ? launch<P, NC, KIND, LAW, NQ, true>(tb, a, sm_count, s)
-                : launch<P, NC, KIND, LAW, NQ, false>(tb, a, sm_count, s);
+cudaError_t launch2(bool colour, int threads, const TetTables& tb, const TetApplyArgs& a, int sm_count,
+                    cudaStream_t s) {
+  return colour ? launch<P, NC, KIND, LAW, NQ, true>(threads, tb, a, sm_count, s)
+                : launch<P, NC, KIND, LAW, NQ, false>(threads, tb, a, sm_count, s);
 }
 
 // Diagonal of the linear forms, per local dof and cell:
@@ -549,32 +549,39 @@ cudaError_t tet_diagonal_launch(int p, int ncomp, int kind, const TetTables& tb,
   return cudaGetLastError();
 }
 
-cudaError_t tet_apply_launch(int p, int ncomp, int kind, int law, bool colour, const TetTables& tb,
+int tet_cb_options(int* out) {
+  out[0] = 128;
+  out[1] = 64;
+  out[2] = 32;
+  return 3;
+}
+
+cudaError_t tet_apply_launch(int p, int ncomp, int kind, int law, bool colour, int threads, const TetTables& tb,
                              const TetApplyArgs& a, int sm_count, cudaStream_t s) {
   const int nq = tb.nq;
   if (p == 1 && ncomp == 1 && nq == 4) {
     switch (kind) {
-      case MFA_FORM_MASS: return launch2<1, 1, MFA_FORM_MASS, 0, 4>(colour, tb, a, sm_count, s);
-      case MFA_FORM_LAPLACE: return launch2<1, 1, MFA_FORM_LAPLACE, 0, 4>(colour, tb, a, sm_count, s);
-      case MFA_FORM_HELMHOLTZ: return launch2<1, 1, MFA_FORM_HELMHOLTZ, 0, 4>(colour, tb, a, sm_count, s);
+      case MFA_FORM_MASS: return launch2<1, 1, MFA_FORM_MASS, 0, 4>(colour, threads, tb, a, sm_count, s);
+      case MFA_FORM_LAPLACE: return launch2<1, 1, MFA_FORM_LAPLACE, 0, 4>(colour, threads, tb, a, sm_count, s);
+      case MFA_FORM_HELMHOLTZ: return launch2<1, 1, MFA_FORM_HELMHOLTZ, 0, 4>(colour, threads, tb, a, sm_count, s);
     }
   }
   if (p == 2 && ncomp == 1) {
-    if (kind == MFA_FORM_MASS && nq == 27) return launch2<2, 1, MFA_FORM_MASS, 0, 27>(colour, tb, a, sm_count, s);
-    if (kind == MFA_FORM_LAPLACE && nq == 4) return launch2<2, 1, MFA_FORM_LAPLACE, 0, 4>(colour, tb, a, sm_count, s);
+    if (kind == MFA_FORM_MASS && nq == 27) return launch2<2, 1, MFA_FORM_MASS, 0, 27>(colour, threads, tb, a, sm_count, s);
+    if (kind == MFA_FORM_LAPLACE && nq == 4) return launch2<2, 1, MFA_FORM_LAPLACE, 0, 4>(colour, threads, tb, a, sm_count, s);
     if (kind == MFA_FORM_HELMHOLTZ && nq == 27)
-      return launch2<2, 1, MFA_FORM_HELMHOLTZ, 0, 27>(colour, tb, a, sm_count, s);
+      return launch2<2, 1, MFA_FORM_HELMHOLTZ, 0, 27>(colour, threads, tb, a, sm_count, s);
   }
   if (p == 2 && ncomp == 3) {
-    if (kind == MFA_FORM_LAPLACE && nq == 4) return launch2<2, 3, MFA_FORM_LAPLACE, 0, 4>(colour, tb, a, sm_count, s);
+    if (kind == MFA_FORM_LAPLACE && nq == 4) return launch2<2, 3, MFA_FORM_LAPLACE, 0, 4>(colour, threads, tb, a, sm_count, s);
     if (kind == MFA_FORM_ELASTICITY && nq == 4)
-      return launch2<2, 3, MFA_FORM_ELASTICITY, 0, 4>(colour, tb, a, sm_count, s);
+      return launch2<2, 3, MFA_FORM_ELASTICITY, 0, 4>(colour, threads, tb, a, sm_count, s);
     if (kind == MFA_FORM_HYPER_RES && nq == 27)
-      return law == MFA_LAW_SVK ? launch_moment<MFA_FORM_HYPER_RES, MFA_LAW_SVK>(colour, tb, a, sm_count, s)
-                                : launch_moment<MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(colour, tb, a, sm_count, s);
+      return law == MFA_LAW_SVK ? launch_moment<MFA_FORM_HYPER_RES, MFA_LAW_SVK>(colour, threads, tb, a, sm_count, s)
+                                : launch_moment<MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(colour, threads, tb, a, sm_count, s);
     if (kind == MFA_FORM_HYPER_JAC && nq == 27)
-      return law == MFA_LAW_SVK ? launch_moment<MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(colour, tb, a, sm_count, s)
-                                : launch_moment<MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(colour, tb, a, sm_count, s);
+      return law == MFA_LAW_SVK ? launch_moment<MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(colour, threads, tb, a, sm_count, s)
+                                : launch_moment<MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(colour, threads, tb, a, sm_count, s);
   }
   return cudaErrorInvalidValue;
 }
