@@ -42,7 +42,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mfa", "reference"], default="mfa")
-    ap.add_argument("--workload", choices=["hex", "tet-p1-mass", "tet-p2", "batched", "pcg"], default="hex",
+    ap.add_argument("--workload", choices=["hex", "hex-vector", "tet-p1-mass", "tet-p2", "batched", "pcg"],
+                    default="hex",
                     help="hex: 64^3 Q1-Q6 Laplace+Helmholtz; tet-p1-mass: 8^3x6 P1 mass; "
                          "tet-p2: 48^3x6 vector P2 elasticity + neo-Hookean residual; "
                          "batched: 64 hex Helmholtz operators (degrees 1-8, 8^3-48^3) in one graph; "
@@ -59,8 +60,10 @@ def parse_args():
     ap.add_argument("--nops", type=int, default=64)
     ap.add_argument("--nx", type=int, default=None)
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
-    ap.add_argument("--degrees", default="1,2,3,4,5,6")
-    ap.add_argument("--forms", default="laplace,helmholtz")
+    ap.add_argument("--degrees", default=None, help="hex: 1,2,3,4,5,6; hex-vector: 1,2,3,4")
+    ap.add_argument("--forms", default=None,
+                    help="hex: laplace,helmholtz; hex-vector: elasticity,hyper_res,hyper_jac "
+                         "(neo-Hookean residual, St Venant-Kirchhoff Jacobian action)")
     ap.add_argument("--scatter", choices=["atomic", "colour"], default="atomic",
                     help="scatter at form creation (the autotuner may change it)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -74,9 +77,10 @@ FORM_IDS = {"mass": 0, "laplace": 1, "helmholtz": 2, "elasticity": 3, "hyper_res
 
 
 def workload_name(args):
-    if args.workload == "hex":
-        return "hex%d^3-perturbed0.1h-Q%s-%s-fp64" % (args.nx, args.degrees.replace(",", ""),
-                                                      args.forms.replace(",", "+"))
+    if args.workload in ("hex", "hex-vector"):
+        return "hex%d^3-perturbed0.1h-Q%s-%s%s-fp64" % (args.nx, args.degrees.replace(",", ""),
+                                                        "vector-" if args.workload == "hex-vector" else "",
+                                                        args.forms.replace(",", "+"))
     if args.workload == "tet-p1-mass":
         return "tet-kuhn%d^3x6-P1-mass-fp64" % args.nx
     return "tet-kuhn%d^3x6-P2vec-elasticity+neohookean-residual-fp64" % args.nx
@@ -85,9 +89,25 @@ def workload_name(args):
 def build_cases(args):
     """Operators of one step.  Each case holds the seeded inputs shared by the GPU and the oracle."""
     if args.nx is None:
-        args.nx = {"hex": 64, "tet-p1-mass": 8, "tet-p2": 48}[args.workload]
+        args.nx = {"hex": 64, "hex-vector": 48, "tet-p1-mass": 8, "tet-p2": 48}[args.workload]
     cases = []
-    if args.workload == "hex":
+    if args.workload == "hex-vector":
+        mesh = fi.hex_box_mesh(args.nx, perturb=0.1, seed=1)
+        laws = {"elasticity": 0, "laplace": 0, "hyper_res": 1, "hyper_jac": 0}
+        lawname = {"elasticity": "", "laplace": "", "hyper_res": " neo-Hookean", "hyper_jac": " SVK"}
+        for p in [int(p) for p in args.degrees.split(",")]:
+            cell_node, nnode = fi.hex_node_map(args.nx, p)
+            m1 = args.nx * p + 1
+            v = np.arange(nnode)
+            grid = np.stack([v % m1, (v // m1) % m1, v // (m1 * m1)], axis=1) / (m1 - 1)
+            u = fi.sinusoid_displacement(grid, seed=2).ravel()  # smooth field on the node grid
+            xr = fi.uniform_vector(3 * nnode, seed=1)
+            for f in args.forms.split(","):
+                kw = dict(lam=1.0, mu=1.0, law=laws[f])
+                cases.append(dict(name="Q%d %s%s" % (p, f, lawname[f]), cell_type=8, mesh=mesh, p=p, ncomp=3, form=f,
+                                  cell_node=cell_node, nnode=nnode, x=u if f == "hyper_res" else xr,
+                                  coef=u if f == "hyper_jac" else None, kw=kw, okw=kw, qdeg=p + 1))
+    elif args.workload == "hex":
         mesh = fi.hex_box_mesh(args.nx, perturb=0.1, seed=1)
         for p in [int(p) for p in args.degrees.split(",")]:
             cell_node, nnode = fi.hex_node_map(args.nx, p)
@@ -219,9 +239,13 @@ def sub_mesh(case, ncell_sample):
 # Cells per oracle sample: about 1-2.5 s of oracle work per operator for the
 # baseline, about 0.1 s per operator and step for the reference arm.
 SAMPLE_BASELINE = {("hex", 1): 262144, ("hex", 2): 64000, ("hex", 3): 21952, ("hex", 4): 8000, ("hex", 5): 2744,
-                   ("hex", 6): 1728, ("hex", 7): 512, ("hex", 8): 216, ("tet", 1): 3072, ("tet", 2): 200000}
+                   ("hex", 6): 1728, ("hex", 7): 512, ("hex", 8): 216, ("tet", 1): 3072, ("tet", 2): 200000,
+                   ("hexv", 1): 110592, ("hexv", 2): 24000, ("hexv", 3): 4000, ("hexv", 4): 1000, ("hexv", 5): 250,
+                   ("hexv", 6): 100}
 SAMPLE_STEP = {("hex", 1): 13824, ("hex", 2): 2744, ("hex", 3): 1000, ("hex", 4): 512, ("hex", 5): 216,
-               ("hex", 6): 125, ("hex", 7): 64, ("hex", 8): 27, ("tet", 1): 3072, ("tet", 2): 6000}
+               ("hex", 6): 125, ("hex", 7): 64, ("hex", 8): 27, ("tet", 1): 3072, ("tet", 2): 6000,
+               ("hexv", 1): 8000, ("hexv", 2): 1500, ("hexv", 3): 250, ("hexv", 4): 64, ("hexv", 5): 16,
+               ("hexv", 6): 8}
 
 
 def oracle_rate(cases, repeats=1, samples=SAMPLE_STEP):
@@ -231,9 +255,9 @@ def oracle_rate(cases, repeats=1, samples=SAMPLE_STEP):
     out = []
     for c in cases:
         ncell = c["mesh"].ncell
-        key = ("hex" if c["cell_type"] == 8 else "tet", c["p"])
+        key = ("tet" if c["cell_type"] == 4 else ("hexv" if c["ncomp"] == 3 else "hex"), c["p"])
         cv, cn, nodes, nsub = sub_mesh(c, samples.get(key, 64))
-        coef = None
+        coef = None if c.get("coef") is None else c["coef"].reshape(-1, c["ncomp"])[nodes].ravel()
         xs = c["x"].reshape(-1, c["ncomp"])[nodes].ravel()
         pb = oracle.Problem(c["cell_type"], c["mesh"].coords, cv, c["p"], cn, nodes.size, FORM_IDS[c["form"]],
                             ncomp=c["ncomp"], qdeg=c["qdeg"], ucoef=coef, **c["okw"])
@@ -304,6 +328,8 @@ def gpu_arm(args, world, rank, local):
                         precision=prec, **c["kw"])
         x = torch.from_numpy(c["x"]).to("cuda")
         y = torch.empty_like(x)
+        if c.get("coef") is not None:
+            form.set_coefficient(torch.from_numpy(c["coef"]).to("cuda"))
         ops.append(dict(case=c, form=form, x=x, y=y, info=form.info()))
     ctx.sync()
     # autotuner: every compiled launch configuration of each form is timed, the fastest kept
@@ -394,7 +420,8 @@ def gpu_arm(args, world, rank, local):
     dom = ops[i_dom]
     achieved = dom["info"].flops / (per_op_ms[i_dom] / 1e3) / 1e12
     if dom["case"]["cell_type"] == 8:
-        ksrc, kbase = VARIANT_KERNELS[dom["cfg"].variant]
+        ksrc, kbase = (("hex_vector.cuh", "hexv::apply_kernel") if dom["case"]["ncomp"] == 3
+                       else VARIANT_KERNELS[dom["cfg"].variant])
         kh = kernel_hash(ksrc)
         kname = kbase + "<n=%d,%s,cb=%d>" % (dom["case"]["p"] + 1, dom["case"]["form"], dom["cfg"].cells_per_block)
     else:
@@ -466,6 +493,12 @@ def gpu_arm(args, world, rank, local):
             cfg.update({"mesh": "%d^3 hex, interior vertices perturbed U[-0.1h,0.1h], seed 1" % args.nx,
                         "quadrature": "p+1 Gauss points per direction", "geometry": "stored FP64 G per point",
                         "input": "x ~ U[-1,1) seed 1"})
+        elif args.workload == "hex-vector":
+            cfg.update({"mesh": "%d^3 hex, interior vertices perturbed U[-0.1h,0.1h], seed 1" % args.nx,
+                        "quadrature": "p+1 Gauss points per direction",
+                        "geometry": "stored FP64 J^-1 and w|det J| per point", "lambda": 1.0, "mu": 1.0,
+                        "input": "residual and coefficient: sinusoid displacement (8 terms, amplitude 0.05, seed 2) "
+                                 "on the node grid; elasticity and Jacobian: x ~ U[-1,1) seed 1"})
         elif args.workload == "tet-p1-mass":
             cfg.update({"mesh": "%d^3 boxes x 6 Kuhn tets" % args.nx, "quadrature": "degree 2",
                         "input": "x ~ U[-1,1) seed 0"})
@@ -706,6 +739,10 @@ def main():
     args = parse_args()
     if args.precision is None:
         args.precision = "fp32" if args.workload == "batched" else "fp64"
+    if args.degrees is None:
+        args.degrees = "1,2,3,4" if args.workload == "hex-vector" else "1,2,3,4,5,6"
+    if args.forms is None:
+        args.forms = "elasticity,hyper_res,hyper_jac" if args.workload == "hex-vector" else "laplace,helmholtz"
     world, rank, local = dist_setup(args)
     if args.workload == "batched" and args.impl != "reference":
         batched_arm(args, world, rank, local)

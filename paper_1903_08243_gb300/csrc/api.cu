@@ -78,7 +78,22 @@ void count_work(mfa_form* f) {
     if (kind != MFA_FORM_MASS) exec_cell += L * (3.0 * line(-1, 0) + 3.0 * line(-1, 1)) + 15.0 * P;  // D, D^T, G g
     if (kind != MFA_FORM_LAPLACE) exec_cell += P;  // c0 w|J| u
   }
-  if (sp->mesh->cell_type == MFA_CELL_HEX8) {
+  if (sp->mesh->cell_type == MFA_CELL_HEX8 && sp->ncomp == 3) {
+    // per component 24 n^4 (B, D, D^T, B^T sweeps; the Jacobian action also interpolates the
+    // linearisation point's gradient, 12 n^4 per component), per point the physical gradient(s)
+    // (45 each), the physics and the flux map (54: 9 entries x 5 + w|J|), scatter adds 3 n^3.
+    // Vector Laplacian: three G g products (3 x 15) per point.
+    const double n = sp->degree + 1, P = n * n * n, n4 = P * n;
+    const bool jac = kind == MFA_FORM_HYPER_JAC, svk = f->p.law == MFA_LAW_SVK;
+    double per_pt = 0.0;
+    if (kind == MFA_FORM_LAPLACE) per_pt = 45.0;
+    else if (kind == MFA_FORM_ELASTICITY) per_pt = 45.0 + 24.0 + 54.0;
+    else if (kind == MFA_FORM_HYPER_RES) per_pt = 45.0 + (svk ? 102.0 : 66.0) + 54.0 + 3.0;
+    else per_pt = 90.0 + (svk ? 243.0 : 202.0) + 54.0;
+    per_cell = 3.0 * 24.0 * n4 + (jac ? 3.0 * 12.0 * n4 : 0.0) + per_pt * P + 3.0 * P;
+    bytes = ncell * (4.0 * P + 8.0 * mfa::hex_geom_entries(kind) * P);
+    if (jac) bytes += 8.0 * ndof;
+  } else if (sp->mesh->cell_type == MFA_CELL_HEX8) {
     // algorithmic count of collocation sum factorisation, whatever the kernel variant:
     // 24 n^4 for n = nq (B, B^T, D, D^T sweeps) + pointwise physics + scatter adds
     const double n = sp->degree + 1, q = f->nq1;
@@ -237,7 +252,13 @@ int apply_form(mfa_form* f, const double* x, double* y, cudaStream_t stream) {
     const int32_t* list = colour ? sp->d_colour_cells + sp->colour_offsets[k] : nullptr;
     const int64_t count = colour ? sp->colour_offsets[k + 1] - sp->colour_offsets[k] : sp->mesh->ncell;
     cudaError_t e;
-    if (sp->mesh->cell_type == MFA_CELL_HEX8) {
+    if (sp->mesh->cell_type == MFA_CELL_HEX8 && sp->ncomp == 3) {
+      mfa::HexVecArgs a{x, y, sp->d_cell_node, static_cast<const double*>(f->d_geom), f->d_coef, list, count,
+                        f->gstride, f->p.lambda, f->p.mu, f->p.b[0], f->p.b[1], f->p.b[2], ctx->d_err};
+      const int n = sp->degree + 1;
+      e = n <= 5 ? mfa::hex_vector_launch_a(n, f->p.kind, f->p.law, colour, f->hex, a, ctx->sm_count, stream)
+                 : mfa::hex_vector_launch_b(n, f->p.kind, f->p.law, colour, f->hex, a, ctx->sm_count, stream);
+    } else if (sp->mesh->cell_type == MFA_CELL_HEX8) {
       mfa::HexApplyArgs a{x, y, sp->d_cell_node, f->d_geom, list, count, ctx->d_err, f->gstride};
       e = mfa::hex_apply_launch(sp->degree + 1, f->nq1, f->p.kind, f->p.precision, colour, f->launch, f->hex, a,
                                 ctx->sm_count, stream);
@@ -399,11 +420,22 @@ int mfa_space_destroy(mfa_space* s) {
   return MFA_OK;
 }
 
+static int default_variant(const mfa_space* sp, int nq, int precision) {
+  if (sp->mesh->cell_type != MFA_CELL_HEX8) return MFA_VARIANT_CELL;
+  if (sp->ncomp == 3) return MFA_VARIANT_POINT;  // the vector forms have the point kernel only
+  return mfa::hex_default_variant(sp->degree + 1, nq, precision);
+}
+
 // Compiled cells-per-block choices of `variant` for this form (default first).
 static int cb_options(const mfa_form* f, int variant, int* out) {
   const mfa_space* sp = f->space;
   const int n = sp->degree + 1, nq = f->p.qdeg > 0 ? f->p.qdeg : n;
   if (sp->mesh->cell_type != MFA_CELL_HEX8) return variant == MFA_VARIANT_CELL ? mfa::tet_cb_options(out) : 0;
+  if (sp->ncomp == 3) {
+    if (variant != MFA_VARIANT_POINT) return 0;
+    out[0] = mfa::hex_cells_per_block(n, n);
+    return 1;
+  }
   if (f->p.precision == MFA_PREC_FP64) {
     if (variant == MFA_VARIANT_POINT) return mfa::hex_point_cb_options(n, nq, out);
     if (variant == MFA_VARIANT_EVEN_ODD) return nq == n ? mfa::hex_eo_cb_options(n, out) : 0;
@@ -464,8 +496,13 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
                 "mfa_form_create: FP32/BF16 cover hex forms with p+1 points per direction and the atomic scatter");
   if (kind >= MFA_FORM_ELASTICITY && sp->ncomp != 3)
     return fail(MFA_ERR_ARG, "mfa_form_create: form %d needs a 3-component space", kind);
-  if (ct == MFA_CELL_HEX8 && (sp->ncomp != 1 || kind > MFA_FORM_HELMHOLTZ))
-    return fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: hex kernels cover scalar mass/Laplace/Helmholtz");
+  if (ct == MFA_CELL_HEX8 && sp->ncomp == 1 && kind > MFA_FORM_HELMHOLTZ)
+    return fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: scalar hex kernels cover mass/Laplace/Helmholtz");
+  if (ct == MFA_CELL_HEX8 && sp->ncomp == 3 &&
+      (kind == MFA_FORM_MASS || kind == MFA_FORM_HELMHOLTZ || prm->precision != MFA_PREC_FP64 ||
+       (prm->qdeg > 0 && prm->qdeg != sp->degree + 1)))
+    return fail(MFA_ERR_UNSUPPORTED,
+                "mfa_form_create: vector hex kernels cover FP64 Laplace/elasticity/hyperelasticity with p+1 points");
   if (ct == MFA_CELL_TET4) {
     const bool ok = (sp->degree == 1 && sp->ncomp == 1 && kind <= MFA_FORM_HELMHOLTZ) ||
                     (sp->degree == 2 && sp->ncomp == 1 && kind <= MFA_FORM_HELMHOLTZ) ||
@@ -479,9 +516,7 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
   f->space = sp;
   f->p = *prm;
   f->scatter = prm->scatter == MFA_SCATTER_COLOUR ? MFA_SCATTER_COLOUR : MFA_SCATTER_ATOMIC;
-  f->launch.variant = ct == MFA_CELL_HEX8 ? mfa::hex_default_variant(sp->degree + 1, prm->qdeg > 0 ? prm->qdeg : sp->degree + 1,
-                                                                     prm->precision)
-                                          : MFA_VARIANT_CELL;
+  f->launch.variant = default_variant(sp, prm->qdeg > 0 ? prm->qdeg : sp->degree + 1, prm->precision);
   int rc = MFA_OK;
   if (prm->cells_per_block != 0) {
     int opts[4];
@@ -575,10 +610,7 @@ int mfa_form_set_config(mfa_form* f, const mfa_launch_config* cfg) {
   if (!f || !cfg) return fail(MFA_ERR_ARG, "mfa_form_set_config: NULL argument");
   mfa_launch_config want = *cfg;
   const mfa_space* sp = f->space;
-  if (want.variant == MFA_VARIANT_AUTO)
-    want.variant = sp->mesh->cell_type == MFA_CELL_HEX8
-                       ? mfa::hex_default_variant(sp->degree + 1, f->nq1, f->p.precision)
-                       : MFA_VARIANT_CELL;
+  if (want.variant == MFA_VARIANT_AUTO) want.variant = default_variant(sp, f->nq1, f->p.precision);
   if (want.cells_per_block == 0) {
     int opts[4];
     if (cb_options(f, want.variant, opts) > 0) want.cells_per_block = opts[0];
@@ -758,6 +790,7 @@ int mfa_diagonal(mfa_ctx* ctx, mfa_form* f, double* d) {
   cudaError_t e;
   if (sp->mesh->cell_type == MFA_CELL_HEX8) {
     if (f->p.precision != MFA_PREC_FP64) return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: FP64 forms only");
+    if (sp->ncomp != 1) return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: scalar hex forms only");
     e = mfa::hex_diagonal_launch(sp->degree + 1, f->nq1, f->p.kind, f->hex, sp->d_cell_node,
                                  static_cast<const double*>(f->d_geom),
                                  sp->mesh->ncell, d, ctx->sm_count, ctx->stream);

@@ -16,6 +16,7 @@ int hex_line_cells_per_block(int n) {
 }
 
 int hex_geom_entries(int kind) {
+  if (kind >= MFA_FORM_ELASTICITY) return 10;  // J^{-1} (row-major) and w|det J|
   return kind == MFA_FORM_MASS ? 1 : (kind == MFA_FORM_LAPLACE ? 6 : 7);
 }
 
@@ -86,6 +87,11 @@ __global__ void hex_geometry_kernel(const __grid_constant__ HexTables tb, int nq
     TG* out = geom + cell * stride + q;
     if (ng == 1) {
       store_geo(out, c0 * wdet);
+      continue;
+    }
+    if (ng == 10) {  // vector forms: J^{-1} row-major, then w|det J|
+      for (int e = 0; e < 9; ++e) store_geo(out + e * pq, Ji[e / 3][e % 3]);
+      store_geo(out + 9 * pq, wdet);
       continue;
     }
     const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};

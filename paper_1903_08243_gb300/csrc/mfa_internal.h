@@ -54,6 +54,24 @@ struct HexApplyArgs {
   int64_t geom_stride;       // elements per cell of geom (ng * nq^3, padded to 16 bytes for FP32/BF16)
 };
 
+// Vector forms on hexes (ncomp = 3, dof = 3 node + c), FP64, p+1 points per direction.
+struct HexVecArgs {
+  const double* x;
+  double* y;
+  const int32_t* cell_node;
+  const double* geom;        // [ncell][ng][n^3]: G (6, vector Laplacian) or J^{-1} row-major + w|det J| (10)
+  const double* ucoef;       // HYPER_JAC linearisation point
+  const int32_t* cell_list;  // cells to process (nullptr: 0..count-1)
+  int64_t count;
+  int64_t geom_stride;       // doubles per cell of geom
+  double lam, mu, b0, b1, b2;
+  int* err;
+};
+cudaError_t hex_vector_launch_a(int n, int kind, int law, bool colour, const HexTables& tb, const HexVecArgs& a,
+                                int sm_count, cudaStream_t s);  // n = 2..5
+cudaError_t hex_vector_launch_b(int n, int kind, int law, bool colour, const HexTables& tb, const HexVecArgs& a,
+                                int sm_count, cudaStream_t s);  // n = 6..9
+
 // Launch the sum-factorised FP64 action for cells [list].  Returns a cudaError_t.
 struct LaunchConfig;
 cudaError_t hex_apply_launch(int n, int nq, int kind, int prec, bool colour, const LaunchConfig& lc,

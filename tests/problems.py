@@ -7,14 +7,38 @@ import oracle
 KIND_NAMES = {"mass": 0, "laplace": 1, "helmholtz": 2, "elasticity": 3, "hyper_res": 4, "hyper_jac": 5}
 
 
-def hex_case(nx, p, perturb=0.1, seed=1, shuffle=False):
+def hex_node_coords(m, cn, p):
+    """Physical positions of the Q_p nodes: trilinear image of numpy-derived GLL points."""
+    from tests import exact
+
+    n = p + 1
+    s = exact.gll_nodes_np(n)
+    out = np.zeros((cn.max() + 1, 3))
+    X = m.coords[m.cell_vert]  # [ncell][8][3]
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                a = i + n * j + n * n * k
+                xi = (s[i], s[j], s[k])
+                w = np.array([(xi[0] if v & 1 else 1 - xi[0]) * (xi[1] if v & 2 else 1 - xi[1]) *
+                              (xi[2] if v & 4 else 1 - xi[2]) for v in range(8)])
+                out[cn[:, a]] = np.einsum("v,cvd->cd", w, X)
+    return out
+
+
+def hex_case(nx, p, perturb=0.1, seed=1, shuffle=False, ncomp=1):
     mesh = fi.hex_box_mesh(nx, perturb=perturb, seed=seed)
     cell_node, nnode = fi.hex_node_map(nx, p)
+    nodes = hex_node_coords(mesh, cell_node, p) if ncomp == 3 else None
     cv = mesh.cell_vert
     if shuffle:
-        cv, cell_node, _ = fi.shuffle_mesh(cv, cell_node, nnode, seed=seed + 100)
-    return dict(cell_type=8, coords=mesh.coords, cell_vert=cv, degree=p, cell_node=cell_node, nnode=nnode, ncomp=1,
-                nodes=None)
+        cv, cell_node, perm = fi.shuffle_mesh(cv, cell_node, nnode, seed=seed + 100)
+        if nodes is not None:
+            inv = np.empty_like(perm)
+            inv[perm] = np.arange(perm.size)
+            nodes = nodes[inv]
+    return dict(cell_type=8, coords=mesh.coords, cell_vert=cv, degree=p, cell_node=cell_node, nnode=nnode,
+                ncomp=ncomp, nodes=nodes)
 
 
 def tet_case(nx, p, ncomp=1, perturb=0.0, seed=0, shuffle=False):

@@ -16,6 +16,7 @@ from numpy.polynomial import legendre as L
 import oracle
 import fe_inputs as fi
 from tests import exact
+from tests.problems import hex_node_coords
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -142,23 +143,6 @@ def hex_problem(nx, p, kind, perturb=0.1, seed=1, **kw):
     cn, nnode = fi.hex_node_map(nx, p)
     pb = oracle.Problem(oracle.HEX, m.coords, m.cell_vert, p, cn, nnode, kind, **kw)
     return pb, m, cn
-
-
-def hex_node_coords(m, cn, p):
-    """Physical positions of the Q_p nodes: trilinear image of numpy-derived GLL points."""
-    n = p + 1
-    s = exact.gll_nodes_np(n)
-    out = np.zeros((cn.max() + 1, 3))
-    X = m.coords[m.cell_vert]  # [ncell][8][3]
-    for k in range(n):
-        for j in range(n):
-            for i in range(n):
-                a = i + n * j + n * n * k
-                xi = (s[i], s[j], s[k])
-                w = np.array([(xi[0] if v & 1 else 1 - xi[0]) * (xi[1] if v & 2 else 1 - xi[1]) *
-                              (xi[2] if v & 4 else 1 - xi[2]) for v in range(8)])
-                out[cn[:, a]] = np.einsum("v,cvd->cd", w, X)
-    return out
 
 
 # ---------------------------------------------------------------- mass / Laplace / Helmholtz
@@ -374,3 +358,97 @@ def test_hyper_homogeneous_deformation_interior_balance(law):
     inside = np.all((nodes > 1e-12) & (nodes < 1 - 1e-12), axis=1)
     assert np.abs(r[inside]).max() < 1e-13
     assert np.abs(r[~inside]).max() > 1e-4
+
+
+# ---------------------------------------------------------------- vector forms on hexahedra
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_hex_elasticity_rigid_modes_and_symmetry(p):
+    """Translations and infinitesimal rotations are in the Q_p space (the trilinear map is in Q_1) and have zero
+    strain, so their action vanishes on a perturbed mesh; the operator is symmetric."""
+    pb, m, cn = hex_problem(2, p, oracle.ELASTICITY, ncomp=3, lam=1.3, mu=0.7)
+    X = hex_node_coords(m, cn, p)
+    for t in np.eye(3):
+        assert np.abs(pb.apply(np.tile(t, (pb.nnode, 1)).ravel())).max() < 1e-13
+    for w in np.eye(3):
+        assert np.abs(pb.apply(np.cross(w, X).ravel())).max() < 1e-13
+    rng = np.random.default_rng(11)
+    x, y = rng.standard_normal(pb.ndof), rng.standard_normal(pb.ndof)
+    ax = pb.apply(x)
+    assert np.abs(ax).max() > 1e-2
+    assert abs(y @ ax - x @ pb.apply(y)) < 1e-12 * np.abs(ax).max() * pb.ndof
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_hex_vector_laplacian_null_space(p):
+    """Constant vector fields are in the kernel; linear fields have zero action at interior nodes."""
+    nx = 3
+    pb, m, cn = hex_problem(nx, p, oracle.LAPLACE, ncomp=3)
+    X = hex_node_coords(m, cn, p)
+    assert np.abs(pb.apply(np.tile([1.0, -2.0, 0.5], pb.nnode))).max() < 1e-13
+    lin = X @ np.array([[1.0, 0.2, -0.3], [0.5, -1.0, 0.1], [0.0, 0.7, 2.0]]).T + np.array([0.1, 0.2, 0.3])
+    y = pb.apply(lin.ravel()).reshape(-1, 3)
+    M = nx * p + 1
+    v = np.arange(M ** 3)
+    i, j, k = v % M, (v // M) % M, v // (M * M)
+    interior = (i > 0) & (i < M - 1) & (j > 0) & (j < M - 1) & (k > 0) & (k < M - 1)
+    assert np.abs(y[interior]).max() < 1e-13
+    assert np.abs(y[~interior]).max() > 1e-3
+
+
+@pytest.mark.parametrize("law", [oracle.SVK, oracle.NEOHOOKE])
+@pytest.mark.parametrize("p", [1, 2])
+def test_hex_hyper_rigid_rotation_has_zero_residual(law, p):
+    pb, m, cn = hex_problem(2, p, oracle.HYPER_RES, ncomp=3, law=law)
+    X = hex_node_coords(m, cn, p)
+    R = _rotation(0.6, [2, -1, 1])
+    assert np.abs(pb.apply((X @ R.T - X).ravel())).max() < 1e-13
+
+
+@pytest.mark.parametrize("law", [oracle.SVK, oracle.NEOHOOKE])
+def test_hex_hyper_homogeneous_deformation_interior_balance(law):
+    """Constant F gives constant stress; Gauss with p+1 points integrates grad(phi) dx exactly on trilinear cells,
+    so interior residuals vanish."""
+    nx, p = 3, 2
+    pb, m, cn = hex_problem(nx, p, oracle.HYPER_RES, ncomp=3, law=law)
+    X = hex_node_coords(m, cn, p)
+    F0 = np.array([[1.1, 0.05, 0.0], [0.02, 0.95, 0.1], [0.0, -0.04, 1.05]])
+    r = pb.apply((X @ (F0 - np.eye(3)).T).ravel()).reshape(-1, 3)
+    M = nx * p + 1
+    v = np.arange(M ** 3)
+    i, j, k = v % M, (v // M) % M, v // (M * M)
+    interior = (i > 0) & (i < M - 1) & (j > 0) & (j < M - 1) & (k > 0) & (k < M - 1)
+    assert np.abs(r[interior]).max() < 1e-13
+    assert np.abs(r[~interior]).max() > 1e-4
+
+
+@pytest.mark.parametrize("law", [oracle.SVK, oracle.NEOHOOKE])
+def test_hex_hyper_residual_is_energy_gradient(law):
+    pb, m, cn = hex_problem(2, 2, oracle.HYPER_RES, ncomp=3, law=law, b=(0.1, -0.2, 0.3))
+    u = fi.sinusoid_displacement(hex_node_coords(m, cn, 2), seed=2).ravel()
+    r = pb.apply(u)
+    rng = np.random.default_rng(12)
+    for _ in range(3):
+        d = rng.standard_normal(pb.ndof)
+        eps = 1e-5
+        fd = (pb.energy(u + eps * d) - pb.energy(u - eps * d)) / (2 * eps)
+        assert abs(fd - r @ d) <= 1e-7 * max(1.0, abs(r @ d)), (fd, r @ d)
+
+
+@pytest.mark.parametrize("law", [oracle.SVK, oracle.NEOHOOKE])
+def test_hex_hyper_jacobian_is_residual_derivative_and_linearises_to_elasticity(law):
+    lam, mu = 1.4, 0.8
+    pbr, m, cn = hex_problem(2, 2, oracle.HYPER_RES, ncomp=3, law=law, lam=lam, mu=mu)
+    u = fi.sinusoid_displacement(hex_node_coords(m, cn, 2), seed=3).ravel()
+    pbj, _, _ = hex_problem(2, 2, oracle.HYPER_JAC, ncomp=3, law=law, lam=lam, mu=mu, ucoef=u)
+    rng = np.random.default_rng(13)
+    d = rng.standard_normal(pbr.ndof)
+    eps = 1e-6
+    fd = (pbr.apply(u + eps * d) - pbr.apply(u - eps * d)) / (2 * eps)
+    jd = pbj.apply(d)
+    assert np.linalg.norm(fd - jd) <= 1e-7 * np.linalg.norm(jd)
+    e = rng.standard_normal(pbr.ndof)
+    assert abs(e @ jd - d @ pbj.apply(e)) < 1e-11 * abs(e @ jd) + 1e-12
+    pb0, _, _ = hex_problem(2, 2, oracle.HYPER_JAC, ncomp=3, law=law, lam=lam, mu=mu, ucoef=np.zeros(pbr.ndof))
+    pbe, _, _ = hex_problem(2, 2, oracle.ELASTICITY, ncomp=3, lam=lam, mu=mu)
+    np.testing.assert_allclose(pb0.apply(d), pbe.apply(d), rtol=1e-12, atol=1e-14)
