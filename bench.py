@@ -64,8 +64,11 @@ def parse_args():
     ap.add_argument("--forms", default=None,
                     help="hex: laplace,helmholtz; hex-vector: elasticity,hyper_res,hyper_jac "
                          "(neo-Hookean residual, St Venant-Kirchhoff Jacobian action)")
-    ap.add_argument("--scatter", choices=["atomic", "colour"], default="atomic",
+    ap.add_argument("--scatter", choices=["atomic", "colour", "warp"], default="atomic",
                     help="scatter at form creation (the autotuner may change it)")
+    ap.add_argument("--order", choices=["lex", "shuffled", "rcm"], default="lex",
+                    help="cell and node numbering: generator (lexicographic), seeded random permutation, or the "
+                         "random permutation renumbered by the library's reverse Cuthill-McKee")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep each form's default launch configuration instead of timing all of them")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -77,6 +80,36 @@ FORM_IDS = {"mass": 0, "laplace": 1, "helmholtz": 2, "elasticity": 3, "hyper_res
 
 
 def workload_name(args):
+    return _workload_name(args) + ("" if args.order == "lex" else "-order-" + args.order)
+
+
+def renumber(args, cell_vert, cell_node, nnode, nvert, vectors):
+    """The maps and node vectors in the numbering `args.order` asks for.  `vectors`: node-major arrays
+    (nnode * ncomp values each) that follow the node permutation."""
+    if args.order == "lex":
+        return cell_vert, cell_node, vectors
+    cv, cn, perm = fi.shuffle_mesh(cell_vert, cell_node, nnode, seed=7)
+    if args.order == "rcm":
+        from paper_1903_08243_gb300 import build as libbuild
+
+        libbuild.build()
+        import paper_1903_08243_gb300 as mfa
+
+        order, perm2 = mfa.mfa_order_rcm(cv, cn, nnode, nvert=nvert)
+        cv, cn = mfa.apply_order(cv, cn, order, perm2)
+        perm = perm2[perm]
+    out = []
+    for v in vectors:
+        if v is None:
+            out.append(None)
+            continue
+        w = np.empty_like(v.reshape(nnode, -1))
+        w[perm] = v.reshape(nnode, -1)
+        out.append(w.ravel())
+    return cv, cn, out
+
+
+def _workload_name(args):
     if args.workload in ("hex", "hex-vector"):
         return "hex%d^3-perturbed0.1h-Q%s-%s%s-fp64" % (args.nx, args.degrees.replace(",", ""),
                                                         "vector-" if args.workload == "hex-vector" else "",
@@ -102,34 +135,38 @@ def build_cases(args):
             grid = np.stack([v % m1, (v // m1) % m1, v // (m1 * m1)], axis=1) / (m1 - 1)
             u = fi.sinusoid_displacement(grid, seed=2).ravel()  # smooth field on the node grid
             xr = fi.uniform_vector(3 * nnode, seed=1)
+            cv, cell_node, (u, xr) = renumber(args, mesh.cell_vert, cell_node, nnode, mesh.nvert, [u, xr])
             for f in args.forms.split(","):
                 kw = dict(lam=1.0, mu=1.0, law=laws[f])
                 cases.append(dict(name="Q%d %s%s" % (p, f, lawname[f]), cell_type=8, mesh=mesh, p=p, ncomp=3, form=f,
-                                  cell_node=cell_node, nnode=nnode, x=u if f == "hyper_res" else xr,
+                                  cell_vert=cv, cell_node=cell_node, nnode=nnode, x=u if f == "hyper_res" else xr,
                                   coef=u if f == "hyper_jac" else None, kw=kw, okw=kw, qdeg=p + 1))
     elif args.workload == "hex":
         mesh = fi.hex_box_mesh(args.nx, perturb=0.1, seed=1)
         for p in [int(p) for p in args.degrees.split(",")]:
             cell_node, nnode = fi.hex_node_map(args.nx, p)
             x = fi.uniform_vector(nnode, seed=1)
+            cv, cell_node, (x,) = renumber(args, mesh.cell_vert, cell_node, nnode, mesh.nvert, [x])
             for f in args.forms.split(","):
                 cases.append(dict(name="Q%d %s" % (p, f), cell_type=8, mesh=mesh, p=p, ncomp=1, form=f,
-                                  cell_node=cell_node, nnode=nnode, x=x, kw=dict(k2=1.0), okw=dict(k2=1.0),
-                                  qdeg=p + 1))
+                                  cell_vert=cv, cell_node=cell_node, nnode=nnode, x=x, kw=dict(k2=1.0),
+                                  okw=dict(k2=1.0), qdeg=p + 1))
     elif args.workload == "tet-p1-mass":
         mesh = fi.kuhn_tet_mesh(args.nx)
         x = fi.uniform_vector(mesh.nvert, seed=0)
-        cases.append(dict(name="P1 mass", cell_type=4, mesh=mesh, p=1, ncomp=1, form="mass",
-                          cell_node=mesh.cell_vert, nnode=mesh.nvert, x=x, kw={}, okw={}, qdeg=2))
+        cv, cn, (x,) = renumber(args, mesh.cell_vert, mesh.cell_vert, mesh.nvert, mesh.nvert, [x])
+        cases.append(dict(name="P1 mass", cell_type=4, mesh=mesh, p=1, ncomp=1, form="mass", cell_vert=cv,
+                          cell_node=cn, nnode=mesh.nvert, x=x, kw={}, okw={}, qdeg=2))
     else:
         mesh = fi.kuhn_tet_mesh(args.nx)
         cn, nnode, edges = fi.p2_node_map(mesh.cell_vert, mesh.nvert)
         u = fi.sinusoid_displacement(fi.p2_node_coords(mesh.coords, edges), seed=2).ravel()
+        cv, cn, (u,) = renumber(args, mesh.cell_vert, cn, nnode, mesh.nvert, [u])
         cases.append(dict(name="P2 elasticity", cell_type=4, mesh=mesh, p=2, ncomp=3, form="elasticity",
-                          cell_node=cn, nnode=nnode, x=u, kw=dict(lam=1.0, mu=1.0), okw=dict(lam=1.0, mu=1.0),
-                          qdeg=4))
+                          cell_vert=cv, cell_node=cn, nnode=nnode, x=u, kw=dict(lam=1.0, mu=1.0),
+                          okw=dict(lam=1.0, mu=1.0), qdeg=4))
         cases.append(dict(name="P2 neo-Hookean residual", cell_type=4, mesh=mesh, p=2, ncomp=3, form="hyper_res",
-                          cell_node=cn, nnode=nnode, x=u, kw=dict(lam=1.0, mu=1.0, law=1),
+                          cell_vert=cv, cell_node=cn, nnode=nnode, x=u, kw=dict(lam=1.0, mu=1.0, law=1),
                           okw=dict(lam=1.0, mu=1.0, law=1), qdeg=4))
     for c in cases:
         c["ndof"] = c["nnode"] * c["ncomp"]
@@ -231,7 +268,7 @@ def allreduce_max(world, v):
 def sub_mesh(case, ncell_sample):
     """The first cells of the mesh (a slab of boxes), with compact node numbering."""
     cells = np.arange(min(ncell_sample, case["mesh"].ncell))
-    cv, cn = case["mesh"].cell_vert[cells], case["cell_node"][cells]
+    cv, cn = case["cell_vert"][cells], case["cell_node"][cells]
     nodes, inv = np.unique(cn, return_inverse=True)
     return cv, inv.reshape(cn.shape).astype(np.int32), nodes, cells.size
 
@@ -312,12 +349,13 @@ def gpu_arm(args, world, rank, local):
     stream = torch.cuda.current_stream()
     ctx = mfa.Context(local, stream)
     cases = build_cases(args)
-    scatter = mfa.MFA_SCATTER_ATOMIC if args.scatter == "atomic" else mfa.MFA_SCATTER_COLOUR
+    scatter = {"atomic": mfa.MFA_SCATTER_ATOMIC, "colour": mfa.MFA_SCATTER_COLOUR,
+               "warp": mfa.MFA_SCATTER_WARP}[args.scatter]
     meshes, spaces, ops = {}, {}, []
     for c in cases:
-        mk = id(c["mesh"])
+        mk = (id(c["mesh"]), hashlib.sha1(np.ascontiguousarray(c["cell_vert"])).hexdigest())
         if mk not in meshes:
-            meshes[mk] = mfa.Mesh(ctx, c["cell_type"], c["mesh"].coords, c["mesh"].cell_vert)
+            meshes[mk] = mfa.Mesh(ctx, c["cell_type"], c["mesh"].coords, c["cell_vert"])
         sk = (mk, c["p"], c["ncomp"])
         if sk not in spaces:
             spaces[sk] = mfa.Space(meshes[mk], c["p"], c["ncomp"], c["cell_node"], c["nnode"])

@@ -83,7 +83,13 @@ enum { MFA_LAW_SVK = 0, MFA_LAW_NEOHOOKE = 1 };
  * arithmetic and accumulation.  x and y stay FP64 in memory for all three.
  * FP32/BF16 cover hexahedral forms with p+1 points per direction. */
 enum { MFA_PREC_FP64 = 0, MFA_PREC_FP32 = 1, MFA_PREC_BF16 = 2 };
-enum { MFA_SCATTER_AUTO = 0, MFA_SCATTER_COLOUR = 1, MFA_SCATTER_ATOMIC = 2 };
+/* Scatter-add of the local results into y (Section 2.2's INC access):
+ * COLOUR  cells of one colour share no node: plain read-modify-write, one launch
+ *         per colour, bitwise reproducible;
+ * ATOMIC  one FP64 atomic add per local dof (the default);
+ * WARP    atomic adds aggregated within a warp: lanes that add into the same
+ *         entry are summed first (FP64 point kernel with p+1 points and tets). */
+enum { MFA_SCATTER_AUTO = 0, MFA_SCATTER_COLOUR = 1, MFA_SCATTER_ATOMIC = 2, MFA_SCATTER_WARP = 3 };
 
 typedef struct {
   int32_t kind;            /* MFA_FORM_*                                               */
@@ -174,7 +180,7 @@ MFA_API int mfa_form_destroy(mfa_form *form);
  *             MFA_VARIANT_CELL   one thread per cell (tets).
  *  - cells_per_block: cells one thread block processes together (tets:
  *    threads per block); 0 in mfa_form_set_config = the variant's default.
- *  - scatter: MFA_SCATTER_ATOMIC or MFA_SCATTER_COLOUR (FP64 only).
+ *  - scatter: MFA_SCATTER_ATOMIC, or (FP64 only) MFA_SCATTER_COLOUR or MFA_SCATTER_WARP.
  *  - ms: mean time of one apply measured by mfa_form_autotune (else 0). */
 enum {
   MFA_VARIANT_AUTO = 0,
@@ -336,6 +342,20 @@ MFA_API int mfa_batch_create(mfa_ctx *ctx, int n, mfa_form *const *forms, const 
 MFA_API int mfa_batch_apply(mfa_ctx *ctx, mfa_batch *batch);
 MFA_API int mfa_batch_info(const mfa_batch *batch, int *ngroups, int *nsingles);
 MFA_API int mfa_batch_destroy(mfa_batch *batch);
+
+/* Locality-restoring renumbering (host only, no device): reverse Cuthill-McKee
+ * on the cell graph (cells adjacent when they share a vertex), then nodes
+ * numbered by first touch along the new cell order.  Section 2.2's gather and
+ * scatter go through the cell->node map; an arbitrary mesh order scatters
+ * them over all of x and y, this brings consecutive cells' nodes together.
+ * Inputs as for mfa_mesh_upload / mfa_space_create (nv = 4 or 8 vertices per
+ * cell, nloc nodes per cell).  Outputs (caller-allocated): cell_order[ncell],
+ * cell_order[new] = old cell; node_perm[nnode], node_perm[old] = new node.
+ * Apply both to the maps (new cell_node[i] = node_perm[old cell_node[cell_order[i]]])
+ * and to the node vectors before upload.  MFA_ERR_RANGE on an index outside
+ * [0, nvert) or [0, nnode). */
+MFA_API int mfa_order_rcm(int64_t ncell, int nv, const int32_t *cell_vert, int64_t nvert, int nloc,
+                          const int32_t *cell_node, int64_t nnode, int32_t *cell_order, int32_t *node_perm);
 
 /* mfa_cg without device allocation.  The paper has no counterpart: this is
  * for callers that cannot call cudaMalloc (an application whose memory pool

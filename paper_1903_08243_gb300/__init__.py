@@ -22,7 +22,7 @@ MFA_FORM_MASS, MFA_FORM_LAPLACE, MFA_FORM_HELMHOLTZ = 0, 1, 2
 MFA_FORM_ELASTICITY, MFA_FORM_HYPER_RES, MFA_FORM_HYPER_JAC = 3, 4, 5
 MFA_LAW_SVK, MFA_LAW_NEOHOOKE = 0, 1
 MFA_PREC_FP64, MFA_PREC_FP32, MFA_PREC_BF16 = 0, 1, 2
-MFA_SCATTER_AUTO, MFA_SCATTER_COLOUR, MFA_SCATTER_ATOMIC = 0, 1, 2
+MFA_SCATTER_AUTO, MFA_SCATTER_COLOUR, MFA_SCATTER_ATOMIC, MFA_SCATTER_WARP = 0, 1, 2, 3
 MFA_PC_NONE, MFA_PC_JACOBI = 0, 1
 MFA_PRECOND_MLP, MFA_PRECOND_LINEAR = 0, 1
 (MFA_VARIANT_AUTO, MFA_VARIANT_POINT, MFA_VARIANT_EVEN_ODD, MFA_VARIANT_LINE, MFA_VARIANT_LINE_STAGED,
@@ -77,7 +77,8 @@ class mfa_launch_config(ctypes.Structure):
 
     def as_dict(self):
         return {"variant": VARIANT_NAMES.get(self.variant, self.variant), "cells_per_block": self.cells_per_block,
-                "scatter": "colour" if self.scatter == MFA_SCATTER_COLOUR else "atomic", "ms": self.ms}
+                "scatter": {MFA_SCATTER_COLOUR: "colour", MFA_SCATTER_WARP: "warp"}.get(self.scatter, "atomic"),
+                "ms": self.ms}
 
 
 _lib = None
@@ -128,6 +129,7 @@ _SIGS = {
     "mfa_batch_apply": ([_VP, _VP], _I),
     "mfa_batch_info": ([_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "mfa_batch_destroy": ([_VP], _I),
+    "mfa_order_rcm": ([_I64, _I, _VP, _I64, _I, _VP, _I64, _VP, _VP], _I),
     "mfa_cg_noalloc": ([_VP, _VP, _I, _VP, _VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
 }
 MFA_CG_NOALLOC_MAX_NDOF = 262144
@@ -237,6 +239,29 @@ def mfa_form_get_info(form):
 
 def mfa_form_destroy(form):
     _check(lib().mfa_form_destroy(form))
+
+
+def mfa_order_rcm(cell_vert, cell_node, nnode, nvert=None):
+    """Reverse Cuthill-McKee renumbering (host): returns (cell_order, node_perm) with
+    cell_order[new] = old cell and node_perm[old] = new node."""
+    cv = np.ascontiguousarray(cell_vert, dtype=np.int32)
+    cn = np.ascontiguousarray(cell_node, dtype=np.int32)
+    ncell, nv = cv.shape
+    nloc = cn.shape[1]
+    if nvert is None:
+        nvert = int(cv.max()) + 1 if cv.size else 0
+    cell_order = np.empty(ncell, dtype=np.int32)
+    node_perm = np.empty(int(nnode), dtype=np.int32)
+    _check(lib().mfa_order_rcm(ncell, nv, cv.ctypes.data, int(nvert), nloc, cn.ctypes.data, int(nnode),
+                               cell_order.ctypes.data, node_perm.ctypes.data))
+    return cell_order, node_perm
+
+
+def apply_order(cell_vert, cell_node, cell_order, node_perm):
+    """Maps in the new numbering: cells in cell_order, node ids through node_perm."""
+    cv = np.ascontiguousarray(np.asarray(cell_vert)[cell_order])
+    cn = np.ascontiguousarray(node_perm[np.asarray(cell_node)[cell_order]]).astype(np.int32)
+    return cv, cn
 
 
 def mfa_form_list_configs(form):

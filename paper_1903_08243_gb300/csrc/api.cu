@@ -260,14 +260,16 @@ int apply_form(mfa_form* f, const double* x, double* y, cudaStream_t stream) {
                  : mfa::hex_vector_launch_b(n, f->p.kind, f->p.law, colour, f->hex, a, ctx->sm_count, stream);
     } else if (sp->mesh->cell_type == MFA_CELL_HEX8) {
       mfa::HexApplyArgs a{x, y, sp->d_cell_node, f->d_geom, list, count, ctx->d_err, f->gstride};
-      e = mfa::hex_apply_launch(sp->degree + 1, f->nq1, f->p.kind, f->p.precision, colour, f->launch, f->hex, a,
+      mfa::LaunchConfig lc = f->launch;
+      lc.agg = f->scatter == MFA_SCATTER_WARP;
+      e = mfa::hex_apply_launch(sp->degree + 1, f->nq1, f->p.kind, f->p.precision, colour, lc, f->hex, a,
                                 ctx->sm_count, stream);
     } else {
       mfa::TetApplyArgs a = tet_args(f, x, y);
       a.cell_list = list;
       a.count = count;
-      e = mfa::tet_apply_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, f->launch.cb ? f->launch.cb : 128,
-                                f->tet, a, ctx->sm_count, stream);
+      e = mfa::tet_apply_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, f->scatter == MFA_SCATTER_WARP,
+                                f->launch.cb ? f->launch.cb : 128, f->tet, a, ctx->sm_count, stream);
     }
     if (e != cudaSuccess) return fail(MFA_ERR_CUDA, "apply kernel launch: %s", cudaGetErrorString(e));
   }
@@ -455,17 +457,23 @@ static std::vector<mfa_launch_config> form_configs(const mfa_form* f) {
   else if (f->p.precision == MFA_PREC_FP64) variants = {MFA_VARIANT_POINT, MFA_VARIANT_EVEN_ODD};
   else variants = {MFA_VARIANT_LINE, MFA_VARIANT_LINE_STAGED};
   const bool colour_ok = f->p.precision == MFA_PREC_FP64;
+  const int n = f->space->degree + 1;
   for (int v : variants) {
     int opts[4];
     const int nopt = cb_options(f, v, opts);
-    for (int i = 0; i < nopt; ++i)
-      for (int sc = 0; sc < (colour_ok ? 2 : 1); ++sc) {
+    for (int i = 0; i < nopt; ++i) {
+      // warp-aggregated scatter: tets, and the scalar point kernel with p+1 points at its default cells per block
+      const bool warp_ok = colour_ok && (v == MFA_VARIANT_CELL || (v == MFA_VARIANT_POINT && f->space->ncomp == 1 &&
+                                                                   f->nq1 == n && i == 0));
+      const int scatters[3] = {MFA_SCATTER_ATOMIC, MFA_SCATTER_COLOUR, MFA_SCATTER_WARP};
+      for (int sc = 0; sc < (colour_ok ? (warp_ok ? 3 : 2) : 1); ++sc) {
         mfa_launch_config c{};
         c.variant = v;
         c.cells_per_block = opts[i];
-        c.scatter = sc == 0 ? MFA_SCATTER_ATOMIC : MFA_SCATTER_COLOUR;
+        c.scatter = scatters[sc];
         all.push_back(c);
       }
+    }
   }
   // move the creation-time configuration to the front
   int dopts[4];
@@ -485,13 +493,13 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
   const double t0 = now_ms();
   const int kind = prm->kind, ct = sp->mesh->cell_type;
   if (kind < MFA_FORM_MASS || kind > MFA_FORM_HYPER_JAC) return fail(MFA_ERR_ARG, "mfa_form_create: kind %d", kind);
-  if (prm->scatter < MFA_SCATTER_AUTO || prm->scatter > MFA_SCATTER_ATOMIC)
+  if (prm->scatter < MFA_SCATTER_AUTO || prm->scatter > MFA_SCATTER_WARP)
     return fail(MFA_ERR_ARG, "mfa_form_create: scatter %d", prm->scatter);
   if (prm->law != MFA_LAW_SVK && prm->law != MFA_LAW_NEOHOOKE) return fail(MFA_ERR_ARG, "mfa_form_create: law %d", prm->law);
   if (prm->precision < MFA_PREC_FP64 || prm->precision > MFA_PREC_BF16)
     return fail(MFA_ERR_ARG, "mfa_form_create: precision %d", prm->precision);
   if (prm->precision != MFA_PREC_FP64 && (ct != MFA_CELL_HEX8 || (prm->qdeg > 0 && prm->qdeg != sp->degree + 1) ||
-                                          prm->scatter == MFA_SCATTER_COLOUR))
+                                          prm->scatter == MFA_SCATTER_COLOUR || prm->scatter == MFA_SCATTER_WARP))
     return fail(MFA_ERR_UNSUPPORTED,
                 "mfa_form_create: FP32/BF16 cover hex forms with p+1 points per direction and the atomic scatter");
   if (kind >= MFA_FORM_ELASTICITY && sp->ncomp != 3)
@@ -515,9 +523,15 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
   f->ctx = ctx;
   f->space = sp;
   f->p = *prm;
-  f->scatter = prm->scatter == MFA_SCATTER_COLOUR ? MFA_SCATTER_COLOUR : MFA_SCATTER_ATOMIC;
+  f->scatter = prm->scatter == MFA_SCATTER_AUTO ? MFA_SCATTER_ATOMIC : prm->scatter;
   f->launch.variant = default_variant(sp, prm->qdeg > 0 ? prm->qdeg : sp->degree + 1, prm->precision);
   int rc = MFA_OK;
+  if (f->scatter == MFA_SCATTER_WARP) {
+    // the warp-aggregated scatter is compiled for the point kernel (scalar hex, p+1 points) and the tet kernels
+    if (ct == MFA_CELL_HEX8 && (sp->ncomp != 1 || (prm->qdeg > 0 && prm->qdeg != sp->degree + 1)))
+      rc = fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: warp-aggregated scatter on this hex form");
+    if (ct == MFA_CELL_HEX8) f->launch.variant = MFA_VARIANT_POINT;
+  }
   if (prm->cells_per_block != 0) {
     int opts[4];
     const int nopt = cb_options(f, f->launch.variant, opts);

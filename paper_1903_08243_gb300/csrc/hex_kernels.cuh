@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 
 #include "mfa_internal.h"
+#include "scatter.cuh"
 
 namespace mfa {
 namespace hexk {
@@ -116,7 +117,7 @@ struct Smem {
 
 // One batch of CB cells of one form: gather, sum-factorised local kernel,
 // scatter.  Every thread of the block calls it (it contains barriers).
-template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0>
+template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0, bool AGG = false>
 __device__ __forceinline__ void hex_cell_batch(const HexApplyArgs& a, int64_t batch,
                                                const Smem<N, NQ, PREC, CBX>& sm) {
   using S = Shape<N, NQ, 8, CBX>;
@@ -241,6 +242,8 @@ __device__ __forceinline__ void hex_cell_batch(const HexApplyArgs& a, int64_t ba
       for (int m = 0; m < NQ; ++m) s = fma(sB[m * N + i], A[m + NQ * bc], s);
       if constexpr (COLOUR) {
         a.y[node] += (double)s;  // no other cell of this colour touches `node`
+      } else if constexpr (AGG) {
+        warp_aggregated_add(a.y, node, (double)s);
       } else {
         atomicAdd(a.y + node, (double)s);
       }
@@ -249,7 +252,7 @@ __device__ __forceinline__ void hex_cell_batch(const HexApplyArgs& a, int64_t ba
   }
 }
 
-template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0>
+template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0, bool AGG = false>
 __global__ void __launch_bounds__(Shape<N, NQ, 8, CBX>::T) hex_apply_kernel(const __grid_constant__ HexTables tb,
                                                                            const HexApplyArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(Shape<N, NQ, 8, CBX>::T) hex_apply_kernel(cons
   constexpr int CB = Shape<N, NQ, 8, CBX>::CB;
   const int64_t nbatch = (a.count + CB - 1) / CB;
   for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x)
-    hex_cell_batch<N, NQ, KIND, COLOUR, PREC, CBX>(a, batch, sm);
+    hex_cell_batch<N, NQ, KIND, COLOUR, PREC, CBX, AGG>(a, batch, sm);
 }
 
 // Many forms of one (n, nq, kind, precision) class in one persistent launch:
@@ -281,10 +284,10 @@ __global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_group_kernel(const 
   }
 }
 
-template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0>
+template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0, bool AGG = false>
 cudaError_t launch_apply(const HexTables& tb, const HexApplyArgs& a, int sm_count, cudaStream_t s) {
   using S = Shape<N, NQ, (int)sizeof(typename Prec<PREC>::T), CBX>;
-  auto kern = hex_apply_kernel<N, NQ, KIND, COLOUR, PREC, CBX>;
+  auto kern = hex_apply_kernel<N, NQ, KIND, COLOUR, PREC, CBX, AGG>;
   static int blocks_per_sm = -1;
   if (blocks_per_sm < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);

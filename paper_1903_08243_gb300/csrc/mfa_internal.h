@@ -103,6 +103,7 @@ inline bool hex_use_eo(int n, int nq, int prec) { return prec == MFA_PREC_FP64 &
 struct LaunchConfig {
   int variant = MFA_VARIANT_AUTO;
   int cb = 0;
+  bool agg = false;  // warp-aggregated atomic scatter (MFA_SCATTER_WARP)
 };
 // Cells per block of a kernel with `per_cell` threads per cell for a target block size.
 constexpr int cells_for_target(int per_cell, int target) { return target / per_cell > 0 ? target / per_cell : 1; }
@@ -116,6 +117,8 @@ cudaError_t hex_point_launch_cb(int n, int nq, int kind, bool colour, int cb, co
                                 const HexApplyArgs& a, int sm_count, cudaStream_t s);
 cudaError_t hex_eo_apply_launch_cb(int n, int kind, bool colour, int cb, const HexApplyArgs& a, int sm_count,
                                    cudaStream_t s);
+cudaError_t hex_point_launch_agg(int n, int nq, int kind, const HexTables& tb, const HexApplyArgs& a, int sm_count,
+                                 cudaStream_t s);
 // FP32/BF16 action with float vectors.
 cudaError_t hex_apply_launch_f32(int n, int kind, int prec, const float* x, float* y, const int32_t* cell_node,
                                  const void* geom, int64_t count, int64_t gstride, int* err, int sm_count,
@@ -155,8 +158,8 @@ struct TetApplyArgs {
 };
 
 // threads: threads (cells) per block, one of tet_cb_options.
-cudaError_t tet_apply_launch(int p, int ncomp, int kind, int law, bool colour, int threads, const TetTables& tb,
-                             const TetApplyArgs& a, int sm_count, cudaStream_t s);
+cudaError_t tet_apply_launch(int p, int ncomp, int kind, int law, bool colour, bool agg, int threads,
+                             const TetTables& tb, const TetApplyArgs& a, int sm_count, cudaStream_t s);
 cudaError_t tet_diagonal_launch(int p, int ncomp, int kind, const TetTables& tb, const TetApplyArgs& a,
                                 double* d, cudaStream_t s);
 

@@ -13,11 +13,13 @@
 // Jacobian action for St Venant-Kirchhoff and compressible neo-Hookean laws.
 #include "mfa_internal.h"
 #include "physics.cuh"
+#include "scatter.cuh"
 
 namespace mfa {
 namespace {
 
-template <int P, int NC, int KIND, int LAW, int NQ, bool COLOUR>
+// SC: scatter mode, 0 atomic, 1 colour (plain read-modify-write), 2 warp-aggregated atomic.
+template <int P, int NC, int KIND, int LAW, int NQ, int SC>
 __global__ void __launch_bounds__(128) tet_apply_kernel(const __grid_constant__ TetTables tb, const TetApplyArgs a) {
   constexpr int NL = P == 1 ? 4 : 10;
   constexpr bool kValue = (KIND == MFA_FORM_MASS || KIND == MFA_FORM_HELMHOLTZ);
@@ -159,9 +161,10 @@ __global__ void __launch_bounds__(128) tet_apply_kernel(const __grid_constant__ 
     for (int i = 0; i < NL; ++i)
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        double* dst = a.y + (int64_t)NC * node[i] + c;
-        if constexpr (COLOUR) *dst += yl[i][c];
-        else atomicAdd(dst, yl[i][c]);
+        const int64_t at = (int64_t)NC * node[i] + c;
+        if constexpr (SC == 1) a.y[at] += yl[i][c];
+        else if constexpr (SC == 2) warp_aggregated_add(a.y, at, yl[i][c]);
+        else atomicAdd(a.y + at, yl[i][c]);
       }
   }
 }
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(128) tet_apply_kernel(const __grid_constant__ 
 // instead of 120), mapped back once per cell.  The body force term is
 // -b |det J| sum_q w_q phi_a(xi_q).  Same quadrature and physics as
 // tet_apply_kernel; only the order of the sums changes.
-template <int KIND, int LAW, bool COLOUR>
+template <int KIND, int LAW, int SC>
 __global__ void __launch_bounds__(128) tet_moment_kernel(const __grid_constant__ TetTables tb, const TetApplyArgs a) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < a.count;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -302,9 +305,10 @@ __global__ void __launch_bounds__(128) tet_moment_kernel(const __grid_constant__
 #pragma unroll
           for (int f = 0; f < 3; ++f) s = fma(tb.beta[i * 9 + e * 3 + f], H1[f][c][e], s);
         }
-        double* dst = a.y + 3 * (int64_t)node[i] + c;
-        if constexpr (COLOUR) *dst += s;
-        else atomicAdd(dst, s);
+        const int64_t at = 3 * (int64_t)node[i] + c;
+        if constexpr (SC == 1) a.y[at] += s;
+        else if constexpr (SC == 2) warp_aggregated_add(a.y, at, s);
+        else atomicAdd(a.y + at, s);
       }
   }
 }
@@ -330,25 +334,28 @@ cudaError_t launch_cells(Kern kern, int (&bps)[4], int threads, const TetTables&
   return cudaGetLastError();
 }
 
+// sc: scatter mode as for the kernels (0 atomic, 1 colour, 2 warp-aggregated)
 template <int KIND, int LAW>
-cudaError_t launch_moment(bool colour, int threads, const TetTables& tb, const TetApplyArgs& a, int sm_count,
+cudaError_t launch_moment(int sc, int threads, const TetTables& tb, const TetApplyArgs& a, int sm_count,
                           cudaStream_t s) {
-  static int bps[2][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}};  // per scatter variant and block size
-  return colour ? launch_cells(tet_moment_kernel<KIND, LAW, true>, bps[1], threads, tb, a, sm_count, s)
-                : launch_cells(tet_moment_kernel<KIND, LAW, false>, bps[0], threads, tb, a, sm_count, s);
+  static int bps[3][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}, {-1, -1, -1, -1}};  // per scatter mode and block size
+  if (sc == 1) return launch_cells(tet_moment_kernel<KIND, LAW, 1>, bps[1], threads, tb, a, sm_count, s);
+  if (sc == 2) return launch_cells(tet_moment_kernel<KIND, LAW, 2>, bps[2], threads, tb, a, sm_count, s);
+  return launch_cells(tet_moment_kernel<KIND, LAW, 0>, bps[0], threads, tb, a, sm_count, s);
 }
 
-template <int P, int NC, int KIND, int LAW, int NQ, bool COLOUR>
+template <int P, int NC, int KIND, int LAW, int NQ, int SC>
 cudaError_t launch(int threads, const TetTables& tb, const TetApplyArgs& a, int sm_count, cudaStream_t s) {
   static int bps[4] = {-1, -1, -1, -1};
-  return launch_cells(tet_apply_kernel<P, NC, KIND, LAW, NQ, COLOUR>, bps, threads, tb, a, sm_count, s);
+  return launch_cells(tet_apply_kernel<P, NC, KIND, LAW, NQ, SC>, bps, threads, tb, a, sm_count, s);
 }
 
 template <int P, int NC, int KIND, int LAW, int NQ>
-cudaError_t launch2(bool colour, int threads, const TetTables& tb, const TetApplyArgs& a, int sm_count,
+cudaError_t launch2(int sc, int threads, const TetTables& tb, const TetApplyArgs& a, int sm_count,
                     cudaStream_t s) {
-  return colour ? launch<P, NC, KIND, LAW, NQ, true>(threads, tb, a, sm_count, s)
-                : launch<P, NC, KIND, LAW, NQ, false>(threads, tb, a, sm_count, s);
+  if (sc == 1) return launch<P, NC, KIND, LAW, NQ, 1>(threads, tb, a, sm_count, s);
+  if (sc == 2) return launch<P, NC, KIND, LAW, NQ, 2>(threads, tb, a, sm_count, s);
+  return launch<P, NC, KIND, LAW, NQ, 0>(threads, tb, a, sm_count, s);
 }
 
 // Diagonal of the linear forms, per local dof and cell:
@@ -418,32 +425,33 @@ int tet_cb_options(int* out) {
   return 3;
 }
 
-cudaError_t tet_apply_launch(int p, int ncomp, int kind, int law, bool colour, int threads, const TetTables& tb,
-                             const TetApplyArgs& a, int sm_count, cudaStream_t s) {
+cudaError_t tet_apply_launch(int p, int ncomp, int kind, int law, bool colour, bool agg, int threads,
+                             const TetTables& tb, const TetApplyArgs& a, int sm_count, cudaStream_t s) {
+  const int sc = colour ? 1 : (agg ? 2 : 0);
   const int nq = tb.nq;
   if (p == 1 && ncomp == 1 && nq == 4) {
     switch (kind) {
-      case MFA_FORM_MASS: return launch2<1, 1, MFA_FORM_MASS, 0, 4>(colour, threads, tb, a, sm_count, s);
-      case MFA_FORM_LAPLACE: return launch2<1, 1, MFA_FORM_LAPLACE, 0, 4>(colour, threads, tb, a, sm_count, s);
-      case MFA_FORM_HELMHOLTZ: return launch2<1, 1, MFA_FORM_HELMHOLTZ, 0, 4>(colour, threads, tb, a, sm_count, s);
+      case MFA_FORM_MASS: return launch2<1, 1, MFA_FORM_MASS, 0, 4>(sc, threads, tb, a, sm_count, s);
+      case MFA_FORM_LAPLACE: return launch2<1, 1, MFA_FORM_LAPLACE, 0, 4>(sc, threads, tb, a, sm_count, s);
+      case MFA_FORM_HELMHOLTZ: return launch2<1, 1, MFA_FORM_HELMHOLTZ, 0, 4>(sc, threads, tb, a, sm_count, s);
     }
   }
   if (p == 2 && ncomp == 1) {
-    if (kind == MFA_FORM_MASS && nq == 27) return launch2<2, 1, MFA_FORM_MASS, 0, 27>(colour, threads, tb, a, sm_count, s);
-    if (kind == MFA_FORM_LAPLACE && nq == 4) return launch2<2, 1, MFA_FORM_LAPLACE, 0, 4>(colour, threads, tb, a, sm_count, s);
+    if (kind == MFA_FORM_MASS && nq == 27) return launch2<2, 1, MFA_FORM_MASS, 0, 27>(sc, threads, tb, a, sm_count, s);
+    if (kind == MFA_FORM_LAPLACE && nq == 4) return launch2<2, 1, MFA_FORM_LAPLACE, 0, 4>(sc, threads, tb, a, sm_count, s);
     if (kind == MFA_FORM_HELMHOLTZ && nq == 27)
-      return launch2<2, 1, MFA_FORM_HELMHOLTZ, 0, 27>(colour, threads, tb, a, sm_count, s);
+      return launch2<2, 1, MFA_FORM_HELMHOLTZ, 0, 27>(sc, threads, tb, a, sm_count, s);
   }
   if (p == 2 && ncomp == 3) {
-    if (kind == MFA_FORM_LAPLACE && nq == 4) return launch2<2, 3, MFA_FORM_LAPLACE, 0, 4>(colour, threads, tb, a, sm_count, s);
+    if (kind == MFA_FORM_LAPLACE && nq == 4) return launch2<2, 3, MFA_FORM_LAPLACE, 0, 4>(sc, threads, tb, a, sm_count, s);
     if (kind == MFA_FORM_ELASTICITY && nq == 4)
-      return launch2<2, 3, MFA_FORM_ELASTICITY, 0, 4>(colour, threads, tb, a, sm_count, s);
+      return launch2<2, 3, MFA_FORM_ELASTICITY, 0, 4>(sc, threads, tb, a, sm_count, s);
     if (kind == MFA_FORM_HYPER_RES && nq == 27)
-      return law == MFA_LAW_SVK ? launch_moment<MFA_FORM_HYPER_RES, MFA_LAW_SVK>(colour, threads, tb, a, sm_count, s)
-                                : launch_moment<MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(colour, threads, tb, a, sm_count, s);
+      return law == MFA_LAW_SVK ? launch_moment<MFA_FORM_HYPER_RES, MFA_LAW_SVK>(sc, threads, tb, a, sm_count, s)
+                                : launch_moment<MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(sc, threads, tb, a, sm_count, s);
     if (kind == MFA_FORM_HYPER_JAC && nq == 27)
-      return law == MFA_LAW_SVK ? launch_moment<MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(colour, threads, tb, a, sm_count, s)
-                                : launch_moment<MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(colour, threads, tb, a, sm_count, s);
+      return law == MFA_LAW_SVK ? launch_moment<MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(sc, threads, tb, a, sm_count, s)
+                                : launch_moment<MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(sc, threads, tb, a, sm_count, s);
   }
   return cudaErrorInvalidValue;
 }
