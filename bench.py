@@ -42,7 +42,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mfa", "reference"], default="mfa")
-    ap.add_argument("--workload", choices=["hex", "hex-vector", "tet-p1-mass", "tet-p2", "batched", "pcg"],
+    ap.add_argument("--workload", choices=["hex", "hex-vector", "tet-p1-mass", "tet-p2", "batched", "pcg",
+                                           "pcg-elasticity"],
                     default="hex",
                     help="hex: 64^3 Q1-Q6 Laplace+Helmholtz; tet-p1-mass: 8^3x6 P1 mass; "
                          "tet-p2: 48^3x6 vector P2 elasticity + neo-Hookean residual; "
@@ -773,6 +774,72 @@ def pcg_arm(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def pcg_elasticity_arm(args, world, rank, local):
+    """Linear elasticity (lambda = mu = 1) on vector P2 tets, clamped on the face x = 0, loaded by a uniform body
+    force: time to ||b - A_D u|| <= 1e-8 ||b|| for FP64 CG and Jacobi-PCG (A_D: the operator with the clamped rows and
+    columns replaced by the identity)."""
+    import torch
+
+    from paper_1903_08243_gb300 import build as libbuild
+
+    libbuild.build()
+    import paper_1903_08243_gb300 as mfa
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = mfa.Context(local, stream)
+    nx = args.nx or 48
+    mesh = fi.kuhn_tet_mesh(nx)
+    cn, nnode, edges = fi.p2_node_map(mesh.cell_vert, mesh.nvert)
+    nodes = fi.p2_node_coords(mesh.coords, edges)
+    m = mfa.Mesh(ctx, mfa.MFA_CELL_TET4, mesh.coords, mesh.cell_vert)
+    sp = mfa.Space(m, 2, 3, cn, nnode)
+    A = mfa.Form(sp, mfa.MFA_FORM_ELASTICITY, lam=1.0, mu=1.0)
+    clamped = np.flatnonzero(nodes[:, 0] < 1e-12)
+    dofs = (3 * clamped[:, None] + np.arange(3)[None, :]).ravel()
+    A.set_dirichlet(dofs)
+    # load f_i = int b . phi_i for b = (0, 0, -1): minus the hyperelastic residual at u = 0 (P(I) = 0)
+    load = mfa.Form(sp, mfa.MFA_FORM_HYPER_RES, lam=1.0, mu=1.0, b=(0.0, 0.0, -1.0))
+    b = -load.apply(torch.zeros(3 * nnode, dtype=torch.float64, device="cuda"))
+    b[torch.from_numpy(dofs).cuda()] = 0.0
+    ctx.sync()
+    rtol = 1e-8
+    rows = []
+    sampler = ClockSampler(local)
+    sampler.start()
+    for r in range(args.nrhs + 1):  # the first solve of each method warms up and is not reported
+        res = {}
+        for name, pc in (("cg_fp64", mfa.MFA_PC_NONE), ("jacobi_pcg_fp64", mfa.MFA_PC_JACOBI)):
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, it, rel = mfa.mfa_cg(ctx.h, A.h, pc, b, x, rtol, 50000)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            true_rel = float(torch.linalg.norm(b - A.apply(x)) / torch.linalg.norm(b))
+            res[name] = {"seconds": dt, "iterations": it, "relres": rel, "true_relres": true_rel, "status": rc,
+                         "ms_per_iteration": dt * 1e3 / max(it, 1)}
+        if r > 0:
+            rows.append(res)
+    clocks = sampler.stop()
+    tc = statistics.mean(r["cg_fp64"]["seconds"] for r in rows)
+    tj = statistics.mean(r["jacobi_pcg_fp64"]["seconds"] for r in rows)
+    if rank == 0:
+        line = {
+            "metric": "PCG time-to-1e-8", "value": tj, "unit": "s", "n_gpus": world, "steps": args.nrhs,
+            "warmup": 1, "ms_per_step": tj * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "pcg-elasticity-tet-kuhn%d^3x6-P2vec-clamped" % nx, "ndof": 3 * nnode,
+                       "constrained_dofs": int(dofs.size), "lambda": 1.0, "mu": 1.0,
+                       "rhs": "f_i = int b . phi_i, b = (0, 0, -1); zero at the clamped dofs",
+                       "boundary": "clamped (u = 0) on the face x = 0, traction-free elsewhere",
+                       "stop": "FP64 ||b - A_D u||_2 <= 1e-8 ||b||_2 from u = 0"},
+            "cg_fp64_seconds": tc, "jacobi_pcg_fp64_seconds": tj, "jacobi_speedup": tc / tj, "solves": rows,
+            "clocks": clocks, "roofline": None, "cpu_baseline": None, "e2e": None,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.precision is None:
@@ -786,6 +853,8 @@ def main():
         batched_arm(args, world, rank, local)
     elif args.workload == "pcg" and args.impl != "reference":
         pcg_arm(args, world, rank, local)
+    elif args.workload == "pcg-elasticity" and args.impl != "reference":
+        pcg_elasticity_arm(args, world, rank, local)
     elif args.impl == "reference":
         reference_arm(args, world, rank)
     else:

@@ -161,6 +161,19 @@ MFA_API int mfa_form_set_coefficient(mfa_form *form, const double *u);
 MFA_API int mfa_form_get_info(const mfa_form *form, mfa_form_info *info);
 MFA_API int mfa_form_destroy(mfa_form *form);
 
+/* Dirichlet constraints on `dofs` (host, n entries in [0, ndof); n = 0
+ * removes them).  The form then acts as A_D x = R A R x + (I - R) x, R the
+ * diagonal projection that zeroes the constrained dofs: the operator with
+ * the constrained rows and columns replaced by the identity, symmetric
+ * positive definite for elasticity with a clamped face (the rigid modes of
+ * the unconstrained operator are gone).  mfa_apply, mfa_cg, mfa_cg_noalloc
+ * and mfa_diagonal (1 at constrained dofs) follow it; a right-hand side for
+ * zero prescribed values has zeros at the constrained dofs.  Allocates 17
+ * bytes per dof on the device; synchronises the context stream.
+ * mfa_apply_f32, mfa_fcg_mixed and mfa_fcg_learned return MFA_ERR_UNSUPPORTED
+ * for constrained forms; set constraints before mfa_batch_create. */
+MFA_API int mfa_form_set_dirichlet(mfa_form *form, const int32_t *dofs, int64_t n);
+
 /* Launch configuration of a form and its autotuner.  The paper picks its
  * batch size (cells per SIMD vector) by the hardware's vector width
  * (Section 4.1); on the GPU the thread-to-data mapping, the number of cells a

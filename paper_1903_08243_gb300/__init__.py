@@ -99,6 +99,7 @@ _SIGS = {
     "mfa_form_set_coefficient": ([_VP, _VP], _I),
     "mfa_form_get_info": ([_VP, ctypes.POINTER(mfa_form_info)], _I),
     "mfa_form_destroy": ([_VP], _I),
+    "mfa_form_set_dirichlet": ([_VP, _VP, _I64], _I),
     "mfa_form_list_configs": ([_VP, _VP, _I, ctypes.POINTER(_I)], _I),
     "mfa_form_get_config": ([_VP, ctypes.POINTER(mfa_launch_config)], _I),
     "mfa_form_set_config": ([_VP, ctypes.POINTER(mfa_launch_config)], _I),
@@ -262,6 +263,11 @@ def apply_order(cell_vert, cell_node, cell_order, node_perm):
     cv = np.ascontiguousarray(np.asarray(cell_vert)[cell_order])
     cn = np.ascontiguousarray(node_perm[np.asarray(cell_node)[cell_order]]).astype(np.int32)
     return cv, cn
+
+
+def mfa_form_set_dirichlet(form, dofs):
+    d = np.ascontiguousarray(dofs, dtype=np.int32)
+    _check(lib().mfa_form_set_dirichlet(form, d.ctypes.data if d.size else None, d.size))
 
 
 def mfa_form_list_configs(form):
@@ -529,6 +535,9 @@ class Form:
 
     def info(self):
         return mfa_form_get_info(self.h)
+
+    def set_dirichlet(self, dofs):
+        mfa_form_set_dirichlet(self.h, dofs)
 
     def configs(self):
         return mfa_form_list_configs(self.h)

@@ -243,7 +243,23 @@ mfa::TetApplyArgs tet_args(mfa_form* f, const double* x, double* y) {
 namespace mfa {
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
+static int apply_form_raw(mfa_form* f, const double* x, double* y, cudaStream_t stream);
+
+// y += A x, or with Dirichlet constraints y += R A R x + (I - R) x (R zeroes the constrained dofs).
 int apply_form(mfa_form* f, const double* x, double* y, cudaStream_t stream) {
+  clear_stale_error();
+  if (!f->d_dir_mask) return apply_form_raw(f, x, y, stream);
+  const int64_t n = f->space->nnode * f->space->ncomp;
+  cudaError_t e = dirichlet_mask_launch(x, f->d_dir_mask, f->d_dir_x, n, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f->d_dir_y, 0, sizeof(double) * n, stream);
+  if (e != cudaSuccess) return fail(MFA_ERR_CUDA, "constrained apply: %s", cudaGetErrorString(e));
+  const int rc = apply_form_raw(f, f->d_dir_x, f->d_dir_y, stream);
+  if (rc) return rc;
+  e = dirichlet_combine_launch(f->d_dir_y, x, f->d_dir_mask, y, n, stream);
+  return e == cudaSuccess ? MFA_OK : fail(MFA_ERR_CUDA, "constrained apply: %s", cudaGetErrorString(e));
+}
+
+static int apply_form_raw(mfa_form* f, const double* x, double* y, cudaStream_t stream) {
   mfa_space* sp = f->space;
   mfa_ctx* ctx = f->ctx;
   const bool colour = f->scatter == MFA_SCATTER_COLOUR;
@@ -338,6 +354,7 @@ int mfa_mesh_upload(mfa_ctx* ctx, int cell_type, int64_t ncell, int64_t nvert, c
   mfa_mesh* m = new (std::nothrow) mfa_mesh();
   if (!m) return fail(MFA_ERR_OOM, "mfa_mesh_upload: host allocation");
   m->ctx = ctx;
+  m->device = ctx->device;
   m->cell_type = cell_type;
   m->ncell = ncell;
   m->nvert = nvert;
@@ -358,7 +375,7 @@ int mfa_mesh_upload(mfa_ctx* ctx, int cell_type, int64_t ncell, int64_t nvert, c
 
 int mfa_mesh_destroy(mfa_mesh* m) {
   if (!m) return MFA_OK;
-  cudaSetDevice(m->ctx->device);
+  cudaSetDevice(m->device);
   cudaFree(m->d_coords);
   cudaFree(m->d_cell_vert);
   delete m;
@@ -390,6 +407,7 @@ int mfa_space_create(mfa_ctx* ctx, mfa_mesh* mesh, int degree, int ncomp, const 
   mfa_space* s = new (std::nothrow) mfa_space();
   if (!s) return fail(MFA_ERR_OOM, "mfa_space_create: host allocation");
   s->ctx = ctx;
+  s->device = ctx->device;
   s->mesh = mesh;
   s->degree = degree;
   s->ncomp = ncomp;
@@ -415,7 +433,7 @@ int mfa_space_ndof(const mfa_space* s, int64_t* ndof) {
 
 int mfa_space_destroy(mfa_space* s) {
   if (!s) return MFA_OK;
-  cudaSetDevice(s->ctx->device);
+  cudaSetDevice(s->device);
   cudaFree(s->d_cell_node);
   cudaFree(s->d_colour_cells);
   delete s;
@@ -521,6 +539,7 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
   mfa_form* f = new (std::nothrow) mfa_form();
   if (!f) return fail(MFA_ERR_OOM, "mfa_form_create: host allocation");
   f->ctx = ctx;
+  f->device = ctx->device;
   f->space = sp;
   f->p = *prm;
   f->scatter = prm->scatter == MFA_SCATTER_AUTO ? MFA_SCATTER_ATOMIC : prm->scatter;
@@ -558,6 +577,7 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
       rc = cuda_alloc((void**)&f->d_geom, esz * f->gstride * sp->mesh->ncell, "geometric factors");
       const double c0 = kind == MFA_FORM_HELMHOLTZ ? prm->k2 : 1.0;
       if (!rc) {
+        mfa::clear_stale_error();
         cudaError_t e = mfa::hex_geometry_launch(f->nq1, kind, prm->precision, c0, f->hex, sp->mesh->d_coords,
                                                  sp->mesh->d_cell_vert, sp->mesh->ncell, f->d_geom, f->gstride,
                                                  ctx->d_err, ctx->stream);
@@ -597,6 +617,43 @@ int mfa_form_get_info(const mfa_form* f, mfa_form_info* info) {
   info->flops_executed = f->flops_executed;
   info->bytes = f->bytes;
   info->setup_ms = f->setup_ms;
+  return MFA_OK;
+}
+
+int mfa_form_set_dirichlet(mfa_form* f, const int32_t* dofs, int64_t n) {
+  if (!f || n < 0 || (n > 0 && !dofs)) return fail(MFA_ERR_ARG, "mfa_form_set_dirichlet: bad argument");
+  const int64_t ndof = f->space->nnode * f->space->ncomp;
+  std::vector<uint8_t> mask(ndof, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    if (dofs[i] < 0 || dofs[i] >= ndof)
+      return fail(MFA_ERR_RANGE, "mfa_form_set_dirichlet: dof %d outside [0, %lld)", dofs[i], (long long)ndof);
+    mask[dofs[i]] = 1;
+  }
+  MFA_CUDA(cudaSetDevice(f->ctx->device));
+  MFA_CUDA(cudaStreamSynchronize(f->ctx->stream));  // no apply of this form may still use the old buffers
+  cudaFree(f->d_dir_mask);
+  cudaFree(f->d_dir_x);
+  cudaFree(f->d_dir_y);
+  f->d_dir_mask = nullptr;
+  f->d_dir_x = f->d_dir_y = nullptr;
+  f->ndir = 0;
+  if (n == 0) return MFA_OK;
+  int rc = cuda_alloc((void**)&f->d_dir_mask, ndof > 0 ? ndof : 1, "dirichlet mask");
+  if (!rc) rc = cuda_alloc((void**)&f->d_dir_x, sizeof(double) * (ndof > 0 ? ndof : 1), "dirichlet work");
+  if (!rc) rc = cuda_alloc((void**)&f->d_dir_y, sizeof(double) * (ndof > 0 ? ndof : 1), "dirichlet work");
+  if (!rc && cudaMemcpy(f->d_dir_mask, mask.data(), ndof, cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = fail(MFA_ERR_CUDA, "mfa_form_set_dirichlet: upload");
+  if (rc) {
+    cudaFree(f->d_dir_mask);
+    cudaFree(f->d_dir_x);
+    cudaFree(f->d_dir_y);
+    f->d_dir_mask = nullptr;
+    f->d_dir_x = f->d_dir_y = nullptr;
+    return rc;
+  }
+  int64_t count = 0;
+  for (uint8_t m : mask) count += m;
+  f->ndir = count;
   return MFA_OK;
 }
 
@@ -713,8 +770,11 @@ int mfa_form_autotune(mfa_ctx* ctx, mfa_form* f, const double* x, double* y, int
 
 int mfa_form_destroy(mfa_form* f) {
   if (!f) return MFA_OK;
-  cudaSetDevice(f->ctx->device);
+  cudaSetDevice(f->device);
   cudaFree(f->d_geom);
+  cudaFree(f->d_dir_mask);
+  cudaFree(f->d_dir_x);
+  cudaFree(f->d_dir_y);
   cudaFree(f->d_stage_x);
   cudaFree(f->d_stage_y);
   delete f;
@@ -738,6 +798,7 @@ int mfa_apply_f32(mfa_ctx* ctx, mfa_form* f, const float* x, float* y, int accum
   if (f->ctx != ctx) return fail(MFA_ERR_ARG, "mfa_apply_f32: form belongs to another context");
   if ((const void*)x == (const void*)y) return fail(MFA_ERR_ARG, "mfa_apply_f32: x and y alias");
   if (f->p.precision == MFA_PREC_FP64) return fail(MFA_ERR_ARG, "mfa_apply_f32: needs an FP32 or BF16 form");
+  if (f->d_dir_mask) return fail(MFA_ERR_UNSUPPORTED, "mfa_apply_f32: forms with Dirichlet constraints");
   MFA_CUDA(cudaSetDevice(ctx->device));
   mfa_space* sp = f->space;
   const int64_t ndof = sp->nnode * sp->ncomp;
@@ -801,6 +862,7 @@ int mfa_diagonal(mfa_ctx* ctx, mfa_form* f, double* d) {
   mfa_space* sp = f->space;
   const int64_t ndof = sp->nnode * sp->ncomp;
   MFA_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * ndof, ctx->stream));
+  mfa::clear_stale_error();
   cudaError_t e;
   if (sp->mesh->cell_type == MFA_CELL_HEX8) {
     if (f->p.precision != MFA_PREC_FP64) return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: FP64 forms only");
@@ -812,6 +874,7 @@ int mfa_diagonal(mfa_ctx* ctx, mfa_form* f, double* d) {
     mfa::TetApplyArgs a = tet_args(f, nullptr, nullptr);
     e = mfa::tet_diagonal_launch(sp->degree, sp->ncomp, f->p.kind, f->tet, a, d, ctx->stream);
   }
+  if (e == cudaSuccess && f->d_dir_mask) e = mfa::dirichlet_diag_launch(f->d_dir_mask, d, ndof, ctx->stream);
   if (e != cudaSuccess) return fail(MFA_ERR_CUDA, "diagonal kernel: %s", cudaGetErrorString(e));
   return MFA_OK;
 }

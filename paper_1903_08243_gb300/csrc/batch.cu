@@ -15,6 +15,7 @@
 
 struct mfa_batch {
   mfa_ctx* ctx = nullptr;
+  int device = 0;  // CUDA device of the handle's memory (destroy does not read ctx)
   struct Group {
     int n, kind, prec;
     mfa::HexTables tb;
@@ -54,6 +55,7 @@ int enqueue(mfa_batch* b, cudaStream_t s) {
 
 int build(mfa_ctx* ctx, int n, mfa_form* const* forms, const double* const* xs, double* const* ys, mfa_batch* b) {
   b->ctx = ctx;
+  b->device = ctx->device;
   std::map<std::tuple<int, int, int>, std::vector<int>> classes;
   for (int k = 0; k < n; ++k) {
     mfa_form* f = forms[k];
@@ -65,7 +67,7 @@ int build(mfa_ctx* ctx, int n, mfa_form* const* forms, const double* const* xs, 
     b->forms.push_back(f);
     b->xs.push_back(xs[k]);
     b->ys.push_back(ys[k]);
-    const bool groupable = f->space->mesh->cell_type == MFA_CELL_HEX8 && f->space->ncomp == 1 &&
+    const bool groupable = f->space->mesh->cell_type == MFA_CELL_HEX8 && f->space->ncomp == 1 && !f->d_dir_mask &&
                            f->scatter == MFA_SCATTER_ATOMIC && f->nq1 == f->space->degree + 1;
     if (groupable) classes[{f->space->degree + 1, f->p.kind, f->p.precision}].push_back(k);
     else b->singles.push_back(k);
@@ -178,7 +180,7 @@ int mfa_batch_info(const mfa_batch* b, int* nlaunch_groups, int* nsingles) {
 
 int mfa_batch_destroy(mfa_batch* b) {
   if (!b) return MFA_OK;
-  cudaSetDevice(b->ctx->device);
+  cudaSetDevice(b->device);
   release(b);
   return MFA_OK;
 }

@@ -60,6 +60,24 @@ __global__ void mul_kernel(const double* __restrict__ a, const double* __restric
     out[i] = a[i] * b[i];
 }
 
+// Dirichlet constraints: mask[i] != 0 marks a constrained dof.
+__global__ void dir_mask_kernel(const double* __restrict__ x, const uint8_t* __restrict__ mask,
+                                double* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = mask[i] ? 0.0 : x[i];
+}
+
+__global__ void dir_combine_kernel(const double* __restrict__ ax, const double* __restrict__ x,
+                                   const uint8_t* __restrict__ mask, double* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += mask[i] ? x[i] : ax[i];
+}
+
+__global__ void dir_diag_kernel(const uint8_t* __restrict__ mask, double* __restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (mask[i]) d[i] = 1.0;
+}
+
 __global__ void recip_kernel(const double* __restrict__ a, double* __restrict__ out, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = 1.0 / a[i];
@@ -195,6 +213,25 @@ cudaError_t dot_launch(const double* a, const double* b, int64_t n, double* part
 cudaError_t axpby_launch(double alpha, const double* x, double beta, double* y, int64_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   axpby_kernel<<<grid_for(n), 256, 0, s>>>(alpha, x, beta, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t dirichlet_mask_launch(const double* x, const uint8_t* mask, double* out, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  dir_mask_kernel<<<grid_for(n), 256, 0, s>>>(x, mask, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t dirichlet_combine_launch(const double* ax, const double* x, const uint8_t* mask, double* y, int64_t n,
+                                     cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  dir_combine_kernel<<<grid_for(n), 256, 0, s>>>(ax, x, mask, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t dirichlet_diag_launch(const uint8_t* mask, double* d, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  dir_diag_kernel<<<grid_for(n), 256, 0, s>>>(mask, d, n);
   return cudaGetLastError();
 }
 

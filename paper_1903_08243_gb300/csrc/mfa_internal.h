@@ -167,6 +167,11 @@ cudaError_t tet_diagonal_launch(int p, int ncomp, int kind, const TetTables& tb,
 cudaError_t dot_launch(const double* a, const double* b, int64_t n, double* partial, double* out, cudaStream_t s);
 cudaError_t axpby_launch(double alpha, const double* x, double beta, double* y, int64_t n, cudaStream_t s);
 cudaError_t pointwise_mul_launch(const double* a, const double* b, double* out, int64_t n, cudaStream_t s);
+// Dirichlet constraints (mask[i] != 0: constrained): out = R x; y += R ax + (I - R) x; d[i] = 1 where constrained.
+cudaError_t dirichlet_mask_launch(const double* x, const uint8_t* mask, double* out, int64_t n, cudaStream_t s);
+cudaError_t dirichlet_combine_launch(const double* ax, const double* x, const uint8_t* mask, double* y, int64_t n,
+                                     cudaStream_t s);
+cudaError_t dirichlet_diag_launch(const uint8_t* mask, double* d, int64_t n, cudaStream_t s);
 cudaError_t reciprocal_launch(const double* a, double* out, int64_t n, cudaStream_t s);
 cudaError_t convert_d2f_launch(const double* x, float* y, int64_t n, cudaStream_t s);
 cudaError_t dot32_launch(const float* a, const float* b, int64_t n, double* partial, double* out, cudaStream_t s);
@@ -185,6 +190,9 @@ int dot_partials();
 
 // Record `msg` as the calling thread's mfa_last_error() and return `code`.
 int set_error(int code, const char* msg);
+// Drop a non-sticky error that an earlier, unrelated runtime call left behind (that call already returned it),
+// so that the cudaGetLastError after the next launch reports that launch.  A sticky device error stays.
+inline void clear_stale_error() { (void)cudaGetLastError(); }
 // z = M(r) of a learned preconditioner, float vectors, on stream s.
 int precond_apply_f32(mfa_precond* pc, const float* r, float* z, cudaStream_t s);
 bool precond_is_linear(const mfa_precond* pc);
@@ -208,6 +216,7 @@ struct mfa_ctx {
 
 struct mfa_mesh {
   mfa_ctx* ctx = nullptr;
+  int device = 0;                // CUDA device of the handle's memory (destroy does not read ctx)
   int cell_type = 0;
   int64_t ncell = 0, nvert = 0;
   double* d_coords = nullptr;
@@ -216,6 +225,7 @@ struct mfa_mesh {
 
 struct mfa_space {
   mfa_ctx* ctx = nullptr;
+  int device = 0;                // CUDA device of the handle's memory (destroy does not read ctx)
   mfa_mesh* mesh = nullptr;
   int degree = 0, ncomp = 1, nloc = 0;
   int64_t nnode = 0;
@@ -229,6 +239,7 @@ struct mfa_space {
 
 struct mfa_form {
   mfa_ctx* ctx = nullptr;
+  int device = 0;                // CUDA device of the handle's memory (destroy does not read ctx)
   mfa_space* space = nullptr;
   mfa_form_params p{};
   int nq1 = 0;                   // hex: points per direction
@@ -241,6 +252,10 @@ struct mfa_form {
   void* d_geom = nullptr;
   int64_t gstride = 0;           // elements per cell of d_geom
   const double* d_coef = nullptr;
+  uint8_t* d_dir_mask = nullptr; // Dirichlet constraints: 1 at constrained dofs (nullptr: none)
+  double* d_dir_x = nullptr;     // R x and A R x work vectors of the constrained apply
+  double* d_dir_y = nullptr;
+  int64_t ndir = 0;
   double* d_stage_x = nullptr;   // mfa_apply_host staging
   double* d_stage_y = nullptr;
   double flops = 0.0, bytes = 0.0, setup_ms = 0.0;

@@ -445,6 +445,7 @@ constexpr int kBwdSmem = 6 * kMatBytes + (kTile + kH) * 4;
 
 struct mfa_precond {
   mfa_ctx* ctx = nullptr;
+  int device = 0;  // CUDA device of the handle's memory (destroy does not read ctx)
   mfa_form* form = nullptr;
   int nloc = 0;
   int64_t ncell = 0, ndof = 0;
@@ -535,6 +536,7 @@ int mfa_precond_create(mfa_ctx* ctx, mfa_form* form, int mode, uint64_t seed, mf
   if (cudaSetDevice(ctx->device) != cudaSuccess) return mfa::set_error(MFA_ERR_CUDA, "cudaSetDevice");
   mfa_precond* pc = new mfa_precond();
   pc->ctx = ctx;
+  pc->device = ctx->device;
   pc->form = form;
   pc->linear = mode == MFA_PRECOND_LINEAR;
   pc->nloc = sp->nloc;
@@ -723,7 +725,7 @@ int mfa_precond_load(mfa_precond* pc, const char* path) {
 
 int mfa_precond_destroy(mfa_precond* pc) {
   if (!pc) return MFA_OK;
-  cudaSetDevice(pc->ctx->device);
+  cudaSetDevice(pc->device);
   void* all[] = {pc->winv, pc->dinv, pc->w, pc->grad, pc->m, pc->v, pc->b1, pc->w1, pc->w2, pc->u, pc->au,
                  pc->scal, pc->partial};
   for (void* p : all) cudaFree(p);

@@ -234,6 +234,8 @@ int fcg(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, mfa_precond* pc, int inn
 
 extern "C" int mfa_fcg_mixed(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, int inner_iters, const double* b,
                              double* x, double rtol, int maxit, int* outer_iters, int* inner_total, double* relres) {
+  if ((outer && outer->d_dir_mask) || (inner && inner->d_dir_mask))
+    return mfa::set_error(MFA_ERR_UNSUPPORTED, "mfa_fcg_mixed: forms with Dirichlet constraints");
   return fcg(ctx, outer, inner, nullptr, inner_iters, b, x, rtol, maxit, outer_iters, inner_total, relres);
 }
 
@@ -243,6 +245,8 @@ extern "C" int mfa_fcg_learned(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, m
   if (!pc) return mfa::set_error(MFA_ERR_ARG, "mfa_fcg_learned: NULL preconditioner");
   if (used_fallback) *used_fallback = 0;
   if (!ctx || !outer || !b || !x) return mfa::set_error(MFA_ERR_ARG, "mfa_fcg_learned: NULL argument");
+  if (outer->d_dir_mask || (inner && inner->d_dir_mask))
+    return mfa::set_error(MFA_ERR_UNSUPPORTED, "mfa_fcg_learned: forms with Dirichlet constraints");
   const int64_t n = outer->space->nnode * outer->space->ncomp;
   double* x0 = nullptr;  // keep the initial guess for the fallback
   if (cudaMalloc((void**)&x0, sizeof(double) * (n > 0 ? n : 1)) != cudaSuccess)

@@ -462,3 +462,23 @@ def test_batch_graph_replay(ctx):
         _check_batch(ys, refs)
     finally:
         mfa.mfa_batch_destroy(b)
+
+
+def test_handles_may_be_destroyed_after_their_context(ctx):
+    """Python's collector may finalise a context before the forms built on it (reference cycles through
+    tracebacks); destroying the form afterwards must neither touch the freed context nor leave an error
+    behind for the next launch."""
+    case = hex_case(2, 2)
+    c2 = mfa.Context(0, torch.cuda.current_stream())
+    m = mfa.Mesh(c2, case["cell_type"], case["coords"], case["cell_vert"])
+    sp = mfa.Space(m, 2, 1, case["cell_node"], case["nnode"])
+    f = mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ)
+    hf, hs, hm = f.h, sp.h, m.h
+    f.h = sp.h = m.h = None  # destroy by hand, context first
+    c2.close()
+    mfa.mfa_form_destroy(hf)
+    mfa.mfa_space_destroy(hs)
+    mfa.mfa_mesh_destroy(hm)
+    x = fi.uniform_vector(case["nnode"], seed=30)
+    ref = oracle_problem(case, "helmholtz").apply(x)
+    compare(run(ctx, gpu_form(ctx, case, "helmholtz"), x), ref)

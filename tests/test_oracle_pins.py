@@ -452,3 +452,21 @@ def test_hex_hyper_jacobian_is_residual_derivative_and_linearises_to_elasticity(
     pb0, _, _ = hex_problem(2, 2, oracle.HYPER_JAC, ncomp=3, law=law, lam=lam, mu=mu, ucoef=np.zeros(pbr.ndof))
     pbe, _, _ = hex_problem(2, 2, oracle.ELASTICITY, ncomp=3, lam=lam, mu=mu)
     np.testing.assert_allclose(pb0.apply(d), pbe.apply(d), rtol=1e-12, atol=1e-14)
+
+
+def test_elasticity_null_space_is_the_six_rigid_modes_and_clamping_removes_it():
+    """The assembled P2 elasticity matrix has exactly the 6 rigid modes as its kernel (3 translations, 3
+    infinitesimal rotations); replacing the rows and columns of a clamped face by the identity leaves an SPD
+    matrix, which is what Dirichlet-constrained CG solves."""
+    pb, m, nodes = tet_problem(2, 2, oracle.ELASTICITY, perturb=0.1, seed=9, ncomp=3, lam=1.0, mu=1.0, qdeg=4)
+    A = pb.dense()
+    ev = np.linalg.eigvalsh(0.5 * (A + A.T))
+    scale = ev.max()
+    assert np.sum(np.abs(ev) < 1e-10 * scale) == 6
+    assert ev.min() > -1e-10 * scale
+    fixed = np.flatnonzero(nodes[:, 0] < 1e-12)
+    dofs = (3 * fixed[:, None] + np.arange(3)).ravel()
+    R = np.ones(pb.ndof)
+    R[dofs] = 0.0
+    AD = R[:, None] * A * R[None, :] + np.diag(1.0 - R)
+    assert np.linalg.eigvalsh(0.5 * (AD + AD.T)).min() > 1e-6 * scale
