@@ -42,7 +42,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mfa", "reference"], default="mfa")
-    ap.add_argument("--workload", choices=["hex", "hex-vector", "tet-p1-mass", "tet-p2", "batched", "pcg",
+    ap.add_argument("--workload", choices=["hex", "hex-vector", "tet-pk", "tet-p1-mass", "tet-p2", "batched", "pcg",
                                            "pcg-elasticity"],
                     default="hex",
                     help="hex: 64^3 Q1-Q6 Laplace+Helmholtz; tet-p1-mass: 8^3x6 P1 mass; "
@@ -117,13 +117,15 @@ def _workload_name(args):
                                                         args.forms.replace(",", "+"))
     if args.workload == "tet-p1-mass":
         return "tet-kuhn%d^3x6-P1-mass-fp64" % args.nx
+    if args.workload == "tet-pk":
+        return "tet-kuhn%d^3x6-P%s-%s-fp64" % (args.nx, args.degrees.replace(",", ""), args.forms.replace(",", "+"))
     return "tet-kuhn%d^3x6-P2vec-elasticity+neohookean-residual-fp64" % args.nx
 
 
 def build_cases(args):
     """Operators of one step.  Each case holds the seeded inputs shared by the GPU and the oracle."""
     if args.nx is None:
-        args.nx = {"hex": 64, "hex-vector": 48, "tet-p1-mass": 8, "tet-p2": 48}[args.workload]
+        args.nx = {"hex": 64, "hex-vector": 48, "tet-pk": 16, "tet-p1-mass": 8, "tet-p2": 48}[args.workload]
     cases = []
     if args.workload == "hex-vector":
         mesh = fi.hex_box_mesh(args.nx, perturb=0.1, seed=1)
@@ -152,6 +154,23 @@ def build_cases(args):
                 cases.append(dict(name="Q%d %s" % (p, f), cell_type=8, mesh=mesh, p=p, ncomp=1, form=f,
                                   cell_vert=cv, cell_node=cell_node, nnode=nnode, x=x, kw=dict(k2=1.0),
                                   okw=dict(k2=1.0), qdeg=p + 1))
+    elif args.workload == "tet-pk":
+        mesh = fi.kuhn_tet_mesh(args.nx)
+        for p in [int(p) for p in args.degrees.split(",")]:
+            cn, nnode, node_coords = fi.pk_node_map(mesh.cell_vert, mesh.nvert, p)
+            nodes = node_coords(mesh.coords)
+            for f in args.forms.split(","):
+                nc = 3 if f in ("elasticity", "hyper_res", "hyper_jac") else 1
+                if nc == 3:
+                    x = fi.sinusoid_displacement(nodes, seed=2).ravel()
+                    kw = dict(lam=1.0, mu=1.0, law=1)
+                else:
+                    x = fi.uniform_vector(nnode, seed=0)
+                    kw = dict(k2=1.0)
+                cv, cnr, (x,) = renumber(args, mesh.cell_vert, cn, nnode, mesh.nvert, [x])
+                cases.append(dict(name="P%d %s" % (p, f), cell_type=4, mesh=mesh, p=p, ncomp=nc, form=f,
+                                  cell_vert=cv, cell_node=cnr, nnode=nnode, x=x, kw=kw, okw=kw,
+                                  qdeg=(max(4, 2 * p) if f.startswith("hyper") else 2 * p)))
     elif args.workload == "tet-p1-mass":
         mesh = fi.kuhn_tet_mesh(args.nx)
         x = fi.uniform_vector(mesh.nvert, seed=0)
@@ -276,36 +295,48 @@ def sub_mesh(case, ncell_sample):
 
 # Cells per oracle sample: about 1-2.5 s of oracle work per operator for the
 # baseline, about 0.1 s per operator and step for the reference arm.
-SAMPLE_BASELINE = {("hex", 1): 262144, ("hex", 2): 64000, ("hex", 3): 21952, ("hex", 4): 8000, ("hex", 5): 2744,
+SAMPLE_BASELINE = {("tet", 3): 6000, ("tet", 4): 1500, ("tet", 5): 400, ("tet", 6): 150,("hex", 1): 262144, ("hex", 2): 64000, ("hex", 3): 21952, ("hex", 4): 8000, ("hex", 5): 2744,
                    ("hex", 6): 1728, ("hex", 7): 512, ("hex", 8): 216, ("tet", 1): 3072, ("tet", 2): 200000,
                    ("hexv", 1): 110592, ("hexv", 2): 24000, ("hexv", 3): 4000, ("hexv", 4): 1000, ("hexv", 5): 250,
                    ("hexv", 6): 100}
-SAMPLE_STEP = {("hex", 1): 13824, ("hex", 2): 2744, ("hex", 3): 1000, ("hex", 4): 512, ("hex", 5): 216,
+SAMPLE_STEP = {("tet", 3): 400, ("tet", 4): 100, ("tet", 5): 30, ("tet", 6): 12,("hex", 1): 13824, ("hex", 2): 2744, ("hex", 3): 1000, ("hex", 4): 512, ("hex", 5): 216,
                ("hex", 6): 125, ("hex", 7): 64, ("hex", 8): 27, ("tet", 1): 3072, ("tet", 2): 6000,
                ("hexv", 1): 8000, ("hexv", 2): 1500, ("hexv", 3): 250, ("hexv", 4): 64, ("hexv", 5): 16,
                ("hexv", 6): 8}
 
 
 def oracle_rate(cases, repeats=1, samples=SAMPLE_STEP):
-    """Extrapolated full-mesh oracle time per operator from timing it on a sub-mesh."""
+    """Extrapolated full-mesh oracle time per operator: the oracle timed on the first n/2 and the first n cells of
+    the mesh; full time = fixed part (its per-call setup: rules and basis tables) + per-cell slope x cells."""
     import oracle
 
     out = []
     for c in cases:
         ncell = c["mesh"].ncell
         key = ("tet" if c["cell_type"] == 4 else ("hexv" if c["ncomp"] == 3 else "hex"), c["p"])
-        cv, cn, nodes, nsub = sub_mesh(c, samples.get(key, 64))
-        coef = None if c.get("coef") is None else c["coef"].reshape(-1, c["ncomp"])[nodes].ravel()
-        xs = c["x"].reshape(-1, c["ncomp"])[nodes].ravel()
-        pb = oracle.Problem(c["cell_type"], c["mesh"].coords, cv, c["p"], cn, nodes.size, FORM_IDS[c["form"]],
-                            ncomp=c["ncomp"], qdeg=c["qdeg"], ucoef=coef, **c["okw"])
-        best = None
-        for _ in range(repeats):
-            t0 = time.perf_counter()
-            pb.apply(xs)
-            dt = time.perf_counter() - t0
-            best = dt if best is None else min(best, dt)
-        out.append(dict(name=c["name"], sample_cells=nsub, sample_s=best, full_s=best * ncell / nsub, ndof=c["ndof"]))
+        n_big = min(samples.get(key, 64), ncell)
+        times = []
+        for n in sorted({max(1, n_big // 2), n_big}):
+            cv, cn, nodes, nsub = sub_mesh(c, n)
+            coef = None if c.get("coef") is None else c["coef"].reshape(-1, c["ncomp"])[nodes].ravel()
+            xs = c["x"].reshape(-1, c["ncomp"])[nodes].ravel()
+            pb = oracle.Problem(c["cell_type"], c["mesh"].coords, cv, c["p"], cn, nodes.size, FORM_IDS[c["form"]],
+                                ncomp=c["ncomp"], qdeg=c["qdeg"], ucoef=coef, **c["okw"])
+            best = None
+            for _ in range(repeats):
+                t0 = time.perf_counter()
+                pb.apply(xs)
+                dt = time.perf_counter() - t0
+                best = dt if best is None else min(best, dt)
+            times.append((nsub, best))
+        if len(times) == 2 and times[1][0] > times[0][0]:
+            (n1, t1), (n2, t2) = times
+            slope = max(t2 - t1, 0.0) / (n2 - n1)
+            fixed = max(t1 - slope * n1, 0.0)
+        else:
+            (n2, t2), fixed, slope = times[-1], 0.0, times[-1][1] / times[-1][0]
+        out.append(dict(name=c["name"], sample_cells=n2, sample_s=t2, full_s=fixed + slope * ncell, ndof=c["ndof"],
+                        fixed_s=fixed))
     return out
 
 
@@ -323,8 +354,8 @@ def reference_arm(args, world, rank):
     ndof = sum(c["ndof"] for c in cases)
     step_s = statistics.mean(times)
     value = ndof / step_s / 1e9
-    sample_desc = "per operator the first cells of the mesh (%s); full-mesh time extrapolated by cell count" % (
-        ", ".join("%s: %d cells" % (o["name"], o["sample_cells"]) for o in samples))
+    sample_desc = ("per operator the first n/2 and n cells of the mesh (%s); full-mesh time = fixed per-call part + "
+                   "per-cell slope x cells" % ", ".join("%s: n=%d" % (o["name"], o["sample_cells"]) for o in samples))
     line = {
         "impl": "reference", "metric": "operator-action GDoF/s", "value": value, "unit": "GDoF/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
@@ -465,7 +496,9 @@ def gpu_arm(args, world, rank, local):
         kname = kbase + "<n=%d,%s,cb=%d>" % (dom["case"]["p"] + 1, dom["case"]["form"], dom["cfg"].cells_per_block)
     else:
         moment = dom["case"]["p"] == 2 and dom["case"]["form"] in ("hyper_res", "hyper_jac")
-        kh, kname = None, ("tet_moment_kernel<%s>" if moment else "tet_apply_kernel<%s>") % dom["case"]["name"]
+        kname = "tet_dense_kernel<%s>" if dom["case"]["p"] >= 3 else (
+            "tet_moment_kernel<%s>" if moment else "tet_apply_kernel<%s>")
+        kh, kname = None, kname % dom["case"]["name"]
     traffic = NCU_TRAFFIC.get((kh, dom["case"]["name"]))
     if args.workload == "hex" and args.precision != "fp64":
         # FP32/BF16 contractions: bound by HBM bandwidth (algorithmic bytes of the dominant operator)
@@ -509,9 +542,9 @@ def gpu_arm(args, world, rank, local):
         r = oracle_rate(cases, samples=SAMPLE_BASELINE)
         full_s = sum(o["full_s"] for o in r)
         cpu = {"value": ndof_step / full_s / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
-               "sample": "per operator the first cells of the mesh (%s), timed once; full-mesh time extrapolated "
-                         "by cell count" % ", ".join("%s %d cells %.2fs" % (o["name"], o["sample_cells"], o["sample_s"])
-                                                     for o in r)}
+               "sample": "per operator the first n/2 and n cells of the mesh (%s), each timed once; full-mesh time = "
+                         "fixed per-call part + per-cell slope x cells" % ", ".join(
+                             "%s n=%d %.2fs" % (o["name"], o["sample_cells"], o["sample_s"]) for o in r)}
 
     per_op = []
     for o, ms in zip(ops, per_op_ms):
@@ -538,6 +571,12 @@ def gpu_arm(args, world, rank, local):
                         "geometry": "stored FP64 J^-1 and w|det J| per point", "lambda": 1.0, "mu": 1.0,
                         "input": "residual and coefficient: sinusoid displacement (8 terms, amplitude 0.05, seed 2) "
                                  "on the node grid; elasticity and Jacobian: x ~ U[-1,1) seed 1"})
+        elif args.workload == "tet-pk":
+            cfg.update({"mesh": "%d^3 boxes x 6 Kuhn tets" % args.nx,
+                        "quadrature": "collapsed Gauss-Jacobi, exact for the polynomial integrand (degree 2p mass/"
+                                      "Helmholtz, 2p-2 Laplace/elasticity; hyperelastic max(4, 2p))",
+                        "basis": "equispaced lattice Lagrange", "lambda": 1.0, "mu": 1.0,
+                        "input": "scalar x ~ U[-1,1) seed 0; vector: sinusoid displacement seed 2"})
         elif args.workload == "tet-p1-mass":
             cfg.update({"mesh": "%d^3 boxes x 6 Kuhn tets" % args.nx, "quadrature": "degree 2",
                         "input": "x ~ U[-1,1) seed 0"})
@@ -845,9 +884,10 @@ def main():
     if args.precision is None:
         args.precision = "fp32" if args.workload == "batched" else "fp64"
     if args.degrees is None:
-        args.degrees = "1,2,3,4" if args.workload == "hex-vector" else "1,2,3,4,5,6"
+        args.degrees = {"hex-vector": "1,2,3,4", "tet-pk": "3,4,5,6"}.get(args.workload, "1,2,3,4,5,6")
     if args.forms is None:
-        args.forms = "elasticity,hyper_res,hyper_jac" if args.workload == "hex-vector" else "laplace,helmholtz"
+        args.forms = {"hex-vector": "elasticity,hyper_res,hyper_jac",
+                      "tet-pk": "helmholtz,elasticity"}.get(args.workload, "laplace,helmholtz")
     world, rank, local = dist_setup(args)
     if args.workload == "batched" and args.impl != "reference":
         batched_arm(args, world, rank, local)

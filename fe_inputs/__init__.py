@@ -10,6 +10,8 @@ from it without sharing any of the computation under test.
 """
 from .rng import splitmix64, uniform, randint
 from .mesh import (
+    pk_lattice,
+    pk_node_map,
     TetMesh,
     HexMesh,
     kuhn_tet_mesh,

@@ -160,6 +160,56 @@ def p2_node_coords(coords, edges):
     return np.concatenate([coords, mid], axis=0)
 
 
+def pk_lattice(k):
+    """Barycentric lattice of P_k on a tet, in local node order: points (i, j, l)/k with i + j + l <= k, i fastest,
+    then j, then l.  Returns int [nloc][4] weights (b0, b1, b2, b3), b_s = k * (barycentric coordinate of vertex s),
+    vertex 0 at the origin and vertex e + 1 at the unit vector e."""
+    pts = []
+    for l in range(k + 1):
+        for j in range(k + 1 - l):
+            for i in range(k + 1 - l - j):
+                pts.append((k - i - j - l, i, j, l))
+    return np.array(pts, dtype=np.int64)
+
+
+def pk_node_map(cell_vert, nvert, k):
+    """Cell -> node map of continuous P_k (k >= 3) on a tet mesh, local nodes in `pk_lattice` order.
+
+    A lattice point is identified across cells by the global vertices of its support and its weights on them
+    (an edge, face or interior point is the same node in every cell that contains it, whatever the local vertex
+    order).  Nodes 0..nvert-1 are the mesh vertices; the other nodes follow in sorted key order.  Returns
+    (cell_node int32 [ncell][nloc], nnode, node_coords_fn) where node_coords_fn(coords) gives the node positions.
+    """
+    cv = cell_vert.astype(np.int64)
+    ncell = cv.shape[0]
+    lat = pk_lattice(k)
+    nloc = lat.shape[0]
+    # per (cell, local node): support vertices sorted by global id, with their weights; padding (-1, 0)
+    gv = cv[:, None, :].repeat(nloc, axis=1)                      # [ncell][nloc][4]
+    w = np.broadcast_to(lat[None, :, :], gv.shape)
+    vkey = np.where(w > 0, gv, np.int64(-1))
+    order = np.argsort(np.where(vkey < 0, np.iinfo(np.int64).max, vkey), axis=2, kind="stable")
+    vs = np.take_along_axis(vkey, order, axis=2)
+    ws = np.take_along_axis(w, order, axis=2)
+    keys = np.concatenate([vs, ws], axis=2).reshape(-1, 8)
+    uniq, inv = np.unique(keys, axis=0, return_inverse=True)
+    inv = inv.reshape(-1)
+    is_vertex = (uniq[:, 4] == k)                                  # a single support vertex with the full weight
+    node_of_key = np.empty(uniq.shape[0], dtype=np.int64)
+    node_of_key[is_vertex] = uniq[is_vertex, 0]
+    nonv = np.flatnonzero(~is_vertex)
+    node_of_key[nonv] = nvert + np.arange(nonv.size)
+    cell_node = node_of_key[inv].reshape(ncell, nloc).astype(np.int32)
+    nnode = nvert + nonv.size
+
+    def node_coords(coords):
+        out = np.zeros((nnode, 3))
+        out[node_of_key[inv].reshape(ncell, nloc)] = np.einsum("ls,csd->cld", lat / k, coords[cv])
+        return out
+
+    return cell_node, nnode, node_coords
+
+
 def shuffle_mesh(cell_vert, cell_node, nnode, seed, shuffle_cells=True, shuffle_nodes=True):
     """Seeded random relabelling of cells and nodes (an unstructured ordering).
 

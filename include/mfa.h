@@ -142,10 +142,15 @@ MFA_API int mfa_mesh_upload(mfa_ctx *ctx, int cell_type, int64_t ncell, int64_t 
                     const int32_t *cell_vert, mfa_mesh **out);
 MFA_API int mfa_mesh_destroy(mfa_mesh *mesh);
 
-/* Continuous Lagrange space of `degree` (P1/P2 on tets, Q1..Q8 on hexes) with
+/* Continuous Lagrange space of `degree` (P1..P6 on tets, Q1..Q8 on hexes) with
  * ncomp in {1, 3}.  cell_node [ncell][nloc] (host, int32) is the cell->node
  * map of Section 2.2 (`cell2dof`); entries must lie in [0, nnode) and be
- * distinct within a cell.  The mesh must outlive the space. */
+ * distinct within a cell.  The mesh must outlive the space.  Local node order:
+ * hex, the GLL tensor points with x fastest; P1/P2 tets, the vertices, then
+ * the midpoints of edges (0,1), (0,2), (0,3), (1,2), (1,3), (2,3); P3..P6
+ * tets, the equispaced lattice points (i, j, k)/p of the reference tet
+ * (vertex 0 at the origin, vertex e+1 at the unit vector e), i fastest, then
+ * j, then k. */
 MFA_API int mfa_space_create(mfa_ctx *ctx, mfa_mesh *mesh, int degree, int ncomp, const int32_t *cell_node,
                      int64_t nnode, mfa_space **out);
 MFA_API int mfa_space_ndof(const mfa_space *space, int64_t *ndof);
@@ -190,7 +195,8 @@ MFA_API int mfa_form_set_dirichlet(mfa_form *form, const int32_t *dofs, int64_t 
  *                                from global memory (FP32/BF16 hex);
  *             MFA_VARIANT_LINE_STAGED as LINE with the factors staged in shared
  *                                memory by bulk copies (FP32/BF16 hex);
- *             MFA_VARIANT_CELL   one thread per cell (tets).
+ *             MFA_VARIANT_CELL   one thread per cell (P1/P2 tets);
+ *             MFA_VARIANT_CELL_WARP one warp per cell, dense tabulated basis (P3..P6 tets).
  *  - cells_per_block: cells one thread block processes together (tets:
  *    threads per block); 0 in mfa_form_set_config = the variant's default.
  *  - scatter: MFA_SCATTER_ATOMIC, or (FP64 only) MFA_SCATTER_COLOUR or MFA_SCATTER_WARP.
@@ -201,7 +207,8 @@ enum {
   MFA_VARIANT_EVEN_ODD = 2,
   MFA_VARIANT_LINE = 3,
   MFA_VARIANT_LINE_STAGED = 4,
-  MFA_VARIANT_CELL = 5
+  MFA_VARIANT_CELL = 5,
+  MFA_VARIANT_CELL_WARP = 6
 };
 typedef struct {
   int32_t variant;

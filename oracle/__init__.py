@@ -117,7 +117,7 @@ def tet_rule(degree):
 
 
 def tet_basis(p, xi):
-    n = 4 if p == 1 else 10
+    n = (p + 1) * (p + 2) * (p + 3) // 6
     phi, dphi = np.zeros(n), np.zeros((n, 3))
     _check(lib().orc_tet_basis(p, _dp(np.ascontiguousarray(xi, dtype=np.float64)), _dp(phi), _dp(dphi)), "tet_basis")
     return phi, dphi

@@ -165,7 +165,10 @@ int orc_tet_rule(int degree, double *pts, double *w) {
 /* ------------------------------------------------------------------ */
 
 /* Monomial exponents of total degree <= p, p <= 2. */
-static int tet_monomials(int p, int e[10][3]) {
+#define ORC_TET_MAXP 6
+#define ORC_TET_MAXN 84 /* (p+1)(p+2)(p+3)/6 at p = 6 */
+
+static int tet_monomials(int p, int e[ORC_TET_MAXN][3]) {
   int n = 0;
   for (int d = 0; d <= p; ++d)
     for (int i = d; i >= 0; --i)
@@ -183,11 +186,24 @@ static long double ipow(long double x, int k) {
   return r;
 }
 
-/* Reference nodes of P1/P2: vertices, then midpoints of edges
- * (0,1), (0,2), (0,3), (1,2), (1,3), (2,3). */
-static void tet_nodes(int p, long double nodes[10][3]) {
+/* Reference nodes.  P1/P2: vertices, then midpoints of edges (0,1), (0,2),
+ * (0,3), (1,2), (1,3), (2,3).  P3..P6: the equispaced lattice points
+ * (i, j, l)/p, i + j + l <= p, with i running fastest, then j, then l. */
+static void tet_nodes(int p, long double nodes[ORC_TET_MAXN][3]) {
   static const long double v[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
   static const int ed[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+  if (p >= 3) {
+    int n = 0;
+    for (int l = 0; l <= p; ++l)
+      for (int j = 0; j <= p - l; ++j)
+        for (int i = 0; i <= p - l - j; ++i) {
+          nodes[n][0] = (long double)i / p;
+          nodes[n][1] = (long double)j / p;
+          nodes[n][2] = (long double)l / p;
+          ++n;
+        }
+    return;
+  }
   for (int i = 0; i < 4; ++i)
     for (int d = 0; d < 3; ++d) nodes[i][d] = v[i][d];
   if (p == 2)
@@ -196,13 +212,13 @@ static void tet_nodes(int p, long double nodes[10][3]) {
 }
 
 int orc_tet_basis(int p, const double xi[3], double *phi, double *dphi) {
-  if ((p != 1 && p != 2) || !xi || !phi || !dphi) return ORC_EARG;
-  int e[10][3];
+  if (p < 1 || p > ORC_TET_MAXP || !xi || !phi || !dphi) return ORC_EARG;
+  int e[ORC_TET_MAXN][3];
   int n = tet_monomials(p, e);
-  long double nodes[10][3];
+  long double nodes[ORC_TET_MAXN][3];
   tet_nodes(p, nodes);
   /* Vandermonde V[i][j] = m_j(node_i); C = V^{-1} gives phi_a = sum_j C[j][a] m_j. */
-  long double M[10][20];
+  static _Thread_local long double M[ORC_TET_MAXN][2 * ORC_TET_MAXN];
   for (int i = 0; i < n; ++i) {
     for (int j = 0; j < n; ++j)
       M[i][j] = ipow(nodes[i][0], e[j][0]) * ipow(nodes[i][1], e[j][1]) * ipow(nodes[i][2], e[j][2]);
@@ -304,7 +320,10 @@ static void free_tables(tables *t) {
 }
 
 static int nloc_of(const orc_problem *pb) {
-  if (pb->cell_type == ORC_TET) return pb->degree == 1 ? 4 : (pb->degree == 2 ? 10 : -1);
+  if (pb->cell_type == ORC_TET) {
+    const int p = pb->degree;
+    return p >= 1 && p <= ORC_TET_MAXP ? (p + 1) * (p + 2) * (p + 3) / 6 : -1;
+  }
   int n = pb->degree + 1;
   return n * n * n;
 }
@@ -312,7 +331,7 @@ static int nloc_of(const orc_problem *pb) {
 static int check_problem(const orc_problem *pb) {
   if (!pb || !pb->coords || !pb->cell_vert || !pb->cell_node) return ORC_EARG;
   if (pb->cell_type != ORC_TET && pb->cell_type != ORC_HEX) return ORC_EARG;
-  if (pb->cell_type == ORC_TET && pb->degree != 1 && pb->degree != 2) return ORC_EARG;
+  if (pb->cell_type == ORC_TET && (pb->degree < 1 || pb->degree > ORC_TET_MAXP)) return ORC_EARG;
   if (pb->cell_type == ORC_HEX && (pb->degree < 1 || pb->degree > 16)) return ORC_EARG;
   if (pb->ncomp != 1 && pb->ncomp != 3) return ORC_EARG;
   if (pb->kind < ORC_MASS || pb->kind > ORC_HYPER_JAC) return ORC_EARG;

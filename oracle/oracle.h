@@ -60,8 +60,11 @@ int orc_gll_nodes(int n, double *x);
 /* Collapsed (conical product) rule on the reference tet exact to `degree`.
  * pts is [nq][3]; returns nq = m^3 with m = ceil((degree+1)/2). */
 int orc_tet_rule(int degree, double *pts, double *w);
-/* Lagrange P_p on the reference tet (p = 1, 2) by inverting the Vandermonde
- * matrix of monomials at the nodes.  phi [ndof], dphi [ndof][3]. */
+/* Lagrange P_p on the reference tet (p = 1..6) by inverting the Vandermonde
+ * matrix of monomials at the nodes.  phi [ndof], dphi [ndof][3].  Nodes:
+ * P1/P2 vertices, then edge midpoints (0,1), (0,2), (0,3), (1,2), (1,3),
+ * (2,3); P3..P6 the lattice points (i, j, l)/p, i + j + l <= p, i fastest,
+ * then j, then l. */
 int orc_tet_basis(int p, const double xi[3], double *phi, double *dphi);
 /* Lagrange Q_p on [0,1]^3; phi [n^3], dphi [n^3][3]. */
 int orc_hex_basis(int p, int equispaced, const double xi[3], double *phi, double *dphi);

@@ -26,8 +26,8 @@ MFA_SCATTER_AUTO, MFA_SCATTER_COLOUR, MFA_SCATTER_ATOMIC, MFA_SCATTER_WARP = 0, 
 MFA_PC_NONE, MFA_PC_JACOBI = 0, 1
 MFA_PRECOND_MLP, MFA_PRECOND_LINEAR = 0, 1
 (MFA_VARIANT_AUTO, MFA_VARIANT_POINT, MFA_VARIANT_EVEN_ODD, MFA_VARIANT_LINE, MFA_VARIANT_LINE_STAGED,
- MFA_VARIANT_CELL) = 0, 1, 2, 3, 4, 5
-VARIANT_NAMES = {1: "point", 2: "even-odd", 3: "line", 4: "line-staged", 5: "cell"}
+ MFA_VARIANT_CELL, MFA_VARIANT_CELL_WARP) = 0, 1, 2, 3, 4, 5, 6
+VARIANT_NAMES = {1: "point", 2: "even-odd", 3: "line", 4: "line-staged", 5: "cell", 6: "cell-warp"}
 
 
 class MfaError(RuntimeError):

@@ -45,7 +45,11 @@ int cuda_alloc(void** p, size_t bytes, const char* what) {
 }
 
 int nloc_of(int cell_type, int degree) {
-  if (cell_type == MFA_CELL_TET4) return degree == 1 ? 4 : (degree == 2 ? 10 : -1);
+  if (cell_type == MFA_CELL_TET4) {
+    if (degree == 1) return 4;
+    if (degree == 2) return 10;
+    return degree >= 3 && degree <= mfa::kTetMaxP ? mfa::tet_lattice_size(degree) : -1;
+  }
   if (cell_type == MFA_CELL_HEX8 && degree >= 1 && degree <= 8) return (degree + 1) * (degree + 1) * (degree + 1);
   return -1;
 }
@@ -115,6 +119,23 @@ void count_work(mfa_form* f) {
     per_cell = 60.0 + 900.0 * fields + 27.0 * (54.0 * fields + 76.0 + phys) + 180.0 + 720.0 + (res ? 60.0 : 0.0) + 30.0;
     bytes = ncell * (4.0 * sp->nloc + 16.0) + 24.0 * sp->mesh->nvert;
     if (kind == MFA_FORM_HYPER_JAC) bytes += 8.0 * ndof;
+  } else if (sp->degree >= 3) {
+    // dense tabulation, per point: interpolation (value 2, gradient 6 per dof and component; the Jacobian
+    // action also the linearisation point's gradient), the physics, and the test-side sums (value 2,
+    // gradient 6 per dof and component); per cell the affine geometry (~70) and the scatter adds
+    const double nl = sp->nloc, nc = sp->ncomp, nq = f->nq;
+    const bool val_in = kind == MFA_FORM_MASS || kind == MFA_FORM_HELMHOLTZ;
+    const bool val_out = val_in || kind == MFA_FORM_HYPER_RES;
+    const bool grad = kind != MFA_FORM_MASS, jac = kind == MFA_FORM_HYPER_JAC, svk = f->p.law == MFA_LAW_SVK;
+    double per_q = nl * nc * ((val_in ? 2.0 : 0.0) + (grad ? 6.0 : 0.0) + (jac ? 6.0 : 0.0));
+    per_q += nl * nc * ((val_out ? 2.0 : 0.0) + (grad ? 6.0 : 0.0));
+    if (kind <= MFA_FORM_HELMHOLTZ) per_q += nc * ((grad ? 3.0 * 5.0 + 3.0 : 0.0) + (val_in ? 2.0 : 0.0)) + 1.0;
+    else if (kind == MFA_FORM_ELASTICITY) per_q += 45.0 + 24.0 + 54.0 + 1.0;
+    else if (kind == MFA_FORM_HYPER_RES) per_q += 45.0 + (svk ? 102.0 : 66.0) + 54.0 + 4.0;
+    else per_q += 90.0 + (svk ? 243.0 : 202.0) + 54.0 + 1.0;
+    per_cell = nq * per_q + 70.0 + nl * nc;
+    bytes = ncell * (4.0 * nl + 16.0) + 24.0 * sp->mesh->nvert;
+    if (jac) bytes += 8.0 * ndof;
   } else {
     const double nl = sp->nloc, nc = sp->ncomp, nq = f->nq;
     double per_q = 0.0;
@@ -172,14 +193,52 @@ int hex_tables(mfa_form* f) {
 // any exact rule, so the kernel takes the cheapest exact one it has; other
 // integrands (neo-Hookean, under-integration) use the conical-product rule
 // of degree qdeg, which defines the result.
+// P3..P6: dense tables in device memory for the warp-per-cell kernel (layouts in TetDenseArgs).
+static int tet_dense_tables(mfa_form* f, int deg) {
+  const int p = f->space->degree, nl = f->space->nloc;
+  const int m = (deg + 2) / 2;
+  if (m > mfa::kMaxN) return fail(MFA_ERR_UNSUPPORTED, "tet rule of degree %d", deg);
+  const int nq = m * m * m;
+  std::vector<double> pts(3 * nq), w(nq), phi((size_t)nq * nl), dphi((size_t)nq * nl * 3);
+  if (mfa::tet_rule_collapsed(deg, pts.data(), w.data()) != nq) return fail(MFA_ERR_UNSUPPORTED, "tet rule");
+  for (int q = 0; q < nq; ++q) mfa::tet_basis_pk(p, &pts[3 * q], &phi[(size_t)q * nl], &dphi[(size_t)q * nl * 3]);
+  const size_t nb = (size_t)nl * nq;
+  std::vector<double> buf(8 * nb + nq);
+  double* phi_aq = buf.data();
+  double* dphi_aeq = phi_aq + nb;
+  double* phi_qa = dphi_aeq + 3 * nb;
+  double* dphi_qae = phi_qa + nb;
+  double* wq = dphi_qae + 3 * nb;
+  for (int q = 0; q < nq; ++q)
+    for (int a = 0; a < nl; ++a) {
+      const double v = phi[(size_t)q * nl + a];
+      phi_aq[(size_t)a * nq + q] = v;
+      phi_qa[(size_t)q * nl + a] = v;
+      for (int e = 0; e < 3; ++e) {
+        const double d = dphi[((size_t)q * nl + a) * 3 + e];
+        dphi_aeq[((size_t)a * 3 + e) * nq + q] = d;
+        dphi_qae[((size_t)q * nl + a) * 3 + e] = d;
+      }
+    }
+  for (int q = 0; q < nq; ++q) wq[q] = w[q];
+  int rc = cuda_alloc((void**)&f->d_tdense, sizeof(double) * buf.size(), "tet tables");
+  if (!rc && cudaMemcpy(f->d_tdense, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = fail(MFA_ERR_CUDA, "tet tables: upload");
+  if (rc) return rc;
+  f->tdense_nq = nq;
+  f->nq = nq;
+  return MFA_OK;
+}
+
 int tet_tables(mfa_form* f) {
   const int p = f->space->degree, kind = f->p.kind;
   int qdeg = f->p.qdeg;
-  if (qdeg <= 0) qdeg = (kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC) ? 4 : 2 * p;
+  if (qdeg <= 0) qdeg = (kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC) ? (p > 2 ? 2 * p : 4) : 2 * p;
   int poly = -1;  // integrand degree on affine cells (-1: not polynomial)
   if (kind == MFA_FORM_MASS || kind == MFA_FORM_HELMHOLTZ) poly = 2 * p;
   if (kind == MFA_FORM_LAPLACE || kind == MFA_FORM_ELASTICITY) poly = 2 * (p - 1);
   if ((kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC) && f->p.law == MFA_LAW_SVK) poly = 4 * (p - 1);
+  if (p >= 3) return tet_dense_tables(f, (poly >= 0 && poly <= qdeg) ? poly : qdeg);
   double pts[mfa::kTetMaxQ * 3];
   int nq;
   if (poly >= 0 && poly <= qdeg && poly <= 2) {
@@ -280,6 +339,31 @@ static int apply_form_raw(mfa_form* f, const double* x, double* y, cudaStream_t 
       lc.agg = f->scatter == MFA_SCATTER_WARP;
       e = mfa::hex_apply_launch(sp->degree + 1, f->nq1, f->p.kind, f->p.precision, colour, lc, f->hex, a,
                                 ctx->sm_count, stream);
+    } else if (sp->degree >= 3) {
+      const int64_t nb = (int64_t)sp->nloc * f->tdense_nq;
+      mfa::TetDenseArgs a{};
+      a.x = x;
+      a.y = y;
+      a.coords = sp->mesh->d_coords;
+      a.cell_vert = sp->mesh->d_cell_vert;
+      a.cell_node = sp->d_cell_node;
+      a.ucoef = f->d_coef;
+      a.cell_list = list;
+      a.count = count;
+      a.phi_aq = f->d_tdense;
+      a.dphi_aeq = a.phi_aq + nb;
+      a.phi_qa = a.dphi_aeq + 3 * nb;
+      a.dphi_qae = a.phi_qa + nb;
+      a.w = a.dphi_qae + 3 * nb;
+      a.nq = f->tdense_nq;
+      a.k2 = f->p.k2;
+      a.lambda = f->p.lambda;
+      a.mu = f->p.mu;
+      a.b0 = f->p.b[0];
+      a.b1 = f->p.b[1];
+      a.b2 = f->p.b[2];
+      a.err = ctx->d_err;
+      e = mfa::tet_dense_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, a, ctx->sm_count, stream);
     } else {
       mfa::TetApplyArgs a = tet_args(f, x, y);
       a.cell_list = list;
@@ -441,7 +525,7 @@ int mfa_space_destroy(mfa_space* s) {
 }
 
 static int default_variant(const mfa_space* sp, int nq, int precision) {
-  if (sp->mesh->cell_type != MFA_CELL_HEX8) return MFA_VARIANT_CELL;
+  if (sp->mesh->cell_type != MFA_CELL_HEX8) return sp->degree >= 3 ? MFA_VARIANT_CELL_WARP : MFA_VARIANT_CELL;
   if (sp->ncomp == 3) return MFA_VARIANT_POINT;  // the vector forms have the point kernel only
   return mfa::hex_default_variant(sp->degree + 1, nq, precision);
 }
@@ -450,7 +534,14 @@ static int default_variant(const mfa_space* sp, int nq, int precision) {
 static int cb_options(const mfa_form* f, int variant, int* out) {
   const mfa_space* sp = f->space;
   const int n = sp->degree + 1, nq = f->p.qdeg > 0 ? f->p.qdeg : n;
-  if (sp->mesh->cell_type != MFA_CELL_HEX8) return variant == MFA_VARIANT_CELL ? mfa::tet_cb_options(out) : 0;
+  if (sp->mesh->cell_type != MFA_CELL_HEX8) {
+    if (sp->degree >= 3) {
+      if (variant != MFA_VARIANT_CELL_WARP) return 0;
+      out[0] = 8;  // one warp per cell, 8 warps per block
+      return 1;
+    }
+    return variant == MFA_VARIANT_CELL ? mfa::tet_cb_options(out) : 0;
+  }
   if (sp->ncomp == 3) {
     if (variant != MFA_VARIANT_POINT) return 0;
     out[0] = mfa::hex_cells_per_block(n, n);
@@ -471,7 +562,7 @@ static std::vector<mfa_launch_config> form_configs(const mfa_form* f) {
   std::vector<mfa_launch_config> all;
   const bool hex = f->space->mesh->cell_type == MFA_CELL_HEX8;
   std::vector<int> variants;
-  if (!hex) variants = {MFA_VARIANT_CELL};
+  if (!hex) variants = {f->space->degree >= 3 ? MFA_VARIANT_CELL_WARP : MFA_VARIANT_CELL};
   else if (f->p.precision == MFA_PREC_FP64) variants = {MFA_VARIANT_POINT, MFA_VARIANT_EVEN_ODD};
   else variants = {MFA_VARIANT_LINE, MFA_VARIANT_LINE_STAGED};
   const bool colour_ok = f->p.precision == MFA_PREC_FP64;
@@ -530,10 +621,11 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
     return fail(MFA_ERR_UNSUPPORTED,
                 "mfa_form_create: vector hex kernels cover FP64 Laplace/elasticity/hyperelasticity with p+1 points");
   if (ct == MFA_CELL_TET4) {
-    const bool ok = (sp->degree == 1 && sp->ncomp == 1 && kind <= MFA_FORM_HELMHOLTZ) ||
-                    (sp->degree == 2 && sp->ncomp == 1 && kind <= MFA_FORM_HELMHOLTZ) ||
-                    (sp->degree == 2 && sp->ncomp == 3 && kind >= MFA_FORM_LAPLACE && kind != MFA_FORM_HELMHOLTZ);
+    const bool ok = (sp->ncomp == 1 && kind <= MFA_FORM_HELMHOLTZ) ||
+                    (sp->degree >= 2 && sp->ncomp == 3 && kind >= MFA_FORM_LAPLACE && kind != MFA_FORM_HELMHOLTZ);
     if (!ok) return fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: form %d on P%d x %d", kind, sp->degree, sp->ncomp);
+    if (sp->degree >= 3 && prm->scatter == MFA_SCATTER_WARP)
+      return fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: warp-aggregated scatter on P%d", sp->degree);
   }
   MFA_CUDA(cudaSetDevice(ctx->device));
   mfa_form* f = new (std::nothrow) mfa_form();
@@ -772,6 +864,7 @@ int mfa_form_destroy(mfa_form* f) {
   if (!f) return MFA_OK;
   cudaSetDevice(f->device);
   cudaFree(f->d_geom);
+  cudaFree(f->d_tdense);
   cudaFree(f->d_dir_mask);
   cudaFree(f->d_dir_x);
   cudaFree(f->d_dir_y);
@@ -858,6 +951,8 @@ int mfa_diagonal(mfa_ctx* ctx, mfa_form* f, double* d) {
   if (!ctx || !f || !d) return fail(MFA_ERR_ARG, "mfa_diagonal: NULL argument");
   if (f->p.kind == MFA_FORM_HYPER_RES || f->p.kind == MFA_FORM_HYPER_JAC)
     return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: linear forms only");
+  if (f->space->mesh->cell_type == MFA_CELL_TET4 && f->space->degree >= 3)
+    return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: tets of degree %d", f->space->degree);
   MFA_CUDA(cudaSetDevice(ctx->device));
   mfa_space* sp = f->space;
   const int64_t ndof = sp->nnode * sp->ncomp;

@@ -27,6 +27,10 @@ int tet_rule_4pt_deg2(double* pts, double* w);  // degree-2, symmetric 4-point
 int tet_rule_collapsed(int degree, double* pts, double* w);  // conical product, m = ceil((deg+1)/2)
 // P1 / P2 basis on the reference tet (closed forms in barycentric coordinates).
 void tet_basis(int p, const double* xi, double* phi, double* dphi);
+// P3..P6 on the equispaced lattice (Silvester's product formula); nodes (i, j, k)/p, i fastest, then j, then k.
+constexpr int kTetMaxP = 6;
+int tet_lattice_size(int p);
+void tet_basis_pk(int p, const double* xi, double* phi, double* dphi);
 
 // ---------------------------------------------------------------- colour.cpp
 // Greedy first-fit colouring: cells sharing a node get different colours.
@@ -160,6 +164,27 @@ struct TetApplyArgs {
 // threads: threads (cells) per block, one of tet_cb_options.
 cudaError_t tet_apply_launch(int p, int ncomp, int kind, int law, bool colour, bool agg, int threads,
                              const TetTables& tb, const TetApplyArgs& a, int sm_count, cudaStream_t s);
+// P3..P6 (dense tabulation, one warp per cell).  Tables in device memory, nl local dofs, nq points.
+struct TetDenseArgs {
+  const double* x;
+  double* y;
+  const double* coords;
+  const int32_t* cell_vert;
+  const int32_t* cell_node;
+  const double* ucoef;
+  const int32_t* cell_list;
+  int64_t count;
+  const double* phi_aq;    // [nl][nq]
+  const double* dphi_aeq;  // [nl][3][nq]
+  const double* phi_qa;    // [nq][nl]
+  const double* dphi_qae;  // [nq][nl][3]
+  const double* w;         // [nq]
+  int nq;
+  double k2, lambda, mu, b0, b1, b2;
+  int* err;
+};
+cudaError_t tet_dense_launch(int p, int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, int sm_count,
+                             cudaStream_t s);
 cudaError_t tet_diagonal_launch(int p, int ncomp, int kind, const TetTables& tb, const TetApplyArgs& a,
                                 double* d, cudaStream_t s);
 
@@ -249,6 +274,8 @@ struct mfa_form {
   double tuned_ms = 0.0;         // time of `launch` measured by mfa_form_autotune
   mfa::HexTables hex{};
   mfa::TetTables tet{};
+  double* d_tdense = nullptr;    // P3..P6 tables (TetDenseArgs layouts), tdense_nq points
+  int tdense_nq = 0;
   void* d_geom = nullptr;
   int64_t gstride = 0;           // elements per cell of d_geom
   const double* d_coef = nullptr;

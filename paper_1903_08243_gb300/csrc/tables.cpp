@@ -202,4 +202,44 @@ void tet_basis(int p, const double* xi, double* phi, double* dphi) {
   }
 }
 
+int tet_lattice_size(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+// P_p (p >= 3) by Silvester's product formula for the equispaced simplex lattice: node b = (b0, b1, b2, b3),
+// b0 + b1 + b2 + b3 = p, has phi_b = prod_s S_{b_s}(l_s) with S_m(l) = prod_{t<m} (p l - t) / (t + 1), l the
+// barycentric coordinates (l0 = 1 - x - y - z, l1 = x, l2 = y, l3 = z).  Nodes in lattice order: (i, j, k)/p with
+// i = b1 fastest, then j = b2, then k = b3.
+void tet_basis_pk(int p, const double* xi, double* phi, double* dphi) {
+  const double l[4] = {1.0 - xi[0] - xi[1] - xi[2], xi[0], xi[1], xi[2]};
+  static const double gl[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  // S_m(l_s) and its derivative in l_s, m = 0..p
+  double S[4][kTetMaxP + 1], dS[4][kTetMaxP + 1];
+  for (int s = 0; s < 4; ++s) {
+    S[s][0] = 1.0;
+    dS[s][0] = 0.0;
+    for (int m = 1; m <= p; ++m) {
+      const double f = (p * l[s] - (m - 1)) / m;
+      S[s][m] = S[s][m - 1] * f;
+      dS[s][m] = dS[s][m - 1] * f + S[s][m - 1] * (double)p / m;
+    }
+  }
+  int n = 0;
+  for (int k = 0; k <= p; ++k)
+    for (int j = 0; j <= p - k; ++j)
+      for (int i = 0; i <= p - k - j; ++i) {
+        const int b[4] = {p - i - j - k, i, j, k};
+        double v = 1.0;
+        for (int s = 0; s < 4; ++s) v *= S[s][b[s]];
+        phi[n] = v;
+        double g[3] = {0.0, 0.0, 0.0};
+        for (int s = 0; s < 4; ++s) {
+          double prod = dS[s][b[s]];
+          for (int r = 0; r < 4; ++r)
+            if (r != s) prod *= S[r][b[r]];
+          for (int d = 0; d < 3; ++d) g[d] += prod * gl[s][d];
+        }
+        for (int d = 0; d < 3; ++d) dphi[3 * n + d] = g[d];
+        ++n;
+      }
+}
+
 }  // namespace mfa

@@ -1,0 +1,289 @@
+// Tetrahedral P3..P6 action by dense tabulation, one warp per cell.
+//
+// The paper's tet kernels (Listing 2) loop over quadrature points and local
+// dofs with tabulated basis values; from P3 on a cell has 20-84 dofs and
+// 27-343 points, too much work and state for one thread.  Here a warp owns a
+// cell: in the point phase each lane takes one quadrature point of a chunk of
+// 32 and interpolates the field and its reference gradient from the cell's
+// dofs (staged in shared memory), evaluates the pointwise physics on the
+// affine cell, and stages the fluxes; in the dof phase each lane takes local
+// dofs and accumulates the test-side sums over the chunk's points.  Both
+// phases read the basis tables (FP64, in global memory, cached in L1/L2) with
+// consecutive lanes on consecutive addresses: [a][q] layout for the point
+// phase, [q][a] for the dof phase.
+#include "mfa_internal.h"
+#include "physics.cuh"
+
+namespace mfa {
+namespace {
+
+constexpr int kWarps = 8;  // cells (warps) per block
+
+template <int NL, int NC, int KIND>
+struct DenseShape {
+  static constexpr bool kVector = NC == 3;
+  // staged per point: value term and reference flux of each component
+  static constexpr int S = 4 * NC;
+  static constexpr int R = (NL + 31) / 32;  // dofs per lane
+  static constexpr int SMEM_WARP = 2 * NL * NC + 32 * S;  // doubles: x (and the coefficient), stage
+};
+
+template <int NL, int NC, int KIND, int LAW, bool COLOUR>
+__global__ void __launch_bounds__(32 * kWarps) tet_dense_kernel(const TetDenseArgs a) {
+  using SH = DenseShape<NL, NC, KIND>;
+  constexpr bool kValue = KIND == MFA_FORM_MASS || KIND == MFA_FORM_HELMHOLTZ || KIND == MFA_FORM_HYPER_RES;
+  constexpr bool kGrad = KIND != MFA_FORM_MASS;
+  constexpr bool kJac = KIND == MFA_FORM_HYPER_JAC;
+  extern __shared__ __align__(16) double smem_d[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double* xl = smem_d + wid * SH::SMEM_WARP;  // [NL][NC]
+  double* ul = xl + NL * NC;                  // [NL][NC] linearisation point
+  double* st = ul + NL * NC;                  // [32][S]
+  const int nq = a.nq;
+  const double bb[3] = {a.b0, a.b1, a.b2};
+  for (int64_t idx = blockIdx.x * (int64_t)kWarps + wid; idx < a.count; idx += (int64_t)gridDim.x * kWarps) {
+    const int64_t cell = a.cell_list ? (int64_t)__ldg(a.cell_list + idx) : idx;
+    // affine geometry (every lane, broadcast loads)
+    double J[3][3];
+    {
+      const int32_t v0 = __ldg(a.cell_vert + 4 * cell);
+      double X0[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) X0[d] = __ldg(a.coords + 3 * (int64_t)v0 + d);
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        const int32_t ve = __ldg(a.cell_vert + 4 * cell + e + 1);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) J[d][e] = __ldg(a.coords + 3 * (int64_t)ve + d) - X0[d];
+      }
+    }
+    double cof[3][3];
+    const double det = det3(J, cof);
+    if (!(det != 0.0) || !isfinite(det)) {
+      if (lane == 0) atomicOr(a.err, 1);
+      continue;  // uniform across the warp
+    }
+    const double idet = 1.0 / det, adet = fabs(det);
+    double Ji[3][3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Ji[e][j] = cof[j][e] * idet;
+    double G[3][3];  // J^{-1} J^{-T}
+#pragma unroll
+    for (int e = 0; e < 3; ++e)
+#pragma unroll
+      for (int f = 0; f < 3; ++f) G[e][f] = Ji[e][0] * Ji[f][0] + Ji[e][1] * Ji[f][1] + Ji[e][2] * Ji[f][2];
+
+    // gather the cell's dofs
+    for (int i = lane; i < NL * NC; i += 32) {
+      const int al = i / NC, c = i - al * NC;
+      const int64_t at = (int64_t)NC * __ldg(a.cell_node + cell * NL + al) + c;
+      xl[i] = __ldg(a.x + at);
+      if constexpr (kJac) ul[i] = __ldg(a.ucoef + at);
+    }
+    __syncwarp();
+
+    double acc[SH::R][NC];
+#pragma unroll
+    for (int r = 0; r < SH::R; ++r)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[r][c] = 0.0;
+    bool ok = true;
+
+    for (int q0 = 0; q0 < nq; q0 += 32) {
+      // ---- point phase: lane = point q
+      const int q = q0 + lane;
+      double sv[NC], sh[NC][3];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        sv[c] = 0.0;
+        sh[c][0] = sh[c][1] = sh[c][2] = 0.0;
+      }
+      if (q < nq) {
+        double u[NC], g[NC][3], gk[NC][3];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          u[c] = 0.0;
+          g[c][0] = g[c][1] = g[c][2] = 0.0;
+          gk[c][0] = gk[c][1] = gk[c][2] = 0.0;
+        }
+#pragma unroll 4
+        for (int al = 0; al < NL; ++al) {
+          const double ph = kValue && KIND != MFA_FORM_HYPER_RES ? __ldg(a.phi_aq + (int64_t)al * nq + q) : 0.0;
+          double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+          if constexpr (kGrad) {
+            d0 = __ldg(a.dphi_aeq + ((int64_t)al * 3 + 0) * nq + q);
+            d1 = __ldg(a.dphi_aeq + ((int64_t)al * 3 + 1) * nq + q);
+            d2 = __ldg(a.dphi_aeq + ((int64_t)al * 3 + 2) * nq + q);
+          }
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const double xv = xl[al * NC + c];
+            if constexpr (kValue && KIND != MFA_FORM_HYPER_RES) u[c] = fma(ph, xv, u[c]);
+            if constexpr (kGrad) {
+              g[c][0] = fma(d0, xv, g[c][0]);
+              g[c][1] = fma(d1, xv, g[c][1]);
+              g[c][2] = fma(d2, xv, g[c][2]);
+            }
+            if constexpr (kJac) {
+              const double uv = ul[al * NC + c];
+              gk[c][0] = fma(d0, uv, gk[c][0]);
+              gk[c][1] = fma(d1, uv, gk[c][1]);
+              gk[c][2] = fma(d2, uv, gk[c][2]);
+            }
+          }
+        }
+        const double wd = __ldg(a.w + q) * adet;
+        if constexpr (KIND == MFA_FORM_MASS || KIND == MFA_FORM_HELMHOLTZ || KIND == MFA_FORM_LAPLACE) {
+          const double c0 = KIND == MFA_FORM_HELMHOLTZ ? a.k2 : 1.0;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            if constexpr (KIND != MFA_FORM_LAPLACE) sv[c] = c0 * wd * u[c];
+            if constexpr (kGrad) {
+#pragma unroll
+              for (int e = 0; e < 3; ++e) sh[c][e] = wd * (G[e][0] * g[c][0] + G[e][1] * g[c][1] + G[e][2] * g[c][2]);
+            }
+          }
+        } else {
+          double gu[3][3], gc[3][3], f1[3][3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+              gu[c][j] = g[c][0] * Ji[0][j] + g[c][1] * Ji[1][j] + g[c][2] * Ji[2][j];
+              gc[c][j] = kJac ? gk[c][0] * Ji[0][j] + gk[c][1] * Ji[1][j] + gk[c][2] * Ji[2][j] : 0.0;
+            }
+          ok = physics<KIND, LAW>(gu, gc, a.lambda, a.mu, f1) && ok;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+#pragma unroll
+            for (int e = 0; e < 3; ++e) sh[c][e] = wd * (f1[c][0] * Ji[e][0] + f1[c][1] * Ji[e][1] + f1[c][2] * Ji[e][2]);
+            if constexpr (KIND == MFA_FORM_HYPER_RES) sv[c] = -bb[c] * wd;
+          }
+        }
+      }
+      double* mine = st + lane * SH::S;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        mine[4 * c + 0] = sv[c];
+        mine[4 * c + 1] = sh[c][0];
+        mine[4 * c + 2] = sh[c][1];
+        mine[4 * c + 3] = sh[c][2];
+      }
+      __syncwarp();
+      // ---- dof phase: lane = local dofs lane, lane + 32, ...
+      const int nqc = nq - q0 < 32 ? nq - q0 : 32;
+#pragma unroll
+      for (int r = 0; r < SH::R; ++r) {
+        const int al = lane + 32 * r;
+        if (al < NL) {
+          for (int t = 0; t < nqc; ++t) {
+            const int64_t qa = (int64_t)(q0 + t) * NL + al;
+            const double* sp = st + t * SH::S;
+            const double ph = kValue ? __ldg(a.phi_qa + qa) : 0.0;
+            double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+            if constexpr (kGrad) {
+              d0 = __ldg(a.dphi_qae + 3 * qa + 0);
+              d1 = __ldg(a.dphi_qae + 3 * qa + 1);
+              d2 = __ldg(a.dphi_qae + 3 * qa + 2);
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+              double s = acc[r][c];
+              if constexpr (kValue) s = fma(ph, sp[4 * c + 0], s);
+              if constexpr (kGrad) {
+                s = fma(d0, sp[4 * c + 1], s);
+                s = fma(d1, sp[4 * c + 2], s);
+                s = fma(d2, sp[4 * c + 3], s);
+              }
+              acc[r][c] = s;
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+    if (!ok) atomicOr(a.err, 2);
+    // scatter
+#pragma unroll
+    for (int r = 0; r < SH::R; ++r) {
+      const int al = lane + 32 * r;
+      if (al < NL) {
+        const int32_t node = __ldg(a.cell_node + cell * NL + al);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          double* dst = a.y + (int64_t)NC * node + c;
+          if constexpr (COLOUR) *dst += acc[r][c];
+          else atomicAdd(dst, acc[r][c]);
+        }
+      }
+    }
+    __syncwarp();  // xl/ul/st are rewritten by the next cell
+  }
+}
+
+template <int NL, int NC, int KIND, int LAW, bool COLOUR>
+cudaError_t launch(const TetDenseArgs& a, int sm_count, cudaStream_t s) {
+  if (a.count == 0) return cudaSuccess;
+  auto kern = tet_dense_kernel<NL, NC, KIND, LAW, COLOUR>;
+  constexpr int smem = kWarps * DenseShape<NL, NC, KIND>::SMEM_WARP * (int)sizeof(double);
+  static int bps = -1;
+  if (bps < 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int v = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, 32 * kWarps, smem);
+    if (e != cudaSuccess) return e;
+    bps = v < 1 ? 1 : v;
+  }
+  int64_t blocks = (a.count + kWarps - 1) / kWarps;
+  const int64_t cap = (int64_t)sm_count * bps;
+  if (blocks > cap) blocks = cap;
+  kern<<<(unsigned)blocks, 32 * kWarps, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int NL, int NC, int KIND, int LAW>
+cudaError_t launch2(bool colour, const TetDenseArgs& a, int sm_count, cudaStream_t s) {
+  return colour ? launch<NL, NC, KIND, LAW, true>(a, sm_count, s) : launch<NL, NC, KIND, LAW, false>(a, sm_count, s);
+}
+
+template <int NL>
+cudaError_t by_form(int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, int sm_count, cudaStream_t s) {
+  const bool nh = law == MFA_LAW_NEOHOOKE;
+  if (ncomp == 1) {
+    switch (kind) {
+      case MFA_FORM_MASS: return launch2<NL, 1, MFA_FORM_MASS, 0>(colour, a, sm_count, s);
+      case MFA_FORM_LAPLACE: return launch2<NL, 1, MFA_FORM_LAPLACE, 0>(colour, a, sm_count, s);
+      case MFA_FORM_HELMHOLTZ: return launch2<NL, 1, MFA_FORM_HELMHOLTZ, 0>(colour, a, sm_count, s);
+    }
+    return cudaErrorInvalidValue;
+  }
+  switch (kind) {
+    case MFA_FORM_LAPLACE: return launch2<NL, 3, MFA_FORM_LAPLACE, 0>(colour, a, sm_count, s);
+    case MFA_FORM_ELASTICITY: return launch2<NL, 3, MFA_FORM_ELASTICITY, 0>(colour, a, sm_count, s);
+    case MFA_FORM_HYPER_RES:
+      return nh ? launch2<NL, 3, MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(colour, a, sm_count, s)
+                : launch2<NL, 3, MFA_FORM_HYPER_RES, MFA_LAW_SVK>(colour, a, sm_count, s);
+    case MFA_FORM_HYPER_JAC:
+      return nh ? launch2<NL, 3, MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(colour, a, sm_count, s)
+                : launch2<NL, 3, MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(colour, a, sm_count, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t tet_dense_launch(int p, int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, int sm_count,
+                             cudaStream_t s) {
+  switch (p) {
+    case 3: return by_form<20>(ncomp, kind, law, colour, a, sm_count, s);
+    case 4: return by_form<35>(ncomp, kind, law, colour, a, sm_count, s);
+    case 5: return by_form<56>(ncomp, kind, law, colour, a, sm_count, s);
+    case 6: return by_form<84>(ncomp, kind, law, colour, a, sm_count, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace mfa

@@ -124,8 +124,32 @@ def _unit(k):
 P2_EDGES = ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))
 
 
+def pk_basis_bary(p):
+    """P_p Lagrange basis on the equispaced lattice (p >= 3) as polynomials in the barycentric coordinates, by the
+    closed product form prod_s prod_{t < b_s} (p lambda_s - t) / (t + 1) (Silvester), in exact rational arithmetic.
+    Node order: lattice points (i, j, l)/p, i fastest, then j, then l; b = (p - i - j - l, i, j, l)."""
+    from fractions import Fraction
+
+    basis = []
+    for l in range(p + 1):
+        for j in range(p + 1 - l):
+            for i in range(p + 1 - l - j):
+                b = (p - i - j - l, i, j, l)
+                poly = {(0, 0, 0, 0): Fraction(1)}
+                for s in range(4):
+                    for tt in range(b[s]):
+                        lin = {_unit(s): Fraction(p, tt + 1)}
+                        if tt:
+                            lin[(0, 0, 0, 0)] = Fraction(-tt, tt + 1)
+                        poly = _pmul(poly, lin)
+                basis.append({e: float(c) for e, c in poly.items() if c != 0})
+    return basis
+
+
 def p_basis_bary(p):
-    """P1/P2 Lagrange basis as polynomials in the barycentric coordinates."""
+    """Lagrange basis as polynomials in the barycentric coordinates (P1/P2 closed forms, P3+ by pk_basis_bary)."""
+    if p >= 3:
+        return pk_basis_bary(p)
     if p == 1:
         return [{_unit(k): 1.0} for k in range(4)]
     basis = []

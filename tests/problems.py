@@ -45,6 +45,9 @@ def tet_case(nx, p, ncomp=1, perturb=0.0, seed=0, shuffle=False):
     mesh = fi.kuhn_tet_mesh(nx, perturb=perturb, seed=seed)
     if p == 1:
         cn, nnode, nodes = mesh.cell_vert, mesh.nvert, mesh.coords
+    elif p >= 3:
+        cn, nnode, node_coords = fi.pk_node_map(mesh.cell_vert, mesh.nvert, p)
+        nodes = node_coords(mesh.coords)
     else:
         cn, nnode, edges = fi.p2_node_map(mesh.cell_vert, mesh.nvert)
         nodes = fi.p2_node_coords(mesh.coords, edges)
@@ -63,7 +66,8 @@ def oracle_problem(case, kind, qdeg=None, **kw):
         if case["cell_type"] == 8:
             qdeg = case["degree"] + 1
         else:
-            qdeg = 4 if kind in ("hyper_res", "hyper_jac") else 2 * case["degree"]
+            p = case["degree"]
+            qdeg = (max(4, 2 * p) if p > 2 else 4) if kind in ("hyper_res", "hyper_jac") else 2 * p
     return oracle.Problem(case["cell_type"], case["coords"], case["cell_vert"], case["degree"], case["cell_node"],
                           case["nnode"], KIND_NAMES[kind], ncomp=case["ncomp"], qdeg=qdeg, **kw)
 

@@ -130,6 +130,9 @@ def tet_problem(nx, p, kind, perturb=0.0, seed=0, ncomp=1, qdeg=None, **kw):
     if p == 1:
         cn, nnode = m.cell_vert, m.nvert
         nodes = m.coords
+    elif p >= 3:
+        cn, nnode, node_coords = fi.pk_node_map(m.cell_vert, m.nvert, p)
+        nodes = node_coords(m.coords)
     else:
         cn, nnode, edges = fi.p2_node_map(m.cell_vert, m.nvert)
         nodes = fi.p2_node_coords(m.coords, edges)
@@ -470,3 +473,80 @@ def test_elasticity_null_space_is_the_six_rigid_modes_and_clamping_removes_it():
     R[dofs] = 0.0
     AD = R[:, None] * A * R[None, :] + np.diag(1.0 - R)
     assert np.linalg.eigvalsh(0.5 * (AD + AD.T)).min() > 1e-6 * scale
+
+
+# ---------------------------------------------------------------- tets of degree 3..6
+
+@pytest.mark.parametrize("p", [3, 4, 5, 6])
+def test_tet_pk_basis_node_order_and_polynomial_reproduction(p):
+    """The oracle's basis is nodal at the input generator's lattice points, in the same order, and reproduces
+    every polynomial of degree p (checked against numpy evaluation)."""
+    lat = fi.pk_lattice(p)
+    nodes = lat[:, 1:] / p
+    n = lat.shape[0]
+    for a in range(n):
+        phi, _ = oracle.tet_basis(p, nodes[a])
+        e = np.zeros(n)
+        e[a] = 1.0
+        np.testing.assert_allclose(phi, e, atol=1e-11)
+    rng = np.random.default_rng(p)
+    terms = [(i, j, k) for i in range(p + 1) for j in range(p + 1 - i) for k in range(p + 1 - i - j)]
+    coef = rng.standard_normal(len(terms))
+
+    def f(x):
+        return sum(c * x[0] ** i * x[1] ** j * x[2] ** k for c, (i, j, k) in zip(coef, terms))
+
+    def grad(x):
+        g = np.zeros(3)
+        for c, (i, j, k) in zip(coef, terms):
+            if i:
+                g[0] += c * i * x[0] ** (i - 1) * x[1] ** j * x[2] ** k
+            if j:
+                g[1] += c * j * x[0] ** i * x[1] ** (j - 1) * x[2] ** k
+            if k:
+                g[2] += c * k * x[0] ** i * x[1] ** j * x[2] ** (k - 1)
+        return g
+
+    vals = np.array([f(x) for x in nodes])
+    for _ in range(5):
+        xi = rng.dirichlet(np.ones(4))[1:]
+        phi, dphi = oracle.tet_basis(p, xi)
+        assert abs(phi @ vals - f(xi)) < 1e-10 * max(1.0, np.abs(vals).max())
+        np.testing.assert_allclose(dphi.T @ vals, grad(xi), atol=1e-9 * max(1.0, np.abs(vals).max()))
+
+
+def test_tet_p3_element_matrices_exact():
+    pb, m, _ = tet_problem(2, 3, oracle.MASS, perturb=0.2, seed=3, qdeg=6)
+    pl, _, _ = tet_problem(2, 3, oracle.LAPLACE, perturb=0.2, seed=3, qdeg=6)
+    for c in [2, 19]:
+        M, I, vol = exact.tet_exact(m.coords[m.cell_vert[c]], 3)
+        np.testing.assert_allclose(pb.element_matrix(c), M, rtol=1e-11, atol=1e-15 * abs(M).max())
+        K = np.einsum("abjj->ab", I)
+        np.testing.assert_allclose(pl.element_matrix(c), K, rtol=1e-10, atol=1e-13 * abs(K).max())
+
+
+@pytest.mark.parametrize("p", [3, 4, 6])
+def test_tet_pk_conservation_and_null_spaces(p):
+    nx = 2
+    pb_m, m, nodes = tet_problem(nx, p, oracle.MASS, perturb=0.15, seed=5)
+    pb_l, _, _ = tet_problem(nx, p, oracle.LAPLACE, perturb=0.15, seed=5)
+    one = np.ones(pb_m.ndof)
+    assert abs(pb_m.apply(one).sum() - 1.0) < 1e-13
+    assert np.abs(pb_l.apply(one)).max() < 1e-12
+    lin = 0.2 + nodes @ np.array([1.0, -0.7, 0.4])
+    y = pb_l.apply(lin)
+    inside = np.all((nodes > 1e-12) & (nodes < 1 - 1e-12), axis=1)
+    assert inside.any() and np.abs(y[inside]).max() < 1e-12
+    assert np.abs(y[~inside]).max() > 1e-4
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_tet_pk_elasticity_rigid_modes_and_hyper_rotation(p):
+    pb, m, nodes = tet_problem(2, p, oracle.ELASTICITY, perturb=0.15, seed=6, ncomp=3, lam=1.0, mu=1.0)
+    for t in np.eye(3):
+        assert np.abs(pb.apply(np.tile(t, (pb.nnode, 1)).ravel())).max() < 1e-13
+    for w in np.eye(3):
+        assert np.abs(pb.apply(np.cross(w, nodes).ravel())).max() < 1e-12
+    ph, _, _ = tet_problem(2, p, oracle.HYPER_RES, perturb=0.15, seed=6, ncomp=3, law=oracle.NEOHOOKE, qdeg=2 * p)
+    R = _rotation(0.5, [1, 1, -2])
+    assert np.abs(ph.apply((nodes @ R.T - nodes).ravel())).max() < 1e-12
