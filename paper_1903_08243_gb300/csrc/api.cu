@@ -83,19 +83,20 @@ void count_work(mfa_form* f) {
     if (kind != MFA_FORM_LAPLACE) exec_cell += P;  // c0 w|J| u
   }
   if (sp->mesh->cell_type == MFA_CELL_HEX8 && sp->ncomp == 3) {
-    // per component 24 n^4 (B, D, D^T, B^T sweeps; the Jacobian action also interpolates the
-    // linearisation point's gradient, 12 n^4 per component), per point the physical gradient(s)
-    // (45 each), the physics and the flux map (54: 9 entries x 5 + w|J|), scatter adds 3 n^3.
-    // Vector Laplacian: three G g products (3 x 15) per point.
-    const double n = sp->degree + 1, P = n * n * n, n4 = P * n;
+    // per component: B and B^T sweeps 4 (q n^3 + q^2 n^2 + q^3 n), D and D^T 12 q^4 (the Jacobian action also
+    // interpolates the linearisation point's gradient: 2 (q n^3 + q^2 n^2 + q^3 n) + 6 q^4); per point the
+    // physical gradient(s) (45 each), the physics and the flux map (54: 9 entries x 5 + w|J|); scatter adds
+    // 3 n^3.  Vector Laplacian: three G g products (3 x 15) per point.  q = n for p+1 points.
+    const double n = sp->degree + 1, q = f->nq1, PN = n * n * n, PQ = q * q * q;
+    const double bsw = 2.0 * (q * n * n * n + q * q * n * n + q * q * q * n);
     const bool jac = kind == MFA_FORM_HYPER_JAC, svk = f->p.law == MFA_LAW_SVK;
     double per_pt = 0.0;
     if (kind == MFA_FORM_LAPLACE) per_pt = 45.0;
     else if (kind == MFA_FORM_ELASTICITY) per_pt = 45.0 + 24.0 + 54.0;
     else if (kind == MFA_FORM_HYPER_RES) per_pt = 45.0 + (svk ? 102.0 : 66.0) + 54.0 + 3.0;
     else per_pt = 90.0 + (svk ? 243.0 : 202.0) + 54.0;
-    per_cell = 3.0 * 24.0 * n4 + (jac ? 3.0 * 12.0 * n4 : 0.0) + per_pt * P + 3.0 * P;
-    bytes = ncell * (4.0 * P + 8.0 * mfa::hex_geom_entries(kind) * P);
+    per_cell = 3.0 * (2.0 * bsw + 12.0 * PQ * q) + (jac ? 3.0 * (bsw + 6.0 * PQ * q) : 0.0) + per_pt * PQ + 3.0 * PN;
+    bytes = ncell * (4.0 * PN + 8.0 * mfa::hex_geom_entries(kind) * PQ);
     if (jac) bytes += 8.0 * ndof;
   } else if (sp->mesh->cell_type == MFA_CELL_HEX8) {
     // algorithmic count of collocation sum factorisation, whatever the kernel variant:
@@ -331,8 +332,8 @@ static int apply_form_raw(mfa_form* f, const double* x, double* y, cudaStream_t 
       mfa::HexVecArgs a{x, y, sp->d_cell_node, static_cast<const double*>(f->d_geom), f->d_coef, list, count,
                         f->gstride, f->p.lambda, f->p.mu, f->p.b[0], f->p.b[1], f->p.b[2], ctx->d_err};
       const int n = sp->degree + 1;
-      e = n <= 5 ? mfa::hex_vector_launch_a(n, f->p.kind, f->p.law, colour, f->hex, a, ctx->sm_count, stream)
-                 : mfa::hex_vector_launch_b(n, f->p.kind, f->p.law, colour, f->hex, a, ctx->sm_count, stream);
+      e = n <= 5 ? mfa::hex_vector_launch_a(n, f->nq1, f->p.kind, f->p.law, colour, f->hex, a, ctx->sm_count, stream)
+                 : mfa::hex_vector_launch_b(n, f->nq1, f->p.kind, f->p.law, colour, f->hex, a, ctx->sm_count, stream);
     } else if (sp->mesh->cell_type == MFA_CELL_HEX8) {
       mfa::HexApplyArgs a{x, y, sp->d_cell_node, f->d_geom, list, count, ctx->d_err, f->gstride};
       mfa::LaunchConfig lc = f->launch;
@@ -615,11 +616,15 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
     return fail(MFA_ERR_ARG, "mfa_form_create: form %d needs a 3-component space", kind);
   if (ct == MFA_CELL_HEX8 && sp->ncomp == 1 && kind > MFA_FORM_HELMHOLTZ)
     return fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: scalar hex kernels cover mass/Laplace/Helmholtz");
-  if (ct == MFA_CELL_HEX8 && sp->ncomp == 3 &&
-      (kind == MFA_FORM_MASS || kind == MFA_FORM_HELMHOLTZ || prm->precision != MFA_PREC_FP64 ||
-       (prm->qdeg > 0 && prm->qdeg != sp->degree + 1)))
-    return fail(MFA_ERR_UNSUPPORTED,
-                "mfa_form_create: vector hex kernels cover FP64 Laplace/elasticity/hyperelasticity with p+1 points");
+  if (ct == MFA_CELL_HEX8 && sp->ncomp == 3) {
+    const int n = sp->degree + 1, nq = prm->qdeg > 0 ? prm->qdeg : n;
+    const bool hyper = kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC;
+    const bool rule_ok = nq == n || (!hyper && nq == n + 1 && n <= 7) || (hyper && nq == 2 * n && n <= 4);
+    if (kind == MFA_FORM_MASS || kind == MFA_FORM_HELMHOLTZ || prm->precision != MFA_PREC_FP64 || !rule_ok)
+      return fail(MFA_ERR_UNSUPPORTED,
+                  "mfa_form_create: vector hex kernels cover FP64 Laplace/elasticity (p+1 or p+2 points) and "
+                  "hyperelasticity (p+1, or 2p+2 for p <= 3)");
+  }
   if (ct == MFA_CELL_TET4) {
     const bool ok = (sp->ncomp == 1 && kind <= MFA_FORM_HELMHOLTZ) ||
                     (sp->degree >= 2 && sp->ncomp == 3 && kind >= MFA_FORM_LAPLACE && kind != MFA_FORM_HELMHOLTZ);
@@ -656,7 +661,8 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
   if (!rc && ct == MFA_CELL_HEX8) {
     const int n = sp->degree + 1;
     f->nq1 = prm->qdeg > 0 ? prm->qdeg : n;
-    if (!(f->nq1 == n || (f->nq1 == n + 1 && n <= 7)) || n > 9)
+    const bool vec_2n = sp->ncomp == 3 && f->nq1 == 2 * n && n <= 4;  // validated above for the hyperelastic forms
+    if (!(f->nq1 == n || (f->nq1 == n + 1 && n <= 7) || vec_2n) || n > 9)
       rc = fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: Q%d with %d Gauss points per direction", sp->degree, f->nq1);
     if (!rc) rc = hex_tables(f);
     f->nq = f->nq1 * f->nq1 * f->nq1;

@@ -52,7 +52,7 @@ struct EShape {
   static constexpr int P = N * N * N;
   static constexpr int CB = CBX > 0 ? CBX : eo_cb_for(N, 256);
   static constexpr int T = ceil32(CB * L);
-  static constexpr int SMEM = 5 * CB * P * 8;
+  static constexpr int SMEM = 4 * CB * P * 8;
 };
 
 template <int KIND>
@@ -111,6 +111,9 @@ __device__ __forceinline__ void eo_sweep(const double* in, double* out, int a, i
   }
 }
 
+// Four shared-memory planes of CB x n^3 doubles: U (gathered input, then the z-derivative and its flux, then
+// the B^T results), V (values at the Gauss points, then the test-side accumulation), F0 and F1 (x- and
+// y-derivatives and their fluxes).
 template <int N, int KIND, bool COLOUR, int CBX = 0>
 __device__ __forceinline__ void eo_batch(const HexApplyArgs& a, int64_t batch, double* smem) {
   using S = EShape<N, CBX>;
@@ -123,14 +126,12 @@ __device__ __forceinline__ void eo_batch(const HexApplyArgs& a, int64_t batch, d
   const bool valid = cl < ncb;
   double* U0 = smem;
   double* V0 = U0 + CB * P;
-  double* G0 = V0 + CB * P;
-  double* G1 = G0 + CB * P;
-  double* G2 = G1 + CB * P;
+  double* F00 = V0 + CB * P;
+  double* F10 = F00 + CB * P;
   double* U = U0 + cl * P;
   double* V = V0 + cl * P;
-  double* F0 = G0 + cl * P;
-  double* F1 = G1 + cl * P;
-  double* F2 = G2 + cl * P;
+  double* F0 = F00 + cl * P;
+  double* F1 = F10 + cl * P;
   const double* geom = static_cast<const double*>(a.geom);
   auto cell_of = [&](int c) -> int64_t { return a.cell_list ? (int64_t)__ldg(a.cell_list + c0 + c) : c0 + c; };
 
@@ -148,13 +149,13 @@ __device__ __forceinline__ void eo_batch(const HexApplyArgs& a, int64_t batch, d
   if constexpr (KIND == MFA_FORM_MASS) {
     for (int i = t; i < ncb * P; i += T) {
       const int c = i / P, q = i - c * P;
-      U0[i] = __ldg(geom + cell_of(c) * P + q) * V0[i];
+      V0[i] *= __ldg(geom + cell_of(c) * P + q);
     }
   } else {
     if (valid) {
       eo_sweep<N, 0, 2, -1, false>(V, F0, la, lb);  // D in x
       eo_sweep<N, 1, 2, -1, false>(V, F1, la, lb);  // D in y
-      eo_sweep<N, 2, 2, -1, false>(V, F2, la, lb);  // D in z
+      eo_sweep<N, 2, 2, -1, false>(V, U, la, lb);   // D in z, into U's plane
     }
     __syncthreads();
     for (int i = t; i < ncb * P; i += T) {  // pointwise physics, point-parallel
@@ -163,32 +164,32 @@ __device__ __forceinline__ void eo_batch(const HexApplyArgs& a, int64_t batch, d
       double g[NG];
 #pragma unroll
       for (int e = 0; e < NG; ++e) g[e] = __ldg(gc + (int64_t)e * P);
-      const double d0 = G0[i], d1 = G1[i], d2 = G2[i];
-      G0[i] = fma(g[0], d0, fma(g[3], d1, g[4] * d2));
-      G1[i] = fma(g[3], d0, fma(g[1], d1, g[5] * d2));
-      G2[i] = fma(g[4], d0, fma(g[5], d1, g[2] * d2));
-      if constexpr (KIND == MFA_FORM_HELMHOLTZ) U0[i] = g[6] * V0[i];
-      else U0[i] = 0.0;
+      const double d0 = F00[i], d1 = F10[i], d2 = U0[i];
+      F00[i] = fma(g[0], d0, fma(g[3], d1, g[4] * d2));
+      F10[i] = fma(g[3], d0, fma(g[1], d1, g[5] * d2));
+      U0[i] = fma(g[4], d0, fma(g[5], d1, g[2] * d2));
+      if constexpr (KIND == MFA_FORM_HELMHOLTZ) V0[i] *= g[6];
+      else V0[i] = 0.0;
     }
     __syncthreads();
-    if (valid) eo_sweep<N, 0, 3, -1, true>(F0, U, la, lb);  // + D_x^T f0
+    if (valid) eo_sweep<N, 0, 3, -1, true>(F0, V, la, lb);  // + D_x^T f0
     __syncthreads();
-    if (valid) eo_sweep<N, 1, 3, -1, true>(F1, U, la, lb);  // + D_y^T f1
+    if (valid) eo_sweep<N, 1, 3, -1, true>(F1, V, la, lb);  // + D_y^T f1
     __syncthreads();
-    if (valid) eo_sweep<N, 2, 3, -1, true>(F2, U, la, lb);  // + D_z^T f2
+    if (valid) eo_sweep<N, 2, 3, -1, true>(U, V, la, lb);   // + D_z^T f2
   }
   __syncthreads();
-  if (valid) eo_sweep<N, 2, 1, 1, false>(U, V, la, lb);  // B^T in z
+  if (valid) eo_sweep<N, 2, 1, 1, false>(V, U, la, lb);  // B^T in z
   __syncthreads();
-  if (valid) eo_sweep<N, 1, 1, 1, false>(V, U, la, lb);  // B^T in y
+  if (valid) eo_sweep<N, 1, 1, 1, false>(U, V, la, lb);  // B^T in y
   __syncthreads();
-  if (valid) eo_sweep<N, 0, 1, 1, false>(U, V, la, lb);  // B^T in x
+  if (valid) eo_sweep<N, 0, 1, 1, false>(V, U, la, lb);  // B^T in x
   __syncthreads();
   for (int i = t; i < ncb * P; i += T) {  // scatter-add, point-parallel
     const int c = i / P, k = i - c * P;
     const int32_t node = __ldg(a.cell_node + cell_of(c) * P + k);
-    if constexpr (COLOUR) a.y[node] += V0[i];  // no other cell of this colour touches `node`
-    else atomicAdd(a.y + node, V0[i]);
+    if constexpr (COLOUR) a.y[node] += U0[i];  // no other cell of this colour touches `node`
+    else atomicAdd(a.y + node, U0[i]);
   }
   __syncthreads();
 }

@@ -25,13 +25,13 @@ namespace hexv {
 using hexk::Shape;
 using hexk::Smem;
 
-template <int N, int KIND, int LAW, bool COLOUR>
-__device__ __forceinline__ void cell_batch(const HexVecArgs& a, int64_t batch, const Smem<N, N, MFA_PREC_FP64>& sm) {
-  using S = Shape<N, N>;
-  constexpr int P = S::P, CB = S::CB;
+template <int N, int NQ, int KIND, int LAW, bool COLOUR>
+__device__ __forceinline__ void cell_batch(const HexVecArgs& a, int64_t batch, const Smem<N, NQ, MFA_PREC_FP64>& sm) {
+  using S = Shape<N, NQ>;
+  constexpr int PN = S::PN, PQ = S::PQ, CB = S::CB;
   constexpr bool JAC = KIND == MFA_FORM_HYPER_JAC;
-  const double* sB = sm.sB;
-  const double* sD = sm.sD;
+  const double* sB = sm.sB;  // [NQ][N]
+  const double* sD = sm.sD;  // [NQ][NQ]
   double* A = sm.A;
   double* Bf = sm.Bf;
   double* F0 = sm.F0;
@@ -39,47 +39,48 @@ __device__ __forceinline__ void cell_batch(const HexVecArgs& a, int64_t batch, c
   double* F2 = sm.F2;
   const int cl = sm.cl, pt = sm.pt;
   const int64_t idx = batch * CB + cl;
-  const bool active = cl < CB && idx < a.count && pt < P;
+  const bool valid = cl < CB && idx < a.count;
   int64_t cell = 0;
   int32_t node = 0;
-  if (active) {
-    cell = a.cell_list ? (int64_t)__ldg(a.cell_list + idx) : idx;
-    node = __ldg(a.cell_node + cell * P + pt);
-  }
-  const int i = pt % N, j = (pt / N) % N, k = pt / (N * N);
+  if (valid) cell = a.cell_list ? (int64_t)__ldg(a.cell_list + idx) : idx;
+  if (valid && pt < PN) node = __ldg(a.cell_node + cell * PN + pt);
+  const bool atq = valid && pt < PQ;  // this thread owns Gauss point pt
+  const int qi = pt % NQ, qj = (pt / NQ) % NQ, qk = pt / (NQ * NQ);
 
-  // reference gradient of component c of the nodal field v at this thread's point
+  // reference gradient of component c of the nodal field v at Gauss point pt
   auto ref_grad = [&](const double* v, int c, double g[3]) {
-    if (active) A[pt] = __ldg(v + 3 * (int64_t)node + c);
+    if (valid && pt < PN) A[pt] = __ldg(v + 3 * (int64_t)node + c);
     __syncthreads();
-    if (active) {  // B in x
+    if (valid && pt < NQ * N * N) {  // B in x: (NQ, N, N) <- (N, N, N)
+      const int i = pt % NQ, jk = pt / NQ;
       double s = 0.0;
 #pragma unroll
-      for (int m = 0; m < N; ++m) s = fma(sB[i * N + m], A[m + N * (j + N * k)], s);
+      for (int m = 0; m < N; ++m) s = fma(sB[i * N + m], A[m + N * jk], s);
       Bf[pt] = s;
     }
     __syncthreads();
-    if (active) {  // B in y
+    if (valid && pt < NQ * NQ * N) {  // B in y: (NQ, NQ, N) <- (NQ, N, N)
+      const int i = pt % NQ, j = (pt / NQ) % NQ, k = pt / (NQ * NQ);
       double s = 0.0;
 #pragma unroll
-      for (int m = 0; m < N; ++m) s = fma(sB[j * N + m], Bf[i + N * (m + N * k)], s);
+      for (int m = 0; m < N; ++m) s = fma(sB[j * N + m], Bf[i + NQ * (m + N * k)], s);
       A[pt] = s;
     }
     __syncthreads();
-    if (active) {  // B in z: u_c at the Gauss points
+    if (atq) {  // B in z: (NQ, NQ, NQ) <- (NQ, NQ, N), u_c at the Gauss points
       double s = 0.0;
 #pragma unroll
-      for (int m = 0; m < N; ++m) s = fma(sB[k * N + m], A[i + N * (j + N * m)], s);
+      for (int m = 0; m < N; ++m) s = fma(sB[qk * N + m], A[qi + NQ * (qj + NQ * m)], s);
       Bf[pt] = s;
     }
     __syncthreads();
     double d0 = 0.0, d1 = 0.0, d2 = 0.0;
-    if (active) {  // collocation derivatives
+    if (atq) {  // collocation derivatives on the Gauss points
 #pragma unroll
-      for (int m = 0; m < N; ++m) {
-        d0 = fma(sD[i * N + m], Bf[m + N * (j + N * k)], d0);
-        d1 = fma(sD[j * N + m], Bf[i + N * (m + N * k)], d1);
-        d2 = fma(sD[k * N + m], Bf[i + N * (j + N * m)], d2);
+      for (int m = 0; m < NQ; ++m) {
+        d0 = fma(sD[qi * NQ + m], Bf[m + NQ * (qj + NQ * qk)], d0);
+        d1 = fma(sD[qj * NQ + m], Bf[qi + NQ * (m + NQ * qk)], d1);
+        d2 = fma(sD[qk * NQ + m], Bf[qi + NQ * (qj + NQ * m)], d2);
       }
     }
     g[0] = d0;
@@ -102,13 +103,13 @@ __device__ __forceinline__ void cell_batch(const HexVecArgs& a, int64_t batch, c
   double h[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   double v0[3] = {0.0, 0.0, 0.0};
   bool ok = true;
-  if (active) {
+  if (atq) {
     const double* gp = a.geom + cell * a.geom_stride + pt;
     if constexpr (KIND == MFA_FORM_LAPLACE) {
       // G = w|J| J^{-1} J^{-T}: (00, 11, 22, 01, 02, 12), one scalar Laplacian per component
       double G[6];
 #pragma unroll
-      for (int e = 0; e < 6; ++e) G[e] = __ldg(gp + e * P);
+      for (int e = 0; e < 6; ++e) G[e] = __ldg(gp + e * PQ);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         h[c][0] = fma(G[0], g[c][0], fma(G[3], g[c][1], G[4] * g[c][2]));
@@ -118,8 +119,8 @@ __device__ __forceinline__ void cell_batch(const HexVecArgs& a, int64_t batch, c
     } else {
       double Ji[3][3];
 #pragma unroll
-      for (int e = 0; e < 9; ++e) Ji[e / 3][e % 3] = __ldg(gp + e * P);
-      const double wdet = __ldg(gp + 9 * P);
+      for (int e = 0; e < 9; ++e) Ji[e / 3][e % 3] = __ldg(gp + e * PQ);
+      const double wdet = __ldg(gp + 9 * PQ);
       double gu[3][3], gc[3][3], f1[3][3];
 #pragma unroll
       for (int c = 0; c < 3; ++c)
@@ -146,42 +147,44 @@ __device__ __forceinline__ void cell_batch(const HexVecArgs& a, int64_t batch, c
   // integrate back and scatter, one component at a time
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const double vc = v0[c];
-    if (active) {
+    if (atq) {
       F0[pt] = h[c][0];
       F1[pt] = h[c][1];
       F2[pt] = h[c][2];
     }
     __syncthreads();
-    if (active) {  // r = v0 + sum_d D_d^T f_d
-      double r = vc;
+    if (atq) {  // r = v0 + sum_d D_d^T f_d
+      double r = v0[c];
 #pragma unroll
-      for (int m = 0; m < N; ++m) {
-        r = fma(sD[m * N + i], F0[m + N * (j + N * k)], r);
-        r = fma(sD[m * N + j], F1[i + N * (m + N * k)], r);
-        r = fma(sD[m * N + k], F2[i + N * (j + N * m)], r);
+      for (int m = 0; m < NQ; ++m) {
+        r = fma(sD[m * NQ + qi], F0[m + NQ * (qj + NQ * qk)], r);
+        r = fma(sD[m * NQ + qj], F1[qi + NQ * (m + NQ * qk)], r);
+        r = fma(sD[m * NQ + qk], F2[qi + NQ * (qj + NQ * m)], r);
       }
       A[pt] = r;
     }
     __syncthreads();
-    if (active) {  // B^T in z
+    if (valid && pt < NQ * NQ * N) {  // B^T in z: (NQ, NQ, N) <- (NQ, NQ, NQ)
+      const int ij = pt % (NQ * NQ), k = pt / (NQ * NQ);
       double s = 0.0;
 #pragma unroll
-      for (int m = 0; m < N; ++m) s = fma(sB[m * N + k], A[i + N * (j + N * m)], s);
+      for (int m = 0; m < NQ; ++m) s = fma(sB[m * N + k], A[ij + NQ * NQ * m], s);
       Bf[pt] = s;
     }
     __syncthreads();
-    if (active) {  // B^T in y
+    if (valid && pt < NQ * N * N) {  // B^T in y: (NQ, N, N) <- (NQ, NQ, N)
+      const int i = pt % NQ, b = (pt / NQ) % N, k = pt / (NQ * N);
       double s = 0.0;
 #pragma unroll
-      for (int m = 0; m < N; ++m) s = fma(sB[m * N + j], Bf[i + N * (m + N * k)], s);
+      for (int m = 0; m < NQ; ++m) s = fma(sB[m * N + b], Bf[i + NQ * (m + NQ * k)], s);
       A[pt] = s;
     }
     __syncthreads();
-    if (active) {  // B^T in x and scatter-add
+    if (valid && pt < PN) {  // B^T in x and scatter-add: (N, N, N) <- (NQ, N, N)
+      const int i = pt % N, bc = pt / N;
       double s = 0.0;
 #pragma unroll
-      for (int m = 0; m < N; ++m) s = fma(sB[m * N + i], A[m + N * (j + N * k)], s);
+      for (int m = 0; m < NQ; ++m) s = fma(sB[m * N + i], A[m + NQ * bc], s);
       double* dst = a.y + 3 * (int64_t)node + c;
       if constexpr (COLOUR) *dst += s;  // no other cell of this colour touches `node`
       else atomicAdd(dst, s);
@@ -191,21 +194,22 @@ __device__ __forceinline__ void cell_batch(const HexVecArgs& a, int64_t batch, c
   __syncthreads();
 }
 
-template <int N, int KIND, int LAW, bool COLOUR>
-__global__ void __launch_bounds__(Shape<N, N>::T) apply_kernel(const __grid_constant__ HexTables tb,
-                                                               const HexVecArgs a) {
+template <int N, int NQ, int KIND, int LAW, bool COLOUR>
+__global__ void __launch_bounds__(Shape<N, NQ>::T) apply_kernel(const __grid_constant__ HexTables tb,
+                                                                const HexVecArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<N, N, MFA_PREC_FP64> sm;
+  Smem<N, NQ, MFA_PREC_FP64> sm;
   sm.init(smem_raw, tb);
-  constexpr int CB = Shape<N, N>::CB;
+  constexpr int CB = Shape<N, NQ>::CB;
   const int64_t nbatch = (a.count + CB - 1) / CB;
-  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) cell_batch<N, KIND, LAW, COLOUR>(a, batch, sm);
+  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x)
+    cell_batch<N, NQ, KIND, LAW, COLOUR>(a, batch, sm);
 }
 
-template <int N, int KIND, int LAW, bool COLOUR>
+template <int N, int NQ, int KIND, int LAW, bool COLOUR>
 cudaError_t launch(const HexTables& tb, const HexVecArgs& a, int sm_count, cudaStream_t s) {
-  using S = Shape<N, N>;
-  auto kern = apply_kernel<N, KIND, LAW, COLOUR>;
+  using S = Shape<N, NQ>;
+  auto kern = apply_kernel<N, NQ, KIND, LAW, COLOUR>;
   static int blocks_per_sm = -1;
   if (blocks_per_sm < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
@@ -222,15 +226,29 @@ cudaError_t launch(const HexTables& tb, const HexVecArgs& a, int sm_count, cudaS
   return cudaGetLastError();
 }
 
-template <int N>
-cudaError_t dispatch(int kind, int law, bool colour, const HexTables& tb, const HexVecArgs& a, int sm_count,
-                     cudaStream_t s) {
+// Linear vector forms (vector Laplacian, elasticity) at NQ points per direction.
+template <int N, int NQ>
+cudaError_t dispatch_linear(int kind, bool colour, const HexTables& tb, const HexVecArgs& a, int sm_count,
+                            cudaStream_t s) {
+  switch (kind) {
+    case MFA_FORM_LAPLACE:
+      return colour ? launch<N, NQ, MFA_FORM_LAPLACE, 0, true>(tb, a, sm_count, s)
+                    : launch<N, NQ, MFA_FORM_LAPLACE, 0, false>(tb, a, sm_count, s);
+    case MFA_FORM_ELASTICITY:
+      return colour ? launch<N, NQ, MFA_FORM_ELASTICITY, 0, true>(tb, a, sm_count, s)
+                    : launch<N, NQ, MFA_FORM_ELASTICITY, 0, false>(tb, a, sm_count, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Hyperelastic forms at NQ points per direction.
+template <int N, int NQ>
+cudaError_t dispatch_hyper(int kind, int law, bool colour, const HexTables& tb, const HexVecArgs& a, int sm_count,
+                           cudaStream_t s) {
   const bool nh = law == MFA_LAW_NEOHOOKE;
 #define MFA_HEXV_CASE(KIND, LAW) \
-  return colour ? launch<N, KIND, LAW, true>(tb, a, sm_count, s) : launch<N, KIND, LAW, false>(tb, a, sm_count, s)
+  return colour ? launch<N, NQ, KIND, LAW, true>(tb, a, sm_count, s) : launch<N, NQ, KIND, LAW, false>(tb, a, sm_count, s)
   switch (kind) {
-    case MFA_FORM_LAPLACE: MFA_HEXV_CASE(MFA_FORM_LAPLACE, 0);
-    case MFA_FORM_ELASTICITY: MFA_HEXV_CASE(MFA_FORM_ELASTICITY, 0);
     case MFA_FORM_HYPER_RES:
       if (nh) MFA_HEXV_CASE(MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE);
       MFA_HEXV_CASE(MFA_FORM_HYPER_RES, MFA_LAW_SVK);
@@ -239,6 +257,23 @@ cudaError_t dispatch(int kind, int law, bool colour, const HexTables& tb, const 
       MFA_HEXV_CASE(MFA_FORM_HYPER_JAC, MFA_LAW_SVK);
   }
 #undef MFA_HEXV_CASE
+  return cudaErrorInvalidValue;
+}
+
+// p+1 points (every form), p+2 points (linear forms, Table 2's elasticity rule, n <= 7) and 2p+2 points
+// (hyperelastic forms, Table 2's hyperelasticity rule, n <= 4).
+template <int N>
+cudaError_t dispatch(int nq, int kind, int law, bool colour, const HexTables& tb, const HexVecArgs& a, int sm_count,
+                     cudaStream_t s) {
+  const bool hyper = kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC;
+  if (nq == N) return hyper ? dispatch_hyper<N, N>(kind, law, colour, tb, a, sm_count, s)
+                            : dispatch_linear<N, N>(kind, colour, tb, a, sm_count, s);
+  if constexpr (N + 1 <= 8) {  // n + 1 points: up to 512 threads per cell
+    if (nq == N + 1 && !hyper) return dispatch_linear<N, N + 1>(kind, colour, tb, a, sm_count, s);
+  }
+  if constexpr (2 * N <= 8) {
+    if (nq == 2 * N && hyper) return dispatch_hyper<N, 2 * N>(kind, law, colour, tb, a, sm_count, s);
+  }
   return cudaErrorInvalidValue;
 }
 

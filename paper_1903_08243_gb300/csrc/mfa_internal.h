@@ -71,10 +71,11 @@ struct HexVecArgs {
   double lam, mu, b0, b1, b2;
   int* err;
 };
-cudaError_t hex_vector_launch_a(int n, int kind, int law, bool colour, const HexTables& tb, const HexVecArgs& a,
-                                int sm_count, cudaStream_t s);  // n = 2..5
-cudaError_t hex_vector_launch_b(int n, int kind, int law, bool colour, const HexTables& tb, const HexVecArgs& a,
-                                int sm_count, cudaStream_t s);  // n = 6..9
+// nq: n (every form), n + 1 (vector Laplacian, elasticity), 2n (hyperelastic forms, n <= 4)
+cudaError_t hex_vector_launch_a(int n, int nq, int kind, int law, bool colour, const HexTables& tb,
+                                const HexVecArgs& a, int sm_count, cudaStream_t s);  // n = 2..5
+cudaError_t hex_vector_launch_b(int n, int nq, int kind, int law, bool colour, const HexTables& tb,
+                                const HexVecArgs& a, int sm_count, cudaStream_t s);  // n = 6..9
 
 // Launch the sum-factorised FP64 action for cells [list].  Returns a cudaError_t.
 struct LaunchConfig;

@@ -87,7 +87,7 @@ def test_hex_vector_colour_is_deterministic(ctx):
 def test_hex_vector_rejections(ctx):
     case = hex_case(2, 2, ncomp=3)
     for kind, kw in [("mass", {}), ("helmholtz", {}), ("elasticity", {"precision": mfa.MFA_PREC_FP32}),
-                     ("elasticity", {"qdeg": 4})]:
+                     ("elasticity", {"qdeg": 5}), ("hyper_res", {"qdeg": 4})]:
         with pytest.raises(mfa.MfaError) as e:
             make_form(ctx, case, kind, **kw)
         assert e.value.code == mfa.MFA_ERR_UNSUPPORTED
@@ -109,3 +109,24 @@ def test_hex_vector_domain_error_is_reported(ctx):
     with pytest.raises(mfa.MfaError) as e:
         ctx.sync()
     assert e.value.code == mfa.MFA_ERR_DOMAIN
+
+
+@pytest.mark.parametrize("p, kind, law", [(1, "elasticity", 0), (3, "elasticity", 0), (6, "elasticity", 0),
+                                          (2, "laplace", 0), (1, "hyper_res", mfa.MFA_LAW_NEOHOOKE),
+                                          (2, "hyper_jac", mfa.MFA_LAW_SVK), (3, "hyper_res", mfa.MFA_LAW_SVK),
+                                          (3, "hyper_jac", mfa.MFA_LAW_NEOHOOKE)])
+def test_hex_vector_table2_quadrature(ctx, p, kind, law):
+    """Table 2's rules on hexahedra: p+2 points per direction for the linear vector forms, 2p+2 for
+    hyperelasticity."""
+    qdeg = 2 * p + 2 if kind.startswith("hyper") else p + 2
+    case = hex_case({1: 4, 2: 3, 3: 2, 6: 2}[p], p, ncomp=3)
+    u, x = inputs(case, kind, seed=20 + p)
+    kw = dict(lam=1.1, mu=0.9, law=law)
+    ref = oracle_problem(case, kind, qdeg=qdeg, ucoef=u if kind == "hyper_jac" else None, **kw).apply(x)
+    form = make_form(ctx, case, kind, qdeg=qdeg, **kw)
+    assert form.info().nq == qdeg ** 3
+    if kind == "hyper_jac":
+        form.set_coefficient(torch.from_numpy(u).cuda())
+    y = form.apply(torch.from_numpy(x).cuda())
+    ctx.sync()
+    check(y.cpu().numpy(), ref)
