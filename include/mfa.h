@@ -145,7 +145,9 @@ MFA_API int mfa_mesh_destroy(mfa_mesh *mesh);
 /* Continuous Lagrange space of `degree` (P1..P6 on tets, Q1..Q8 on hexes) with
  * ncomp in {1, 3}.  cell_node [ncell][nloc] (host, int32) is the cell->node
  * map of Section 2.2 (`cell2dof`); entries must lie in [0, nnode) and be
- * distinct within a cell.  The mesh must outlive the space.  Local node order:
+ * distinct within a cell.  cell_node = NULL: the library builds the map from
+ * the mesh (mfa_build_cell_node; nnode is then ignored; read it back with
+ * mfa_space_get_cell_node and the node count with mfa_space_ndof).  The mesh must outlive the space.  Local node order:
  * hex, the GLL tensor points with x fastest; P1/P2 tets, the vertices, then
  * the midpoints of edges (0,1), (0,2), (0,3), (1,2), (1,3), (2,3); P3..P6
  * tets, the equispaced lattice points (i, j, k)/p of the reference tet
@@ -153,6 +155,23 @@ MFA_API int mfa_mesh_destroy(mfa_mesh *mesh);
  * j, then k. */
 MFA_API int mfa_space_create(mfa_ctx *ctx, mfa_mesh *mesh, int degree, int ncomp, const int32_t *cell_node,
                      int64_t nnode, mfa_space **out);
+/* The space's cell -> node map, copied to host memory [ncell][nloc]. */
+MFA_API int mfa_space_get_cell_node(const mfa_space *space, int32_t *cell_node);
+
+/* Cell -> node map of the continuous Q_p (hex, p <= 8) or P_p (tet, p <= 6)
+ * space from the vertex connectivity alone (host only, no device), in the
+ * local node order of mfa_space_create.  A node on a vertex, edge or face is
+ * the same global node in every cell that contains it, whatever the cells'
+ * local vertex orders.  Nodes 0..nvert-1 are the mesh vertices; the others
+ * follow in order of first appearance along the cells.  cell_node
+ * [ncell][nloc] is caller-allocated; *nnode receives the node count.
+ * mfa_space_create with cell_node = NULL calls this. */
+MFA_API int mfa_build_cell_node(int cell_type, int degree, int64_t ncell, const int32_t *cell_vert, int64_t nvert,
+                                int32_t *cell_node, int64_t *nnode);
+/* Physical positions of the nodes, out [nnode][3] (host only): the trilinear
+ * (hex) or affine (tet) image of the reference nodes. */
+MFA_API int mfa_node_coords(int cell_type, int degree, int64_t ncell, const int32_t *cell_vert, const double *coords,
+                            const int32_t *cell_node, int64_t nnode, double *out);
 MFA_API int mfa_space_ndof(const mfa_space *space, int64_t *ndof);
 MFA_API int mfa_space_destroy(mfa_space *space);
 

@@ -93,6 +93,9 @@ _SIGS = {
     "mfa_mesh_upload": ([_VP, _I, _I64, _I64, _VP, _VP, _PP], _I),
     "mfa_mesh_destroy": ([_VP], _I),
     "mfa_space_create": ([_VP, _VP, _I, _I, _VP, _I64, _PP], _I),
+    "mfa_space_get_cell_node": ([_VP, _VP], _I),
+    "mfa_build_cell_node": ([_I, _I, _I64, _VP, _I64, _VP, ctypes.POINTER(_I64)], _I),
+    "mfa_node_coords": ([_I, _I, _I64, _VP, _VP, _VP, _I64, _VP], _I),
     "mfa_space_ndof": ([_VP, ctypes.POINTER(_I64)], _I),
     "mfa_space_destroy": ([_VP], _I),
     "mfa_form_create": ([_VP, _VP, ctypes.POINTER(mfa_form_params), _PP], _I),
@@ -205,10 +208,12 @@ def mfa_mesh_destroy(mesh):
     _check(lib().mfa_mesh_destroy(mesh))
 
 
-def mfa_space_create(ctx, mesh, degree, ncomp, cell_node, nnode):
-    cell_node = np.ascontiguousarray(cell_node, dtype=np.int32)
+def mfa_space_create(ctx, mesh, degree, ncomp, cell_node=None, nnode=0):
+    """cell_node None: the library builds the map from the mesh."""
+    if cell_node is not None:
+        cell_node = np.ascontiguousarray(cell_node, dtype=np.int32)
     h = ctypes.c_void_p()
-    _check(lib().mfa_space_create(ctx, mesh, degree, ncomp, _ptr(cell_node), nnode, ctypes.byref(h)))
+    _check(lib().mfa_space_create(ctx, mesh, degree, ncomp, _ptr(cell_node), int(nnode), ctypes.byref(h)))
     return h
 
 
@@ -240,6 +245,38 @@ def mfa_form_get_info(form):
 
 def mfa_form_destroy(form):
     _check(lib().mfa_form_destroy(form))
+
+
+def _nloc(cell_type, degree):
+    if cell_type == MFA_CELL_HEX8:
+        return (degree + 1) ** 3
+    return {1: 4, 2: 10}.get(degree, (degree + 1) * (degree + 2) * (degree + 3) // 6)
+
+
+def mfa_build_cell_node(cell_type, degree, cell_vert, nvert):
+    """Conforming cell -> node map from the vertex connectivity (host): returns (cell_node, nnode)."""
+    cv = np.ascontiguousarray(cell_vert, dtype=np.int32)
+    cn = np.empty((cv.shape[0], _nloc(cell_type, degree)), dtype=np.int32)
+    nn = ctypes.c_int64()
+    _check(lib().mfa_build_cell_node(cell_type, degree, cv.shape[0], cv.ctypes.data, int(nvert), cn.ctypes.data,
+                                     ctypes.byref(nn)))
+    return cn, nn.value
+
+
+def mfa_node_coords(cell_type, degree, cell_vert, coords, cell_node, nnode):
+    cv = np.ascontiguousarray(cell_vert, dtype=np.int32)
+    X = np.ascontiguousarray(coords, dtype=np.float64)
+    cn = np.ascontiguousarray(cell_node, dtype=np.int32)
+    out = np.empty((int(nnode), 3))
+    _check(lib().mfa_node_coords(cell_type, degree, cv.shape[0], cv.ctypes.data, X.ctypes.data, cn.ctypes.data,
+                                 int(nnode), out.ctypes.data))
+    return out
+
+
+def mfa_space_get_cell_node(space, ncell, nloc):
+    out = np.empty((ncell, nloc), dtype=np.int32)
+    _check(lib().mfa_space_get_cell_node(space, out.ctypes.data))
+    return out
 
 
 def mfa_order_rcm(cell_vert, cell_node, nnode, nvert=None):
@@ -501,11 +538,15 @@ class Mesh:
 
 
 class Space:
-    def __init__(self, mesh, degree, ncomp, cell_node, nnode):
+    def __init__(self, mesh, degree, ncomp, cell_node=None, nnode=0):
         self.mesh = mesh
-        self.degree, self.ncomp, self.nnode = degree, ncomp, int(nnode)
+        self.degree, self.ncomp = degree, ncomp
         self.h = mfa_space_create(mesh.ctx.h, mesh.h, degree, ncomp, cell_node, nnode)
         self.ndof = mfa_space_ndof(self.h)
+        self.nnode = self.ndof // ncomp
+
+    def cell_node(self):
+        return mfa_space_get_cell_node(self.h, self.mesh.ncell, _nloc(self.mesh.cell_type, self.degree))
 
     def __del__(self):
         try:

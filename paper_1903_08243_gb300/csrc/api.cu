@@ -469,10 +469,20 @@ int mfa_mesh_destroy(mfa_mesh* m) {
 
 int mfa_space_create(mfa_ctx* ctx, mfa_mesh* mesh, int degree, int ncomp, const int32_t* cell_node, int64_t nnode,
                      mfa_space** out) {
-  if (!ctx || !mesh || !out || !cell_node) return fail(MFA_ERR_ARG, "mfa_space_create: NULL argument");
+  if (!ctx || !mesh || !out) return fail(MFA_ERR_ARG, "mfa_space_create: NULL argument");
   *out = nullptr;
   const int nl = nloc_of(mesh->cell_type, degree);
   if (nl < 0) return fail(MFA_ERR_UNSUPPORTED, "mfa_space_create: degree %d on cell type %d", degree, mesh->cell_type);
+  std::vector<int32_t> built;
+  if (!cell_node) {  // build the map from the mesh's vertex connectivity
+    std::vector<int32_t> cv((size_t)mesh->ncell * mesh->cell_type);
+    if (!cv.empty())
+      MFA_CUDA(cudaMemcpy(cv.data(), mesh->d_cell_vert, cv.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    built.resize((size_t)mesh->ncell * nl);
+    int rc = mfa_build_cell_node(mesh->cell_type, degree, mesh->ncell, cv.data(), mesh->nvert, built.data(), &nnode);
+    if (rc) return rc;
+    cell_node = built.data();
+  }
   if (ncomp != 1 && ncomp != 3) return fail(MFA_ERR_ARG, "mfa_space_create: ncomp %d", ncomp);
   if (nnode <= 0 || nnode * ncomp > INT32_MAX) return fail(MFA_ERR_ARG, "mfa_space_create: nnode %lld", (long long)nnode);
   {
@@ -513,6 +523,14 @@ int mfa_space_create(mfa_ctx* ctx, mfa_mesh* mesh, int degree, int ncomp, const 
 int mfa_space_ndof(const mfa_space* s, int64_t* ndof) {
   if (!s || !ndof) return fail(MFA_ERR_ARG, "mfa_space_ndof: NULL argument");
   *ndof = s->nnode * s->ncomp;
+  return MFA_OK;
+}
+
+int mfa_space_get_cell_node(const mfa_space* s, int32_t* out) {
+  if (!s || !out) return fail(MFA_ERR_ARG, "mfa_space_get_cell_node: NULL argument");
+  const size_t bytes = sizeof(int32_t) * (size_t)s->nloc * s->mesh->ncell;
+  MFA_CUDA(cudaSetDevice(s->device));
+  if (bytes) MFA_CUDA(cudaMemcpy(out, s->d_cell_node, bytes, cudaMemcpyDeviceToHost));
   return MFA_OK;
 }
 

@@ -482,3 +482,23 @@ def test_handles_may_be_destroyed_after_their_context(ctx):
     x = fi.uniform_vector(case["nnode"], seed=30)
     ref = oracle_problem(case, "helmholtz").apply(x)
     compare(run(ctx, gpu_form(ctx, case, "helmholtz"), x), ref)
+
+
+@pytest.mark.parametrize("cell, p, kind", [("hex", 3, "helmholtz"), ("tet", 2, "elasticity"), ("tet", 4, "laplace")])
+def test_space_with_library_built_map(ctx, cell, p, kind):
+    """mfa_space_create without a map: the library builds it from the mesh; the operator on that map matches the
+    oracle on the same map (read back from the space)."""
+    mesh = fi.hex_box_mesh(3, perturb=0.1, seed=8) if cell == "hex" else fi.kuhn_tet_mesh(3, perturb=0.1, seed=8)
+    ct = 8 if cell == "hex" else 4
+    ncomp = 3 if kind == "elasticity" else 1
+    m = mfa.Mesh(ctx, ct, mesh.coords, mesh.cell_vert)
+    sp = mfa.Space(m, p, ncomp)
+    cn = sp.cell_node()
+    f = mfa.Form(sp, KIND_NAMES[kind])
+    x = fi.uniform_vector(sp.ndof, seed=9)
+    qdeg = p + 1 if cell == "hex" else 2 * p
+    ref = oracle.Problem(ct, mesh.coords, mesh.cell_vert, p, cn, sp.nnode, KIND_NAMES[kind], ncomp=ncomp,
+                         qdeg=qdeg).apply(x)
+    y = f.apply(torch.from_numpy(x).cuda())
+    ctx.sync()
+    compare(y.cpu().numpy(), ref)
