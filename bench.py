@@ -67,6 +67,8 @@ def parse_args():
                          "(neo-Hookean residual, St Venant-Kirchhoff Jacobian action)")
     ap.add_argument("--scatter", choices=["atomic", "colour", "warp"], default="atomic",
                     help="scatter at form creation (the autotuner may change it)")
+    ap.add_argument("--geometry", choices=["stored", "onthefly"], default="stored",
+                    help="hex FP64: geometric factors stored at setup, or recomputed at every point from the vertices")
     ap.add_argument("--order", choices=["lex", "shuffled", "rcm"], default="lex",
                     help="cell and node numbering: generator (lexicographic), seeded random permutation, or the "
                          "random permutation renumbered by the library's reverse Cuthill-McKee")
@@ -81,7 +83,8 @@ FORM_IDS = {"mass": 0, "laplace": 1, "helmholtz": 2, "elasticity": 3, "hyper_res
 
 
 def workload_name(args):
-    return _workload_name(args) + ("" if args.order == "lex" else "-order-" + args.order)
+    return (_workload_name(args) + ("" if args.order == "lex" else "-order-" + args.order) +
+            ("-geometry-onthefly" if args.geometry == "onthefly" else ""))
 
 
 def renumber(args, cell_vert, cell_node, nnode, nvert, vectors):
@@ -394,8 +397,9 @@ def gpu_arm(args, world, rank, local):
         prec = {"fp64": mfa.MFA_PREC_FP64, "fp32": mfa.MFA_PREC_FP32, "bf16": mfa.MFA_PREC_BF16}[args.precision]
         if c["cell_type"] != 8:
             prec = mfa.MFA_PREC_FP64
+        geo = mfa.MFA_GEOM_ONTHEFLY if (args.geometry == "onthefly" and c["cell_type"] == 8) else mfa.MFA_GEOM_STORED
         form = mfa.Form(spaces[sk], FORM_IDS[c["form"]], scatter=scatter, qdeg=c["qdeg"] if c["cell_type"] == 8 else 0,
-                        precision=prec, **c["kw"])
+                        precision=prec, geometry=geo, **c["kw"])
         x = torch.from_numpy(c["x"]).to("cuda")
         y = torch.empty_like(x)
         if c.get("coef") is not None:

@@ -83,6 +83,13 @@ enum { MFA_LAW_SVK = 0, MFA_LAW_NEOHOOKE = 1 };
  * arithmetic and accumulation.  x and y stay FP64 in memory for all three.
  * FP32/BF16 cover hexahedral forms with p+1 points per direction. */
 enum { MFA_PREC_FP64 = 0, MFA_PREC_FP32 = 1, MFA_PREC_BF16 = 2 };
+/* Geometry of hexahedral forms.  STORED: w |det J| J^{-1} J^{-T} (and c0 w |det J|)
+ * computed once per Gauss point at form creation and streamed by every apply.
+ * ONTHEFLY: recomputed at every Gauss point of every apply from the cell's 8
+ * vertices, as Section 4.1 describes for bilinear/trilinear cells (~270 more
+ * FP64 operations per point, no stored factors; FP64 scalar hex forms with
+ * p+1 points, atomic or colour scatter). */
+enum { MFA_GEOM_STORED = 0, MFA_GEOM_ONTHEFLY = 1 };
 /* Scatter-add of the local results into y (Section 2.2's INC access):
  * COLOUR  cells of one colour share no node: plain read-modify-write, one launch
  *         per colour, bitwise reproducible;
@@ -103,6 +110,8 @@ typedef struct {
   double k2;               /* Helmholtz coefficient (paper: 1)                          */
   double lambda, mu;       /* Lame parameters (elasticity, hyperelasticity)             */
   double b[3];             /* body force of the hyperelastic residual                   */
+  int32_t geometry;        /* MFA_GEOM_STORED (0, default) or MFA_GEOM_ONTHEFLY          */
+  int32_t reserved;        /* 0                                                          */
 } mfa_form_params;
 
 typedef struct {
@@ -219,6 +228,8 @@ MFA_API int mfa_form_set_dirichlet(mfa_form *form, const int32_t *dofs, int64_t 
  *  - cells_per_block: cells one thread block processes together (tets:
  *    threads per block); 0 in mfa_form_set_config = the variant's default.
  *  - scatter: MFA_SCATTER_ATOMIC, or (FP64 only) MFA_SCATTER_COLOUR or MFA_SCATTER_WARP.
+ *  - geometry: stored factors or on-the-fly (the FP64 scalar point kernel; a
+ *    form created with on-the-fly geometry has no stored factors to switch to).
  *  - ms: mean time of one apply measured by mfa_form_autotune (else 0). */
 enum {
   MFA_VARIANT_AUTO = 0,
@@ -233,7 +244,7 @@ typedef struct {
   int32_t variant;
   int32_t cells_per_block;
   int32_t scatter;
-  int32_t reserved;        /* 0 */
+  int32_t geometry;        /* MFA_GEOM_STORED or MFA_GEOM_ONTHEFLY (hex) */
   double ms;
 } mfa_launch_config;
 

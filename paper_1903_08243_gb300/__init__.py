@@ -22,6 +22,7 @@ MFA_FORM_MASS, MFA_FORM_LAPLACE, MFA_FORM_HELMHOLTZ = 0, 1, 2
 MFA_FORM_ELASTICITY, MFA_FORM_HYPER_RES, MFA_FORM_HYPER_JAC = 3, 4, 5
 MFA_LAW_SVK, MFA_LAW_NEOHOOKE = 0, 1
 MFA_PREC_FP64, MFA_PREC_FP32, MFA_PREC_BF16 = 0, 1, 2
+MFA_GEOM_STORED, MFA_GEOM_ONTHEFLY = 0, 1
 MFA_SCATTER_AUTO, MFA_SCATTER_COLOUR, MFA_SCATTER_ATOMIC, MFA_SCATTER_WARP = 0, 1, 2, 3
 MFA_PC_NONE, MFA_PC_JACOBI = 0, 1
 MFA_PRECOND_MLP, MFA_PRECOND_LINEAR = 0, 1
@@ -48,6 +49,8 @@ class mfa_form_params(ctypes.Structure):
         ("lam", ctypes.c_double),
         ("mu", ctypes.c_double),
         ("b", ctypes.c_double * 3),
+        ("geometry", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -71,14 +74,14 @@ class mfa_launch_config(ctypes.Structure):
         ("variant", ctypes.c_int32),
         ("cells_per_block", ctypes.c_int32),
         ("scatter", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("geometry", ctypes.c_int32),
         ("ms", ctypes.c_double),
     ]
 
     def as_dict(self):
         return {"variant": VARIANT_NAMES.get(self.variant, self.variant), "cells_per_block": self.cells_per_block,
                 "scatter": {MFA_SCATTER_COLOUR: "colour", MFA_SCATTER_WARP: "warp"}.get(self.scatter, "atomic"),
-                "ms": self.ms}
+                "geometry": "on-the-fly" if self.geometry == MFA_GEOM_ONTHEFLY else "stored", "ms": self.ms}
 
 
 _lib = None
@@ -557,10 +560,10 @@ class Space:
 
 
 def form_params(kind, law=MFA_LAW_SVK, qdeg=0, precision=MFA_PREC_FP64, scatter=MFA_SCATTER_AUTO, k2=1.0,
-                lam=1.0, mu=1.0, b=(0.0, 0.0, 0.0), cells_per_block=0):
+                lam=1.0, mu=1.0, b=(0.0, 0.0, 0.0), cells_per_block=0, geometry=MFA_GEOM_STORED):
     p = mfa_form_params()
     p.kind, p.law, p.qdeg, p.precision, p.scatter = kind, law, qdeg, precision, scatter
-    p.cells_per_block = cells_per_block
+    p.cells_per_block, p.geometry = cells_per_block, geometry
     p.k2, p.lam, p.mu = k2, lam, mu
     p.b[0], p.b[1], p.b[2] = b
     return p

@@ -108,6 +108,12 @@ void count_work(mfa_form* f) {
     if (kind != MFA_FORM_LAPLACE) per_cell += q * q * q;                            // c0 w|J| u
     const double esz = f->p.precision == MFA_PREC_FP64 ? 8.0 : (f->p.precision == MFA_PREC_FP32 ? 4.0 : 2.0);
     bytes = ncell * (4.0 * n * n * n + esz * mfa::hex_geom_entries(kind) * q * q * q);
+    if (f->launch.otf) {
+      // trilinear Jacobian from 8 vertices (~200), adjugate, determinant and G (~70) at every point; the vertex
+      // coordinates and map replace the stored factors
+      per_cell += 270.0 * q * q * q;
+      bytes = ncell * (4.0 * n * n * n + 32.0) + 24.0 * sp->mesh->nvert;
+    }
   } else if (sp->degree == 2 && sp->ncomp == 3 && f->nq == 27 &&
              (kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC)) {
     // moment kernel: per field 10x3x12 FMA moments + 36 mapped entries (900), per point the
@@ -336,6 +342,9 @@ static int apply_form_raw(mfa_form* f, const double* x, double* y, cudaStream_t 
                  : mfa::hex_vector_launch_b(n, f->nq1, f->p.kind, f->p.law, colour, f->hex, a, ctx->sm_count, stream);
     } else if (sp->mesh->cell_type == MFA_CELL_HEX8) {
       mfa::HexApplyArgs a{x, y, sp->d_cell_node, f->d_geom, list, count, ctx->d_err, f->gstride};
+      a.coords = sp->mesh->d_coords;
+      a.cell_vert = sp->mesh->d_cell_vert;
+      a.c0 = f->p.kind == MFA_FORM_HELMHOLTZ ? f->p.k2 : 1.0;
       mfa::LaunchConfig lc = f->launch;
       lc.agg = f->scatter == MFA_SCATTER_WARP;
       e = mfa::hex_apply_launch(sp->degree + 1, f->nq1, f->p.kind, f->p.precision, colour, lc, f->hex, a,
@@ -586,20 +595,30 @@ static std::vector<mfa_launch_config> form_configs(const mfa_form* f) {
   else variants = {MFA_VARIANT_LINE, MFA_VARIANT_LINE_STAGED};
   const bool colour_ok = f->p.precision == MFA_PREC_FP64;
   const int n = f->space->degree + 1;
+  const bool stored = !hex || f->d_geom != nullptr;  // the on-the-fly forms have no stored factors
+  // on-the-fly geometry: the FP64 scalar point kernel with p+1 points, default cells per block
+  const bool otf_ok = hex && f->p.precision == MFA_PREC_FP64 && f->space->ncomp == 1 && f->nq1 == n &&
+                      f->p.kind <= MFA_FORM_HELMHOLTZ;
   for (int v : variants) {
     int opts[4];
     const int nopt = cb_options(f, v, opts);
     for (int i = 0; i < nopt; ++i) {
-      // warp-aggregated scatter: tets, and the scalar point kernel with p+1 points at its default cells per block
-      const bool warp_ok = colour_ok && (v == MFA_VARIANT_CELL || (v == MFA_VARIANT_POINT && f->space->ncomp == 1 &&
-                                                                   f->nq1 == n && i == 0));
-      const int scatters[3] = {MFA_SCATTER_ATOMIC, MFA_SCATTER_COLOUR, MFA_SCATTER_WARP};
-      for (int sc = 0; sc < (colour_ok ? (warp_ok ? 3 : 2) : 1); ++sc) {
-        mfa_launch_config c{};
-        c.variant = v;
-        c.cells_per_block = opts[i];
-        c.scatter = scatters[sc];
-        all.push_back(c);
+      for (int geo = 0; geo < 2; ++geo) {
+        if (geo == 0 && !stored) continue;
+        if (geo == 1 && !(otf_ok && v == MFA_VARIANT_POINT && i == 0)) continue;
+        // warp-aggregated scatter: tets, and the scalar point kernel with p+1 points at its default cells per block
+        const bool warp_ok = colour_ok && geo == 0 &&
+                             (v == MFA_VARIANT_CELL || (v == MFA_VARIANT_POINT && f->space->ncomp == 1 && f->nq1 == n &&
+                                                        i == 0));
+        const int scatters[3] = {MFA_SCATTER_ATOMIC, MFA_SCATTER_COLOUR, MFA_SCATTER_WARP};
+        for (int sc = 0; sc < (colour_ok ? (warp_ok ? 3 : 2) : 1); ++sc) {
+          mfa_launch_config c{};
+          c.variant = v;
+          c.cells_per_block = opts[i];
+          c.scatter = scatters[sc];
+          c.geometry = geo ? MFA_GEOM_ONTHEFLY : MFA_GEOM_STORED;
+          all.push_back(c);
+        }
       }
     }
   }
@@ -607,8 +626,10 @@ static std::vector<mfa_launch_config> form_configs(const mfa_form* f) {
   int dopts[4];
   const int dn = cb_options(f, f->launch.variant, dopts);
   const int dcb = f->launch.cb ? f->launch.cb : (dn > 0 ? dopts[0] : 0);
+  const int dgeo = f->launch.otf ? MFA_GEOM_ONTHEFLY : MFA_GEOM_STORED;
   for (size_t i = 0; i < all.size(); ++i)
-    if (all[i].variant == f->launch.variant && all[i].cells_per_block == dcb && all[i].scatter == f->scatter) {
+    if (all[i].variant == f->launch.variant && all[i].cells_per_block == dcb && all[i].scatter == f->scatter &&
+        all[i].geometry == dgeo) {
       std::rotate(all.begin(), all.begin() + i, all.begin() + i + 1);
       break;
     }
@@ -626,6 +647,15 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
   if (prm->law != MFA_LAW_SVK && prm->law != MFA_LAW_NEOHOOKE) return fail(MFA_ERR_ARG, "mfa_form_create: law %d", prm->law);
   if (prm->precision < MFA_PREC_FP64 || prm->precision > MFA_PREC_BF16)
     return fail(MFA_ERR_ARG, "mfa_form_create: precision %d", prm->precision);
+  if (prm->geometry != MFA_GEOM_STORED && prm->geometry != MFA_GEOM_ONTHEFLY)
+    return fail(MFA_ERR_ARG, "mfa_form_create: geometry %d", prm->geometry);
+  if (prm->geometry == MFA_GEOM_ONTHEFLY &&
+      (ct != MFA_CELL_HEX8 || sp->ncomp != 1 || kind > MFA_FORM_HELMHOLTZ || prm->precision != MFA_PREC_FP64 ||
+       (prm->qdeg > 0 && prm->qdeg != sp->degree + 1) || prm->scatter == MFA_SCATTER_WARP ||
+       prm->cells_per_block != 0))
+    return fail(MFA_ERR_UNSUPPORTED,
+                "mfa_form_create: on-the-fly geometry covers FP64 scalar hex forms with p+1 points (atomic or colour "
+                "scatter, default cells per block)");
   if (prm->precision != MFA_PREC_FP64 && (ct != MFA_CELL_HEX8 || (prm->qdeg > 0 && prm->qdeg != sp->degree + 1) ||
                                           prm->scatter == MFA_SCATTER_COLOUR || prm->scatter == MFA_SCATTER_WARP))
     return fail(MFA_ERR_UNSUPPORTED,
@@ -684,7 +714,11 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
       rc = fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: Q%d with %d Gauss points per direction", sp->degree, f->nq1);
     if (!rc) rc = hex_tables(f);
     f->nq = f->nq1 * f->nq1 * f->nq1;
-    if (!rc) {
+    if (!rc && prm->geometry == MFA_GEOM_ONTHEFLY) {
+      // the trilinear map is recomputed at every point from the vertices: nothing to store
+      f->launch.otf = true;
+      f->launch.variant = MFA_VARIANT_POINT;
+    } else if (!rc) {
       const int ng = mfa::hex_geom_entries(kind);
       const size_t esz = prm->precision == MFA_PREC_FP64 ? 8 : (prm->precision == MFA_PREC_FP32 ? 4 : 2);
       // FP32/BF16 blocks are padded to 16 bytes per cell: the kernel moves them with bulk copies
@@ -789,6 +823,7 @@ int mfa_form_get_config(const mfa_form* f, mfa_launch_config* cfg) {
   cfg->variant = f->launch.variant;
   cfg->cells_per_block = f->launch.cb ? f->launch.cb : (nopt > 0 ? opts[0] : 0);
   cfg->scatter = f->scatter;
+  cfg->geometry = f->launch.otf ? MFA_GEOM_ONTHEFLY : MFA_GEOM_STORED;
   cfg->ms = f->tuned_ms;
   return MFA_OK;
 }
@@ -797,23 +832,29 @@ int mfa_form_set_config(mfa_form* f, const mfa_launch_config* cfg) {
   if (!f || !cfg) return fail(MFA_ERR_ARG, "mfa_form_set_config: NULL argument");
   mfa_launch_config want = *cfg;
   const mfa_space* sp = f->space;
-  if (want.variant == MFA_VARIANT_AUTO) want.variant = default_variant(sp, f->nq1, f->p.precision);
+  if (want.variant == MFA_VARIANT_AUTO) {
+    want.variant = default_variant(sp, f->nq1, f->p.precision);
+    if (sp->mesh->cell_type == MFA_CELL_HEX8 && !f->d_geom) want.variant = MFA_VARIANT_POINT;
+  }
   if (want.cells_per_block == 0) {
     int opts[4];
     if (cb_options(f, want.variant, opts) > 0) want.cells_per_block = opts[0];
   }
   bool found = false;
   for (const mfa_launch_config& c : form_configs(f))
-    found = found || (c.variant == want.variant && c.cells_per_block == want.cells_per_block && c.scatter == want.scatter);
+    found = found || (c.variant == want.variant && c.cells_per_block == want.cells_per_block &&
+                      c.scatter == want.scatter && c.geometry == want.geometry);
   if (!found)
-    return fail(MFA_ERR_UNSUPPORTED, "mfa_form_set_config: variant %d, %d cells per block, scatter %d not compiled",
-                want.variant, want.cells_per_block, want.scatter);
+    return fail(MFA_ERR_UNSUPPORTED,
+                "mfa_form_set_config: variant %d, %d cells per block, scatter %d, geometry %d not available",
+                want.variant, want.cells_per_block, want.scatter, want.geometry);
   if (want.scatter == MFA_SCATTER_COLOUR) {
     int rc = build_colouring(f->space);
     if (rc) return rc;
   }
   f->launch.variant = want.variant;
   f->launch.cb = want.cells_per_block;
+  f->launch.otf = want.geometry == MFA_GEOM_ONTHEFLY;
   f->scatter = want.scatter;
   f->tuned_ms = 0.0;
   count_work(f);
@@ -986,6 +1027,7 @@ int mfa_diagonal(mfa_ctx* ctx, mfa_form* f, double* d) {
   if (sp->mesh->cell_type == MFA_CELL_HEX8) {
     if (f->p.precision != MFA_PREC_FP64) return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: FP64 forms only");
     if (sp->ncomp != 1) return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: scalar hex forms only");
+    if (!f->d_geom) return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: needs stored geometric factors");
     e = mfa::hex_diagonal_launch(sp->degree + 1, f->nq1, f->p.kind, f->hex, sp->d_cell_node,
                                  static_cast<const double*>(f->d_geom),
                                  sp->mesh->ncell, d, ctx->sm_count, ctx->stream);

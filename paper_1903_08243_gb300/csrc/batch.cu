@@ -68,6 +68,7 @@ int build(mfa_ctx* ctx, int n, mfa_form* const* forms, const double* const* xs, 
     b->xs.push_back(xs[k]);
     b->ys.push_back(ys[k]);
     const bool groupable = f->space->mesh->cell_type == MFA_CELL_HEX8 && f->space->ncomp == 1 && !f->d_dir_mask &&
+                           f->d_geom != nullptr &&
                            f->scatter == MFA_SCATTER_ATOMIC && f->nq1 == f->space->degree + 1;
     if (groupable) classes[{f->space->degree + 1, f->p.kind, f->p.precision}].push_back(k);
     else b->singles.push_back(k);

@@ -149,11 +149,15 @@ cudaError_t hex_apply_launch(int n, int nq, int kind, int prec, bool colour, con
   if (prec != MFA_PREC_FP64) return hex_apply_launch_mixed(n, nq, kind, prec, colour, lc, tb, a, sm_count, s);
   const int variant = lc.variant == MFA_VARIANT_AUTO ? hex_default_variant(n, nq, prec) : lc.variant;
   if (variant == MFA_VARIANT_EVEN_ODD) {
-    if (nq != n || n < 5 || n > 9 || lc.agg) return cudaErrorInvalidValue;
+    if (nq != n || n < 5 || n > 9 || lc.agg || lc.otf) return cudaErrorInvalidValue;
     if (lc.cb == 0 || lc.cb == hex_eo_cells_per_block(n)) return hex_eo_apply_launch(n, kind, colour, a, sm_count, s);
     return hex_eo_apply_launch_cb(n, kind, colour, lc.cb, a, sm_count, s);
   }
   if (variant != MFA_VARIANT_POINT) return cudaErrorInvalidValue;
+  if (lc.otf) {
+    if (lc.agg || (lc.cb != 0 && lc.cb != hex_cells_per_block(n, nq))) return cudaErrorInvalidValue;
+    return hex_point_launch_otf(n, nq, kind, colour, tb, a, sm_count, s);
+  }
   if (lc.agg) {
     if (colour || (lc.cb != 0 && lc.cb != hex_cells_per_block(n, nq))) return cudaErrorInvalidValue;
     return hex_point_launch_agg(n, nq, kind, tb, a, sm_count, s);

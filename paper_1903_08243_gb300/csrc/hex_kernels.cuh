@@ -117,9 +117,63 @@ struct Smem {
 
 // One batch of CB cells of one form: gather, sum-factorised local kernel,
 // scatter.  Every thread of the block calls it (it contains barriers).
-template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0, bool AGG = false>
+// Geometric factors of Gauss point (qi, qj, qk) from the cell's vertices X[8][3] (shared memory): the
+// trilinear Jacobian J, then G = w |det J| J^{-1} J^{-T} = (w / |det J|) adj(J)^T adj(J) (6 entries) and
+// c0 w |det J|, in the stored layout's entry order.  Returns false if det J is zero or not finite.
+template <int NG>
+__device__ __forceinline__ bool point_geometry(const double* X, const HexTables& tb, int qi, int qj, int qk,
+                                               double c0, double g[NG]) {
+  const double xi[3] = {tb.x1[qi], tb.x1[qj], tb.x1[qk]};
+  const double w = tb.w1[qi] * tb.w1[qj] * tb.w1[qk];
+  double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    const double fx = (v & 1) ? xi[0] : 1.0 - xi[0], fy = (v & 2) ? xi[1] : 1.0 - xi[1],
+                 fz = (v & 4) ? xi[2] : 1.0 - xi[2];
+    const double dN[3] = {((v & 1) ? fy : -fy) * fz, fx * ((v & 2) ? fz : -fz), fx * ((v & 4) ? fy : -fy)};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double Xd = X[3 * v + d];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) J[d][e] = fma(Xd, dN[e], J[d][e]);
+    }
+  }
+  // cofactors: cof[r][c] of J; adj(J) = cof^T, J^{-1} = cof^T / det
+  double cof[3][3];
+  cof[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  cof[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  cof[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  cof[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  cof[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  cof[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  cof[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  cof[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  cof[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  const double det = J[0][0] * cof[0][0] + J[0][1] * cof[0][1] + J[0][2] * cof[0][2];
+  if (!(det != 0.0) || !isfinite(det)) {
+#pragma unroll
+    for (int e = 0; e < NG; ++e) g[e] = 0.0;
+    return false;
+  }
+  const double adet = fabs(det);
+  if constexpr (NG == 1) {
+    g[0] = c0 * w * adet;
+  } else {
+    const double s = w / adet;
+    // G[a][b] = s * sum_k cof[k][a] cof[k][b]: (00, 11, 22, 01, 02, 12)
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int e = 0; e < 6; ++e)
+      g[e] = s * (cof[0][ia[e]] * cof[0][ib[e]] + cof[1][ia[e]] * cof[1][ib[e]] + cof[2][ia[e]] * cof[2][ib[e]]);
+    if constexpr (NG == 7) g[6] = c0 * w * adet;
+  }
+  return true;
+}
+
+template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0, bool AGG = false, bool OTF = false>
 __device__ __forceinline__ void hex_cell_batch(const HexApplyArgs& a, int64_t batch,
-                                               const Smem<N, NQ, PREC, CBX>& sm) {
+                                               const Smem<N, NQ, PREC, CBX>& sm, const HexTables& tb,
+                                               double* sX) {
   using S = Shape<N, NQ, 8, CBX>;
   using T = typename Prec<PREC>::T;
   using TG = typename Prec<PREC>::TG;
@@ -146,13 +200,26 @@ __device__ __forceinline__ void hex_cell_batch(const HexApplyArgs& a, int64_t ba
       node = __ldg(a.cell_node + cell * PN + pt);
       A[pt] = Prec<PREC>::in(__ldg(a.x + node));
     }
-    // stored geometric factors of this point (consumed after three sweeps)
+    // geometric factors of this point (consumed after three sweeps): stored, or from the vertices
     T g[NG];
-    if (valid && pt < PQ) {
+    if constexpr (OTF) {
+      if (valid && pt < PN)  // 24 coordinates per cell (a Q1 cell has only 8 threads)
+        for (int i = pt; i < 24; i += PN)
+          sX[cl * 24 + i] = __ldg(a.coords + 3 * (int64_t)__ldg(a.cell_vert + 8 * cell + i / 3) + i % 3);
+      __syncthreads();
+      if (valid && pt < PQ) {
+        double gd[NG];
+        if (!point_geometry<NG>(sX + cl * 24, tb, pt % NQ, (pt / NQ) % NQ, pt / (NQ * NQ), a.c0, gd)) atomicOr(a.err, 1);
 #pragma unroll
-      for (int e = 0; e < NG; ++e) g[e] = Prec<PREC>::geo(geom + (cell * NG + e) * PQ + pt);
+        for (int e = 0; e < NG; ++e) g[e] = gd[e];
+      }
+    } else {
+      if (valid && pt < PQ) {
+#pragma unroll
+        for (int e = 0; e < NG; ++e) g[e] = Prec<PREC>::geo(geom + (cell * NG + e) * PQ + pt);
+      }
+      __syncthreads();
     }
-    __syncthreads();
 
     // B in x: (NQ, N, N) <- (N, N, N)
     if (valid && pt < NQ * N * N) {
@@ -252,16 +319,17 @@ __device__ __forceinline__ void hex_cell_batch(const HexApplyArgs& a, int64_t ba
   }
 }
 
-template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0, bool AGG = false>
+template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0, bool AGG = false, bool OTF = false>
 __global__ void __launch_bounds__(Shape<N, NQ, 8, CBX>::T) hex_apply_kernel(const __grid_constant__ HexTables tb,
                                                                            const HexApplyArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int CB = Shape<N, NQ, 8, CBX>::CB;
+  __shared__ double sX[OTF ? CB * 24 : 1];  // the batch's vertex coordinates (on-the-fly geometry)
   Smem<N, NQ, PREC, CBX> sm;
   sm.init(smem_raw, tb);
-  constexpr int CB = Shape<N, NQ, 8, CBX>::CB;
   const int64_t nbatch = (a.count + CB - 1) / CB;
   for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x)
-    hex_cell_batch<N, NQ, KIND, COLOUR, PREC, CBX, AGG>(a, batch, sm);
+    hex_cell_batch<N, NQ, KIND, COLOUR, PREC, CBX, AGG, OTF>(a, batch, sm, tb, sX);
 }
 
 // Many forms of one (n, nq, kind, precision) class in one persistent launch:
@@ -280,14 +348,14 @@ __global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_group_kernel(const 
   for (int64_t gb = blockIdx.x; gb < total; gb += gridDim.x) {
     while (k + 1 < nitems && gb >= first[k + 1]) ++k;  // batches only increase within a block
     const HexApplyArgs a = items[k];
-    hex_cell_batch<N, NQ, KIND, false, PREC>(a, gb - first[k], sm);
+    hex_cell_batch<N, NQ, KIND, false, PREC>(a, gb - first[k], sm, tb, nullptr);
   }
 }
 
-template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0, bool AGG = false>
+template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0, bool AGG = false, bool OTF = false>
 cudaError_t launch_apply(const HexTables& tb, const HexApplyArgs& a, int sm_count, cudaStream_t s) {
   using S = Shape<N, NQ, (int)sizeof(typename Prec<PREC>::T), CBX>;
-  auto kern = hex_apply_kernel<N, NQ, KIND, COLOUR, PREC, CBX, AGG>;
+  auto kern = hex_apply_kernel<N, NQ, KIND, COLOUR, PREC, CBX, AGG, OTF>;
   static int blocks_per_sm = -1;
   if (blocks_per_sm < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);

@@ -56,6 +56,10 @@ struct HexApplyArgs {
   int64_t count;             // number of cells to process
   int* err;
   int64_t geom_stride;       // elements per cell of geom (ng * nq^3, padded to 16 bytes for FP32/BF16)
+  // on-the-fly geometry (FP64 point kernel): the trilinear map from the vertices, c0 = k2 (Helmholtz) or 1
+  const double* coords = nullptr;
+  const int32_t* cell_vert = nullptr;
+  double c0 = 1.0;
 };
 
 // Vector forms on hexes (ncomp = 3, dof = 3 node + c), FP64, p+1 points per direction.
@@ -109,6 +113,7 @@ struct LaunchConfig {
   int variant = MFA_VARIANT_AUTO;
   int cb = 0;
   bool agg = false;  // warp-aggregated atomic scatter (MFA_SCATTER_WARP)
+  bool otf = false;  // geometry recomputed at every point from the vertices (MFA_GEOM_ONTHEFLY)
 };
 // Cells per block of a kernel with `per_cell` threads per cell for a target block size.
 constexpr int cells_for_target(int per_cell, int target) { return target / per_cell > 0 ? target / per_cell : 1; }
@@ -124,6 +129,8 @@ cudaError_t hex_eo_apply_launch_cb(int n, int kind, bool colour, int cb, const H
                                    cudaStream_t s);
 cudaError_t hex_point_launch_agg(int n, int nq, int kind, const HexTables& tb, const HexApplyArgs& a, int sm_count,
                                  cudaStream_t s);
+cudaError_t hex_point_launch_otf(int n, int nq, int kind, bool colour, const HexTables& tb, const HexApplyArgs& a,
+                                 int sm_count, cudaStream_t s);
 // FP32/BF16 action with float vectors.
 cudaError_t hex_apply_launch_f32(int n, int kind, int prec, const float* x, float* y, const int32_t* cell_node,
                                  const void* geom, int64_t count, int64_t gstride, int* err, int sm_count,

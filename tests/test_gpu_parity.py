@@ -502,3 +502,44 @@ def test_space_with_library_built_map(ctx, cell, p, kind):
     y = f.apply(torch.from_numpy(x).cuda())
     ctx.sync()
     compare(y.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 6, 8])
+@pytest.mark.parametrize("kind", ["mass", "laplace", "helmholtz"])
+@pytest.mark.parametrize("scatter", ["atomic", "colour"])
+def test_hex_on_the_fly_geometry(ctx, p, kind, scatter):
+    """Geometry recomputed at every point from the vertices (no stored factors): same operator."""
+    nx = {1: 7, 2: 5, 3: 5, 4: 3, 6: 3, 8: 2}[p]
+    case = hex_case(nx, p)
+    x = fi.uniform_vector(case["nnode"], seed=31)
+    ref = oracle_problem(case, kind, k2=0.6).apply(x)
+    form = gpu_form(ctx, case, kind, k2=0.6, scatter=SCATTER[scatter], geometry=mfa.MFA_GEOM_ONTHEFLY)
+    cfg = form.config()
+    assert cfg.geometry == mfa.MFA_GEOM_ONTHEFLY and cfg.variant == mfa.MFA_VARIANT_POINT
+    assert all(c.geometry == mfa.MFA_GEOM_ONTHEFLY for c in form.configs())
+    compare(run(ctx, form, x), ref)
+
+
+def test_on_the_fly_geometry_limits(ctx):
+    case = hex_case(3, 2)
+    form = gpu_form(ctx, case, "helmholtz", geometry=mfa.MFA_GEOM_ONTHEFLY)
+    with pytest.raises(mfa.MfaError) as e:
+        form.diagonal()
+    assert e.value.code == mfa.MFA_ERR_UNSUPPORTED
+    stored = mfa.mfa_launch_config(variant=mfa.MFA_VARIANT_POINT, cells_per_block=0, scatter=mfa.MFA_SCATTER_ATOMIC,
+                                   geometry=mfa.MFA_GEOM_STORED)
+    with pytest.raises(mfa.MfaError) as e:
+        form.set_config(stored)  # no stored factors to switch to
+    assert e.value.code == mfa.MFA_ERR_UNSUPPORTED
+    for kw in [dict(precision=mfa.MFA_PREC_FP32), dict(qdeg=4), dict(scatter=mfa.MFA_SCATTER_WARP)]:
+        with pytest.raises(mfa.MfaError) as e:
+            gpu_form(ctx, case, "helmholtz", geometry=mfa.MFA_GEOM_ONTHEFLY, **kw)
+        assert e.value.code == mfa.MFA_ERR_UNSUPPORTED
+    # a stored form lists the on-the-fly configuration too, and it gives the same result
+    f2 = gpu_form(ctx, case, "helmholtz")
+    otf = [c for c in f2.configs() if c.geometry == mfa.MFA_GEOM_ONTHEFLY]
+    assert otf
+    x = fi.uniform_vector(case["nnode"], seed=32)
+    y_stored = run(ctx, f2, x)
+    f2.set_config(otf[0])
+    compare(run(ctx, f2, x), y_stored, tol=1e-13)
