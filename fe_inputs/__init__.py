@@ -10,6 +10,12 @@ from it without sharing any of the computation under test.
 """
 from .rng import splitmix64, uniform, randint
 from .mesh import (
+    PlaneMesh,
+    quad_mesh,
+    tri_mesh,
+    quad_node_map,
+    tri_lattice,
+    tri_node_map,
     pk_lattice,
     pk_node_map,
     TetMesh,

@@ -160,6 +160,112 @@ def p2_node_coords(coords, edges):
     return np.concatenate([coords, mid], axis=0)
 
 
+@dataclass
+class PlaneMesh:
+    """A 2D mesh of the unit square; coordinates carry a zero third component."""
+    coords: np.ndarray     # float64 [nvert][3], z = 0
+    cell_vert: np.ndarray  # int32 [ncell][3] (triangles) or [ncell][4] (quadrilaterals)
+    nx: int
+    h: float
+
+    @property
+    def ncell(self):
+        return self.cell_vert.shape[0]
+
+    @property
+    def nvert(self):
+        return self.coords.shape[0]
+
+
+def _grid_vertices_2d(nx, perturb, seed):
+    m = nx + 1
+    h = 1.0 / nx
+    j, i = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+    coords = np.stack([i.ravel() * h, j.ravel() * h, np.zeros(m * m)], axis=1).astype(np.float64)
+    if perturb > 0.0:
+        ii, jj = i.ravel(), j.ravel()
+        interior = (ii > 0) & (ii < nx) & (jj > 0) & (jj < nx)
+        shift = uniform(seed, 0x5E52, 2 * coords.shape[0], -perturb * h, perturb * h).reshape(-1, 2)
+        coords[interior, :2] += shift[interior]
+    return coords, h
+
+
+def quad_mesh(nx, perturb=0.1, seed=1):
+    """Unit square as nx^2 quadrilaterals (local vertex v at corner (v & 1, v >> 1 & 1)); interior vertices shifted
+    by U[-perturb*h, perturb*h]^2."""
+    coords, h = _grid_vertices_2d(nx, perturb, seed)
+    m = nx + 1
+    j, i = np.meshgrid(np.arange(nx), np.arange(nx), indexing="ij")
+    i, j = i.ravel(), j.ravel()
+    cv = np.stack([(i + di) + m * (j + dj) for dj in (0, 1) for di in (0, 1)], axis=1)
+    return PlaneMesh(coords=coords, cell_vert=cv.astype(np.int32), nx=nx, h=h)
+
+
+def tri_mesh(nx, perturb=0.0, seed=0):
+    """Unit square as nx^2 boxes split along the (0,0)-(1,1) diagonal into 2 triangles each, counter-clockwise;
+    interior vertices shifted by U[-perturb*h, perturb*h]^2."""
+    coords, h = _grid_vertices_2d(nx, perturb, seed)
+    m = nx + 1
+    j, i = np.meshgrid(np.arange(nx), np.arange(nx), indexing="ij")
+    i, j = i.ravel(), j.ravel()
+    v00, v10, v01, v11 = i + m * j, i + 1 + m * j, i + m * (j + 1), i + 1 + m * (j + 1)
+    cells = np.stack([np.stack([v00, v10, v11], 1), np.stack([v00, v11, v01], 1)], axis=1).reshape(-1, 3)
+    return PlaneMesh(coords=coords, cell_vert=cells.astype(np.int32), nx=nx, h=h)
+
+
+def quad_node_map(nx, p):
+    """Cell -> node map of continuous Q_p on an nx^2 structured quad mesh.  Local node i + n*j of cell (ci, cj) is
+    global grid node (p*ci + i, p*cj + j) on the (nx*p + 1)^2 lattice."""
+    n = p + 1
+    m = nx * p + 1
+    j, i = np.meshgrid(np.arange(nx), np.arange(nx), indexing="ij")
+    i, j = i.ravel().astype(np.int64), j.ravel().astype(np.int64)
+    lj, li = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    li, lj = li.ravel(), lj.ravel()
+    node = (p * i[:, None] + li[None, :]) + m * (p * j[:, None] + lj[None, :])
+    return node.astype(np.int32), m * m
+
+
+def tri_lattice(k):
+    """Barycentric lattice of P_k on a triangle, in local node order: points (i, j)/k with i + j <= k, i fastest,
+    then j.  Returns int [nloc][3] weights (b0, b1, b2) = (k - i - j, i, j)."""
+    return np.array([(k - i - j, i, j) for j in range(k + 1) for i in range(k + 1 - j)], dtype=np.int64)
+
+
+def tri_node_map(cell_vert, nvert, k):
+    """Cell -> node map of continuous P_k on a triangle mesh, local nodes in `tri_lattice` order.  A lattice point is
+    the same node in every cell that contains it (keyed by the global vertices of its support and its weights on
+    them); nodes 0..nvert-1 are the vertices, the others follow in sorted key order.  Returns (cell_node, nnode,
+    node_coords_fn)."""
+    cv = cell_vert.astype(np.int64)
+    ncell = cv.shape[0]
+    lat = tri_lattice(k)
+    nloc = lat.shape[0]
+    gv = cv[:, None, :].repeat(nloc, axis=1)
+    w = np.broadcast_to(lat[None, :, :], gv.shape)
+    vkey = np.where(w > 0, gv, np.int64(-1))
+    order = np.argsort(np.where(vkey < 0, np.iinfo(np.int64).max, vkey), axis=2, kind="stable")
+    vs = np.take_along_axis(vkey, order, axis=2)
+    ws = np.take_along_axis(w, order, axis=2)
+    keys = np.concatenate([vs, ws], axis=2).reshape(-1, 6)
+    uniq, inv = np.unique(keys, axis=0, return_inverse=True)
+    inv = inv.reshape(-1)
+    is_vertex = uniq[:, 3] == k
+    node_of_key = np.empty(uniq.shape[0], dtype=np.int64)
+    node_of_key[is_vertex] = uniq[is_vertex, 0]
+    nonv = np.flatnonzero(~is_vertex)
+    node_of_key[nonv] = nvert + np.arange(nonv.size)
+    cell_node = node_of_key[inv].reshape(ncell, nloc).astype(np.int32)
+    nnode = nvert + nonv.size
+
+    def node_coords(coords):
+        out = np.zeros((nnode, 3))
+        out[node_of_key[inv].reshape(ncell, nloc)] = np.einsum("ls,csd->cld", lat / k, coords[cv])
+        return out
+
+    return cell_node, nnode, node_coords
+
+
 def pk_lattice(k):
     """Barycentric lattice of P_k on a tet, in local node order: points (i, j, l)/k with i + j + l <= k, i fastest,
     then j, then l.  Returns int [nloc][4] weights (b0, b1, b2, b3), b_s = k * (barycentric coordinate of vertex s),

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
 
-TET, HEX = 4, 8
+TET, HEX, TRI, QUAD = 4, 8, 3, 40
 MASS, LAPLACE, HELMHOLTZ, ELASTICITY, HYPER_RES, HYPER_JAC = range(6)
 SVK, NEOHOOKE = 0, 1
 
@@ -71,6 +71,9 @@ def lib():
         _lib.orc_tet_rule.argtypes = [i, d, d]
         _lib.orc_tet_basis.argtypes = [i, d, d, d]
         _lib.orc_hex_basis.argtypes = [i, i, d, d, d]
+        _lib.orc_tri_rule.argtypes = [i, d, d]
+        _lib.orc_tri_basis.argtypes = [i, d, d, d]
+        _lib.orc_quad_basis.argtypes = [i, d, d, d]
         _lib.orc_apply.argtypes = [ctypes.POINTER(_Problem), d, d, ctypes.POINTER(ctypes.c_int64), i64]
         _lib.orc_energy.argtypes = [ctypes.POINTER(_Problem), d, d]
         _lib.orc_element_matrix.argtypes = [ctypes.POINTER(_Problem), i64, d]
@@ -133,6 +136,27 @@ def hex_basis(p, xi, equispaced=False):
     return phi, dphi
 
 
+def tri_rule(degree):
+    m = (degree + 2) // 2
+    pts, w = np.zeros((m * m, 2)), np.zeros(m * m)
+    _check(lib().orc_tri_rule(degree, _dp(pts), _dp(w)), "tri_rule")
+    return pts, w
+
+
+def tri_basis(p, xi):
+    n = (p + 1) * (p + 2) // 2
+    phi, dphi = np.zeros(n), np.zeros((n, 2))
+    _check(lib().orc_tri_basis(p, _dp(np.ascontiguousarray(xi, dtype=np.float64)), _dp(phi), _dp(dphi)), "tri_basis")
+    return phi, dphi
+
+
+def quad_basis(p, xi):
+    n = (p + 1) ** 2
+    phi, dphi = np.zeros(n), np.zeros((n, 2))
+    _check(lib().orc_quad_basis(p, _dp(np.ascontiguousarray(xi, dtype=np.float64)), _dp(phi), _dp(dphi)), "quad_basis")
+    return phi, dphi
+
+
 class Problem:
     """A mesh, a space and a form, held as arrays the C oracle reads."""
 
@@ -144,7 +168,7 @@ class Problem:
         self.cell_node = np.ascontiguousarray(cell_node, dtype=np.int32)
         self.ucoef = None if ucoef is None else np.ascontiguousarray(ucoef, dtype=np.float64).ravel()
         if qdeg is None:
-            qdeg = degree + 1 if cell_type == HEX else 2 * degree
+            qdeg = degree + 1 if cell_type in (HEX, QUAD) else 2 * degree
         s = _Problem()
         s.cell_type, s.degree, s.ncomp, s.kind, s.law, s.qdeg = cell_type, degree, ncomp, kind, law, qdeg
         s.equispaced = int(equispaced)

@@ -160,6 +160,24 @@ int orc_tet_rule(int degree, double *pts, double *w) {
   return q;
 }
 
+int orc_tri_rule(int degree, double *pts, double *w) {
+  if (degree < 0 || degree > 30 || !pts || !w) return ORC_EARG;
+  int m = (degree + 2) / 2;
+  double xa[32], wa[32], xb[32], wb[32];
+  orc_gauss_jacobi(m, 0, xa, wa);
+  orc_gauss_jacobi(m, 1, xb, wb);
+  int q = 0;
+  /* (a,b) in [0,1]^2 -> x = a(1-b), y = b, the Jacobian (1-b) absorbed by the Jacobi weight */
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i < m; ++i) {
+      pts[2 * q + 0] = xa[i] * (1.0 - xb[j]);
+      pts[2 * q + 1] = xb[j];
+      w[q] = wa[i] * wb[j];
+      ++q;
+    }
+  return q;
+}
+
 /* ------------------------------------------------------------------ */
 /* Basis functions                                                      */
 /* ------------------------------------------------------------------ */
@@ -302,12 +320,88 @@ int orc_hex_basis(int p, int equispaced, const double xi[3], double *phi, double
   return n * n * n;
 }
 
+int orc_tri_basis(int p, const double xi[2], double *phi, double *dphi) {
+  if (p < 1 || p > ORC_TET_MAXP || !xi || !phi || !dphi) return ORC_EARG;
+  enum { MAXN = (ORC_TET_MAXP + 1) * (ORC_TET_MAXP + 2) / 2 };
+  int e[MAXN][2], n = 0;
+  for (int d = 0; d <= p; ++d)
+    for (int i = d; i >= 0; --i) {
+      e[n][0] = i;
+      e[n][1] = d - i;
+      ++n;
+    }
+  long double nodes[MAXN][2];
+  int k = 0;
+  for (int j = 0; j <= p; ++j)
+    for (int i = 0; i <= p - j; ++i) {
+      nodes[k][0] = (long double)i / p;
+      nodes[k][1] = (long double)j / p;
+      ++k;
+    }
+  long double M[MAXN][2 * MAXN];
+  for (int r = 0; r < n; ++r) {
+    for (int c = 0; c < n; ++c) M[r][c] = ipow(nodes[r][0], e[c][0]) * ipow(nodes[r][1], e[c][1]);
+    for (int c = 0; c < n; ++c) M[r][n + c] = (r == c) ? 1.0L : 0.0L;
+  }
+  for (int c = 0; c < n; ++c) { /* Gauss-Jordan with partial pivoting */
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabsl(M[r][c]) > fabsl(M[piv][c])) piv = r;
+    if (fabsl(M[piv][c]) < 1e-30L) return ORC_EARG;
+    if (piv != c)
+      for (int j = 0; j < 2 * n; ++j) { long double tt = M[c][j]; M[c][j] = M[piv][j]; M[piv][j] = tt; }
+    long double d = M[c][c];
+    for (int j = 0; j < 2 * n; ++j) M[c][j] /= d;
+    for (int r = 0; r < n; ++r)
+      if (r != c) {
+        long double f = M[r][c];
+        for (int j = 0; j < 2 * n; ++j) M[r][j] -= f * M[c][j];
+      }
+  }
+  long double x = xi[0], y = xi[1];
+  for (int a = 0; a < n; ++a) {
+    long double v = 0, gx = 0, gy = 0;
+    for (int j = 0; j < n; ++j) {
+      long double c = M[j][n + a];
+      int i0 = e[j][0], i1 = e[j][1];
+      v += c * ipow(x, i0) * ipow(y, i1);
+      if (i0) gx += c * i0 * ipow(x, i0 - 1) * ipow(y, i1);
+      if (i1) gy += c * i1 * ipow(x, i0) * ipow(y, i1 - 1);
+    }
+    phi[a] = (double)v;
+    dphi[2 * a + 0] = (double)gx;
+    dphi[2 * a + 1] = (double)gy;
+  }
+  return n;
+}
+
+int orc_quad_basis(int p, const double xi[2], double *phi, double *dphi) {
+  if (p < 1 || p > 16 || !xi || !phi || !dphi) return ORC_EARG;
+  int n = p + 1;
+  double s[17];
+  hex_nodes1d(p, 0, s);
+  long double v[2][17], d[2][17];
+  for (int dim = 0; dim < 2; ++dim)
+    for (int i = 0; i < n; ++i) lagrange1d(n, s, i, xi[dim], &v[dim][i], &d[dim][i]);
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) {
+      int a = i + n * j;
+      phi[a] = (double)(v[0][i] * v[1][j]);
+      dphi[2 * a + 0] = (double)(d[0][i] * v[1][j]);
+      dphi[2 * a + 1] = (double)(v[0][i] * d[1][j]);
+    }
+  return n * n;
+}
+
 /* ------------------------------------------------------------------ */
 /* Tabulation of one problem                                            */
 /* ------------------------------------------------------------------ */
 
+static int nv_of(int ct) { return ct == ORC_TRI ? 3 : (ct == ORC_TET || ct == ORC_QUAD) ? 4 : 8; }
+static int dim_of(int ct) { return (ct == ORC_TRI || ct == ORC_QUAD) ? 2 : 3; }
+
 typedef struct {
-  int nq, nloc, nv, nc;
+  int nq, nloc, nv, nc, dim;
   double *w;      /* [nq] */
   double *phi;    /* [nq][nloc] */
   double *dphi;   /* [nq][nloc][3] reference gradients */
@@ -320,6 +414,11 @@ static void free_tables(tables *t) {
 }
 
 static int nloc_of(const orc_problem *pb) {
+  if (pb->cell_type == ORC_TRI) {
+    const int p = pb->degree;
+    return p >= 1 && p <= ORC_TET_MAXP ? (p + 1) * (p + 2) / 2 : -1;
+  }
+  if (pb->cell_type == ORC_QUAD) return (pb->degree + 1) * (pb->degree + 1);
   if (pb->cell_type == ORC_TET) {
     const int p = pb->degree;
     return p >= 1 && p <= ORC_TET_MAXP ? (p + 1) * (p + 2) * (p + 3) / 6 : -1;
@@ -330,19 +429,21 @@ static int nloc_of(const orc_problem *pb) {
 
 static int check_problem(const orc_problem *pb) {
   if (!pb || !pb->coords || !pb->cell_vert || !pb->cell_node) return ORC_EARG;
-  if (pb->cell_type != ORC_TET && pb->cell_type != ORC_HEX) return ORC_EARG;
-  if (pb->cell_type == ORC_TET && (pb->degree < 1 || pb->degree > ORC_TET_MAXP)) return ORC_EARG;
-  if (pb->cell_type == ORC_HEX && (pb->degree < 1 || pb->degree > 16)) return ORC_EARG;
-  if (pb->ncomp != 1 && pb->ncomp != 3) return ORC_EARG;
+  const int ct = pb->cell_type;
+  if (ct != ORC_TET && ct != ORC_HEX && ct != ORC_TRI && ct != ORC_QUAD) return ORC_EARG;
+  if ((ct == ORC_TET || ct == ORC_TRI) && (pb->degree < 1 || pb->degree > ORC_TET_MAXP)) return ORC_EARG;
+  if ((ct == ORC_HEX || ct == ORC_QUAD) && (pb->degree < 1 || pb->degree > 16)) return ORC_EARG;
+  const int dim = dim_of(ct);
+  if (pb->ncomp != 1 && pb->ncomp != dim) return ORC_EARG;
   if (pb->kind < ORC_MASS || pb->kind > ORC_HYPER_JAC) return ORC_EARG;
-  if (pb->kind >= ORC_ELASTICITY && pb->ncomp != 3) return ORC_EARG;
+  if (pb->kind >= ORC_ELASTICITY && pb->ncomp != dim) return ORC_EARG;
   if (pb->kind == ORC_HYPER_JAC && !pb->ucoef) return ORC_EARG;
   if (pb->qdeg < 1) return ORC_EARG;
   if (pb->ncell < 0 || pb->nvert < 0 || pb->nnode < 0) return ORC_EARG;
   int nl = nloc_of(pb);
   for (int64_t c = 0; c < pb->ncell; ++c) {
-    for (int v = 0; v < pb->cell_type; ++v) {
-      int32_t id = pb->cell_vert[c * pb->cell_type + v];
+    for (int v = 0; v < nv_of(ct); ++v) {
+      int32_t id = pb->cell_vert[c * nv_of(ct) + v];
       if (id < 0 || id >= pb->nvert) return ORC_EARG;
     }
     for (int a = 0; a < nl; ++a) {
@@ -356,10 +457,37 @@ static int check_problem(const orc_problem *pb) {
 static int build_tables(const orc_problem *pb, tables *t) {
   memset(t, 0, sizeof(*t));
   t->nloc = nloc_of(pb);
-  t->nv = pb->cell_type;
+  t->nv = nv_of(pb->cell_type);
   t->nc = pb->ncomp;
+  t->dim = dim_of(pb->cell_type);
   double *pts;
-  if (pb->cell_type == ORC_TET) {
+  if (pb->cell_type == ORC_TRI || pb->cell_type == ORC_QUAD) {
+    /* points stored with a zero z coordinate */
+    int m = pb->cell_type == ORC_TRI ? (pb->qdeg + 2) / 2 : pb->qdeg;
+    if (m > 64) return ORC_EARG;
+    t->nq = m * m;
+    pts = calloc(3 * (size_t)t->nq, sizeof(double));
+    t->w = malloc(sizeof(double) * t->nq);
+    double *p2 = malloc(sizeof(double) * 2 * t->nq);
+    if (!pts || !t->w || !p2) { free(pts); free(p2); free_tables(t); return ORC_EMEM; }
+    if (pb->cell_type == ORC_TRI) {
+      orc_tri_rule(pb->qdeg, p2, t->w);
+    } else {
+      double x1[64], w1[64];
+      orc_gauss_legendre(m, x1, w1);
+      for (int j = 0; j < m; ++j)
+        for (int i = 0; i < m; ++i) {
+          p2[2 * (i + m * j)] = x1[i];
+          p2[2 * (i + m * j) + 1] = x1[j];
+          t->w[i + m * j] = w1[i] * w1[j];
+        }
+    }
+    for (int q = 0; q < t->nq; ++q) {
+      pts[3 * q] = p2[2 * q];
+      pts[3 * q + 1] = p2[2 * q + 1];
+    }
+    free(p2);
+  } else if (pb->cell_type == ORC_TET) {
     int m = (pb->qdeg + 2) / 2;
     t->nq = m * m * m;
     pts = malloc(sizeof(double) * 3 * t->nq);
@@ -392,6 +520,30 @@ static int build_tables(const orc_problem *pb, tables *t) {
   for (int q = 0; q < t->nq; ++q) {
     const double *xq = pts + 3 * q;
     double Nv[8], dNv[24];
+    if (t->dim == 2) {
+      /* 2D: basis and coordinate-map gradients with a zero z component */
+      double phi2[64 * 64], dphi2[2 * 64 * 64], N2[4], dN2[8];
+      if (pb->cell_type == ORC_TRI) {
+        orc_tri_basis(pb->degree, xq, phi2, dphi2);
+        orc_tri_basis(1, xq, N2, dN2);
+      } else {
+        orc_quad_basis(pb->degree, xq, phi2, dphi2);
+        orc_quad_basis(1, xq, N2, dN2);
+      }
+      for (int a = 0; a < t->nloc; ++a) {
+        t->phi[q * t->nloc + a] = phi2[a];
+        t->dphi[(q * t->nloc + a) * 3 + 0] = dphi2[2 * a];
+        t->dphi[(q * t->nloc + a) * 3 + 1] = dphi2[2 * a + 1];
+        t->dphi[(q * t->nloc + a) * 3 + 2] = 0.0;
+      }
+      for (int v = 0; v < t->nv; ++v) {
+        dNv[3 * v] = dN2[2 * v];
+        dNv[3 * v + 1] = dN2[2 * v + 1];
+        dNv[3 * v + 2] = 0.0;
+      }
+      memcpy(t->dN + q * t->nv * 3, dNv, sizeof(double) * t->nv * 3);
+      continue;
+    }
     if (pb->cell_type == ORC_TET) {
       orc_tet_basis(pb->degree, xq, t->phi + q * t->nloc, t->dphi + q * t->nloc * 3);
       orc_tet_basis(1, xq, Nv, dNv);
@@ -536,8 +688,9 @@ static int geometry(const tables *t, int q, const double *X, double *wdet, doubl
   double J[3][3] = {{0}};
   const double *dN = t->dN + q * t->nv * 3;
   for (int v = 0; v < t->nv; ++v)
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < t->dim; ++i)
       for (int j = 0; j < 3; ++j) J[i][j] += X[3 * v + i] * dN[3 * v + j];
+  if (t->dim == 2) J[2][2] = 1.0; /* the plane: no z dependence */
   double det = det3(J);
   if (!(det != 0.0) || !isfinite(det)) return ORC_EDET;
   inv3(J, det, Jinv);
@@ -569,8 +722,8 @@ static int cell_kernel(const orc_problem *pb, const tables *t, const double *X, 
       }
     if (pb->kind == ORC_HYPER_JAC)
       for (int a = 0; a < nl; ++a)
-        for (int c = 0; c < 3; ++c)
-          for (int j = 0; j < 3; ++j) gc[c][j] += ul[a * 3 + c] * grad[3 * a + j];
+        for (int c = 0; c < nc; ++c)
+          for (int j = 0; j < 3; ++j) gc[c][j] += ul[a * nc + c] * grad[3 * a + j];
     /* integrand: f0 multiplies the test value, f1 the test gradient */
     double f0[3] = {0}, f1[3][3] = {{0}};
     switch (pb->kind) {
@@ -702,10 +855,10 @@ done:
 int orc_energy(const orc_problem *pb, const double *u, double *energy) {
   int rc = check_problem(pb);
   if (rc) return rc;
-  if (!u || !energy || pb->ncomp != 3) return ORC_EARG;
+  if (!u || !energy || pb->ncomp != dim_of(pb->cell_type)) return ORC_EARG;
   tables t;
   if ((rc = build_tables(pb, &t))) return rc;
-  const int nl = t.nloc;
+  const int nl = t.nloc, nc = t.nc;
   double *xl = malloc(sizeof(double) * nl * 3), *grad = malloc(sizeof(double) * nl * 3);
   double total = 0.0;
   if (!xl || !grad) { rc = ORC_EMEM; goto done; }
@@ -722,9 +875,9 @@ int orc_energy(const orc_problem *pb, const double *u, double *energy) {
         double g[3];
         for (int j = 0; j < 3; ++j)
           g[j] = dphi[3 * a + 0] * Jinv[0][j] + dphi[3 * a + 1] * Jinv[1][j] + dphi[3 * a + 2] * Jinv[2][j];
-        for (int cc = 0; cc < 3; ++cc) {
-          uq[cc] += phi[a] * xl[3 * a + cc];
-          for (int j = 0; j < 3; ++j) F[cc][j] += xl[3 * a + cc] * g[j];
+        for (int cc = 0; cc < nc; ++cc) {
+          uq[cc] += phi[a] * xl[nc * a + cc];
+          for (int j = 0; j < 3; ++j) F[cc][j] += xl[nc * a + cc] * g[j];
         }
       }
       double psi;

@@ -22,7 +22,11 @@
 extern "C" {
 #endif
 
-enum { ORC_TET = 4, ORC_HEX = 8 };
+/* Cell types (ids, not vertex counts): tetrahedron (4 vertices), hexahedron (8),
+ * triangle (3) and quadrilateral (4) in the plane z = 0.  A 2D problem is the
+ * 3D one with no z dependence: J gets a unit (z, z) entry, reference gradients
+ * have no z component, vector fields have 2 components (plane strain). */
+enum { ORC_TRI = 3, ORC_TET = 4, ORC_HEX = 8, ORC_QUAD = 40 };
 enum {
   ORC_MASS = 0,
   ORC_LAPLACE = 1,
@@ -68,6 +72,15 @@ int orc_tet_rule(int degree, double *pts, double *w);
 int orc_tet_basis(int p, const double xi[3], double *phi, double *dphi);
 /* Lagrange Q_p on [0,1]^3; phi [n^3], dphi [n^3][3]. */
 int orc_hex_basis(int p, int equispaced, const double xi[3], double *phi, double *dphi);
+/* Collapsed rule on the reference triangle exact to `degree`: pts [nq][2],
+ * nq = m^2 with m = ceil((degree+1)/2). */
+int orc_tri_rule(int degree, double *pts, double *w);
+/* Lagrange P_p (p = 1..6) on the reference triangle by inverting the
+ * Vandermonde matrix of monomials at the lattice nodes (i, j)/p, i + j <= p, i
+ * fastest.  phi [ndof], dphi [ndof][2]. */
+int orc_tri_basis(int p, const double xi[2], double *phi, double *dphi);
+/* Lagrange Q_p on [0,1]^2 at GLL nodes, node i + n j; phi [n^2], dphi [n^2][2]. */
+int orc_quad_basis(int p, const double xi[2], double *phi, double *dphi);
 
 /* y = A(x) restricted to the listed cells (cells == NULL: all cells).
  * y is overwritten.  Returns 0, or a negative error (bad argument,
