@@ -42,8 +42,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mfa", "reference"], default="mfa")
-    ap.add_argument("--workload", choices=["hex", "hex-vector", "tet-pk", "tet-p1-mass", "tet-p2", "batched", "pcg",
-                                           "pcg-elasticity"],
+    ap.add_argument("--workload", choices=["hex", "hex-vector", "tet-pk", "planar", "tet-p1-mass", "tet-p2", "batched",
+                                           "pcg", "pcg-elasticity"],
                     default="hex",
                     help="hex: 64^3 Q1-Q6 Laplace+Helmholtz; tet-p1-mass: 8^3x6 P1 mass; "
                          "tet-p2: 48^3x6 vector P2 elasticity + neo-Hookean residual; "
@@ -122,13 +122,17 @@ def _workload_name(args):
         return "tet-kuhn%d^3x6-P1-mass-fp64" % args.nx
     if args.workload == "tet-pk":
         return "tet-kuhn%d^3x6-P%s-%s-fp64" % (args.nx, args.degrees.replace(",", ""), args.forms.replace(",", "+"))
+    if args.workload == "planar":
+        return "quad%d^2+tri%d^2x2-p%s-%s-fp64" % (args.nx, args.nx // 2, args.degrees.replace(",", ""),
+                                                    args.forms.replace(",", "+"))
     return "tet-kuhn%d^3x6-P2vec-elasticity+neohookean-residual-fp64" % args.nx
 
 
 def build_cases(args):
     """Operators of one step.  Each case holds the seeded inputs shared by the GPU and the oracle."""
     if args.nx is None:
-        args.nx = {"hex": 64, "hex-vector": 48, "tet-pk": 16, "tet-p1-mass": 8, "tet-p2": 48}[args.workload]
+        args.nx = {"hex": 64, "hex-vector": 48, "tet-pk": 16, "planar": 512, "tet-p1-mass": 8,
+                   "tet-p2": 48}[args.workload]
     cases = []
     if args.workload == "hex-vector":
         mesh = fi.hex_box_mesh(args.nx, perturb=0.1, seed=1)
@@ -157,6 +161,32 @@ def build_cases(args):
                 cases.append(dict(name="Q%d %s" % (p, f), cell_type=8, mesh=mesh, p=p, ncomp=1, form=f,
                                   cell_vert=cv, cell_node=cell_node, nnode=nnode, x=x, kw=dict(k2=1.0),
                                   okw=dict(k2=1.0), qdeg=p + 1))
+    elif args.workload == "planar":
+        for cell in ("quad", "tri"):
+            mesh = fi.quad_mesh(args.nx, perturb=0.1, seed=1) if cell == "quad" else fi.tri_mesh(args.nx // 2,
+                                                                                                 perturb=0.1, seed=1)
+            for p in [int(p) for p in args.degrees.split(",")]:
+                if cell == "quad":
+                    cn, nnode = fi.quad_node_map(args.nx, p)
+                    m1 = args.nx * p + 1
+                    v = np.arange(nnode)
+                    nodes = np.stack([v % m1, v // m1, np.zeros(nnode)], axis=1) / (m1 - 1)  # the node grid
+                else:
+                    cn, nnode, node_coords = fi.tri_node_map(mesh.cell_vert, mesh.nvert, p)
+                    nodes = node_coords(mesh.coords)
+                for f in args.forms.split(","):
+                    nc = 2 if f in ("elasticity", "hyper_res", "hyper_jac") else 1
+                    if nc == 2:
+                        x = fi.sinusoid_displacement(nodes, seed=2)[:, :2].ravel()
+                        kw = dict(lam=1.0, mu=1.0, law=1)
+                    else:
+                        x = fi.uniform_vector(nnode, seed=0)
+                        kw = dict(k2=1.0)
+                    ct = 40 if cell == "quad" else 3
+                    qd = p + 1 if cell == "quad" else (max(4, 2 * p) if f.startswith("hyper") else 2 * p)
+                    cases.append(dict(name="%s %s%d %s" % (cell, "Q" if cell == "quad" else "P", p, f), cell_type=ct,
+                                      mesh=mesh, p=p, ncomp=nc, form=f, cell_vert=mesh.cell_vert, cell_node=cn,
+                                      nnode=nnode, x=x, kw=kw, okw=kw, qdeg=qd))
     elif args.workload == "tet-pk":
         mesh = fi.kuhn_tet_mesh(args.nx)
         for p in [int(p) for p in args.degrees.split(",")]:
@@ -298,11 +328,13 @@ def sub_mesh(case, ncell_sample):
 
 # Cells per oracle sample: about 1-2.5 s of oracle work per operator for the
 # baseline, about 0.1 s per operator and step for the reference arm.
-SAMPLE_BASELINE = {("tet", 3): 6000, ("tet", 4): 1500, ("tet", 5): 400, ("tet", 6): 150,("hex", 1): 262144, ("hex", 2): 64000, ("hex", 3): 21952, ("hex", 4): 8000, ("hex", 5): 2744,
+SAMPLE_BASELINE = {("quad", 1): 200000, ("quad", 2): 100000, ("quad", 3): 50000, ("quad", 4): 25000,
+                   ("tri", 1): 100000, ("tri", 2): 50000, ("tri", 3): 20000, ("tri", 4): 10000, ("tet", 3): 6000, ("tet", 4): 1500, ("tet", 5): 400, ("tet", 6): 150,("hex", 1): 262144, ("hex", 2): 64000, ("hex", 3): 21952, ("hex", 4): 8000, ("hex", 5): 2744,
                    ("hex", 6): 1728, ("hex", 7): 512, ("hex", 8): 216, ("tet", 1): 3072, ("tet", 2): 200000,
                    ("hexv", 1): 110592, ("hexv", 2): 24000, ("hexv", 3): 4000, ("hexv", 4): 1000, ("hexv", 5): 250,
                    ("hexv", 6): 100}
-SAMPLE_STEP = {("tet", 3): 400, ("tet", 4): 100, ("tet", 5): 30, ("tet", 6): 12,("hex", 1): 13824, ("hex", 2): 2744, ("hex", 3): 1000, ("hex", 4): 512, ("hex", 5): 216,
+SAMPLE_STEP = {("quad", 1): 20000, ("quad", 2): 8000, ("quad", 3): 3000, ("quad", 4): 1500, ("tri", 1): 10000,
+               ("tri", 2): 4000, ("tri", 3): 1500, ("tri", 4): 700, ("tet", 3): 400, ("tet", 4): 100, ("tet", 5): 30, ("tet", 6): 12,("hex", 1): 13824, ("hex", 2): 2744, ("hex", 3): 1000, ("hex", 4): 512, ("hex", 5): 216,
                ("hex", 6): 125, ("hex", 7): 64, ("hex", 8): 27, ("tet", 1): 3072, ("tet", 2): 6000,
                ("hexv", 1): 8000, ("hexv", 2): 1500, ("hexv", 3): 250, ("hexv", 4): 64, ("hexv", 5): 16,
                ("hexv", 6): 8}
@@ -316,7 +348,7 @@ def oracle_rate(cases, repeats=1, samples=SAMPLE_STEP):
     out = []
     for c in cases:
         ncell = c["mesh"].ncell
-        key = ("tet" if c["cell_type"] == 4 else ("hexv" if c["ncomp"] == 3 else "hex"), c["p"])
+        key = ({3: "tri", 4: "tet", 40: "quad"}.get(c["cell_type"]) or ("hexv" if c["ncomp"] == 3 else "hex"), c["p"])
         n_big = min(samples.get(key, 64), ncell)
         times = []
         for n in sorted({max(1, n_big // 2), n_big}):
@@ -502,6 +534,10 @@ def gpu_arm(args, world, rank, local):
         moment = dom["case"]["p"] == 2 and dom["case"]["form"] in ("hyper_res", "hyper_jac")
         kname = "tet_dense_kernel<%s>" if dom["case"]["p"] >= 3 else (
             "tet_moment_kernel<%s>" if moment else "tet_apply_kernel<%s>")
+        if dom["case"]["cell_type"] == 40:
+            kname = "quad_apply_kernel<%s>"
+        elif dom["case"]["cell_type"] == 3:
+            kname = "simplex_dense_kernel<DIM=2, %s>"
         kh, kname = None, kname % dom["case"]["name"]
     traffic = NCU_TRAFFIC.get((kh, dom["case"]["name"]))
     if args.workload == "hex" and args.precision != "fp64":
@@ -575,6 +611,12 @@ def gpu_arm(args, world, rank, local):
                         "geometry": "stored FP64 J^-1 and w|det J| per point", "lambda": 1.0, "mu": 1.0,
                         "input": "residual and coefficient: sinusoid displacement (8 terms, amplitude 0.05, seed 2) "
                                  "on the node grid; elasticity and Jacobian: x ~ U[-1,1) seed 1"})
+        elif args.workload == "planar":
+            cfg.update({"mesh": "%d^2 quads and %d^2 boxes x 2 triangles, unit square, interior vertices perturbed "
+                                "U[-0.1h,0.1h], seed 1" % (args.nx, args.nx // 2),
+                        "quadrature": "quads: p+1 Gauss points per direction; triangles: collapsed rule exact for the "
+                                      "polynomial integrand", "vector forms": "plane strain, lambda = mu = 1",
+                        "input": "scalar x ~ U[-1,1) seed 0; vector: sinusoid displacement seed 2"})
         elif args.workload == "tet-pk":
             cfg.update({"mesh": "%d^3 boxes x 6 Kuhn tets" % args.nx,
                         "quadrature": "collapsed Gauss-Jacobi, exact for the polynomial integrand (degree 2p mass/"
@@ -888,10 +930,11 @@ def main():
     if args.precision is None:
         args.precision = "fp32" if args.workload == "batched" else "fp64"
     if args.degrees is None:
-        args.degrees = {"hex-vector": "1,2,3,4", "tet-pk": "3,4,5,6"}.get(args.workload, "1,2,3,4,5,6")
+        args.degrees = {"hex-vector": "1,2,3,4", "tet-pk": "3,4,5,6", "planar": "1,2,3,4"}.get(args.workload,
+                                                                                                "1,2,3,4,5,6")
     if args.forms is None:
-        args.forms = {"hex-vector": "elasticity,hyper_res,hyper_jac",
-                      "tet-pk": "helmholtz,elasticity"}.get(args.workload, "laplace,helmholtz")
+        args.forms = {"hex-vector": "elasticity,hyper_res,hyper_jac", "tet-pk": "helmholtz,elasticity",
+                      "planar": "helmholtz,elasticity"}.get(args.workload, "laplace,helmholtz")
     world, rank, local = dist_setup(args)
     if args.workload == "batched" and args.impl != "reference":
         batched_arm(args, world, rank, local)

@@ -64,7 +64,12 @@ typedef enum {
   MFA_ERR_DOMAIN = 9         /* a kernel met det J <= 0 or a deformation with J <= 0 */
 } mfa_status;
 
-enum { MFA_CELL_TET4 = 4, MFA_CELL_HEX8 = 8 };
+/* Cell types (ids, not vertex counts): tetrahedra (4 vertices), hexahedra (8),
+ * and in the plane z = 0 triangles (3) and quadrilaterals (4, local vertex v at
+ * corner (v & 1, v >> 1 & 1)).  On planar meshes coords keep 3 entries per
+ * vertex (z ignored), vector fields have 2 components and the vector forms are
+ * plane strain. */
+enum { MFA_CELL_TRI3 = 3, MFA_CELL_TET4 = 4, MFA_CELL_HEX8 = 8, MFA_CELL_QUAD4 = 40 };
 
 /* Forms of the Supplementary material (bilinear forms taken by their action). */
 enum {
@@ -151,8 +156,8 @@ MFA_API int mfa_mesh_upload(mfa_ctx *ctx, int cell_type, int64_t ncell, int64_t 
                     const int32_t *cell_vert, mfa_mesh **out);
 MFA_API int mfa_mesh_destroy(mfa_mesh *mesh);
 
-/* Continuous Lagrange space of `degree` (P1..P6 on tets, Q1..Q8 on hexes) with
- * ncomp in {1, 3}.  cell_node [ncell][nloc] (host, int32) is the cell->node
+/* Continuous Lagrange space of `degree` (P1..P6 on tets and triangles, Q1..Q8 on
+ * hexes and quads) with ncomp in {1, 3} (planar meshes: {1, 2}).  cell_node [ncell][nloc] (host, int32) is the cell->node
  * map of Section 2.2 (`cell2dof`); entries must lie in [0, nnode) and be
  * distinct within a cell.  cell_node = NULL: the library builds the map from
  * the mesh (mfa_build_cell_node; nnode is then ignored; read it back with
@@ -161,13 +166,14 @@ MFA_API int mfa_mesh_destroy(mfa_mesh *mesh);
  * the midpoints of edges (0,1), (0,2), (0,3), (1,2), (1,3), (2,3); P3..P6
  * tets, the equispaced lattice points (i, j, k)/p of the reference tet
  * (vertex 0 at the origin, vertex e+1 at the unit vector e), i fastest, then
- * j, then k. */
+ * j, then k; quads, the GLL tensor points with x fastest; triangles (every
+ * degree), the lattice points (i, j)/p, i fastest. */
 MFA_API int mfa_space_create(mfa_ctx *ctx, mfa_mesh *mesh, int degree, int ncomp, const int32_t *cell_node,
                      int64_t nnode, mfa_space **out);
 /* The space's cell -> node map, copied to host memory [ncell][nloc]. */
 MFA_API int mfa_space_get_cell_node(const mfa_space *space, int32_t *cell_node);
 
-/* Cell -> node map of the continuous Q_p (hex, p <= 8) or P_p (tet, p <= 6)
+/* Cell -> node map of the continuous Q_p (hex and quad, p <= 8) or P_p (tet and triangle, p <= 6)
  * space from the vertex connectivity alone (host only, no device), in the
  * local node order of mfa_space_create.  A node on a vertex, edge or face is
  * the same global node in every cell that contains it, whatever the cells'

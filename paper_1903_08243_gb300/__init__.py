@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libmfa.so")
 # ---- constants mirrored from include/mfa.h
 MFA_OK, MFA_ERR_ARG, MFA_ERR_RANGE, MFA_ERR_UNSUPPORTED, MFA_ERR_CUDA = 0, 1, 2, 3, 4
 MFA_ERR_OOM, MFA_ERR_TIMEOUT, MFA_ERR_NOT_CONVERGED, MFA_ERR_BREAKDOWN, MFA_ERR_DOMAIN = 5, 6, 7, 8, 9
-MFA_CELL_TET4, MFA_CELL_HEX8 = 4, 8
+MFA_CELL_TRI3, MFA_CELL_TET4, MFA_CELL_HEX8, MFA_CELL_QUAD4 = 3, 4, 8, 40
 MFA_FORM_MASS, MFA_FORM_LAPLACE, MFA_FORM_HELMHOLTZ = 0, 1, 2
 MFA_FORM_ELASTICITY, MFA_FORM_HYPER_RES, MFA_FORM_HYPER_JAC = 3, 4, 5
 MFA_LAW_SVK, MFA_LAW_NEOHOOKE = 0, 1
@@ -253,6 +253,10 @@ def mfa_form_destroy(form):
 def _nloc(cell_type, degree):
     if cell_type == MFA_CELL_HEX8:
         return (degree + 1) ** 3
+    if cell_type == MFA_CELL_QUAD4:
+        return (degree + 1) ** 2
+    if cell_type == MFA_CELL_TRI3:
+        return (degree + 1) * (degree + 2) // 2
     return {1: 4, 2: 10}.get(degree, (degree + 1) * (degree + 2) * (degree + 3) // 6)
 
 

@@ -51,6 +51,8 @@ int nloc_of(int cell_type, int degree) {
     return degree >= 3 && degree <= mfa::kTetMaxP ? mfa::tet_lattice_size(degree) : -1;
   }
   if (cell_type == MFA_CELL_HEX8 && degree >= 1 && degree <= 8) return (degree + 1) * (degree + 1) * (degree + 1);
+  if (cell_type == MFA_CELL_TRI3 && degree >= 1 && degree <= mfa::kTetMaxP) return mfa::tri_lattice_size(degree);
+  if (cell_type == MFA_CELL_QUAD4 && degree >= 1 && degree <= 8) return (degree + 1) * (degree + 1);
   return -1;
 }
 
@@ -68,6 +70,40 @@ void count_work(mfa_form* f) {
   const int kind = f->p.kind;
   double per_cell = 0.0, bytes = 0.0;
   double exec_cell = -1.0;  // operations the kernel executes, where fewer than the algorithmic count
+  if (mfa::is_planar(sp->mesh->cell_type)) {
+    // Planar cells.  Quads: per component B and B^T 2 x 2 (q n^2 + q^2 n), D and D^T 8 q^3 (the Jacobian action
+    // also interpolates the linearisation point: 2 (q n^2 + q^2 n) + 4 q^3); per point the pointwise work; scatter
+    // adds.  Triangles (dense): per point interpolation 2 (value) + 4 (gradient) per dof and component, test side
+    // the same, the pointwise work.  Pointwise: scalar G g 6 + value terms; vector: physical gradient(s) 12 each,
+    // the physics (3D laws in plane strain), flux map 13.
+    const double nl = sp->nloc, nc = sp->ncomp;
+    const bool val = kind == MFA_FORM_MASS || kind == MFA_FORM_HELMHOLTZ, grad = kind != MFA_FORM_MASS;
+    const bool jac = kind == MFA_FORM_HYPER_JAC, svk = f->p.law == MFA_LAW_SVK;
+    double per_pt;
+    if (kind <= MFA_FORM_HELMHOLTZ) per_pt = nc * ((grad ? 6.0 : 0.0) + (val ? 2.0 : 0.0));
+    else if (kind == MFA_FORM_ELASTICITY) per_pt = 12.0 + 24.0 + 13.0;
+    else if (kind == MFA_FORM_HYPER_RES) per_pt = 12.0 + (svk ? 102.0 : 66.0) + 13.0 + 2.0;
+    else per_pt = 24.0 + (svk ? 243.0 : 202.0) + 13.0;
+    if (sp->mesh->cell_type == MFA_CELL_QUAD4) {
+      const double n = sp->degree + 1, q = f->nq1, bsw = 2.0 * (q * n * n + q * q * n);
+      per_cell = nc * (2.0 * bsw + (grad || kind == MFA_FORM_HYPER_RES ? 8.0 * q * q * q : 0.0)) +
+                 (jac ? nc * (bsw + 4.0 * q * q * q) : 0.0) + per_pt * q * q + nc * n * n;
+      bytes = ncell * (4.0 * n * n + 8.0 * mfa::quad_geom_entries(kind) * q * q);
+    } else {
+      const double nq = f->nq;
+      const bool val_out = val || kind == MFA_FORM_HYPER_RES;
+      const double per_q = nl * nc * ((val ? 2.0 : 0.0) + (grad ? 4.0 : 0.0) + (jac ? 4.0 : 0.0)) +
+                           nl * nc * ((val_out ? 2.0 : 0.0) + (grad ? 4.0 : 0.0)) + per_pt + 1.0;
+      per_cell = nq * per_q + 20.0 + nl * nc;
+      bytes = ncell * (4.0 * nl + 12.0) + 24.0 * sp->mesh->nvert;
+    }
+    if (jac) bytes += 8.0 * ndof;
+    bytes += 16.0 * ndof;
+    if (f->scatter == MFA_SCATTER_COLOUR) bytes += 4.0 * ncell;
+    f->flops = f->flops_executed = per_cell * ncell;
+    f->bytes = bytes;
+    return;
+  }
   if (sp->mesh->cell_type == MFA_CELL_HEX8 && f->launch.variant == MFA_VARIANT_EVEN_ODD) {
     // even-odd line products: per line, forming e/o (2h adds), then per mirror pair of outputs
     // (odd: one multiply) + 2h FMA + 2 adds, and for odd n a middle output
@@ -237,6 +273,50 @@ static int tet_dense_tables(mfa_form* f, int deg) {
   return MFA_OK;
 }
 
+// Triangles P1..P6: dense tables for the warp-per-cell kernel, gradients with 2 components.
+int tri_tables(mfa_form* f) {
+  const int p = f->space->degree, kind = f->p.kind, nl = f->space->nloc;
+  int qdeg = f->p.qdeg;
+  if (qdeg <= 0) qdeg = (kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC) ? (p > 2 ? 2 * p : 4) : 2 * p;
+  int poly = -1;  // integrand degree on affine cells (-1: not polynomial)
+  if (kind == MFA_FORM_MASS || kind == MFA_FORM_HELMHOLTZ) poly = 2 * p;
+  if (kind == MFA_FORM_LAPLACE || kind == MFA_FORM_ELASTICITY) poly = 2 * (p - 1);
+  if ((kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC) && f->p.law == MFA_LAW_SVK) poly = 4 * (p - 1);
+  const int deg = (poly >= 0 && poly <= qdeg) ? poly : qdeg;
+  const int m = (deg + 2) / 2;
+  if (m > mfa::kMaxN) return fail(MFA_ERR_UNSUPPORTED, "triangle rule of degree %d", deg);
+  const int nq = m * m;
+  std::vector<double> pts(2 * nq), w(nq), phi((size_t)nq * nl), dphi((size_t)nq * nl * 2);
+  mfa::tri_rule_collapsed(deg, pts.data(), w.data());
+  for (int q = 0; q < nq; ++q) mfa::tri_basis_pk(p, &pts[2 * q], &phi[(size_t)q * nl], &dphi[(size_t)q * nl * 2]);
+  const size_t nb = (size_t)nl * nq;
+  std::vector<double> buf(6 * nb + nq);
+  double* phi_aq = buf.data();
+  double* dphi_aeq = phi_aq + nb;
+  double* phi_qa = dphi_aeq + 2 * nb;
+  double* dphi_qae = phi_qa + nb;
+  double* wq = dphi_qae + 2 * nb;
+  for (int q = 0; q < nq; ++q)
+    for (int a = 0; a < nl; ++a) {
+      const double v = phi[(size_t)q * nl + a];
+      phi_aq[(size_t)a * nq + q] = v;
+      phi_qa[(size_t)q * nl + a] = v;
+      for (int e = 0; e < 2; ++e) {
+        const double d = dphi[((size_t)q * nl + a) * 2 + e];
+        dphi_aeq[((size_t)a * 2 + e) * nq + q] = d;
+        dphi_qae[((size_t)q * nl + a) * 2 + e] = d;
+      }
+    }
+  for (int q = 0; q < nq; ++q) wq[q] = w[q];
+  int rc = cuda_alloc((void**)&f->d_tdense, sizeof(double) * buf.size(), "triangle tables");
+  if (!rc && cudaMemcpy(f->d_tdense, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = fail(MFA_ERR_CUDA, "triangle tables: upload");
+  if (rc) return rc;
+  f->tdense_nq = nq;
+  f->nq = nq;
+  return MFA_OK;
+}
+
 int tet_tables(mfa_form* f) {
   const int p = f->space->degree, kind = f->p.kind;
   int qdeg = f->p.qdeg;
@@ -334,7 +414,37 @@ static int apply_form_raw(mfa_form* f, const double* x, double* y, cudaStream_t 
     const int32_t* list = colour ? sp->d_colour_cells + sp->colour_offsets[k] : nullptr;
     const int64_t count = colour ? sp->colour_offsets[k + 1] - sp->colour_offsets[k] : sp->mesh->ncell;
     cudaError_t e;
-    if (sp->mesh->cell_type == MFA_CELL_HEX8 && sp->ncomp == 3) {
+    if (sp->mesh->cell_type == MFA_CELL_QUAD4) {
+      mfa::QuadArgs a{x, y, sp->d_cell_node, static_cast<const double*>(f->d_geom), f->d_coef, list, count,
+                      f->p.lambda, f->p.mu, f->p.b[0], f->p.b[1], ctx->d_err};
+      e = mfa::quad_apply_launch(sp->degree + 1, f->nq1, sp->ncomp, f->p.kind, f->p.law, colour, f->hex, a,
+                                 ctx->sm_count, stream);
+    } else if (sp->mesh->cell_type == MFA_CELL_TRI3) {
+      const int64_t nb = (int64_t)sp->nloc * f->tdense_nq;
+      mfa::TetDenseArgs a{};
+      a.x = x;
+      a.y = y;
+      a.coords = sp->mesh->d_coords;
+      a.cell_vert = sp->mesh->d_cell_vert;
+      a.cell_node = sp->d_cell_node;
+      a.ucoef = f->d_coef;
+      a.cell_list = list;
+      a.count = count;
+      a.phi_aq = f->d_tdense;
+      a.dphi_aeq = a.phi_aq + nb;
+      a.phi_qa = a.dphi_aeq + 2 * nb;
+      a.dphi_qae = a.phi_qa + nb;
+      a.w = a.dphi_qae + 2 * nb;
+      a.nq = f->tdense_nq;
+      a.k2 = f->p.k2;
+      a.lambda = f->p.lambda;
+      a.mu = f->p.mu;
+      a.b0 = f->p.b[0];
+      a.b1 = f->p.b[1];
+      a.b2 = 0.0;
+      a.err = ctx->d_err;
+      e = mfa::tri_dense_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, a, ctx->sm_count, stream);
+    } else if (sp->mesh->cell_type == MFA_CELL_HEX8 && sp->ncomp == 3) {
       mfa::HexVecArgs a{x, y, sp->d_cell_node, static_cast<const double*>(f->d_geom), f->d_coef, list, count,
                         f->gstride, f->p.lambda, f->p.mu, f->p.b[0], f->p.b[1], f->p.b[2], ctx->d_err};
       const int n = sp->degree + 1;
@@ -436,11 +546,13 @@ int mfa_mesh_upload(mfa_ctx* ctx, int cell_type, int64_t ncell, int64_t nvert, c
                     const int32_t* cell_vert, mfa_mesh** out) {
   if (!ctx || !out || !coords || !cell_vert) return fail(MFA_ERR_ARG, "mfa_mesh_upload: NULL argument");
   *out = nullptr;
-  if (cell_type != MFA_CELL_TET4 && cell_type != MFA_CELL_HEX8)
+  if (cell_type != MFA_CELL_TET4 && cell_type != MFA_CELL_HEX8 && cell_type != MFA_CELL_TRI3 &&
+      cell_type != MFA_CELL_QUAD4)
     return fail(MFA_ERR_ARG, "mfa_mesh_upload: cell_type %d", cell_type);
+  const int nv = mfa::verts_of(cell_type);
   if (ncell < 0 || nvert <= 0 || nvert > INT32_MAX || ncell > INT32_MAX)
     return fail(MFA_ERR_ARG, "mfa_mesh_upload: ncell %lld nvert %lld", (long long)ncell, (long long)nvert);
-  for (int64_t i = 0; i < ncell * cell_type; ++i)
+  for (int64_t i = 0; i < ncell * nv; ++i)
     if (cell_vert[i] < 0 || cell_vert[i] >= nvert)
       return fail(MFA_ERR_RANGE, "mfa_mesh_upload: cell_vert[%lld] = %d outside [0, %lld)", (long long)i,
                   cell_vert[i], (long long)nvert);
@@ -453,11 +565,11 @@ int mfa_mesh_upload(mfa_ctx* ctx, int cell_type, int64_t ncell, int64_t nvert, c
   m->ncell = ncell;
   m->nvert = nvert;
   int rc = cuda_alloc((void**)&m->d_coords, sizeof(double) * 3 * nvert, "coords");
-  if (!rc) rc = cuda_alloc((void**)&m->d_cell_vert, sizeof(int32_t) * cell_type * ncell, "cell_vert");
+  if (!rc) rc = cuda_alloc((void**)&m->d_cell_vert, sizeof(int32_t) * nv * ncell, "cell_vert");
   if (!rc && cudaMemcpy(m->d_coords, coords, sizeof(double) * 3 * nvert, cudaMemcpyHostToDevice) != cudaSuccess)
     rc = fail(MFA_ERR_CUDA, "mfa_mesh_upload: copy coords");
   if (!rc && ncell > 0 &&
-      cudaMemcpy(m->d_cell_vert, cell_vert, sizeof(int32_t) * cell_type * ncell, cudaMemcpyHostToDevice) != cudaSuccess)
+      cudaMemcpy(m->d_cell_vert, cell_vert, sizeof(int32_t) * nv * ncell, cudaMemcpyHostToDevice) != cudaSuccess)
     rc = fail(MFA_ERR_CUDA, "mfa_mesh_upload: copy cell_vert");
   if (rc) {
     mfa_mesh_destroy(m);
@@ -484,7 +596,7 @@ int mfa_space_create(mfa_ctx* ctx, mfa_mesh* mesh, int degree, int ncomp, const 
   if (nl < 0) return fail(MFA_ERR_UNSUPPORTED, "mfa_space_create: degree %d on cell type %d", degree, mesh->cell_type);
   std::vector<int32_t> built;
   if (!cell_node) {  // build the map from the mesh's vertex connectivity
-    std::vector<int32_t> cv((size_t)mesh->ncell * mesh->cell_type);
+    std::vector<int32_t> cv((size_t)mesh->ncell * mfa::verts_of(mesh->cell_type));
     if (!cv.empty())
       MFA_CUDA(cudaMemcpy(cv.data(), mesh->d_cell_vert, cv.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
     built.resize((size_t)mesh->ncell * nl);
@@ -492,7 +604,9 @@ int mfa_space_create(mfa_ctx* ctx, mfa_mesh* mesh, int degree, int ncomp, const 
     if (rc) return rc;
     cell_node = built.data();
   }
-  if (ncomp != 1 && ncomp != 3) return fail(MFA_ERR_ARG, "mfa_space_create: ncomp %d", ncomp);
+  const bool planar = mfa::is_planar(mesh->cell_type);
+  if (ncomp != 1 && ncomp != (planar ? 2 : 3))
+    return fail(MFA_ERR_ARG, "mfa_space_create: ncomp %d (1 or %d on this mesh)", ncomp, planar ? 2 : 3);
   if (nnode <= 0 || nnode * ncomp > INT32_MAX) return fail(MFA_ERR_ARG, "mfa_space_create: nnode %lld", (long long)nnode);
   {
     std::vector<int64_t> stamp(nnode, -1);
@@ -553,6 +667,8 @@ int mfa_space_destroy(mfa_space* s) {
 }
 
 static int default_variant(const mfa_space* sp, int nq, int precision) {
+  if (sp->mesh->cell_type == MFA_CELL_QUAD4) return MFA_VARIANT_POINT;
+  if (sp->mesh->cell_type == MFA_CELL_TRI3) return MFA_VARIANT_CELL_WARP;
   if (sp->mesh->cell_type != MFA_CELL_HEX8) return sp->degree >= 3 ? MFA_VARIANT_CELL_WARP : MFA_VARIANT_CELL;
   if (sp->ncomp == 3) return MFA_VARIANT_POINT;  // the vector forms have the point kernel only
   return mfa::hex_default_variant(sp->degree + 1, nq, precision);
@@ -562,6 +678,16 @@ static int default_variant(const mfa_space* sp, int nq, int precision) {
 static int cb_options(const mfa_form* f, int variant, int* out) {
   const mfa_space* sp = f->space;
   const int n = sp->degree + 1, nq = f->p.qdeg > 0 ? f->p.qdeg : n;
+  if (sp->mesh->cell_type == MFA_CELL_QUAD4) {
+    if (variant != MFA_VARIANT_POINT) return 0;
+    out[0] = mfa::quad_cells_per_block(n, nq);
+    return 1;
+  }
+  if (sp->mesh->cell_type == MFA_CELL_TRI3) {
+    if (variant != MFA_VARIANT_CELL_WARP) return 0;
+    out[0] = 8;  // one warp per cell, 8 warps per block
+    return 1;
+  }
   if (sp->mesh->cell_type != MFA_CELL_HEX8) {
     if (sp->degree >= 3) {
       if (variant != MFA_VARIANT_CELL_WARP) return 0;
@@ -590,7 +716,10 @@ static std::vector<mfa_launch_config> form_configs(const mfa_form* f) {
   std::vector<mfa_launch_config> all;
   const bool hex = f->space->mesh->cell_type == MFA_CELL_HEX8;
   std::vector<int> variants;
-  if (!hex) variants = {f->space->degree >= 3 ? MFA_VARIANT_CELL_WARP : MFA_VARIANT_CELL};
+  const int ctype = f->space->mesh->cell_type;
+  if (ctype == MFA_CELL_QUAD4) variants = {MFA_VARIANT_POINT};
+  else if (ctype == MFA_CELL_TRI3) variants = {MFA_VARIANT_CELL_WARP};
+  else if (!hex) variants = {f->space->degree >= 3 ? MFA_VARIANT_CELL_WARP : MFA_VARIANT_CELL};
   else if (f->p.precision == MFA_PREC_FP64) variants = {MFA_VARIANT_POINT, MFA_VARIANT_EVEN_ODD};
   else variants = {MFA_VARIANT_LINE, MFA_VARIANT_LINE_STAGED};
   const bool colour_ok = f->p.precision == MFA_PREC_FP64;
@@ -660,8 +789,23 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
                                           prm->scatter == MFA_SCATTER_COLOUR || prm->scatter == MFA_SCATTER_WARP))
     return fail(MFA_ERR_UNSUPPORTED,
                 "mfa_form_create: FP32/BF16 cover hex forms with p+1 points per direction and the atomic scatter");
-  if (kind >= MFA_FORM_ELASTICITY && sp->ncomp != 3)
-    return fail(MFA_ERR_ARG, "mfa_form_create: form %d needs a 3-component space", kind);
+  const bool planar = mfa::is_planar(ct);
+  if (kind >= MFA_FORM_ELASTICITY && sp->ncomp != (planar ? 2 : 3))
+    return fail(MFA_ERR_ARG, "mfa_form_create: form %d needs a vector space", kind);
+  if (planar) {
+    const int n = sp->degree + 1, nq = prm->qdeg > 0 ? prm->qdeg : n;
+    const bool hyper = kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC;
+    bool ok = (sp->ncomp == 1 && kind <= MFA_FORM_HELMHOLTZ) ||
+              (sp->ncomp == 2 && kind >= MFA_FORM_LAPLACE && kind != MFA_FORM_HELMHOLTZ);
+    ok = ok && prm->precision == MFA_PREC_FP64 && prm->scatter != MFA_SCATTER_WARP && prm->cells_per_block == 0;
+    if (ct == MFA_CELL_QUAD4) ok = ok && (nq == n || (nq == n + 1 && n + 1 <= mfa::kMaxN) ||
+                                          (hyper && nq == 2 * n && 2 * n <= mfa::kMaxN));
+    if (!ok)
+      return fail(MFA_ERR_UNSUPPORTED,
+                  "mfa_form_create: planar cells cover FP64 mass/Laplace/Helmholtz and vector Laplace/elasticity/"
+                  "hyperelasticity (quads: p+1 or p+2 points, 2p+2 for the hyperelastic forms), atomic or colour "
+                  "scatter");
+  }
   if (ct == MFA_CELL_HEX8 && sp->ncomp == 1 && kind > MFA_FORM_HELMHOLTZ)
     return fail(MFA_ERR_UNSUPPORTED, "mfa_form_create: scalar hex kernels cover mass/Laplace/Helmholtz");
   if (ct == MFA_CELL_HEX8 && sp->ncomp == 3) {
@@ -706,7 +850,27 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
                 prm->cells_per_block);
     f->launch.cb = prm->cells_per_block;
   }
-  if (!rc && ct == MFA_CELL_HEX8) {
+  if (!rc && ct == MFA_CELL_QUAD4) {
+    const int n = sp->degree + 1;
+    f->nq1 = prm->qdeg > 0 ? prm->qdeg : n;
+    rc = hex_tables(f);  // 1D tables: the same B, D, points and weights
+    f->nq = f->nq1 * f->nq1;
+    if (!rc) {
+      const int ng = mfa::quad_geom_entries(kind);
+      f->gstride = (int64_t)ng * f->nq;
+      rc = cuda_alloc((void**)&f->d_geom, sizeof(double) * f->gstride * sp->mesh->ncell, "geometric factors");
+      if (!rc) {
+        mfa::clear_stale_error();
+        cudaError_t e = mfa::quad_geometry_launch(f->nq1, kind, kind == MFA_FORM_HELMHOLTZ ? prm->k2 : 1.0, f->hex,
+                                                  sp->mesh->d_coords, sp->mesh->d_cell_vert, sp->mesh->ncell,
+                                                  static_cast<double*>(f->d_geom), ctx->d_err, ctx->stream);
+        if (e != cudaSuccess) rc = fail(MFA_ERR_CUDA, "geometry kernel: %s", cudaGetErrorString(e));
+      }
+      if (!rc) rc = mfa_sync(ctx);
+    }
+  } else if (!rc && ct == MFA_CELL_TRI3) {
+    rc = tri_tables(f);
+  } else if (!rc && ct == MFA_CELL_HEX8) {
     const int n = sp->degree + 1;
     f->nq1 = prm->qdeg > 0 ? prm->qdeg : n;
     const bool vec_2n = sp->ncomp == 3 && f->nq1 == 2 * n && n <= 4;  // validated above for the hyperelastic forms
@@ -1018,6 +1182,7 @@ int mfa_diagonal(mfa_ctx* ctx, mfa_form* f, double* d) {
     return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: linear forms only");
   if (f->space->mesh->cell_type == MFA_CELL_TET4 && f->space->degree >= 3)
     return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: tets of degree %d", f->space->degree);
+  if (mfa::is_planar(f->space->mesh->cell_type)) return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: planar cells");
   MFA_CUDA(cudaSetDevice(ctx->device));
   mfa_space* sp = f->space;
   const int64_t ndof = sp->nnode * sp->ncomp;

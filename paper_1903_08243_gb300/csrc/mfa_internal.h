@@ -31,6 +31,13 @@ void tet_basis(int p, const double* xi, double* phi, double* dphi);
 constexpr int kTetMaxP = 6;
 int tet_lattice_size(int p);
 void tet_basis_pk(int p, const double* xi, double* phi, double* dphi);
+// Triangles: collapsed rule (pts [nq][2]) and the P_p lattice basis (nodes (i, j)/p, i fastest; dphi [n][2]).
+int tri_rule_collapsed(int degree, double* pts, double* w);
+int tri_lattice_size(int p);
+void tri_basis_pk(int p, const double* xi, double* phi, double* dphi);
+// Vertices per cell of each cell type, and whether it is planar.
+inline int verts_of(int ct) { return ct == MFA_CELL_TRI3 ? 3 : ((ct == MFA_CELL_TET4 || ct == MFA_CELL_QUAD4) ? 4 : 8); }
+inline bool is_planar(int ct) { return ct == MFA_CELL_TRI3 || ct == MFA_CELL_QUAD4; }
 
 // ---------------------------------------------------------------- colour.cpp
 // Greedy first-fit colouring: cells sharing a node get different colours.
@@ -172,6 +179,25 @@ struct TetApplyArgs {
 // threads: threads (cells) per block, one of tet_cb_options.
 cudaError_t tet_apply_launch(int p, int ncomp, int kind, int law, bool colour, bool agg, int threads,
                              const TetTables& tb, const TetApplyArgs& a, int sm_count, cudaStream_t s);
+// ---------------------------------------------------------------- quad kernels (quad_kernels.cu)
+struct QuadArgs {
+  const double* x;
+  double* y;
+  const int32_t* cell_node;  // [ncell][n^2]
+  const double* geom;        // [ncell][ng][nq^2] (quad_geom_entries)
+  const double* ucoef;       // HYPER_JAC linearisation point
+  const int32_t* cell_list;
+  int64_t count;
+  double lambda, mu, b0, b1;
+  int* err;
+};
+int quad_geom_entries(int kind);
+int quad_cells_per_block(int n, int nq);
+cudaError_t quad_geometry_launch(int nq, int kind, double c0, const HexTables& tb, const double* coords,
+                                 const int32_t* cell_vert, int64_t ncell, double* geom, int* err, cudaStream_t s);
+cudaError_t quad_apply_launch(int n, int nq, int ncomp, int kind, int law, bool colour, const HexTables& tb,
+                              const QuadArgs& a, int sm_count, cudaStream_t s);
+
 // P3..P6 (dense tabulation, one warp per cell).  Tables in device memory, nl local dofs, nq points.
 struct TetDenseArgs {
   const double* x;
@@ -192,6 +218,19 @@ struct TetDenseArgs {
   int* err;
 };
 cudaError_t tet_dense_launch(int p, int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, int sm_count,
+                             cudaStream_t s);
+// Triangles P1..P3, one thread per cell (tri_kernels.cu): tables as a kernel parameter, at most 16 points.
+constexpr int kTriMaxNl = 10, kTriMaxQ = 16;
+struct TriTables {
+  int nq;
+  double w[kTriMaxQ];
+  double phi[kTriMaxQ * kTriMaxNl];       // [q][a]
+  double dphi[kTriMaxQ * kTriMaxNl * 2];  // [q][a][e]
+};
+cudaError_t tri_cell_launch(int p, int ncomp, int kind, int law, bool colour, int threads, const TriTables& tb,
+                            const TetDenseArgs& a, int sm_count, cudaStream_t s);
+// Triangles P1..P6 with the same kernel in the plane (gradient tables with 2 components: [nl][2][nq], [nq][nl][2]).
+cudaError_t tri_dense_launch(int p, int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, int sm_count,
                              cudaStream_t s);
 cudaError_t tet_diagonal_launch(int p, int ncomp, int kind, const TetTables& tb, const TetApplyArgs& a,
                                 double* d, cudaStream_t s);
@@ -283,6 +322,7 @@ struct mfa_form {
   mfa::HexTables hex{};
   mfa::TetTables tet{};
   double* d_tdense = nullptr;    // P3..P6 tables (TetDenseArgs layouts), tdense_nq points
+  mfa::TriTables tri{};          // triangles P1..P3: tables of the thread-per-cell kernel (tri.nq = 0: none)
   int tdense_nq = 0;
   void* d_geom = nullptr;
   int64_t gstride = 0;           // elements per cell of d_geom

@@ -89,6 +89,31 @@ int32_t hex_node_id(const int32_t* cv, int p, int i, int j, int k, int64_t cell,
   return num.get(Key{3, cell, i, j, k});  // interior
 }
 
+// Q_p node (i, j) of a quadrilateral whose local vertex v sits at reference corner (v & 1, v >> 1 & 1).
+int32_t quad_node_id(const int32_t* cv, int p, int i, int j, int64_t cell, Numbering& num) {
+  const bool ei = i == 0 || i == p, ej = j == 0 || j == p;
+  if (ei && ej) return cv[(i == p ? 1 : 0) | (j == p ? 2 : 0)];
+  if (ei || ej) {  // an edge along the free axis
+    const int f = ei ? 1 : 0, fixed_bit = ei ? (i == p ? 1 : 0) : (j == p ? 2 : 0);
+    const int32_t A = cv[fixed_bit], B = cv[fixed_bit | (1 << f)];
+    const int tt = f == 0 ? i : j;
+    return A < B ? num.get(Key{1, A, B, tt, 0}) : num.get(Key{1, B, A, p - tt, 0});
+  }
+  return num.get(Key{3, cell, i, j, 0});
+}
+
+// P_p node with barycentric weights b[3] (sum p) on the triangle's local vertices.
+int32_t tri_node_id(const int32_t* cv, int p, const int b[3], int64_t cell, Numbering& num) {
+  int support[3], ns = 0;
+  for (int s = 0; s < 3; ++s)
+    if (b[s] > 0) support[ns++] = s;
+  if (ns == 1) return cv[support[0]];
+  if (ns == 3) return num.get(Key{3, cell, b[1], b[2], 0});
+  std::pair<int32_t, int> sv[2] = {{cv[support[0]], b[support[0]]}, {cv[support[1]], b[support[1]]}};
+  if (sv[1].first < sv[0].first) std::swap(sv[0], sv[1]);
+  return num.get(Key{1, sv[0].first, sv[1].first, sv[0].second, 0});
+}
+
 // P_p node with barycentric weights b[4] (sum p) on the tet's local vertices.
 int32_t tet_node_id(const int32_t* cv, int p, const int b[4], int64_t cell, Numbering& num) {
   int support[4], ns = 0;
@@ -133,13 +158,15 @@ void tet_local_weights(int p, std::vector<std::array<int, 4>>& out) {
 
 extern "C" int mfa_build_cell_node(int cell_type, int degree, int64_t ncell, const int32_t* cell_vert, int64_t nvert,
                                    int32_t* cell_node, int64_t* nnode) {
-  if ((cell_type != MFA_CELL_HEX8 && cell_type != MFA_CELL_TET4) || ncell < 0 || nvert < 0 || !nnode ||
-      (ncell > 0 && (!cell_vert || !cell_node)))
+  if ((cell_type != MFA_CELL_HEX8 && cell_type != MFA_CELL_TET4 && cell_type != MFA_CELL_TRI3 &&
+       cell_type != MFA_CELL_QUAD4) ||
+      ncell < 0 || nvert < 0 || !nnode || (ncell > 0 && (!cell_vert || !cell_node)))
     return mfa::set_error(MFA_ERR_ARG, "mfa_build_cell_node: bad argument");
-  const bool hex = cell_type == MFA_CELL_HEX8;
-  if ((hex && (degree < 1 || degree > 8)) || (!hex && (degree < 1 || degree > mfa::kTetMaxP)))
+  const bool hex = cell_type == MFA_CELL_HEX8, tensor = hex || cell_type == MFA_CELL_QUAD4;
+  if ((tensor && (degree < 1 || degree > 8)) || (!tensor && (degree < 1 || degree > mfa::kTetMaxP)))
     return mfa::set_error(MFA_ERR_UNSUPPORTED, "mfa_build_cell_node: degree");
-  for (int64_t i = 0; i < ncell * cell_type; ++i)
+  const int nv = mfa::verts_of(cell_type);
+  for (int64_t i = 0; i < ncell * nv; ++i)
     if (cell_vert[i] < 0 || cell_vert[i] >= nvert)
       return mfa::set_error(MFA_ERR_RANGE, "mfa_build_cell_node: vertex index outside [0, nvert)");
   Numbering num((int32_t)nvert);
@@ -151,6 +178,21 @@ extern "C" int mfa_build_cell_node(int cell_type, int degree, int64_t ncell, con
       for (int k = 0; k < n; ++k)
         for (int j = 0; j < n; ++j)
           for (int i = 0; i < n; ++i) cell_node[c * nl + i + n * (j + n * k)] = hex_node_id(cv, p, i, j, k, c, num);
+    }
+  } else if (cell_type == MFA_CELL_QUAD4) {
+    const int n = p + 1, nl = n * n;
+    for (int64_t c = 0; c < ncell; ++c)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) cell_node[c * nl + i + n * j] = quad_node_id(cell_vert + 4 * c, p, i, j, c, num);
+  } else if (cell_type == MFA_CELL_TRI3) {
+    const int nl = mfa::tri_lattice_size(p);
+    for (int64_t c = 0; c < ncell; ++c) {
+      int a = 0;
+      for (int j = 0; j <= p; ++j)
+        for (int i = 0; i <= p - j; ++i, ++a) {
+          const int b[3] = {p - i - j, i, j};
+          cell_node[c * nl + a] = tri_node_id(cell_vert + 3 * c, p, b, c, num);
+        }
     }
   } else {
     std::vector<std::array<int, 4>> w;
@@ -166,14 +208,52 @@ extern "C" int mfa_build_cell_node(int cell_type, int degree, int64_t ncell, con
 
 extern "C" int mfa_node_coords(int cell_type, int degree, int64_t ncell, const int32_t* cell_vert, const double* coords,
                                const int32_t* cell_node, int64_t nnode, double* out) {
-  if ((cell_type != MFA_CELL_HEX8 && cell_type != MFA_CELL_TET4) || ncell < 0 || nnode < 0 ||
-      (ncell > 0 && (!cell_vert || !coords || !cell_node)) || (nnode > 0 && !out))
+  if ((cell_type != MFA_CELL_HEX8 && cell_type != MFA_CELL_TET4 && cell_type != MFA_CELL_TRI3 &&
+       cell_type != MFA_CELL_QUAD4) ||
+      ncell < 0 || nnode < 0 || (ncell > 0 && (!cell_vert || !coords || !cell_node)) || (nnode > 0 && !out))
     return mfa::set_error(MFA_ERR_ARG, "mfa_node_coords: bad argument");
   const int p = degree;
-  const bool hex = cell_type == MFA_CELL_HEX8;
-  if ((hex && (p < 1 || p > 8)) || (!hex && (p < 1 || p > mfa::kTetMaxP)))
+  const bool hex = cell_type == MFA_CELL_HEX8, tensor = hex || cell_type == MFA_CELL_QUAD4;
+  if ((tensor && (p < 1 || p > 8)) || (!tensor && (p < 1 || p > mfa::kTetMaxP)))
     return mfa::set_error(MFA_ERR_UNSUPPORTED, "mfa_node_coords: degree");
   std::fill(out, out + 3 * nnode, 0.0);
+  if (cell_type == MFA_CELL_QUAD4) {
+    const int n = p + 1, nl = n * n;
+    double s[mfa::kMaxN];
+    mfa::gll01(n, s);
+    for (int64_t c = 0; c < ncell; ++c)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          const int32_t node = cell_node[c * nl + i + n * j];
+          if (node < 0 || node >= nnode) return mfa::set_error(MFA_ERR_RANGE, "mfa_node_coords: node index");
+          for (int d = 0; d < 3; ++d) {
+            double x = 0.0;
+            for (int v = 0; v < 4; ++v)
+              x += ((v & 1) ? s[i] : 1.0 - s[i]) * ((v & 2) ? s[j] : 1.0 - s[j]) *
+                   coords[3 * (int64_t)cell_vert[4 * c + v] + d];
+            out[3 * (int64_t)node + d] = x;
+          }
+        }
+    return MFA_OK;
+  }
+  if (cell_type == MFA_CELL_TRI3) {
+    const int nl = mfa::tri_lattice_size(p);
+    for (int64_t c = 0; c < ncell; ++c) {
+      int a = 0;
+      for (int j = 0; j <= p; ++j)
+        for (int i = 0; i <= p - j; ++i, ++a) {
+          const int32_t node = cell_node[c * nl + a];
+          if (node < 0 || node >= nnode) return mfa::set_error(MFA_ERR_RANGE, "mfa_node_coords: node index");
+          const double b[3] = {(double)(p - i - j) / p, (double)i / p, (double)j / p};
+          for (int d = 0; d < 3; ++d) {
+            double x = 0.0;
+            for (int s = 0; s < 3; ++s) x += b[s] * coords[3 * (int64_t)cell_vert[3 * c + s] + d];
+            out[3 * (int64_t)node + d] = x;
+          }
+        }
+    }
+    return MFA_OK;
+  }
   if (hex) {
     const int n = p + 1, nl = n * n * n;
     double s[mfa::kMaxN];

@@ -242,4 +242,58 @@ void tet_basis_pk(int p, const double* xi, double* phi, double* dphi) {
       }
 }
 
+// Collapsed rule on the reference triangle exact to `degree`: (a, b) -> (a (1 - b), b), the Jacobian (1 - b) in the
+// Jacobi weight of the b direction.  pts [nq][2].
+int tri_rule_collapsed(int degree, double* pts, double* w) {
+  const int m = (degree + 2) / 2;
+  double xa[kMaxN], wa[kMaxN], xb[kMaxN], wb[kMaxN];
+  gauss_jacobi01(m, 0, xa, wa);
+  gauss_jacobi01(m, 1, xb, wb);
+  int q = 0;
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i < m; ++i) {
+      pts[2 * q + 0] = xa[i] * (1.0 - xb[j]);
+      pts[2 * q + 1] = xb[j];
+      w[q] = wa[i] * wb[j];
+      ++q;
+    }
+  return q;
+}
+
+int tri_lattice_size(int p) { return (p + 1) * (p + 2) / 2; }
+
+// P_p on the equispaced triangle lattice by Silvester's product formula, nodes (i, j)/p with i fastest; barycentric
+// l0 = 1 - x - y, l1 = x, l2 = y; dphi [n][2].
+void tri_basis_pk(int p, const double* xi, double* phi, double* dphi) {
+  const double l[3] = {1.0 - xi[0] - xi[1], xi[0], xi[1]};
+  static const double gl[3][2] = {{-1, -1}, {1, 0}, {0, 1}};
+  double S[3][kTetMaxP + 1], dS[3][kTetMaxP + 1];
+  for (int s = 0; s < 3; ++s) {
+    S[s][0] = 1.0;
+    dS[s][0] = 0.0;
+    for (int m = 1; m <= p; ++m) {
+      const double f = (p * l[s] - (m - 1)) / m;
+      S[s][m] = S[s][m - 1] * f;
+      dS[s][m] = dS[s][m - 1] * f + S[s][m - 1] * (double)p / m;
+    }
+  }
+  int n = 0;
+  for (int j = 0; j <= p; ++j)
+    for (int i = 0; i <= p - j; ++i) {
+      const int b[3] = {p - i - j, i, j};
+      phi[n] = S[0][b[0]] * S[1][b[1]] * S[2][b[2]];
+      double g[2] = {0.0, 0.0};
+      for (int s = 0; s < 3; ++s) {
+        double prod = dS[s][b[s]];
+        for (int r = 0; r < 3; ++r)
+          if (r != s) prod *= S[r][b[r]];
+        g[0] += prod * gl[s][0];
+        g[1] += prod * gl[s][1];
+      }
+      dphi[2 * n] = g[0];
+      dphi[2 * n + 1] = g[1];
+      ++n;
+    }
+}
+
 }  // namespace mfa

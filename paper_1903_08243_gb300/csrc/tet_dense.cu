@@ -1,4 +1,4 @@
-// Tetrahedral P3..P6 action by dense tabulation, one warp per cell.
+// Simplex action by dense tabulation, one warp per cell: tetrahedra P3..P6 and triangles P1..P6.
 //
 // The paper's tet kernels (Listing 2) loop over quadrature points and local
 // dofs with tabulated basis values; from P3 on a cell has 20-84 dofs and
@@ -21,16 +21,17 @@ constexpr int kWarps = 8;  // cells (warps) per block
 
 template <int NL, int NC, int KIND>
 struct DenseShape {
-  static constexpr bool kVector = NC == 3;
-  // staged per point: value term and reference flux of each component
+  // staged per point: value term and reference flux (up to 3 directions) of each component
   static constexpr int S = 4 * NC;
   static constexpr int R = (NL + 31) / 32;  // dofs per lane
   static constexpr int SMEM_WARP = 2 * NL * NC + 32 * S;  // doubles: x (and the coefficient), stage
 };
 
-template <int NL, int NC, int KIND, int LAW, bool COLOUR>
-__global__ void __launch_bounds__(32 * kWarps) tet_dense_kernel(const TetDenseArgs a) {
+// DIM = 3: tetrahedra (4 vertices); DIM = 2: triangles in the plane (3 vertices, plane strain for NC = 2).
+template <int DIM, int NL, int NC, int KIND, int LAW, bool COLOUR>
+__global__ void __launch_bounds__(32 * kWarps) simplex_dense_kernel(const TetDenseArgs a) {
   using SH = DenseShape<NL, NC, KIND>;
+  constexpr int NV = DIM + 1;
   constexpr bool kValue = KIND == MFA_FORM_MASS || KIND == MFA_FORM_HELMHOLTZ || KIND == MFA_FORM_HYPER_RES;
   constexpr bool kGrad = KIND != MFA_FORM_MASS;
   constexpr bool kJac = KIND == MFA_FORM_HYPER_JAC;
@@ -43,19 +44,20 @@ __global__ void __launch_bounds__(32 * kWarps) tet_dense_kernel(const TetDenseAr
   const double bb[3] = {a.b0, a.b1, a.b2};
   for (int64_t idx = blockIdx.x * (int64_t)kWarps + wid; idx < a.count; idx += (int64_t)gridDim.x * kWarps) {
     const int64_t cell = a.cell_list ? (int64_t)__ldg(a.cell_list + idx) : idx;
-    // affine geometry (every lane, broadcast loads)
-    double J[3][3];
+    // affine geometry (every lane, broadcast loads), embedded in 3x3 with J_zz = 1 in the plane
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     {
-      const int32_t v0 = __ldg(a.cell_vert + 4 * cell);
+      const int32_t v0 = __ldg(a.cell_vert + NV * cell);
       double X0[3];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) X0[d] = __ldg(a.coords + 3 * (int64_t)v0 + d);
+      for (int d = 0; d < DIM; ++d) X0[d] = __ldg(a.coords + 3 * (int64_t)v0 + d);
 #pragma unroll
-      for (int e = 0; e < 3; ++e) {
-        const int32_t ve = __ldg(a.cell_vert + 4 * cell + e + 1);
+      for (int e = 0; e < DIM; ++e) {
+        const int32_t ve = __ldg(a.cell_vert + NV * cell + e + 1);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) J[d][e] = __ldg(a.coords + 3 * (int64_t)ve + d) - X0[d];
+        for (int d = 0; d < DIM; ++d) J[d][e] = __ldg(a.coords + 3 * (int64_t)ve + d) - X0[d];
       }
+      if constexpr (DIM == 2) J[2][2] = 1.0;
     }
     double cof[3][3];
     const double det = det3(J, cof);
@@ -111,26 +113,23 @@ __global__ void __launch_bounds__(32 * kWarps) tet_dense_kernel(const TetDenseAr
 #pragma unroll 4
         for (int al = 0; al < NL; ++al) {
           const double ph = kValue && KIND != MFA_FORM_HYPER_RES ? __ldg(a.phi_aq + (int64_t)al * nq + q) : 0.0;
-          double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+          double d[3] = {0.0, 0.0, 0.0};
           if constexpr (kGrad) {
-            d0 = __ldg(a.dphi_aeq + ((int64_t)al * 3 + 0) * nq + q);
-            d1 = __ldg(a.dphi_aeq + ((int64_t)al * 3 + 1) * nq + q);
-            d2 = __ldg(a.dphi_aeq + ((int64_t)al * 3 + 2) * nq + q);
+#pragma unroll
+            for (int e = 0; e < DIM; ++e) d[e] = __ldg(a.dphi_aeq + ((int64_t)al * DIM + e) * nq + q);
           }
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
             const double xv = xl[al * NC + c];
             if constexpr (kValue && KIND != MFA_FORM_HYPER_RES) u[c] = fma(ph, xv, u[c]);
             if constexpr (kGrad) {
-              g[c][0] = fma(d0, xv, g[c][0]);
-              g[c][1] = fma(d1, xv, g[c][1]);
-              g[c][2] = fma(d2, xv, g[c][2]);
+#pragma unroll
+              for (int e = 0; e < DIM; ++e) g[c][e] = fma(d[e], xv, g[c][e]);
             }
             if constexpr (kJac) {
               const double uv = ul[al * NC + c];
-              gk[c][0] = fma(d0, uv, gk[c][0]);
-              gk[c][1] = fma(d1, uv, gk[c][1]);
-              gk[c][2] = fma(d2, uv, gk[c][2]);
+#pragma unroll
+              for (int e = 0; e < DIM; ++e) gk[c][e] = fma(d[e], uv, gk[c][e]);
             }
           }
         }
@@ -142,23 +141,23 @@ __global__ void __launch_bounds__(32 * kWarps) tet_dense_kernel(const TetDenseAr
             if constexpr (KIND != MFA_FORM_LAPLACE) sv[c] = c0 * wd * u[c];
             if constexpr (kGrad) {
 #pragma unroll
-              for (int e = 0; e < 3; ++e) sh[c][e] = wd * (G[e][0] * g[c][0] + G[e][1] * g[c][1] + G[e][2] * g[c][2]);
+              for (int e = 0; e < DIM; ++e) sh[c][e] = wd * (G[e][0] * g[c][0] + G[e][1] * g[c][1] + G[e][2] * g[c][2]);
             }
           }
         } else {
-          double gu[3][3], gc[3][3], f1[3][3];
+          double gu[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, f1[3][3];
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
+          for (int c = 0; c < NC; ++c)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
+            for (int j = 0; j < DIM; ++j) {
               gu[c][j] = g[c][0] * Ji[0][j] + g[c][1] * Ji[1][j] + g[c][2] * Ji[2][j];
               gc[c][j] = kJac ? gk[c][0] * Ji[0][j] + gk[c][1] * Ji[1][j] + gk[c][2] * Ji[2][j] : 0.0;
             }
           ok = physics<KIND, LAW>(gu, gc, a.lambda, a.mu, f1) && ok;
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
+          for (int c = 0; c < NC; ++c) {
 #pragma unroll
-            for (int e = 0; e < 3; ++e) sh[c][e] = wd * (f1[c][0] * Ji[e][0] + f1[c][1] * Ji[e][1] + f1[c][2] * Ji[e][2]);
+            for (int e = 0; e < DIM; ++e) sh[c][e] = wd * (f1[c][0] * Ji[e][0] + f1[c][1] * Ji[e][1] + f1[c][2] * Ji[e][2]);
             if constexpr (KIND == MFA_FORM_HYPER_RES) sv[c] = -bb[c] * wd;
           }
         }
@@ -178,24 +177,22 @@ __global__ void __launch_bounds__(32 * kWarps) tet_dense_kernel(const TetDenseAr
       for (int r = 0; r < SH::R; ++r) {
         const int al = lane + 32 * r;
         if (al < NL) {
-          for (int t = 0; t < nqc; ++t) {
-            const int64_t qa = (int64_t)(q0 + t) * NL + al;
-            const double* sp = st + t * SH::S;
+          for (int tq = 0; tq < nqc; ++tq) {
+            const int64_t qa = (int64_t)(q0 + tq) * NL + al;
+            const double* sp = st + tq * SH::S;
             const double ph = kValue ? __ldg(a.phi_qa + qa) : 0.0;
-            double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+            double d[3] = {0.0, 0.0, 0.0};
             if constexpr (kGrad) {
-              d0 = __ldg(a.dphi_qae + 3 * qa + 0);
-              d1 = __ldg(a.dphi_qae + 3 * qa + 1);
-              d2 = __ldg(a.dphi_qae + 3 * qa + 2);
+#pragma unroll
+              for (int e = 0; e < DIM; ++e) d[e] = __ldg(a.dphi_qae + DIM * qa + e);
             }
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
               double s = acc[r][c];
               if constexpr (kValue) s = fma(ph, sp[4 * c + 0], s);
               if constexpr (kGrad) {
-                s = fma(d0, sp[4 * c + 1], s);
-                s = fma(d1, sp[4 * c + 2], s);
-                s = fma(d2, sp[4 * c + 3], s);
+#pragma unroll
+                for (int e = 0; e < DIM; ++e) s = fma(d[e], sp[4 * c + 1 + e], s);
               }
               acc[r][c] = s;
             }
@@ -223,10 +220,10 @@ __global__ void __launch_bounds__(32 * kWarps) tet_dense_kernel(const TetDenseAr
   }
 }
 
-template <int NL, int NC, int KIND, int LAW, bool COLOUR>
+template <int DIM, int NL, int NC, int KIND, int LAW, bool COLOUR>
 cudaError_t launch(const TetDenseArgs& a, int sm_count, cudaStream_t s) {
   if (a.count == 0) return cudaSuccess;
-  auto kern = tet_dense_kernel<NL, NC, KIND, LAW, COLOUR>;
+  auto kern = simplex_dense_kernel<DIM, NL, NC, KIND, LAW, COLOUR>;
   constexpr int smem = kWarps * DenseShape<NL, NC, KIND>::SMEM_WARP * (int)sizeof(double);
   static int bps = -1;
   if (bps < 0) {
@@ -244,31 +241,33 @@ cudaError_t launch(const TetDenseArgs& a, int sm_count, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int NL, int NC, int KIND, int LAW>
+template <int DIM, int NL, int NC, int KIND, int LAW>
 cudaError_t launch2(bool colour, const TetDenseArgs& a, int sm_count, cudaStream_t s) {
-  return colour ? launch<NL, NC, KIND, LAW, true>(a, sm_count, s) : launch<NL, NC, KIND, LAW, false>(a, sm_count, s);
+  return colour ? launch<DIM, NL, NC, KIND, LAW, true>(a, sm_count, s)
+                : launch<DIM, NL, NC, KIND, LAW, false>(a, sm_count, s);
 }
 
-template <int NL>
+template <int DIM, int NL>
 cudaError_t by_form(int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, int sm_count, cudaStream_t s) {
   const bool nh = law == MFA_LAW_NEOHOOKE;
   if (ncomp == 1) {
     switch (kind) {
-      case MFA_FORM_MASS: return launch2<NL, 1, MFA_FORM_MASS, 0>(colour, a, sm_count, s);
-      case MFA_FORM_LAPLACE: return launch2<NL, 1, MFA_FORM_LAPLACE, 0>(colour, a, sm_count, s);
-      case MFA_FORM_HELMHOLTZ: return launch2<NL, 1, MFA_FORM_HELMHOLTZ, 0>(colour, a, sm_count, s);
+      case MFA_FORM_MASS: return launch2<DIM, NL, 1, MFA_FORM_MASS, 0>(colour, a, sm_count, s);
+      case MFA_FORM_LAPLACE: return launch2<DIM, NL, 1, MFA_FORM_LAPLACE, 0>(colour, a, sm_count, s);
+      case MFA_FORM_HELMHOLTZ: return launch2<DIM, NL, 1, MFA_FORM_HELMHOLTZ, 0>(colour, a, sm_count, s);
     }
     return cudaErrorInvalidValue;
   }
+  if (ncomp != DIM) return cudaErrorInvalidValue;
   switch (kind) {
-    case MFA_FORM_LAPLACE: return launch2<NL, 3, MFA_FORM_LAPLACE, 0>(colour, a, sm_count, s);
-    case MFA_FORM_ELASTICITY: return launch2<NL, 3, MFA_FORM_ELASTICITY, 0>(colour, a, sm_count, s);
+    case MFA_FORM_LAPLACE: return launch2<DIM, NL, DIM, MFA_FORM_LAPLACE, 0>(colour, a, sm_count, s);
+    case MFA_FORM_ELASTICITY: return launch2<DIM, NL, DIM, MFA_FORM_ELASTICITY, 0>(colour, a, sm_count, s);
     case MFA_FORM_HYPER_RES:
-      return nh ? launch2<NL, 3, MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(colour, a, sm_count, s)
-                : launch2<NL, 3, MFA_FORM_HYPER_RES, MFA_LAW_SVK>(colour, a, sm_count, s);
+      return nh ? launch2<DIM, NL, DIM, MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(colour, a, sm_count, s)
+                : launch2<DIM, NL, DIM, MFA_FORM_HYPER_RES, MFA_LAW_SVK>(colour, a, sm_count, s);
     case MFA_FORM_HYPER_JAC:
-      return nh ? launch2<NL, 3, MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(colour, a, sm_count, s)
-                : launch2<NL, 3, MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(colour, a, sm_count, s);
+      return nh ? launch2<DIM, NL, DIM, MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(colour, a, sm_count, s)
+                : launch2<DIM, NL, DIM, MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(colour, a, sm_count, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -278,10 +277,23 @@ cudaError_t by_form(int ncomp, int kind, int law, bool colour, const TetDenseArg
 cudaError_t tet_dense_launch(int p, int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, int sm_count,
                              cudaStream_t s) {
   switch (p) {
-    case 3: return by_form<20>(ncomp, kind, law, colour, a, sm_count, s);
-    case 4: return by_form<35>(ncomp, kind, law, colour, a, sm_count, s);
-    case 5: return by_form<56>(ncomp, kind, law, colour, a, sm_count, s);
-    case 6: return by_form<84>(ncomp, kind, law, colour, a, sm_count, s);
+    case 3: return by_form<3, 20>(ncomp, kind, law, colour, a, sm_count, s);
+    case 4: return by_form<3, 35>(ncomp, kind, law, colour, a, sm_count, s);
+    case 5: return by_form<3, 56>(ncomp, kind, law, colour, a, sm_count, s);
+    case 6: return by_form<3, 84>(ncomp, kind, law, colour, a, sm_count, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t tri_dense_launch(int p, int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, int sm_count,
+                             cudaStream_t s) {
+  switch (p) {
+    case 1: return by_form<2, 3>(ncomp, kind, law, colour, a, sm_count, s);
+    case 2: return by_form<2, 6>(ncomp, kind, law, colour, a, sm_count, s);
+    case 3: return by_form<2, 10>(ncomp, kind, law, colour, a, sm_count, s);
+    case 4: return by_form<2, 15>(ncomp, kind, law, colour, a, sm_count, s);
+    case 5: return by_form<2, 21>(ncomp, kind, law, colour, a, sm_count, s);
+    case 6: return by_form<2, 28>(ncomp, kind, law, colour, a, sm_count, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -61,9 +61,36 @@ def tet_case(nx, p, ncomp=1, perturb=0.0, seed=0, shuffle=False):
                 nodes=nodes)
 
 
+def quad_case(nx, p, ncomp=1, perturb=0.1, seed=1):
+    """Perturbed unit-square quads with the structured Q_p map; node positions for vector inputs."""
+    mesh = fi.quad_mesh(nx, perturb=perturb, seed=seed)
+    cn, nnode = fi.quad_node_map(nx, p)
+    nodes = None
+    if ncomp == 2:
+        from tests import exact
+
+        n = p + 1
+        s = exact.gll_nodes_np(n)
+        nodes = np.zeros((nnode, 3))
+        X = mesh.coords[mesh.cell_vert]
+        for j in range(n):
+            for i in range(n):
+                w = np.array([(s[i] if v & 1 else 1 - s[i]) * (s[j] if v & 2 else 1 - s[j]) for v in range(4)])
+                nodes[cn[:, i + n * j]] = np.einsum("v,cvd->cd", w, X)
+    return dict(cell_type=40, coords=mesh.coords, cell_vert=mesh.cell_vert, degree=p, cell_node=cn, nnode=nnode,
+                ncomp=ncomp, nodes=nodes)
+
+
+def tri_case(nx, p, ncomp=1, perturb=0.15, seed=2):
+    mesh = fi.tri_mesh(nx, perturb=perturb, seed=seed)
+    cn, nnode, node_coords = fi.tri_node_map(mesh.cell_vert, mesh.nvert, p)
+    return dict(cell_type=3, coords=mesh.coords, cell_vert=mesh.cell_vert, degree=p, cell_node=cn, nnode=nnode,
+                ncomp=ncomp, nodes=node_coords(mesh.coords))
+
+
 def oracle_problem(case, kind, qdeg=None, **kw):
     if qdeg is None:
-        if case["cell_type"] == 8:
+        if case["cell_type"] in (8, 40):
             qdeg = case["degree"] + 1
         else:
             p = case["degree"]

@@ -138,3 +138,39 @@ def test_map_builder_errors():
     with pytest.raises(mfa.MfaError) as e:
         mfa.mfa_build_cell_node(mfa.MFA_CELL_TET4, 2, cv, 3)  # vertex 3 outside [0, 3)
     assert e.value.code == mfa.MFA_ERR_RANGE
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_planar_maps_equal_the_generator_maps(p):
+    q = fi.quad_mesh(4)
+    cn, nn = mfa.mfa_build_cell_node(mfa.MFA_CELL_QUAD4, p, q.cell_vert, q.nvert)
+    cn_ref, nn_ref = fi.quad_node_map(4, p)
+    assert nn == nn_ref and same_partition(cn, cn_ref)
+    t = fi.tri_mesh(4)
+    cn, nn = mfa.mfa_build_cell_node(mfa.MFA_CELL_TRI3, p, t.cell_vert, t.nvert)
+    cn_ref, nn_ref, _ = fi.tri_node_map(t.cell_vert, t.nvert, p)
+    assert nn == nn_ref and same_partition(cn, cn_ref)
+
+
+def test_quad_map_conforming_under_rotated_local_orders():
+    p = 3
+    q = fi.quad_mesh(3, perturb=0.1, seed=2)
+    rots = [[0, 1, 2, 3], [1, 3, 0, 2], [3, 2, 1, 0], [2, 0, 3, 1]]  # the 4 rotations of the square's corners
+    rng = np.random.default_rng(1)
+    cv = np.array([c[rots[rng.integers(4)]] for c in q.cell_vert], dtype=np.int32)
+    cn, nn = mfa.mfa_build_cell_node(mfa.MFA_CELL_QUAD4, p, cv, q.nvert)
+    n = p + 1
+    s = exact.gll_nodes_np(n)
+    seen = {}
+    for c in range(cv.shape[0]):
+        X = q.coords[cv[c]]
+        for j in range(n):
+            for i in range(n):
+                w = np.array([(s[i] if v & 1 else 1 - s[i]) * (s[j] if v & 2 else 1 - s[j]) for v in range(4)])
+                pos = w @ X
+                node = cn[c, i + n * j]
+                if node in seen:
+                    np.testing.assert_allclose(seen[node], pos, atol=1e-13)
+                else:
+                    seen[node] = pos
+    assert len(seen) == nn == (3 * p + 1) ** 2
