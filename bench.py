@@ -537,7 +537,7 @@ def gpu_arm(args, world, rank, local):
         if dom["case"]["cell_type"] == 40:
             kname = "quad_apply_kernel<%s>"
         elif dom["case"]["cell_type"] == 3:
-            kname = "simplex_dense_kernel<DIM=2, %s>"
+            kname = ("tri_cell_kernel<%s>" if dom["cfg"].variant == 5 else "simplex_dense_kernel<DIM=2, %s>")
         kh, kname = None, kname % dom["case"]["name"]
     traffic = NCU_TRAFFIC.get((kh, dom["case"]["name"]))
     if args.workload == "hex" and args.precision != "fp64":

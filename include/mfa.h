@@ -229,10 +229,13 @@ MFA_API int mfa_form_set_dirichlet(mfa_form *form, const int32_t *dofs, int64_t 
  *                                from global memory (FP32/BF16 hex);
  *             MFA_VARIANT_LINE_STAGED as LINE with the factors staged in shared
  *                                memory by bulk copies (FP32/BF16 hex);
- *             MFA_VARIANT_CELL   one thread per cell (P1/P2 tets);
- *             MFA_VARIANT_CELL_WARP one warp per cell, dense tabulated basis (P3..P6 tets).
- *  - cells_per_block: cells one thread block processes together (tets:
- *    threads per block); 0 in mfa_form_set_config = the variant's default.
+ *             MFA_VARIANT_CELL   one thread per cell (P1/P2 tets; P1..P4 triangles
+ *                                whose rule has at most 25 points, but not the
+ *                                P4 hyperelastic Jacobian action);
+ *             MFA_VARIANT_CELL_WARP one warp per cell, dense tabulated basis (P3..P6 tets,
+ *                                P1..P6 triangles).
+ *  - cells_per_block: cells one thread block processes together (one thread
+ *    per cell: threads per block); 0 in mfa_form_set_config = the variant's default.
  *  - scatter: MFA_SCATTER_ATOMIC, or (FP64 only) MFA_SCATTER_COLOUR or MFA_SCATTER_WARP.
  *  - geometry: stored factors or on-the-fly (the FP64 scalar point kernel; a
  *    form created with on-the-fly geometry has no stored factors to switch to).

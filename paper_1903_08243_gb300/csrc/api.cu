@@ -274,15 +274,30 @@ static int tet_dense_tables(mfa_form* f, int deg) {
 }
 
 // Triangles P1..P6: dense tables for the warp-per-cell kernel, gradients with 2 components.
-int tri_tables(mfa_form* f) {
-  const int p = f->space->degree, kind = f->p.kind, nl = f->space->nloc;
+// Exactness degree of the triangle rule of a form: the integrand's degree on
+// affine cells where it is a polynomial, else the requested (or default) degree.
+int tri_rule_degree(const mfa_form* f) {
+  const int p = f->space->degree, kind = f->p.kind;
   int qdeg = f->p.qdeg;
   if (qdeg <= 0) qdeg = (kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC) ? (p > 2 ? 2 * p : 4) : 2 * p;
   int poly = -1;  // integrand degree on affine cells (-1: not polynomial)
   if (kind == MFA_FORM_MASS || kind == MFA_FORM_HELMHOLTZ) poly = 2 * p;
   if (kind == MFA_FORM_LAPLACE || kind == MFA_FORM_ELASTICITY) poly = 2 * (p - 1);
   if ((kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC) && f->p.law == MFA_LAW_SVK) poly = 4 * (p - 1);
-  const int deg = (poly >= 0 && poly <= qdeg) ? poly : qdeg;
+  return (poly >= 0 && poly <= qdeg) ? poly : qdeg;
+}
+
+// The thread-per-cell triangle kernel covers P1..P4 with at most 25 points (P4 Jacobian action: no).
+bool tri_cell_ok(const mfa_form* f) {
+  if (f->space->mesh->cell_type != MFA_CELL_TRI3 || f->space->degree > 4) return false;
+  if (f->space->degree == 4 && f->p.kind == MFA_FORM_HYPER_JAC) return false;  // register-bound: one warp per cell
+  const int m = (tri_rule_degree(f) + 2) / 2;
+  return m * m <= mfa::kTriMaxQ;
+}
+
+int tri_tables(mfa_form* f) {
+  const int p = f->space->degree, nl = f->space->nloc;
+  const int deg = tri_rule_degree(f);
   const int m = (deg + 2) / 2;
   if (m > mfa::kMaxN) return fail(MFA_ERR_UNSUPPORTED, "triangle rule of degree %d", deg);
   const int nq = m * m;
@@ -308,6 +323,17 @@ int tri_tables(mfa_form* f) {
       }
     }
   for (int q = 0; q < nq; ++q) wq[q] = w[q];
+  if (tri_cell_ok(f)) {  // the same tables as a kernel parameter of the thread-per-cell kernel
+    f->tri.nq = nq;
+    for (int q = 0; q < nq; ++q) {
+      f->tri.w[q] = w[q];
+      for (int a = 0; a < nl; ++a) {
+        f->tri.phi[q * mfa::kTriMaxNl + a] = phi[(size_t)q * nl + a];
+        for (int e = 0; e < 2; ++e)
+          f->tri.dphi[(q * mfa::kTriMaxNl + a) * 2 + e] = dphi[((size_t)q * nl + a) * 2 + e];
+      }
+    }
+  }
   int rc = cuda_alloc((void**)&f->d_tdense, sizeof(double) * buf.size(), "triangle tables");
   if (!rc && cudaMemcpy(f->d_tdense, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     rc = fail(MFA_ERR_CUDA, "triangle tables: upload");
@@ -443,7 +469,11 @@ static int apply_form_raw(mfa_form* f, const double* x, double* y, cudaStream_t 
       a.b1 = f->p.b[1];
       a.b2 = 0.0;
       a.err = ctx->d_err;
-      e = mfa::tri_dense_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, a, ctx->sm_count, stream);
+      if (f->launch.variant == MFA_VARIANT_CELL)
+        e = mfa::tri_cell_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, f->launch.cb ? f->launch.cb : 128,
+                                 f->tri, a, ctx->sm_count, stream);
+      else
+        e = mfa::tri_dense_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, a, ctx->sm_count, stream);
     } else if (sp->mesh->cell_type == MFA_CELL_HEX8 && sp->ncomp == 3) {
       mfa::HexVecArgs a{x, y, sp->d_cell_node, static_cast<const double*>(f->d_geom), f->d_coef, list, count,
                         f->gstride, f->p.lambda, f->p.mu, f->p.b[0], f->p.b[1], f->p.b[2], ctx->d_err};
@@ -684,6 +714,7 @@ static int cb_options(const mfa_form* f, int variant, int* out) {
     return 1;
   }
   if (sp->mesh->cell_type == MFA_CELL_TRI3) {
+    if (variant == MFA_VARIANT_CELL) return tri_cell_ok(f) ? mfa::tet_cb_options(out) : 0;  // threads per block
     if (variant != MFA_VARIANT_CELL_WARP) return 0;
     out[0] = 8;  // one warp per cell, 8 warps per block
     return 1;
@@ -718,6 +749,7 @@ static std::vector<mfa_launch_config> form_configs(const mfa_form* f) {
   std::vector<int> variants;
   const int ctype = f->space->mesh->cell_type;
   if (ctype == MFA_CELL_QUAD4) variants = {MFA_VARIANT_POINT};
+  else if (ctype == MFA_CELL_TRI3 && tri_cell_ok(f)) variants = {MFA_VARIANT_CELL, MFA_VARIANT_CELL_WARP};
   else if (ctype == MFA_CELL_TRI3) variants = {MFA_VARIANT_CELL_WARP};
   else if (!hex) variants = {f->space->degree >= 3 ? MFA_VARIANT_CELL_WARP : MFA_VARIANT_CELL};
   else if (f->p.precision == MFA_PREC_FP64) variants = {MFA_VARIANT_POINT, MFA_VARIANT_EVEN_ODD};
@@ -737,8 +769,8 @@ static std::vector<mfa_launch_config> form_configs(const mfa_form* f) {
         if (geo == 1 && !(otf_ok && v == MFA_VARIANT_POINT && i == 0)) continue;
         // warp-aggregated scatter: tets, and the scalar point kernel with p+1 points at its default cells per block
         const bool warp_ok = colour_ok && geo == 0 &&
-                             (v == MFA_VARIANT_CELL || (v == MFA_VARIANT_POINT && f->space->ncomp == 1 && f->nq1 == n &&
-                                                        i == 0));
+                             ((v == MFA_VARIANT_CELL && ctype == MFA_CELL_TET4) ||
+                              (v == MFA_VARIANT_POINT && hex && f->space->ncomp == 1 && f->nq1 == n && i == 0));
         const int scatters[3] = {MFA_SCATTER_ATOMIC, MFA_SCATTER_COLOUR, MFA_SCATTER_WARP};
         for (int sc = 0; sc < (colour_ok ? (warp_ok ? 3 : 2) : 1); ++sc) {
           mfa_launch_config c{};
@@ -797,7 +829,7 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
     const bool hyper = kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC;
     bool ok = (sp->ncomp == 1 && kind <= MFA_FORM_HELMHOLTZ) ||
               (sp->ncomp == 2 && kind >= MFA_FORM_LAPLACE && kind != MFA_FORM_HELMHOLTZ);
-    ok = ok && prm->precision == MFA_PREC_FP64 && prm->scatter != MFA_SCATTER_WARP && prm->cells_per_block == 0;
+    ok = ok && prm->precision == MFA_PREC_FP64 && prm->scatter != MFA_SCATTER_WARP;
     if (ct == MFA_CELL_QUAD4) ok = ok && (nq == n || (nq == n + 1 && n + 1 <= mfa::kMaxN) ||
                                           (hyper && nq == 2 * n && 2 * n <= mfa::kMaxN));
     if (!ok)
@@ -833,6 +865,7 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
   f->p = *prm;
   f->scatter = prm->scatter == MFA_SCATTER_AUTO ? MFA_SCATTER_ATOMIC : prm->scatter;
   f->launch.variant = default_variant(sp, prm->qdeg > 0 ? prm->qdeg : sp->degree + 1, prm->precision);
+  if (tri_cell_ok(f)) f->launch.variant = MFA_VARIANT_CELL;
   int rc = MFA_OK;
   if (f->scatter == MFA_SCATTER_WARP) {
     // the warp-aggregated scatter is compiled for the point kernel (scalar hex, p+1 points) and the tet kernels
@@ -998,6 +1031,7 @@ int mfa_form_set_config(mfa_form* f, const mfa_launch_config* cfg) {
   const mfa_space* sp = f->space;
   if (want.variant == MFA_VARIANT_AUTO) {
     want.variant = default_variant(sp, f->nq1, f->p.precision);
+    if (tri_cell_ok(f)) want.variant = MFA_VARIANT_CELL;
     if (sp->mesh->cell_type == MFA_CELL_HEX8 && !f->d_geom) want.variant = MFA_VARIANT_POINT;
   }
   if (want.cells_per_block == 0) {

@@ -219,8 +219,8 @@ struct TetDenseArgs {
 };
 cudaError_t tet_dense_launch(int p, int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, int sm_count,
                              cudaStream_t s);
-// Triangles P1..P3, one thread per cell (tri_kernels.cu): tables as a kernel parameter, at most 16 points.
-constexpr int kTriMaxNl = 10, kTriMaxQ = 16;
+// Triangles P1..P4, one thread per cell (tri_kernels.cu): tables as a kernel parameter (9.2 KB), at most 25 points.
+constexpr int kTriMaxNl = 15, kTriMaxQ = 25;
 struct TriTables {
   int nq;
   double w[kTriMaxQ];
@@ -322,7 +322,7 @@ struct mfa_form {
   mfa::HexTables hex{};
   mfa::TetTables tet{};
   double* d_tdense = nullptr;    // P3..P6 tables (TetDenseArgs layouts), tdense_nq points
-  mfa::TriTables tri{};          // triangles P1..P3: tables of the thread-per-cell kernel (tri.nq = 0: none)
+  mfa::TriTables tri{};          // triangles P1..P4: tables of the thread-per-cell kernel (tri.nq = 0: none)
   int tdense_nq = 0;
   void* d_geom = nullptr;
   int64_t gstride = 0;           // elements per cell of d_geom

@@ -1,6 +1,6 @@
 """GPU parity of the planar cells (Table 2's tri and quad columns) against the FP64 oracle: quadrilaterals Q1-Q8
-(sum-factorised, p+1 / p+2 / 2p+2 points) and triangles P1-P6 (dense, one warp per cell), every form; vector forms
-in plane strain."""
+(sum-factorised, p+1 / p+2 / 2p+2 points) and triangles P1-P6 (one thread per cell for P1-P4, one warp per cell for
+every degree), every form; vector forms in plane strain."""
 import numpy as np
 import pytest
 
@@ -65,6 +65,8 @@ def test_quad_scalar(ctx, p, kind, scatter):
     x = fi.uniform_vector(case["nnode"], seed=p)
     f = run_check(ctx, case, kind, x, k2=0.8, scatter=scatter)
     assert f.config().variant == mfa.MFA_VARIANT_POINT
+    # one kernel, atomic or colour scatter (no warp-aggregated one for quads)
+    assert sorted(c.scatter for c in f.configs()) == sorted([mfa.MFA_SCATTER_ATOMIC, mfa.MFA_SCATTER_COLOUR])
 
 
 @pytest.mark.parametrize("p", [1, 3, 6])
@@ -99,7 +101,7 @@ def test_tri_scalar(ctx, p, kind):
     case = tri_case({1: 12, 2: 8, 3: 6, 4: 5, 5: 4, 6: 4}[p], p)
     f = run_check(ctx, case, kind, fi.uniform_vector(case["nnode"], seed=40 + p), k2=0.6,
                   scatter=mfa.MFA_SCATTER_COLOUR if p % 2 else mfa.MFA_SCATTER_ATOMIC)
-    assert f.config().variant == mfa.MFA_VARIANT_CELL_WARP
+    assert f.config().variant == (mfa.MFA_VARIANT_CELL if p <= 4 else mfa.MFA_VARIANT_CELL_WARP)
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 5])
@@ -111,6 +113,46 @@ def test_tri_vector(ctx, p, kind, law):
     if kind == "hyper_res":
         kw["b"] = (0.05, 0.1, 0.0)
     run_check(ctx, case, kind, x, u, **kw)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("kind, law, ncomp", [("mass", 0, 1), ("laplace", 0, 1), ("helmholtz", 0, 1)] +
+                         [(k, law, 2) for k, law in VECTOR])
+def test_tri_every_config(ctx, p, kind, law, ncomp):
+    """P1-P4 have two kernels (one thread per cell, the default, and one warp per cell; the P4 Jacobian action only
+    the second): every configuration the form lists, thread counts and scatters included, gives the oracle's
+    result."""
+    case = tri_case(5, p, ncomp=ncomp, seed=9)
+    if ncomp == 1:
+        u, x = None, fi.uniform_vector(case["nnode"], seed=70 + p)
+        kw = dict(k2=0.6)
+    else:
+        u, x = vec_inputs(case, kind, seed=70 + p)
+        kw = dict(lam=1.2, mu=0.9, law=law, b=(0.05, 0.1, 0.0))
+    okw = dict(kw) if ncomp == 2 and kind == "hyper_res" else {k: v for k, v in kw.items() if k != "b"}
+    ref = oracle_problem(case, kind, ucoef=u if kind == "hyper_jac" else None, **okw).apply(x)
+    form = make_form(ctx, case, kind, **okw)
+    if kind == "hyper_jac":
+        form.set_coefficient(torch.from_numpy(u).cuda())
+    cfgs = form.configs()
+    variants = {c.variant for c in cfgs}
+    if p == 4 and kind == "hyper_jac":
+        assert variants == {mfa.MFA_VARIANT_CELL_WARP}
+    else:
+        assert variants == {mfa.MFA_VARIANT_CELL, mfa.MFA_VARIANT_CELL_WARP}
+        assert {c.cells_per_block for c in cfgs if c.variant == mfa.MFA_VARIANT_CELL} == {32, 64, 128}
+    assert all(c.scatter != mfa.MFA_SCATTER_WARP for c in cfgs)
+    xd = torch.from_numpy(x).cuda()
+    for c in cfgs:
+        form.set_config(c)
+        y = form.apply(xd)
+        ctx.sync()
+        y = y.cpu().numpy()
+        rel = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+        assert rel <= TOL and np.abs(y - ref).max() <= TOL * np.abs(ref).max(), (c.as_dict(), rel)
+    yd = torch.empty_like(xd)
+    best = form.autotune(xd, yd)
+    assert form.config().variant in variants and best is not None
 
 
 @pytest.mark.parametrize("cell, p", [("quad", 3), ("tri", 4)])
