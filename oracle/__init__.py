@@ -42,7 +42,7 @@ class _Problem(ctypes.Structure):
         ("law", ctypes.c_int32),
         ("qdeg", ctypes.c_int32),
         ("equispaced", ctypes.c_int32),
-        ("pad_", ctypes.c_int32),
+        ("nq_rule", ctypes.c_int32),
         ("ncell", ctypes.c_int64),
         ("nvert", ctypes.c_int64),
         ("nnode", ctypes.c_int64),
@@ -54,6 +54,8 @@ class _Problem(ctypes.Structure):
         ("mu", ctypes.c_double),
         ("b", ctypes.c_double * 3),
         ("ucoef", ctypes.c_void_p),
+        ("qpts", ctypes.c_void_p),
+        ("qw", ctypes.c_void_p),
     ]
 
 
@@ -162,7 +164,7 @@ class Problem:
 
     def __init__(self, cell_type, coords, cell_vert, degree, cell_node, nnode, kind, ncomp=1,
                  qdeg=None, k2=1.0, lam=1.0, mu=1.0, law=SVK, b=(0.0, 0.0, 0.0), ucoef=None,
-                 equispaced=False):
+                 equispaced=False, rule="collapsed"):
         self.coords = np.ascontiguousarray(coords, dtype=np.float64)
         self.cell_vert = np.ascontiguousarray(cell_vert, dtype=np.int32)
         self.cell_node = np.ascontiguousarray(cell_node, dtype=np.int32)
@@ -179,6 +181,14 @@ class Problem:
         s.k2, s.lam, s.mu = k2, lam, mu
         s.b[0], s.b[1], s.b[2] = b
         s.ucoef = None if self.ucoef is None else self.ucoef.ctypes.data
+        if rule not in ("collapsed", "symmetric"):
+            raise ValueError("rule must be 'collapsed' or 'symmetric'")
+        if rule == "symmetric" and cell_type in (TET, TRI) and qdeg <= 6:
+            # Table 2's fully symmetric rules up to degree 6 (the collapsed rule above)
+            from oracle import symmetric
+            pts, w = symmetric.rule(3 if cell_type == TET else 2, qdeg)
+            self._qpts, self._qw = np.ascontiguousarray(pts), np.ascontiguousarray(w)
+            s.nq_rule, s.qpts, s.qw = len(w), self._qpts.ctypes.data, self._qw.ctypes.data
         self._s = s
         self.ncomp = ncomp
         self.nnode = nnode

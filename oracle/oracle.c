@@ -439,6 +439,8 @@ static int check_problem(const orc_problem *pb) {
   if (pb->kind >= ORC_ELASTICITY && pb->ncomp != dim) return ORC_EARG;
   if (pb->kind == ORC_HYPER_JAC && !pb->ucoef) return ORC_EARG;
   if (pb->qdeg < 1) return ORC_EARG;
+  if (pb->nq_rule < 0 || (pb->nq_rule > 0 && (!pb->qpts || !pb->qw || (ct != ORC_TET && ct != ORC_TRI))))
+    return ORC_EARG;
   if (pb->ncell < 0 || pb->nvert < 0 || pb->nnode < 0) return ORC_EARG;
   int nl = nloc_of(pb);
   for (int64_t c = 0; c < pb->ncell; ++c) {
@@ -461,7 +463,17 @@ static int build_tables(const orc_problem *pb, tables *t) {
   t->nc = pb->ncomp;
   t->dim = dim_of(pb->cell_type);
   double *pts;
-  if (pb->cell_type == ORC_TRI || pb->cell_type == ORC_QUAD) {
+  if (pb->nq_rule > 0) {
+    /* an explicit simplex rule (the symmetric rules of Table 2), points stored with zero padding */
+    t->nq = pb->nq_rule;
+    pts = calloc(3 * (size_t)t->nq, sizeof(double));
+    t->w = malloc(sizeof(double) * t->nq);
+    if (!pts || !t->w) { free(pts); free_tables(t); return ORC_EMEM; }
+    for (int q = 0; q < t->nq; ++q) {
+      for (int e = 0; e < t->dim; ++e) pts[3 * q + e] = pb->qpts[(size_t)q * t->dim + e];
+      t->w[q] = pb->qw[q];
+    }
+  } else if (pb->cell_type == ORC_TRI || pb->cell_type == ORC_QUAD) {
     /* points stored with a zero z coordinate */
     int m = pb->cell_type == ORC_TRI ? (pb->qdeg + 2) / 2 : pb->qdeg;
     if (m > 64) return ORC_EARG;

@@ -45,7 +45,8 @@ typedef struct {
   int32_t law;         /* ORC_SVK or ORC_NEOHOOKE (hyperelastic forms) */
   int32_t qdeg;        /* tet: rule degree; hex: Gauss points per direction */
   int32_t equispaced;  /* hex only: 1 = equispaced nodes, 0 = Gauss-Lobatto */
-  int32_t pad_;
+  int32_t nq_rule;     /* tet/tri: > 0 = integrate with the explicit rule qpts/qw
+                          of nq_rule points instead of the collapsed rule of qdeg */
   int64_t ncell, nvert, nnode;
   const double *coords;      /* [nvert][3] */
   const int32_t *cell_vert;  /* [ncell][4 or 8] */
@@ -53,6 +54,8 @@ typedef struct {
   double k2, lambda, mu;
   double b[3];               /* body force of the hyperelastic residual */
   const double *ucoef;       /* [nnode*3] linearisation point of HYPER_JAC */
+  const double *qpts;        /* nq_rule > 0: reference points [nq_rule][dim] */
+  const double *qw;          /* nq_rule > 0: weights [nq_rule] (they sum to the reference volume) */
 } orc_problem;
 
 /* 1D rules on [0,1].  Return the number of points or a negative error. */
