@@ -102,12 +102,27 @@ enum { MFA_GEOM_STORED = 0, MFA_GEOM_ONTHEFLY = 1 };
  * WARP    atomic adds aggregated within a warp: lanes that add into the same
  *         entry are summed first (FP64 point kernel with p+1 points and tets). */
 enum { MFA_SCATTER_AUTO = 0, MFA_SCATTER_COLOUR = 1, MFA_SCATTER_ATOMIC = 2, MFA_SCATTER_WARP = 3 };
+/* Quadrature on simplices (tetrahedra, triangles).  The integrand of mass and
+ * Helmholtz has degree 2p on an affine cell, Laplace and elasticity 2(p-1),
+ * St Venant-Kirchhoff 4(p-1); call it d.  The rule's degree is d when d <= qdeg
+ * (the integral is then exact), else qdeg.  Rules: Table 2's fully symmetric
+ * ones up to degree 6 (1, 4, 14, 24 points on tets for degree 1, 2, 3-5, 6;
+ * 1, 3, 6, 12 on triangles for degree 1, 2, 3-4, 5-6; see mfa_simplex_rule),
+ * collapsed Gauss-Jacobi products above (m^3 or m^2 points, m = floor(deg/2)+1).
+ * AUTO       the symmetric rule where the integral is exact and its degree is
+ *            <= 6; the collapsed rule otherwise (the neo-Hookean integrand,
+ *            or qdeg < d), so a rule only ever changes rounding;
+ * SYMMETRIC  the symmetric rule whenever the rule's degree is <= 6, whatever
+ *            the integrand (Table 2's choice, also for neo-Hookean).
+ * Hexahedra and quadrilaterals ignore it (Gauss-Legendre products). */
+enum { MFA_RULE_AUTO = 0, MFA_RULE_SYMMETRIC = 1 };
 
 typedef struct {
   int32_t kind;            /* MFA_FORM_*                                               */
   int32_t law;             /* MFA_LAW_* (hyperelastic forms)                           */
-  int32_t qdeg;            /* 0 = default.  Hex: Gauss points per direction (default p+1).
-                              Tet: degree of the rule (default 2p; hyperelastic 4).     */
+  int32_t qdeg;            /* 0 = default.  Hex/quad: Gauss points per direction (default
+                              p+1).  Tet/triangle: largest rule degree (default 2p;
+                              hyperelastic 4 for p <= 2, 2p above); see MFA_RULE_*.     */
   int32_t precision;       /* MFA_PREC_*                                               */
   int32_t scatter;         /* MFA_SCATTER_*                                            */
   int32_t cells_per_block; /* 0 = automatic; else one of the default variant's choices
@@ -116,7 +131,7 @@ typedef struct {
   double lambda, mu;       /* Lame parameters (elasticity, hyperelasticity)             */
   double b[3];             /* body force of the hyperelastic residual                   */
   int32_t geometry;        /* MFA_GEOM_STORED (0, default) or MFA_GEOM_ONTHEFLY          */
-  int32_t reserved;        /* 0                                                          */
+  int32_t rule;            /* MFA_RULE_AUTO (0, default) or MFA_RULE_SYMMETRIC (simplices) */
 } mfa_form_params;
 
 typedef struct {
@@ -183,6 +198,21 @@ MFA_API int mfa_space_get_cell_node(const mfa_space *space, int32_t *cell_node);
  * mfa_space_create with cell_node = NULL calls this. */
 MFA_API int mfa_build_cell_node(int cell_type, int degree, int64_t ncell, const int32_t *cell_vert, int64_t nvert,
                                 int32_t *cell_node, int64_t *nnode);
+/* The fully symmetric quadrature rule of degree `degree` (0..6) on the
+ * reference triangle (cell_type MFA_CELL_TRI3; vertices (0,0), (1,0), (0,1)) or
+ * tetrahedron (MFA_CELL_TET4; vertices 0, e1, e2, e3) that the forms use (host
+ * only).  Table 2 gives the point counts: 1, 3, 6, 12 (triangle) and 1, 4, 14,
+ * 24 (tetrahedron) for degree 0-1, 2, 3-4 / 3-5, 5-6 / 6.  Each rule is a union
+ * of orbits of the barycentric permutations, with one weight per orbit, whose
+ * weights and positions integrate every monomial of the rule's design degree
+ * (triangle 1, 2, 4, 6; tet 1, 2, 5, 6) exactly; among the solutions with
+ * positive weights and every point strictly inside, the one whose smallest
+ * barycentric coordinate is largest.  Derived on first use (0.1-0.3 s for the
+ * 24-point rule), then cached.  Outputs (caller-allocated, max_points entries):
+ * pts [nq][2 or 3], w [nq] (summing to the reference area 1/2 or volume 1/6);
+ * *nq receives the count.  MFA_ERR_ARG on a bad cell type, degree or a
+ * max_points below the count; MFA_ERR_UNSUPPORTED if the derivation fails. */
+MFA_API int mfa_simplex_rule(int cell_type, int degree, int max_points, double *pts, double *w, int *nq);
 /* Physical positions of the nodes, out [nnode][3] (host only): the trilinear
  * (hex) or affine (tet) image of the reference nodes. */
 MFA_API int mfa_node_coords(int cell_type, int degree, int64_t ncell, const int32_t *cell_vert, const double *coords,

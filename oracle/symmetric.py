@@ -17,7 +17,8 @@ with S31 = (a, a, a, 1 - 3a), S22 = (a, a, 1/2 - a, 1/2 - a), S211 = (a, a, b, 1
 S111 = (a, b, 1 - a - b) and all their distinct permutations.  The moment equations are solved in the least
 squares sense by variable projection: for given orbit positions the moment equations are linear in the weights,
 which are solved for by linear least squares, and Levenberg-Marquardt (scipy) moves the positions from seeded
-random starts inside the simplex to a zero of the remaining residual.  A solution is admissible when every
+random starts inside the simplex to a zero of the remaining residual; the rule taken is then polished by
+Gauss-Newton in extended precision (np.longdouble).  A solution is admissible when every
 weight is positive and every point is strictly inside the simplex.  The rule taken is the admissible one whose
 smallest barycentric coordinate is largest (its points are farthest from the boundary).  The only structures
 with more than one admissible solution are the 12-point triangle rule, which has two, and the 3-point triangle
@@ -127,6 +128,60 @@ class MomentSystem:
     def residual(self, x):
         return self.weights(x)[2]
 
+    def polish(self, x, iters=6):
+        """Gauss-Newton on weights and positions together in extended precision (np.longdouble), from a double
+        solution: the rule to well below double rounding, whatever the conditioning of the moment equations.
+        Returns orbit weights and positions."""
+        ld = np.longdouble
+        wo = self.weights(x)[0]
+        u = np.concatenate([wo, x]).astype(ld)
+        norb, const, lin = len(self.struct), self.const.astype(ld), self.lin.astype(ld)
+        exps, mean = self.exps, np.array([ld(m) for m in self.mean])
+        for _ in range(iters):
+            w, xs = u[:norb], u[norb:]
+            bary = const + lin @ xs
+            lam = bary[:, :self.dim]
+            powers = [[lam[:, i] ** int(e) for e in range(exps.max() + 1)] for i in range(self.dim)]
+            vals = np.ones((self.npts, len(mean)), dtype=ld)
+            for q, ex in enumerate(exps):
+                for i in range(self.dim):
+                    vals[:, q] *= powers[i][ex[i]]
+            wp = w[self.owner]
+            r = wp @ vals - mean
+            J = np.zeros((len(mean), len(u)), dtype=ld)
+            for k in range(norb):
+                J[:, k] = vals[self.owner == k].sum(axis=0)
+            for q, ex in enumerate(exps):
+                dm = np.zeros((self.npts, self.dim), dtype=ld)  # d(monomial)/d(lambda_i)
+                for i in range(self.dim):
+                    if ex[i] == 0:
+                        continue
+                    d = ld(int(ex[i])) * powers[i][ex[i] - 1]
+                    for k in range(self.dim):
+                        if k != i:
+                            d = d * powers[k][ex[k]]
+                    dm[:, i] = d
+                J[q, norb:] = np.einsum("p,pi,pij->j", wp, dm, lin[:, :self.dim, :])
+            u = u + _solve_ld(J.T @ J, -(J.T @ r))
+        return u[:norb], u[norb:]
+
+
+def _solve_ld(A, b):
+    """Gaussian elimination with partial pivoting in the arrays' precision (LAPACK has no long double)."""
+    A, b = A.copy(), b.copy()
+    n = len(b)
+    for c in range(n):
+        piv = c + int(np.argmax(np.abs(A[c:, c])))
+        A[[c, piv]], b[[c, piv]] = A[[piv, c]], b[[piv, c]]
+        for r in range(c + 1, n):
+            f = A[r, c] / A[c, c]
+            A[r, c:] -= f * A[c, c:]
+            b[r] -= f * b[c]
+    x = np.zeros_like(b)
+    for r in range(n - 1, -1, -1):
+        x[r] = (b[r] - A[r, r + 1:] @ x[r + 1:]) / A[r, r]
+    return x
+
 
 def random_start(rng, struct):
     """Orbit positions drawn uniformly from the parameter ranges that keep the orbit inside the simplex."""
@@ -151,7 +206,7 @@ def admissible(bary, w, margin=1e-9):
     return bool(w.min() > 0 and bary.min() > margin)
 
 
-def search(dim, degree, starts=None, seed=0, tol=1e-13):
+def search(dim, degree, starts=None, seed=0, tol=1e-13, keep_x=False):
     """Every distinct admissible solution found from `starts` seeded random starts, with the number of starts
     that reached it: a list of (barycentric points, weights, hits), best first by the selection rule."""
     from scipy.optimize import least_squares
@@ -160,7 +215,8 @@ def search(dim, degree, starts=None, seed=0, tol=1e-13):
     if struct is None:
         raise ValueError("no symmetric rule of degree %d on the %d-simplex" % (degree, dim))
     if struct == [CENTROID]:
-        return [(np.full((1, dim + 1), 1.0 / (dim + 1)), np.ones(1), starts)]
+        one = (np.full((1, dim + 1), 1.0 / (dim + 1)), np.ones(1), starts)
+        return [(None,) + one + (None,)] if keep_x else [one]
     system = MomentSystem(dim, degree)
     if starts is None:  # about 1 start in 40 reaches the 24-point rule, 1 in 4 or more the others
         starts = 400 if len(system.owner) == 24 else 200
@@ -181,9 +237,9 @@ def search(dim, degree, starts=None, seed=0, tol=1e-13):
                 item[3] += 1
                 break
         else:
-            found.append([key, bary, w, 1])
+            found.append([key, bary, w, 1, r.x])
     found.sort(key=lambda it: -it[1].min())
-    return [(bary, w, hits) for _, bary, w, hits in found]
+    return [(bary, w, hits) for _, bary, w, hits, _ in found] if not keep_x else found
 
 
 _CACHE = {}
@@ -195,10 +251,15 @@ def rule(dim, degree):
     degree = design_degree(dim, degree)
     key = (dim, degree)
     if key not in _CACHE:
-        sols = search(dim, degree)
+        sols = search(dim, degree, keep_x=True)
         if not sols:
             raise RuntimeError("no admissible symmetric rule of degree %d found" % degree)
-        bary, w, _ = sols[0]
+        bary, w, x = sols[0][1], sols[0][2], sols[0][4]
+        if x is not None and len(x):
+            system = MomentSystem(dim, degree)
+            wo, xs = system.polish(x)
+            bary = (system.const.astype(np.longdouble) + system.lin.astype(np.longdouble) @ xs).astype(float)
+            w = wo[system.owner].astype(float)
         _CACHE[key] = (np.ascontiguousarray(bary[:, 1:]), w / math.factorial(dim))
     pts, w = _CACHE[key]
     return pts.copy(), w.copy()

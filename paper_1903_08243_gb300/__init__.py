@@ -23,6 +23,7 @@ MFA_FORM_ELASTICITY, MFA_FORM_HYPER_RES, MFA_FORM_HYPER_JAC = 3, 4, 5
 MFA_LAW_SVK, MFA_LAW_NEOHOOKE = 0, 1
 MFA_PREC_FP64, MFA_PREC_FP32, MFA_PREC_BF16 = 0, 1, 2
 MFA_GEOM_STORED, MFA_GEOM_ONTHEFLY = 0, 1
+MFA_RULE_AUTO, MFA_RULE_SYMMETRIC = 0, 1
 MFA_SCATTER_AUTO, MFA_SCATTER_COLOUR, MFA_SCATTER_ATOMIC, MFA_SCATTER_WARP = 0, 1, 2, 3
 MFA_PC_NONE, MFA_PC_JACOBI = 0, 1
 MFA_PRECOND_MLP, MFA_PRECOND_LINEAR = 0, 1
@@ -50,7 +51,7 @@ class mfa_form_params(ctypes.Structure):
         ("mu", ctypes.c_double),
         ("b", ctypes.c_double * 3),
         ("geometry", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("rule", ctypes.c_int32),
     ]
 
 
@@ -99,6 +100,7 @@ _SIGS = {
     "mfa_space_get_cell_node": ([_VP, _VP], _I),
     "mfa_build_cell_node": ([_I, _I, _I64, _VP, _I64, _VP, ctypes.POINTER(_I64)], _I),
     "mfa_node_coords": ([_I, _I, _I64, _VP, _VP, _VP, _I64, _VP], _I),
+    "mfa_simplex_rule": ([_I, _I, _I, _VP, _VP, ctypes.POINTER(_I)], _I),
     "mfa_space_ndof": ([_VP, ctypes.POINTER(_I64)], _I),
     "mfa_space_destroy": ([_VP], _I),
     "mfa_form_create": ([_VP, _VP, ctypes.POINTER(mfa_form_params), _PP], _I),
@@ -278,6 +280,14 @@ def mfa_node_coords(cell_type, degree, cell_vert, coords, cell_node, nnode):
     _check(lib().mfa_node_coords(cell_type, degree, cv.shape[0], cv.ctypes.data, X.ctypes.data, cn.ctypes.data,
                                  int(nnode), out.ctypes.data))
     return out
+
+
+def mfa_simplex_rule(cell_type, degree):
+    """The library's fully symmetric simplex rule of `degree`: (points [nq][dim], weights [nq])."""
+    dim = 2 if cell_type == MFA_CELL_TRI3 else 3
+    pts, w, n = np.empty((24, dim)), np.empty(24), ctypes.c_int()
+    _check(lib().mfa_simplex_rule(cell_type, degree, 24, pts.ctypes.data, w.ctypes.data, ctypes.byref(n)))
+    return pts[:n.value].copy(), w[:n.value].copy()
 
 
 def mfa_space_get_cell_node(space, ncell, nloc):
@@ -564,10 +574,10 @@ class Space:
 
 
 def form_params(kind, law=MFA_LAW_SVK, qdeg=0, precision=MFA_PREC_FP64, scatter=MFA_SCATTER_AUTO, k2=1.0,
-                lam=1.0, mu=1.0, b=(0.0, 0.0, 0.0), cells_per_block=0, geometry=MFA_GEOM_STORED):
+                lam=1.0, mu=1.0, b=(0.0, 0.0, 0.0), cells_per_block=0, geometry=MFA_GEOM_STORED, rule=MFA_RULE_AUTO):
     p = mfa_form_params()
     p.kind, p.law, p.qdeg, p.precision, p.scatter = kind, law, qdeg, precision, scatter
-    p.cells_per_block, p.geometry = cells_per_block, geometry
+    p.cells_per_block, p.geometry, p.rule = cells_per_block, geometry, rule
     p.k2, p.lam, p.mu = k2, lam, mu
     p.b[0], p.b[1], p.b[2] = b
     return p

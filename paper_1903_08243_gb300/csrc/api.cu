@@ -150,8 +150,7 @@ void count_work(mfa_form* f) {
       per_cell += 270.0 * q * q * q;
       bytes = ncell * (4.0 * n * n * n + 32.0) + 24.0 * sp->mesh->nvert;
     }
-  } else if (sp->degree == 2 && sp->ncomp == 3 && f->nq == 27 &&
-             (kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC)) {
+  } else if (sp->degree == 2 && sp->ncomp == 3 && (kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC)) {
     // moment kernel: per field 10x3x12 FMA moments + 36 mapped entries (900), per point the
     // gradient(s) (54 each), wd and wd*xi (4), the physics, the moment sums (72); per cell the
     // map back (180), the outputs (720), the body force (60, residual) and the scatter adds (30).
@@ -159,7 +158,7 @@ void count_work(mfa_form* f) {
     const bool res = kind == MFA_FORM_HYPER_RES, svk = f->p.law == MFA_LAW_SVK;
     const double phys = res ? (svk ? 102.0 : 66.0) : (svk ? 243.0 : 202.0);
     const double fields = res ? 1.0 : 2.0;
-    per_cell = 60.0 + 900.0 * fields + 27.0 * (54.0 * fields + 76.0 + phys) + 180.0 + 720.0 + (res ? 60.0 : 0.0) + 30.0;
+    per_cell = 60.0 + 900.0 * fields + f->nq * (54.0 * fields + 76.0 + phys) + 180.0 + 720.0 + (res ? 60.0 : 0.0) + 30.0;
     bytes = ncell * (4.0 * sp->nloc + 16.0) + 24.0 * sp->mesh->nvert;
     if (kind == MFA_FORM_HYPER_JAC) bytes += 8.0 * ndof;
   } else if (sp->degree >= 3) {
@@ -237,13 +236,10 @@ int hex_tables(mfa_form* f) {
 // integrands (neo-Hookean, under-integration) use the conical-product rule
 // of degree qdeg, which defines the result.
 // P3..P6: dense tables in device memory for the warp-per-cell kernel (layouts in TetDenseArgs).
-static int tet_dense_tables(mfa_form* f, int deg) {
+static int tet_dense_tables(mfa_form* f, const std::vector<double>& pts, const std::vector<double>& w) {
   const int p = f->space->degree, nl = f->space->nloc;
-  const int m = (deg + 2) / 2;
-  if (m > mfa::kMaxN) return fail(MFA_ERR_UNSUPPORTED, "tet rule of degree %d", deg);
-  const int nq = m * m * m;
-  std::vector<double> pts(3 * nq), w(nq), phi((size_t)nq * nl), dphi((size_t)nq * nl * 3);
-  if (mfa::tet_rule_collapsed(deg, pts.data(), w.data()) != nq) return fail(MFA_ERR_UNSUPPORTED, "tet rule");
+  const int nq = (int)w.size();
+  std::vector<double> phi((size_t)nq * nl), dphi((size_t)nq * nl * 3);
   for (int q = 0; q < nq; ++q) mfa::tet_basis_pk(p, &pts[3 * q], &phi[(size_t)q * nl], &dphi[(size_t)q * nl * 3]);
   const size_t nb = (size_t)nl * nq;
   std::vector<double> buf(8 * nb + nq);
@@ -274,35 +270,73 @@ static int tet_dense_tables(mfa_form* f, int deg) {
 }
 
 // Triangles P1..P6: dense tables for the warp-per-cell kernel, gradients with 2 components.
-// Exactness degree of the triangle rule of a form: the integrand's degree on
-// affine cells where it is a polynomial, else the requested (or default) degree.
-int tri_rule_degree(const mfa_form* f) {
+// The simplex rule of a form.  The integrand has degree d on affine cells
+// (-1: not a polynomial); the rule's degree is d when d <= qdeg (exact), else
+// qdeg.  MFA_RULE_AUTO takes the symmetric rule where the integral is exact
+// and the degree <= 6, MFA_RULE_SYMMETRIC wherever the degree <= 6; the
+// collapsed product rule otherwise.
+struct SimplexRuleChoice {
+  int degree;
+  bool symmetric;
+};
+
+SimplexRuleChoice simplex_rule_choice(const mfa_form* f) {
   const int p = f->space->degree, kind = f->p.kind;
   int qdeg = f->p.qdeg;
   if (qdeg <= 0) qdeg = (kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC) ? (p > 2 ? 2 * p : 4) : 2 * p;
-  int poly = -1;  // integrand degree on affine cells (-1: not polynomial)
+  int poly = -1;
   if (kind == MFA_FORM_MASS || kind == MFA_FORM_HELMHOLTZ) poly = 2 * p;
   if (kind == MFA_FORM_LAPLACE || kind == MFA_FORM_ELASTICITY) poly = 2 * (p - 1);
   if ((kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC) && f->p.law == MFA_LAW_SVK) poly = 4 * (p - 1);
-  return (poly >= 0 && poly <= qdeg) ? poly : qdeg;
+  const bool exact = poly >= 0 && poly <= qdeg;
+  const int deg = exact ? poly : qdeg;
+  return {deg, deg <= 6 && (exact || f->p.rule == MFA_RULE_SYMMETRIC)};
+}
+
+// Points of the rule simplex_rule_choice picks (without deriving it).
+int simplex_rule_points(const mfa_form* f, int dim) {
+  const SimplexRuleChoice c = simplex_rule_choice(f);
+  if (c.symmetric) {
+    static const int tri[7] = {1, 1, 3, 6, 6, 12, 12}, tet[7] = {1, 1, 4, 14, 14, 14, 24};
+    return dim == 3 ? tet[c.degree] : tri[c.degree];
+  }
+  const int m = c.degree / 2 + 1;
+  return dim == 3 ? m * m * m : m * m;
+}
+
+int simplex_form_rule(const mfa_form* f, int dim, std::vector<double>& pts, std::vector<double>& w) {
+  const SimplexRuleChoice c = simplex_rule_choice(f);
+  if (c.symmetric) {
+    if (mfa::simplex_rule_symmetric(dim, c.degree, pts, w) <= 0)
+      return fail(MFA_ERR_UNSUPPORTED, "symmetric simplex rule of degree %d", c.degree);
+    return MFA_OK;
+  }
+  const int m = c.degree / 2 + 1;
+  if (m > mfa::kMaxN) return fail(MFA_ERR_UNSUPPORTED, "simplex rule of degree %d", c.degree);
+  const int nq = dim == 3 ? m * m * m : m * m;
+  pts.resize((size_t)dim * nq);
+  w.resize(nq);
+  const int got = dim == 3 ? mfa::tet_rule_collapsed(c.degree, pts.data(), w.data())
+                           : mfa::tri_rule_collapsed(c.degree, pts.data(), w.data());
+  if (got != nq) return fail(MFA_ERR_UNSUPPORTED, "simplex rule of degree %d", c.degree);
+  return MFA_OK;
 }
 
 // The thread-per-cell triangle kernel covers P1..P4 with at most 25 points (P4 Jacobian action: no).
 bool tri_cell_ok(const mfa_form* f) {
   if (f->space->mesh->cell_type != MFA_CELL_TRI3 || f->space->degree > 4) return false;
   if (f->space->degree == 4 && f->p.kind == MFA_FORM_HYPER_JAC) return false;  // register-bound: one warp per cell
-  const int m = (tri_rule_degree(f) + 2) / 2;
-  return m * m <= mfa::kTriMaxQ;
+  return simplex_rule_points(f, 2) <= mfa::kTriMaxQ;
 }
 
 int tri_tables(mfa_form* f) {
   const int p = f->space->degree, nl = f->space->nloc;
-  const int deg = tri_rule_degree(f);
-  const int m = (deg + 2) / 2;
-  if (m > mfa::kMaxN) return fail(MFA_ERR_UNSUPPORTED, "triangle rule of degree %d", deg);
-  const int nq = m * m;
-  std::vector<double> pts(2 * nq), w(nq), phi((size_t)nq * nl), dphi((size_t)nq * nl * 2);
-  mfa::tri_rule_collapsed(deg, pts.data(), w.data());
+  std::vector<double> pts, w;
+  const int rrc = simplex_form_rule(f, 2, pts, w);
+  if (rrc) return rrc;
+  const int nq = (int)w.size();
+  if (tri_cell_ok(f) && nq > mfa::kTriMaxQ) return fail(MFA_ERR_UNSUPPORTED, "triangle rule of %d points", nq);
+  std::vector<double> phi((size_t)nq * nl), dphi((size_t)nq * nl * 2);
   for (int q = 0; q < nq; ++q) mfa::tri_basis_pk(p, &pts[2 * q], &phi[(size_t)q * nl], &dphi[(size_t)q * nl * 2]);
   const size_t nb = (size_t)nl * nq;
   std::vector<double> buf(6 * nb + nq);
@@ -345,24 +379,15 @@ int tri_tables(mfa_form* f) {
 
 int tet_tables(mfa_form* f) {
   const int p = f->space->degree, kind = f->p.kind;
-  int qdeg = f->p.qdeg;
-  if (qdeg <= 0) qdeg = (kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC) ? (p > 2 ? 2 * p : 4) : 2 * p;
-  int poly = -1;  // integrand degree on affine cells (-1: not polynomial)
-  if (kind == MFA_FORM_MASS || kind == MFA_FORM_HELMHOLTZ) poly = 2 * p;
-  if (kind == MFA_FORM_LAPLACE || kind == MFA_FORM_ELASTICITY) poly = 2 * (p - 1);
-  if ((kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC) && f->p.law == MFA_LAW_SVK) poly = 4 * (p - 1);
-  if (p >= 3) return tet_dense_tables(f, (poly >= 0 && poly <= qdeg) ? poly : qdeg);
-  double pts[mfa::kTetMaxQ * 3];
-  int nq;
-  if (poly >= 0 && poly <= qdeg && poly <= 2) {
-    nq = mfa::tet_rule_4pt_deg2(pts, f->tet.w);
-  } else {
-    const int deg = (poly >= 0 && poly <= qdeg) ? poly : qdeg;
-    const int m = (deg + 2) / 2;
-    if (m * m * m > mfa::kTetMaxQ) return fail(MFA_ERR_UNSUPPORTED, "tet rule of degree %d needs %d points", deg, m * m * m);
-    nq = mfa::tet_rule_collapsed(deg, pts, f->tet.w);
-    if (nq != 27) return fail(MFA_ERR_UNSUPPORTED, "tet kernels are built for 4- and 27-point rules (got %d)", nq);
-  }
+  std::vector<double> rpts, rw;
+  const int rrc = simplex_form_rule(f, 3, rpts, rw);
+  if (rrc) return rrc;
+  if (p >= 3) return tet_dense_tables(f, rpts, rw);
+  const int nq = (int)rw.size();
+  if (!mfa::tet_rule_compiled(p, f->space->ncomp, kind, nq))
+    return fail(MFA_ERR_UNSUPPORTED, "P%d form %d: no kernel for a rule of %d points", p, kind, nq);
+  const double* pts = rpts.data();
+  for (int q = 0; q < nq; ++q) f->tet.w[q] = rw[q];
   f->tet.nq = nq;
   const int nl = f->space->nloc;
   for (int i = 0; i < nq; ++i) mfa::tet_basis(p, pts + 3 * i, f->tet.phi + i * nl, f->tet.dphi + i * nl * 3);
@@ -810,6 +835,8 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
     return fail(MFA_ERR_ARG, "mfa_form_create: precision %d", prm->precision);
   if (prm->geometry != MFA_GEOM_STORED && prm->geometry != MFA_GEOM_ONTHEFLY)
     return fail(MFA_ERR_ARG, "mfa_form_create: geometry %d", prm->geometry);
+  if (prm->rule != MFA_RULE_AUTO && prm->rule != MFA_RULE_SYMMETRIC)
+    return fail(MFA_ERR_ARG, "mfa_form_create: rule %d", prm->rule);
   if (prm->geometry == MFA_GEOM_ONTHEFLY &&
       (ct != MFA_CELL_HEX8 || sp->ncomp != 1 || kind > MFA_FORM_HELMHOLTZ || prm->precision != MFA_PREC_FP64 ||
        (prm->qdeg > 0 && prm->qdeg != sp->degree + 1) || prm->scatter == MFA_SCATTER_WARP ||

@@ -23,8 +23,11 @@ void lagrange_matrix(int n, const double* nodes, int m, const double* pts, doubl
 // Collocation derivative on `pts` (m points): D[q*m + r] = l_r'(pts[q]).
 void collocation_derivative(int m, const double* pts, double* D);
 // Reference-tet rules.  Returns the number of points.
-int tet_rule_4pt_deg2(double* pts, double* w);  // degree-2, symmetric 4-point
 int tet_rule_collapsed(int degree, double* pts, double* w);  // conical product, m = ceil((deg+1)/2)
+// Table 2's fully symmetric rule of degree <= 6 on the reference triangle (dim 2)
+// or tetrahedron (dim 3): pts [nq][dim], w [nq]; returns nq, 0 above degree 6,
+// -1 if the derivation fails (simplex_rules.cpp).
+int simplex_rule_symmetric(int dim, int degree, std::vector<double>& pts, std::vector<double>& w);
 // P1 / P2 basis on the reference tet (closed forms in barycentric coordinates).
 void tet_basis(int p, const double* xi, double* phi, double* dphi);
 // P3..P6 on the equispaced lattice (Silvester's product formula); nodes (i, j, k)/p, i fastest, then j, then k.
@@ -177,6 +180,9 @@ struct TetApplyArgs {
 };
 
 // threads: threads (cells) per block, one of tet_cb_options.
+// Whether tet_apply_launch has a kernel for P_p (p = 1, 2) with ncomp
+// components, form `kind` and an nq-point rule.
+bool tet_rule_compiled(int p, int ncomp, int kind, int nq);
 cudaError_t tet_apply_launch(int p, int ncomp, int kind, int law, bool colour, bool agg, int threads,
                              const TetTables& tb, const TetApplyArgs& a, int sm_count, cudaStream_t s);
 // ---------------------------------------------------------------- quad kernels (quad_kernels.cu)

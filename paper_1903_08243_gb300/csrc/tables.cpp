@@ -145,21 +145,6 @@ void collocation_derivative(int m, const double* pts, double* D) {
   }
 }
 
-int tet_rule_4pt_deg2(double* pts, double* w) {
-  // barycentric (a, b, b, b) and permutations, a = (5 + 3 sqrt5)/20, b = (5 - sqrt5)/20
-  const double s5 = std::sqrt(5.0);
-  const double a = (5.0 + 3.0 * s5) / 20.0, b = (5.0 - s5) / 20.0;
-  for (int q = 0; q < 4; ++q) {
-    double lam[4] = {b, b, b, b};
-    lam[q] = a;
-    pts[3 * q + 0] = lam[1];
-    pts[3 * q + 1] = lam[2];
-    pts[3 * q + 2] = lam[3];
-    w[q] = 1.0 / 24.0;
-  }
-  return 4;
-}
-
 int tet_rule_collapsed(int degree, double* pts, double* w) {
   const int m = (degree + 2) / 2;
   double xa[kMaxN], wa[kMaxN], xb[kMaxN], wb[kMaxN], xc[kMaxN], wc[kMaxN];

@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(128) tet_moment_kernel(const __grid_constant__
         for (int j = 0; j < 3; ++j) K1[f][c][j] = 0.0;
     bool ok = true;
 #pragma unroll 1
-    for (int q = 0; q < 27; ++q) {
+    for (int q = 0; q < tb.nq; ++q) {
       const double x0 = tb.pts[3 * q], x1 = tb.pts[3 * q + 1], x2 = tb.pts[3 * q + 2];
       const double wd = tb.w[q] * adet;
       double gu[3][3], gc[3][3], f1[3][3];
@@ -425,33 +425,51 @@ int tet_cb_options(int* out) {
   return 3;
 }
 
+// Rules by form: P1 Laplace 1 point (degree 0), P1 mass / Helmholtz 4 (degree
+// 2), P2 scalar mass / Helmholtz 14 (degree 4), P2 Laplace and elasticity 4
+// (degree 2); the P2 hyperelastic moment kernel takes any rule of up to 27
+// points (14 symmetric, 27 collapsed).
+bool tet_rule_compiled(int p, int ncomp, int kind, int nq) {
+  if (p == 1 && ncomp == 1)
+    return (kind == MFA_FORM_LAPLACE && nq == 1) || ((kind == MFA_FORM_MASS || kind == MFA_FORM_HELMHOLTZ) && nq == 4);
+  if (p == 2 && ncomp == 1)
+    return (kind == MFA_FORM_LAPLACE && nq == 4) || ((kind == MFA_FORM_MASS || kind == MFA_FORM_HELMHOLTZ) && nq == 14);
+  if (p == 2 && ncomp == 3) {
+    if (kind == MFA_FORM_LAPLACE || kind == MFA_FORM_ELASTICITY) return nq == 4;
+    if (kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC) return nq >= 1 && nq <= kTetMaxQ;
+  }
+  return false;
+}
+
 cudaError_t tet_apply_launch(int p, int ncomp, int kind, int law, bool colour, bool agg, int threads,
                              const TetTables& tb, const TetApplyArgs& a, int sm_count, cudaStream_t s) {
   const int sc = colour ? 1 : (agg ? 2 : 0);
-  const int nq = tb.nq;
-  if (p == 1 && ncomp == 1 && nq == 4) {
+  if (!tet_rule_compiled(p, ncomp, kind, tb.nq)) return cudaErrorInvalidValue;
+  if (p == 1) {
     switch (kind) {
       case MFA_FORM_MASS: return launch2<1, 1, MFA_FORM_MASS, 0, 4>(sc, threads, tb, a, sm_count, s);
-      case MFA_FORM_LAPLACE: return launch2<1, 1, MFA_FORM_LAPLACE, 0, 4>(sc, threads, tb, a, sm_count, s);
+      case MFA_FORM_LAPLACE: return launch2<1, 1, MFA_FORM_LAPLACE, 0, 1>(sc, threads, tb, a, sm_count, s);
       case MFA_FORM_HELMHOLTZ: return launch2<1, 1, MFA_FORM_HELMHOLTZ, 0, 4>(sc, threads, tb, a, sm_count, s);
     }
   }
   if (p == 2 && ncomp == 1) {
-    if (kind == MFA_FORM_MASS && nq == 27) return launch2<2, 1, MFA_FORM_MASS, 0, 27>(sc, threads, tb, a, sm_count, s);
-    if (kind == MFA_FORM_LAPLACE && nq == 4) return launch2<2, 1, MFA_FORM_LAPLACE, 0, 4>(sc, threads, tb, a, sm_count, s);
-    if (kind == MFA_FORM_HELMHOLTZ && nq == 27)
-      return launch2<2, 1, MFA_FORM_HELMHOLTZ, 0, 27>(sc, threads, tb, a, sm_count, s);
+    switch (kind) {
+      case MFA_FORM_MASS: return launch2<2, 1, MFA_FORM_MASS, 0, 14>(sc, threads, tb, a, sm_count, s);
+      case MFA_FORM_LAPLACE: return launch2<2, 1, MFA_FORM_LAPLACE, 0, 4>(sc, threads, tb, a, sm_count, s);
+      case MFA_FORM_HELMHOLTZ: return launch2<2, 1, MFA_FORM_HELMHOLTZ, 0, 14>(sc, threads, tb, a, sm_count, s);
+    }
   }
   if (p == 2 && ncomp == 3) {
-    if (kind == MFA_FORM_LAPLACE && nq == 4) return launch2<2, 3, MFA_FORM_LAPLACE, 0, 4>(sc, threads, tb, a, sm_count, s);
-    if (kind == MFA_FORM_ELASTICITY && nq == 4)
-      return launch2<2, 3, MFA_FORM_ELASTICITY, 0, 4>(sc, threads, tb, a, sm_count, s);
-    if (kind == MFA_FORM_HYPER_RES && nq == 27)
-      return law == MFA_LAW_SVK ? launch_moment<MFA_FORM_HYPER_RES, MFA_LAW_SVK>(sc, threads, tb, a, sm_count, s)
-                                : launch_moment<MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(sc, threads, tb, a, sm_count, s);
-    if (kind == MFA_FORM_HYPER_JAC && nq == 27)
-      return law == MFA_LAW_SVK ? launch_moment<MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(sc, threads, tb, a, sm_count, s)
-                                : launch_moment<MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(sc, threads, tb, a, sm_count, s);
+    switch (kind) {
+      case MFA_FORM_LAPLACE: return launch2<2, 3, MFA_FORM_LAPLACE, 0, 4>(sc, threads, tb, a, sm_count, s);
+      case MFA_FORM_ELASTICITY: return launch2<2, 3, MFA_FORM_ELASTICITY, 0, 4>(sc, threads, tb, a, sm_count, s);
+      case MFA_FORM_HYPER_RES:
+        return law == MFA_LAW_SVK ? launch_moment<MFA_FORM_HYPER_RES, MFA_LAW_SVK>(sc, threads, tb, a, sm_count, s)
+                                  : launch_moment<MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(sc, threads, tb, a, sm_count, s);
+      case MFA_FORM_HYPER_JAC:
+        return law == MFA_LAW_SVK ? launch_moment<MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(sc, threads, tb, a, sm_count, s)
+                                  : launch_moment<MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(sc, threads, tb, a, sm_count, s);
+    }
   }
   return cudaErrorInvalidValue;
 }
