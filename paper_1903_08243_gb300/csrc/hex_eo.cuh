@@ -53,7 +53,52 @@ struct EShape {
   static constexpr int CB = CBX > 0 ? CBX : eo_cb_for(N, 256);
   static constexpr int T = ceil32(CB * L);
   static constexpr int SMEM = 4 * CB * P * 8;
+  static constexpr int K = (CB * P + T - 1) / T;  // points per thread in the point-parallel phases
+  // blocks per SM that shared memory allows (228 KB per SM, 1 KB reserved per block): the register
+  // budget of __launch_bounds__, so that registers never cut occupancy below it
+  static constexpr int MINB0 = (228 * 1024) / (SMEM + 1024);
+  static constexpr int MINB = MINB0 < 1 ? 1 : (MINB0 * T > 2048 ? 2048 / T : MINB0);
 };
+
+// Asks L2 to fetch [p, p + bytes) with one bulk prefetch (no registers, no
+// completion to wait for).  The range is trimmed inward to 16-byte boundaries,
+// as the bulk-copy unit requires, so it never leaves the buffer.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uintptr_t s = (a + 15) & ~uintptr_t(15), e = (a + bytes) & ~uintptr_t(15);
+  if (e > s) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"((unsigned)(e - s)) : "memory");
+}
+
+// Geometric factors of batch `batch` into L2, one cell per thread (factors of
+// a cell are contiguous: [entry][point]).
+template <int N, int CBX, int NG>
+__device__ __forceinline__ void eo_prefetch_factors(const HexApplyArgs& a, int64_t batch) {
+  using S = EShape<N, CBX>;
+  const int64_t c0 = batch * S::CB;
+  const int ncb = (int)(a.count - c0 < S::CB ? a.count - c0 : S::CB);
+  if ((int)threadIdx.x < ncb && a.geom) {
+    const int64_t cell = a.cell_list ? (int64_t)__ldg(a.cell_list + c0 + threadIdx.x) : c0 + threadIdx.x;
+    prefetch_l2(static_cast<const double*>(a.geom) + cell * (int64_t)NG * S::P, sizeof(double) * NG * S::P);
+  }
+}
+
+// Node of each of this thread's points of batch `batch` (-1 past the batch's end).
+template <int N, int CBX>
+__device__ __forceinline__ void eo_load_nodes(const HexApplyArgs& a, int64_t batch, int32_t (&node)[EShape<N, CBX>::K]) {
+  using S = EShape<N, CBX>;
+  const int64_t c0 = batch * S::CB;
+  const int ncb = (int)(a.count - c0 < S::CB ? a.count - c0 : S::CB);
+#pragma unroll
+  for (int k = 0; k < S::K; ++k) {
+    const int i = threadIdx.x + k * S::T;
+    node[k] = -1;
+    if (i < ncb * S::P) {
+      const int c = i / S::P, q = i - c * S::P;
+      const int64_t cell = a.cell_list ? (int64_t)__ldg(a.cell_list + c0 + c) : c0 + c;
+      node[k] = __ldg(a.cell_node + cell * S::P + q);
+    }
+  }
+}
 
 template <int KIND>
 __host__ __device__ constexpr int geom_entries() {
@@ -114,10 +159,13 @@ __device__ __forceinline__ void eo_sweep(const double* in, double* out, int a, i
 // Four shared-memory planes of CB x n^3 doubles: U (gathered input, then the z-derivative and its flux, then
 // the B^T results), V (values at the Gauss points, then the test-side accumulation), F0 and F1 (x- and
 // y-derivatives and their fluxes).
+// `node` holds the nodes of this thread's points (eo_load_nodes), loaded ahead
+// of time: the gather and the scatter then wait on one load, not two.
 template <int N, int KIND, bool COLOUR, int CBX = 0>
-__device__ __forceinline__ void eo_batch(const HexApplyArgs& a, int64_t batch, double* smem) {
+__device__ __forceinline__ void eo_batch(const HexApplyArgs& a, int64_t batch, double* smem,
+                                         const int32_t (&node)[EShape<N, CBX>::K]) {
   using S = EShape<N, CBX>;
-  constexpr int L = S::L, P = S::P, CB = S::CB, T = S::T, NG = geom_entries<KIND>();
+  constexpr int L = S::L, P = S::P, CB = S::CB, T = S::T, K = S::K, NG = geom_entries<KIND>();
   const int t = threadIdx.x;
   const int cl = t / L, l = t - cl * L;
   const int la = l % N, lb = l / N;
@@ -135,10 +183,9 @@ __device__ __forceinline__ void eo_batch(const HexApplyArgs& a, int64_t batch, d
   const double* geom = static_cast<const double*>(a.geom);
   auto cell_of = [&](int c) -> int64_t { return a.cell_list ? (int64_t)__ldg(a.cell_list + c0 + c) : c0 + c; };
 
-  for (int i = t; i < ncb * P; i += T) {  // gather, point-parallel
-    const int c = i / P, k = i - c * P;
-    U0[i] = __ldg(a.x + __ldg(a.cell_node + cell_of(c) * P + k));
-  }
+#pragma unroll
+  for (int k = 0; k < K; ++k)  // gather, point-parallel
+    if (node[k] >= 0) U0[t + k * T] = __ldg(a.x + node[k]);
   __syncthreads();
   if (valid) eo_sweep<N, 0, 0, 1, false>(U, V, la, lb);  // B in x
   __syncthreads();
@@ -185,26 +232,40 @@ __device__ __forceinline__ void eo_batch(const HexApplyArgs& a, int64_t batch, d
   __syncthreads();
   if (valid) eo_sweep<N, 0, 1, 1, false>(V, U, la, lb);  // B^T in x
   __syncthreads();
-  for (int i = t; i < ncb * P; i += T) {  // scatter-add, point-parallel
-    const int c = i / P, k = i - c * P;
-    const int32_t node = __ldg(a.cell_node + cell_of(c) * P + k);
-    if constexpr (COLOUR) a.y[node] += U0[i];  // no other cell of this colour touches `node`
-    else atomicAdd(a.y + node, U0[i]);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {  // scatter-add, point-parallel
+    if (node[k] < 0) continue;
+    if constexpr (COLOUR) a.y[node[k]] += U0[t + k * T];  // no other cell of this colour touches the node
+    else atomicAdd(a.y + node[k], U0[t + k * T]);
   }
   __syncthreads();
 }
 
 template <int N, int KIND, bool COLOUR, int CBX = 0>
-__global__ void __launch_bounds__(EShape<N, CBX>::T) eo_apply_kernel(const HexApplyArgs a) {
+__global__ void __launch_bounds__(EShape<N, CBX>::T, EShape<N, CBX>::MINB) eo_apply_kernel(const HexApplyArgs a) {
   extern __shared__ __align__(16) double smem_eo[];
-  constexpr int CB = EShape<N, CBX>::CB;
-  const int64_t nbatch = (a.count + CB - 1) / CB;
-  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x)
-    eo_batch<N, KIND, COLOUR, CBX>(a, batch, smem_eo);
+  using S = EShape<N, CBX>;
+  const int64_t nbatch = (a.count + S::CB - 1) / S::CB;
+  // the next batch's nodes are requested before this batch's work, so they arrive during it, and its
+  // geometric factors are prefetched into L2
+  int32_t node[S::K], next[S::K];
+  if (blockIdx.x < nbatch) {
+    eo_load_nodes<N, CBX>(a, blockIdx.x, next);
+    eo_prefetch_factors<N, CBX, geom_entries<KIND>()>(a, blockIdx.x);
+  }
+  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
+#pragma unroll
+    for (int k = 0; k < S::K; ++k) node[k] = next[k];
+    if (batch + gridDim.x < nbatch) {
+      eo_load_nodes<N, CBX>(a, batch + gridDim.x, next);
+      eo_prefetch_factors<N, CBX, geom_entries<KIND>()>(a, batch + gridDim.x);
+    }
+    eo_batch<N, KIND, COLOUR, CBX>(a, batch, smem_eo, node);
+  }
 }
 
 template <int N, int KIND>
-__global__ void __launch_bounds__(EShape<N>::T) eo_group_kernel(const HexApplyArgs* __restrict__ items,
+__global__ void __launch_bounds__(EShape<N>::T, EShape<N>::MINB) eo_group_kernel(const HexApplyArgs* __restrict__ items,
                                                                 const int64_t* __restrict__ first, int nitems) {
   extern __shared__ __align__(16) double smem_eo[];
   const int64_t total = first[nitems];
@@ -212,7 +273,9 @@ __global__ void __launch_bounds__(EShape<N>::T) eo_group_kernel(const HexApplyAr
   for (int64_t gb = blockIdx.x; gb < total; gb += gridDim.x) {
     while (k + 1 < nitems && gb >= first[k + 1]) ++k;
     const HexApplyArgs h = items[k];
-    eo_batch<N, KIND, false>(h, gb - first[k], smem_eo);
+    int32_t node[EShape<N>::K];
+    eo_load_nodes<N, 0>(h, gb - first[k], node);
+    eo_batch<N, KIND, false>(h, gb - first[k], smem_eo, node);
   }
 }
 
