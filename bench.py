@@ -33,7 +33,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # while the kernel source is unchanged (sha1 of hex_kernels.cuh).
 # 32^3 capture (868.2 MB per launch) scaled by the cell count to the 64^3 launch;
 # see profiles/hex_apply_q6_helmholtz_hex32.md.
-NCU_TRAFFIC = {("ca970882721b", "Q6 helmholtz"): 8 * 872.65e6}  # eo kernel, ncu on 32^3 scaled by cells to 64^3
+NCU_TRAFFIC = {("34a9a704426a", "Q6 helmholtz"): 8 * 869.22e6}  # eo kernel, ncu on 32^3 scaled by cells to 64^3
 
 
 def parse_args():

@@ -60,28 +60,6 @@ struct EShape {
   static constexpr int MINB = MINB0 < 1 ? 1 : (MINB0 * T > 2048 ? 2048 / T : MINB0);
 };
 
-// Asks L2 to fetch [p, p + bytes) with one bulk prefetch (no registers, no
-// completion to wait for).  The range is trimmed inward to 16-byte boundaries,
-// as the bulk-copy unit requires, so it never leaves the buffer.
-__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
-  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-  const uintptr_t s = (a + 15) & ~uintptr_t(15), e = (a + bytes) & ~uintptr_t(15);
-  if (e > s) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"((unsigned)(e - s)) : "memory");
-}
-
-// Geometric factors of batch `batch` into L2, one cell per thread (factors of
-// a cell are contiguous: [entry][point]).
-template <int N, int CBX, int NG>
-__device__ __forceinline__ void eo_prefetch_factors(const HexApplyArgs& a, int64_t batch) {
-  using S = EShape<N, CBX>;
-  const int64_t c0 = batch * S::CB;
-  const int ncb = (int)(a.count - c0 < S::CB ? a.count - c0 : S::CB);
-  if ((int)threadIdx.x < ncb && a.geom) {
-    const int64_t cell = a.cell_list ? (int64_t)__ldg(a.cell_list + c0 + threadIdx.x) : c0 + threadIdx.x;
-    prefetch_l2(static_cast<const double*>(a.geom) + cell * (int64_t)NG * S::P, sizeof(double) * NG * S::P);
-  }
-}
-
 // Node of each of this thread's points of batch `batch` (-1 past the batch's end).
 template <int N, int CBX>
 __device__ __forceinline__ void eo_load_nodes(const HexApplyArgs& a, int64_t batch, int32_t (&node)[EShape<N, CBX>::K]) {
@@ -246,20 +224,15 @@ __global__ void __launch_bounds__(EShape<N, CBX>::T, EShape<N, CBX>::MINB) eo_ap
   extern __shared__ __align__(16) double smem_eo[];
   using S = EShape<N, CBX>;
   const int64_t nbatch = (a.count + S::CB - 1) / S::CB;
-  // the next batch's nodes are requested before this batch's work, so they arrive during it, and its
-  // geometric factors are prefetched into L2
+  // the next batch's nodes are requested before this batch's work, so they arrive during it.  (Prefetching
+  // the next batch's geometric factors into L2 as well gained 0.5% and raised DRAM reads by a quarter:
+  // not done.)
   int32_t node[S::K], next[S::K];
-  if (blockIdx.x < nbatch) {
-    eo_load_nodes<N, CBX>(a, blockIdx.x, next);
-    eo_prefetch_factors<N, CBX, geom_entries<KIND>()>(a, blockIdx.x);
-  }
+  if (blockIdx.x < nbatch) eo_load_nodes<N, CBX>(a, blockIdx.x, next);
   for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
 #pragma unroll
     for (int k = 0; k < S::K; ++k) node[k] = next[k];
-    if (batch + gridDim.x < nbatch) {
-      eo_load_nodes<N, CBX>(a, batch + gridDim.x, next);
-      eo_prefetch_factors<N, CBX, geom_entries<KIND>()>(a, batch + gridDim.x);
-    }
+    if (batch + gridDim.x < nbatch) eo_load_nodes<N, CBX>(a, batch + gridDim.x, next);
     eo_batch<N, KIND, COLOUR, CBX>(a, batch, smem_eo, node);
   }
 }
