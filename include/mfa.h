@@ -326,6 +326,16 @@ MFA_API int mfa_convert_f32_to_f64(mfa_ctx *ctx, const float *x, double *y, int6
 /* Same with host buffers: copies x to the device, applies, copies y back and
  * waits.  The device staging buffers are owned by the form. */
 MFA_API int mfa_apply_host(mfa_ctx *ctx, mfa_form *form, const double *x_host, double *y_host);
+/* y_host[i] = A_i x_host[i] for n forms, with the copies overlapped with the
+ * applies: the copies in run ahead on one library-owned stream and the copies
+ * out behind on another, so form i+1's x moves to the device and form i-1's y
+ * to the host while form i computes (the applies stay in order on the context
+ * stream).  Host buffers are best pinned (page-locked); they must stay valid
+ * until the call returns, which is after everything finished.  Staging
+ * buffers are owned by each form, as for mfa_apply_host, so a form may appear
+ * only once per call (MFA_ERR_ARG otherwise). */
+MFA_API int mfa_apply_host_many(mfa_ctx *ctx, int n, mfa_form *const *forms, const double *const *x_host,
+                                double *const *y_host);
 /* Wait for the context stream; MFA_ERR_DOMAIN if a kernel flagged det J <= 0
  * or a deformation with J <= 0, MFA_ERR_TIMEOUT if a kernel gave up a bounded
  * wait, since the last mfa_sync (the flag is cleared). */

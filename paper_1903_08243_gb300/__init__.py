@@ -114,6 +114,7 @@ _SIGS = {
     "mfa_form_autotune": ([_VP, _VP, _VP, _VP, _I, _VP, _I, ctypes.POINTER(_I)], _I),
     "mfa_apply": ([_VP, _VP, _VP, _VP, _I], _I),
     "mfa_apply_host": ([_VP, _VP, _VP, _VP], _I),
+    "mfa_apply_host_many": ([_VP, _I, _VP, _VP, _VP], _I),
     "mfa_apply_f32": ([_VP, _VP, _VP, _VP, _I], _I),
     "mfa_convert_f64_to_f32": ([_VP, _VP, _VP, _I64], _I),
     "mfa_convert_f32_to_f64": ([_VP, _VP, _VP, _I64], _I),
@@ -369,6 +370,18 @@ def mfa_convert_f32_to_f64(ctx, x, y):
 
 def mfa_apply_host(ctx, form, x_host, y_host):
     _check(lib().mfa_apply_host(ctx, form, _ptr(x_host), _ptr(y_host)))
+
+
+def mfa_apply_host_many(ctx, forms, xs_host, ys_host):
+    """ys_host[i] = A_i xs_host[i] with the host<->device copies overlapped with the applies (host tensors, best
+    pinned)."""
+    n = len(forms)
+    if len(xs_host) != n or len(ys_host) != n:
+        raise ValueError("one x and one y per form")
+    fa = (ctypes.c_void_p * max(n, 1))(*[f for f in forms])
+    xa = (ctypes.c_void_p * max(n, 1))(*[_ptr(x) for x in xs_host])
+    ya = (ctypes.c_void_p * max(n, 1))(*[_ptr(y) for y in ys_host])
+    _check(lib().mfa_apply_host_many(ctx, n, fa, xa, ya))
 
 
 def mfa_sync(ctx):

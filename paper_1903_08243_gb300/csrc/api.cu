@@ -591,6 +591,9 @@ int mfa_set_stream(mfa_ctx* ctx, void* stream) {
 int mfa_destroy(mfa_ctx* ctx) {
   if (!ctx) return MFA_OK;
   cudaSetDevice(ctx->device);
+  if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
+  if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
+  for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_scratch);
   delete ctx;
@@ -1219,6 +1222,55 @@ int mfa_apply_host(mfa_ctx* ctx, mfa_form* f, const double* xh, double* yh) {
   rc = mfa_apply(ctx, f, f->d_stage_x, f->d_stage_y, 0);
   if (rc) return rc;
   MFA_CUDA(cudaMemcpyAsync(yh, f->d_stage_y, sizeof(double) * ndof, cudaMemcpyDeviceToHost, ctx->stream));
+  return mfa_sync(ctx);
+}
+
+int mfa_apply_host_many(mfa_ctx* ctx, int n, mfa_form* const* forms, const double* const* xh, double* const* yh) {
+  if (!ctx || n < 0 || (n > 0 && (!forms || !xh || !yh))) return fail(MFA_ERR_ARG, "mfa_apply_host_many: bad argument");
+  for (int i = 0; i < n; ++i) {
+    if (!forms[i] || !xh[i] || !yh[i]) return fail(MFA_ERR_ARG, "mfa_apply_host_many: NULL entry %d", i);
+    for (int j = 0; j < i; ++j)
+      if (forms[j] == forms[i]) return fail(MFA_ERR_ARG, "mfa_apply_host_many: form %d repeated", i);
+  }
+  MFA_CUDA(cudaSetDevice(ctx->device));
+  if (!ctx->copy_in) MFA_CUDA(cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking));
+  if (!ctx->copy_out) MFA_CUDA(cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking));
+  while ((int)ctx->events.size() < 2 * n + 1) {
+    cudaEvent_t e;
+    MFA_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->events.push_back(e);
+  }
+  for (int i = 0; i < n; ++i) {
+    mfa_form* f = forms[i];
+    const int64_t ndof = f->space->nnode * f->space->ncomp;
+    int rc = MFA_OK;
+    if (!f->d_stage_x) rc = cuda_alloc((void**)&f->d_stage_x, sizeof(double) * ndof, "staging x");
+    if (!rc && !f->d_stage_y) rc = cuda_alloc((void**)&f->d_stage_y, sizeof(double) * ndof, "staging y");
+    if (rc) return rc;
+  }
+  // the copies in start after whatever the context stream already holds (a staging buffer may still be in use)
+  cudaEvent_t start = ctx->events[2 * n];
+  MFA_CUDA(cudaEventRecord(start, ctx->stream));
+  MFA_CUDA(cudaStreamWaitEvent(ctx->copy_in, start, 0));
+  for (int i = 0; i < n; ++i) {
+    mfa_form* f = forms[i];
+    const int64_t ndof = f->space->nnode * f->space->ncomp;
+    cudaEvent_t in_done = ctx->events[2 * i], applied = ctx->events[2 * i + 1];
+    MFA_CUDA(cudaMemcpyAsync(f->d_stage_x, xh[i], sizeof(double) * ndof, cudaMemcpyHostToDevice, ctx->copy_in));
+    MFA_CUDA(cudaEventRecord(in_done, ctx->copy_in));
+    MFA_CUDA(cudaStreamWaitEvent(ctx->stream, in_done, 0));
+    const int rc = mfa_apply(ctx, f, f->d_stage_x, f->d_stage_y, 0);
+    if (rc) {
+      cudaStreamSynchronize(ctx->copy_in);
+      cudaStreamSynchronize(ctx->copy_out);
+      return rc;
+    }
+    MFA_CUDA(cudaEventRecord(applied, ctx->stream));
+    MFA_CUDA(cudaStreamWaitEvent(ctx->copy_out, applied, 0));
+    MFA_CUDA(cudaMemcpyAsync(yh[i], f->d_stage_y, sizeof(double) * ndof, cudaMemcpyDeviceToHost, ctx->copy_out));
+  }
+  MFA_CUDA(cudaStreamSynchronize(ctx->copy_in));
+  MFA_CUDA(cudaStreamSynchronize(ctx->copy_out));
   return mfa_sync(ctx);
 }
 

@@ -290,6 +290,8 @@ struct mfa_ctx {
   cudaStream_t stream = nullptr;
   int* d_err = nullptr;          // kernel error flags (bit 0: det J <= 0, bit 1: J <= 0)
   double* d_scratch = nullptr;   // reduction scratch (partials + result)
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;  // mfa_apply_host_many's copy streams (created on first use)
+  std::vector<cudaEvent_t> events;                    // and its events, two per form, kept for reuse
 };
 
 struct mfa_mesh {
