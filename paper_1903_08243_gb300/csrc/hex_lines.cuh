@@ -57,7 +57,23 @@ struct LShape {
   static constexpr int CB = CBX > 0 ? CBX : line_cb_for(N, 256);
   static constexpr int T = ceil32(CB * L);
   static constexpr int SMEM = 5 * CB * P * 4;
+  static constexpr int K = (CB * P + T - 1) / T;  // points per thread in the point-parallel phases
 };
+
+// Node of each of this thread's points of batch `batch` (-1 past the batch's end): requested a batch
+// ahead, so the gather and the scatter wait on one load instead of two.
+template <int N, int CBX>
+__device__ __forceinline__ void line_load_nodes(const int32_t* cell_node, int64_t count, int64_t batch,
+                                                int32_t (&node)[LShape<N, CBX>::K]) {
+  using S = LShape<N, CBX>;
+  const int64_t c0 = batch * S::CB;
+  const int ncb = (int)(count - c0 < S::CB ? count - c0 : S::CB);
+#pragma unroll
+  for (int k = 0; k < S::K; ++k) {
+    const int i = threadIdx.x + k * S::T;
+    node[k] = i < ncb * S::P ? __ldg(cell_node + c0 * S::P + i) : -1;
+  }
+}
 
 // Elements per cell of the padded factor block (16-byte multiple).
 __host__ __device__ constexpr int64_t geom_stride(int ng, int p, int esz) {
@@ -202,9 +218,9 @@ __device__ __forceinline__ void issue_factors(const LineArgs& a, int64_t batch, 
 // the bulk-copied stage.  `next` >= 0: batch (of `an`) to prefetch afterwards.
 template <int N, int KIND, int PREC, typename TX, bool STG = staged<PREC>(), int CBX = 0>
 __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, float* smem, Stage& st,
-                                           const LineArgs* an, int64_t next) {
+                                           const LineArgs* an, int64_t next, const int32_t (&node)[LShape<N, CBX>::K]) {
   using S = LShape<N, CBX>;
-  constexpr int L = S::L, P = S::P, CB = S::CB, T = S::T, NG = geom_entries<KIND>();
+  constexpr int L = S::L, P = S::P, CB = S::CB, T = S::T, K = S::K, NG = geom_entries<KIND>();
   constexpr int variant = PREC == MFA_PREC_BF16 ? 1 : 0;
   const int t = threadIdx.x;
   const int cl = t / L, l = t - cl * L;
@@ -221,7 +237,9 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
   const TX* x = static_cast<const TX*>(a.x);
 
   // gather, point-parallel: point i of the batch is local point i % P of cell c0 + i / P
-  for (int i = t; i < ncb * P; i += T) U0[i] = load_x(x, __ldg(a.cell_node + c0 * P + i), variant == 1);
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (node[k] >= 0) U0[t + k * T] = load_x(x, node[k], variant == 1);
   __syncthreads();
   if (valid) sweep<N, 0, 0, false, false, variant>(U, V, la, lb);  // B in x
   __syncthreads();
@@ -293,10 +311,11 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
   if (valid) sweep<N, 0, 0, true, false, variant>(U, V, la, lb);  // B^T in x
   __syncthreads();
   // scatter-add, point-parallel
-  for (int i = t; i < ncb * P; i += T) {
-    const int32_t node = __ldg(a.cell_node + c0 * P + i);
-    if constexpr (sizeof(TX) == 8) add_y(static_cast<double*>(a.y), node, V0[i]);
-    else add_y(static_cast<float*>(a.y), node, V0[i]);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (node[k] < 0) continue;
+    if constexpr (sizeof(TX) == 8) add_y(static_cast<double*>(a.y), node[k], V0[t + k * T]);
+    else add_y(static_cast<float*>(a.y), node[k], V0[t + k * T]);
   }
   __syncthreads();
   return true;
@@ -338,12 +357,17 @@ __global__ void __launch_bounds__(LShape<N, CBX>::T) line_apply_kernel(const Lin
   __shared__ int abort_flag;
   Stage st;
   stage_setup<N, KIND, PREC, STG, CBX>(smem_l, st, &abort_flag);
-  constexpr int CB = LShape<N, CBX>::CB;
-  const int64_t nbatch = (a.count + CB - 1) / CB;
+  using S = LShape<N, CBX>;
+  const int64_t nbatch = (a.count + S::CB - 1) / S::CB;
   if ((int64_t)blockIdx.x < nbatch && threadIdx.x == 0) issue_factors<N, KIND, PREC, STG, CBX>(a, blockIdx.x, st);
+  int32_t node[S::K], nodes_next[S::K];
+  if ((int64_t)blockIdx.x < nbatch) line_load_nodes<N, CBX>(a.cell_node, a.count, blockIdx.x, nodes_next);
   for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
     const int64_t next = batch + gridDim.x < nbatch ? batch + gridDim.x : -1;
-    if (!line_batch<N, KIND, PREC, TX, STG, CBX>(a, batch, smem_l, st, &a, next)) return;
+#pragma unroll
+    for (int k = 0; k < S::K; ++k) node[k] = nodes_next[k];
+    if (next >= 0) line_load_nodes<N, CBX>(a.cell_node, a.count, next, nodes_next);
+    if (!line_batch<N, KIND, PREC, TX, STG, CBX>(a, batch, smem_l, st, &a, next, node)) return;
   }
 }
 
@@ -359,13 +383,14 @@ __global__ void __launch_bounds__(LShape<N>::T) line_group_kernel(const HexApply
     const HexApplyArgs h = items[k];
     return LineArgs{h.x, h.y, h.cell_node, h.geom, h.count, h.geom_stride, h.err};
   };
+  constexpr int K = LShape<N>::K;
+  int32_t node[K], nodes_next[K];
   int k = 0;
   if ((int64_t)blockIdx.x < total) {
     while (k + 1 < nitems && (int64_t)blockIdx.x >= first[k + 1]) ++k;
-    if (threadIdx.x == 0) {
-      const LineArgs a0 = args_of(k);
-      issue_factors<N, KIND, PREC>(a0, blockIdx.x - first[k], st);
-    }
+    const LineArgs a0 = args_of(k);
+    if (threadIdx.x == 0) issue_factors<N, KIND, PREC>(a0, blockIdx.x - first[k], st);
+    line_load_nodes<N, 0>(a0.cell_node, a0.count, blockIdx.x - first[k], nodes_next);
   }
   for (int64_t gb = blockIdx.x; gb < total; gb += gridDim.x) {
     while (k + 1 < nitems && gb >= first[k + 1]) ++k;
@@ -375,7 +400,10 @@ __global__ void __launch_bounds__(LShape<N>::T) line_group_kernel(const HexApply
     while (kn + 1 < nitems && gn >= first[kn + 1]) ++kn;
     const LineArgs an = args_of(kn < nitems ? kn : k);
     const int64_t next = gn < total ? gn - first[kn] : -1;
-    if (!line_batch<N, KIND, PREC, double>(a, gb - first[k], smem_l, st, &an, next)) return;
+#pragma unroll
+    for (int j = 0; j < K; ++j) node[j] = nodes_next[j];
+    if (next >= 0) line_load_nodes<N, 0>(an.cell_node, an.count, next, nodes_next);
+    if (!line_batch<N, KIND, PREC, double>(a, gb - first[k], smem_l, st, &an, next, node)) return;
   }
 }
 
