@@ -170,10 +170,22 @@ __device__ __forceinline__ bool point_geometry(const double* X, const HexTables&
   return true;
 }
 
+// Node of this thread's point in batch `batch` (-1 for no point): requested a
+// batch ahead, so the gather waits on one load instead of two.
+template <int N, int NQ, int CBX>
+__device__ __forceinline__ int32_t point_node(const HexApplyArgs& a, int64_t batch, int cl, int pt) {
+  using S = Shape<N, NQ, 8, CBX>;
+  const int64_t idx = batch * S::CB + cl;
+  if (cl >= S::CB || idx >= a.count || pt >= S::PN) return -1;
+  const int64_t cell = a.cell_list ? (int64_t)__ldg(a.cell_list + idx) : idx;
+  return __ldg(a.cell_node + cell * S::PN + pt);
+}
+
+// `node_ahead`: this point's node, loaded ahead by point_node (-1: load it here).
 template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0, bool AGG = false, bool OTF = false>
 __device__ __forceinline__ void hex_cell_batch(const HexApplyArgs& a, int64_t batch,
                                                const Smem<N, NQ, PREC, CBX>& sm, const HexTables& tb,
-                                               double* sX) {
+                                               double* sX, int32_t node_ahead = -1) {
   using S = Shape<N, NQ, 8, CBX>;
   using T = typename Prec<PREC>::T;
   using TG = typename Prec<PREC>::TG;
@@ -197,7 +209,7 @@ __device__ __forceinline__ void hex_cell_batch(const HexApplyArgs& a, int64_t ba
     // gather x through the cell->node map; keep the node for the scatter
     int32_t node = 0;
     if (valid && pt < PN) {
-      node = __ldg(a.cell_node + cell * PN + pt);
+      node = node_ahead >= 0 ? node_ahead : __ldg(a.cell_node + cell * PN + pt);
       A[pt] = Prec<PREC>::in(__ldg(a.x + node));
     }
     // geometric factors of this point (consumed after three sweeps): stored, or from the vertices
@@ -328,8 +340,12 @@ __global__ void __launch_bounds__(Shape<N, NQ, 8, CBX>::T) hex_apply_kernel(cons
   Smem<N, NQ, PREC, CBX> sm;
   sm.init(smem_raw, tb);
   const int64_t nbatch = (a.count + CB - 1) / CB;
-  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x)
-    hex_cell_batch<N, NQ, KIND, COLOUR, PREC, CBX, AGG, OTF>(a, batch, sm, tb, sX);
+  int32_t next = (int64_t)blockIdx.x < nbatch ? point_node<N, NQ, CBX>(a, blockIdx.x, sm.cl, sm.pt) : -1;
+  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
+    const int32_t node = next;
+    if (batch + gridDim.x < nbatch) next = point_node<N, NQ, CBX>(a, batch + gridDim.x, sm.cl, sm.pt);
+    hex_cell_batch<N, NQ, KIND, COLOUR, PREC, CBX, AGG, OTF>(a, batch, sm, tb, sX, node);
+  }
 }
 
 // Many forms of one (n, nq, kind, precision) class in one persistent launch:

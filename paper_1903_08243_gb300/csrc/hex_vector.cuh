@@ -26,7 +26,8 @@ using hexk::Shape;
 using hexk::Smem;
 
 template <int N, int NQ, int KIND, int LAW, bool COLOUR>
-__device__ __forceinline__ void cell_batch(const HexVecArgs& a, int64_t batch, const Smem<N, NQ, MFA_PREC_FP64>& sm) {
+__device__ __forceinline__ void cell_batch(const HexVecArgs& a, int64_t batch, const Smem<N, NQ, MFA_PREC_FP64>& sm,
+                                           int32_t node_ahead) {  // node_ahead: this point's node (0 for none)
   using S = Shape<N, NQ>;
   constexpr int PN = S::PN, PQ = S::PQ, CB = S::CB;
   constexpr bool JAC = KIND == MFA_FORM_HYPER_JAC;
@@ -41,9 +42,8 @@ __device__ __forceinline__ void cell_batch(const HexVecArgs& a, int64_t batch, c
   const int64_t idx = batch * CB + cl;
   const bool valid = cl < CB && idx < a.count;
   int64_t cell = 0;
-  int32_t node = 0;
+  int32_t node = node_ahead;
   if (valid) cell = a.cell_list ? (int64_t)__ldg(a.cell_list + idx) : idx;
-  if (valid && pt < PN) node = __ldg(a.cell_node + cell * PN + pt);
   const bool atq = valid && pt < PQ;  // this thread owns Gauss point pt
   const int qi = pt % NQ, qj = (pt / NQ) % NQ, qk = pt / (NQ * NQ);
 
@@ -200,10 +200,21 @@ __global__ void __launch_bounds__(Shape<N, NQ>::T) apply_kernel(const __grid_con
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<N, NQ, MFA_PREC_FP64> sm;
   sm.init(smem_raw, tb);
-  constexpr int CB = Shape<N, NQ>::CB;
+  constexpr int CB = Shape<N, NQ>::CB, PN = Shape<N, NQ>::PN;
   const int64_t nbatch = (a.count + CB - 1) / CB;
-  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x)
-    cell_batch<N, NQ, KIND, LAW, COLOUR>(a, batch, sm);
+  // this thread's node in a batch (0 for no point), requested a batch ahead so the gathers wait on one load
+  auto node_of = [&](int64_t batch) -> int32_t {
+    const int64_t idx = batch * CB + sm.cl;
+    if (!(sm.cl < CB && idx < a.count && sm.pt < PN)) return 0;
+    const int64_t cell = a.cell_list ? (int64_t)__ldg(a.cell_list + idx) : idx;
+    return __ldg(a.cell_node + cell * PN + sm.pt);
+  };
+  int32_t next = (int64_t)blockIdx.x < nbatch ? node_of(blockIdx.x) : 0;
+  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
+    const int32_t node = next;
+    if (batch + gridDim.x < nbatch) next = node_of(batch + gridDim.x);
+    cell_batch<N, NQ, KIND, LAW, COLOUR>(a, batch, sm, node);
+  }
 }
 
 template <int N, int NQ, int KIND, int LAW, bool COLOUR>

@@ -60,15 +60,23 @@ __global__ void __launch_bounds__(QShape<N, NQ>::T) quad_apply_kernel(const __gr
   double* F1 = F0 + CB * PQ;
   const int qi = pt % NQ, qj = pt / NQ;
   const int64_t nbatch = (a.count + CB - 1) / CB;
+  // this thread's node in a batch (0 for no point), requested a batch ahead so the gather waits on one load
+  auto node_of = [&](int64_t batch) -> int32_t {
+    const int64_t idx = batch * CB + cl;
+    if (!(cl < CB && idx < a.count && pt < PN)) return 0;
+    const int64_t cell = a.cell_list ? (int64_t)__ldg(a.cell_list + idx) : idx;
+    return __ldg(a.cell_node + cell * PN + pt);
+  };
+  int32_t next = (int64_t)blockIdx.x < nbatch ? node_of(blockIdx.x) : 0;
   __syncthreads();
   for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
     const int64_t idx = batch * CB + cl;
     const bool valid = cl < CB && idx < a.count;
     const bool atq = valid && pt < PQ;
     int64_t cell = 0;
-    int32_t node = 0;
+    const int32_t node = next;
+    if (batch + gridDim.x < nbatch) next = node_of(batch + gridDim.x);
     if (valid) cell = a.cell_list ? (int64_t)__ldg(a.cell_list + idx) : idx;
-    if (valid && pt < PN) node = __ldg(a.cell_node + cell * PN + pt);
 
     // value and reference gradient of component c of the nodal field v at Gauss point pt
     auto interp = [&](const double* v, int c, double& u, double& g0, double& g1) {
