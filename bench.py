@@ -419,24 +419,35 @@ def gpu_arm(args, world, rank, local):
     scatter = {"atomic": mfa.MFA_SCATTER_ATOMIC, "colour": mfa.MFA_SCATTER_COLOUR,
                "warp": mfa.MFA_SCATTER_WARP}[args.scatter]
     meshes, spaces, ops = {}, {}, []
+    setup_s = {"mesh_upload": 0.0, "space": 0.0, "forms": 0.0}  # wall time, each creation synchronised
     for c in cases:
         mk = (id(c["mesh"]), hashlib.sha1(np.ascontiguousarray(c["cell_vert"])).hexdigest())
         if mk not in meshes:
+            t0 = time.perf_counter()
             meshes[mk] = mfa.Mesh(ctx, c["cell_type"], c["mesh"].coords, c["cell_vert"])
+            ctx.sync()
+            setup_s["mesh_upload"] += time.perf_counter() - t0
         sk = (mk, c["p"], c["ncomp"])
         if sk not in spaces:
+            t0 = time.perf_counter()
             spaces[sk] = mfa.Space(meshes[mk], c["p"], c["ncomp"], c["cell_node"], c["nnode"])
+            ctx.sync()
+            setup_s["space"] += time.perf_counter() - t0
         prec = {"fp64": mfa.MFA_PREC_FP64, "fp32": mfa.MFA_PREC_FP32, "bf16": mfa.MFA_PREC_BF16}[args.precision]
         if c["cell_type"] != 8:
             prec = mfa.MFA_PREC_FP64
         geo = mfa.MFA_GEOM_ONTHEFLY if (args.geometry == "onthefly" and c["cell_type"] == 8) else mfa.MFA_GEOM_STORED
+        t0 = time.perf_counter()
         form = mfa.Form(spaces[sk], FORM_IDS[c["form"]], scatter=scatter, qdeg=c["qdeg"] if c["cell_type"] == 8 else 0,
                         precision=prec, geometry=geo, **c["kw"])
+        ctx.sync()
+        form_s = time.perf_counter() - t0
+        setup_s["forms"] += form_s
         x = torch.from_numpy(c["x"]).to("cuda")
         y = torch.empty_like(x)
         if c.get("coef") is not None:
             form.set_coefficient(torch.from_numpy(c["coef"]).to("cuda"))
-        ops.append(dict(case=c, form=form, x=x, y=y, info=form.info()))
+        ops.append(dict(case=c, form=form, x=x, y=y, info=form.info(), setup_ms=form_s * 1e3))
     ctx.sync()
     # autotuner: every compiled launch configuration of each form is timed, the fastest kept
     tune_s = 0.0
@@ -593,12 +604,16 @@ def gpu_arm(args, world, rank, local):
                        "frac_fp64": o["info"].flops / ms / 1e9 / FP64_PEAK_TFLOPS,
                        "frac_fp64_executed": o["info"].flops_executed / ms / 1e9 / FP64_PEAK_TFLOPS,
                        "ncolours": o["info"].ncolours,
-                       "launch": dict(o["cfg"].as_dict(), ms=None), "tune": o.get("tune")})
+                       "launch": dict(o["cfg"].as_dict(), ms=None), "tune": o.get("tune"),
+                       "setup_ms": o["setup_ms"]})
     if rank == 0:
         cfg = {"workload": workload_name(args), "operators": [c["name"] for c in cases], "scatter": args.scatter,
                "ndof_per_step": ndof_step, "graph_replay": bool(args.graph),
                "l2": "flushed between steps (256 MiB write outside the timed events)",
                "parallelism": "replicas" if world > 1 else "single",
+               "setup_ms": {k: v * 1e3 for k, v in setup_s.items()},
+               "setup_note": "outside the timed region: mesh upload; space (map upload, colouring); forms (tables, "
+                             "stored geometric factors); each synchronised, wall clock",
                "autotune": None if args.no_autotune else "every compiled launch configuration timed (3 reps, "
                                                           "warm L2) before warm-up; %.2f s" % tune_s}
         if args.workload == "hex":
