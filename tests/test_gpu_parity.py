@@ -312,6 +312,30 @@ def test_cg_matches_dense_solve(ctx, precond):
     np.testing.assert_allclose(xd.cpu().numpy(), xs, rtol=0, atol=1e-8 * np.abs(xs).max())
 
 
+@pytest.mark.parametrize("precond", [mfa.MFA_PC_NONE, mfa.MFA_PC_JACOBI])
+def test_cg_error_decreases_in_the_energy_norm(ctx, precond):
+    """(P)CG minimises the A-norm of the error over a growing Krylov space, so from x0 = 0 the iterate after k
+    steps is at least as close to the solution in that norm as the iterate after k - 1 (dense oracle matrix)."""
+    case = hex_case(3, 2)
+    A = oracle_problem(case, "helmholtz", k2=0.5).dense()
+    b = fi.uniform_vector(case["nnode"], seed=31)
+    xs = np.linalg.solve(A, b)
+    form = gpu_form(ctx, case, "helmholtz", k2=0.5)
+    bd = torch.from_numpy(b).cuda()
+    errs = []
+    for k in range(1, 16):
+        xd = torch.zeros_like(bd)
+        rc, it, rel = form.cg(bd, xd, precond=precond, rtol=1e-30, maxit=k)
+        assert rc == mfa.MFA_ERR_NOT_CONVERGED and it == k
+        e = xd.cpu().numpy() - xs
+        errs.append(float(np.sqrt(e @ A @ e)))
+    e0 = float(np.sqrt(xs @ A @ xs))
+    assert errs[0] < e0
+    for k in range(1, len(errs)):
+        assert errs[k] <= errs[k - 1] * (1 + 1e-12), (k, errs[k - 1], errs[k])
+    assert errs[-1] < 0.5 * errs[0]
+
+
 @pytest.mark.parametrize("inner_prec,inner_iters", [("fp64", 0), ("fp32", 6), ("bf16", 4), ("fp64", 10)])
 def test_fcg_mixed_matches_dense_solve(ctx, inner_prec, inner_iters):
     case = hex_case(4, 2)
