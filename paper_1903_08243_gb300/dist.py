@@ -15,6 +15,14 @@ ghost.  One distributed apply is then
 Scalars of Krylov methods are sums over owned entries, all-reduced.  The
 exchange uses torch.distributed point-to-point messages between neighbouring
 ranks (NCCL between GPUs, gloo on CPU).
+
+The overlapped apply splits a rank's cells into boundary cells (touching a
+node shared with another rank) and interior cells (touching none): after the
+import, the boundary cells are applied first, which completes the partial sums
+at every shared node; the reverse exchange is then in flight while the
+interior cells are applied, since those touch no shared node.  In production
+each part is its own form (two meshes over the rank's node numbering, the
+second applied with accumulate).
 """
 from dataclasses import dataclass, field
 
@@ -34,6 +42,8 @@ class HaloPlan:
     recv_import: dict = field(default_factory=dict)  # ghost nodes whose x comes from the owner
     send_reverse: dict = field(default_factory=dict)  # ghost nodes whose partial y goes to the owner
     recv_reverse: dict = field(default_factory=dict)  # owned nodes receiving partial y from a neighbour
+    boundary_cells: np.ndarray = None  # local cell indices touching a node shared with another rank
+    interior_cells: np.ndarray = None  # local cell indices touching no shared node
 
 
 def contiguous_partition(ncell, nranks):
@@ -75,11 +85,17 @@ def build_plan(cell_node, nnode, nranks, rank, parts=None):
             ids = np.array([g2l[int(g)] for g in theirs], dtype=np.int64)
             plan.recv_import[other] = ids
             plan.send_reverse[other] = ids
+    shared = np.zeros(l2g.size, dtype=bool)
+    for ids in list(plan.send_import.values()) + list(plan.recv_import.values()):
+        shared[ids] = True
+    on_boundary = shared[plan.local_cell_node].any(axis=1)
+    plan.boundary_cells = np.flatnonzero(on_boundary)
+    plan.interior_cells = np.flatnonzero(~on_boundary)
     return plan
 
 
-def _exchange(send, recv, values, combine):
-    """Point-to-point exchange: send values[ids] to each peer, combine received data at ids."""
+def _start_exchange(send, recv, values):
+    """Post the point-to-point messages: values[ids] to each peer, a buffer per peer to receive into."""
     import torch
     import torch.distributed as dist
 
@@ -90,11 +106,23 @@ def _exchange(send, recv, values, combine):
         reqs.append(dist.irecv(buf, src=peer))
     for peer, ids in send.items():
         reqs.append(dist.isend(values[torch.as_tensor(ids, device=values.device)].contiguous(), dst=peer))
+    return reqs, bufs
+
+
+def _finish_exchange(recv, values, combine, pending):
+    import torch
+
+    reqs, bufs = pending
     for r in reqs:
         r.wait()
     for peer, ids in recv.items():
         idx = torch.as_tensor(ids, device=values.device)
         combine(values, idx, bufs[peer])
+
+
+def _exchange(send, recv, values, combine):
+    """Point-to-point exchange: send values[ids] to each peer, combine received data at ids."""
+    _finish_exchange(recv, values, combine, _start_exchange(send, recv, values))
 
 
 def import_ghosts(plan, x_local):
@@ -120,6 +148,24 @@ def distributed_apply(plan, local_apply, x_local):
     return y
 
 
+def distributed_apply_overlapped(plan, apply_boundary, apply_interior, x_local):
+    """distributed_apply with the reverse exchange in flight during the interior cells.
+
+    apply_boundary(x) and apply_interior(x, y) apply the rank's boundary and interior cells
+    (plan.boundary_cells, plan.interior_cells): the first returns a new y, the second adds into y."""
+    import_ghosts(plan, x_local)
+    y = apply_boundary(x_local)  # every shared node's partial sum is now final on this rank
+
+    def add(v, idx, buf):
+        v.index_add_(0, idx, buf)
+
+    pending = _start_exchange(plan.send_reverse, plan.recv_reverse, y)  # partial sums at ghosts -> owners
+    apply_interior(x_local, y)  # touches no shared node: cannot race with the messages
+    _finish_exchange(plan.recv_reverse, y, add, pending)
+    import_ghosts(plan, y)  # ghost copies take the owners' full sums
+    return y
+
+
 def owned_dot(plan, a, b):
     import torch
     import torch.distributed as dist
@@ -130,9 +176,16 @@ def owned_dot(plan, a, b):
     return float(s.item())
 
 
-def distributed_cg(plan, local_apply, b_local, x_local, diag_local=None, rtol=1e-8, maxit=1000):
-    """Jacobi-preconditioned CG over the partitioned operator (reference logic for N > 1)."""
-    r = b_local - distributed_apply(plan, local_apply, x_local.clone())
+def distributed_cg(plan, local_apply, b_local, x_local, diag_local=None, rtol=1e-8, maxit=1000, overlapped=None):
+    """Jacobi-preconditioned CG over the partitioned operator (reference logic for N > 1).
+
+    overlapped: (apply_boundary, apply_interior) to use distributed_apply_overlapped instead."""
+    def dapply(v):
+        if overlapped is not None:
+            return distributed_apply_overlapped(plan, overlapped[0], overlapped[1], v)
+        return distributed_apply(plan, local_apply, v)
+
+    r = b_local - dapply(x_local.clone())
     dinv = None if diag_local is None else 1.0 / diag_local
     z = r if dinv is None else dinv * r
     p = z.clone()
@@ -140,7 +193,7 @@ def distributed_cg(plan, local_apply, b_local, x_local, diag_local=None, rtol=1e
     bnorm = owned_dot(plan, b_local, b_local) ** 0.5
     it, res = 0, owned_dot(plan, r, r) ** 0.5 / bnorm
     while res > rtol and it < maxit:
-        q = distributed_apply(plan, local_apply, p.clone())
+        q = dapply(p.clone())
         alpha = rz / owned_dot(plan, p, q)
         x_local += alpha * p
         r -= alpha * q

@@ -1,8 +1,9 @@
 """Partitioned operator action and CG on 2 gloo ranks (CPU), local applies by the oracle.
 
 Checks the halo plan and the exchange logic of paper_1903_08243_gb300.dist:
-the distributed action equals the single-domain action on every node, and
-distributed CG converges to the dense solution.
+the distributed action (plain, and boundary cells first with the reverse
+exchange overlapping the interior cells) equals the single-domain action on
+every node, and distributed CG converges to the dense solution.
 """
 import os
 import socket
@@ -29,7 +30,7 @@ def _problem(kind):
     if kind == "hex":
         case = hex_case(4, 2)
         return case, oracle_problem(case, "helmholtz")
-    case = tet_case(3, 2, ncomp=3, perturb=0.1, seed=4)
+    case = tet_case(4, 2, ncomp=3, perturb=0.1, seed=4)  # 4^3: each rank keeps interior cells
     return case, oracle_problem(case, "elasticity")
 
 
@@ -58,6 +59,31 @@ def _worker(rank, world, port, kind, out):
         yref = pb.apply(x.reshape(-1)).reshape(-1, nc)
         err_apply = float(np.abs(y.numpy() - yref[plan.l2g]).max() / np.abs(yref).max())
 
+        # boundary cells first, the reverse exchange in flight during the interior cells
+        parts = {}
+        for name, sel in (("boundary", plan.boundary_cells), ("interior", plan.interior_cells)):
+            parts[name] = oracle.Problem(case["cell_type"], case["coords"], case["cell_vert"][plan.cells[sel]],
+                                         case["degree"], np.ascontiguousarray(plan.local_cell_node[sel]),
+                                         plan.l2g.size, pb._s.kind, ncomp=nc, qdeg=pb._s.qdeg)
+
+        def apply_boundary(xl_):
+            return torch.from_numpy(parts["boundary"].apply(xl_.numpy().reshape(-1)).reshape(xl_.shape))
+
+        def apply_interior(xl_, y_):
+            y_ += torch.from_numpy(parts["interior"].apply(xl_.numpy().reshape(-1)).reshape(xl_.shape))
+
+        xl2 = torch.from_numpy(x[plan.l2g].copy())
+        xl2[~torch.from_numpy(plan.owned)] = 0.0
+        y2 = mdist.distributed_apply_overlapped(plan, apply_boundary, apply_interior, xl2)
+        err_apply = max(err_apply, float(np.abs(y2.numpy() - yref[plan.l2g]).max() / np.abs(yref).max()))
+        # interior cells touch no node shared with the other rank, and the two parts cover every cell once
+        shared = np.zeros(plan.l2g.size, dtype=bool)
+        for ids in list(plan.send_import.values()) + list(plan.recv_import.values()):
+            shared[ids] = True
+        split_ok = (not shared[plan.local_cell_node[plan.interior_cells]].any() and len(plan.interior_cells) > 0 and
+                    np.array_equal(np.sort(np.concatenate([plan.boundary_cells, plan.interior_cells])),
+                                   np.arange(len(plan.cells))))
+
         err_cg = 0.0
         if kind == "hex":
             A = pb.dense()
@@ -68,7 +94,10 @@ def _worker(rank, world, port, kind, out):
             xl0 = torch.zeros_like(bl)
             xsol, it, res = mdist.distributed_cg(plan, local_apply, bl, xl0, dl, rtol=1e-12, maxit=500)
             err_cg = float(np.abs(xsol.numpy().ravel() - xs[plan.l2g]).max() / np.abs(xs).max())
-        out[rank] = (err_apply, err_cg, int(plan.owned.sum()))
+            xsol2, it2, res2 = mdist.distributed_cg(plan, None, bl, torch.zeros_like(bl), dl, rtol=1e-12, maxit=500,
+                                                    overlapped=(apply_boundary, apply_interior))
+            err_cg = max(err_cg, float(np.abs(xsol2.numpy().ravel() - xs[plan.l2g]).max() / np.abs(xs).max()))
+        out[rank] = (err_apply, err_cg, int(plan.owned.sum()), bool(split_ok))
     finally:
         dist.destroy_process_group()
 
@@ -82,12 +111,13 @@ def test_partitioned_apply_and_cg_two_ranks(kind):
     mp.start_processes(_worker, args=(world, port, kind, out), nprocs=world, join=True, start_method="spawn")
     assert len(out) == world
     for rank in range(world):
-        err_apply, err_cg, nowned = out[rank]
+        err_apply, err_cg, nowned, split_ok = out[rank]
         assert err_apply <= 1e-13, err_apply
         assert err_cg <= 1e-8, err_cg
+        assert split_ok
     from tests.problems import hex_case, tet_case
 
-    nnode = hex_case(4, 2)["nnode"] if kind == "hex" else tet_case(3, 2, ncomp=3, perturb=0.1, seed=4)["nnode"]
+    nnode = hex_case(4, 2)["nnode"] if kind == "hex" else tet_case(4, 2, ncomp=3, perturb=0.1, seed=4)["nnode"]
     assert sum(out[r][2] for r in range(world)) == nnode  # every node owned exactly once
 
 
