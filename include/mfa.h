@@ -341,8 +341,11 @@ MFA_API int mfa_apply_host_many(mfa_ctx *ctx, int n, mfa_form *const *forms, con
  * wait, since the last mfa_sync (the flag is cleared). */
 MFA_API int mfa_sync(mfa_ctx *ctx);
 
-/* d_i = A_ii (linear forms): the matrix-free diagonal, assembled per cell
- * from the same quadrature as mfa_apply.  d: device, ndof FP64. */
+/* d_i = A_ii (linear forms: mass, Laplace, Helmholtz, vector Laplace,
+ * elasticity): the matrix-free diagonal, assembled per cell from the same
+ * quadrature as mfa_apply, for every cell type and degree.  d: device, ndof
+ * FP64.  MFA_ERR_UNSUPPORTED for the hyperelastic forms, FP32/BF16 forms and
+ * forms without stored geometric factors (on-the-fly geometry). */
 MFA_API int mfa_diagonal(mfa_ctx *ctx, mfa_form *form, double *d);
 
 /* Conjugate gradients on a symmetric positive-definite linear form in FP64.

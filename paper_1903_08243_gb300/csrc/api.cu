@@ -1293,22 +1293,48 @@ int mfa_diagonal(mfa_ctx* ctx, mfa_form* f, double* d) {
   if (!ctx || !f || !d) return fail(MFA_ERR_ARG, "mfa_diagonal: NULL argument");
   if (f->p.kind == MFA_FORM_HYPER_RES || f->p.kind == MFA_FORM_HYPER_JAC)
     return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: linear forms only");
-  if (f->space->mesh->cell_type == MFA_CELL_TET4 && f->space->degree >= 3)
-    return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: tets of degree %d", f->space->degree);
-  if (mfa::is_planar(f->space->mesh->cell_type)) return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: planar cells");
   MFA_CUDA(cudaSetDevice(ctx->device));
   mfa_space* sp = f->space;
+  const int ct = sp->mesh->cell_type;
   const int64_t ndof = sp->nnode * sp->ncomp;
+  if ((ct == MFA_CELL_HEX8 || ct == MFA_CELL_QUAD4) && f->p.precision != MFA_PREC_FP64)
+    return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: FP64 forms only");
+  if ((ct == MFA_CELL_HEX8 || ct == MFA_CELL_QUAD4) && !f->d_geom)
+    return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: needs stored geometric factors");
   MFA_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * ndof, ctx->stream));
   mfa::clear_stale_error();
   cudaError_t e;
-  if (sp->mesh->cell_type == MFA_CELL_HEX8) {
-    if (f->p.precision != MFA_PREC_FP64) return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: FP64 forms only");
-    if (sp->ncomp != 1) return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: scalar hex forms only");
-    if (!f->d_geom) return fail(MFA_ERR_UNSUPPORTED, "mfa_diagonal: needs stored geometric factors");
+  const auto dense_args = [&]() {  // the [q][a] tables of the P3+ tets and the triangles
+    const int dim = ct == MFA_CELL_TRI3 ? 2 : 3;
+    const int64_t nb = (int64_t)sp->nloc * f->tdense_nq;
+    mfa::TetDenseArgs a{};
+    a.coords = sp->mesh->d_coords;
+    a.cell_vert = sp->mesh->d_cell_vert;
+    a.cell_node = sp->d_cell_node;
+    a.count = sp->mesh->ncell;
+    a.phi_aq = f->d_tdense;
+    a.dphi_aeq = a.phi_aq + nb;
+    a.phi_qa = a.dphi_aeq + dim * nb;
+    a.dphi_qae = a.phi_qa + nb;
+    a.w = a.dphi_qae + dim * nb;
+    a.nq = f->tdense_nq;
+    a.k2 = f->p.k2;
+    a.lambda = f->p.lambda;
+    a.mu = f->p.mu;
+    a.err = ctx->d_err;
+    return a;
+  };
+  if (ct == MFA_CELL_HEX8 && sp->ncomp == 1) {
     e = mfa::hex_diagonal_launch(sp->degree + 1, f->nq1, f->p.kind, f->hex, sp->d_cell_node,
                                  static_cast<const double*>(f->d_geom),
                                  sp->mesh->ncell, d, ctx->sm_count, ctx->stream);
+  } else if (ct == MFA_CELL_HEX8 || ct == MFA_CELL_QUAD4) {
+    e = mfa::tensor_diagonal_launch(ct == MFA_CELL_HEX8 ? 3 : 2, sp->ncomp, sp->degree + 1, f->nq1, f->p.kind, f->hex,
+                                    sp->d_cell_node, static_cast<const double*>(f->d_geom), f->gstride,
+                                    sp->mesh->ncell, f->p.lambda, f->p.mu, d, ctx->stream);
+  } else if (ct == MFA_CELL_TRI3 || sp->degree >= 3) {
+    e = mfa::simplex_diagonal_launch(ct == MFA_CELL_TRI3 ? 2 : 3, sp->ncomp, sp->nloc, f->p.kind, dense_args(), d,
+                                     ctx->stream);
   } else {
     mfa::TetApplyArgs a = tet_args(f, nullptr, nullptr);
     e = mfa::tet_diagonal_launch(sp->degree, sp->ncomp, f->p.kind, f->tet, a, d, ctx->stream);

@@ -226,6 +226,14 @@ struct TetDenseArgs {
 };
 cudaError_t tet_dense_launch(int p, int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, int sm_count,
                              cudaStream_t s);
+// Diagonals without a sum-factorised kernel (diag.cu): simplices from the
+// dense [q][a] tables (tets P3..P6, triangles), tensor cells from the 1D
+// tables and stored factors (quads, hex vector forms).
+cudaError_t simplex_diagonal_launch(int dim, int ncomp, int nl, int kind, const TetDenseArgs& a, double* d,
+                                    cudaStream_t s);
+cudaError_t tensor_diagonal_launch(int dim, int ncomp, int n, int nq, int kind, const HexTables& tb,
+                                   const int32_t* cell_node, const double* geom, int64_t gstride, int64_t ncell,
+                                   double lambda, double mu, double* d, cudaStream_t s);
 // Triangles P1..P4, one thread per cell (tri_kernels.cu): tables as a kernel parameter (9.2 KB), at most 25 points.
 constexpr int kTriMaxNl = 15, kTriMaxQ = 25;
 struct TriTables {

@@ -91,8 +91,8 @@ def test_hex_vector_rejections(ctx):
         with pytest.raises(mfa.MfaError) as e:
             make_form(ctx, case, kind, **kw)
         assert e.value.code == mfa.MFA_ERR_UNSUPPORTED
-    form = make_form(ctx, case, "elasticity")
-    with pytest.raises(mfa.MfaError) as e:
+    form = make_form(ctx, case, "hyper_res")
+    with pytest.raises(mfa.MfaError) as e:  # the diagonal covers the linear forms (test_gpu_diag.py)
         form.diagonal()
     assert e.value.code == mfa.MFA_ERR_UNSUPPORTED
     jac = make_form(ctx, case, "hyper_jac")

@@ -94,7 +94,7 @@ def test_tet_pk_unsupported_paths(ctx):
     with pytest.raises(mfa.MfaError) as e:
         make_form(ctx, case, "helmholtz", scatter=mfa.MFA_SCATTER_WARP)
     assert e.value.code == mfa.MFA_ERR_UNSUPPORTED
-    form = make_form(ctx, case, "helmholtz")
-    with pytest.raises(mfa.MfaError) as e:
+    form = make_form(ctx, tet_case(2, 3, ncomp=3), "hyper_res", law=mfa.MFA_LAW_SVK)
+    with pytest.raises(mfa.MfaError) as e:  # the diagonal covers the linear forms (test_gpu_diag.py)
         form.diagonal()
     assert e.value.code == mfa.MFA_ERR_UNSUPPORTED
