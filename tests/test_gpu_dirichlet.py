@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import fe_inputs as fi
-from tests.problems import KIND_NAMES, hex_case, oracle_problem, tet_case
+from tests.problems import KIND_NAMES, hex_case, oracle_problem, quad_case, tet_case, tri_case
 
 pytestmark = pytest.mark.gpu
 
@@ -28,8 +28,12 @@ def make_form(ctx, case, kind, **kw):
 
 
 def clamped_dofs(case):
+    nc = case["ncomp"]
     fixed = np.flatnonzero(case["nodes"][:, 0] < 1e-12)
-    return (3 * fixed[:, None] + np.arange(3)[None, :]).ravel()
+    return (nc * fixed[:, None] + np.arange(nc)[None, :]).ravel()
+
+
+PLANAR = {"quad": lambda seed: quad_case(3, 2, ncomp=2, seed=seed), "tri": lambda seed: tri_case(3, 3, ncomp=2, seed=seed)}
 
 
 def constrained(pb, x, dofs):
@@ -38,11 +42,14 @@ def constrained(pb, x, dofs):
     return r * pb.apply(r * x) + (1.0 - r) * x
 
 
-@pytest.mark.parametrize("cell", ["tet", "hex"])
+@pytest.mark.parametrize("cell", ["tet", "hex", "quad", "tri"])
 def test_constrained_action_matches_the_definition(ctx, cell):
-    case = tet_case(3, 2, ncomp=3, perturb=0.1, seed=2) if cell == "tet" else hex_case(3, 2, ncomp=3)
+    if cell in PLANAR:
+        case = PLANAR[cell](2)
+    else:
+        case = tet_case(3, 2, ncomp=3, perturb=0.1, seed=2) if cell == "tet" else hex_case(3, 2, ncomp=3)
     dofs = clamped_dofs(case)
-    x = fi.uniform_vector(case["nnode"] * 3, seed=21)
+    x = fi.uniform_vector(case["nnode"] * case["ncomp"], seed=21)
     ref = constrained(oracle_problem(case, "elasticity", lam=1.2, mu=0.8), x, dofs)
     form = make_form(ctx, case, "elasticity", lam=1.2, mu=0.8)
     form.set_dirichlet(dofs)
@@ -79,9 +86,13 @@ def test_constrained_diagonal(ctx):
 
 
 @pytest.mark.parametrize("cell, precond", [("tet", mfa.MFA_PC_JACOBI), ("tet", mfa.MFA_PC_NONE),
-                                           ("hex", mfa.MFA_PC_NONE)])
+                                           ("hex", mfa.MFA_PC_NONE), ("hex", mfa.MFA_PC_JACOBI),
+                                           ("quad", mfa.MFA_PC_JACOBI), ("tri", mfa.MFA_PC_JACOBI)])
 def test_clamped_elasticity_cg_matches_dense_solve(ctx, cell, precond):
-    case = tet_case(2, 2, ncomp=3, perturb=0.1, seed=4) if cell == "tet" else hex_case(2, 2, ncomp=3)
+    if cell in PLANAR:
+        case = PLANAR[cell](4)
+    else:
+        case = tet_case(2, 2, ncomp=3, perturb=0.1, seed=4) if cell == "tet" else hex_case(2, 2, ncomp=3)
     dofs = clamped_dofs(case)
     pb = oracle_problem(case, "elasticity")
     A = pb.dense()
