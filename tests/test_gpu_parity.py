@@ -11,7 +11,7 @@ import pytest
 
 import fe_inputs as fi
 import oracle
-from tests.problems import KIND_NAMES, cells_touching, hex_case, oracle_problem, tet_case
+from tests.problems import KIND_NAMES, cells_touching, hex_case, oracle_problem, quad_case, tet_case, tri_case
 
 pytestmark = pytest.mark.gpu
 
@@ -454,6 +454,13 @@ def _batch_inputs(ctx):
     forms.append(f)
     xs.append(torch.from_numpy(x).cuda())
     refs.append((oracle_problem(hcase, "helmholtz").apply(x), 1e-12))
+    # and two planar ones (a quad and a triangle form)
+    for pcase, kind, seed in [(quad_case(4, 3), "helmholtz", 302), (tri_case(4, 2, ncomp=2), "elasticity", 303)]:
+        f = gpu_form(ctx, pcase, kind)
+        x = fi.uniform_vector(pcase["nnode"] * pcase["ncomp"], seed=seed)
+        forms.append(f)
+        xs.append(torch.from_numpy(x).cuda())
+        refs.append((oracle_problem(pcase, kind).apply(x), 1e-12))
     return forms, xs, refs
 
 
@@ -477,7 +484,7 @@ def test_batch_graph_replay(ctx):
     b = mfa.mfa_batch_create(ctx.h, [f.h for f in forms], xs, ys)
     try:
         ngroups, nsingles = mfa.mfa_batch_info(b)
-        assert nsingles == 2 and ngroups == 7  # (1,H,64) (2,L,64) (3,M,32) (3,H,32) (4,H,16) (2,H,32) (8,H,64)
+        assert nsingles == 4 and ngroups == 7  # (1,H,64) (2,L,64) (3,M,32) (3,H,32) (4,H,16) (2,H,32) (8,H,64)
         for y in ys:
             y.fill_(-1.0)
         for _ in range(2):
