@@ -231,10 +231,9 @@ int hex_tables(mfa_form* f) {
   return MFA_OK;
 }
 
-// Tet rule: polynomial integrands of degree <= qdeg are integrated exactly by
-// any exact rule, so the kernel takes the cheapest exact one it has; other
-// integrands (neo-Hookean, under-integration) use the conical-product rule
-// of degree qdeg, which defines the result.
+// Simplex rules come from simplex_rule_choice (below): the symmetric rule where
+// the integral is exact (or the form asks for MFA_RULE_SYMMETRIC), else the
+// collapsed rule of degree qdeg, which then defines the result.
 // P3..P6: dense tables in device memory for the warp-per-cell kernel (layouts in TetDenseArgs).
 static int tet_dense_tables(mfa_form* f, const std::vector<double>& pts, const std::vector<double>& w) {
   const int p = f->space->degree, nl = f->space->nloc;
