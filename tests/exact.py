@@ -3,7 +3,6 @@
 Everything here uses either closed forms or numpy's polynomial routines; none
 of it calls the oracle's quadrature, basis or geometry code.
 """
-import itertools
 import math
 
 import numpy as np
