@@ -103,7 +103,7 @@ int32_t quad_node_id(const int32_t* cv, int p, int i, int j, int64_t cell, Numbe
 }
 
 // P_p node with barycentric weights b[3] (sum p) on the triangle's local vertices.
-int32_t tri_node_id(const int32_t* cv, int p, const int b[3], int64_t cell, Numbering& num) {
+int32_t tri_node_id(const int32_t* cv, const int b[3], int64_t cell, Numbering& num) {
   int support[3], ns = 0;
   for (int s = 0; s < 3; ++s)
     if (b[s] > 0) support[ns++] = s;
@@ -191,7 +191,7 @@ extern "C" int mfa_build_cell_node(int cell_type, int degree, int64_t ncell, con
       for (int j = 0; j <= p; ++j)
         for (int i = 0; i <= p - j; ++i, ++a) {
           const int b[3] = {p - i - j, i, j};
-          cell_node[c * nl + a] = tri_node_id(cell_vert + 3 * c, p, b, c, num);
+          cell_node[c * nl + a] = tri_node_id(cell_vert + 3 * c, b, c, num);
         }
     }
   } else {
