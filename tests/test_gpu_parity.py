@@ -429,7 +429,8 @@ def _batch_inputs(ctx):
     rng = np.random.default_rng(77)
     forms, xs, refs = [], [], []
     specs = [(1, "helmholtz", "fp64"), (2, "laplace", "fp64"), (2, "laplace", "fp64"), (3, "mass", "fp32"),
-             (3, "helmholtz", "fp32"), (4, "helmholtz", "bf16"), (2, "helmholtz", "fp32"), (8, "helmholtz", "fp64")]
+             (3, "helmholtz", "fp32"), (4, "helmholtz", "bf16"), (2, "helmholtz", "fp32"), (8, "helmholtz", "fp64"),
+             (5, "helmholtz", "fp64")]
     keep = []
     for i, (p, kind, prec) in enumerate(specs):
         nx = int(rng.integers(2, 5))
@@ -484,7 +485,8 @@ def test_batch_graph_replay(ctx):
     b = mfa.mfa_batch_create(ctx.h, [f.h for f in forms], xs, ys)
     try:
         ngroups, nsingles = mfa.mfa_batch_info(b)
-        assert nsingles == 4 and ngroups == 7  # (1,H,64) (2,L,64) (3,M,32) (3,H,32) (4,H,16) (2,H,32) (8,H,64)
+        # (1,H,64) (2,L,64) (3,M,32) (3,H,32) (4,H,16) (2,H,32) (8,H,64) (5,H,64: the even-odd group kernel)
+        assert nsingles == 4 and ngroups == 8
         for y in ys:
             y.fill_(-1.0)
         for _ in range(2):
