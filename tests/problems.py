@@ -104,3 +104,16 @@ def cells_touching(cell_node, dofs, ncomp=1):
     nodes = np.unique(np.asarray(dofs) // ncomp)
     mask = np.isin(cell_node, nodes).any(axis=1)
     return np.nonzero(mask)[0]
+
+
+def assembled_dense(pb, case):
+    """The global matrix assembled from the oracle's element matrices (local dofs a * ncomp + c): the same matrix
+    as pb.dense(), one oracle call per cell instead of one per dof."""
+    nc, cn = case["ncomp"], case["cell_node"]
+    n = case["nnode"] * nc
+    A = np.zeros((n, n))
+    for cell in range(cn.shape[0]):
+        Ae = pb.element_matrix(cell)
+        dofs = (nc * cn[cell][:, None] + np.arange(nc)[None, :]).ravel()
+        A[np.ix_(dofs, dofs)] += Ae
+    return A

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import fe_inputs as fi
-from tests.problems import KIND_NAMES, hex_case, oracle_problem, quad_case, tet_case, tri_case
+from tests.problems import KIND_NAMES, assembled_dense, hex_case, oracle_problem, quad_case, tet_case, tri_case
 
 pytestmark = pytest.mark.gpu
 
@@ -81,7 +81,7 @@ def test_jacobi_pcg(ctx, which):
     case = {"quad-Q3": lambda: quad_case(5, 3), "tri-P4": lambda: tri_case(5, 4),
             "tet-P3": lambda: tet_case(2, 3, perturb=0.1, seed=3)}[which]()
     kw = {"k2": 1.0}
-    A = oracle_problem(case, "helmholtz", **kw).dense()
+    A = assembled_dense(oracle_problem(case, "helmholtz", **kw), case)
     b = fi.uniform_vector(case["nnode"], seed=12)
     xs = np.linalg.solve(A, b)
     form = make(ctx, case, "helmholtz", **kw)

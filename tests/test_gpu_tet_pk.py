@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import fe_inputs as fi
-from tests.problems import KIND_NAMES, oracle_problem, tet_case
+from tests.problems import KIND_NAMES, assembled_dense, oracle_problem, tet_case
 
 pytestmark = pytest.mark.gpu
 
@@ -79,7 +79,7 @@ def test_tet_pk_shuffled_numbering_and_cg(ctx):
     ctx.sync()
     check(y.cpu().numpy(), pb.apply(x))
     # the Helmholtz operator is SPD: plain CG reaches the dense solution
-    A = pb.dense()
+    A = assembled_dense(pb, case)
     b = fi.uniform_vector(case["nnode"], seed=71)
     bd = torch.from_numpy(b).cuda()
     xs = torch.zeros_like(bd)

@@ -550,3 +550,17 @@ def test_tet_pk_elasticity_rigid_modes_and_hyper_rotation(p):
     ph, _, _ = tet_problem(2, p, oracle.HYPER_RES, perturb=0.15, seed=6, ncomp=3, law=oracle.NEOHOOKE, qdeg=2 * p)
     R = _rotation(0.5, [1, 1, -2])
     assert np.abs(ph.apply((nodes @ R.T - nodes).ravel())).max() < 1e-12
+
+
+@pytest.mark.parametrize("which", ["tet-P2-elasticity", "quad-Q2-helmholtz", "tri-P3-laplace"])
+def test_element_matrix_assembly_equals_unit_vector_matrix(which):
+    """The assembled element matrices and the action on every unit vector give the same global matrix (the
+    faster assembly stands in for dense() in the larger GPU tests)."""
+    from tests.problems import assembled_dense, oracle_problem, quad_case, tet_case, tri_case
+
+    case, kind = {"tet-P2-elasticity": (tet_case(1, 2, ncomp=3, perturb=0.1, seed=3), "elasticity"),
+                  "quad-Q2-helmholtz": (quad_case(2, 2), "helmholtz"),
+                  "tri-P3-laplace": (tri_case(2, 3), "laplace")}[which]
+    pb = oracle_problem(case, kind)
+    A1, A2 = pb.dense(), assembled_dense(pb, case)
+    assert np.abs(A1 - A2).max() <= 1e-14 * np.abs(A1).max()
