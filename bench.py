@@ -543,7 +543,7 @@ def gpu_arm(args, world, rank, local):
         kname = kbase + "<n=%d,%s,cb=%d>" % (dom["case"]["p"] + 1, dom["case"]["form"], dom["cfg"].cells_per_block)
     else:
         moment = dom["case"]["p"] == 2 and dom["case"]["form"] in ("hyper_res", "hyper_jac")
-        kname = "tet_dense_kernel<%s>" if dom["case"]["p"] >= 3 else (
+        kname = "simplex_dense_kernel<DIM=3, %s>" if dom["case"]["p"] >= 3 else (
             "tet_moment_kernel<%s>" if moment else "tet_apply_kernel<%s>")
         if dom["case"]["cell_type"] == 40:
             kname = "quad_apply_kernel<%s>"
