@@ -174,3 +174,38 @@ def test_2d_hyper_energy_gradient_jacobian_and_linearisation(law, cell):
     kwe = {k: v for k, v in kw.items() if k != "law"}
     pe, _, _ = make(2, 2, oracle.ELASTICITY, **kwe)
     np.testing.assert_allclose(pz.apply(d), pe.apply(d), rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("kind, law", [("elasticity", oracle.SVK), ("hyper_res", oracle.SVK),
+                                       ("hyper_res", oracle.NEOHOOKE)])
+def test_plane_strain_is_the_z_invariant_3d_problem(p, kind, law):
+    """Plane strain pinned to the 3D oracle: the quad mesh extruded one unit in z as hexahedra, with the in-plane
+    displacement (u1, u2, 0) at every z-level, gives residuals whose sums over each column of z-nodes equal the
+    quad residual (in-plane components) and vanish (z component). The z-invariant test function is the sum of the
+    column's z basis functions, so the 3D weak form reduces to the 2D one times the unit thickness."""
+    from tests.problems import quad_case
+
+    q = quad_case(3, p, ncomp=2, seed=4)
+    nq, nvq = q["nnode"], q["coords"].shape[0]
+    n = p + 1
+    # extruded mesh: vertex v + nvq * k at height k, hex local vertex a + 2b + 4c over quad local vertex a + 2b
+    coords = np.vstack([np.column_stack([q["coords"][:, :2], np.full(nvq, float(k))]) for k in (0, 1)])
+    cv = np.hstack([q["cell_vert"], q["cell_vert"] + nvq]).astype(np.int32)
+    # hex node (quad node, z-level k): quad node + nq * k; local hex node aq + n^2 * k
+    cn = np.hstack([q["cell_node"] + nq * k for k in range(n)]).astype(np.int32)
+    u2 = fi.sinusoid_displacement(q["nodes"], seed=5)[:, :2]
+    u3 = np.zeros((nq * n, 3))
+    for k in range(n):
+        u3[nq * k:nq * (k + 1), :2] = u2
+    kw = dict(lam=1.1, mu=0.7, law=law)
+    if kind == "hyper_res":
+        kw["b"] = (0.05, -0.02, 0.0)
+    okind = {"elasticity": oracle.ELASTICITY, "hyper_res": oracle.HYPER_RES}[kind]
+    r2 = oracle.Problem(oracle.QUAD, q["coords"], q["cell_vert"], p, q["cell_node"], nq, okind, ncomp=2,
+                        qdeg=p + 1, **kw).apply(u2.ravel()).reshape(-1, 2)
+    r3 = oracle.Problem(oracle.HEX, coords, cv, p, cn, nq * n, okind, ncomp=3, qdeg=p + 1,
+                        **kw).apply(u3.ravel()).reshape(n, nq, 3).sum(axis=0)
+    scale = np.abs(r2).max()
+    assert np.abs(r3[:, :2] - r2).max() <= 1e-12 * scale
+    assert np.abs(r3[:, 2]).max() <= 1e-12 * scale
