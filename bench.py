@@ -786,6 +786,15 @@ def pcg_arm(args, world, rank, local):
     A32 = mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ, k2=1.0, precision=iprec)
     M64 = mfa.Form(sp, mfa.MFA_FORM_MASS)
     rtol = 1e-8
+    # the solver's operators take the autotuner's launch configuration (setup, outside every timed solve)
+    tune_x = torch.rand(sp.ndof, dtype=torch.float64, device="cuda")
+    tune_y = torch.empty_like(tune_x)
+    tuned = {}
+    for name, F in (("fp64 outer", A64), ("inner", A32)):
+        if not args.no_autotune:
+            F.autotune(tune_x, tune_y)
+        tuned[name] = F.config().as_dict()
+    del tune_x, tune_y
 
     def grf_rhs(seed):
         f = torch.from_numpy(fi.grf_lattice(nx * p + 1, seed=seed)).cuda()
@@ -861,6 +870,7 @@ def pcg_arm(args, world, rank, local):
                        "rhs": "b = M f_h, f a Gaussian random field (256 random Fourier features, correlation length 0.1) "
                               "on the node lattice; training seeds 300.., test seeds 401..",
                        "stop": "FP64 ||b - A x||_2 <= 1e-8 ||b||_2 from x = 0",
+                       "operators": tuned,
                        "learned": "flexible CG (FP64 operator) preconditioned by %d steps of PCG with the %s operator "
                                   "and the learned linear element preconditioner" % (args.inner, args.inner_precision),
                        "training": {"data": args.train_data, "rhs": args.train_rhs, "plain_cg_iterates": list(its),
@@ -895,6 +905,10 @@ def pcg_elasticity_arm(args, world, rank, local):
     m = mfa.Mesh(ctx, mfa.MFA_CELL_TET4, mesh.coords, mesh.cell_vert)
     sp = mfa.Space(m, 2, 3, cn, nnode)
     A = mfa.Form(sp, mfa.MFA_FORM_ELASTICITY, lam=1.0, mu=1.0)
+    if not args.no_autotune:  # the operator's launch configuration (setup, outside the timed solves)
+        tx = torch.rand(3 * nnode, dtype=torch.float64, device="cuda")
+        A.autotune(tx, torch.empty_like(tx))
+        del tx
     clamped = np.flatnonzero(nodes[:, 0] < 1e-12)
     dofs = (3 * clamped[:, None] + np.arange(3)[None, :]).ravel()
     A.set_dirichlet(dofs)
@@ -933,7 +947,8 @@ def pcg_elasticity_arm(args, world, rank, local):
                        "constrained_dofs": int(dofs.size), "lambda": 1.0, "mu": 1.0,
                        "rhs": "f_i = int b . phi_i, b = (0, 0, -1); zero at the clamped dofs",
                        "boundary": "clamped (u = 0) on the face x = 0, traction-free elsewhere",
-                       "stop": "FP64 ||b - A_D u||_2 <= 1e-8 ||b||_2 from u = 0"},
+                       "stop": "FP64 ||b - A_D u||_2 <= 1e-8 ||b||_2 from u = 0",
+                       "operator": A.config().as_dict()},
             "cg_fp64_seconds": tc, "jacobi_pcg_fp64_seconds": tj, "jacobi_speedup": tc / tj, "solves": rows,
             "clocks": clocks, "roofline": None, "cpu_baseline": None, "e2e": None,
         }
