@@ -52,21 +52,51 @@ def contiguous_partition(ncell, nranks):
     return [(int(bounds[r]), int(bounds[r + 1])) for r in range(nranks)]
 
 
+def rcb_partition(coords, cell_vert, nranks):
+    """Recursive coordinate bisection of the cells by their centroids: each split cuts the longest extent of
+    the current set at the cell count proportional to the ranks on either side.  Compact parts whatever the
+    cell numbering (shuffled or unstructured meshes), so halos stay small.  Returns sorted cell ids per rank."""
+    cent = np.asarray(coords)[np.asarray(cell_vert)].mean(axis=1)
+    out = []
+
+    def split(ids, k):
+        if k == 1:
+            out.append(np.sort(ids))
+            return
+        ext = cent[ids].max(axis=0) - cent[ids].min(axis=0)
+        axis = int(np.argmax(ext))
+        order = ids[np.argsort(cent[ids, axis], kind="stable")]
+        k0 = k // 2
+        cut = int(round(len(ids) * k0 / k))
+        split(order[:cut], k0)
+        split(order[cut:], k - k0)
+
+    split(np.arange(len(cent), dtype=np.int64), nranks)
+    return out
+
+
+def _part_cells(part):
+    """A part given as a (start, end) range or as an array of cell ids."""
+    if isinstance(part, tuple):
+        return np.arange(part[0], part[1], dtype=np.int64)
+    return np.asarray(part, dtype=np.int64)
+
+
 def build_plan(cell_node, nnode, nranks, rank, parts=None):
-    """Halo plan of `rank`; every rank computes the same global ownership."""
+    """Halo plan of `rank`; every rank computes the same global ownership.  parts: per rank a (start, end) range
+    or an array of cell ids (contiguous_partition, rcb_partition); default contiguous ranges."""
     ncell = cell_node.shape[0]
     parts = parts or contiguous_partition(ncell, nranks)
     touch_min = np.full(nnode, nranks, dtype=np.int64)  # owner = lowest rank touching the node
     touched_by = [None] * nranks
-    for r, (s, e) in enumerate(parts):
-        nodes = np.unique(cell_node[s:e])
+    for r, part in enumerate(parts):
+        nodes = np.unique(cell_node[_part_cells(part)])
         touched_by[r] = nodes
         touch_min[nodes] = np.minimum(touch_min[nodes], r)
-    s, e = parts[rank]
-    cells = np.arange(s, e, dtype=np.int64)
-    l2g, local = np.unique(cell_node[s:e], return_inverse=True)
+    cells = _part_cells(parts[rank])
+    l2g, local = np.unique(cell_node[cells], return_inverse=True)
     plan = HaloPlan(rank=rank, nranks=nranks, cells=cells,
-                    local_cell_node=local.reshape(e - s, -1).astype(np.int32), l2g=l2g,
+                    local_cell_node=local.reshape(len(cells), -1).astype(np.int32), l2g=l2g,
                     owned=touch_min[l2g] == rank)
     g2l = {int(g): i for i, g in enumerate(l2g)}
     for other in range(nranks):
@@ -164,6 +194,11 @@ def distributed_apply_overlapped(plan, apply_boundary, apply_interior, x_local):
     _finish_exchange(plan.recv_reverse, y, add, pending)
     import_ghosts(plan, y)  # ghost copies take the owners' full sums
     return y
+
+
+def halo_nodes(plan):
+    """Ghost nodes of the plan (nodes this rank touches and another rank owns)."""
+    return int((~plan.owned).sum())
 
 
 def owned_dot(plan, a, b):

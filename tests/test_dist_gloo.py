@@ -30,6 +30,9 @@ def _problem(kind):
     if kind == "hex":
         case = hex_case(4, 2)
         return case, oracle_problem(case, "helmholtz")
+    if kind == "hex-shuffled-rcb":
+        case = hex_case(4, 2, shuffle=True)
+        return case, oracle_problem(case, "helmholtz")
     case = tet_case(4, 2, ncomp=3, perturb=0.1, seed=4)  # 4^3: each rank keeps interior cells
     return case, oracle_problem(case, "elasticity")
 
@@ -45,7 +48,8 @@ def _worker(rank, world, port, kind, out):
 
         case, pb = _problem(kind)
         nc = case["ncomp"]
-        plan = mdist.build_plan(case["cell_node"], case["nnode"], world, rank)
+        parts = mdist.rcb_partition(case["coords"], case["cell_vert"], world) if kind.endswith("rcb") else None
+        plan = mdist.build_plan(case["cell_node"], case["nnode"], world, rank, parts)
         local = oracle.Problem(case["cell_type"], case["coords"], case["cell_vert"][plan.cells], case["degree"],
                                plan.local_cell_node, plan.l2g.size, pb._s.kind, ncomp=nc, qdeg=pb._s.qdeg)
 
@@ -85,7 +89,7 @@ def _worker(rank, world, port, kind, out):
                                    np.arange(len(plan.cells))))
 
         err_cg = 0.0
-        if kind == "hex":
+        if kind.startswith("hex"):
             A = pb.dense()
             b = fi.uniform_vector(case["nnode"], seed=10)
             xs = np.linalg.solve(A, b)
@@ -102,7 +106,7 @@ def _worker(rank, world, port, kind, out):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("kind", ["hex", "tet"])
+@pytest.mark.parametrize("kind", ["hex", "tet", "hex-shuffled-rcb"])
 def test_partitioned_apply_and_cg_two_ranks(kind):
     world = 2
     mgr = mp.get_context("spawn").Manager()
@@ -117,7 +121,7 @@ def test_partitioned_apply_and_cg_two_ranks(kind):
         assert split_ok
     from tests.problems import hex_case, tet_case
 
-    nnode = hex_case(4, 2)["nnode"] if kind == "hex" else tet_case(4, 2, ncomp=3, perturb=0.1, seed=4)["nnode"]
+    nnode = hex_case(4, 2)["nnode"] if kind.startswith("hex") else tet_case(4, 2, ncomp=3, perturb=0.1, seed=4)["nnode"]
     assert sum(out[r][2] for r in range(world)) == nnode  # every node owned exactly once
 
 
@@ -133,3 +137,21 @@ def test_plan_ownership_three_ranks():
         for peer, ids in p.send_import.items():
             assert np.array_equal(np.sort(plans[peer].l2g[plans[peer].recv_import[p.rank]]), np.sort(p.l2g[ids]))
     assert np.all(owned == 1)
+
+
+@pytest.mark.parametrize("nranks", [2, 3, 5])
+def test_rcb_partition_is_balanced_and_compact(nranks):
+    """Recursive coordinate bisection covers every cell once, balances the counts to one cell, and on a shuffled
+    numbering keeps the halos far smaller than contiguous cell ranges."""
+    from paper_1903_08243_gb300 import dist as mdist
+    from tests.problems import hex_case
+
+    case = hex_case(6, 2, shuffle=True)
+    ncell = case["cell_vert"].shape[0]
+    parts = mdist.rcb_partition(case["coords"], case["cell_vert"], nranks)
+    assert np.array_equal(np.sort(np.concatenate(parts)), np.arange(ncell))
+    sizes = [len(p) for p in parts]
+    assert max(sizes) - min(sizes) <= 1
+    halo = lambda ps: sum(mdist.halo_nodes(mdist.build_plan(case["cell_node"], case["nnode"], nranks, r, ps))  # noqa
+                          for r in range(nranks))
+    assert halo(parts) * 4 < halo(None)
