@@ -67,6 +67,9 @@ def parse_args():
                          "(neo-Hookean residual, St Venant-Kirchhoff Jacobian action)")
     ap.add_argument("--scatter", choices=["atomic", "colour", "warp"], default="atomic",
                     help="scatter at form creation (the autotuner may change it)")
+    ap.add_argument("--rule", choices=["auto", "symmetric"], default="auto",
+                    help="simplices: the cheapest exact rule where the integrand is a polynomial (auto), or Table 2's "
+                         "symmetric rules whatever the integrand (symmetric; changes the neo-Hookean result)")
     ap.add_argument("--geometry", choices=["stored", "onthefly"], default="stored",
                     help="hex FP64: geometric factors stored at setup, or recomputed at every point from the vertices")
     ap.add_argument("--order", choices=["lex", "shuffled", "rcm"], default="lex",
@@ -84,7 +87,8 @@ FORM_IDS = {"mass": 0, "laplace": 1, "helmholtz": 2, "elasticity": 3, "hyper_res
 
 def workload_name(args):
     return (_workload_name(args) + ("" if args.order == "lex" else "-order-" + args.order) +
-            ("-geometry-onthefly" if args.geometry == "onthefly" else ""))
+            ("-geometry-onthefly" if args.geometry == "onthefly" else "") +
+            ("-rule-symmetric" if args.rule == "symmetric" else ""))
 
 
 def renumber(args, cell_vert, cell_node, nnode, nvert, vectors):
@@ -223,6 +227,8 @@ def build_cases(args):
                           okw=dict(lam=1.0, mu=1.0, law=1), qdeg=4))
     for c in cases:
         c["ndof"] = c["nnode"] * c["ncomp"]
+        if getattr(args, "rule", "auto") == "symmetric" and c["cell_type"] in (3, 4):
+            c["okw"] = dict(c["okw"], rule="symmetric")  # the oracle legs integrate with the same rules
     return cases
 
 
@@ -438,8 +444,9 @@ def gpu_arm(args, world, rank, local):
             prec = mfa.MFA_PREC_FP64
         geo = mfa.MFA_GEOM_ONTHEFLY if (args.geometry == "onthefly" and c["cell_type"] == 8) else mfa.MFA_GEOM_STORED
         t0 = time.perf_counter()
+        rule = mfa.MFA_RULE_SYMMETRIC if (args.rule == "symmetric" and c["cell_type"] in (3, 4)) else mfa.MFA_RULE_AUTO
         form = mfa.Form(spaces[sk], FORM_IDS[c["form"]], scatter=scatter, qdeg=c["qdeg"] if c["cell_type"] == 8 else 0,
-                        precision=prec, geometry=geo, **c["kw"])
+                        precision=prec, geometry=geo, rule=rule, **c["kw"])
         ctx.sync()
         form_s = time.perf_counter() - t0
         setup_s["forms"] += form_s
@@ -629,20 +636,25 @@ def gpu_arm(args, world, rank, local):
         elif args.workload == "planar":
             cfg.update({"mesh": "%d^2 quads and %d^2 boxes x 2 triangles, unit square, interior vertices perturbed "
                                 "U[-0.1h,0.1h], seed 1" % (args.nx, args.nx // 2),
-                        "quadrature": "quads: p+1 Gauss points per direction; triangles: collapsed rule exact for the "
-                                      "polynomial integrand", "vector forms": "plane strain, lambda = mu = 1",
+                        "quadrature": "quads: p+1 Gauss points per direction; triangles: the cheapest rule exact for "
+                                      "the polynomial integrand (Table 2's symmetric rules up to degree 6)",
+                        "vector forms": "plane strain, lambda = mu = 1",
                         "input": "scalar x ~ U[-1,1) seed 0; vector: sinusoid displacement seed 2"})
         elif args.workload == "tet-pk":
             cfg.update({"mesh": "%d^3 boxes x 6 Kuhn tets" % args.nx,
-                        "quadrature": "collapsed Gauss-Jacobi, exact for the polynomial integrand (degree 2p mass/"
-                                      "Helmholtz, 2p-2 Laplace/elasticity; hyperelastic max(4, 2p))",
+                        "quadrature": "the cheapest rule exact for the polynomial integrand (degree 2p mass/Helmholtz, "
+                                      "2p-2 Laplace/elasticity): Table 2's symmetric rules up to degree 6 (P3: 24 / "
+                                      "14 points), collapsed Gauss-Jacobi above",
                         "basis": "equispaced lattice Lagrange", "lambda": 1.0, "mu": 1.0,
                         "input": "scalar x ~ U[-1,1) seed 0; vector: sinusoid displacement seed 2"})
         elif args.workload == "tet-p1-mass":
             cfg.update({"mesh": "%d^3 boxes x 6 Kuhn tets" % args.nx, "quadrature": "degree 2",
                         "input": "x ~ U[-1,1) seed 0"})
         else:
-            cfg.update({"mesh": "%d^3 boxes x 6 Kuhn tets" % args.nx, "quadrature": "degree 4",
+            cfg.update({"mesh": "%d^3 boxes x 6 Kuhn tets" % args.nx,
+                        "quadrature": "elasticity: the 4-point degree-2 rule (exact); neo-Hookean: degree 4, the "
+                                      "27-point collapsed rule, or Table 2's 14-point symmetric rule with --rule "
+                                      "symmetric",
                         "lambda": 1.0, "mu": 1.0, "input": "sinusoid displacement, 8 terms, amplitude 0.05, seed 2"})
         line = {
             "metric": "operator-action GDoF/s", "value": value, "unit": "GDoF/s", "n_gpus": world,
