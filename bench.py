@@ -334,7 +334,7 @@ def sub_mesh(case, ncell_sample):
 
 # Cells per oracle sample: about 1-2.5 s of oracle work per operator for the
 # baseline, about 0.1 s per operator and step for the reference arm.
-SAMPLE_BASELINE = {("quad", 1): 200000, ("quad", 2): 100000, ("quad", 3): 50000, ("quad", 4): 25000,
+SAMPLE_CPU_LEG = {("quad", 1): 200000, ("quad", 2): 100000, ("quad", 3): 50000, ("quad", 4): 25000,
                    ("tri", 1): 100000, ("tri", 2): 50000, ("tri", 3): 20000, ("tri", 4): 10000, ("tet", 3): 6000, ("tet", 4): 1500, ("tet", 5): 400, ("tet", 6): 150,("hex", 1): 262144, ("hex", 2): 64000, ("hex", 3): 21952, ("hex", 4): 8000, ("hex", 5): 2744,
                    ("hex", 6): 1728, ("hex", 7): 512, ("hex", 8): 216, ("tet", 1): 3072, ("tet", 2): 200000,
                    ("hexv", 1): 110592, ("hexv", 2): 24000, ("hexv", 3): 4000, ("hexv", 4): 1000, ("hexv", 5): 250,
@@ -597,7 +597,7 @@ def gpu_arm(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = oracle_rate(cases, samples=SAMPLE_BASELINE)
+        r = oracle_rate(cases, samples=SAMPLE_CPU_LEG)
         full_s = sum(o["full_s"] for o in r)
         cpu = {"value": ndof_step / full_s / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
                "sample": "per operator the first n/2 and n cells of the mesh (%s), each timed once; full-mesh time = "
