@@ -50,3 +50,31 @@ def test_reference_arm_under_torchrun_prints_once():
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1 and json.loads(lines[0])["n_gpus"] == 2
+
+
+def test_all_cores_oracle_timing_splits_cells_exactly():
+    """The all-cores CPU figure runs the unchanged oracle on disjoint cell shares in spawned processes; the
+    reduced result equals one oracle apply over the whole sample."""
+    import argparse
+    import importlib.util
+
+    import oracle
+
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    sys.modules["bench"] = bench
+    spec.loader.exec_module(bench)
+    args = argparse.Namespace(workload="tet-p2", nx=3, degrees=None, forms=None, order="lex", rule="auto",
+                              geometry="stored", precision="fp64")
+    cases = bench.build_cases(args)
+    single = bench.oracle_rate(cases, samples={("tet", 2): 100})
+    for workers in (2, 3):
+        allc = bench.oracle_rate_all_cores(cases, single, workers)
+        for c, s, a in zip(cases, single, allc):
+            cv, cn, nodes, nsub = bench.sub_mesh(c, s["sample_cells"])
+            xs = c["x"].reshape(-1, c["ncomp"])[nodes].ravel()
+            pb = oracle.Problem(c["cell_type"], c["mesh"].coords, cv, c["p"], cn, nodes.size,
+                                bench.FORM_IDS[c["form"]], ncomp=c["ncomp"], qdeg=c["qdeg"], **c["okw"])
+            ref = float(pb.apply(xs).sum())
+            assert a["sample_cells"] == nsub and a["full_s"] > 0
+            assert abs(a["checksum"] - ref) <= 1e-12 * max(1.0, abs(ref))
