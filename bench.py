@@ -401,7 +401,8 @@ def oracle_rate_all_cores(cases, single, workers):
 
     out = []
     with mp.get_context("spawn").Pool(workers) as pool:
-        pool.map(abs, range(workers))  # start every worker before timing
+        # start every worker before timing; every wait is bounded (a lost worker raises, the pool is terminated)
+        pool.map_async(abs, range(workers)).get(timeout=300)
         for c, s in zip(cases, single):
             cv, cn, nodes, nsub = sub_mesh(c, s["sample_cells"])
             verts, cv_local = np.unique(cv, return_inverse=True)
@@ -411,7 +412,7 @@ def oracle_rate_all_cores(cases, single, workers):
             tasks = [(c["cell_type"], c["mesh"].coords[verts], cv_local.reshape(cv.shape).astype(np.int32), c["p"],
                       cn, nodes.size, FORM_IDS[c["form"]], c["ncomp"], c["qdeg"], coef, c["okw"], xs, ch)
                      for ch in chunks if ch.size]
-            res = pool.map(_oracle_chunk_apply, tasks)
+            res = pool.map_async(_oracle_chunk_apply, tasks).get(timeout=300)
             t0 = time.perf_counter()
             y = np.sum([r[1] for r in res], axis=0)
             wall = max(r[0] for r in res) + (time.perf_counter() - t0)
