@@ -17,10 +17,11 @@
 // consumed its factors, so the copy overlaps the transposed sweeps, the
 // scatter and the next gather.  Each cell's factor block is padded to 16
 // bytes for the copy.  Waits are bounded: on timeout the kernel sets error
-// bit 4 and every thread leaves.  The FP32 variant reads its factors directly
-// (point-parallel, coalesced): its stage would be twice as large, and the
-// shared memory it takes costs more in residency than the copy saves
-// (measured on GB300: Q6 FP32 1.97 ms staged against 1.40 ms direct).
+// bit 4 and every thread leaves.  FP32 reads its factors directly by default
+// (point-parallel, coalesced): its stage is twice as large, and the shared
+// memory it takes can cost more in residency than the copy saves.  The staged
+// form is compiled for FP32 as well (MFA_VARIANT_LINE_STAGED), and the
+// autotuner takes it where it is faster (most FP32 operators on 64^3).
 #pragma once
 
 #include <cuda_bf16.h>
