@@ -269,6 +269,14 @@ MFA_API int mfa_form_set_dirichlet(mfa_form *form, const int32_t *dofs, int64_t 
  *  - scatter: MFA_SCATTER_ATOMIC, or (FP64 only) MFA_SCATTER_COLOUR or MFA_SCATTER_WARP.
  *  - geometry: stored factors or on-the-fly (the FP64 scalar point kernel; a
  *    form created with on-the-fly geometry has no stored factors to switch to).
+ *  - max_blocks: 0 (default) sizes each persistent launch as one wave of
+ *    resident blocks on every SM (fewer when there are fewer batches of
+ *    cells); k > 0 caps the grid at k blocks, so that each block walks more
+ *    batches.  The result does not depend on it (up to the rounding order of
+ *    the atomic scatter).  It exists to exercise the multi-batch path of the
+ *    persistent kernels on small meshes, and to leave SMs free for other work.
+ *    mfa_form_list_configs lists 0; mfa_form_set_config keeps any k >= 0
+ *    (MFA_ERR_ARG below 0); mfa_form_autotune times with 0 and leaves 0.
  *  - ms: mean time of one apply measured by mfa_form_autotune (else 0). */
 enum {
   MFA_VARIANT_AUTO = 0,
@@ -284,6 +292,8 @@ typedef struct {
   int32_t cells_per_block;
   int32_t scatter;
   int32_t geometry;        /* MFA_GEOM_STORED or MFA_GEOM_ONTHEFLY (hex) */
+  int32_t max_blocks;      /* grid cap, >= 0 (see above) */
+  int32_t reserved;        /* 0 */
   double ms;
 } mfa_launch_config;
 

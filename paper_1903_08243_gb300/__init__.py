@@ -76,13 +76,16 @@ class mfa_launch_config(ctypes.Structure):
         ("cells_per_block", ctypes.c_int32),
         ("scatter", ctypes.c_int32),
         ("geometry", ctypes.c_int32),
+        ("max_blocks", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
         ("ms", ctypes.c_double),
     ]
 
     def as_dict(self):
         return {"variant": VARIANT_NAMES.get(self.variant, self.variant), "cells_per_block": self.cells_per_block,
                 "scatter": {MFA_SCATTER_COLOUR: "colour", MFA_SCATTER_WARP: "warp"}.get(self.scatter, "atomic"),
-                "geometry": "on-the-fly" if self.geometry == MFA_GEOM_ONTHEFLY else "stored", "ms": self.ms}
+                "geometry": "on-the-fly" if self.geometry == MFA_GEOM_ONTHEFLY else "stored",
+                "max_blocks": self.max_blocks, "ms": self.ms}
 
 
 _lib = None
@@ -617,6 +620,12 @@ class Form:
         return mfa_form_get_config(self.h)
 
     def set_config(self, cfg):
+        mfa_form_set_config(self.h, cfg)
+
+    def set_max_blocks(self, k):
+        """Cap the persistent grid of this form's launches at k blocks (0: one wave per SM)."""
+        cfg = mfa_form_get_config(self.h)
+        cfg.max_blocks = int(k)
         mfa_form_set_config(self.h, cfg)
 
     def autotune(self, x, y, reps=3):

@@ -458,6 +458,7 @@ int apply_form(mfa_form* f, const double* x, double* y, cudaStream_t stream) {
 static int apply_form_raw(mfa_form* f, const double* x, double* y, cudaStream_t stream) {
   mfa_space* sp = f->space;
   mfa_ctx* ctx = f->ctx;
+  const mfa::GridBudget budget{ctx->sm_count, f->launch.max_blocks};
   const bool colour = f->scatter == MFA_SCATTER_COLOUR;
   const int ncol = colour ? sp->ncolours : 1;
   for (int k = 0; k < ncol; ++k) {
@@ -468,7 +469,7 @@ static int apply_form_raw(mfa_form* f, const double* x, double* y, cudaStream_t 
       mfa::QuadArgs a{x, y, sp->d_cell_node, static_cast<const double*>(f->d_geom), f->d_coef, list, count,
                       f->p.lambda, f->p.mu, f->p.b[0], f->p.b[1], ctx->d_err};
       e = mfa::quad_apply_launch(sp->degree + 1, f->nq1, sp->ncomp, f->p.kind, f->p.law, colour, f->hex, a,
-                                 ctx->sm_count, stream);
+                                 budget, stream);
     } else if (sp->mesh->cell_type == MFA_CELL_TRI3) {
       const int64_t nb = (int64_t)sp->nloc * f->tdense_nq;
       mfa::TetDenseArgs a{};
@@ -495,15 +496,15 @@ static int apply_form_raw(mfa_form* f, const double* x, double* y, cudaStream_t 
       a.err = ctx->d_err;
       if (f->launch.variant == MFA_VARIANT_CELL)
         e = mfa::tri_cell_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, f->launch.cb ? f->launch.cb : 128,
-                                 f->tri, a, ctx->sm_count, stream);
+                                 f->tri, a, budget, stream);
       else
-        e = mfa::tri_dense_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, a, ctx->sm_count, stream);
+        e = mfa::tri_dense_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, a, budget, stream);
     } else if (sp->mesh->cell_type == MFA_CELL_HEX8 && sp->ncomp == 3) {
       mfa::HexVecArgs a{x, y, sp->d_cell_node, static_cast<const double*>(f->d_geom), f->d_coef, list, count,
                         f->gstride, f->p.lambda, f->p.mu, f->p.b[0], f->p.b[1], f->p.b[2], ctx->d_err};
       const int n = sp->degree + 1;
-      e = n <= 5 ? mfa::hex_vector_launch_a(n, f->nq1, f->p.kind, f->p.law, colour, f->hex, a, ctx->sm_count, stream)
-                 : mfa::hex_vector_launch_b(n, f->nq1, f->p.kind, f->p.law, colour, f->hex, a, ctx->sm_count, stream);
+      e = n <= 5 ? mfa::hex_vector_launch_a(n, f->nq1, f->p.kind, f->p.law, colour, f->hex, a, budget, stream)
+                 : mfa::hex_vector_launch_b(n, f->nq1, f->p.kind, f->p.law, colour, f->hex, a, budget, stream);
     } else if (sp->mesh->cell_type == MFA_CELL_HEX8) {
       mfa::HexApplyArgs a{x, y, sp->d_cell_node, f->d_geom, list, count, ctx->d_err, f->gstride};
       a.coords = sp->mesh->d_coords;
@@ -512,7 +513,7 @@ static int apply_form_raw(mfa_form* f, const double* x, double* y, cudaStream_t 
       mfa::LaunchConfig lc = f->launch;
       lc.agg = f->scatter == MFA_SCATTER_WARP;
       e = mfa::hex_apply_launch(sp->degree + 1, f->nq1, f->p.kind, f->p.precision, colour, lc, f->hex, a,
-                                ctx->sm_count, stream);
+                                budget, stream);
     } else if (sp->degree >= 3) {
       const int64_t nb = (int64_t)sp->nloc * f->tdense_nq;
       mfa::TetDenseArgs a{};
@@ -537,13 +538,13 @@ static int apply_form_raw(mfa_form* f, const double* x, double* y, cudaStream_t 
       a.b1 = f->p.b[1];
       a.b2 = f->p.b[2];
       a.err = ctx->d_err;
-      e = mfa::tet_dense_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, a, ctx->sm_count, stream);
+      e = mfa::tet_dense_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, a, budget, stream);
     } else {
       mfa::TetApplyArgs a = tet_args(f, x, y);
       a.cell_list = list;
       a.count = count;
       e = mfa::tet_apply_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, f->scatter == MFA_SCATTER_WARP,
-                                f->launch.cb ? f->launch.cb : 128, f->tet, a, ctx->sm_count, stream);
+                                f->launch.cb ? f->launch.cb : 128, f->tet, a, budget, stream);
     }
     if (e != cudaSuccess) return fail(MFA_ERR_CUDA, "apply kernel launch: %s", cudaGetErrorString(e));
   }
@@ -1050,6 +1051,7 @@ int mfa_form_get_config(const mfa_form* f, mfa_launch_config* cfg) {
   cfg->cells_per_block = f->launch.cb ? f->launch.cb : (nopt > 0 ? opts[0] : 0);
   cfg->scatter = f->scatter;
   cfg->geometry = f->launch.otf ? MFA_GEOM_ONTHEFLY : MFA_GEOM_STORED;
+  cfg->max_blocks = f->launch.max_blocks;
   cfg->ms = f->tuned_ms;
   return MFA_OK;
 }
@@ -1057,6 +1059,7 @@ int mfa_form_get_config(const mfa_form* f, mfa_launch_config* cfg) {
 int mfa_form_set_config(mfa_form* f, const mfa_launch_config* cfg) {
   if (!f || !cfg) return fail(MFA_ERR_ARG, "mfa_form_set_config: NULL argument");
   mfa_launch_config want = *cfg;
+  if (want.max_blocks < 0) return fail(MFA_ERR_ARG, "mfa_form_set_config: max_blocks %d < 0", want.max_blocks);
   const mfa_space* sp = f->space;
   if (want.variant == MFA_VARIANT_AUTO) {
     want.variant = default_variant(sp, f->nq1, f->p.precision);
@@ -1082,6 +1085,7 @@ int mfa_form_set_config(mfa_form* f, const mfa_launch_config* cfg) {
   f->launch.variant = want.variant;
   f->launch.cb = want.cells_per_block;
   f->launch.otf = want.geometry == MFA_GEOM_ONTHEFLY;
+  f->launch.max_blocks = want.max_blocks;
   f->scatter = want.scatter;
   f->tuned_ms = 0.0;
   count_work(f);
@@ -1189,7 +1193,7 @@ int mfa_apply_f32(mfa_ctx* ctx, mfa_form* f, const float* x, float* y, int accum
   const int64_t ndof = sp->nnode * sp->ncomp;
   if (!accumulate) MFA_CUDA(cudaMemsetAsync(y, 0, sizeof(float) * ndof, ctx->stream));
   cudaError_t e = mfa::hex_apply_launch_f32(sp->degree + 1, f->p.kind, f->p.precision, x, y, sp->d_cell_node,
-                                            f->d_geom, sp->mesh->ncell, f->gstride, ctx->d_err, ctx->sm_count,
+                                            f->d_geom, sp->mesh->ncell, f->gstride, ctx->d_err, mfa::GridBudget{ctx->sm_count, f->launch.max_blocks},
                                             ctx->stream);
   if (e != cudaSuccess) return fail(MFA_ERR_CUDA, "mfa_apply_f32: %s", cudaGetErrorString(e));
   return MFA_OK;
@@ -1326,7 +1330,7 @@ int mfa_diagonal(mfa_ctx* ctx, mfa_form* f, double* d) {
   if (ct == MFA_CELL_HEX8 && sp->ncomp == 1) {
     e = mfa::hex_diagonal_launch(sp->degree + 1, f->nq1, f->p.kind, f->hex, sp->d_cell_node,
                                  static_cast<const double*>(f->d_geom),
-                                 sp->mesh->ncell, d, ctx->sm_count, ctx->stream);
+                                 sp->mesh->ncell, d, mfa::GridBudget{ctx->sm_count, 0}, ctx->stream);
   } else if (ct == MFA_CELL_HEX8 || ct == MFA_CELL_QUAD4) {
     e = mfa::tensor_diagonal_launch(ct == MFA_CELL_HEX8 ? 3 : 2, sp->ncomp, sp->degree + 1, f->nq1, f->p.kind, f->hex,
                                     sp->d_cell_node, static_cast<const double*>(f->d_geom), f->gstride,

@@ -23,6 +23,7 @@ struct mfa_batch {
     int64_t* d_first = nullptr;
     int nitems = 0;
     int64_t total = 0;
+    int max_blocks = 0;  // smallest positive grid cap of the members (0: none)
   };
   std::vector<Group> groups;
   std::vector<int> singles;  // forms applied one by one
@@ -43,7 +44,7 @@ int enqueue(mfa_batch* b, cudaStream_t s) {
   }
   for (auto& g : b->groups) {
     cudaError_t e = mfa::hex_group_launch(g.n, g.kind, g.prec, g.tb, g.d_items, g.d_first, g.nitems, g.total,
-                                          b->ctx->sm_count, s);
+                                          mfa::GridBudget{b->ctx->sm_count, g.max_blocks}, s);
     if (e != cudaSuccess) return mfa::set_error(MFA_ERR_CUDA, cudaGetErrorString(e));
   }
   for (int k : b->singles) {
@@ -89,6 +90,8 @@ int build(mfa_ctx* ctx, int n, mfa_form* const* forms, const double* const* xs, 
       mfa::HexApplyArgs a{xs[k], ys[k], f->space->d_cell_node, f->d_geom,     nullptr,
                           f->space->mesh->ncell, ctx->d_err, f->gstride};
       items.push_back(a);
+      if (f->launch.max_blocks > 0 && (g.max_blocks == 0 || f->launch.max_blocks < g.max_blocks))
+        g.max_blocks = f->launch.max_blocks;
       first.push_back(first.back() + (f->space->mesh->ncell + cb - 1) / cb);
     }
     g.nitems = (int)items.size();

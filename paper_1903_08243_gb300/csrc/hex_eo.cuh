@@ -263,14 +263,14 @@ int occupancy(Kern kern, int threads, int smem) {
 }
 
 template <int N, int KIND, bool COLOUR, int CBX = 0>
-cudaError_t launch(const HexApplyArgs& a, int sm_count, cudaStream_t s) {
+cudaError_t launch(const HexApplyArgs& a, GridBudget budget, cudaStream_t s) {
   using S = EShape<N, CBX>;
   auto kern = eo_apply_kernel<N, KIND, COLOUR, CBX>;
   static int bps = -1;
   if (bps < 0) bps = occupancy(kern, S::T, S::SMEM);
   const int64_t nbatch = (a.count + S::CB - 1) / S::CB;
   if (nbatch == 0) return cudaSuccess;
-  const int64_t cap = (int64_t)sm_count * bps;
+  const int64_t cap = budget.cap(bps);
   kern<<<(unsigned)(nbatch < cap ? nbatch : cap), S::T, S::SMEM, s>>>(a);
   return cudaGetLastError();
 }

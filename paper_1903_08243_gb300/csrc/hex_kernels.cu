@@ -145,25 +145,25 @@ int hex_point_cb_options(int n, int nq, int* out) {
 }
 
 cudaError_t hex_apply_launch(int n, int nq, int kind, int prec, bool colour, const LaunchConfig& lc,
-                             const HexTables& tb, const HexApplyArgs& a, int sm_count, cudaStream_t s) {
-  if (prec != MFA_PREC_FP64) return hex_apply_launch_mixed(n, nq, kind, prec, colour, lc, tb, a, sm_count, s);
+                             const HexTables& tb, const HexApplyArgs& a, GridBudget budget, cudaStream_t s) {
+  if (prec != MFA_PREC_FP64) return hex_apply_launch_mixed(n, nq, kind, prec, colour, lc, tb, a, budget, s);
   const int variant = lc.variant == MFA_VARIANT_AUTO ? hex_default_variant(n, nq, prec) : lc.variant;
   if (variant == MFA_VARIANT_EVEN_ODD) {
     if (nq != n || n < 5 || n > 9 || lc.agg || lc.otf) return cudaErrorInvalidValue;
-    if (lc.cb == 0 || lc.cb == hex_eo_cells_per_block(n)) return hex_eo_apply_launch(n, kind, colour, a, sm_count, s);
-    return hex_eo_apply_launch_cb(n, kind, colour, lc.cb, a, sm_count, s);
+    if (lc.cb == 0 || lc.cb == hex_eo_cells_per_block(n)) return hex_eo_apply_launch(n, kind, colour, a, budget, s);
+    return hex_eo_apply_launch_cb(n, kind, colour, lc.cb, a, budget, s);
   }
   if (variant != MFA_VARIANT_POINT) return cudaErrorInvalidValue;
   if (lc.otf) {
     if (lc.agg || (lc.cb != 0 && lc.cb != hex_cells_per_block(n, nq))) return cudaErrorInvalidValue;
-    return hex_point_launch_otf(n, nq, kind, colour, tb, a, sm_count, s);
+    return hex_point_launch_otf(n, nq, kind, colour, tb, a, budget, s);
   }
   if (lc.agg) {
     if (colour || (lc.cb != 0 && lc.cb != hex_cells_per_block(n, nq))) return cudaErrorInvalidValue;
-    return hex_point_launch_agg(n, nq, kind, tb, a, sm_count, s);
+    return hex_point_launch_agg(n, nq, kind, tb, a, budget, s);
   }
   if (lc.cb != 0 && lc.cb != hex_cells_per_block(n, nq))
-    return hex_point_launch_cb(n, nq, kind, colour, lc.cb, tb, a, sm_count, s);
+    return hex_point_launch_cb(n, nq, kind, colour, lc.cb, tb, a, budget, s);
   using namespace hexk;
   MFA_HEX_KIND_CASES(2, 2, MFA_PREC_FP64)
   MFA_HEX_KIND_CASES(3, 3, MFA_PREC_FP64)
@@ -183,9 +183,9 @@ cudaError_t hex_apply_launch(int n, int nq, int kind, int prec, bool colour, con
 }
 
 cudaError_t hex_group_launch(int n, int kind, int prec, const HexTables& tb, const HexApplyArgs* items,
-                             const int64_t* first, int nitems, int64_t total, int sm_count, cudaStream_t s) {
-  if (prec != MFA_PREC_FP64) return hex_group_launch_mixed(n, kind, prec, tb, items, first, nitems, total, sm_count, s);
-  if (hex_use_eo(n, n, prec)) return hex_eo_group_launch(n, kind, items, first, nitems, total, sm_count, s);
+                             const int64_t* first, int nitems, int64_t total, GridBudget budget, cudaStream_t s) {
+  if (prec != MFA_PREC_FP64) return hex_group_launch_mixed(n, kind, prec, tb, items, first, nitems, total, budget, s);
+  if (hex_use_eo(n, n, prec)) return hex_eo_group_launch(n, kind, items, first, nitems, total, budget, s);
   using namespace hexk;
   MFA_HEX_GROUP_CASES(2, MFA_PREC_FP64)
   MFA_HEX_GROUP_CASES(3, MFA_PREC_FP64)
@@ -202,18 +202,18 @@ cudaError_t hex_group_launch(int n, int kind, int prec, const HexTables& tb, con
   if (n == NN && nq == NQQ) {                                                                         \
     switch (kind) {                                                                                   \
       case MFA_FORM_MASS:                                                                             \
-        return hexk::launch_diag<NN, NQQ, MFA_FORM_MASS>(tb, cell_node, geom, ncell, d, sm_count, s); \
+        return hexk::launch_diag<NN, NQQ, MFA_FORM_MASS>(tb, cell_node, geom, ncell, d, budget, s); \
       case MFA_FORM_LAPLACE:                                                                          \
-        return hexk::launch_diag<NN, NQQ, MFA_FORM_LAPLACE>(tb, cell_node, geom, ncell, d, sm_count, s); \
+        return hexk::launch_diag<NN, NQQ, MFA_FORM_LAPLACE>(tb, cell_node, geom, ncell, d, budget, s); \
       case MFA_FORM_HELMHOLTZ:                                                                        \
-        return hexk::launch_diag<NN, NQQ, MFA_FORM_HELMHOLTZ>(tb, cell_node, geom, ncell, d, sm_count, s); \
+        return hexk::launch_diag<NN, NQQ, MFA_FORM_HELMHOLTZ>(tb, cell_node, geom, ncell, d, budget, s); \
       default:                                                                                        \
         return cudaErrorInvalidValue;                                                                 \
     }                                                                                                 \
   }
 
 cudaError_t hex_diagonal_launch(int n, int nq, int kind, const HexTables& tb, const int32_t* cell_node,
-                                const double* geom, int64_t ncell, double* d, int sm_count, cudaStream_t s) {
+                                const double* geom, int64_t ncell, double* d, GridBudget budget, cudaStream_t s) {
   MFA_HEX_DIAG_CASE(2, 2)
   MFA_HEX_DIAG_CASE(3, 3)
   MFA_HEX_DIAG_CASE(4, 4)

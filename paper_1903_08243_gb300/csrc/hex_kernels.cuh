@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(Shape<N, NQ>::T) hex_apply_group_kernel(const 
 }
 
 template <int N, int NQ, int KIND, bool COLOUR, int PREC, int CBX = 0, bool AGG = false, bool OTF = false>
-cudaError_t launch_apply(const HexTables& tb, const HexApplyArgs& a, int sm_count, cudaStream_t s) {
+cudaError_t launch_apply(const HexTables& tb, const HexApplyArgs& a, GridBudget budget, cudaStream_t s) {
   using S = Shape<N, NQ, (int)sizeof(typename Prec<PREC>::T), CBX>;
   auto kern = hex_apply_kernel<N, NQ, KIND, COLOUR, PREC, CBX, AGG, OTF>;
   static int blocks_per_sm = -1;
@@ -382,14 +382,14 @@ cudaError_t launch_apply(const HexTables& tb, const HexApplyArgs& a, int sm_coun
   }
   const int64_t nbatch = (a.count + S::CB - 1) / S::CB;
   if (nbatch == 0) return cudaSuccess;
-  const int64_t grid = nbatch < (int64_t)sm_count * blocks_per_sm ? nbatch : (int64_t)sm_count * blocks_per_sm;
+  const int64_t grid = nbatch < budget.cap(blocks_per_sm) ? nbatch : budget.cap(blocks_per_sm);
   kern<<<(unsigned)grid, S::T, S::SMEM, s>>>(tb, a);
   return cudaGetLastError();
 }
 
 template <int N, int NQ, int KIND, int PREC>
 cudaError_t launch_group(const HexTables& tb, const HexApplyArgs* items, const int64_t* first, int nitems,
-                         int64_t total_batches, int sm_count, cudaStream_t s) {
+                         int64_t total_batches, GridBudget budget, cudaStream_t s) {
   using S = Shape<N, NQ, (int)sizeof(typename Prec<PREC>::T)>;
   auto kern = hex_apply_group_kernel<N, NQ, KIND, PREC>;
   static int blocks_per_sm = -1;
@@ -401,7 +401,7 @@ cudaError_t launch_group(const HexTables& tb, const HexApplyArgs* items, const i
     if (blocks_per_sm < 1) blocks_per_sm = 1;
   }
   if (total_batches == 0) return cudaSuccess;
-  const int64_t cap = (int64_t)sm_count * blocks_per_sm;
+  const int64_t cap = budget.cap(blocks_per_sm);
   kern<<<(unsigned)(total_batches < cap ? total_batches : cap), S::T, S::SMEM, s>>>(tb, items, first, nitems);
   return cudaGetLastError();
 }
@@ -410,11 +410,11 @@ cudaError_t launch_group(const HexTables& tb, const HexApplyArgs* items, const i
   if (n == NN) {                                                                                       \
     switch (kind) {                                                                                    \
       case MFA_FORM_MASS:                                                                              \
-        return launch_group<NN, NN, MFA_FORM_MASS, PREC>(tb, items, first, nitems, total, sm_count, s); \
+        return launch_group<NN, NN, MFA_FORM_MASS, PREC>(tb, items, first, nitems, total, budget, s); \
       case MFA_FORM_LAPLACE:                                                                           \
-        return launch_group<NN, NN, MFA_FORM_LAPLACE, PREC>(tb, items, first, nitems, total, sm_count, s); \
+        return launch_group<NN, NN, MFA_FORM_LAPLACE, PREC>(tb, items, first, nitems, total, budget, s); \
       case MFA_FORM_HELMHOLTZ:                                                                         \
-        return launch_group<NN, NN, MFA_FORM_HELMHOLTZ, PREC>(tb, items, first, nitems, total, sm_count, s); \
+        return launch_group<NN, NN, MFA_FORM_HELMHOLTZ, PREC>(tb, items, first, nitems, total, budget, s); \
       default:                                                                                         \
         return cudaErrorInvalidValue;                                                                  \
     }                                                                                                  \
@@ -425,14 +425,14 @@ cudaError_t launch_group(const HexTables& tb, const HexApplyArgs* items, const i
   if (n == NN && nq == NQQ) {                                                                          \
     switch (kind) {                                                                                    \
       case MFA_FORM_MASS:                                                                              \
-        return colour ? launch_apply<NN, NQQ, MFA_FORM_MASS, true, PREC>(tb, a, sm_count, s)           \
-                      : launch_apply<NN, NQQ, MFA_FORM_MASS, false, PREC>(tb, a, sm_count, s);         \
+        return colour ? launch_apply<NN, NQQ, MFA_FORM_MASS, true, PREC>(tb, a, budget, s)           \
+                      : launch_apply<NN, NQQ, MFA_FORM_MASS, false, PREC>(tb, a, budget, s);         \
       case MFA_FORM_LAPLACE:                                                                           \
-        return colour ? launch_apply<NN, NQQ, MFA_FORM_LAPLACE, true, PREC>(tb, a, sm_count, s)        \
-                      : launch_apply<NN, NQQ, MFA_FORM_LAPLACE, false, PREC>(tb, a, sm_count, s);      \
+        return colour ? launch_apply<NN, NQQ, MFA_FORM_LAPLACE, true, PREC>(tb, a, budget, s)        \
+                      : launch_apply<NN, NQQ, MFA_FORM_LAPLACE, false, PREC>(tb, a, budget, s);      \
       case MFA_FORM_HELMHOLTZ:                                                                         \
-        return colour ? launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, true, PREC>(tb, a, sm_count, s)      \
-                      : launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, false, PREC>(tb, a, sm_count, s);    \
+        return colour ? launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, true, PREC>(tb, a, budget, s)      \
+                      : launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, false, PREC>(tb, a, budget, s);    \
       default:                                                                                         \
         return cudaErrorInvalidValue;                                                                  \
     }                                                                                                  \
@@ -443,14 +443,14 @@ cudaError_t launch_group(const HexTables& tb, const HexApplyArgs* items, const i
   if (n == NN && nq == NQQ && cb == CBB) {                                                             \
     switch (kind) {                                                                                    \
       case MFA_FORM_MASS:                                                                              \
-        return colour ? launch_apply<NN, NQQ, MFA_FORM_MASS, true, PREC, CBB>(tb, a, sm_count, s)      \
-                      : launch_apply<NN, NQQ, MFA_FORM_MASS, false, PREC, CBB>(tb, a, sm_count, s);    \
+        return colour ? launch_apply<NN, NQQ, MFA_FORM_MASS, true, PREC, CBB>(tb, a, budget, s)      \
+                      : launch_apply<NN, NQQ, MFA_FORM_MASS, false, PREC, CBB>(tb, a, budget, s);    \
       case MFA_FORM_LAPLACE:                                                                           \
-        return colour ? launch_apply<NN, NQQ, MFA_FORM_LAPLACE, true, PREC, CBB>(tb, a, sm_count, s)   \
-                      : launch_apply<NN, NQQ, MFA_FORM_LAPLACE, false, PREC, CBB>(tb, a, sm_count, s); \
+        return colour ? launch_apply<NN, NQQ, MFA_FORM_LAPLACE, true, PREC, CBB>(tb, a, budget, s)   \
+                      : launch_apply<NN, NQQ, MFA_FORM_LAPLACE, false, PREC, CBB>(tb, a, budget, s); \
       case MFA_FORM_HELMHOLTZ:                                                                         \
-        return colour ? launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, true, PREC, CBB>(tb, a, sm_count, s) \
-                      : launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, false, PREC, CBB>(tb, a, sm_count, s); \
+        return colour ? launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, true, PREC, CBB>(tb, a, budget, s) \
+                      : launch_apply<NN, NQQ, MFA_FORM_HELMHOLTZ, false, PREC, CBB>(tb, a, budget, s); \
       default:                                                                                         \
         return cudaErrorInvalidValue;                                                                  \
     }                                                                                                  \
@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(Shape<N, NQ>::T) hex_diag_kernel(const __grid_
 
 template <int N, int NQ, int KIND>
 cudaError_t launch_diag(const HexTables& tb, const int32_t* cell_node, const double* geom, int64_t ncell, double* d,
-                        int sm_count, cudaStream_t s) {
+                        GridBudget budget, cudaStream_t s) {
   using S = Shape<N, NQ>;
   auto kern = hex_diag_kernel<N, NQ, KIND>;
   const int smem = (3 * NQ * N + 2 * S::CB * S::P) * 8;
@@ -543,7 +543,7 @@ cudaError_t launch_diag(const HexTables& tb, const int32_t* cell_node, const dou
   if (e != cudaSuccess) return e;
   const int64_t nbatch = (ncell + S::CB - 1) / S::CB;
   if (nbatch == 0) return cudaSuccess;
-  const int64_t grid = nbatch < (int64_t)sm_count * 4 ? nbatch : (int64_t)sm_count * 4;
+  const int64_t grid = nbatch < budget.cap(4) ? nbatch : budget.cap(4);
   kern<<<(unsigned)grid, S::T, smem, s>>>(tb, cell_node, geom, ncell, d);
   return cudaGetLastError();
 }

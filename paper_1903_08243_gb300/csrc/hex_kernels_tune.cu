@@ -5,7 +5,7 @@
 namespace mfa {
 
 cudaError_t hex_point_launch_cb(int n, int nq, int kind, bool colour, int cb, const HexTables& tb,
-                                const HexApplyArgs& a, int sm_count, cudaStream_t s) {
+                                const HexApplyArgs& a, GridBudget budget, cudaStream_t s) {
   using namespace hexk;
   MFA_HEX_KIND_CASES_CB(2, 2, 16, MFA_PREC_FP64)
   MFA_HEX_KIND_CASES_CB(2, 2, 64, MFA_PREC_FP64)

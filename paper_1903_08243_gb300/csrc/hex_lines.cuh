@@ -417,7 +417,7 @@ int occupancy(Kern kern, int threads, int smem) {
 }
 
 template <int N, int KIND, int PREC, typename TX, bool STG = staged<PREC>(), int CBX = 0>
-cudaError_t launch_line(const LineArgs& a, int sm_count, cudaStream_t s) {
+cudaError_t launch_line(const LineArgs& a, GridBudget budget, cudaStream_t s) {
   using S = LShape<N, CBX>;
   constexpr int smem = line_smem<N, KIND, PREC, STG, CBX>();
   auto kern = line_apply_kernel<N, KIND, PREC, TX, STG, CBX>;
@@ -425,21 +425,21 @@ cudaError_t launch_line(const LineArgs& a, int sm_count, cudaStream_t s) {
   if (bps < 0) bps = occupancy(kern, S::T, smem);
   const int64_t nbatch = (a.count + S::CB - 1) / S::CB;
   if (nbatch == 0) return cudaSuccess;
-  const int64_t cap = (int64_t)sm_count * bps;
+  const int64_t cap = budget.cap(bps);
   kern<<<(unsigned)(nbatch < cap ? nbatch : cap), S::T, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int N, int KIND, int PREC>
 cudaError_t launch_line_group(const HexApplyArgs* items, const int64_t* first, int nitems, int64_t total,
-                              int sm_count, cudaStream_t s) {
+                              GridBudget budget, cudaStream_t s) {
   using S = LShape<N>;
   constexpr int smem = line_smem<N, KIND, PREC>();
   auto kern = line_group_kernel<N, KIND, PREC>;
   static int bps = -1;
   if (bps < 0) bps = occupancy(kern, S::T, smem);
   if (total == 0) return cudaSuccess;
-  const int64_t cap = (int64_t)sm_count * bps;
+  const int64_t cap = budget.cap(bps);
   kern<<<(unsigned)(total < cap ? total : cap), S::T, smem, s>>>(items, first, nitems);
   return cudaGetLastError();
 }

@@ -4,18 +4,18 @@
 
 namespace mfa {
 
-cudaError_t hex_line_apply_a(int n, int kind, int prec, bool f32vec, const hexl::LineArgs& a, int sm_count,
+cudaError_t hex_line_apply_a(int n, int kind, int prec, bool f32vec, const hexl::LineArgs& a, GridBudget budget,
                              cudaStream_t s);
-cudaError_t hex_line_apply_b(int n, int kind, int prec, bool f32vec, const hexl::LineArgs& a, int sm_count,
+cudaError_t hex_line_apply_b(int n, int kind, int prec, bool f32vec, const hexl::LineArgs& a, GridBudget budget,
                              cudaStream_t s);
 cudaError_t hex_line_group_a(int n, int kind, int prec, const HexApplyArgs* items, const int64_t* first, int nitems,
-                             int64_t total, int sm_count, cudaStream_t s);
+                             int64_t total, GridBudget budget, cudaStream_t s);
 cudaError_t hex_line_group_b(int n, int kind, int prec, const HexApplyArgs* items, const int64_t* first, int nitems,
-                             int64_t total, int sm_count, cudaStream_t s);
+                             int64_t total, GridBudget budget, cudaStream_t s);
 
-cudaError_t hex_line_tuned_a(int n, int kind, int prec, bool stg, int cb, const hexl::LineArgs& a, int sm_count,
+cudaError_t hex_line_tuned_a(int n, int kind, int prec, bool stg, int cb, const hexl::LineArgs& a, GridBudget budget,
                              cudaStream_t s);
-cudaError_t hex_line_tuned_b(int n, int kind, int prec, bool stg, int cb, const hexl::LineArgs& a, int sm_count,
+cudaError_t hex_line_tuned_b(int n, int kind, int prec, bool stg, int cb, const hexl::LineArgs& a, GridBudget budget,
                              cudaStream_t s);
 
 // Default (256-thread target), then the 512-thread target (hex_lines_tune_*.cu).
@@ -27,7 +27,7 @@ int hex_line_cb_options(int n, int* out) {
 }
 
 cudaError_t hex_apply_launch_mixed(int n, int nq, int kind, int prec, bool colour, const LaunchConfig& lc,
-                                   const HexTables&, const HexApplyArgs& a, int sm_count, cudaStream_t s) {
+                                   const HexTables&, const HexApplyArgs& a, GridBudget budget, cudaStream_t s) {
   if (nq != n || colour || a.cell_list) return cudaErrorInvalidValue;
   const int variant = lc.variant == MFA_VARIANT_AUTO ? hex_default_variant(n, nq, prec) : lc.variant;
   if (variant != MFA_VARIANT_LINE && variant != MFA_VARIANT_LINE_STAGED) return cudaErrorInvalidValue;
@@ -35,25 +35,25 @@ cudaError_t hex_apply_launch_mixed(int n, int nq, int kind, int prec, bool colou
   const bool stg_default = prec == MFA_PREC_BF16 ? hexl::staged<MFA_PREC_BF16>() : hexl::staged<MFA_PREC_FP32>();
   const hexl::LineArgs la{a.x, a.y, a.cell_node, a.geom, a.count, a.geom_stride, a.err};
   if (stg == stg_default && (lc.cb == 0 || lc.cb == hexl::line_cb_for(n, 256)))
-    return n <= 5 ? hex_line_apply_a(n, kind, prec, false, la, sm_count, s)
-                  : hex_line_apply_b(n, kind, prec, false, la, sm_count, s);
+    return n <= 5 ? hex_line_apply_a(n, kind, prec, false, la, budget, s)
+                  : hex_line_apply_b(n, kind, prec, false, la, budget, s);
   const int cb = lc.cb == 0 ? hexl::line_cb_for(n, 256) : lc.cb;
-  return n <= 5 ? hex_line_tuned_a(n, kind, prec, stg, cb, la, sm_count, s)
-                : hex_line_tuned_b(n, kind, prec, stg, cb, la, sm_count, s);
+  return n <= 5 ? hex_line_tuned_a(n, kind, prec, stg, cb, la, budget, s)
+                : hex_line_tuned_b(n, kind, prec, stg, cb, la, budget, s);
 }
 
 cudaError_t hex_apply_launch_f32(int n, int kind, int prec, const float* x, float* y, const int32_t* cell_node,
-                                 const void* geom, int64_t count, int64_t gstride, int* err, int sm_count,
+                                 const void* geom, int64_t count, int64_t gstride, int* err, GridBudget budget,
                                  cudaStream_t s) {
   const hexl::LineArgs la{x, y, cell_node, geom, count, gstride, err};
-  return n <= 5 ? hex_line_apply_a(n, kind, prec, true, la, sm_count, s)
-                : hex_line_apply_b(n, kind, prec, true, la, sm_count, s);
+  return n <= 5 ? hex_line_apply_a(n, kind, prec, true, la, budget, s)
+                : hex_line_apply_b(n, kind, prec, true, la, budget, s);
 }
 
 cudaError_t hex_group_launch_mixed(int n, int kind, int prec, const HexTables&, const HexApplyArgs* items,
-                                   const int64_t* first, int nitems, int64_t total, int sm_count, cudaStream_t s) {
-  return n <= 5 ? hex_line_group_a(n, kind, prec, items, first, nitems, total, sm_count, s)
-                : hex_line_group_b(n, kind, prec, items, first, nitems, total, sm_count, s);
+                                   const int64_t* first, int nitems, int64_t total, GridBudget budget, cudaStream_t s) {
+  return n <= 5 ? hex_line_group_a(n, kind, prec, items, first, nitems, total, budget, s)
+                : hex_line_group_b(n, kind, prec, items, first, nitems, total, budget, s);
 }
 
 }  // namespace mfa

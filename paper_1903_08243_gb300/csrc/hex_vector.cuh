@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(Shape<N, NQ>::T) apply_kernel(const __grid_con
 }
 
 template <int N, int NQ, int KIND, int LAW, bool COLOUR>
-cudaError_t launch(const HexTables& tb, const HexVecArgs& a, int sm_count, cudaStream_t s) {
+cudaError_t launch(const HexTables& tb, const HexVecArgs& a, GridBudget budget, cudaStream_t s) {
   using S = Shape<N, NQ>;
   auto kern = apply_kernel<N, NQ, KIND, LAW, COLOUR>;
   static int blocks_per_sm = -1;
@@ -232,33 +232,33 @@ cudaError_t launch(const HexTables& tb, const HexVecArgs& a, int sm_count, cudaS
   }
   const int64_t nbatch = (a.count + S::CB - 1) / S::CB;
   if (nbatch == 0) return cudaSuccess;
-  const int64_t cap = (int64_t)sm_count * blocks_per_sm;
+  const int64_t cap = budget.cap(blocks_per_sm);
   kern<<<(unsigned)(nbatch < cap ? nbatch : cap), S::T, S::SMEM, s>>>(tb, a);
   return cudaGetLastError();
 }
 
 // Linear vector forms (vector Laplacian, elasticity) at NQ points per direction.
 template <int N, int NQ>
-cudaError_t dispatch_linear(int kind, bool colour, const HexTables& tb, const HexVecArgs& a, int sm_count,
+cudaError_t dispatch_linear(int kind, bool colour, const HexTables& tb, const HexVecArgs& a, GridBudget budget,
                             cudaStream_t s) {
   switch (kind) {
     case MFA_FORM_LAPLACE:
-      return colour ? launch<N, NQ, MFA_FORM_LAPLACE, 0, true>(tb, a, sm_count, s)
-                    : launch<N, NQ, MFA_FORM_LAPLACE, 0, false>(tb, a, sm_count, s);
+      return colour ? launch<N, NQ, MFA_FORM_LAPLACE, 0, true>(tb, a, budget, s)
+                    : launch<N, NQ, MFA_FORM_LAPLACE, 0, false>(tb, a, budget, s);
     case MFA_FORM_ELASTICITY:
-      return colour ? launch<N, NQ, MFA_FORM_ELASTICITY, 0, true>(tb, a, sm_count, s)
-                    : launch<N, NQ, MFA_FORM_ELASTICITY, 0, false>(tb, a, sm_count, s);
+      return colour ? launch<N, NQ, MFA_FORM_ELASTICITY, 0, true>(tb, a, budget, s)
+                    : launch<N, NQ, MFA_FORM_ELASTICITY, 0, false>(tb, a, budget, s);
   }
   return cudaErrorInvalidValue;
 }
 
 // Hyperelastic forms at NQ points per direction.
 template <int N, int NQ>
-cudaError_t dispatch_hyper(int kind, int law, bool colour, const HexTables& tb, const HexVecArgs& a, int sm_count,
+cudaError_t dispatch_hyper(int kind, int law, bool colour, const HexTables& tb, const HexVecArgs& a, GridBudget budget,
                            cudaStream_t s) {
   const bool nh = law == MFA_LAW_NEOHOOKE;
 #define MFA_HEXV_CASE(KIND, LAW) \
-  return colour ? launch<N, NQ, KIND, LAW, true>(tb, a, sm_count, s) : launch<N, NQ, KIND, LAW, false>(tb, a, sm_count, s)
+  return colour ? launch<N, NQ, KIND, LAW, true>(tb, a, budget, s) : launch<N, NQ, KIND, LAW, false>(tb, a, budget, s)
   switch (kind) {
     case MFA_FORM_HYPER_RES:
       if (nh) MFA_HEXV_CASE(MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE);
@@ -274,16 +274,16 @@ cudaError_t dispatch_hyper(int kind, int law, bool colour, const HexTables& tb, 
 // p+1 points (every form), p+2 points (linear forms, Table 2's elasticity rule, n <= 7) and 2p+2 points
 // (hyperelastic forms, Table 2's hyperelasticity rule, n <= 4).
 template <int N>
-cudaError_t dispatch(int nq, int kind, int law, bool colour, const HexTables& tb, const HexVecArgs& a, int sm_count,
+cudaError_t dispatch(int nq, int kind, int law, bool colour, const HexTables& tb, const HexVecArgs& a, GridBudget budget,
                      cudaStream_t s) {
   const bool hyper = kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC;
-  if (nq == N) return hyper ? dispatch_hyper<N, N>(kind, law, colour, tb, a, sm_count, s)
-                            : dispatch_linear<N, N>(kind, colour, tb, a, sm_count, s);
+  if (nq == N) return hyper ? dispatch_hyper<N, N>(kind, law, colour, tb, a, budget, s)
+                            : dispatch_linear<N, N>(kind, colour, tb, a, budget, s);
   if constexpr (N + 1 <= 8) {  // n + 1 points: up to 512 threads per cell
-    if (nq == N + 1 && !hyper) return dispatch_linear<N, N + 1>(kind, colour, tb, a, sm_count, s);
+    if (nq == N + 1 && !hyper) return dispatch_linear<N, N + 1>(kind, colour, tb, a, budget, s);
   }
   if constexpr (2 * N <= 8) {
-    if (nq == 2 * N && hyper) return dispatch_hyper<N, 2 * N>(kind, law, colour, tb, a, sm_count, s);
+    if (nq == 2 * N && hyper) return dispatch_hyper<N, 2 * N>(kind, law, colour, tb, a, budget, s);
   }
   return cudaErrorInvalidValue;
 }

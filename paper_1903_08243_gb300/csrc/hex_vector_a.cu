@@ -4,12 +4,12 @@
 namespace mfa {
 
 cudaError_t hex_vector_launch_a(int n, int nq, int kind, int law, bool colour, const HexTables& tb, const HexVecArgs& a,
-                                int sm_count, cudaStream_t s) {
+                                GridBudget budget, cudaStream_t s) {
   switch (n) {
-    case 2: return hexv::dispatch<2>(nq, kind, law, colour, tb, a, sm_count, s);
-    case 3: return hexv::dispatch<3>(nq, kind, law, colour, tb, a, sm_count, s);
-    case 4: return hexv::dispatch<4>(nq, kind, law, colour, tb, a, sm_count, s);
-    case 5: return hexv::dispatch<5>(nq, kind, law, colour, tb, a, sm_count, s);
+    case 2: return hexv::dispatch<2>(nq, kind, law, colour, tb, a, budget, s);
+    case 3: return hexv::dispatch<3>(nq, kind, law, colour, tb, a, budget, s);
+    case 4: return hexv::dispatch<4>(nq, kind, law, colour, tb, a, budget, s);
+    case 5: return hexv::dispatch<5>(nq, kind, law, colour, tb, a, budget, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -13,6 +13,19 @@ namespace mfa {
 
 constexpr int kMaxN = 10;  // nodes or quadrature points per direction (Q_p, p <= 8; p+2 points)
 
+// Grid of a persistent launch: each block walks work units (batches of cells)
+// with a stride of gridDim.x.  By default one wave of `bps` resident blocks on
+// every SM; with max_blocks > 0 at most that many blocks, so that each block
+// walks more units (mfa_launch_config.max_blocks).
+struct GridBudget {
+  int sms = 0;
+  int max_blocks = 0;
+  int64_t cap(int bps) const {
+    const int64_t c = (int64_t)sms * (bps > 0 ? bps : 1);
+    return max_blocks > 0 && max_blocks < c ? max_blocks : c;
+  }
+};
+
 // ---------------------------------------------------------------- tables.cpp
 // Quadrature rules and 1D/3D basis tabulations built on the host in FP64.
 void gauss_jacobi01(int n, int alpha, double* x, double* w);  // weight (1-x)^alpha on [0,1]
@@ -87,27 +100,27 @@ struct HexVecArgs {
 };
 // nq: n (every form), n + 1 (vector Laplacian, elasticity), 2n (hyperelastic forms, n <= 4)
 cudaError_t hex_vector_launch_a(int n, int nq, int kind, int law, bool colour, const HexTables& tb,
-                                const HexVecArgs& a, int sm_count, cudaStream_t s);  // n = 2..5
+                                const HexVecArgs& a, GridBudget budget, cudaStream_t s);  // n = 2..5
 cudaError_t hex_vector_launch_b(int n, int nq, int kind, int law, bool colour, const HexTables& tb,
-                                const HexVecArgs& a, int sm_count, cudaStream_t s);  // n = 6..9
+                                const HexVecArgs& a, GridBudget budget, cudaStream_t s);  // n = 6..9
 
 // Launch the sum-factorised FP64 action for cells [list].  Returns a cudaError_t.
 struct LaunchConfig;
 cudaError_t hex_apply_launch(int n, int nq, int kind, int prec, bool colour, const LaunchConfig& lc,
-                             const HexTables& tb, const HexApplyArgs& a, int sm_count, cudaStream_t s);
+                             const HexTables& tb, const HexApplyArgs& a, GridBudget budget, cudaStream_t s);
 cudaError_t hex_apply_launch_mixed(int n, int nq, int kind, int prec, bool colour, const LaunchConfig& lc,
-                                   const HexTables& tb, const HexApplyArgs& a, int sm_count, cudaStream_t s);
+                                   const HexTables& tb, const HexApplyArgs& a, GridBudget budget, cudaStream_t s);
 // One persistent launch over many forms of the same (n, n, kind, precision).
 cudaError_t hex_group_launch(int n, int kind, int prec, const HexTables& tb, const HexApplyArgs* items,
-                             const int64_t* first, int nitems, int64_t total, int sm_count, cudaStream_t s);
+                             const int64_t* first, int nitems, int64_t total, GridBudget budget, cudaStream_t s);
 cudaError_t hex_group_launch_mixed(int n, int kind, int prec, const HexTables& tb, const HexApplyArgs* items,
-                                   const int64_t* first, int nitems, int64_t total, int sm_count, cudaStream_t s);
+                                   const int64_t* first, int nitems, int64_t total, GridBudget budget, cudaStream_t s);
 int hex_cells_per_block(int n, int nq);
 int hex_line_cells_per_block(int n);
 // FP64 even-odd action for n = 5..9, p+1 points (hex_eo.cuh).
-cudaError_t hex_eo_apply_launch(int n, int kind, bool colour, const HexApplyArgs& a, int sm_count, cudaStream_t s);
+cudaError_t hex_eo_apply_launch(int n, int kind, bool colour, const HexApplyArgs& a, GridBudget budget, cudaStream_t s);
 cudaError_t hex_eo_group_launch(int n, int kind, const HexApplyArgs* items, const int64_t* first, int nitems,
-                                int64_t total, int sm_count, cudaStream_t s);
+                                int64_t total, GridBudget budget, cudaStream_t s);
 int hex_eo_cells_per_block(int n);
 // FP64 kernel choice.  The even-odd line kernel issues 16-30% fewer FP64
 // instructions (n = 5..9) but, with n^2 threads per cell, keeps the FP64 pipe
@@ -125,6 +138,7 @@ struct LaunchConfig {
   int cb = 0;
   bool agg = false;  // warp-aggregated atomic scatter (MFA_SCATTER_WARP)
   bool otf = false;  // geometry recomputed at every point from the vertices (MFA_GEOM_ONTHEFLY)
+  int max_blocks = 0;  // grid cap (GridBudget::max_blocks); 0: one wave of resident blocks
 };
 // Cells per block of a kernel with `per_cell` threads per cell for a target block size.
 constexpr int cells_for_target(int per_cell, int target) { return target / per_cell > 0 ? target / per_cell : 1; }
@@ -135,22 +149,22 @@ int hex_eo_cb_options(int n, int* out);
 int hex_line_cb_options(int n, int* out);
 int tet_cb_options(int* out);
 cudaError_t hex_point_launch_cb(int n, int nq, int kind, bool colour, int cb, const HexTables& tb,
-                                const HexApplyArgs& a, int sm_count, cudaStream_t s);
-cudaError_t hex_eo_apply_launch_cb(int n, int kind, bool colour, int cb, const HexApplyArgs& a, int sm_count,
+                                const HexApplyArgs& a, GridBudget budget, cudaStream_t s);
+cudaError_t hex_eo_apply_launch_cb(int n, int kind, bool colour, int cb, const HexApplyArgs& a, GridBudget budget,
                                    cudaStream_t s);
-cudaError_t hex_point_launch_agg(int n, int nq, int kind, const HexTables& tb, const HexApplyArgs& a, int sm_count,
+cudaError_t hex_point_launch_agg(int n, int nq, int kind, const HexTables& tb, const HexApplyArgs& a, GridBudget budget,
                                  cudaStream_t s);
 cudaError_t hex_point_launch_otf(int n, int nq, int kind, bool colour, const HexTables& tb, const HexApplyArgs& a,
-                                 int sm_count, cudaStream_t s);
+                                 GridBudget budget, cudaStream_t s);
 // FP32/BF16 action with float vectors.
 cudaError_t hex_apply_launch_f32(int n, int kind, int prec, const float* x, float* y, const int32_t* cell_node,
-                                 const void* geom, int64_t count, int64_t gstride, int* err, int sm_count,
+                                 const void* geom, int64_t count, int64_t gstride, int* err, GridBudget budget,
                                  cudaStream_t s);
 cudaError_t hex_geometry_launch(int nq, int kind, int prec, double c0, const HexTables& tb, const double* coords,
                                 const int32_t* cell_vert, int64_t ncell, void* geom, int64_t stride, int* err,
                                 cudaStream_t s);
 cudaError_t hex_diagonal_launch(int n, int nq, int kind, const HexTables& tb, const int32_t* cell_node,
-                                const double* geom, int64_t ncell, double* d, int sm_count, cudaStream_t s);
+                                const double* geom, int64_t ncell, double* d, GridBudget budget, cudaStream_t s);
 int hex_geom_entries(int kind);  // stored FP64 values per quadrature point
 
 // ---------------------------------------------------------------- tet kernels
@@ -185,7 +199,7 @@ struct TetApplyArgs {
 // components, form `kind` and an nq-point rule.
 bool tet_rule_compiled(int p, int ncomp, int kind, int nq);
 cudaError_t tet_apply_launch(int p, int ncomp, int kind, int law, bool colour, bool agg, int threads,
-                             const TetTables& tb, const TetApplyArgs& a, int sm_count, cudaStream_t s);
+                             const TetTables& tb, const TetApplyArgs& a, GridBudget budget, cudaStream_t s);
 // ---------------------------------------------------------------- quad kernels (quad_kernels.cu)
 struct QuadArgs {
   const double* x;
@@ -203,7 +217,7 @@ int quad_cells_per_block(int n, int nq);
 cudaError_t quad_geometry_launch(int nq, int kind, double c0, const HexTables& tb, const double* coords,
                                  const int32_t* cell_vert, int64_t ncell, double* geom, int* err, cudaStream_t s);
 cudaError_t quad_apply_launch(int n, int nq, int ncomp, int kind, int law, bool colour, const HexTables& tb,
-                              const QuadArgs& a, int sm_count, cudaStream_t s);
+                              const QuadArgs& a, GridBudget budget, cudaStream_t s);
 
 // P3..P6 (dense tabulation, one warp per cell).  Tables in device memory, nl local dofs, nq points.
 struct TetDenseArgs {
@@ -224,7 +238,7 @@ struct TetDenseArgs {
   double k2, lambda, mu, b0, b1, b2;
   int* err;
 };
-cudaError_t tet_dense_launch(int p, int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, int sm_count,
+cudaError_t tet_dense_launch(int p, int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, GridBudget budget,
                              cudaStream_t s);
 // Diagonals without a sum-factorised kernel (diag.cu): simplices from the
 // dense [q][a] tables (tets P3..P6, triangles), tensor cells from the 1D
@@ -243,9 +257,9 @@ struct TriTables {
   double dphi[kTriMaxQ * kTriMaxNl * 2];  // [q][a][e]
 };
 cudaError_t tri_cell_launch(int p, int ncomp, int kind, int law, bool colour, int threads, const TriTables& tb,
-                            const TetDenseArgs& a, int sm_count, cudaStream_t s);
+                            const TetDenseArgs& a, GridBudget budget, cudaStream_t s);
 // Triangles P1..P6 with the same kernel in the plane (gradient tables with 2 components: [nl][2][nq], [nq][nl][2]).
-cudaError_t tri_dense_launch(int p, int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, int sm_count,
+cudaError_t tri_dense_launch(int p, int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, GridBudget budget,
                              cudaStream_t s);
 cudaError_t tet_diagonal_launch(int p, int ncomp, int kind, const TetTables& tb, const TetApplyArgs& a,
                                 double* d, cudaStream_t s);

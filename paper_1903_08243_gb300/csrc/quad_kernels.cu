@@ -57,9 +57,9 @@ __global__ void quad_geometry_kernel(const __grid_constant__ HexTables tb, int n
 }  // namespace
 
 cudaError_t quad_apply_launch_a(int n, int nq, int ncomp, int kind, int law, bool colour, const HexTables& tb,
-                                const QuadArgs& a, int sm_count, cudaStream_t s);
+                                const QuadArgs& a, GridBudget budget, cudaStream_t s);
 cudaError_t quad_apply_launch_b(int n, int nq, int ncomp, int kind, int law, bool colour, const HexTables& tb,
-                                const QuadArgs& a, int sm_count, cudaStream_t s);
+                                const QuadArgs& a, GridBudget budget, cudaStream_t s);
 
 int quad_geom_entries(int kind) { return quad_geom_entries_for(kind); }
 
@@ -79,9 +79,9 @@ int quad_cells_per_block(int n, int nq) {
 }
 
 cudaError_t quad_apply_launch(int n, int nq, int ncomp, int kind, int law, bool colour, const HexTables& tb,
-                              const QuadArgs& a, int sm_count, cudaStream_t s) {
-  return n <= 5 ? quad_apply_launch_a(n, nq, ncomp, kind, law, colour, tb, a, sm_count, s)
-                : quad_apply_launch_b(n, nq, ncomp, kind, law, colour, tb, a, sm_count, s);
+                              const QuadArgs& a, GridBudget budget, cudaStream_t s) {
+  return n <= 5 ? quad_apply_launch_a(n, nq, ncomp, kind, law, colour, tb, a, budget, s)
+                : quad_apply_launch_b(n, nq, ncomp, kind, law, colour, tb, a, budget, s);
 }
 
 }  // namespace mfa

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(QShape<N, NQ>::T) quad_apply_kernel(const __gr
 }
 
 template <int N, int NQ, int NC, int KIND, int LAW, bool COLOUR>
-cudaError_t launch(const HexTables& tb, const QuadArgs& a, int sm_count, cudaStream_t s) {
+cudaError_t launch(const HexTables& tb, const QuadArgs& a, GridBudget budget, cudaStream_t s) {
   using S = QShape<N, NQ>;
   auto kern = quad_apply_kernel<N, NQ, NC, KIND, LAW, COLOUR>;
   static int bps = -1;
@@ -219,38 +219,38 @@ cudaError_t launch(const HexTables& tb, const QuadArgs& a, int sm_count, cudaStr
   }
   const int64_t nbatch = (a.count + S::CB - 1) / S::CB;
   if (nbatch == 0) return cudaSuccess;
-  const int64_t cap = (int64_t)sm_count * bps;
+  const int64_t cap = budget.cap(bps);
   kern<<<(unsigned)(nbatch < cap ? nbatch : cap), S::T, S::SMEM, s>>>(tb, a);
   return cudaGetLastError();
 }
 
 template <int N, int NQ, int NC, int KIND, int LAW>
-cudaError_t launch2(bool colour, const HexTables& tb, const QuadArgs& a, int sm_count, cudaStream_t s) {
-  return colour ? launch<N, NQ, NC, KIND, LAW, true>(tb, a, sm_count, s)
-                : launch<N, NQ, NC, KIND, LAW, false>(tb, a, sm_count, s);
+cudaError_t launch2(bool colour, const HexTables& tb, const QuadArgs& a, GridBudget budget, cudaStream_t s) {
+  return colour ? launch<N, NQ, NC, KIND, LAW, true>(tb, a, budget, s)
+                : launch<N, NQ, NC, KIND, LAW, false>(tb, a, budget, s);
 }
 
 template <int N, int NQ>
-cudaError_t by_form(int ncomp, int kind, int law, bool colour, const HexTables& tb, const QuadArgs& a, int sm_count,
+cudaError_t by_form(int ncomp, int kind, int law, bool colour, const HexTables& tb, const QuadArgs& a, GridBudget budget,
                     cudaStream_t s) {
   const bool nh = law == MFA_LAW_NEOHOOKE;
   if (ncomp == 1) {
     switch (kind) {
-      case MFA_FORM_MASS: return launch2<N, NQ, 1, MFA_FORM_MASS, 0>(colour, tb, a, sm_count, s);
-      case MFA_FORM_LAPLACE: return launch2<N, NQ, 1, MFA_FORM_LAPLACE, 0>(colour, tb, a, sm_count, s);
-      case MFA_FORM_HELMHOLTZ: return launch2<N, NQ, 1, MFA_FORM_HELMHOLTZ, 0>(colour, tb, a, sm_count, s);
+      case MFA_FORM_MASS: return launch2<N, NQ, 1, MFA_FORM_MASS, 0>(colour, tb, a, budget, s);
+      case MFA_FORM_LAPLACE: return launch2<N, NQ, 1, MFA_FORM_LAPLACE, 0>(colour, tb, a, budget, s);
+      case MFA_FORM_HELMHOLTZ: return launch2<N, NQ, 1, MFA_FORM_HELMHOLTZ, 0>(colour, tb, a, budget, s);
     }
     return cudaErrorInvalidValue;
   }
   switch (kind) {
-    case MFA_FORM_LAPLACE: return launch2<N, NQ, 2, MFA_FORM_LAPLACE, 0>(colour, tb, a, sm_count, s);
-    case MFA_FORM_ELASTICITY: return launch2<N, NQ, 2, MFA_FORM_ELASTICITY, 0>(colour, tb, a, sm_count, s);
+    case MFA_FORM_LAPLACE: return launch2<N, NQ, 2, MFA_FORM_LAPLACE, 0>(colour, tb, a, budget, s);
+    case MFA_FORM_ELASTICITY: return launch2<N, NQ, 2, MFA_FORM_ELASTICITY, 0>(colour, tb, a, budget, s);
     case MFA_FORM_HYPER_RES:
-      return nh ? launch2<N, NQ, 2, MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(colour, tb, a, sm_count, s)
-                : launch2<N, NQ, 2, MFA_FORM_HYPER_RES, MFA_LAW_SVK>(colour, tb, a, sm_count, s);
+      return nh ? launch2<N, NQ, 2, MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(colour, tb, a, budget, s)
+                : launch2<N, NQ, 2, MFA_FORM_HYPER_RES, MFA_LAW_SVK>(colour, tb, a, budget, s);
     case MFA_FORM_HYPER_JAC:
-      return nh ? launch2<N, NQ, 2, MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(colour, tb, a, sm_count, s)
-                : launch2<N, NQ, 2, MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(colour, tb, a, sm_count, s);
+      return nh ? launch2<N, NQ, 2, MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(colour, tb, a, budget, s)
+                : launch2<N, NQ, 2, MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(colour, tb, a, budget, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -258,14 +258,14 @@ cudaError_t by_form(int ncomp, int kind, int law, bool colour, const HexTables& 
 // p+1 and p+2 points per direction for every form, 2p+2 for the hyperelastic forms (2n <= 10).
 template <int N>
 cudaError_t by_rule(int nq, int ncomp, int kind, int law, bool colour, const HexTables& tb, const QuadArgs& a,
-                    int sm_count, cudaStream_t s) {
-  if (nq == N) return by_form<N, N>(ncomp, kind, law, colour, tb, a, sm_count, s);
+                    GridBudget budget, cudaStream_t s) {
+  if (nq == N) return by_form<N, N>(ncomp, kind, law, colour, tb, a, budget, s);
   if constexpr (N + 1 <= kMaxN) {
-    if (nq == N + 1) return by_form<N, N + 1>(ncomp, kind, law, colour, tb, a, sm_count, s);
+    if (nq == N + 1) return by_form<N, N + 1>(ncomp, kind, law, colour, tb, a, budget, s);
   }
   if constexpr (2 * N <= kMaxN && 2 * N != N + 1) {
     if (nq == 2 * N && (kind == MFA_FORM_HYPER_RES || kind == MFA_FORM_HYPER_JAC))
-      return by_form<N, 2 * N>(ncomp, kind, law, colour, tb, a, sm_count, s);
+      return by_form<N, 2 * N>(ncomp, kind, law, colour, tb, a, budget, s);
   }
   return cudaErrorInvalidValue;
 }

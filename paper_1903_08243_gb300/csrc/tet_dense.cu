@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(32 * kWarps) simplex_dense_kernel(const TetDen
 }
 
 template <int DIM, int NL, int NC, int KIND, int LAW, bool COLOUR>
-cudaError_t launch(const TetDenseArgs& a, int sm_count, cudaStream_t s) {
+cudaError_t launch(const TetDenseArgs& a, GridBudget budget, cudaStream_t s) {
   if (a.count == 0) return cudaSuccess;
   auto kern = simplex_dense_kernel<DIM, NL, NC, KIND, LAW, COLOUR>;
   constexpr int smem = kWarps * DenseShape<NL, NC, KIND>::SMEM_WARP * (int)sizeof(double);
@@ -235,65 +235,65 @@ cudaError_t launch(const TetDenseArgs& a, int sm_count, cudaStream_t s) {
     bps = v < 1 ? 1 : v;
   }
   int64_t blocks = (a.count + kWarps - 1) / kWarps;
-  const int64_t cap = (int64_t)sm_count * bps;
+  const int64_t cap = budget.cap(bps);
   if (blocks > cap) blocks = cap;
   kern<<<(unsigned)blocks, 32 * kWarps, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int DIM, int NL, int NC, int KIND, int LAW>
-cudaError_t launch2(bool colour, const TetDenseArgs& a, int sm_count, cudaStream_t s) {
-  return colour ? launch<DIM, NL, NC, KIND, LAW, true>(a, sm_count, s)
-                : launch<DIM, NL, NC, KIND, LAW, false>(a, sm_count, s);
+cudaError_t launch2(bool colour, const TetDenseArgs& a, GridBudget budget, cudaStream_t s) {
+  return colour ? launch<DIM, NL, NC, KIND, LAW, true>(a, budget, s)
+                : launch<DIM, NL, NC, KIND, LAW, false>(a, budget, s);
 }
 
 template <int DIM, int NL>
-cudaError_t by_form(int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, int sm_count, cudaStream_t s) {
+cudaError_t by_form(int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, GridBudget budget, cudaStream_t s) {
   const bool nh = law == MFA_LAW_NEOHOOKE;
   if (ncomp == 1) {
     switch (kind) {
-      case MFA_FORM_MASS: return launch2<DIM, NL, 1, MFA_FORM_MASS, 0>(colour, a, sm_count, s);
-      case MFA_FORM_LAPLACE: return launch2<DIM, NL, 1, MFA_FORM_LAPLACE, 0>(colour, a, sm_count, s);
-      case MFA_FORM_HELMHOLTZ: return launch2<DIM, NL, 1, MFA_FORM_HELMHOLTZ, 0>(colour, a, sm_count, s);
+      case MFA_FORM_MASS: return launch2<DIM, NL, 1, MFA_FORM_MASS, 0>(colour, a, budget, s);
+      case MFA_FORM_LAPLACE: return launch2<DIM, NL, 1, MFA_FORM_LAPLACE, 0>(colour, a, budget, s);
+      case MFA_FORM_HELMHOLTZ: return launch2<DIM, NL, 1, MFA_FORM_HELMHOLTZ, 0>(colour, a, budget, s);
     }
     return cudaErrorInvalidValue;
   }
   if (ncomp != DIM) return cudaErrorInvalidValue;
   switch (kind) {
-    case MFA_FORM_LAPLACE: return launch2<DIM, NL, DIM, MFA_FORM_LAPLACE, 0>(colour, a, sm_count, s);
-    case MFA_FORM_ELASTICITY: return launch2<DIM, NL, DIM, MFA_FORM_ELASTICITY, 0>(colour, a, sm_count, s);
+    case MFA_FORM_LAPLACE: return launch2<DIM, NL, DIM, MFA_FORM_LAPLACE, 0>(colour, a, budget, s);
+    case MFA_FORM_ELASTICITY: return launch2<DIM, NL, DIM, MFA_FORM_ELASTICITY, 0>(colour, a, budget, s);
     case MFA_FORM_HYPER_RES:
-      return nh ? launch2<DIM, NL, DIM, MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(colour, a, sm_count, s)
-                : launch2<DIM, NL, DIM, MFA_FORM_HYPER_RES, MFA_LAW_SVK>(colour, a, sm_count, s);
+      return nh ? launch2<DIM, NL, DIM, MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(colour, a, budget, s)
+                : launch2<DIM, NL, DIM, MFA_FORM_HYPER_RES, MFA_LAW_SVK>(colour, a, budget, s);
     case MFA_FORM_HYPER_JAC:
-      return nh ? launch2<DIM, NL, DIM, MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(colour, a, sm_count, s)
-                : launch2<DIM, NL, DIM, MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(colour, a, sm_count, s);
+      return nh ? launch2<DIM, NL, DIM, MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(colour, a, budget, s)
+                : launch2<DIM, NL, DIM, MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(colour, a, budget, s);
   }
   return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-cudaError_t tet_dense_launch(int p, int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, int sm_count,
+cudaError_t tet_dense_launch(int p, int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, GridBudget budget,
                              cudaStream_t s) {
   switch (p) {
-    case 3: return by_form<3, 20>(ncomp, kind, law, colour, a, sm_count, s);
-    case 4: return by_form<3, 35>(ncomp, kind, law, colour, a, sm_count, s);
-    case 5: return by_form<3, 56>(ncomp, kind, law, colour, a, sm_count, s);
-    case 6: return by_form<3, 84>(ncomp, kind, law, colour, a, sm_count, s);
+    case 3: return by_form<3, 20>(ncomp, kind, law, colour, a, budget, s);
+    case 4: return by_form<3, 35>(ncomp, kind, law, colour, a, budget, s);
+    case 5: return by_form<3, 56>(ncomp, kind, law, colour, a, budget, s);
+    case 6: return by_form<3, 84>(ncomp, kind, law, colour, a, budget, s);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t tri_dense_launch(int p, int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, int sm_count,
+cudaError_t tri_dense_launch(int p, int ncomp, int kind, int law, bool colour, const TetDenseArgs& a, GridBudget budget,
                              cudaStream_t s) {
   switch (p) {
-    case 1: return by_form<2, 3>(ncomp, kind, law, colour, a, sm_count, s);
-    case 2: return by_form<2, 6>(ncomp, kind, law, colour, a, sm_count, s);
-    case 3: return by_form<2, 10>(ncomp, kind, law, colour, a, sm_count, s);
-    case 4: return by_form<2, 15>(ncomp, kind, law, colour, a, sm_count, s);
-    case 5: return by_form<2, 21>(ncomp, kind, law, colour, a, sm_count, s);
-    case 6: return by_form<2, 28>(ncomp, kind, law, colour, a, sm_count, s);
+    case 1: return by_form<2, 3>(ncomp, kind, law, colour, a, budget, s);
+    case 2: return by_form<2, 6>(ncomp, kind, law, colour, a, budget, s);
+    case 3: return by_form<2, 10>(ncomp, kind, law, colour, a, budget, s);
+    case 4: return by_form<2, 15>(ncomp, kind, law, colour, a, budget, s);
+    case 5: return by_form<2, 21>(ncomp, kind, law, colour, a, budget, s);
+    case 6: return by_form<2, 28>(ncomp, kind, law, colour, a, budget, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(128) tet_moment_kernel(const __grid_constant__
 // the resident blocks of all SMs; `bps` caches the occupancy per block size.
 template <typename Kern>
 cudaError_t launch_cells(Kern kern, int (&bps)[4], int threads, const TetTables& tb, const TetApplyArgs& a,
-                         int sm_count, cudaStream_t s) {
+                         GridBudget budget, cudaStream_t s) {
   if (a.count == 0) return cudaSuccess;
   if (threads != 32 && threads != 64 && threads != 128) return cudaErrorInvalidValue;
   int& b = bps[threads / 32 - 1];
@@ -328,7 +328,7 @@ cudaError_t launch_cells(Kern kern, int (&bps)[4], int threads, const TetTables&
     b = v < 1 ? 1 : v;
   }
   int64_t blocks = (a.count + threads - 1) / threads;
-  const int64_t cap = (int64_t)sm_count * b;
+  const int64_t cap = budget.cap(b);
   if (blocks > cap) blocks = cap;
   kern<<<(unsigned)blocks, threads, 0, s>>>(tb, a);
   return cudaGetLastError();
@@ -336,26 +336,26 @@ cudaError_t launch_cells(Kern kern, int (&bps)[4], int threads, const TetTables&
 
 // sc: scatter mode as for the kernels (0 atomic, 1 colour, 2 warp-aggregated)
 template <int KIND, int LAW>
-cudaError_t launch_moment(int sc, int threads, const TetTables& tb, const TetApplyArgs& a, int sm_count,
+cudaError_t launch_moment(int sc, int threads, const TetTables& tb, const TetApplyArgs& a, GridBudget budget,
                           cudaStream_t s) {
   static int bps[3][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}, {-1, -1, -1, -1}};  // per scatter mode and block size
-  if (sc == 1) return launch_cells(tet_moment_kernel<KIND, LAW, 1>, bps[1], threads, tb, a, sm_count, s);
-  if (sc == 2) return launch_cells(tet_moment_kernel<KIND, LAW, 2>, bps[2], threads, tb, a, sm_count, s);
-  return launch_cells(tet_moment_kernel<KIND, LAW, 0>, bps[0], threads, tb, a, sm_count, s);
+  if (sc == 1) return launch_cells(tet_moment_kernel<KIND, LAW, 1>, bps[1], threads, tb, a, budget, s);
+  if (sc == 2) return launch_cells(tet_moment_kernel<KIND, LAW, 2>, bps[2], threads, tb, a, budget, s);
+  return launch_cells(tet_moment_kernel<KIND, LAW, 0>, bps[0], threads, tb, a, budget, s);
 }
 
 template <int P, int NC, int KIND, int LAW, int NQ, int SC>
-cudaError_t launch(int threads, const TetTables& tb, const TetApplyArgs& a, int sm_count, cudaStream_t s) {
+cudaError_t launch(int threads, const TetTables& tb, const TetApplyArgs& a, GridBudget budget, cudaStream_t s) {
   static int bps[4] = {-1, -1, -1, -1};
-  return launch_cells(tet_apply_kernel<P, NC, KIND, LAW, NQ, SC>, bps, threads, tb, a, sm_count, s);
+  return launch_cells(tet_apply_kernel<P, NC, KIND, LAW, NQ, SC>, bps, threads, tb, a, budget, s);
 }
 
 template <int P, int NC, int KIND, int LAW, int NQ>
-cudaError_t launch2(int sc, int threads, const TetTables& tb, const TetApplyArgs& a, int sm_count,
+cudaError_t launch2(int sc, int threads, const TetTables& tb, const TetApplyArgs& a, GridBudget budget,
                     cudaStream_t s) {
-  if (sc == 1) return launch<P, NC, KIND, LAW, NQ, 1>(threads, tb, a, sm_count, s);
-  if (sc == 2) return launch<P, NC, KIND, LAW, NQ, 2>(threads, tb, a, sm_count, s);
-  return launch<P, NC, KIND, LAW, NQ, 0>(threads, tb, a, sm_count, s);
+  if (sc == 1) return launch<P, NC, KIND, LAW, NQ, 1>(threads, tb, a, budget, s);
+  if (sc == 2) return launch<P, NC, KIND, LAW, NQ, 2>(threads, tb, a, budget, s);
+  return launch<P, NC, KIND, LAW, NQ, 0>(threads, tb, a, budget, s);
 }
 
 // Diagonal of the linear forms, per local dof and cell:
@@ -442,33 +442,33 @@ bool tet_rule_compiled(int p, int ncomp, int kind, int nq) {
 }
 
 cudaError_t tet_apply_launch(int p, int ncomp, int kind, int law, bool colour, bool agg, int threads,
-                             const TetTables& tb, const TetApplyArgs& a, int sm_count, cudaStream_t s) {
+                             const TetTables& tb, const TetApplyArgs& a, GridBudget budget, cudaStream_t s) {
   const int sc = colour ? 1 : (agg ? 2 : 0);
   if (!tet_rule_compiled(p, ncomp, kind, tb.nq)) return cudaErrorInvalidValue;
   if (p == 1) {
     switch (kind) {
-      case MFA_FORM_MASS: return launch2<1, 1, MFA_FORM_MASS, 0, 4>(sc, threads, tb, a, sm_count, s);
-      case MFA_FORM_LAPLACE: return launch2<1, 1, MFA_FORM_LAPLACE, 0, 1>(sc, threads, tb, a, sm_count, s);
-      case MFA_FORM_HELMHOLTZ: return launch2<1, 1, MFA_FORM_HELMHOLTZ, 0, 4>(sc, threads, tb, a, sm_count, s);
+      case MFA_FORM_MASS: return launch2<1, 1, MFA_FORM_MASS, 0, 4>(sc, threads, tb, a, budget, s);
+      case MFA_FORM_LAPLACE: return launch2<1, 1, MFA_FORM_LAPLACE, 0, 1>(sc, threads, tb, a, budget, s);
+      case MFA_FORM_HELMHOLTZ: return launch2<1, 1, MFA_FORM_HELMHOLTZ, 0, 4>(sc, threads, tb, a, budget, s);
     }
   }
   if (p == 2 && ncomp == 1) {
     switch (kind) {
-      case MFA_FORM_MASS: return launch2<2, 1, MFA_FORM_MASS, 0, 14>(sc, threads, tb, a, sm_count, s);
-      case MFA_FORM_LAPLACE: return launch2<2, 1, MFA_FORM_LAPLACE, 0, 4>(sc, threads, tb, a, sm_count, s);
-      case MFA_FORM_HELMHOLTZ: return launch2<2, 1, MFA_FORM_HELMHOLTZ, 0, 14>(sc, threads, tb, a, sm_count, s);
+      case MFA_FORM_MASS: return launch2<2, 1, MFA_FORM_MASS, 0, 14>(sc, threads, tb, a, budget, s);
+      case MFA_FORM_LAPLACE: return launch2<2, 1, MFA_FORM_LAPLACE, 0, 4>(sc, threads, tb, a, budget, s);
+      case MFA_FORM_HELMHOLTZ: return launch2<2, 1, MFA_FORM_HELMHOLTZ, 0, 14>(sc, threads, tb, a, budget, s);
     }
   }
   if (p == 2 && ncomp == 3) {
     switch (kind) {
-      case MFA_FORM_LAPLACE: return launch2<2, 3, MFA_FORM_LAPLACE, 0, 4>(sc, threads, tb, a, sm_count, s);
-      case MFA_FORM_ELASTICITY: return launch2<2, 3, MFA_FORM_ELASTICITY, 0, 4>(sc, threads, tb, a, sm_count, s);
+      case MFA_FORM_LAPLACE: return launch2<2, 3, MFA_FORM_LAPLACE, 0, 4>(sc, threads, tb, a, budget, s);
+      case MFA_FORM_ELASTICITY: return launch2<2, 3, MFA_FORM_ELASTICITY, 0, 4>(sc, threads, tb, a, budget, s);
       case MFA_FORM_HYPER_RES:
-        return law == MFA_LAW_SVK ? launch_moment<MFA_FORM_HYPER_RES, MFA_LAW_SVK>(sc, threads, tb, a, sm_count, s)
-                                  : launch_moment<MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(sc, threads, tb, a, sm_count, s);
+        return law == MFA_LAW_SVK ? launch_moment<MFA_FORM_HYPER_RES, MFA_LAW_SVK>(sc, threads, tb, a, budget, s)
+                                  : launch_moment<MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(sc, threads, tb, a, budget, s);
       case MFA_FORM_HYPER_JAC:
-        return law == MFA_LAW_SVK ? launch_moment<MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(sc, threads, tb, a, sm_count, s)
-                                  : launch_moment<MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(sc, threads, tb, a, sm_count, s);
+        return law == MFA_LAW_SVK ? launch_moment<MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(sc, threads, tb, a, budget, s)
+                                  : launch_moment<MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(sc, threads, tb, a, budget, s);
     }
   }
   return cudaErrorInvalidValue;

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(128) tri_cell_kernel(const __grid_constant__ T
 }
 
 template <int NL, int NC, int KIND, int LAW, bool COLOUR>
-cudaError_t launch(int threads, const TriTables& tb, const TetDenseArgs& a, int sm_count, cudaStream_t s) {
+cudaError_t launch(int threads, const TriTables& tb, const TetDenseArgs& a, GridBudget budget, cudaStream_t s) {
   if (a.count == 0) return cudaSuccess;
   if (threads != 32 && threads != 64 && threads != 128) return cudaErrorInvalidValue;
   auto kern = tri_cell_kernel<NL, NC, KIND, LAW, COLOUR>;
@@ -144,41 +144,41 @@ cudaError_t launch(int threads, const TriTables& tb, const TetDenseArgs& a, int 
     b = v < 1 ? 1 : v;
   }
   int64_t blocks = (a.count + threads - 1) / threads;
-  const int64_t cap = (int64_t)sm_count * b;
+  const int64_t cap = budget.cap(b);
   if (blocks > cap) blocks = cap;
   kern<<<(unsigned)blocks, threads, 0, s>>>(tb, a);
   return cudaGetLastError();
 }
 
 template <int NL, int NC, int KIND, int LAW>
-cudaError_t launch2(bool colour, int threads, const TriTables& tb, const TetDenseArgs& a, int sm_count,
+cudaError_t launch2(bool colour, int threads, const TriTables& tb, const TetDenseArgs& a, GridBudget budget,
                     cudaStream_t s) {
-  return colour ? launch<NL, NC, KIND, LAW, true>(threads, tb, a, sm_count, s)
-                : launch<NL, NC, KIND, LAW, false>(threads, tb, a, sm_count, s);
+  return colour ? launch<NL, NC, KIND, LAW, true>(threads, tb, a, budget, s)
+                : launch<NL, NC, KIND, LAW, false>(threads, tb, a, budget, s);
 }
 
 template <int NL>
 cudaError_t by_form(int ncomp, int kind, int law, bool colour, int threads, const TriTables& tb,
-                    const TetDenseArgs& a, int sm_count, cudaStream_t s) {
+                    const TetDenseArgs& a, GridBudget budget, cudaStream_t s) {
   const bool nh = law == MFA_LAW_NEOHOOKE;
   if (ncomp == 1) {
     switch (kind) {
-      case MFA_FORM_MASS: return launch2<NL, 1, MFA_FORM_MASS, 0>(colour, threads, tb, a, sm_count, s);
-      case MFA_FORM_LAPLACE: return launch2<NL, 1, MFA_FORM_LAPLACE, 0>(colour, threads, tb, a, sm_count, s);
-      case MFA_FORM_HELMHOLTZ: return launch2<NL, 1, MFA_FORM_HELMHOLTZ, 0>(colour, threads, tb, a, sm_count, s);
+      case MFA_FORM_MASS: return launch2<NL, 1, MFA_FORM_MASS, 0>(colour, threads, tb, a, budget, s);
+      case MFA_FORM_LAPLACE: return launch2<NL, 1, MFA_FORM_LAPLACE, 0>(colour, threads, tb, a, budget, s);
+      case MFA_FORM_HELMHOLTZ: return launch2<NL, 1, MFA_FORM_HELMHOLTZ, 0>(colour, threads, tb, a, budget, s);
     }
     return cudaErrorInvalidValue;
   }
   switch (kind) {
-    case MFA_FORM_LAPLACE: return launch2<NL, 2, MFA_FORM_LAPLACE, 0>(colour, threads, tb, a, sm_count, s);
-    case MFA_FORM_ELASTICITY: return launch2<NL, 2, MFA_FORM_ELASTICITY, 0>(colour, threads, tb, a, sm_count, s);
+    case MFA_FORM_LAPLACE: return launch2<NL, 2, MFA_FORM_LAPLACE, 0>(colour, threads, tb, a, budget, s);
+    case MFA_FORM_ELASTICITY: return launch2<NL, 2, MFA_FORM_ELASTICITY, 0>(colour, threads, tb, a, budget, s);
     case MFA_FORM_HYPER_RES:
-      return nh ? launch2<NL, 2, MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(colour, threads, tb, a, sm_count, s)
-                : launch2<NL, 2, MFA_FORM_HYPER_RES, MFA_LAW_SVK>(colour, threads, tb, a, sm_count, s);
+      return nh ? launch2<NL, 2, MFA_FORM_HYPER_RES, MFA_LAW_NEOHOOKE>(colour, threads, tb, a, budget, s)
+                : launch2<NL, 2, MFA_FORM_HYPER_RES, MFA_LAW_SVK>(colour, threads, tb, a, budget, s);
     case MFA_FORM_HYPER_JAC:
       if constexpr (NL <= 10) {
-        return nh ? launch2<NL, 2, MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(colour, threads, tb, a, sm_count, s)
-                  : launch2<NL, 2, MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(colour, threads, tb, a, sm_count, s);
+        return nh ? launch2<NL, 2, MFA_FORM_HYPER_JAC, MFA_LAW_NEOHOOKE>(colour, threads, tb, a, budget, s)
+                  : launch2<NL, 2, MFA_FORM_HYPER_JAC, MFA_LAW_SVK>(colour, threads, tb, a, budget, s);
       } else {
         return cudaErrorInvalidValue;  // P4: the linearisation point would spill; one warp per cell instead
       }
@@ -189,12 +189,12 @@ cudaError_t by_form(int ncomp, int kind, int law, bool colour, int threads, cons
 }  // namespace
 
 cudaError_t tri_cell_launch(int p, int ncomp, int kind, int law, bool colour, int threads, const TriTables& tb,
-                            const TetDenseArgs& a, int sm_count, cudaStream_t s) {
+                            const TetDenseArgs& a, GridBudget budget, cudaStream_t s) {
   switch (p) {
-    case 1: return by_form<3>(ncomp, kind, law, colour, threads, tb, a, sm_count, s);
-    case 2: return by_form<6>(ncomp, kind, law, colour, threads, tb, a, sm_count, s);
-    case 3: return by_form<10>(ncomp, kind, law, colour, threads, tb, a, sm_count, s);
-    case 4: return by_form<15>(ncomp, kind, law, colour, threads, tb, a, sm_count, s);
+    case 1: return by_form<3>(ncomp, kind, law, colour, threads, tb, a, budget, s);
+    case 2: return by_form<6>(ncomp, kind, law, colour, threads, tb, a, budget, s);
+    case 3: return by_form<10>(ncomp, kind, law, colour, threads, tb, a, budget, s);
+    case 4: return by_form<15>(ncomp, kind, law, colour, threads, tb, a, budget, s);
   }
   return cudaErrorInvalidValue;
 }
