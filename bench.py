@@ -29,11 +29,12 @@ import fe_inputs as fi  # noqa: E402
 
 # FP64 pipe of GB300: 152 SMs x 2 DFMA lanes/clk x 2 flop x 2070 MHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-# DRAM traffic per launch of the dominant kernel from one ncu capture, valid only
-# while the kernel source is unchanged (sha1 of hex_kernels.cuh).
-# 32^3 capture (868.2 MB per launch) scaled by the cell count to the 64^3 launch;
-# see profiles/hex_apply_q6_helmholtz_hex32.md.
-NCU_TRAFFIC = {("34a9a704426a", "Q6 helmholtz"): 8 * 869.22e6}  # eo kernel, ncu on 32^3 scaled by cells to 64^3
+# DRAM traffic per launch of the dominant kernel from one ncu capture, keyed by the
+# sha1 (first 12 hex digits) of the kernel's source file and the operator, so that
+# it is reported only while that source is unchanged.  Even-odd kernel (hex_eo.cuh),
+# Q6 Helmholtz: the 32^3 capture (869.22 MB per launch) scaled by the cell count to
+# the 64^3 launch (profiles/eo_apply_q6_helmholtz_hex32.md).
+NCU_TRAFFIC = {("34a9a704426a", "Q6 helmholtz"): 8 * 869.22e6}
 
 
 def parse_args():
@@ -574,7 +575,7 @@ def gpu_arm(args, world, rank, local):
     time.sleep(0.3)
     clocks = sampler.stop()
     ctx.sync()
-    per_op_ms = [statistics.mean(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
+    per_op_ms = [statistics.median(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
                  for i in range(len(ops))]
     step_ms = allreduce_max(world, sum(per_op_ms))
     ndof_step = sum(o["case"]["ndof"] for o in ops)
@@ -716,7 +717,11 @@ def gpu_arm(args, world, rank, local):
             "dtype": {"fp64": "f64", "fp32": "f32 (FP64 vectors)", "bf16": "bf16 operands, f32 accumulation"}[
                 args.precision if args.workload == "hex" else "fp64"],
             "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": launches_per_step * args.steps, "wall_s_timed_region": t_wall, "per_operator": per_op,
+            "gpu_launches": launches_per_step * args.steps, "wall_s_timed_region": t_wall,
+            "ms_per_step_bracketed": t_wall / args.steps * 1e3,
+            "timing": "ms_per_step = sum over operators of the median (over steps) of each operator's CUDA-event "
+                      "time; ms_per_step_bracketed = wall time of the timed steps / steps (includes the L2 flush)",
+            "per_operator": per_op,
         }
         print(json.dumps(line), flush=True)
 
@@ -726,6 +731,42 @@ def batched_specs(nops, seed=3):
     deg = fi.randint(seed, 0xDE6, nops, 1, 8)
     side = fi.randint(seed, 0x51DE, nops, 8, 48)
     return [(int(p), int(n)) for p, n in zip(deg, side)]
+
+
+BATCHED_SAMPLE_DOFS = {1: 64, 2: 64, 3: 48, 4: 32, 5: 24, 6: 16, 7: 12, 8: 8}
+
+
+def batched_oracle_leg(hosts, y_host, world):
+    """Per operator: the FP64 oracle on the cells touching a few random dofs (seeded), its time (CPU baseline,
+    one core, scaled by cells to the whole operator) and the relative L2 and max errors of the GPU result at those
+    dofs (the reference there is complete: every cell that adds into them is applied)."""
+    import oracle
+
+    errs, full_s, ncells, nsample = [], 0.0, 0, 0
+    tol = None
+    for i, h in enumerate(hosts):
+        rng = np.random.default_rng(4000 + i)
+        dofs = rng.choice(h["nnode"], size=min(BATCHED_SAMPLE_DOFS[h["p"]], h["nnode"]), replace=False)
+        cells = np.nonzero(np.isin(h["cell_node"], dofs).any(axis=1))[0]
+        pb = oracle.Problem(oracle.HEX, h["mesh"].coords, h["mesh"].cell_vert, h["p"], h["cell_node"], h["nnode"],
+                            oracle.HELMHOLTZ, k2=1.0)
+        t0 = time.perf_counter()
+        ref = pb.apply(h["x"], cells=cells)
+        dt = time.perf_counter() - t0
+        full_s += dt * h["mesh"].ncell / cells.size
+        ncells += cells.size
+        nsample += dofs.size
+        y, r = y_host[i][dofs], ref[dofs]
+        errs.append({"rel_l2": float(np.linalg.norm(y - r) / np.linalg.norm(r)),
+                     "max_rel": float(np.abs(y - r).max() / np.abs(r).max())})
+    ndof = sum(h["nnode"] for h in hosts)
+    cpu = {"value": world * ndof / full_s / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+           "sample": "per operator the cells touching %d random dofs (8 to 64 by degree; %d cells in all), timed "
+                     "once and scaled by cells to the whole operator" % (nsample, ncells)}
+    acc = {"reference": "FP64 oracle (oracle/) on the cells touching the sampled dofs", "dofs_sampled": nsample,
+           "per_operator": errs, "max_rel_l2": max(e["rel_l2"] for e in errs),
+           "max_max_rel": max(e["max_rel"] for e in errs)}
+    return cpu, acc
 
 
 def batched_arm(args, world, rank, local):
@@ -741,22 +782,21 @@ def batched_arm(args, world, rank, local):
     ctx = mfa.Context(local, stream)
     prec = {"fp64": mfa.MFA_PREC_FP64, "fp32": mfa.MFA_PREC_FP32, "bf16": mfa.MFA_PREC_BF16}[args.precision]
     specs = batched_specs(args.nops)
-    keep, forms, ref_forms, xs, ys, yrefs, infos = [], [], [], [], [], [], []
+    keep, forms, xs, ys, infos, hosts = [], [], [], [], [], []
     for i, (p, n) in enumerate(specs):
         mesh = fi.hex_box_mesh(n, perturb=0.1, seed=1000 + i)
         cell_node, nnode = fi.hex_node_map(n, p)
         m = mfa.Mesh(ctx, mfa.MFA_CELL_HEX8, mesh.coords, mesh.cell_vert)
         sp = mfa.Space(m, p, 1, cell_node, nnode)
         f = mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ, k2=1.0, precision=prec)
-        x = torch.from_numpy(fi.uniform_vector(nnode, seed=2000 + i)).cuda()
+        xh = fi.uniform_vector(nnode, seed=2000 + i)
+        x = torch.from_numpy(xh).cuda()
         keep.append((m, sp))
         forms.append(f)
         xs.append(x)
         ys.append(torch.empty_like(x))
         infos.append(f.info())
-        if prec != mfa.MFA_PREC_FP64:
-            ref_forms.append(mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ, k2=1.0, precision=mfa.MFA_PREC_FP64))
-            yrefs.append(torch.empty_like(x))
+        hosts.append(dict(p=p, n=n, mesh=mesh, cell_node=cell_node, nnode=nnode, x=xh))
     ctx.sync()
     batch = mfa.mfa_batch_create(ctx.h, [f.h for f in forms], xs, ys)
     ngroups, nsingles = mfa.mfa_batch_info(batch)
@@ -783,16 +823,33 @@ def batched_arm(args, world, rank, local):
     time.sleep(0.3)
     clocks = sampler.stop()
     ctx.sync()
-    step_ms = allreduce_max(world, statistics.mean(a.elapsed_time(b) for a, b in ev))
+    step_ms = allreduce_max(world, statistics.median(a.elapsed_time(b) for a, b in ev))
     ndof = sum(i.ndof for i in infos)
     value = world * ndof / (step_ms / 1e3) / 1e9
-    errors = []
-    if ref_forms:
-        for f, x, y, yr in zip(ref_forms, xs, ys, yrefs):
-            f.apply(x, yr)
-        ctx.sync()
-        for y, yr in zip(ys, yrefs):
-            errors.append(float(torch.linalg.norm(y - yr) / torch.linalg.norm(yr)))
+    y_host = [y.cpu().numpy() for y in ys]
+
+    # end to end through the C ABI with host buffers: every operator's x copied in and y copied out each step
+    e2e = None
+    if args.e2e_steps > 0:
+        hx = [torch.from_numpy(h["x"]).pin_memory() for h in hosts]
+        hy = [torch.empty_like(t).pin_memory() for t in hx]
+        forms_h = [f.h for f in forms]
+        mfa.mfa_apply_host_many(ctx.h, forms_h, hx, hy)  # warm the staging buffers and copy streams
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            mfa.mfa_apply_host_many(ctx.h, forms_h, hx, hy)
+        dt = allreduce_max(world, (time.perf_counter() - t0) / args.e2e_steps)
+        e2e = {"value": world * ndof / dt / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * ndof,
+               "d2h_bytes_per_step": 8 * ndof, "ms_per_step": dt * 1e3,
+               "path": "mfa_apply_host_many: pinned FP64 host buffers, copies overlapped with the applies (one "
+                       "launch per operator, not the grouped graph)"}
+
+    # CPU baseline and accuracy: the FP64 oracle on the cells touching a few random dofs of every operator, timed
+    # (one core), and the GPU result at those dofs compared with it
+    cpu, accuracy = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu, accuracy = batched_oracle_leg(hosts, y_host, world)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
@@ -821,8 +878,8 @@ def batched_arm(args, world, rank, local):
                        "launch": "one CUDA graph replay: %d grouped persistent launches + %d single launches" % (ngroups, nsingles),
                        "l2": "flushed between steps (256 MiB write outside the timed events)"},
             "roofline": roofline, "clocks": clocks, "gpu_launches": (ngroups + nsingles) * args.steps,
-            "error_vs_fp64": {"max": max(errors), "mean": statistics.mean(errors)} if errors else None,
-            "wall_s_timed_region": t_wall, "cpu_baseline": None, "e2e": None,
+            "error_vs_oracle": accuracy, "wall_s_timed_region": t_wall,
+            "ms_per_step_bracketed": t_wall / args.steps * 1e3, "cpu_baseline": cpu, "e2e": e2e,
         }
         print(json.dumps(line), flush=True)
     mfa.mfa_batch_destroy(batch)

@@ -11,6 +11,14 @@ each node) at the cell's nodes, D is the operator diagonal.  Training
 minimises L = (M(r) - e)^T A (M(r) - e) / (e^T A e) over (residual, error)
 pairs; `loss_and_grad` returns L and its exact gradient by backpropagation
 through the MLP, the scaling, and the assembly.
+
+Operand precision.  The network's weights are BF16 (the caller passes them
+rounded), and the kernels that evaluate it multiply BF16 operands with FP32
+accumulation: the normalised inputs Z and the hidden activations H in the
+forward pass, dL/dO and dL/dH in the backward pass.  `rnd`, when given, is
+applied to exactly those four operands, so that a test can compare a kernel
+with this oracle at the kernel's operand precision; the default (None) keeps
+everything in FP64.  It rounds values only: the order of the steps is the same.
 """
 import numpy as np
 
@@ -20,29 +28,35 @@ def multiplicity_weights(cell_node, nnode):
     return 1.0 / np.maximum(mult, 1.0)
 
 
-def apply(r, cell_node, winv, dinv, W1, b1, W2):
-    """M(r) in FP64.  W1 [H][nloc], b1 [H], W2 [nloc][H]."""
+def _keep(a):
+    return a
+
+
+def apply(r, cell_node, winv, dinv, W1, b1, W2, rnd=None):
+    """M(r) in FP64.  W1 [H][nloc], b1 [H], W2 [nloc][H]; rnd: operand rounding (module docstring)."""
+    rnd = rnd or _keep
     out = dinv * r
     R = r[cell_node]                      # [ncell][nloc]
     s = np.linalg.norm(R, axis=1)         # [ncell]
     safe = np.where(s > 0, s, 1.0)
-    Z = R / safe[:, None]
+    Z = rnd(R / safe[:, None])
     Hpre = Z @ W1.T + b1
-    H = np.maximum(Hpre, 0.0)
+    H = rnd(np.maximum(Hpre, 0.0))
     O = H @ W2.T                          # [ncell][nloc]
     contrib = winv[cell_node] * (s[:, None] * O) * (s[:, None] > 0)
     np.add.at(out, cell_node, contrib)
     return out
 
 
-def loss_and_grad(r, e, A_apply, cell_node, winv, dinv, W1, b1, W2):
-    """Loss L and (dL/dW1, dL/db1, dL/dW2) for one pair; A_apply(v) = A v."""
+def loss_and_grad(r, e, A_apply, cell_node, winv, dinv, W1, b1, W2, rnd=None):
+    """Loss L and (dL/dW1, dL/db1, dL/dW2) for one pair; A_apply(v) = A v; rnd as for `apply`."""
+    rnd = rnd or _keep
     R = r[cell_node]
     s = np.linalg.norm(R, axis=1)
     safe = np.where(s > 0, s, 1.0)
-    Z = R / safe[:, None]
+    Z = rnd(R / safe[:, None])
     Hpre = Z @ W1.T + b1
-    H = np.maximum(Hpre, 0.0)
+    H = rnd(np.maximum(Hpre, 0.0))
     O = H @ W2.T
     alive = (s > 0)[:, None]
     M = dinv * r
@@ -52,9 +66,9 @@ def loss_and_grad(r, e, A_apply, cell_node, winv, dinv, W1, b1, W2):
     den = e @ A_apply(e)
     L = (u @ Au) / den
     g = 2.0 * Au / den                    # dL/du (A symmetric)
-    Delta = winv[cell_node] * g[cell_node] * s[:, None] * alive  # dL/dO
+    Delta = rnd(winv[cell_node] * g[cell_node] * s[:, None] * alive)  # dL/dO
     dW2 = Delta.T @ H
-    dH = (Delta @ W2) * (Hpre > 0)
+    dH = rnd((Delta @ W2) * (H > 0))
     dW1 = dH.T @ Z
     db1 = dH.sum(axis=0)
     return L, dW1, db1, dW2

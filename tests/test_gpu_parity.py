@@ -309,7 +309,16 @@ def test_cg_matches_dense_solve(ctx, precond):
     xd = torch.zeros_like(bd)
     rc, it, rel = form.cg(bd, xd, precond=precond, rtol=1e-12, maxit=500)
     assert rc == mfa.MFA_OK and rel <= 1e-12
-    np.testing.assert_allclose(xd.cpu().numpy(), xs, rtol=0, atol=1e-8 * np.abs(xs).max())
+    # The error is bounded by the residual: ||x - x*|| / ||x*|| <= kappa_2(A) ||b - A x|| / ||b||.  This matrix has
+    # kappa_2 ~ 605, so a residual of 1e-12 allows a relative error of ~6e-10 in the 2-norm (~4e-9 of max|x*| in
+    # the max-norm here, which is why a max-norm bound of 1e-9 max|x*| does not follow).  The residual is taken
+    # again on the host with the dense matrix; 1e-13 covers the rounding of the dense solve itself (kappa eps).
+    x = xd.cpu().numpy()
+    ev = np.linalg.eigvalsh(A)
+    kappa = ev.max() / ev.min()
+    true_rel = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+    assert true_rel <= 2e-12
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= kappa * true_rel + 1e-13, (kappa, true_rel)
 
 
 @pytest.mark.parametrize("precond", [mfa.MFA_PC_NONE, mfa.MFA_PC_JACOBI])

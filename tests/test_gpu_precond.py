@@ -26,6 +26,18 @@ def bf16_round(a):
     return t.numpy()
 
 
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+# The kernels multiply BF16 operands (weights, Z and H forward, dL/dO and dL/dH backward) with FP32 accumulation;
+# the oracle is evaluated with the same operands rounded to BF16 (its `rnd` argument) and the FP32 inputs r, e.
+# What remains is FP32 accumulation over <= 128 products (<= 128 * 2^-24 ~ 8e-6 relative) and the few operands
+# whose FP32 and FP64 values fall on different sides of a BF16 rounding boundary (one BF16 unit in the last
+# place, 2^-8 ~ 4e-3 relative, on roughly one operand in 10^3): together well below 1e-3 of the result.
+OPERAND_TOL = 1e-3
+
+
 def setup(ctx, nx, p, seed=0, w2scale=0.05):
     case = hex_case(nx, p)
     m = mfa.Mesh(ctx, 8, case["coords"], case["cell_vert"])
@@ -50,17 +62,19 @@ def test_precond_forward_matches_oracle(ctx, nx, p):
     A = pb.dense() if case["nnode"] <= 4000 else None
     dinv = 1.0 / (np.diag(A) if A is not None else None)
     winv = op.multiplicity_weights(case["cell_node"], case["nnode"])
-    r = fi.uniform_vector(case["nnode"], seed=3)
-    # the kernels run the MLP on bfloat16 weights
-    ref = op.apply(r, case["cell_node"], winv, dinv, bf16_round(W1), b1, bf16_round(W2))
+    r = f32(fi.uniform_vector(case["nnode"], seed=3))
+    dinv = f32(dinv)
+    # the kernels run the MLP on bfloat16 weights and operands
+    ref = op.apply(r, case["cell_node"], winv, dinv, bf16_round(W1), b1, bf16_round(W2), rnd=bf16_round)
     rd = torch.from_numpy(r).float().cuda()
     z = torch.empty_like(rd)
     mfa.mfa_precond_apply(ctx.h, pc, rd, z)
     ctx.sync()
     zg = z.double().cpu().numpy()
     net_ref, net = ref - dinv * r, zg - dinv * r
-    assert np.linalg.norm(net - net_ref) <= 3e-2 * np.linalg.norm(net_ref)
-    assert np.linalg.norm(zg - ref) <= 1e-2 * np.linalg.norm(ref)
+    err = np.linalg.norm(net - net_ref) / np.linalg.norm(net_ref)
+    assert err <= OPERAND_TOL, err
+    assert np.linalg.norm(zg - ref) <= OPERAND_TOL * np.linalg.norm(ref)
     mfa.mfa_precond_destroy(pc)
 
 
@@ -86,19 +100,19 @@ def test_precond_gradient_matches_oracle(ctx):
     A = oracle_problem(case, "helmholtz").dense()
     winv = op.multiplicity_weights(case["cell_node"], case["nnode"])
     dinv = 1.0 / np.diag(A)
-    e = fi.uniform_vector(case["nnode"], seed=6)
-    r = A @ e
-    L, dW1, db1, dW2 = op.loss_and_grad(r, e, lambda v: A @ v, case["cell_node"], winv, dinv, bf16_round(W1), b1,
-                                        bf16_round(W2))
+    e = f32(fi.uniform_vector(case["nnode"], seed=6))
+    r = f32(A @ e)
+    L, dW1, db1, dW2 = op.loss_and_grad(r, e, lambda v: A @ v, case["cell_node"], winv, f32(dinv), bf16_round(W1),
+                                        b1, bf16_round(W2), rnd=bf16_round)
     loss, g = mfa.mfa_precond_loss_grad(ctx.h, pc, keep[3].h, torch.from_numpy(r).float().cuda(),
                                         torch.from_numpy(e).float().cuda())
     gW1, gb1, gW2 = mfa.unpack_precond_weights(g, (p + 1) ** 3)
-    assert abs(loss - L) <= 1e-2 * L
+    # the loss goes through the FP32 operator (relative error ~1e-6) instead of the dense FP64 matrix
+    assert abs(loss - L) <= 1e-4 * L, (loss, L)
     for name, ref, got in [("W1", dW1, gW1), ("b1", db1, gb1), ("W2", dW2, gW2)]:
         got = got.astype(np.float64)
-        cos = (ref.ravel() @ got.ravel()) / (np.linalg.norm(ref) * np.linalg.norm(got))
-        assert cos > 0.999, (name, cos)
-        assert np.linalg.norm(got - ref) <= 5e-2 * np.linalg.norm(ref), name
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= 2 * OPERAND_TOL, (name, err)
     mfa.mfa_precond_destroy(pc)
 
 

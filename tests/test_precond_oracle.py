@@ -87,3 +87,30 @@ def test_linear_variant_gradient_matches_finite_differences(small):
     fd = (op.loss_and_grad_linear(r, e, lambda v: A @ v, cn, winv, dinv, W1 + eps * D)[0] -
           op.loss_and_grad_linear(r, e, lambda v: A @ v, cn, winv, dinv, W1 - eps * D)[0]) / (2 * eps)
     assert abs(fd - np.sum(dW1 * D)) <= 1e-6 * max(1.0, abs(fd))
+
+
+def _golden(name):
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "precond_hand_worked.txt")
+    for line in open(path):
+        if line.startswith(name + ":"):
+            return np.array([float(v) for v in line.split(":")[1].split()])
+    raise KeyError(name)
+
+
+def test_hand_worked_forward():
+    """A case evaluated by hand (tests/golden/precond_hand_worked.txt): the bias, the activation cutting one unit,
+    the scaling by s_K, the partition-of-unity weights and the zero-residual cell each change the result, so a
+    dropped or misplaced term fails here."""
+    cn = np.array([[0, 1], [1, 2], [2, 3]], dtype=np.int32)
+    winv = op.multiplicity_weights(cn, 4)
+    np.testing.assert_array_equal(winv, [1.0, 0.5, 0.5, 1.0])
+    dinv = np.array([0.5, 0.25, 1.0, 2.0])
+    r = np.array([3.0, 4.0, 0.0, 0.0])
+    W1 = np.array([[1.0, 2.0], [-2.0, 1.0]])
+    b1 = np.array([-0.5, 0.5])
+    W2 = np.array([[1.0, -1.0], [2.0, 3.0]])
+    np.testing.assert_allclose(op.apply(r, cn, winv, dinv, W1, b1, W2), _golden("mlp"), rtol=0, atol=1e-14)
+    W1l = np.array([[1.0, 2.0], [0.0, 1.0]])
+    np.testing.assert_allclose(op.apply_linear(r, cn, winv, dinv, W1l), _golden("linear"), rtol=0, atol=1e-14)
