@@ -481,7 +481,11 @@ MFA_API int mfa_order_rcm(int64_t ncell, int nv, const int32_t *cell_vert, int64
  *  - ndof above MFA_CG_NOALLOC_MAX_NDOF returns MFA_ERR_ARG, before any work.
  *  - The first call on a device looks up the array's device address (once per
  *    device, with that device current); make that first call before any
- *    stream capture.
+ *    stream capture.  Later calls made while the context stream is not
+ *    capturing look it up again, so a reset of the device (after which every
+ *    other handle must be created anew) leaves no stale address behind.
+ *  - Errors: those of mfa_cg; a failure inside mfa_apply, mfa_diagonal or
+ *    mfa_sync keeps that call's message in mfa_last_error().
  *  - All calls on a device share the array: calls that overlap on the GPU
  *    (other streams, other host threads) race.  Each call writes every part
  *    of the array it reads before reading it. */

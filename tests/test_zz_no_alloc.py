@@ -66,6 +66,25 @@ def test_noalloc_cg_matches_cg_on_two_calls_in_a_row():
     assert it1 > 0 and it2 > 0
 
 
+def test_noalloc_cg_allocates_no_device_memory():
+    """After a first call (which looks up the array's address), a further call leaves the device's free memory
+    unchanged: every work vector comes from the fixed array (cudaMalloc reserves whole 2 MiB pages, so any
+    allocation would show)."""
+    torch.cuda.set_device(0)
+    ctx = mfa.Context(0, torch.cuda.current_stream())
+    form, n = helmholtz_form(ctx, 10, 3)
+    b = torch.from_numpy(fi.uniform_vector(n, seed=43)).cuda()
+    x = torch.zeros_like(b)
+    mfa.mfa_cg_noalloc(ctx.h, form.h, mfa.MFA_PC_JACOBI, b, x, 1e-10, 2000)
+    x.zero_()
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    rc, it, rel = mfa.mfa_cg_noalloc(ctx.h, form.h, mfa.MFA_PC_JACOBI, b, x, 1e-10, 2000)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before
+    assert rc == mfa.MFA_OK and rel <= 1e-10 and it > 0
+
+
 def test_noalloc_cg_rejects_sizes_beyond_its_limit():
     torch.cuda.set_device(0)
     ctx = mfa.Context(0, torch.cuda.current_stream())
