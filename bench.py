@@ -78,6 +78,9 @@ def parse_args():
                          "random permutation renumbered by the library's reverse Cuthill-McKee")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep each form's default launch configuration instead of timing all of them")
+    ap.add_argument("--parallelism", choices=["auto", "sharded", "replicas"], default="auto",
+                    help="N > 1: the hex workload shards a box of N nx^3 z-slabs over the ranks (auto), the others "
+                         "run a replica per rank")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     return ap.parse_args()
@@ -726,6 +729,212 @@ def gpu_arm(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ sharded hex workload (N > 1)
+
+def sharded_operators(world, rank, nx, degrees, forms, make_part, to_tensor):
+    """This rank's operators of the z-slab sharded hex workload (weak scaling): the box [0,1]^2 x [0, N] of
+    nx * nx * (N nx) perturbed hexahedra, rank r holding cell layers [r nx, (r + 1) nx), so that every rank has
+    the single-GPU workload's nx^3 cells.  For each degree and form: the slab's halo plan, its two parts (the
+    cells touching a node shared with a neighbour, and the rest) built by make_part(mesh, plan, cells, p, form),
+    the rank's slice of the global seeded x, and y.  Part objects have apply(x, y, accumulate)."""
+    from paper_1903_08243_gb300 import dist as mdist
+
+    mesh = fi.hex_slab_mesh(nx, nx * world, rank * nx, nx, perturb=0.1, seed=1)
+    out = []
+    for p in degrees:
+        plan = mdist.slab_plan(nx, nx, p, world, rank)
+        x = to_tensor(fi.uniform_vector(plan.l2g.size, seed=1, start=int(plan.l2g[0])))
+        for f in forms:
+            parts = {name: (make_part(mesh, plan, cells, p, f) if cells.size else None)
+                     for name, cells in (("boundary", plan.boundary_cells), ("interior", plan.interior_cells))}
+            out.append(dict(name="Q%d %s" % (p, f), p=p, form=f, plan=plan, parts=parts, x=x, y=x.clone(),
+                            ndof_owned=int(plan.owned.sum())))
+    return out
+
+
+def sharded_step(op, plan, halo_ops, on_interior=None):
+    """One distributed action y = A x of a sharded operator on this rank: import x at the ghost plane, apply the
+    boundary cells, post the reverse exchange of their partial sums, apply the interior cells while it is in
+    flight, then add the received partial sums into the owned plane (on_interior(apply) wraps the interior
+    apply, e.g. to time it)."""
+    from paper_1903_08243_gb300 import dist as mdist
+
+    b, i = op["parts"]["boundary"], op["parts"]["interior"]
+
+    def apply_boundary(x, y):
+        if b is None:
+            y.zero_()
+        else:
+            b.apply(x, y, False)
+        return y
+
+    def apply_interior(x, y):
+        if i is not None:
+            (on_interior or (lambda fn: fn()))(lambda: i.apply(x, y, True))
+
+    return mdist.distributed_apply_overlapped(plan, apply_boundary, apply_interior, op["x"], halo_ops, y=op["y"],
+                                              refresh=False)
+
+
+def sharded_hex_arm(args, world, rank, local):
+    """The hex workload sharded over N GPUs (z-slabs, halo exchange by NCCL point-to-point messages, the reverse
+    exchange overlapping the interior cells); weak scaling, nx^3 cells per GPU."""
+    import torch
+
+    from paper_1903_08243_gb300 import build as libbuild
+    from paper_1903_08243_gb300 import dist as mdist
+
+    libbuild.build()
+    import paper_1903_08243_gb300 as mfa
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = mfa.Context(local, stream)
+    halo = mdist.LibraryHaloOps(ctx)
+    args.nx = args.nx or 64
+    degrees = [int(p) for p in args.degrees.split(",")]
+    forms = args.forms.split(",")
+    keep = []
+
+    class Part:
+        def __init__(self, mesh, plan, cells, p, f):
+            m = mfa.Mesh(ctx, mfa.MFA_CELL_HEX8, mesh.coords, np.ascontiguousarray(mesh.cell_vert[cells]))
+            sp = mfa.Space(m, p, 1, np.ascontiguousarray(plan.local_cell_node[cells]), plan.l2g.size)
+            self.form = mfa.Form(sp, FORM_IDS[f], k2=1.0)
+            keep.append((m, sp))
+
+        def apply(self, x, y, accumulate):
+            mfa.mfa_apply(ctx.h, self.form.h, x, y, accumulate)
+
+    t0 = time.perf_counter()
+    ops = sharded_operators(world, rank, args.nx, degrees, forms, Part, lambda a: torch.from_numpy(a).cuda())
+    plans = {}
+    for o in ops:
+        if o["p"] not in plans:
+            plans[o["p"]] = mdist.device_plan(o["plan"], "cuda")
+        o["dplan"] = plans[o["p"]]
+    ctx.sync()
+    setup_s = time.perf_counter() - t0
+    if not args.no_autotune:
+        for o in ops:
+            for part in o["parts"].values():
+                if part is not None:
+                    part.form.autotune(o["x"], o["y"], reps=3)
+    ctx.sync()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    kev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in ops]
+           for _ in range(args.steps)]
+    ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in ops]
+          for _ in range(args.steps)]
+
+    def run_step(k=None):
+        for i, o in enumerate(ops):
+            if k is not None:
+                ev[k][i][0].record(stream)
+
+            def timed(fn, k=k, i=i):
+                if k is not None:
+                    kev[k][i][0].record(stream)
+                fn()
+                if k is not None:
+                    kev[k][i][1].record(stream)
+            sharded_step(o, o["dplan"], halo, timed)
+            if k is not None:
+                ev[k][i][1].record(stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        run_step()
+    ctx.sync()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        run_step(k)
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall
+    time.sleep(0.3)
+    clocks = sampler.stop()
+    ctx.sync()
+    per_op_ms = [statistics.median(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
+                 for i in range(len(ops))]
+    kern_ms = [statistics.median(kev[k][i][0].elapsed_time(kev[k][i][1]) for k in range(args.steps))
+               if ops[i]["parts"]["interior"] is not None else 0.0 for i in range(len(ops))]
+    step_ms = allreduce_max(world, sum(per_op_ms))
+    ndof_rank = sum(o["ndof_owned"] for o in ops)
+    ndof_step = ndof_rank
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ndof_rank], dtype=torch.int64, device="cuda")
+        dist.all_reduce(t)
+        ndof_step = int(t.item())
+    value = ndof_step / (step_ms / 1e3) / 1e9
+    i_dom = int(np.argmax(kern_ms))
+    dom = ops[i_dom]["parts"]["interior"]
+    info = dom.form.info() if dom is not None else None
+    roofline = None
+    if info is not None and kern_ms[i_dom] > 0:
+        achieved = info.flops / (kern_ms[i_dom] / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "operator": ops[i_dom]["name"],
+                    "scope": "the interior cells' apply kernel of rank %d (CUDA events on the context stream)" % rank,
+                    "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (FP64 pipe; recipe unit counts)",
+                    "frac_executed": info.flops_executed / (kern_ms[i_dom] / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
+
+    # end to end: each step copies the rank's x in from pinned host memory and its y back
+    e2e = None
+    if args.e2e_steps > 0:
+        hx = [torch.from_numpy(o["x"].cpu().numpy()).pin_memory() for o in ops]
+        hy = [torch.empty_like(h).pin_memory() for h in hx]
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for o, xh, yh in zip(ops, hx, hy):
+                o["x"].copy_(xh, non_blocking=True)
+                sharded_step(o, o["dplan"], halo)
+                yh.copy_(o["y"], non_blocking=True)
+            torch.cuda.synchronize()
+        dt = allreduce_max(world, (time.perf_counter() - t0) / args.e2e_steps)
+        nbytes = 8 * sum(o["x"].numel() for o in ops)
+        e2e = {"value": ndof_step / dt / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": dt * 1e3,
+               "path": "per rank and operator: pinned x copied in, the sharded action (halo exchange included), y "
+                       "copied out"}
+    # this rank's library launches per step: halo pack/unpack per peer and direction, and the two parts' applies
+    launches = sum(len(o["plan"].send_import) + len(o["plan"].recv_import) + len(o["plan"].send_reverse) +
+                   len(o["plan"].recv_reverse) + sum(part is not None for part in o["parts"].values()) for o in ops)
+    if rank == 0:
+        halo_nodes = {o["name"]: int(sum(ids.size for ids in o["plan"].recv_import.values())) for o in ops}
+        line = {
+            "metric": "operator-action GDoF/s", "value": value, "unit": "GDoF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args) + "-sharded", "operators": [o["name"] for o in ops],
+                       "parallelism": "sharded", "ndof_per_step": ndof_step,
+                       "mesh": "[0,1]^2 x [0,%d] as %d x %d x %d hexahedra (h = 1/%d), interior vertices perturbed "
+                               "U[-0.1h,0.1h], seed 1; rank r holds cell layers [%d r, %d (r+1))"
+                               % (world, args.nx, args.nx, args.nx * world, args.nx, args.nx, args.nx),
+                       "exchange": "NCCL point-to-point, one grouped exchange per direction: x imported at the "
+                                   "ghost node plane before the apply; the boundary cells' partial sums sent back "
+                                   "while the interior cells are applied",
+                       "halo_nodes_rank0": halo_nodes,
+                       "l2": "flushed between steps (256 MiB write outside the timed events)",
+                       "setup_s": setup_s, "input": "the rank's slice of the global x ~ U[-1,1) seed 1"},
+            "roofline": roofline, "cpu_baseline": None, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches * args.steps, "wall_s_timed_region": t_wall,
+            "per_operator": [{"operator": o["name"], "ms": ms, "interior_kernel_ms": km}
+                             for o, ms, km in zip(ops, per_op_ms, kern_ms)],
+        }
+        print(json.dumps(line), flush=True)
+
+
 def batched_specs(nops, seed=3):
     """Operator list of the batched workload: degree ~ U{1..8}, cells per side ~ U{8..48}."""
     deg = fi.randint(seed, 0xDE6, nops, 1, 8)
@@ -1096,6 +1305,8 @@ def main():
         pcg_elasticity_arm(args, world, rank, local)
     elif args.impl == "reference":
         reference_arm(args, world, rank)
+    elif args.workload == "hex" and world > 1 and args.parallelism != "replicas":
+        sharded_hex_arm(args, world, rank, local)
     else:
         gpu_arm(args, world, rank, local)
     if world > 1:

@@ -22,6 +22,7 @@ from .mesh import (
     HexMesh,
     kuhn_tet_mesh,
     hex_box_mesh,
+    hex_slab_mesh,
     p2_node_map,
     hex_node_map,
     shuffle_mesh,
@@ -37,6 +38,7 @@ __all__ = [
     "HexMesh",
     "kuhn_tet_mesh",
     "hex_box_mesh",
+    "hex_slab_mesh",
     "p2_node_map",
     "hex_node_map",
     "shuffle_mesh",

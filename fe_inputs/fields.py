@@ -4,9 +4,9 @@ import numpy as np
 from .rng import uniform, randint
 
 
-def uniform_vector(n, seed, tag=0x7EC, lo=-1.0, hi=1.0):
-    """``n`` doubles uniform in [lo, hi)."""
-    return uniform(seed, tag, n, lo, hi)
+def uniform_vector(n, seed, tag=0x7EC, lo=-1.0, hi=1.0, start=0):
+    """``n`` doubles uniform in [lo, hi): entries start .. start+n-1 of the seeded vector."""
+    return uniform(seed, tag, n, lo, hi, start=start)
 
 
 def _sinusoid_params(seed, nterm=8):

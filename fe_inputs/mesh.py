@@ -114,16 +114,46 @@ def hex_box_mesh(nx, perturb=0.1, seed=1):
     return HexMesh(coords=coords, cell_vert=cv.astype(np.int32), nx=nx, h=h)
 
 
-def hex_node_map(nx, p):
-    """Cell -> node map of continuous Q_p on an nx^3 structured hex mesh.
+def hex_slab_mesh(nx, nz_total, z0, nz, perturb=0.1, seed=1):
+    """Layers z0 .. z0+nz-1 of the box [0,1]^2 x [0, nz_total/nx] meshed by nx * nx * nz_total hexahedra of side
+    h = 1/nx (one part of a z-slab partition).
 
-    Returns (cell_node int32 [nx^3][(p+1)^3], nnode).  Local node
-    i + n*j + n*n*k of cell (ci, cj, ck) is global grid node
-    (p*ci + i, p*cj + j, p*ck + k) on the (nx*p + 1)^3 lattice.
+    Vertices and cells are numbered lexicographically within the slab.  Every vertex interior to the whole box is
+    shifted by U[-perturb*h, perturb*h]^3 drawn at its index in the whole box's lexicographic numbering, so two
+    slabs that share a vertex plane agree on it, and the single slab (nz_total = nz = nx, z0 = 0) is
+    hex_box_mesh(nx, perturb, seed).
+    """
+    m = nx + 1
+    h = 1.0 / nx
+    k, j, i = np.meshgrid(np.arange(z0, z0 + nz + 1), np.arange(m), np.arange(m), indexing="ij")
+    i, j, k = i.ravel(), j.ravel(), k.ravel()
+    coords = np.stack([i * h, j * h, k * h], axis=1).astype(np.float64)
+    if perturb > 0.0:
+        interior = (i > 0) & (i < nx) & (j > 0) & (j < nx) & (k > 0) & (k < nz_total)
+        first = m * m * z0  # the slab's vertices are consecutive in the whole box's numbering
+        shift = uniform(seed, 0x5E57, 3 * coords.shape[0], -perturb * h, perturb * h, start=3 * first).reshape(-1, 3)
+        coords[interior] += shift[interior]
+    kc, jc, ic = np.meshgrid(np.arange(nz), np.arange(nx), np.arange(nx), indexing="ij")
+    ic, jc, kc = ic.ravel(), jc.ravel(), kc.ravel()
+    cv = np.empty((ic.size, 8), dtype=np.int64)
+    for c in range(2):
+        for b in range(2):
+            for a in range(2):
+                cv[:, a + 2 * b + 4 * c] = (ic + a) + m * ((jc + b) + m * (kc + c))
+    return HexMesh(coords=coords, cell_vert=cv.astype(np.int32), nx=nx, h=h)
+
+
+def hex_node_map(nx, p, nz=None):
+    """Cell -> node map of continuous Q_p on a structured hex mesh of nx * nx * nz cells (nz = nx by default).
+
+    Returns (cell_node int32 [ncell][(p+1)^3], nnode).  Local node
+    i + n*j + n*n*k of cell (ci, cj, ck) is grid node
+    (p*ci + i, p*cj + j, p*ck + k) on the (nx*p + 1)^2 (nz*p + 1) lattice, numbered lexicographically.
     """
     n = p + 1
     m = nx * p + 1
-    k, j, i = np.meshgrid(np.arange(nx), np.arange(nx), np.arange(nx), indexing="ij")
+    nz = nx if nz is None else nz
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(nx), np.arange(nx), indexing="ij")
     i, j, k = i.ravel().astype(np.int64), j.ravel().astype(np.int64), k.ravel().astype(np.int64)
     lk, lj, li = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
     li, lj, lk = li.ravel(), lj.ravel(), lk.ravel()
@@ -131,7 +161,7 @@ def hex_node_map(nx, p):
     J = p * j[:, None] + lj[None, :]
     K = p * k[:, None] + lk[None, :]
     node = I + m * (J + m * K)
-    return node.astype(np.int32), m ** 3
+    return node.astype(np.int32), m * m * (nz * p + 1)
 
 
 def p2_node_map(cell_vert, nvert):

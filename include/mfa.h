@@ -469,6 +469,28 @@ MFA_API int mfa_batch_destroy(mfa_batch *batch);
 MFA_API int mfa_order_rcm(int64_t ncell, int nv, const int32_t *cell_vert, int64_t nvert, int nloc,
                           const int32_t *cell_node, int64_t nnode, int32_t *cell_order, int32_t *node_perm);
 
+/* Halo buffers of a cell-partitioned operator (Section 2.2's global assembly
+ * with the cells split over ranks, one exchange per apply).  A rank applies
+ * its cells over its local node numbering; a node that cells of several ranks
+ * touch is owned by one rank and held as a ghost by the others.  Before the
+ * apply, x at the ghosts is imported from the owners; after it, the ghosts'
+ * partial sums are added into the owners' entries (the reverse exchange).
+ * These calls move values between a node vector and the contiguous buffer a
+ * rank sends or receives; the messages themselves are the caller's (NCCL).
+ *  - ids: device int32 [n], local node ids in [0, nnode); v: device FP64
+ *    [nnode][ncomp] (dof ncomp * node + c); buf: device FP64 [n][ncomp].
+ *  - pack:   buf[k][c] = v[ids[k]][c].
+ *  - unpack: v[ids[k]][c] = buf[k][c] (accumulate = 0) or += (accumulate = 1);
+ *    ids must be distinct within one call.
+ *  - Asynchronous on the context stream.  An id outside [0, nnode) is skipped
+ *    (pack writes 0) and mfa_sync reports MFA_ERR_RANGE.
+ * Not in the paper as a call: its runs are MPI-parallel with PyOP2's halo
+ * exchange; this is the device side of that exchange. */
+MFA_API int mfa_halo_pack(mfa_ctx *ctx, const int32_t *ids, int64_t n, int ncomp, int64_t nnode, const double *v,
+                          double *buf);
+MFA_API int mfa_halo_unpack(mfa_ctx *ctx, const int32_t *ids, int64_t n, int ncomp, int64_t nnode,
+                            const double *buf, double *v, int accumulate);
+
 /* mfa_cg without device allocation.  The paper has no counterpart: this is
  * for callers that cannot call cudaMalloc (an application whose memory pool
  * already holds the device memory, a solver step inside another framework's

@@ -128,6 +128,8 @@ _SIGS = {
                        ctypes.POINTER(_D)], _I),
     "mfa_fcg_learned": ([_VP, _VP, _VP, _VP, _I, _VP, _VP, _D, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
                          ctypes.POINTER(_D), ctypes.POINTER(_I)], _I),
+    "mfa_halo_pack": ([_VP, _VP, _I64, _I, _I64, _VP, _VP], _I),
+    "mfa_halo_unpack": ([_VP, _VP, _I64, _I, _I64, _VP, _VP, _I], _I),
     "mfa_precond_create": ([_VP, _VP, _I, ctypes.c_uint64, _PP], _I),
     "mfa_precond_apply": ([_VP, _VP, _VP, _VP], _I),
     "mfa_precond_loss_grad": ([_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_D), _VP], _I),
@@ -361,6 +363,16 @@ def mfa_apply(ctx, form, x, y, accumulate=False):
 
 def mfa_apply_f32(ctx, form, x, y, accumulate=False):
     _check(lib().mfa_apply_f32(ctx, form, _ptr(x), _ptr(y), int(accumulate)))
+
+
+def mfa_halo_pack(ctx, ids, ncomp, nnode, v, buf):
+    """buf[k] = v[ids[k]] (device tensors: ids int32, v and buf float64, ncomp values per node)."""
+    _check(lib().mfa_halo_pack(ctx, _ptr(ids), ids.numel(), ncomp, nnode, _ptr(v), _ptr(buf)))
+
+
+def mfa_halo_unpack(ctx, ids, ncomp, nnode, buf, v, accumulate=False):
+    """v[ids[k]] = buf[k] (or += with accumulate)."""
+    _check(lib().mfa_halo_unpack(ctx, _ptr(ids), ids.numel(), ncomp, nnode, _ptr(buf), _ptr(v), int(accumulate)))
 
 
 def mfa_convert_f64_to_f32(ctx, x, y):

@@ -1286,6 +1286,7 @@ int mfa_sync(mfa_ctx* ctx) {
   if (flag) {
     MFA_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
     if (flag & 4) return fail(MFA_ERR_TIMEOUT, "a kernel gave up waiting for a bulk copy");
+    if (flag & 8) return fail(MFA_ERR_RANGE, "a halo node id was outside [0, nnode)");
     return fail(MFA_ERR_DOMAIN, "kernel reported %s%s", (flag & 1) ? "det J == 0 or non-finite " : "",
                 (flag & 2) ? "deformation with J <= 0" : "");
   }

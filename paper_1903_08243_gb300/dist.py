@@ -14,7 +14,10 @@ ghost.  One distributed apply is then
 
 Scalars of Krylov methods are sums over owned entries, all-reduced.  The
 exchange uses torch.distributed point-to-point messages between neighbouring
-ranks (NCCL between GPUs, gloo on CPU).
+ranks (NCCL between GPUs), posted as one group per exchange.  Moving values
+between a node vector and a message buffer is the job of a halo-ops object:
+on the GPU, LibraryHaloOps runs the library's kernels (mfa_halo_pack /
+mfa_halo_unpack) on the context stream.
 
 The overlapped apply splits a rank's cells into boundary cells (touching a
 node shared with another rank) and interior cells (touching none): after the
@@ -124,75 +127,158 @@ def build_plan(cell_node, nnode, nranks, rank, parts=None):
     return plan
 
 
-def _start_exchange(send, recv, values):
-    """Post the point-to-point messages: values[ids] to each peer, a buffer per peer to receive into."""
+def slab_plan(nx, nz, p, nranks, rank):
+    """Halo plan of a z-slab partition of the structured Q_p hex mesh of nx * nx * (nz * nranks) cells, computed
+    from the lattice instead of from the global map (build_plan gives the same plan for contiguous_partition).
+
+    Rank r owns cell layers [r nz, (r + 1) nz); its local nodes are the (nx p + 1)^2 (nz p + 1) lattice nodes of
+    its slab, numbered lexicographically (the map of fe_inputs.hex_node_map(nx, p, nz)), which are consecutive
+    global nodes.  The node plane shared with rank r - 1 (local plane 0) is owned by r - 1, the lowest rank that
+    touches it: a ghost here.  The plane shared with rank r + 1 (local plane nz p) is owned here.  Boundary cells
+    are the cell layers that touch a shared plane."""
+    import fe_inputs as fi
+
+    m = nx * p + 1
+    plane = m * m
+    cell_node, nlocal = fi.hex_node_map(nx, p, nz)
+    cells_per_rank = nx * nx * nz
+    plan = HaloPlan(rank=rank, nranks=nranks,
+                    cells=rank * cells_per_rank + np.arange(cells_per_rank, dtype=np.int64),
+                    local_cell_node=cell_node, l2g=rank * nz * p * plane + np.arange(nlocal, dtype=np.int64),
+                    owned=np.ones(nlocal, dtype=bool))
+    bottom = np.arange(plane, dtype=np.int64)
+    top = nz * p * plane + np.arange(plane, dtype=np.int64)
+    layer = np.arange(cells_per_rank) // (nx * nx)
+    on_boundary = np.zeros(cells_per_rank, dtype=bool)
+    if rank > 0:
+        plan.owned[bottom] = False
+        plan.recv_import[rank - 1] = bottom
+        plan.send_reverse[rank - 1] = bottom
+        on_boundary |= layer == 0
+    if rank < nranks - 1:
+        plan.send_import[rank + 1] = top
+        plan.recv_reverse[rank + 1] = top
+        on_boundary |= layer == nz - 1
+    plan.boundary_cells = np.flatnonzero(on_boundary)
+    plan.interior_cells = np.flatnonzero(~on_boundary)
+    return plan
+
+
+class LibraryHaloOps:
+    """Halo buffers moved by the library's kernels on the context stream (device tensors).
+
+    pack(ids, v) returns the buffer v[ids]; put(ids, buf, v) sets v[ids] = buf; add(ids, buf, v) adds buf into
+    v[ids].  ids: int32 device tensors (see device_plan); v: float64 [nnode] or [nnode][ncomp]."""
+
+    def __init__(self, ctx):
+        self.ctx = ctx
+
+    @staticmethod
+    def _shape(v):
+        return (v.shape[0], 1 if v.dim() == 1 else int(v.shape[1]))
+
+    def pack(self, ids, v):
+        import torch
+
+        from . import mfa_halo_pack
+
+        nnode, nc = self._shape(v)
+        buf = torch.empty((ids.numel(),) + tuple(v.shape[1:]), dtype=v.dtype, device=v.device)
+        mfa_halo_pack(self.ctx.h, ids, nc, nnode, v, buf)
+        return buf
+
+    def put(self, ids, buf, v):
+        from . import mfa_halo_unpack
+
+        nnode, nc = self._shape(v)
+        mfa_halo_unpack(self.ctx.h, ids, nc, nnode, buf, v, False)
+
+    def add(self, ids, buf, v):
+        from . import mfa_halo_unpack
+
+        nnode, nc = self._shape(v)
+        mfa_halo_unpack(self.ctx.h, ids, nc, nnode, buf, v, True)
+
+
+def device_plan(plan, device):
+    """A copy of the plan whose exchange lists are int32 tensors on `device` (uploaded once, reused by every
+    exchange)."""
+    import copy
+
+    import torch
+
+    out = copy.copy(plan)
+    for name in ("send_import", "recv_import", "send_reverse", "recv_reverse"):
+        setattr(out, name, {peer: torch.as_tensor(np.asarray(ids, dtype=np.int32), device=device)
+                            for peer, ids in getattr(plan, name).items()})
+    return out
+
+
+def _start_exchange(send, recv, values, ops):
+    """Post the point-to-point messages of one exchange as one group: the packed values[ids] to each peer, and a
+    buffer per peer to receive into."""
     import torch
     import torch.distributed as dist
 
-    reqs, bufs = [], {}
+    p2p, bufs = [], {}
     for peer, ids in recv.items():
         buf = torch.empty((len(ids),) + tuple(values.shape[1:]), dtype=values.dtype, device=values.device)
         bufs[peer] = buf
-        reqs.append(dist.irecv(buf, src=peer))
+        p2p.append(dist.P2POp(dist.irecv, buf, peer))
     for peer, ids in send.items():
-        reqs.append(dist.isend(values[torch.as_tensor(ids, device=values.device)].contiguous(), dst=peer))
+        p2p.append(dist.P2POp(dist.isend, ops.pack(ids, values), peer))
+    reqs = dist.batch_isend_irecv(p2p) if p2p else []
     return reqs, bufs
 
 
 def _finish_exchange(recv, values, combine, pending):
-    import torch
-
     reqs, bufs = pending
     for r in reqs:
         r.wait()
     for peer, ids in recv.items():
-        idx = torch.as_tensor(ids, device=values.device)
-        combine(values, idx, bufs[peer])
+        combine(ids, bufs[peer], values)
 
 
-def _exchange(send, recv, values, combine):
+def _exchange(send, recv, values, combine, ops):
     """Point-to-point exchange: send values[ids] to each peer, combine received data at ids."""
-    _finish_exchange(recv, values, combine, _start_exchange(send, recv, values))
+    _finish_exchange(recv, values, combine, _start_exchange(send, recv, values, ops))
 
 
-def import_ghosts(plan, x_local):
+def import_ghosts(plan, x_local, ops):
     """x at ghost nodes <- owner's value."""
-    def put(v, idx, buf):
-        v[idx] = buf
-    _exchange(plan.send_import, plan.recv_import, x_local, put)
+    _exchange(plan.send_import, plan.recv_import, x_local, ops.put, ops)
 
 
-def reverse_add(plan, y_local):
-    """Owner's y += each neighbour's partial sums at its ghost copies; ghosts then hold the full value."""
-    def add(v, idx, buf):
-        v.index_add_(0, idx, buf)
-    _exchange(plan.send_reverse, plan.recv_reverse, y_local, add)
-    import_ghosts(plan, y_local)  # make ghost copies consistent with the owner
+def reverse_add(plan, y_local, ops, refresh=True):
+    """Owner's y += each neighbour's partial sums at its ghost copies; with refresh the ghosts then hold the
+    full value too."""
+    _exchange(plan.send_reverse, plan.recv_reverse, y_local, ops.add, ops)
+    if refresh:
+        import_ghosts(plan, y_local, ops)  # make ghost copies consistent with the owner
 
 
-def distributed_apply(plan, local_apply, x_local):
+def distributed_apply(plan, local_apply, x_local, ops):
     """y_local = (A x)_local on every local node (owned and ghost), x_local holding owned values."""
-    import_ghosts(plan, x_local)
+    import_ghosts(plan, x_local, ops)
     y = local_apply(x_local)
-    reverse_add(plan, y)
+    reverse_add(plan, y, ops)
     return y
 
 
-def distributed_apply_overlapped(plan, apply_boundary, apply_interior, x_local):
+def distributed_apply_overlapped(plan, apply_boundary, apply_interior, x_local, ops, y=None, refresh=True):
     """distributed_apply with the reverse exchange in flight during the interior cells.
 
-    apply_boundary(x) and apply_interior(x, y) apply the rank's boundary and interior cells
-    (plan.boundary_cells, plan.interior_cells): the first returns a new y, the second adds into y."""
-    import_ghosts(plan, x_local)
-    y = apply_boundary(x_local)  # every shared node's partial sum is now final on this rank
-
-    def add(v, idx, buf):
-        v.index_add_(0, idx, buf)
-
-    pending = _start_exchange(plan.send_reverse, plan.recv_reverse, y)  # partial sums at ghosts -> owners
+    apply_boundary(x, y) and apply_interior(x, y) apply the rank's boundary and interior cells
+    (plan.boundary_cells, plan.interior_cells): the first overwrites y, the second adds into it (y is allocated
+    by apply_boundary's caller when None: apply_boundary(x, None) returns it).  Without refresh the ghost
+    entries of y keep this rank's partial sums (the owned entries are complete either way)."""
+    import_ghosts(plan, x_local, ops)
+    y = apply_boundary(x_local, y)  # every shared node's partial sum is now final on this rank
+    pending = _start_exchange(plan.send_reverse, plan.recv_reverse, y, ops)  # partial sums at ghosts -> owners
     apply_interior(x_local, y)  # touches no shared node: cannot race with the messages
-    _finish_exchange(plan.recv_reverse, y, add, pending)
-    import_ghosts(plan, y)  # ghost copies take the owners' full sums
+    _finish_exchange(plan.recv_reverse, y, ops.add, pending)
+    if refresh:
+        import_ghosts(plan, y, ops)  # ghost copies take the owners' full sums
     return y
 
 
@@ -211,14 +297,15 @@ def owned_dot(plan, a, b):
     return float(s.item())
 
 
-def distributed_cg(plan, local_apply, b_local, x_local, diag_local=None, rtol=1e-8, maxit=1000, overlapped=None):
+def distributed_cg(plan, local_apply, b_local, x_local, ops, diag_local=None, rtol=1e-8, maxit=1000,
+                   overlapped=None):
     """Jacobi-preconditioned CG over the partitioned operator (reference logic for N > 1).
 
     overlapped: (apply_boundary, apply_interior) to use distributed_apply_overlapped instead."""
     def dapply(v):
         if overlapped is not None:
-            return distributed_apply_overlapped(plan, overlapped[0], overlapped[1], v)
-        return distributed_apply(plan, local_apply, v)
+            return distributed_apply_overlapped(plan, overlapped[0], overlapped[1], v, ops)
+        return distributed_apply(plan, local_apply, v, ops)
 
     r = b_local - dapply(x_local.clone())
     dinv = None if diag_local is None else 1.0 / diag_local
