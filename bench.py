@@ -516,6 +516,7 @@ def gpu_arm(args, world, rank, local):
     for o in ops:
         o["cfg"] = o["form"].config()
     ctx.sync()
+    probe_tflops, probe_mhz = mfa.mfa_probe_fp64_fma(ctx.h)  # the measured FP64 FMA rate (outside the timing)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
     launches_per_step = sum(o["info"].ncolours if o["info"].scatter == mfa.MFA_SCATTER_COLOUR else 1 for o in ops)
 
@@ -621,7 +622,11 @@ def gpu_arm(args, world, rank, local):
                     "algorithmic_flops_per_launch": dom["info"].flops,
                     "executed_flops_per_launch": dom["info"].flops_executed,
                     "frac_executed": dom["info"].flops_executed / (per_op_ms[i_dom] / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
-                    "algorithmic_bytes_per_launch": dom["info"].bytes, "kernel_sha1": kh}
+                    "algorithmic_bytes_per_launch": dom["info"].bytes, "kernel_sha1": kh,
+                    "fp64_probe": {"tflops": probe_tflops, "sm_mhz": probe_mhz,
+                                   "frac_of_derived_peak": probe_tflops / FP64_PEAK_TFLOPS,
+                                   "source": "mfa_probe_fp64_fma: 8 independent FMA chains per thread, one wave "
+                                             "of blocks per SM, CUDA events"}}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
@@ -952,7 +957,6 @@ def batched_oracle_leg(hosts, y_host, world):
     import oracle
 
     errs, full_s, ncells, nsample = [], 0.0, 0, 0
-    tol = None
     for i, h in enumerate(hosts):
         rng = np.random.default_rng(4000 + i)
         dofs = rng.choice(h["nnode"], size=min(BATCHED_SAMPLE_DOFS[h["p"]], h["nnode"]), replace=False)

@@ -491,6 +491,17 @@ MFA_API int mfa_halo_pack(mfa_ctx *ctx, const int32_t *ids, int64_t n, int ncomp
 MFA_API int mfa_halo_unpack(mfa_ctx *ctx, const int32_t *ids, int64_t n, int ncomp, int64_t nnode,
                             const double *buf, double *v, int accumulate);
 
+/* FP64 FMA throughput of this GPU, measured: one wave of blocks on every SM,
+ * each thread running 8 independent FMA chains for 2^15 steps, timed with
+ * CUDA events (after one shorter warm-up launch).  *tflops = 2 flops per FMA
+ * / elapsed time; *sm_mhz (may be NULL) = the median over blocks of SM clock
+ * ticks per nanosecond of the global timer during the timed launch.  The
+ * FP64 operator kernels are bound by this rate (their arithmetic intensity is
+ * far above the FP64 ridge point), so it is the measured denominator of their
+ * roofline.  Synchronous; allocates a few KB.  Not in the paper (the paper
+ * quotes its CPUs' peak from clock and vector width, Table 1). */
+MFA_API int mfa_probe_fp64_fma(mfa_ctx *ctx, double *tflops, double *sm_mhz);
+
 /* mfa_cg without device allocation.  The paper has no counterpart: this is
  * for callers that cannot call cudaMalloc (an application whose memory pool
  * already holds the device memory, a solver step inside another framework's

@@ -128,6 +128,7 @@ _SIGS = {
                        ctypes.POINTER(_D)], _I),
     "mfa_fcg_learned": ([_VP, _VP, _VP, _VP, _I, _VP, _VP, _D, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
                          ctypes.POINTER(_D), ctypes.POINTER(_I)], _I),
+    "mfa_probe_fp64_fma": ([_VP, ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "mfa_halo_pack": ([_VP, _VP, _I64, _I, _I64, _VP, _VP], _I),
     "mfa_halo_unpack": ([_VP, _VP, _I64, _I, _I64, _VP, _VP, _I], _I),
     "mfa_precond_create": ([_VP, _VP, _I, ctypes.c_uint64, _PP], _I),
@@ -363,6 +364,13 @@ def mfa_apply(ctx, form, x, y, accumulate=False):
 
 def mfa_apply_f32(ctx, form, x, y, accumulate=False):
     _check(lib().mfa_apply_f32(ctx, form, _ptr(x), _ptr(y), int(accumulate)))
+
+
+def mfa_probe_fp64_fma(ctx):
+    """Measured FP64 FMA throughput: (TFLOP/s, median SM MHz during the probe)."""
+    t, f = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mfa_probe_fp64_fma(ctx, ctypes.byref(t), ctypes.byref(f)))
+    return t.value, f.value
 
 
 def mfa_halo_pack(ctx, ids, ncomp, nnode, v, buf):

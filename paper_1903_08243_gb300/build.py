@@ -17,7 +17,7 @@ SOURCES = ["api.cu", "hex_kernels.cu", "hex_kernels_tune.cu", "hex_kernels_agg.c
            "hex_vector_b.cu", "tet_kernels.cu", "tet_dense.cu",
     "tri_kernels.cu", "quad_kernels.cu", "quad_kernels_a.cu",
            "quad_kernels_b.cu", "blas.cu",
-           "batch.cu", "solve.cu", "precond.cu", "cg_noalloc.cu", "halo.cu", "tables.cpp", "colour.cpp", "order.cpp", "space_map.cpp",
+           "batch.cu", "solve.cu", "precond.cu", "cg_noalloc.cu", "halo.cu", "probe.cu", "tables.cpp", "colour.cpp", "order.cpp", "space_map.cpp",
            "simplex_rules.cpp", "diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]

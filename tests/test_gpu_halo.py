@@ -84,14 +84,13 @@ def test_two_slab_ranks_in_one_process(ctx, p):
 
     ranks = [bench.sharded_operators(world, r, nx, [p], ["helmholtz"], Part, lambda a: torch.from_numpy(a).cuda())[0]
              for r in range(world)]
-    halo = mfa.dist.LibraryHaloOps(ctx) if hasattr(mfa, "dist") else mdist.LibraryHaloOps(ctx)
+    halo = mdist.LibraryHaloOps(ctx)
     plans = [mdist.device_plan(o["plan"], "cuda") for o in ranks]
     for o in ranks:
         o["x"][~torch.from_numpy(o["plan"].owned).cuda()] = 0.0  # ghosts come from the import
     # import: rank 0 sends its top plane, rank 1 receives it as its ghost plane
-    ops1 = halo
-    buf = ops1.pack(plans[0].send_import[1], ranks[0]["x"])
-    ops1.put(plans[1].recv_import[0], buf, ranks[1]["x"])
+    buf = halo.pack(plans[0].send_import[1], ranks[0]["x"])
+    halo.put(plans[1].recv_import[0], buf, ranks[1]["x"])
     for o in ranks:
         b, i = o["parts"]["boundary"], o["parts"]["interior"]
         b.apply(o["x"], o["y"], False)
