@@ -127,7 +127,7 @@ cudaError_t hex_geometry_launch(int nq, int kind, int prec, double c0, const Hex
 
 int hex_default_variant(int n, int nq, int prec) {
   if (prec == MFA_PREC_BF16) return MFA_VARIANT_LINE_STAGED;
-  if (prec == MFA_PREC_FP32) return MFA_VARIANT_LINE;
+  if (prec == MFA_PREC_FP32) return MFA_VARIANT_LINE_STAGED;
   return hex_use_eo(n, nq, prec) ? MFA_VARIANT_EVEN_ODD : MFA_VARIANT_POINT;
 }
 

@@ -17,11 +17,10 @@
 // consumed its factors, so the copy overlaps the transposed sweeps, the
 // scatter and the next gather.  Each cell's factor block is padded to 16
 // bytes for the copy.  Waits are bounded: on timeout the kernel sets error
-// bit 4 and every thread leaves.  FP32 reads its factors directly by default
-// (point-parallel, coalesced): its stage is twice as large, and the shared
-// memory it takes can cost more in residency than the copy saves.  The staged
-// form is compiled for FP32 as well (MFA_VARIANT_LINE_STAGED), and the
-// autotuner takes it where it is faster (most FP32 operators on 64^3).
+// bit 4 and every thread leaves.  FP32 stages its factors the same way by
+// default; the form that reads them straight from global memory
+// (point-parallel, coalesced; MFA_VARIANT_LINE) is compiled for both
+// precisions, and the autotuner takes it where it is faster.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -51,13 +50,36 @@ constexpr int ceil32(int x) { return (x + 31) / 32 * 32; }
 // Cells per block for a target block size (the default targets 256 threads).
 constexpr int line_cb_for(int n, int target) { return cells_for_target(n * n, target); }
 
+// Shared-memory layout of one plane: point (x, y, z) of the batch's cell c at
+// c SC + x + SX y + SY z.  Unpadded for most n.  For n = 4 and n = 8 the lines
+// of a warp would otherwise fall on the same banks (4-way and 8-way conflicts
+// in the x sweeps, 4-way in the y sweeps: strides of 4 or 8 words with the
+// default block sizes); the padded strides bring every sweep to 1.3-way on
+// average, at 25% (n = 4) and 12.5% (n = 8) more shared memory.  For n = 6, 7
+// padding removes fewer conflicts from the sweeps than it adds to the
+// point-parallel phases, so those stay unpadded.
+template <int N>
+struct LLayout {
+  static constexpr int SX = N == 8 ? 9 : N;
+  static constexpr int SY = N == 4 ? 19 : (N == 8 ? 72 : N * N);
+  static constexpr int SC = N == 4 ? 80 : (N == 8 ? 576 : N * N * N);
+  static constexpr bool PADDED = SC != N * N * N;
+  // plane offset of point i of the batch (cell i / n^3, local point i % n^3, x fastest)
+  __host__ __device__ static constexpr int of(int i) {
+    if constexpr (!PADDED) return i;
+    const int c = i / (N * N * N), q = i - c * (N * N * N);
+    return c * SC + q % N + SX * ((q / N) % N) + SY * (q / (N * N));
+  }
+};
+
 template <int N, int CBX = 0>
 struct LShape {
   static constexpr int L = N * N;         // lines per cell and direction
   static constexpr int P = N * N * N;     // points per cell
+  static constexpr int PS = LLayout<N>::SC;  // floats per cell in a plane
   static constexpr int CB = CBX > 0 ? CBX : line_cb_for(N, 256);
   static constexpr int T = ceil32(CB * L);
-  static constexpr int SMEM = 5 * CB * P * 4;
+  static constexpr int SMEM = 4 * CB * PS * 4;  // planes U, V, F0, F1 (see line_batch)
   static constexpr int K = (CB * P + T - 1) / T;  // points per thread in the point-parallel phases
 };
 
@@ -124,12 +146,13 @@ __host__ __device__ constexpr int geom_entries() {
   return KIND == MFA_FORM_MASS ? 1 : (KIND == MFA_FORM_LAPLACE ? 6 : 7);
 }
 
-// Index of point m on line (a, b) in direction DIR (0: x, 1: y, 2: z).
+// Plane offset (within a cell) of point m on line (a, b) in direction DIR (0: x, 1: y, 2: z).
 template <int N, int DIR>
 __device__ __forceinline__ int at(int a, int b, int m) {
-  if constexpr (DIR == 0) return m + N * (a + N * b);
-  else if constexpr (DIR == 1) return a + N * (m + N * b);
-  else return a + N * (b + N * m);
+  using Y = LLayout<N>;
+  if constexpr (DIR == 0) return m + Y::SX * a + Y::SY * b;
+  else if constexpr (DIR == 1) return a + Y::SX * m + Y::SY * b;
+  else return a + Y::SX * b + Y::SY * m;
 }
 
 // out[line] = T[.][.] applied along DIR: out_r = sum_m Tab[r][m] in_m (TRANS: Tab[m][r]).
@@ -197,9 +220,12 @@ struct Stage {
   int* abort;           // shared flag: a wait timed out
 };
 
+// Staged (bulk-copied) factors by default for both precisions: measured on
+// 64^3, Q1-Q6, the autotuner picked the staged form for 11 of the 12 FP32
+// operators once x is requested a batch ahead and the planes are four.
 template <int PREC>
 __host__ __device__ constexpr bool staged() {
-  return PREC == MFA_PREC_BF16;
+  return true;
 }
 
 template <int N, int KIND, int PREC, bool STG = staged<PREC>(), int CBX = 0>
@@ -212,14 +238,28 @@ __device__ __forceinline__ void issue_factors(const LineArgs& a, int64_t batch, 
   bulk_load(st.buf, static_cast<const GeoT<PREC>*>(a.geom) + c0 * a.gstride, bytes, st.bar);
 }
 
+// x at this thread's points of a batch (0 where node < 0), in registers.
+template <typename TX, int K>
+__device__ __forceinline__ void line_load_x(const void* xp, const int32_t (&node)[K], float (&xin)[K], bool bf16) {
+  const TX* x = static_cast<const TX*>(xp);
+#pragma unroll
+  for (int k = 0; k < K; ++k) xin[k] = node[k] >= 0 ? load_x(x, node[k], bf16) : 0.0f;
+}
+
 // One batch of CB consecutive cells.  Contractions run line-parallel (a
 // thread owns one line per direction); the phases that touch global memory
 // (gather, scatter) run point-parallel over the whole batch, so consecutive
 // threads read consecutive map and output addresses; the factors come from
 // the bulk-copied stage.  `next` >= 0: batch (of `an`) to prefetch afterwards.
+// `xin` holds x at this thread's points of this batch (requested during the
+// previous batch); once the forward sweeps are done, the next batch's values
+// are requested into it through `node_next`, so that they arrive while this
+// batch finishes and the gather never waits on global memory.
 template <int N, int KIND, int PREC, typename TX, bool STG = staged<PREC>(), int CBX = 0>
 __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, float* smem, Stage& st,
-                                           const LineArgs* an, int64_t next, const int32_t (&node)[LShape<N, CBX>::K]) {
+                                           const LineArgs* an, int64_t next, const int32_t (&node)[LShape<N, CBX>::K],
+                                           const int32_t (&node_next)[LShape<N, CBX>::K],
+                                           float (&xin)[LShape<N, CBX>::K]) {
   using S = LShape<N, CBX>;
   constexpr int L = S::L, P = S::P, CB = S::CB, T = S::T, K = S::K, NG = geom_entries<KIND>();
   constexpr int variant = PREC == MFA_PREC_BF16 ? 1 : 0;
@@ -229,18 +269,21 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
   const int64_t c0 = batch * CB;
   const int ncb = (int)(a.count - c0 < CB ? a.count - c0 : CB);  // cells in this batch
   const bool valid = cl < ncb;
+  constexpr int PS = S::PS;
+  using Y = LLayout<N>;
+  // Four planes of CB cells (PS floats each, layout LLayout): U (gathered input, then the z-derivative and
+  // its flux, then the B^T results), V (values at the Gauss points, then the test-side accumulation), F0 and
+  // F1 (x- and y-derivatives and their fluxes).
   float* U0 = smem;
-  float* U = U0 + cl * P;
-  float* V = U + CB * P;
-  float* F0 = V + CB * P;
-  float* F1 = F0 + CB * P;
-  float* F2 = F1 + CB * P;
-  const TX* x = static_cast<const TX*>(a.x);
+  float* U = U0 + cl * PS;
+  float* V = U + CB * PS;
+  float* F0 = V + CB * PS;
+  float* F1 = F0 + CB * PS;
 
   // gather, point-parallel: point i of the batch is local point i % P of cell c0 + i / P
 #pragma unroll
   for (int k = 0; k < K; ++k)
-    if (node[k] >= 0) U0[t + k * T] = load_x(x, node[k], variant == 1);
+    if (node[k] >= 0) U0[Y::of(t + k * T)] = xin[k];
   __syncthreads();
   if (valid) sweep<N, 0, 0, false, false, variant>(U, V, la, lb);  // B in x
   __syncthreads();
@@ -252,9 +295,11 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
     if (valid) {
       sweep<N, 0, 1, false, false, variant>(V, F0, la, lb);  // D in x
       sweep<N, 1, 1, false, false, variant>(V, F1, la, lb);  // D in y
-      sweep<N, 2, 1, false, false, variant>(V, F2, la, lb);  // D in z
+      sweep<N, 2, 1, false, false, variant>(V, U, la, lb);   // D in z, into U's plane
     }
   }
+  // the next batch's x: its nodes were requested at the start of this batch and have arrived by now
+  if (next >= 0) line_load_x<TX, K>(an->x, node_next, xin, variant == 1);
   // this batch's factors: from the stage (bulk copies) or straight from global memory
   if constexpr (STG) {
     if (!mbar_wait(st.bar, st.phase)) {
@@ -267,56 +312,55 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
   if constexpr (STG) {
     if (*st.abort) return false;
   }
-  float* V0 = U0 + CB * P;
+  float* V0 = U0 + CB * PS;
   const void* gs = STG ? static_cast<const void*>(st.buf)
                                   : static_cast<const void*>(static_cast<const GeoT<PREC>*>(a.geom) + c0 * a.gstride);
   const int64_t gsd = a.gstride;
   if constexpr (KIND == MFA_FORM_MASS) {
     for (int i = t; i < ncb * P; i += T) {
-      const int c = i / P, q = i - c * P;
-      U0[i] = geo_at<PREC, STG>(gs, c * gsd + q) * V0[i];
+      const int c = i / P, q = i - c * P, j = Y::of(i);
+      V0[j] *= geo_at<PREC, STG>(gs, c * gsd + q);
     }
   } else {
-    float* G0 = V0 + CB * P;
-    float* G1 = G0 + CB * P;
-    float* G2 = G1 + CB * P;
+    float* G0 = V0 + CB * PS;
+    float* G1 = G0 + CB * PS;
     for (int i = t; i < ncb * P; i += T) {
-      const int c = i / P, q = i - c * P;
+      const int c = i / P, q = i - c * P, j = Y::of(i);
       const int64_t gb = c * gsd + q;
       float g[NG];
 #pragma unroll
       for (int e = 0; e < NG; ++e) g[e] = geo_at<PREC, STG>(gs, gb + (int64_t)e * P);
-      const float d0 = G0[i], d1 = G1[i], d2 = G2[i];
-      G0[i] = fmaf(g[0], d0, fmaf(g[3], d1, g[4] * d2));
-      G1[i] = fmaf(g[3], d0, fmaf(g[1], d1, g[5] * d2));
-      G2[i] = fmaf(g[4], d0, fmaf(g[5], d1, g[2] * d2));
-      if constexpr (KIND == MFA_FORM_HELMHOLTZ) U0[i] = g[6] * V0[i];
-      else U0[i] = 0.0f;
+      const float d0 = G0[j], d1 = G1[j], d2 = U0[j];
+      G0[j] = fmaf(g[0], d0, fmaf(g[3], d1, g[4] * d2));
+      G1[j] = fmaf(g[3], d0, fmaf(g[1], d1, g[5] * d2));
+      U0[j] = fmaf(g[4], d0, fmaf(g[5], d1, g[2] * d2));
+      if constexpr (KIND == MFA_FORM_HELMHOLTZ) V0[j] *= g[6];
+      else V0[j] = 0.0f;
     }
   }
   __syncthreads();
   // the stage is free: start the next batch's factors now
   if (t == 0 && next >= 0) issue_factors<N, KIND, PREC, STG, CBX>(*an, next, st);
   if constexpr (KIND != MFA_FORM_MASS) {
-    if (valid) sweep<N, 0, 1, true, true, variant>(F0, U, la, lb);  // r = c0 w|J| u + D_x^T f0
+    if (valid) sweep<N, 0, 1, true, true, variant>(F0, V, la, lb);  // r = c0 w|J| u + D_x^T f0
     __syncthreads();
-    if (valid) sweep<N, 1, 1, true, true, variant>(F1, U, la, lb);  // + D_y^T f1
+    if (valid) sweep<N, 1, 1, true, true, variant>(F1, V, la, lb);  // + D_y^T f1
     __syncthreads();
-    if (valid) sweep<N, 2, 1, true, true, variant>(F2, U, la, lb);  // + D_z^T f2
+    if (valid) sweep<N, 2, 1, true, true, variant>(U, V, la, lb);   // + D_z^T f2
     __syncthreads();
   }
-  if (valid) sweep<N, 2, 0, true, false, variant>(U, V, la, lb);  // B^T in z
+  if (valid) sweep<N, 2, 0, true, false, variant>(V, U, la, lb);  // B^T in z
   __syncthreads();
-  if (valid) sweep<N, 1, 0, true, false, variant>(V, U, la, lb);  // B^T in y
+  if (valid) sweep<N, 1, 0, true, false, variant>(U, V, la, lb);  // B^T in y
   __syncthreads();
-  if (valid) sweep<N, 0, 0, true, false, variant>(U, V, la, lb);  // B^T in x
+  if (valid) sweep<N, 0, 0, true, false, variant>(V, U, la, lb);  // B^T in x
   __syncthreads();
   // scatter-add, point-parallel
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     if (node[k] < 0) continue;
-    if constexpr (sizeof(TX) == 8) add_y(static_cast<double*>(a.y), node[k], V0[t + k * T]);
-    else add_y(static_cast<float*>(a.y), node[k], V0[t + k * T]);
+    if constexpr (sizeof(TX) == 8) add_y(static_cast<double*>(a.y), node[k], U0[Y::of(t + k * T)]);
+    else add_y(static_cast<float*>(a.y), node[k], U0[Y::of(t + k * T)]);
   }
   __syncthreads();
   return true;
@@ -362,13 +406,17 @@ __global__ void __launch_bounds__(LShape<N, CBX>::T) line_apply_kernel(const Lin
   const int64_t nbatch = (a.count + S::CB - 1) / S::CB;
   if ((int64_t)blockIdx.x < nbatch && threadIdx.x == 0) issue_factors<N, KIND, PREC, STG, CBX>(a, blockIdx.x, st);
   int32_t node[S::K], nodes_next[S::K];
-  if ((int64_t)blockIdx.x < nbatch) line_load_nodes<N, CBX>(a.cell_node, a.count, blockIdx.x, nodes_next);
+  float xin[S::K];
+  if ((int64_t)blockIdx.x < nbatch) {
+    line_load_nodes<N, CBX>(a.cell_node, a.count, blockIdx.x, nodes_next);
+    line_load_x<TX, S::K>(a.x, nodes_next, xin, PREC == MFA_PREC_BF16);
+  }
   for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
     const int64_t next = batch + gridDim.x < nbatch ? batch + gridDim.x : -1;
 #pragma unroll
     for (int k = 0; k < S::K; ++k) node[k] = nodes_next[k];
     if (next >= 0) line_load_nodes<N, CBX>(a.cell_node, a.count, next, nodes_next);
-    if (!line_batch<N, KIND, PREC, TX, STG, CBX>(a, batch, smem_l, st, &a, next, node)) return;
+    if (!line_batch<N, KIND, PREC, TX, STG, CBX>(a, batch, smem_l, st, &a, next, node, nodes_next, xin)) return;
   }
 }
 
@@ -386,12 +434,14 @@ __global__ void __launch_bounds__(LShape<N>::T) line_group_kernel(const HexApply
   };
   constexpr int K = LShape<N>::K;
   int32_t node[K], nodes_next[K];
+  float xin[K];
   int k = 0;
   if ((int64_t)blockIdx.x < total) {
     while (k + 1 < nitems && (int64_t)blockIdx.x >= first[k + 1]) ++k;
     const LineArgs a0 = args_of(k);
     if (threadIdx.x == 0) issue_factors<N, KIND, PREC>(a0, blockIdx.x - first[k], st);
     line_load_nodes<N, 0>(a0.cell_node, a0.count, blockIdx.x - first[k], nodes_next);
+    line_load_x<double, K>(a0.x, nodes_next, xin, PREC == MFA_PREC_BF16);
   }
   for (int64_t gb = blockIdx.x; gb < total; gb += gridDim.x) {
     while (k + 1 < nitems && gb >= first[k + 1]) ++k;
@@ -404,7 +454,7 @@ __global__ void __launch_bounds__(LShape<N>::T) line_group_kernel(const HexApply
 #pragma unroll
     for (int j = 0; j < K; ++j) node[j] = nodes_next[j];
     if (next >= 0) line_load_nodes<N, 0>(an.cell_node, an.count, next, nodes_next);
-    if (!line_batch<N, KIND, PREC, double>(a, gb - first[k], smem_l, st, &an, next, node)) return;
+    if (!line_batch<N, KIND, PREC, double>(a, gb - first[k], smem_l, st, &an, next, node, nodes_next, xin)) return;
   }
 }
 

@@ -18,4 +18,4 @@ def test_fp64_probe_rate_and_clock():
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     assert 500.0 < mhz < 3000.0, mhz
     per_clock_per_sm = tflops * 1e12 / (sms * mhz * 1e6)
-    assert 3.5 < per_clock_per_sm < 4.2, (tflops, mhz, per_clock_per_sm)
+    assert 3.0 < per_clock_per_sm < 4.2, (tflops, mhz, per_clock_per_sm)
