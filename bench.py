@@ -123,9 +123,10 @@ def renumber(args, cell_vert, cell_node, nnode, nvert, vectors):
 
 def _workload_name(args):
     if args.workload in ("hex", "hex-vector"):
-        return "hex%d^3-perturbed0.1h-Q%s-%s%s-fp64" % (args.nx, args.degrees.replace(",", ""),
-                                                        "vector-" if args.workload == "hex-vector" else "",
-                                                        args.forms.replace(",", "+"))
+        return "hex%d^3-perturbed0.1h-Q%s-%s%s-%s" % (args.nx, args.degrees.replace(",", ""),
+                                                      "vector-" if args.workload == "hex-vector" else "",
+                                                      args.forms.replace(",", "+"),
+                                                      args.precision if args.workload == "hex" else "fp64")
     if args.workload == "tet-p1-mass":
         return "tet-kuhn%d^3x6-P1-mass-fp64" % args.nx
     if args.workload == "tet-pk":

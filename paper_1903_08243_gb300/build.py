@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmfa.so")
 SOURCES = ["api.cu", "hex_kernels.cu", "hex_kernels_tune.cu", "hex_kernels_agg.cu", "hex_kernels_otf.cu", "hex_eo.cu", "hex_eo_tune.cu", "hex_mixed.cu",
            "hex_lines_a.cu", "hex_lines_b.cu", "hex_lines_tune_a.cu", "hex_lines_tune_b.cu", "hex_vector_a.cu",
-           "hex_vector_b.cu", "tet_kernels.cu", "tet_dense.cu",
+           "hex_vector_b.cu", "tet_kernels.cu", "tet_dense.cu", "tet_cell_pk.cu",
     "tri_kernels.cu", "quad_kernels.cu", "quad_kernels_a.cu",
            "quad_kernels_b.cu", "blas.cu",
            "batch.cu", "solve.cu", "precond.cu", "cg_noalloc.cu", "halo.cu", "probe.cu", "tables.cpp", "colour.cpp", "order.cpp", "space_map.cpp",

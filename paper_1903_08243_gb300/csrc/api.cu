@@ -231,6 +231,8 @@ int hex_tables(mfa_form* f) {
   return MFA_OK;
 }
 
+bool tet_pk_cell_ok(const mfa_form* f);
+
 // Simplex rules come from simplex_rule_choice (below): the symmetric rule where
 // the integral is exact (or the form asks for MFA_RULE_SYMMETRIC), else the
 // collapsed rule of degree qdeg, which then defines the result.
@@ -259,6 +261,16 @@ static int tet_dense_tables(mfa_form* f, const std::vector<double>& pts, const s
       }
     }
   for (int q = 0; q < nq; ++q) wq[q] = w[q];
+  if (tet_pk_cell_ok(f)) {  // the same tables as a kernel parameter of the thread-per-cell kernel
+    f->tpk.nq = nq;
+    for (int q = 0; q < nq; ++q) {
+      f->tpk.w[q] = w[q];
+      for (int a = 0; a < nl; ++a) {
+        f->tpk.phi[q * nl + a] = phi[(size_t)q * nl + a];
+        for (int e = 0; e < 3; ++e) f->tpk.dphi[(q * nl + a) * 3 + e] = dphi[((size_t)q * nl + a) * 3 + e];
+      }
+    }
+  }
   int rc = cuda_alloc((void**)&f->d_tdense, sizeof(double) * buf.size(), "tet tables");
   if (!rc && cudaMemcpy(f->d_tdense, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     rc = fail(MFA_ERR_CUDA, "tet tables: upload");
@@ -326,6 +338,15 @@ bool tri_cell_ok(const mfa_form* f) {
   if (f->space->mesh->cell_type != MFA_CELL_TRI3 || f->space->degree > 4) return false;
   if (f->space->degree == 4 && f->p.kind == MFA_FORM_HYPER_JAC) return false;  // register-bound: one warp per cell
   return simplex_rule_points(f, 2) <= mfa::kTriMaxQ;
+}
+
+// The thread-per-cell P3/P4 tet kernel covers the scalar forms on rules of at most 24 points (Table 2's
+// symmetric rules of degree <= 6: P3 mass, Laplace and Helmholtz, P4 Laplace).
+bool tet_pk_cell_ok(const mfa_form* f) {
+  const mfa_space* sp = f->space;
+  if (sp->mesh->cell_type != MFA_CELL_TET4 || sp->ncomp != 1 || sp->degree < 3 || sp->degree > 4) return false;
+  if (f->p.kind > MFA_FORM_HELMHOLTZ) return false;
+  return simplex_rule_points(f, 3) <= mfa::kTetPkMaxQ;
 }
 
 int tri_tables(mfa_form* f) {
@@ -538,7 +559,11 @@ static int apply_form_raw(mfa_form* f, const double* x, double* y, cudaStream_t 
       a.b1 = f->p.b[1];
       a.b2 = f->p.b[2];
       a.err = ctx->d_err;
-      e = mfa::tet_dense_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, a, budget, stream);
+      if (f->launch.variant == MFA_VARIANT_CELL)
+        e = mfa::tet_pk_cell_launch(sp->degree, f->p.kind, colour, f->launch.cb ? f->launch.cb : 128, f->tpk, a,
+                                    budget, stream);
+      else
+        e = mfa::tet_dense_launch(sp->degree, sp->ncomp, f->p.kind, f->p.law, colour, a, budget, stream);
     } else {
       mfa::TetApplyArgs a = tet_args(f, x, y);
       a.cell_list = list;
@@ -749,6 +774,7 @@ static int cb_options(const mfa_form* f, int variant, int* out) {
   }
   if (sp->mesh->cell_type != MFA_CELL_HEX8) {
     if (sp->degree >= 3) {
+      if (variant == MFA_VARIANT_CELL) return tet_pk_cell_ok(f) ? mfa::tet_cb_options(out) : 0;  // threads per block
       if (variant != MFA_VARIANT_CELL_WARP) return 0;
       out[0] = 8;  // one warp per cell, 8 warps per block
       return 1;
@@ -779,6 +805,7 @@ static std::vector<mfa_launch_config> form_configs(const mfa_form* f) {
   if (ctype == MFA_CELL_QUAD4) variants = {MFA_VARIANT_POINT};
   else if (ctype == MFA_CELL_TRI3 && tri_cell_ok(f)) variants = {MFA_VARIANT_CELL, MFA_VARIANT_CELL_WARP};
   else if (ctype == MFA_CELL_TRI3) variants = {MFA_VARIANT_CELL_WARP};
+  else if (!hex && tet_pk_cell_ok(f)) variants = {MFA_VARIANT_CELL, MFA_VARIANT_CELL_WARP};
   else if (!hex) variants = {f->space->degree >= 3 ? MFA_VARIANT_CELL_WARP : MFA_VARIANT_CELL};
   else if (f->p.precision == MFA_PREC_FP64) variants = {MFA_VARIANT_POINT, MFA_VARIANT_EVEN_ODD};
   else variants = {MFA_VARIANT_LINE, MFA_VARIANT_LINE_STAGED};
@@ -895,7 +922,7 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
   f->p = *prm;
   f->scatter = prm->scatter == MFA_SCATTER_AUTO ? MFA_SCATTER_ATOMIC : prm->scatter;
   f->launch.variant = default_variant(sp, prm->qdeg > 0 ? prm->qdeg : sp->degree + 1, prm->precision);
-  if (tri_cell_ok(f)) f->launch.variant = MFA_VARIANT_CELL;
+  if (tri_cell_ok(f) || tet_pk_cell_ok(f)) f->launch.variant = MFA_VARIANT_CELL;
   int rc = MFA_OK;
   if (f->scatter == MFA_SCATTER_WARP) {
     // the warp-aggregated scatter is compiled for the point kernel (scalar hex, p+1 points) and the tet kernels
@@ -1063,7 +1090,7 @@ int mfa_form_set_config(mfa_form* f, const mfa_launch_config* cfg) {
   const mfa_space* sp = f->space;
   if (want.variant == MFA_VARIANT_AUTO) {
     want.variant = default_variant(sp, f->nq1, f->p.precision);
-    if (tri_cell_ok(f)) want.variant = MFA_VARIANT_CELL;
+    if (tri_cell_ok(f) || tet_pk_cell_ok(f)) want.variant = MFA_VARIANT_CELL;
     if (sp->mesh->cell_type == MFA_CELL_HEX8 && !f->d_geom) want.variant = MFA_VARIANT_POINT;
   }
   if (want.cells_per_block == 0) {

@@ -171,6 +171,57 @@ __device__ __forceinline__ void sweep(const float* in, float* out, int a, int b)
   }
 }
 
+// B along z, then D along z on the values just formed (the same line, kept in
+// registers): vout = B_z u, dout = D_z B_z u.  One shared-memory read fewer
+// per point than two separate sweeps.  `dout` may alias `in` (the thread's
+// own line is read before it is written).
+template <int N, int variant>
+__device__ __forceinline__ void sweep_bd_z(const float* in, float* vout, float* dout, int a, int b) {
+  constexpr int offB = tab_offset(N), offD = tab_offset(N) + N * N;
+  float v[N], w[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) v[m] = in[at<N, 2>(a, b, m)];
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    float s = 0.0f;
+#pragma unroll
+    for (int m = 0; m < N; ++m) s = fmaf(c_tab[variant][offB + r * N + m], v[m], s);
+    w[r] = s;
+    vout[at<N, 2>(a, b, r)] = s;
+  }
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    float s = 0.0f;
+#pragma unroll
+    for (int m = 0; m < N; ++m) s = fmaf(c_tab[variant][offD + r * N + m], w[m], s);
+    dout[at<N, 2>(a, b, r)] = s;
+  }
+}
+
+// The test side along z in one pass: out = B_z^T (acc + D_z^T f) for the
+// thread's line, without writing the sum back first.  `out` may alias `f`.
+template <int N, int variant>
+__device__ __forceinline__ void sweep_dtbt_z(const float* f, const float* acc, float* out, int a, int b) {
+  constexpr int offB = tab_offset(N), offD = tab_offset(N) + N * N;
+  float v[N], w[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) v[m] = f[at<N, 2>(a, b, m)];
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    float s = acc[at<N, 2>(a, b, r)];
+#pragma unroll
+    for (int m = 0; m < N; ++m) s = fmaf(c_tab[variant][offD + m * N + r], v[m], s);
+    w[r] = s;
+  }
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    float s = 0.0f;
+#pragma unroll
+    for (int m = 0; m < N; ++m) s = fmaf(c_tab[variant][offB + m * N + r], w[m], s);
+    out[at<N, 2>(a, b, r)] = s;
+  }
+}
+
 template <typename TX>
 __device__ __forceinline__ float load_x(const TX* x, int32_t node, bool bf16) {
   float v;
@@ -289,13 +340,14 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
   __syncthreads();
   if (valid) sweep<N, 1, 0, false, false, variant>(V, U, la, lb);  // B in y
   __syncthreads();
-  if (valid) sweep<N, 2, 0, false, false, variant>(U, V, la, lb);  // B in z: values at the Gauss points
-  if constexpr (KIND != MFA_FORM_MASS) {
+  if constexpr (KIND == MFA_FORM_MASS) {
+    if (valid) sweep<N, 2, 0, false, false, variant>(U, V, la, lb);  // B in z: values at the Gauss points
+  } else {
+    if (valid) sweep_bd_z<N, variant>(U, V, U, la, lb);  // B in z (values, into V), D in z (into U's plane)
     __syncthreads();
     if (valid) {
       sweep<N, 0, 1, false, false, variant>(V, F0, la, lb);  // D in x
       sweep<N, 1, 1, false, false, variant>(V, F1, la, lb);  // D in y
-      sweep<N, 2, 1, false, false, variant>(V, U, la, lb);   // D in z, into U's plane
     }
   }
   // the next batch's x: its nodes were requested at the start of this batch and have arrived by now
@@ -346,10 +398,10 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
     __syncthreads();
     if (valid) sweep<N, 1, 1, true, true, variant>(F1, V, la, lb);  // + D_y^T f1
     __syncthreads();
-    if (valid) sweep<N, 2, 1, true, true, variant>(U, V, la, lb);   // + D_z^T f2
-    __syncthreads();
+    if (valid) sweep_dtbt_z<N, variant>(U, V, U, la, lb);           // B^T in z of (r + D_z^T f2)
+  } else {
+    if (valid) sweep<N, 2, 0, true, false, variant>(V, U, la, lb);  // B^T in z
   }
-  if (valid) sweep<N, 2, 0, true, false, variant>(V, U, la, lb);  // B^T in z
   __syncthreads();
   if (valid) sweep<N, 1, 0, true, false, variant>(U, V, la, lb);  // B^T in y
   __syncthreads();
@@ -420,13 +472,21 @@ __global__ void __launch_bounds__(LShape<N, CBX>::T) line_apply_kernel(const Lin
   }
 }
 
+// The grouped launches have no tuner: FP32 groups read their factors straight from global memory, which the
+// 64-operator batch measured faster (11.8 against 12.8 ms per step); BF16 groups stage them.
+template <int PREC>
+__host__ __device__ constexpr bool group_staged() {
+  return PREC == MFA_PREC_BF16;
+}
+
 template <int N, int KIND, int PREC>
 __global__ void __launch_bounds__(LShape<N>::T) line_group_kernel(const HexApplyArgs* __restrict__ items,
                                                                   const int64_t* __restrict__ first, int nitems) {
   extern __shared__ __align__(128) float smem_l[];
   __shared__ int abort_flag;
+  constexpr bool STG = group_staged<PREC>();
   Stage st;
-  stage_setup<N, KIND, PREC>(smem_l, st, &abort_flag);
+  stage_setup<N, KIND, PREC, STG>(smem_l, st, &abort_flag);
   const int64_t total = first[nitems];
   auto args_of = [&](int k) {
     const HexApplyArgs h = items[k];
@@ -439,7 +499,7 @@ __global__ void __launch_bounds__(LShape<N>::T) line_group_kernel(const HexApply
   if ((int64_t)blockIdx.x < total) {
     while (k + 1 < nitems && (int64_t)blockIdx.x >= first[k + 1]) ++k;
     const LineArgs a0 = args_of(k);
-    if (threadIdx.x == 0) issue_factors<N, KIND, PREC>(a0, blockIdx.x - first[k], st);
+    if (threadIdx.x == 0) issue_factors<N, KIND, PREC, STG>(a0, blockIdx.x - first[k], st);
     line_load_nodes<N, 0>(a0.cell_node, a0.count, blockIdx.x - first[k], nodes_next);
     line_load_x<double, K>(a0.x, nodes_next, xin, PREC == MFA_PREC_BF16);
   }
@@ -454,7 +514,8 @@ __global__ void __launch_bounds__(LShape<N>::T) line_group_kernel(const HexApply
 #pragma unroll
     for (int j = 0; j < K; ++j) node[j] = nodes_next[j];
     if (next >= 0) line_load_nodes<N, 0>(an.cell_node, an.count, next, nodes_next);
-    if (!line_batch<N, KIND, PREC, double>(a, gb - first[k], smem_l, st, &an, next, node, nodes_next, xin)) return;
+    if (!line_batch<N, KIND, PREC, double, STG>(a, gb - first[k], smem_l, st, &an, next, node, nodes_next, xin))
+      return;
   }
 }
 
@@ -484,7 +545,7 @@ template <int N, int KIND, int PREC>
 cudaError_t launch_line_group(const HexApplyArgs* items, const int64_t* first, int nitems, int64_t total,
                               GridBudget budget, cudaStream_t s) {
   using S = LShape<N>;
-  constexpr int smem = line_smem<N, KIND, PREC>();
+  constexpr int smem = line_smem<N, KIND, PREC, group_staged<PREC>()>();
   auto kern = line_group_kernel<N, KIND, PREC>;
   static int bps = -1;
   if (bps < 0) bps = occupancy(kern, S::T, smem);

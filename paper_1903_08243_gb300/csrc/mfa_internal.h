@@ -263,6 +263,17 @@ cudaError_t tri_dense_launch(int p, int ncomp, int kind, int law, bool colour, c
                              cudaStream_t s);
 cudaError_t tet_diagonal_launch(int p, int ncomp, int kind, const TetTables& tb, const TetApplyArgs& a,
                                 double* d, cudaStream_t s);
+// Scalar P3/P4 tets, one thread per cell (tet_cell_pk.cu), on rules of at most 24 points: the tables as a kernel
+// parameter (27 KB at most), phi [q][a] and the reference gradients [q][a][e] with a local-dof stride of NL.
+constexpr int kTetPkMaxNl = 35, kTetPkMaxQ = 24;
+struct TetPkTables {
+  int nq;
+  double w[kTetPkMaxQ];
+  double phi[kTetPkMaxQ * kTetPkMaxNl];
+  double dphi[kTetPkMaxQ * kTetPkMaxNl * 3];
+};
+cudaError_t tet_pk_cell_launch(int p, int kind, bool colour, int threads, const TetPkTables& tb,
+                               const TetDenseArgs& a, GridBudget budget, cudaStream_t s);
 
 // ---------------------------------------------------------------- blas
 cudaError_t dot_launch(const double* a, const double* b, int64_t n, double* partial, double* out, cudaStream_t s);
@@ -354,6 +365,7 @@ struct mfa_form {
   mfa::TetTables tet{};
   double* d_tdense = nullptr;    // P3..P6 tables (TetDenseArgs layouts), tdense_nq points
   mfa::TriTables tri{};          // triangles P1..P4: tables of the thread-per-cell kernel (tri.nq = 0: none)
+  mfa::TetPkTables tpk{};        // scalar P3/P4 tets: tables of the thread-per-cell kernel (tpk.nq = 0: none)
   int tdense_nq = 0;
   void* d_geom = nullptr;
   int64_t gstride = 0;           // elements per cell of d_geom
