@@ -46,10 +46,18 @@ def test_tet_pk_scalar_parity(ctx, p, kind, scatter):
     x = fi.uniform_vector(case["nnode"], seed=40 + p)
     ref = oracle_problem(case, kind, k2=0.7).apply(x)
     form = make_form(ctx, case, kind, k2=0.7, scatter=scatter)
-    assert form.config().variant == mfa.MFA_VARIANT_CELL_WARP
-    y = form.apply(torch.from_numpy(x).cuda())
-    ctx.sync()
-    check(y.cpu().numpy(), ref)
+    # one thread per cell where the rule has at most 24 points (Table 2's symmetric rules: P3 every scalar form,
+    # P4 Laplace), else one warp per cell; every listed configuration gives the oracle's result
+    cell = p == 3 or (p == 4 and kind == "laplace")
+    assert form.config().variant == (mfa.MFA_VARIANT_CELL if cell else mfa.MFA_VARIANT_CELL_WARP)
+    variants = {c.variant for c in form.configs()}
+    assert variants == ({mfa.MFA_VARIANT_CELL, mfa.MFA_VARIANT_CELL_WARP} if cell else {mfa.MFA_VARIANT_CELL_WARP})
+    xd = torch.from_numpy(x).cuda()
+    for c in form.configs():
+        form.set_config(c)
+        y = form.apply(xd)
+        ctx.sync()
+        check(y.cpu().numpy(), ref)
 
 
 @pytest.mark.parametrize("p", [3, 4, 5, 6])
