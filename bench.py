@@ -56,7 +56,8 @@ def parse_args():
     ap.add_argument("--train-rhs", type=int, default=3)
     ap.add_argument("--train-steps", type=int, default=800)
     ap.add_argument("--train-lr", type=float, default=2e-3)
-    ap.add_argument("--train-data", choices=["grf", "white"], default="white")
+    ap.add_argument("--train-data", choices=["grf", "white", "mixed"], default="white")
+    ap.add_argument("--lanczos", type=int, default=300, help="pcg: PCG steps of the spectrum estimate")
     ap.add_argument("--precision", choices=["fp64", "fp32", "bf16"], default=None,
                     help="arithmetic (hex and batched workloads; default fp64 for hex, fp32 for batched)")
     ap.add_argument("--nops", type=int, default=64)
@@ -1140,24 +1141,28 @@ def pcg_arm(args, world, rank, local):
 
     # ---- training data: (r, e) pairs from plain CG iterates.  "grf": right-hand sides like the test
     # ones, reference solution by the mixed solver; "white": manufactured solutions x* ~ U[-1,1) per dof,
-    # b = A x*, whose early plain-CG errors span the whole spectrum (the part a local preconditioner can act on).
+    # b = A x*, whose early plain-CG errors span the whole spectrum (the part a local preconditioner can act on);
+    # "mixed": both, so that the loss also sees the smooth late errors that set the smallest eigenvalue of M A.
     t0 = time.perf_counter()
     rs, es = [], []
-    its = (2, 6, 20, 60, 150) if args.train_data == "grf" else (0, 1, 2, 4, 8, 16)
-    for j in range(args.train_rhs):
-        if args.train_data == "grf":
-            b = grf_rhs(300 + j)
-            xs = torch.zeros_like(b)
-            mfa.mfa_fcg_mixed(ctx.h, A64.h, A32.h, args.inner, b, xs, 1e-10, 5000)
-        else:
-            xs = torch.from_numpy(fi.uniform_vector(nnode, seed=300 + j)).cuda()
-            b = A64.apply(xs)
-        for k in its:
-            x = torch.zeros_like(b)
-            mfa.mfa_cg(ctx.h, A32.h, mfa.MFA_PC_NONE, b, x, 1e-30, k)  # k plain CG steps
-            r = b - A64.apply(x)
-            rs.append(r.float())
-            es.append((xs - x).float())
+    kinds = {"grf": ["grf"], "white": ["white"], "mixed": ["white", "grf"]}[args.train_data]
+    its_of = {"grf": (2, 6, 20, 60, 150), "white": (0, 1, 2, 4, 8, 16)}
+    its = tuple(k for kind in kinds for k in its_of[kind])
+    for kind in kinds:
+        for j in range(args.train_rhs):
+            if kind == "grf":
+                b = grf_rhs(300 + j)
+                xs = torch.zeros_like(b)
+                mfa.mfa_fcg_mixed(ctx.h, A64.h, A32.h, args.inner, b, xs, 1e-10, 5000)
+            else:
+                xs = torch.from_numpy(fi.uniform_vector(nnode, seed=300 + j)).cuda()
+                b = A64.apply(xs)
+            for k in its_of[kind]:
+                x = torch.zeros_like(b)
+                mfa.mfa_cg(ctx.h, A32.h, mfa.MFA_PC_NONE, b, x, 1e-30, k)  # k plain CG steps
+                r = b - A64.apply(x)
+                rs.append(r.float())
+                es.append((xs - x).float())
     ctx.sync()
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -1167,13 +1172,33 @@ def pcg_arm(args, world, rank, local):
     t_train = time.perf_counter() - t0
     del rs, es
 
+    # spectrum of the preconditioned operator (untimed): Ritz values of M A from the Lanczos coefficients of
+    # PCG, with M = Jacobi and M = the learned linear preconditioner (symmetric positive definite)
+    dA = A64.diagonal()
+    ctx.sync()
+
+    def apply_jacobi(r):
+        return r / dA
+
+    def apply_learned(r):
+        z = torch.empty_like(r, dtype=torch.float32)
+        mfa.mfa_precond_apply(ctx.h, pc, r.float(), z)
+        return z.double()
+
+    b_spec = grf_rhs(399)
+    spectrum = {"iterations": args.lanczos}
+    for name, apply_m in (("jacobi", apply_jacobi), ("learned", apply_learned)):
+        lo, hi = pcg_ritz_extremes(lambda v: A64.apply(v), apply_m, b_spec, args.lanczos)
+        spectrum[name] = {"lambda_min": lo, "lambda_max": hi, "kappa": hi / lo}
+
     rows = []
     sampler = ClockSampler(local)
     sampler.start()
+    methods = ("jacobi_pcg_fp64", "fcg_mixed", "fcg_learned", "fcg_learned_fallback")
     for r in range(args.nrhs + 1):  # the first solve of each method warms up and is not reported
         b = grf_rhs(400 + r)
         res = {}
-        for name in ("jacobi_pcg_fp64", "fcg_mixed", "fcg_learned"):
+        for name in methods:
             x = torch.zeros_like(b)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -1183,13 +1208,16 @@ def pcg_arm(args, world, rank, local):
                 inner = 0
             elif name == "fcg_mixed":
                 rc, it, inner, rel = mfa.mfa_fcg_mixed(ctx.h, A64.h, A32.h, args.inner, b, x, rtol, 5000)
-            else:
-                rc, it, inner, rel, fb = mfa.mfa_fcg_learned(ctx.h, A64.h, A32.h, pc, args.inner, b, x, rtol, 5000)
+            else:  # the learned solver on its own, then with the in-solve fallback to the Jacobi inner loop
+                rc, it, inner, rel, fb = mfa.mfa_fcg_learned(ctx.h, A64.h, A32.h, pc, args.inner, b, x, rtol, 5000,
+                                                             fallback=name.endswith("fallback"),
+                                                             raise_on_breakdown=False)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             true_rel = float(torch.linalg.norm(b - A64.apply(x)) / torch.linalg.norm(b))
             res[name] = {"seconds": dt, "iterations": it, "inner_iterations": inner, "relres": rel,
-                         "true_relres": true_rel, "status": rc, "fallback": fb}
+                         "true_relres": true_rel, "status": rc, "converged": bool(true_rel <= 1.01 * rtol),
+                         "fallback": fb}
         if r > 0:
             rows.append(res)
     clocks = sampler.stop()
@@ -1197,6 +1225,8 @@ def pcg_arm(args, world, rank, local):
     tj = statistics.mean(r["jacobi_pcg_fp64"]["seconds"] for r in rows)
     tm = statistics.mean(r["fcg_mixed"]["seconds"] for r in rows)
     tl = statistics.mean(r["fcg_learned"]["seconds"] for r in rows)
+    tlf = statistics.mean(r["fcg_learned_fallback"]["seconds"] for r in rows)
+    learned_converged = all(r["fcg_learned"]["converged"] for r in rows)
     if rank == 0:
         line = {
             "metric": "PCG time-to-1e-8", "value": tl, "unit": "s", "n_gpus": world, "steps": args.nrhs,
@@ -1213,11 +1243,49 @@ def pcg_arm(args, world, rank, local):
                                     "steps": args.train_steps,
                                     "lr": args.train_lr, "data_seconds": t_data, "train_seconds": t_train,
                                     "loss_first (Jacobi step)": loss_first, "loss_last": loss_last}},
+            "value_is": "the learned solver on its own (no fallback to the Jacobi inner loop)%s" % (
+                "" if learned_converged else "; it did NOT reach 1e-8 on every right-hand side within 5000 outer "
+                                             "iterations, so the value is a time to the iteration limit"),
             "jacobi_pcg_fp64_seconds": tj, "fcg_mixed_jacobi_seconds": tm, "fcg_learned_seconds": tl,
-            "speedup_vs_jacobi_pcg_fp64": tj / tl, "learned_gain_vs_jacobi_inner": tm / tl, "solves": rows,
+            "fcg_learned_with_fallback_seconds": tlf,
+            "fallback_used": [r["fcg_learned_fallback"]["fallback"] for r in rows],
+            "speedup_vs_jacobi_pcg_fp64": tj / tl, "learned_gain_vs_jacobi_inner": tm / tl,
+            "learned_beats_jacobi_inner": bool(learned_converged and tl < tm),
+            "spectrum_of_MA": spectrum, "solves": rows,
             "clocks": clocks, "roofline": None, "cpu_baseline": None, "e2e": None,
         }
         print(json.dumps(line), flush=True)
+
+
+def pcg_ritz_extremes(apply_a, apply_m, b, iters):
+    """Smallest and largest Ritz values of M A after `iters` PCG steps from x = 0 (the Lanczos tridiagonal of the
+    PCG coefficients: diagonal 1/alpha_j + beta_{j-1}/alpha_{j-1}, off-diagonal sqrt(beta_j)/alpha_j)."""
+    import torch
+
+    r = b.clone()
+    z = apply_m(r)
+    p = z.clone()
+    rz = float(torch.dot(r, z))
+    alphas, betas = [], []
+    for _ in range(iters):
+        q = apply_a(p)
+        alpha = rz / float(torch.dot(p, q))
+        r -= alpha * q
+        z = apply_m(r)
+        rz_new = float(torch.dot(r, z))
+        beta = rz_new / rz
+        alphas.append(alpha)
+        betas.append(beta)
+        p = z + beta * p
+        rz = rz_new
+    k = len(alphas)
+    T = np.zeros((k, k))
+    for j in range(k):
+        T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j + 1 < k:
+            T[j, j + 1] = T[j + 1, j] = np.sqrt(betas[j]) / alphas[j]
+    ev = np.linalg.eigvalsh(T)
+    return float(ev[0]), float(ev[-1])
 
 
 def pcg_elasticity_arm(args, world, rank, local):
