@@ -6,8 +6,11 @@
 // cell: in the point phase each lane takes one quadrature point of a chunk of
 // 32 and interpolates the field and its reference gradient from the cell's
 // dofs (staged in shared memory), evaluates the pointwise physics on the
-// affine cell, and stages the fluxes; in the dof phase each lane takes local
-// dofs and accumulates the test-side sums over the chunk's points.  Both
+// affine cell, and stages the fluxes; in the dof phase each lane takes
+// (local dof, component) pairs and accumulates the test-side sums over the
+// chunk's points (a vector P3 cell has 60 such pairs: two rounds of 32 lanes,
+// 94% busy, where one lane per dof with its three components kept 20 of 32
+// lanes busy).  Both
 // phases read the basis tables (FP64, in global memory, cached in L1/L2) with
 // consecutive lanes on consecutive addresses: [a][q] layout for the point
 // phase, [q][a] for the dof phase.
@@ -23,7 +26,7 @@ template <int NL, int NC, int KIND>
 struct DenseShape {
   // staged per point: value term and reference flux (up to 3 directions) of each component
   static constexpr int S = 4 * NC;
-  static constexpr int R = (NL + 31) / 32;  // dofs per lane
+  static constexpr int R = (NL * NC + 31) / 32;  // (dof, component) pairs per lane
   static constexpr int SMEM_WARP = 2 * NL * NC + 32 * S;  // doubles: x (and the coefficient), stage
 };
 
@@ -86,11 +89,9 @@ __global__ void __launch_bounds__(32 * kWarps) simplex_dense_kernel(const TetDen
     }
     __syncwarp();
 
-    double acc[SH::R][NC];
+    double acc[SH::R];
 #pragma unroll
-    for (int r = 0; r < SH::R; ++r)
-#pragma unroll
-      for (int c = 0; c < NC; ++c) acc[r][c] = 0.0;
+    for (int r = 0; r < SH::R; ++r) acc[r] = 0.0;
     bool ok = true;
 
     for (int q0 = 0; q0 < nq; q0 += 32) {
@@ -171,32 +172,25 @@ __global__ void __launch_bounds__(32 * kWarps) simplex_dense_kernel(const TetDen
         mine[4 * c + 3] = sh[c][2];
       }
       __syncwarp();
-      // ---- dof phase: lane = local dofs lane, lane + 32, ...
+      // ---- dof phase: lane = (local dof, component) pairs lane, lane + 32, ... (pair i: dof i / NC, component
+      // i % NC)
       const int nqc = nq - q0 < 32 ? nq - q0 : 32;
 #pragma unroll
       for (int r = 0; r < SH::R; ++r) {
-        const int al = lane + 32 * r;
-        if (al < NL) {
+        const int task = lane + 32 * r;
+        if (task < NL * NC) {
+          const int al = task / NC, c = task - al * NC;
+          double s = acc[r];
           for (int tq = 0; tq < nqc; ++tq) {
             const int64_t qa = (int64_t)(q0 + tq) * NL + al;
-            const double* sp = st + tq * SH::S;
-            const double ph = kValue ? __ldg(a.phi_qa + qa) : 0.0;
-            double d[3] = {0.0, 0.0, 0.0};
+            const double* sp = st + tq * SH::S + 4 * c;
+            if constexpr (kValue) s = fma(__ldg(a.phi_qa + qa), sp[0], s);
             if constexpr (kGrad) {
 #pragma unroll
-              for (int e = 0; e < DIM; ++e) d[e] = __ldg(a.dphi_qae + DIM * qa + e);
-            }
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-              double s = acc[r][c];
-              if constexpr (kValue) s = fma(ph, sp[4 * c + 0], s);
-              if constexpr (kGrad) {
-#pragma unroll
-                for (int e = 0; e < DIM; ++e) s = fma(d[e], sp[4 * c + 1 + e], s);
-              }
-              acc[r][c] = s;
+              for (int e = 0; e < DIM; ++e) s = fma(__ldg(a.dphi_qae + DIM * qa + e), sp[1 + e], s);
             }
           }
+          acc[r] = s;
         }
       }
       __syncwarp();
@@ -205,15 +199,13 @@ __global__ void __launch_bounds__(32 * kWarps) simplex_dense_kernel(const TetDen
     // scatter
 #pragma unroll
     for (int r = 0; r < SH::R; ++r) {
-      const int al = lane + 32 * r;
-      if (al < NL) {
+      const int task = lane + 32 * r;
+      if (task < NL * NC) {
+        const int al = task / NC, c = task - al * NC;
         const int32_t node = __ldg(a.cell_node + cell * NL + al);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          double* dst = a.y + (int64_t)NC * node + c;
-          if constexpr (COLOUR) *dst += acc[r][c];
-          else atomicAdd(dst, acc[r][c]);
-        }
+        double* dst = a.y + (int64_t)NC * node + c;
+        if constexpr (COLOUR) *dst += acc[r];
+        else atomicAdd(dst, acc[r]);
       }
     }
     __syncwarp();  // xl/ul/st are rewritten by the next cell
