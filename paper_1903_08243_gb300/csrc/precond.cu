@@ -162,16 +162,35 @@ __device__ __forceinline__ void load_weights(bf16* W1s, bf16* W2s, float* b1s, c
   for (int i = threadIdx.x; i < kH; i += kThreads) b1s[i] = a.b1[i];
 }
 
+// Entries gathered or scattered per thread and round: the tile's node ids
+// are read first (consecutive, coalesced), then every value they point to, so
+// that kUnr dependent load pairs are in flight per thread instead of one.
+constexpr int kUnr = 8;
+
 // Gather r for the tile into F (float [kTile][kK]), then per-cell norms and
 // the normalised BF16 inputs Z (zero-padded).  Ends with a block barrier.
 __device__ __forceinline__ void gather_inputs(const MlpArgs& a, int64_t c0, int ncb, float* F, float* scale, bf16* Zs) {
   const int nloc = a.nloc;
   for (int i = threadIdx.x; i < kTile * kK; i += kThreads) F[i] = 0.0f;
   __syncthreads();
-  for (int i = threadIdx.x; i < ncb * nloc; i += kThreads) {
-    const int c = i / nloc, k = i - c * nloc;
-    const int32_t node = __ldg(a.cell_node + (c0 + c) * nloc + k);
-    F[c * kK + k] = a.linear ? __ldg(a.winv + node) * __ldg(a.r + node) : __ldg(a.r + node);
+  const int total = ncb * nloc;
+  const int32_t* cn = a.cell_node + c0 * nloc;  // the tile's rows of the map are consecutive
+  for (int i0 = threadIdx.x; i0 < total; i0 += kThreads * kUnr) {
+    int32_t nd[kUnr];
+    float v[kUnr];
+#pragma unroll
+    for (int u = 0; u < kUnr; ++u) nd[u] = i0 + u * kThreads < total ? __ldg(cn + i0 + u * kThreads) : -1;
+#pragma unroll
+    for (int u = 0; u < kUnr; ++u)
+      v[u] = nd[u] < 0 ? 0.0f : (a.linear ? __ldg(a.winv + nd[u]) * __ldg(a.r + nd[u]) : __ldg(a.r + nd[u]));
+#pragma unroll
+    for (int u = 0; u < kUnr; ++u) {
+      const int i = i0 + u * kThreads;
+      if (i < total) {
+        const int c = i / nloc, k = i - c * nloc;
+        F[c * kK + k] = v[u];
+      }
+    }
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -254,10 +273,25 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_forward_kernel(const MlpArgs 
       F[(row + 8) * kK + n + 1] = acc[t][3] * scale[row + 8];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < ncb * a.nloc; i += kThreads) {  // assemble with the partition-of-unity weights
-      const int c = i / a.nloc, k = i - c * a.nloc;
-      const int32_t node = __ldg(a.cell_node + (c0 + c) * a.nloc + k);
-      atomicAdd(a.y + node, __ldg(a.winv + node) * F[c * kK + k]);
+    {  // assemble with the partition-of-unity weights
+      const int total = ncb * a.nloc;
+      const int32_t* cn = a.cell_node + c0 * a.nloc;
+      for (int i0 = threadIdx.x; i0 < total; i0 += kThreads * kUnr) {
+        int32_t nd[kUnr];
+        float w[kUnr];
+#pragma unroll
+        for (int u = 0; u < kUnr; ++u) nd[u] = i0 + u * kThreads < total ? __ldg(cn + i0 + u * kThreads) : -1;
+#pragma unroll
+        for (int u = 0; u < kUnr; ++u) w[u] = nd[u] < 0 ? 0.0f : __ldg(a.winv + nd[u]);
+#pragma unroll
+        for (int u = 0; u < kUnr; ++u) {
+          const int i = i0 + u * kThreads;
+          if (nd[u] >= 0) {
+            const int c = i / a.nloc, k = i - c * a.nloc;
+            atomicAdd(a.y + nd[u], w[u] * F[c * kK + k]);
+          }
+        }
+      }
     }
     __syncthreads();
   }
@@ -292,10 +326,25 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_backward_kernel(const MlpArgs
     // Delta[c][o] = s_c w[node] dL/du[node]  (dL/dO), zero-padded
     for (int i = threadIdx.x; i < kTile * kLd; i += kThreads) Ds[i] = __float2bfloat16_rn(0.0f);
     __syncthreads();
-    for (int i = threadIdx.x; i < ncb * a.nloc; i += kThreads) {
-      const int c = i / a.nloc, k = i - c * a.nloc;
-      const int32_t node = __ldg(a.cell_node + (c0 + c) * a.nloc + k);
-      Ds[c * kLd + k] = __float2bfloat16_rn(scale[c] * __ldg(a.winv + node) * gs * __ldg(a.g + node));
+    {
+      const int total = ncb * a.nloc;
+      const int32_t* cn = a.cell_node + c0 * a.nloc;
+      for (int i0 = threadIdx.x; i0 < total; i0 += kThreads * kUnr) {
+        int32_t nd[kUnr];
+        float v[kUnr];
+#pragma unroll
+        for (int u = 0; u < kUnr; ++u) nd[u] = i0 + u * kThreads < total ? __ldg(cn + i0 + u * kThreads) : -1;
+#pragma unroll
+        for (int u = 0; u < kUnr; ++u) v[u] = nd[u] < 0 ? 0.0f : __ldg(a.winv + nd[u]) * __ldg(a.g + nd[u]);
+#pragma unroll
+        for (int u = 0; u < kUnr; ++u) {
+          const int i = i0 + u * kThreads;
+          if (nd[u] >= 0) {
+            const int c = i / a.nloc, k = i - c * a.nloc;
+            Ds[c * kLd + k] = __float2bfloat16_rn(scale[c] * v[u] * gs);
+          }
+        }
+      }
     }
     __syncthreads();
     if (a.linear) {
