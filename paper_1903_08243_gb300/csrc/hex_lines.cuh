@@ -25,7 +25,6 @@
 
 #include <cuda_bf16.h>
 
-#include <algorithm>
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -46,10 +45,10 @@ constexpr int kTabFloats = tab_offset(10);
 // One copy per translation unit; filled by upload_tables() of that unit.
 static __constant__ float c_tab[2][kTabFloats];  // [0]: FP32 tables, [1]: tables rounded to bfloat16
 
-__host__ __device__ constexpr int ceil32(int x) { return (x + 31) / 32 * 32; }
+constexpr int ceil32(int x) { return (x + 31) / 32 * 32; }
 
 // Cells per block for a target block size (the default targets 256 threads).
-__host__ __device__ constexpr int line_cb_for(int n, int target) { return cells_for_target(n * n, target); }
+constexpr int line_cb_for(int n, int target) { return cells_for_target(n * n, target); }
 
 // Shared-memory layout of one plane: point (x, y, z) of the batch's cell c at
 // c SC + x + SX y + SY z.  Unpadded for most n.  For n = 4 and n = 8 the lines
@@ -83,49 +82,6 @@ struct LShape {
   static constexpr int SMEM = 4 * CB * PS * 4;  // planes U, V, F0, F1 (see line_batch)
   static constexpr int K = (CB * P + T - 1) / T;  // points per thread in the point-parallel phases
 };
-
-// Line-to-thread maps of the y and z sweeps for odd n.  With thread t on
-// line t of its direction, the lines a warp reads at once start at
-// addresses (a + n^2 b + n^3 c) mod 32 (y) or (a + n b + n^3 c) mod 32 (z)
-// that repeat: for n = 7 the y sweeps average 2.9-way bank conflicts.  The
-// host assigns the lines of each such sweep to threads so that a warp's lines
-// fall on distinct banks wherever the counts allow (greedy over the residues
-// mod 32), for n = 5, 7, 9 at both cells-per-block choices: the y sweeps of
-// n = 7 drop to 1.4-1.6-way, the z sweeps to 1.0-1.4.  Even n are handled by
-// the padded layout instead (their residues are all even).  Entry: cell << 8
-// | a << 4 | b, or 0xFFFF for a thread without a line.
-__host__ __device__ constexpr bool line_mapped(int n) { return n == 5 || n == 7 || n == 9; }
-__host__ __device__ constexpr int lmap_threads(int n, int target) { return ceil32(line_cb_for(n, target) * n * n); }
-__host__ __device__ constexpr int lmap_offset(int n, int target, int dir) {
-  int off = 0;
-  for (int k = 5; k <= 9; k += 2)
-    for (int tg = 256; tg <= 512; tg += 256)
-      for (int d = 1; d <= 2; ++d) {
-        if (k == n && tg == target && d == dir) return off;
-        off += lmap_threads(k, tg);
-      }
-  return off;
-}
-constexpr int kLmapEntries = lmap_offset(0, 0, 0);
-static __constant__ uint16_t c_lmap[kLmapEntries];
-
-// The line (cell, a, b) of thread t in direction DIR (cell >= CB: none).
-template <int N, int CBX, int DIR>
-__device__ __forceinline__ void line_of(int t, int& cl, int& a, int& b) {
-  using S = LShape<N, CBX>;
-  if constexpr (DIR == 0 || !line_mapped(N)) {
-    cl = t / S::L;
-    const int l = t - cl * S::L;
-    a = l % N;
-    b = l / N;
-  } else {
-    constexpr int off = lmap_offset(N, S::CB == line_cb_for(N, 256) ? 256 : 512, DIR);
-    const uint32_t v = c_lmap[off + t];
-    cl = v == 0xFFFFu ? S::CB : (int)(v >> 8);
-    a = (int)((v >> 4) & 15u);
-    b = (int)(v & 15u);
-  }
-}
 
 // Node of each of this thread's points of batch `batch` (-1 past the batch's end): requested a batch
 // ahead, so the gather and the scatter wait on one load instead of two.
@@ -356,46 +312,43 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
                                            const int32_t (&node_next)[LShape<N, CBX>::K],
                                            float (&xin)[LShape<N, CBX>::K]) {
   using S = LShape<N, CBX>;
-  constexpr int P = S::P, CB = S::CB, T = S::T, K = S::K, NG = geom_entries<KIND>();
+  constexpr int L = S::L, P = S::P, CB = S::CB, T = S::T, K = S::K, NG = geom_entries<KIND>();
   constexpr int variant = PREC == MFA_PREC_BF16 ? 1 : 0;
   const int t = threadIdx.x;
+  const int cl = t / L, l = t - cl * L;
+  const int la = l % N, lb = l / N;
   const int64_t c0 = batch * CB;
   const int ncb = (int)(a.count - c0 < CB ? a.count - c0 : CB);  // cells in this batch
+  const bool valid = cl < ncb;
   constexpr int PS = S::PS;
   using Y = LLayout<N>;
-  // this thread's line in each direction (x: line t; y, z: line_of)
-  int cx, la, lb, cy, ya, yb, cz, za, zb;
-  line_of<N, CBX, 0>(t, cx, la, lb);
-  line_of<N, CBX, 1>(t, cy, ya, yb);
-  line_of<N, CBX, 2>(t, cz, za, zb);
-  const bool vx = cx < ncb, vy = cy < ncb, vz = cz < ncb;
   // Four planes of CB cells (PS floats each, layout LLayout): U (gathered input, then the z-derivative and
   // its flux, then the B^T results), V (values at the Gauss points, then the test-side accumulation), F0 and
-  // F1 (x- and y-derivatives and their fluxes).  Xd: the plane X at the cell of this thread's line along d.
+  // F1 (x- and y-derivatives and their fluxes).
   float* U0 = smem;
-  float* V0p = U0 + CB * PS;
-  float* F00 = V0p + CB * PS;
-  float* F10 = F00 + CB * PS;
-  float *Ux = U0 + cx * PS, *Vx = V0p + cx * PS, *F0x = F00 + cx * PS;
-  float *Uy = U0 + cy * PS, *Vy = V0p + cy * PS, *F1y = F10 + cy * PS;
-  float *Uz = U0 + cz * PS, *Vz = V0p + cz * PS;
+  float* U = U0 + cl * PS;
+  float* V = U + CB * PS;
+  float* F0 = V + CB * PS;
+  float* F1 = F0 + CB * PS;
 
   // gather, point-parallel: point i of the batch is local point i % P of cell c0 + i / P
 #pragma unroll
   for (int k = 0; k < K; ++k)
     if (node[k] >= 0) U0[Y::of(t + k * T)] = xin[k];
   __syncthreads();
-  if (vx) sweep<N, 0, 0, false, false, variant>(Ux, Vx, la, lb);  // B in x
+  if (valid) sweep<N, 0, 0, false, false, variant>(U, V, la, lb);  // B in x
   __syncthreads();
-  if (vy) sweep<N, 1, 0, false, false, variant>(Vy, Uy, ya, yb);  // B in y
+  if (valid) sweep<N, 1, 0, false, false, variant>(V, U, la, lb);  // B in y
   __syncthreads();
   if constexpr (KIND == MFA_FORM_MASS) {
-    if (vz) sweep<N, 2, 0, false, false, variant>(Uz, Vz, za, zb);  // B in z: values at the Gauss points
+    if (valid) sweep<N, 2, 0, false, false, variant>(U, V, la, lb);  // B in z: values at the Gauss points
   } else {
-    if (vz) sweep_bd_z<N, variant>(Uz, Vz, Uz, za, zb);  // B in z (values, into V), D in z (into U's plane)
+    if (valid) sweep_bd_z<N, variant>(U, V, U, la, lb);  // B in z (values, into V), D in z (into U's plane)
     __syncthreads();
-    if (vx) sweep<N, 0, 1, false, false, variant>(Vx, F0x, la, lb);  // D in x
-    if (vy) sweep<N, 1, 1, false, false, variant>(Vy, F1y, ya, yb);  // D in y
+    if (valid) {
+      sweep<N, 0, 1, false, false, variant>(V, F0, la, lb);  // D in x
+      sweep<N, 1, 1, false, false, variant>(V, F1, la, lb);  // D in y
+    }
   }
   // the next batch's x: its nodes were requested at the start of this batch and have arrived by now
   if (next >= 0) line_load_x<TX, K>(an->x, node_next, xin, variant == 1);
@@ -411,7 +364,7 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
   if constexpr (STG) {
     if (*st.abort) return false;
   }
-  float* V0 = V0p;
+  float* V0 = U0 + CB * PS;
   const void* gs = STG ? static_cast<const void*>(st.buf)
                                   : static_cast<const void*>(static_cast<const GeoT<PREC>*>(a.geom) + c0 * a.gstride);
   const int64_t gsd = a.gstride;
@@ -441,18 +394,18 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
   // the stage is free: start the next batch's factors now
   if (t == 0 && next >= 0) issue_factors<N, KIND, PREC, STG, CBX>(*an, next, st);
   if constexpr (KIND != MFA_FORM_MASS) {
-    if (vx) sweep<N, 0, 1, true, true, variant>(F0x, Vx, la, lb);  // r = c0 w|J| u + D_x^T f0
+    if (valid) sweep<N, 0, 1, true, true, variant>(F0, V, la, lb);  // r = c0 w|J| u + D_x^T f0
     __syncthreads();
-    if (vy) sweep<N, 1, 1, true, true, variant>(F1y, Vy, ya, yb);  // + D_y^T f1
+    if (valid) sweep<N, 1, 1, true, true, variant>(F1, V, la, lb);  // + D_y^T f1
     __syncthreads();
-    if (vz) sweep_dtbt_z<N, variant>(Uz, Vz, Uz, za, zb);           // B^T in z of (r + D_z^T f2)
+    if (valid) sweep_dtbt_z<N, variant>(U, V, U, la, lb);           // B^T in z of (r + D_z^T f2)
   } else {
-    if (vz) sweep<N, 2, 0, true, false, variant>(Vz, Uz, za, zb);  // B^T in z
+    if (valid) sweep<N, 2, 0, true, false, variant>(V, U, la, lb);  // B^T in z
   }
   __syncthreads();
-  if (vy) sweep<N, 1, 0, true, false, variant>(Uy, Vy, ya, yb);  // B^T in y
+  if (valid) sweep<N, 1, 0, true, false, variant>(U, V, la, lb);  // B^T in y
   __syncthreads();
-  if (vx) sweep<N, 0, 0, true, false, variant>(Vx, Ux, la, lb);  // B^T in x
+  if (valid) sweep<N, 0, 0, true, false, variant>(V, U, la, lb);  // B^T in x
   __syncthreads();
   // scatter-add, point-parallel
 #pragma unroll
@@ -604,42 +557,6 @@ cudaError_t launch_line_group(const HexApplyArgs* items, const int64_t* first, i
 
 namespace {  // one copy per translation unit, like c_tab
 
-// Threads-to-lines map of direction `dir` (1: y, 2: z) for cb cells of n^3 points and t threads (line_of).
-// Greedy: lines are taken residue class by residue class (the largest classes first) and each goes to the
-// warp with room that holds the fewest lines of its class.
-inline void build_line_map(int n, int cb, int t, int dir, uint16_t* out) {
-  const int nw = t / 32;
-  std::vector<std::vector<int>> byres(32);
-  for (int c = 0; c < cb; ++c)
-    for (int b = 0; b < n; ++b)
-      for (int a = 0; a < n; ++a) {
-        const int base = c * n * n * n + a + (dir == 1 ? n * n : n) * b;
-        byres[base % 32].push_back((c << 8) | (a << 4) | b);
-      }
-  std::vector<int> order(32);
-  for (int r = 0; r < 32; ++r) order[r] = r;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int x, int y) { return byres[x].size() > byres[y].size(); });
-  std::vector<std::vector<int>> warps(nw);
-  std::vector<std::vector<int>> count(nw, std::vector<int>(32, 0));
-  int start = 0;
-  for (int r : order)
-    for (int line : byres[r]) {
-      int best = -1;
-      for (int k = 0; k < nw; ++k) {
-        const int w = (start + k) % nw;
-        if ((int)warps[w].size() >= 32) continue;
-        if (best < 0 || count[w][r] < count[best][r]) best = w;
-        if (count[w][r] == 0) break;
-      }
-      warps[best].push_back(line);
-      ++count[best][r];
-      start = (best + 1) % nw;
-    }
-  for (int w = 0; w < nw; ++w)
-    for (int i = 0; i < 32; ++i) out[32 * w + i] = i < (int)warps[w].size() ? (uint16_t)warps[w][i] : 0xFFFF;
-}
-
 std::mutex g_tab_mutex;
 bool g_tab_ready[64] = {false};
 
@@ -669,13 +586,6 @@ inline cudaError_t upload_tables() {
     }
   }
   e = cudaMemcpyToSymbol(c_tab, tab.data(), sizeof(float) * 2 * kTabFloats);
-  if (e != cudaSuccess) return e;
-  std::vector<uint16_t> lmap(kLmapEntries);
-  for (int n = 5; n <= 9; n += 2)
-    for (int tg = 256; tg <= 512; tg += 256)
-      for (int d = 1; d <= 2; ++d)
-        build_line_map(n, line_cb_for(n, tg), lmap_threads(n, tg), d, lmap.data() + lmap_offset(n, tg, d));
-  e = cudaMemcpyToSymbol(c_lmap, lmap.data(), sizeof(uint16_t) * kLmapEntries);
   if (e == cudaSuccess) g_tab_ready[dev] = true;
   return e;
 }

@@ -141,7 +141,7 @@ struct LaunchConfig {
   int max_blocks = 0;  // grid cap (GridBudget::max_blocks); 0: one wave of resident blocks
 };
 // Cells per block of a kernel with `per_cell` threads per cell for a target block size.
-__host__ __device__ constexpr int cells_for_target(int per_cell, int target) { return target / per_cell > 0 ? target / per_cell : 1; }
+constexpr int cells_for_target(int per_cell, int target) { return target / per_cell > 0 ? target / per_cell : 1; }
 int hex_default_variant(int n, int nq, int prec);
 // Compiled cells-per-block choices, the default first; return the count (<= 4).
 int hex_point_cb_options(int n, int nq, int* out);
