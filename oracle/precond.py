@@ -77,10 +77,12 @@ def loss_and_grad(r, e, A_apply, cell_node, winv, dinv, W1, b1, W2, rnd=None):
 # ---- linear (tied, symmetric) variant:
 #   M(r) = D^{-1} r + sum_K R_K^T w_K W1^T W1 (w_K R_K r)
 
-def apply_linear(r, cell_node, winv, dinv, W1):
+def apply_linear(r, cell_node, winv, dinv, W1, rnd=None):
+    """M(r) of the linear variant; rnd: operand rounding of Z and H (module docstring)."""
+    rnd = rnd or _keep
     out = dinv * r
-    Z = winv[cell_node] * r[cell_node]
-    O = (Z @ W1.T) @ W1
+    Z = rnd(winv[cell_node] * r[cell_node])
+    O = rnd(Z @ W1.T) @ W1
     np.add.at(out, cell_node, winv[cell_node] * O)
     return out
 

@@ -297,6 +297,76 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_forward_kernel(const MlpArgs 
   }
 }
 
+// The linear mode's forward pass, M(r) = D^{-1} r + sum_K R_K^T w_K W1^T W1 (w_K R_K r): only W1 is needed
+// and z = w R r is not normalised, so the tile is gathered straight into its BF16 operand Zs and the output
+// goes back through the Zs / Hs region.  Three BF16 tiles (105 KB) instead of four tiles and an FP32 one
+// (206 KB): two blocks per SM instead of one, so that one block's gather or scatter overlaps the other's
+// products.  The padding columns of Zs (local dofs >= nloc) are zeroed once; rows past the last cell of a
+// tile hold the previous tile's values and are never scattered.
+__global__ void __launch_bounds__(kThreads, 2) mlp_linear_forward_kernel(const MlpArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  bf16* W1s = reinterpret_cast<bf16*>(smem);
+  bf16* Zs = W1s + kTile * kLd;
+  bf16* Hs = Zs + kTile * kLd;
+  float* F = reinterpret_cast<float*>(Zs);  // [kTile][kK] FP32 output, over Zs and Hs once both are consumed
+  const int nloc = a.nloc;
+  for (int i = threadIdx.x; i < kH * kK; i += kThreads) W1s[(i / kK) * kLd + i % kK] = a.w1[i];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, r0 = warp * 16;
+  const int64_t ntile = (a.ncell + kTile - 1) / kTile;
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int64_t c0 = tile * kTile;
+    const int ncb = (int)(a.ncell - c0 < kTile ? a.ncell - c0 : kTile);
+    const int total = ncb * nloc;
+    for (int i = threadIdx.x; i < kTile * (kK - nloc); i += kThreads)  // padding columns (F overwrote them)
+      Zs[(i / (kK - nloc)) * kLd + nloc + i % (kK - nloc)] = __float2bfloat16_rn(0.0f);
+    const int32_t* cn = a.cell_node + c0 * nloc;
+    for (int i0 = threadIdx.x; i0 < total; i0 += kThreads * kUnr) {  // gather z = w R r
+      int32_t nd[kUnr];
+      float v[kUnr];
+#pragma unroll
+      for (int u = 0; u < kUnr; ++u) nd[u] = i0 + u * kThreads < total ? __ldg(cn + i0 + u * kThreads) : -1;
+#pragma unroll
+      for (int u = 0; u < kUnr; ++u) v[u] = nd[u] < 0 ? 0.0f : __ldg(a.winv + nd[u]) * __ldg(a.r + nd[u]);
+#pragma unroll
+      for (int u = 0; u < kUnr; ++u) {
+        const int i = i0 + u * kThreads;
+        if (nd[u] >= 0) Zs[(i / nloc) * kLd + i % nloc] = __float2bfloat16_rn(v[u]);
+      }
+    }
+    __syncthreads();
+    hidden_layer(Zs, W1s, nullptr, Hs, r0, lane, true);  // H = Z W1^T, this warp's 16 cells
+    float acc[16][4];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.0f;
+    gemm_ay<16>(acc, Hs, r0, W1s, 0, lane);  // O = H W1
+    __syncthreads();  // every warp is done with Zs and Hs
+    const int row = r0 + (lane >> 2), col = (lane & 3) * 2;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      const int n = 8 * t + col;
+      F[row * kK + n] = acc[t][0];
+      F[row * kK + n + 1] = acc[t][1];
+      F[(row + 8) * kK + n] = acc[t][2];
+      F[(row + 8) * kK + n + 1] = acc[t][3];
+    }
+    __syncthreads();
+    for (int i0 = threadIdx.x; i0 < total; i0 += kThreads * kUnr) {  // assemble with the weights w
+      int32_t nd[kUnr];
+      float w[kUnr];
+#pragma unroll
+      for (int u = 0; u < kUnr; ++u) nd[u] = i0 + u * kThreads < total ? __ldg(cn + i0 + u * kThreads) : -1;
+#pragma unroll
+      for (int u = 0; u < kUnr; ++u) w[u] = nd[u] < 0 ? 0.0f : __ldg(a.winv + nd[u]);
+#pragma unroll
+      for (int u = 0; u < kUnr; ++u) {
+        const int i = i0 + u * kThreads;
+        if (nd[u] >= 0) atomicAdd(a.y + nd[u], w[u] * F[(i / nloc) * kK + i % nloc]);
+      }
+    }
+    __syncthreads();  // the next tile's gather rewrites Zs (over F)
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) mlp_backward_kernel(const MlpArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   bf16* W1s = reinterpret_cast<bf16*>(smem);
@@ -488,6 +558,8 @@ uint64_t splitmix(uint64_t z) {
 }
 
 constexpr int kFwdSmem = 4 * kMatBytes + (kTile * kK + kTile + kH) * 4;
+constexpr int kLinSmem = 3 * kMatBytes;
+static_assert(2 * kMatBytes >= kTile * kK * 4, "the FP32 output tile fits over Zs and Hs");
 constexpr int kBwdSmem = 6 * kMatBytes + (kTile + kH) * 4;
 
 }  // namespace
@@ -504,7 +576,7 @@ struct mfa_precond {
   double* scal = nullptr;  // [0] num, [1] den, [2] gscale, [3..] dot result
   double* partial = nullptr;
   int64_t adam_t = 0;
-  int fwd_blocks = 0, bwd_blocks = 0;
+  int fwd_blocks = 0, bwd_blocks = 0, lin_blocks = 0;
   int linear = 0;
 };
 
@@ -539,8 +611,13 @@ int forward(mfa_precond* pc, const float* r, float* z, cudaStream_t s) {
   jacobi32_kernel<<<grid1(pc->ndof), 256, 0, s>>>(pc->dinv, r, z, pc->ndof);
   const int64_t ntile = (pc->ncell + kTile - 1) / kTile;
   if (ntile > 0) {
-    const int64_t grid = ntile < pc->fwd_blocks ? ntile : pc->fwd_blocks;
-    mlp_forward_kernel<<<(unsigned)grid, kThreads, kFwdSmem, s>>>(mlp_args(pc, r, z, nullptr));
+    if (pc->linear) {
+      const int64_t grid = ntile < pc->lin_blocks ? ntile : pc->lin_blocks;
+      mlp_linear_forward_kernel<<<(unsigned)grid, kThreads, kLinSmem, s>>>(mlp_args(pc, r, z, nullptr));
+    } else {
+      const int64_t grid = ntile < pc->fwd_blocks ? ntile : pc->fwd_blocks;
+      mlp_forward_kernel<<<(unsigned)grid, kThreads, kFwdSmem, s>>>(mlp_args(pc, r, z, nullptr));
+    }
   }
   return check(cudaGetLastError(), "mlp forward");
 }
@@ -642,12 +719,17 @@ int mfa_precond_create(mfa_ctx* ctx, mfa_form* form, int mode, uint64_t seed, mf
                       "smem attribute");
   if (!rc) rc = check(cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwdSmem),
                       "smem attribute");
+  if (!rc)
+    rc = check(cudaFuncSetAttribute(mlp_linear_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kLinSmem),
+               "smem attribute");
   if (!rc) {
-    int bf = 1, bb = 1;
+    int bf = 1, bb = 1, bl = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, mlp_forward_kernel, kThreads, kFwdSmem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, mlp_backward_kernel, kThreads, kBwdSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, mlp_linear_forward_kernel, kThreads, kLinSmem);
     pc->fwd_blocks = ctx->sm_count * (bf > 0 ? bf : 1);
     pc->bwd_blocks = ctx->sm_count * (bb > 0 ? bb : 1);
+    pc->lin_blocks = ctx->sm_count * (bl > 0 ? bl : 1);
   }
   if (!rc) rc = check(cudaStreamSynchronize(s), "synchronize");
   cudaFree(diag);

@@ -181,14 +181,16 @@ def test_linear_precond_forward_and_gradient_match_oracle(ctx):
     mfa.mfa_precond_set_weights(pc, mfa.pack_precond_weights(W1, np.zeros(128), np.zeros((nloc, 128))))
     winv = op.multiplicity_weights(case["cell_node"], case["nnode"])
     dinv = 1.0 / np.diag(A)
-    r = fi.uniform_vector(case["nnode"], seed=8)
+    r = f32(fi.uniform_vector(case["nnode"], seed=8))
     W1b = bf16_round(W1)
-    ref = op.apply_linear(r, case["cell_node"], winv, dinv, W1b)
+    ref = op.apply_linear(r, case["cell_node"], f32(winv), f32(dinv), W1b, rnd=bf16_round)
     z = torch.empty(case["nnode"], dtype=torch.float32, device="cuda")
     mfa.mfa_precond_apply(ctx.h, pc, torch.from_numpy(r).float().cuda(), z)
     ctx.sync()
     zg = z.double().cpu().numpy()
-    assert np.linalg.norm(zg - ref) <= 2e-2 * np.linalg.norm(ref - dinv * r)
+    net = ref - f32(dinv) * r
+    err = np.linalg.norm((zg - f32(dinv) * r) - net) / np.linalg.norm(net)
+    assert err <= OPERAND_TOL, err
     e = fi.uniform_vector(case["nnode"], seed=9)
     rr = A @ e
     L, dW1 = op.loss_and_grad_linear(rr, e, lambda v: A @ v, case["cell_node"], winv, dinv, W1b)
@@ -199,6 +201,31 @@ def test_linear_precond_forward_and_gradient_match_oracle(ctx):
     cos = (dW1.ravel() @ gW1.ravel()) / (np.linalg.norm(dW1) * np.linalg.norm(gW1))
     assert cos > 0.999 and np.linalg.norm(gW1 - dW1) <= 5e-2 * np.linalg.norm(dW1)
     assert not gb1.any() and not gW2.any()
+    mfa.mfa_precond_destroy(pc)
+
+
+def test_linear_precond_forward_many_tiles(ctx):
+    """The linear mode's forward kernel on 46,656 cells (365 tiles of 128 cells: more tiles than resident blocks,
+    so blocks walk several, and a ragged last tile) against the oracle at the kernels' operand precision."""
+    case = hex_case(36, 1)
+    m = mfa.Mesh(ctx, 8, case["coords"], case["cell_vert"])
+    sp = mfa.Space(m, 1, 1, case["cell_node"], case["nnode"])
+    f64 = mfa.Form(sp, mfa.MFA_FORM_HELMHOLTZ)
+    pc = mfa.mfa_precond_create(ctx.h, f64.h, 3, mode=mfa.MFA_PRECOND_LINEAR)
+    W1 = (0.3 * np.random.default_rng(5).standard_normal((128, 8))).astype(np.float32)
+    mfa.mfa_precond_set_weights(pc, mfa.pack_precond_weights(W1, np.zeros(128), np.zeros((8, 128))))
+    d = f64.diagonal()
+    ctx.sync()
+    dinv = f32(1.0 / d.cpu().numpy())
+    winv = f32(op.multiplicity_weights(case["cell_node"], case["nnode"]))
+    r = f32(fi.uniform_vector(case["nnode"], seed=12))
+    ref = op.apply_linear(r, case["cell_node"], winv, dinv, bf16_round(W1), rnd=bf16_round)
+    z = torch.empty(case["nnode"], dtype=torch.float32, device="cuda")
+    mfa.mfa_precond_apply(ctx.h, pc, torch.from_numpy(r).float().cuda(), z)
+    ctx.sync()
+    net, got = ref - dinv * r, z.double().cpu().numpy() - dinv * r
+    err = np.linalg.norm(got - net) / np.linalg.norm(net)
+    assert err <= OPERAND_TOL, err
     mfa.mfa_precond_destroy(pc)
 
 
