@@ -26,7 +26,7 @@ def bf16_round(a):
     return t.numpy()
 
 
-def f32(a):
+def to_f32(a):
     return np.asarray(a, dtype=np.float32).astype(np.float64)
 
 
@@ -62,8 +62,8 @@ def test_precond_forward_matches_oracle(ctx, nx, p):
     A = pb.dense() if case["nnode"] <= 4000 else None
     dinv = 1.0 / (np.diag(A) if A is not None else None)
     winv = op.multiplicity_weights(case["cell_node"], case["nnode"])
-    r = f32(fi.uniform_vector(case["nnode"], seed=3))
-    dinv = f32(dinv)
+    r = to_f32(fi.uniform_vector(case["nnode"], seed=3))
+    dinv = to_f32(dinv)
     # the kernels run the MLP on bfloat16 weights and operands
     ref = op.apply(r, case["cell_node"], winv, dinv, bf16_round(W1), b1, bf16_round(W2), rnd=bf16_round)
     rd = torch.from_numpy(r).float().cuda()
@@ -100,9 +100,9 @@ def test_precond_gradient_matches_oracle(ctx):
     A = oracle_problem(case, "helmholtz").dense()
     winv = op.multiplicity_weights(case["cell_node"], case["nnode"])
     dinv = 1.0 / np.diag(A)
-    e = f32(fi.uniform_vector(case["nnode"], seed=6))
-    r = f32(A @ e)
-    L, dW1, db1, dW2 = op.loss_and_grad(r, e, lambda v: A @ v, case["cell_node"], winv, f32(dinv), bf16_round(W1),
+    e = to_f32(fi.uniform_vector(case["nnode"], seed=6))
+    r = to_f32(A @ e)
+    L, dW1, db1, dW2 = op.loss_and_grad(r, e, lambda v: A @ v, case["cell_node"], winv, to_f32(dinv), bf16_round(W1),
                                         b1, bf16_round(W2), rnd=bf16_round)
     loss, g = mfa.mfa_precond_loss_grad(ctx.h, pc, keep[3].h, torch.from_numpy(r).float().cuda(),
                                         torch.from_numpy(e).float().cuda())
@@ -181,15 +181,15 @@ def test_linear_precond_forward_and_gradient_match_oracle(ctx):
     mfa.mfa_precond_set_weights(pc, mfa.pack_precond_weights(W1, np.zeros(128), np.zeros((nloc, 128))))
     winv = op.multiplicity_weights(case["cell_node"], case["nnode"])
     dinv = 1.0 / np.diag(A)
-    r = f32(fi.uniform_vector(case["nnode"], seed=8))
+    r = to_f32(fi.uniform_vector(case["nnode"], seed=8))
     W1b = bf16_round(W1)
-    ref = op.apply_linear(r, case["cell_node"], f32(winv), f32(dinv), W1b, rnd=bf16_round)
+    ref = op.apply_linear(r, case["cell_node"], to_f32(winv), to_f32(dinv), W1b, rnd=bf16_round)
     z = torch.empty(case["nnode"], dtype=torch.float32, device="cuda")
     mfa.mfa_precond_apply(ctx.h, pc, torch.from_numpy(r).float().cuda(), z)
     ctx.sync()
     zg = z.double().cpu().numpy()
-    net = ref - f32(dinv) * r
-    err = np.linalg.norm((zg - f32(dinv) * r) - net) / np.linalg.norm(net)
+    net = ref - to_f32(dinv) * r
+    err = np.linalg.norm((zg - to_f32(dinv) * r) - net) / np.linalg.norm(net)
     assert err <= OPERAND_TOL, err
     e = fi.uniform_vector(case["nnode"], seed=9)
     rr = A @ e
@@ -216,9 +216,9 @@ def test_linear_precond_forward_many_tiles(ctx):
     mfa.mfa_precond_set_weights(pc, mfa.pack_precond_weights(W1, np.zeros(128), np.zeros((8, 128))))
     d = f64.diagonal()
     ctx.sync()
-    dinv = f32(1.0 / d.cpu().numpy())
-    winv = f32(op.multiplicity_weights(case["cell_node"], case["nnode"]))
-    r = f32(fi.uniform_vector(case["nnode"], seed=12))
+    dinv = to_f32(1.0 / d.cpu().numpy())
+    winv = to_f32(op.multiplicity_weights(case["cell_node"], case["nnode"]))
+    r = to_f32(fi.uniform_vector(case["nnode"], seed=12))
     ref = op.apply_linear(r, case["cell_node"], winv, dinv, bf16_round(W1), rnd=bf16_round)
     z = torch.empty(case["nnode"], dtype=torch.float32, device="cuda")
     mfa.mfa_precond_apply(ctx.h, pc, torch.from_numpy(r).float().cuda(), z)
