@@ -426,7 +426,7 @@ MFA_API int mfa_precond_destroy(mfa_precond *pc);
  * learned M of `pc`; otherwise as mfa_fcg_mixed.  With fallback = 1 the
  * Jacobi inner loop of mfa_fcg_mixed takes over (a) for the rest of the solve
  * once the learned one stops reducing the FP64 residual (by less than 10%
- * over 10 outer steps): *used_fallback = 1; (b) from the initial guess if the
+ * over 30 outer steps): *used_fallback = 1; (b) from the initial guess if the
  * solve breaks down or reaches maxit: *used_fallback = 2.  With fallback = 0
  * the learned solver's own status is returned and *used_fallback = 0. */
 MFA_API int mfa_fcg_learned(mfa_ctx *ctx, mfa_form *outer, mfa_form *inner, mfa_precond *pc, int inner_iters,

@@ -214,12 +214,13 @@ int fcg(mfa_ctx* ctx, mfa_form* outer, mfa_form* inner, mfa_precond* pc, int inn
     pq_prev = pq;
     hist.push_back(res);
     // Jacobi fallback inside the solve: a learned inner loop that stops
-    // reducing the FP64 residual (< 10% over 10 outer steps) is replaced by the
-    // Jacobi inner loop for the rest of the solve (flexible CG allows it).  A
-    // shorter window mistook the plateaus of a converging solve for a stall:
-    // with 3 steps and 20% it switched a learned Q4 solve on 64^3 that reaches
-    // 1e-8 in 110 outer steps on its own, which then took 361.
-    if (allow_switch && use_learned && it >= 10 && res > 0.9 * hist[it - 10]) {
+    // reducing the FP64 residual (< 10% over 30 outer steps) is replaced by the
+    // Jacobi inner loop for the rest of the solve (flexible CG allows it).
+    // Shorter windows mistook the plateaus of a converging solve for a stall:
+    // with 3 steps and 20%, and with 10 steps and 10%, they switched a learned
+    // Q4 solve on 64^3 that reaches 1e-8 in 110 outer steps on its own, which
+    // then took 295-361.
+    if (allow_switch && use_learned && it >= 30 && res > 0.9 * hist[it - 30]) {
       use_learned = false;
       if (switched_at) *switched_at = it;
     }
