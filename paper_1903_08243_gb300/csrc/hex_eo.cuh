@@ -31,10 +31,12 @@ namespace hexeo {
 // Split table of one n x n matrix: E [h][h], O [h][h], Mc [h] = S[i][mid],
 // Mr [h+1] = (S[mid][j], j < h; S[mid][mid]).
 __host__ __device__ constexpr int split_size(int n) { return 2 * (n / 2) * (n / 2) + (n / 2) + (n / 2) + 1; }
-// Four matrices per n (0: B, 1: B^T, 2: D, 3: D^T), n = 5..9.
+// Five matrices per n (0: B, 1: B^T, 2: D, 3: D^T, 4: D for the fused z sweep: E, O and Mr doubled, Mc as
+// for D), n = 5..9.
+constexpr int kMats = 5;
 __host__ __device__ constexpr int tab_offset(int n, int mat) {
   int off = 0;
-  for (int k = 5; k < n; ++k) off += 4 * split_size(k);
+  for (int k = 5; k < n; ++k) off += kMats * split_size(k);
   return off + mat * split_size(n);
 }
 constexpr int kTabDoubles = tab_offset(10, 0);
@@ -134,6 +136,130 @@ __device__ __forceinline__ void eo_sweep(const double* in, double* out, int a, i
   }
 }
 
+// B then D along z on the thread's own z-line: vout = B u (values at the Gauss points), dout = D B u.  The
+// even and odd parts of B u along z are 2 pe and 2 po of the B product (and its middle value), so the D
+// product starts from them with the doubled split table (matrix 4) and needs no additions of its own before
+// its products.  `dout` may alias `in`.
+template <int N>
+__device__ __forceinline__ void eo_sweep_bd_z(const double* in, double* vout, double* dout, int a, int b) {
+  constexpr int H = N / 2;
+  constexpr bool ODD = (N & 1) != 0;
+  constexpr int bB = tab_offset(N, 0), bD = tab_offset(N, 4);
+  constexpr int oEB = bB, oOB = bB + H * H, oMcB = bB + 2 * H * H, oMrB = oMcB + H;
+  constexpr int oED = bD, oOD = bD + H * H, oMcD = bD + 2 * H * H, oMrD = oMcD + H;
+  double v[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) v[m] = in[at<N, 2>(a, b, m)];
+  double e[H], o[H], pe[H], po[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    e[j] = v[j] + v[N - 1 - j];
+    o[j] = v[j] - v[N - 1 - j];
+  }
+  double mid = 0.0;
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    double se = 0.0, so = 0.0;
+    if constexpr (ODD) se = c_eo[oMcB + i] * v[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      se = fma(c_eo[oEB + i * H + j], e[j], se);
+      so = fma(c_eo[oOB + i * H + j], o[j], so);
+    }
+    pe[i] = se;
+    po[i] = so;
+    vout[at<N, 2>(a, b, i)] = se + so;
+    vout[at<N, 2>(a, b, N - 1 - i)] = se - so;
+  }
+  if constexpr (ODD) {
+    double sm = c_eo[oMrB + H] * v[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) sm = fma(c_eo[oMrB + j], e[j], sm);
+    mid = sm;
+    vout[at<N, 2>(a, b, H)] = sm;
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {  // D (anti-centrosymmetric): out_i = pe + po, out_{n-1-i} = po - pe
+    double se = 0.0, so = 0.0;
+    if constexpr (ODD) se = c_eo[oMcD + i] * mid;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      se = fma(c_eo[oED + i * H + j], pe[j], se);
+      so = fma(c_eo[oOD + i * H + j], po[j], so);
+    }
+    dout[at<N, 2>(a, b, i)] = se + so;
+    dout[at<N, 2>(a, b, N - 1 - i)] = so - se;
+  }
+  if constexpr (ODD) {  // the middle diagonal of D is zero
+    double sm = 0.0;
+#pragma unroll
+    for (int j = 0; j < H; ++j) sm = fma(c_eo[oMrD + j], po[j], sm);
+    dout[at<N, 2>(a, b, H)] = sm;
+  }
+}
+
+// The test side along z in one pass: out = B^T (acc + D^T f) on the thread's own z-line.  With lo, hi the
+// D^T product's outputs (lo = pe + po, hi = po - pe), the even and odd parts of acc + D^T f are
+// (acc_j + acc_{n-1-j}) + 2 po_j and (acc_j - acc_{n-1-j}) + 2 pe_j: one addition and one FMA each, where
+// adding, recombining and splitting take six operations per pair.  `out` may alias `f`.
+template <int N>
+__device__ __forceinline__ void eo_sweep_dtbt_z(const double* f, const double* acc, double* out, int a, int b) {
+  constexpr int H = N / 2;
+  constexpr bool ODD = (N & 1) != 0;
+  constexpr int bT = tab_offset(N, 3), bB = tab_offset(N, 1);
+  constexpr int oET = bT, oOT = bT + H * H, oMcT = bT + 2 * H * H, oMrT = oMcT + H;
+  constexpr int oEB = bB, oOB = bB + H * H, oMcB = bB + 2 * H * H, oMrB = oMcB + H;
+  double v[N], ac[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) {
+    v[m] = f[at<N, 2>(a, b, m)];
+    ac[m] = acc[at<N, 2>(a, b, m)];
+  }
+  double e[H], o[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    e[j] = v[j] + v[N - 1 - j];
+    o[j] = v[j] - v[N - 1 - j];
+  }
+  double te[H], to[H], tmid = 0.0;  // even and odd parts of t = acc + D^T f
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    double se = 0.0, so = 0.0;
+    if constexpr (ODD) se = c_eo[oMcT + i] * v[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      se = fma(c_eo[oET + i * H + j], e[j], se);
+      so = fma(c_eo[oOT + i * H + j], o[j], so);
+    }
+    te[i] = fma(2.0, so, ac[i] + ac[N - 1 - i]);
+    to[i] = fma(2.0, se, ac[i] - ac[N - 1 - i]);
+  }
+  if constexpr (ODD) {  // middle of D^T f: the middle diagonal of D^T is zero
+    double sm = 0.0;
+#pragma unroll
+    for (int j = 0; j < H; ++j) sm = fma(c_eo[oMrT + j], o[j], sm);
+    tmid = ac[H] + sm;
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {  // B^T (centrosymmetric) on t
+    double se = 0.0, so = 0.0;
+    if constexpr (ODD) se = c_eo[oMcB + i] * tmid;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      se = fma(c_eo[oEB + i * H + j], te[j], se);
+      so = fma(c_eo[oOB + i * H + j], to[j], so);
+    }
+    out[at<N, 2>(a, b, i)] = se + so;
+    out[at<N, 2>(a, b, N - 1 - i)] = se - so;
+  }
+  if constexpr (ODD) {
+    double sm = c_eo[oMrB + H] * tmid;
+#pragma unroll
+    for (int j = 0; j < H; ++j) sm = fma(c_eo[oMrB + j], te[j], sm);
+    out[at<N, 2>(a, b, H)] = sm;
+  }
+}
+
 // Four shared-memory planes of CB x n^3 doubles: U (gathered input, then the z-derivative and its flux, then
 // the B^T results), V (values at the Gauss points, then the test-side accumulation), F0 and F1 (x- and
 // y-derivatives and their fluxes).
@@ -169,18 +295,21 @@ __device__ __forceinline__ void eo_batch(const HexApplyArgs& a, int64_t batch, d
   __syncthreads();
   if (valid) eo_sweep<N, 1, 0, 1, false>(V, U, la, lb);  // B in y
   __syncthreads();
-  if (valid) eo_sweep<N, 2, 0, 1, false>(U, V, la, lb);  // B in z: values at the Gauss points
-  __syncthreads();
   if constexpr (KIND == MFA_FORM_MASS) {
+    if (valid) eo_sweep<N, 2, 0, 1, false>(U, V, la, lb);  // B in z: values at the Gauss points
+    __syncthreads();
     for (int i = t; i < ncb * P; i += T) {
       const int c = i / P, q = i - c * P;
       V0[i] *= __ldg(geom + cell_of(c) * P + q);
     }
+    __syncthreads();
+    if (valid) eo_sweep<N, 2, 1, 1, false>(V, U, la, lb);  // B^T in z
   } else {
+    if (valid) eo_sweep_bd_z<N>(U, V, U, la, lb);  // B in z (values, into V), D in z (into U's plane)
+    __syncthreads();
     if (valid) {
       eo_sweep<N, 0, 2, -1, false>(V, F0, la, lb);  // D in x
       eo_sweep<N, 1, 2, -1, false>(V, F1, la, lb);  // D in y
-      eo_sweep<N, 2, 2, -1, false>(V, U, la, lb);   // D in z, into U's plane
     }
     __syncthreads();
     for (int i = t; i < ncb * P; i += T) {  // pointwise physics, point-parallel
@@ -201,10 +330,8 @@ __device__ __forceinline__ void eo_batch(const HexApplyArgs& a, int64_t batch, d
     __syncthreads();
     if (valid) eo_sweep<N, 1, 3, -1, true>(F1, V, la, lb);  // + D_y^T f1
     __syncthreads();
-    if (valid) eo_sweep<N, 2, 3, -1, true>(U, V, la, lb);   // + D_z^T f2
+    if (valid) eo_sweep_dtbt_z<N>(U, V, U, la, lb);       // B^T in z of (r + D_z^T f2)
   }
-  __syncthreads();
-  if (valid) eo_sweep<N, 2, 1, 1, false>(V, U, la, lb);  // B^T in z
   __syncthreads();
   if (valid) eo_sweep<N, 1, 1, 1, false>(U, V, la, lb);  // B^T in y
   __syncthreads();
@@ -294,20 +421,21 @@ inline cudaError_t upload_tables() {
     lagrange_matrix(n, gll, n, xg, B);  // B[q][a]
     collocation_derivative(n, xg, D);   // D[q][r]
     const int h = n / 2;
-    for (int mat = 0; mat < 4; ++mat) {
+    for (int mat = 0; mat < kMats; ++mat) {
       auto S = [&](int i, int j) {
-        const double* M = mat < 2 ? B : D;
-        return (mat % 2 == 0) ? M[i * n + j] : M[j * n + i];  // odd mat: transpose
+        const double* M = (mat < 2) ? B : D;
+        return (mat == 1 || mat == 3) ? M[j * n + i] : M[i * n + j];  // 1, 3: transposes
       };
+      const double scale = mat == 4 ? 2.0 : 1.0;  // matrix 4: D fed with the halves of an even-odd split
       double* o = tab.data() + tab_offset(n, mat);
       for (int i = 0; i < h; ++i)
         for (int j = 0; j < h; ++j) {
-          o[i * h + j] = 0.5 * (S(i, j) + S(i, n - 1 - j));              // E
-          o[h * h + i * h + j] = 0.5 * (S(i, j) - S(i, n - 1 - j));      // O
+          o[i * h + j] = scale * 0.5 * (S(i, j) + S(i, n - 1 - j));          // E
+          o[h * h + i * h + j] = scale * 0.5 * (S(i, j) - S(i, n - 1 - j));  // O
         }
       if (n & 1) {
-        for (int i = 0; i < h; ++i) o[2 * h * h + i] = S(i, h);          // Mc
-        for (int j = 0; j <= h; ++j) o[2 * h * h + h + j] = S(h, j);     // Mr
+        for (int i = 0; i < h; ++i) o[2 * h * h + i] = S(i, h);            // Mc (the middle value is whole)
+        for (int j = 0; j <= h; ++j) o[2 * h * h + h + j] = scale * S(h, j); // Mr
       }
     }
   }
