@@ -34,7 +34,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # it is reported only while that source is unchanged.  Even-odd kernel (hex_eo.cuh),
 # Q6 Helmholtz: the 32^3 capture (869.22 MB per launch) scaled by the cell count to
 # the 64^3 launch (profiles/eo_apply_q6_helmholtz_hex32.md).
-NCU_TRAFFIC = {("34a9a704426a", "Q6 helmholtz"): 8 * 869.22e6}
+NCU_TRAFFIC = {("84cd050d57a6", "Q6 helmholtz"): 8 * 869.0e6}
 
 
 def parse_args():
@@ -326,6 +326,53 @@ def allreduce_max(world, v):
     t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def host_link_gbs(nbytes=512 << 20, reps=3):
+    """The host link as the end-to-end leg meets it: one pinned host->device copy, one device->host copy, then
+    both at once on two streams, each timed with CUDA events on its own stream (median of `reps`). Context for
+    the e2e figure only: these copies are plain cudaMemcpyAsync calls made by torch, not part of the library."""
+    import torch
+
+    n = nbytes // 8
+    h_in = torch.empty(n, dtype=torch.float64).pin_memory()
+    h_out = torch.empty(n, dtype=torch.float64).pin_memory()
+    d_in = torch.empty(n, dtype=torch.float64, device="cuda")
+    d_out = torch.zeros(n, dtype=torch.float64, device="cuda")
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(which):
+        t = {}
+        ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in which}
+        torch.cuda.synchronize()
+        if "h2d" in which:
+            with torch.cuda.stream(s_in):
+                ev["h2d"][0].record(s_in)
+                d_in.copy_(h_in, non_blocking=True)
+                ev["h2d"][1].record(s_in)
+        if "d2h" in which:
+            with torch.cuda.stream(s_out):
+                ev["d2h"][0].record(s_out)
+                h_out.copy_(d_out, non_blocking=True)
+                ev["d2h"][1].record(s_out)
+        torch.cuda.synchronize()
+        for k in which:
+            t[k] = ev[k][0].elapsed_time(ev[k][1]) / 1e3
+        return t
+
+    timed(("h2d", "d2h"))  # first touch of the pinned pages and the streams
+    alone = {"h2d": [], "d2h": []}
+    both = {"h2d": [], "d2h": []}
+    for _ in range(reps):
+        for k in ("h2d", "d2h"):
+            alone[k].append(timed((k,))[k])
+        t = timed(("h2d", "d2h"))
+        for k in t:
+            both[k].append(t[k])
+    gbs = lambda ts: nbytes / statistics.median(ts) / 1e9  # noqa: E731
+    return {"h2d_gbs": gbs(alone["h2d"]), "d2h_gbs": gbs(alone["d2h"]),
+            "h2d_gbs_concurrent": gbs(both["h2d"]), "d2h_gbs_concurrent": gbs(both["d2h"]),
+            "bytes_per_copy": nbytes, "source": "pinned torch tensors, one cudaMemcpyAsync per direction, CUDA events"}
 
 
 # ------------------------------------------------------------------ CPU oracle (baseline / reference arm)
@@ -639,13 +686,17 @@ def gpu_arm(args, world, rank, local):
         mfa.mfa_apply_host_many(ctx.h, forms_h, hx, hy)  # warm the staging buffers and copy streams
         barrier(world)
         t0 = time.perf_counter()
+        marks = []
         for _ in range(args.e2e_steps):
             mfa.mfa_apply_host_many(ctx.h, forms_h, hx, hy)
+            marks.append(time.perf_counter())
         dt = (time.perf_counter() - t0) / args.e2e_steps
         dt = allreduce_max(world, dt)
+        each = [1e3 * (b - a) for a, b in zip([t0] + marks[:-1], marks)]
         e2e = {"value": world * ndof_step / dt / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * ndof_step,
-               "d2h_bytes_per_step": 8 * ndof_step, "ms_per_step": dt * 1e3,
-               "path": "mfa_apply_host_many: pinned host buffers, copies overlapped with the applies"}
+               "d2h_bytes_per_step": 8 * ndof_step, "ms_per_step": dt * 1e3, "ms_each_step": each,
+               "path": "mfa_apply_host_many: pinned host buffers, copies overlapped with the applies",
+               "host_link": host_link_gbs()}
 
     cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
