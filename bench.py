@@ -34,7 +34,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # it is reported only while that source is unchanged.  Even-odd kernel (hex_eo.cuh),
 # Q6 Helmholtz: the 32^3 capture (869.22 MB per launch) scaled by the cell count to
 # the 64^3 launch (profiles/eo_apply_q6_helmholtz_hex32.md).
-NCU_TRAFFIC = {("84cd050d57a6", "Q6 helmholtz"): 8 * 869.0e6}
+NCU_TRAFFIC = {("7855a4e73280", "Q6 helmholtz"): 8 * 868.7e6}
 
 
 def parse_args():
@@ -83,7 +83,7 @@ def parse_args():
                     help="N > 1: the hex workload shards a box of N nx^3 z-slabs over the ranks (auto), the others "
                          "run a replica per rank")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     return ap.parse_args()
 
 
@@ -683,18 +683,28 @@ def gpu_arm(args, world, rank, local):
         hx = [torch.from_numpy(o["case"]["x"]).pin_memory() for o in ops]
         hy = [torch.empty_like(h).pin_memory() for h in hx]
         forms_h = [o["form"].h for o in ops]
-        mfa.mfa_apply_host_many(ctx.h, forms_h, hx, hy)  # warm the staging buffers and copy streams
+        for _ in range(max(1, args.warmup)):  # warm-up calls, untimed like the device leg's: staging buffers,
+            mfa.mfa_apply_host_many(ctx.h, forms_h, hx, hy)  # copy streams, first touch of the pinned pages
+        # per step also the span on the context stream between events recorded before and after the call (the
+        # call returns once its copies are done): a step whose wall time exceeds its span lost time on the host
+        spans = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(args.e2e_steps)]
         barrier(world)
         t0 = time.perf_counter()
         marks = []
-        for _ in range(args.e2e_steps):
+        for k in range(args.e2e_steps):
+            spans[k][0].record(stream)
             mfa.mfa_apply_host_many(ctx.h, forms_h, hx, hy)
+            spans[k][1].record(stream)
             marks.append(time.perf_counter())
         dt = (time.perf_counter() - t0) / args.e2e_steps
         dt = allreduce_max(world, dt)
+        torch.cuda.synchronize()
         each = [1e3 * (b - a) for a, b in zip([t0] + marks[:-1], marks)]
+        span_each = [a.elapsed_time(b) for a, b in spans]
         e2e = {"value": world * ndof_step / dt / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * ndof_step,
                "d2h_bytes_per_step": 8 * ndof_step, "ms_per_step": dt * 1e3, "ms_each_step": each,
+               "stream_span_ms_each_step": span_each,
                "path": "mfa_apply_host_many: pinned host buffers, copies overlapped with the applies",
                "host_link": host_link_gbs()}
 
@@ -950,15 +960,21 @@ def sharded_hex_arm(args, world, rank, local):
     if args.e2e_steps > 0:
         hx = [torch.from_numpy(o["x"].cpu().numpy()).pin_memory() for o in ops]
         hy = [torch.empty_like(h).pin_memory() for h in hx]
-        barrier(world)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
+
+        def e2e_step():
             for o, xh, yh in zip(ops, hx, hy):
                 o["x"].copy_(xh, non_blocking=True)
                 sharded_step(o, o["dplan"], halo)
                 yh.copy_(o["y"], non_blocking=True)
             torch.cuda.synchronize()
+
+        for _ in range(max(1, args.warmup)):  # untimed, like the device leg's warm-up
+            e2e_step()
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
         dt = allreduce_max(world, (time.perf_counter() - t0) / args.e2e_steps)
         nbytes = 8 * sum(o["x"].numel() for o in ops)
         e2e = {"value": ndof_step / dt / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": nbytes,
@@ -1100,7 +1116,8 @@ def batched_arm(args, world, rank, local):
         hx = [torch.from_numpy(h["x"]).pin_memory() for h in hosts]
         hy = [torch.empty_like(t).pin_memory() for t in hx]
         forms_h = [f.h for f in forms]
-        mfa.mfa_apply_host_many(ctx.h, forms_h, hx, hy)  # warm the staging buffers and copy streams
+        for _ in range(max(1, args.warmup)):  # warm-up calls, untimed like the device leg's: staging buffers,
+            mfa.mfa_apply_host_many(ctx.h, forms_h, hx, hy)  # copy streams, first touch of the pinned pages
         barrier(world)
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
@@ -1109,7 +1126,7 @@ def batched_arm(args, world, rank, local):
         e2e = {"value": world * ndof / dt / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * ndof,
                "d2h_bytes_per_step": 8 * ndof, "ms_per_step": dt * 1e3,
                "path": "mfa_apply_host_many: pinned FP64 host buffers, copies overlapped with the applies (one "
-                       "launch per operator, not the grouped graph)"}
+                       "launch per operator, not the grouped graph)", "host_link": host_link_gbs()}
 
     # CPU baseline and accuracy: the FP64 oracle on the cells touching a few random dofs of every operator, timed
     # (one core), and the GPU result at those dofs compared with it

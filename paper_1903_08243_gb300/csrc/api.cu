@@ -116,9 +116,13 @@ void count_work(mfa_form* f) {
     const double L = (double)n * n, P = (double)n * n * n;
     exec_cell = L * 6.0 * line(1, 0) + P;  // B, B^T and the scatter adds
     // D, D^T, G g; the D product along z, fused with B, takes the halves of B's split and forms no e/o of
-    // its own (2h flops fewer per line); the fused D^T / B^T pair along z does the same flops in fewer
-    // instructions (an addition and an FMA per half, where three additions were)
-    if (kind != MFA_FORM_MASS) exec_cell += L * (3.0 * line(-1, 0) + 3.0 * line(-1, 1) - 2.0 * h) + 15.0 * P;
+    // its own (2h flops fewer per line); the fused D^T / B^T pair along z starts its product chains from the
+    // accumulator's sum and difference with doubled tables (one addition per half, where three additions
+    // were: 4h flops fewer per line, 3h + 1 for odd n, whose middle multiply becomes an FMA and whose middle
+    // addition goes into the chain).  Recombining a mirror pair as one FMA instead of two additions changes
+    // no flop count.
+    if (kind != MFA_FORM_MASS)
+      exec_cell += L * (3.0 * line(-1, 0) + 3.0 * line(-1, 1) - 2.0 * h - (odd ? 3.0 * h + 1.0 : 4.0 * h)) + 15.0 * P;
     if (kind != MFA_FORM_LAPLACE) exec_cell += P;  // c0 w|J| u
   }
   if (sp->mesh->cell_type == MFA_CELL_HEX8 && sp->ncomp == 3) {

@@ -12,8 +12,12 @@
 //   out_i = pe_i + po_i,  out_{n-1-i} = sigma (pe_i - po_i),
 //
 // with E = (S[i][j] + S[i][n-1-j]) / 2, O = (S[i][j] - S[i][n-1-j]) / 2 and
-// sigma = +1 for B, -1 for D.  For n = 5 this is 21 instead of 25 FP64
-// operations per line, for n = 7 37 instead of 49, for n = 9 57 instead of 81.
+// sigma = +1 for B, -1 for D.  The odd products accumulate onto pe_i, which
+// gives out_i without an addition, and the mirror output is then one FMA,
+// sigma (2 pe_i - out_i).  For n = 5 this is 19 instead of 25 FP64
+// instructions per line, for n = 7 34 instead of 49, for n = 9 53 instead of 81.
+// The FP64 pipe retires one warp instruction per SM sub-partition only every
+// few dozen cycles, so instruction count, not dependency depth, sets the time.
 // The sweep order and the pointwise physics are those of hex_kernels.cuh;
 // one thread owns one line per direction, the table entries are
 // compile-time offsets into __constant__ memory (FMA operands), and the
@@ -31,9 +35,9 @@ namespace hexeo {
 // Split table of one n x n matrix: E [h][h], O [h][h], Mc [h] = S[i][mid],
 // Mr [h+1] = (S[mid][j], j < h; S[mid][mid]).
 __host__ __device__ constexpr int split_size(int n) { return 2 * (n / 2) * (n / 2) + (n / 2) + (n / 2) + 1; }
-// Five matrices per n (0: B, 1: B^T, 2: D, 3: D^T, 4: D for the fused z sweep: E, O and Mr doubled, Mc as
-// for D), n = 5..9.
-constexpr int kMats = 5;
+// Six matrices per n, n = 5..9: 0: B, 1: B^T, 2: D, 3: D^T, 4: D for the fused B/D sweep along z (E, O and
+// Mr doubled, Mc as for D), 5: D^T for the fused D^T/B^T sweep along z (E, O and Mc doubled, Mr as for D^T).
+constexpr int kMats = 6;
 __host__ __device__ constexpr int tab_offset(int n, int mat) {
   int off = 0;
   for (int k = 5; k < n; ++k) off += kMats * split_size(k);
@@ -110,15 +114,14 @@ __device__ __forceinline__ void eo_sweep(const double* in, double* out, int a, i
   }
 #pragma unroll
   for (int i = 0; i < H; ++i) {
-    double pe = 0.0, po = 0.0;
+    double pe = 0.0;
     if constexpr (ODD) pe = c_eo[oMc + i] * v[H];
 #pragma unroll
-    for (int j = 0; j < H; ++j) {
-      pe = fma(c_eo[oE + i * H + j], e[j], pe);
-      po = fma(c_eo[oO + i * H + j], o[j], po);
-    }
-    const double lo = pe + po;
-    const double hi = SIGMA > 0 ? pe - po : po - pe;
+    for (int j = 0; j < H; ++j) pe = fma(c_eo[oE + i * H + j], e[j], pe);
+    double lo = pe;  // pe + po
+#pragma unroll
+    for (int j = 0; j < H; ++j) lo = fma(c_eo[oO + i * H + j], o[j], lo);
+    const double hi = SIGMA > 0 ? fma(2.0, pe, -lo) : fma(-2.0, pe, lo);  // sigma (pe - po)
     if constexpr (ACC) {
       out[at<N, DIR>(a, b, i)] += lo;
       out[at<N, DIR>(a, b, N - 1 - i)] += hi;
@@ -179,16 +182,16 @@ __device__ __forceinline__ void eo_sweep_bd_z(const double* in, double* vout, do
     vout[at<N, 2>(a, b, H)] = sm;
   }
 #pragma unroll
-  for (int i = 0; i < H; ++i) {  // D (anti-centrosymmetric): out_i = pe + po, out_{n-1-i} = po - pe
-    double se = 0.0, so = 0.0;
+  for (int i = 0; i < H; ++i) {  // D (anti-centrosymmetric): out_i = se + so, out_{n-1-i} = so - se
+    double se = 0.0;
     if constexpr (ODD) se = c_eo[oMcD + i] * mid;
 #pragma unroll
-    for (int j = 0; j < H; ++j) {
-      se = fma(c_eo[oED + i * H + j], pe[j], se);
-      so = fma(c_eo[oOD + i * H + j], po[j], so);
-    }
-    dout[at<N, 2>(a, b, i)] = se + so;
-    dout[at<N, 2>(a, b, N - 1 - i)] = so - se;
+    for (int j = 0; j < H; ++j) se = fma(c_eo[oED + i * H + j], pe[j], se);
+    double lo = se;
+#pragma unroll
+    for (int j = 0; j < H; ++j) lo = fma(c_eo[oOD + i * H + j], po[j], lo);
+    dout[at<N, 2>(a, b, i)] = lo;
+    dout[at<N, 2>(a, b, N - 1 - i)] = fma(-2.0, se, lo);
   }
   if constexpr (ODD) {  // the middle diagonal of D is zero
     double sm = 0.0;
@@ -200,13 +203,14 @@ __device__ __forceinline__ void eo_sweep_bd_z(const double* in, double* vout, do
 
 // The test side along z in one pass: out = B^T (acc + D^T f) on the thread's own z-line.  With lo, hi the
 // D^T product's outputs (lo = pe + po, hi = po - pe), the even and odd parts of acc + D^T f are
-// (acc_j + acc_{n-1-j}) + 2 po_j and (acc_j - acc_{n-1-j}) + 2 pe_j: one addition and one FMA each, where
-// adding, recombining and splitting take six operations per pair.  `out` may alias `f`.
+// (acc_j + acc_{n-1-j}) + 2 po_j and (acc_j - acc_{n-1-j}) + 2 pe_j.  The D^T table with E, O and Mc
+// doubled (matrix 5) lets each product chain start from the accumulator's sum or difference: one addition
+// per half, where adding, recombining and splitting take six operations per pair.  `out` may alias `f`.
 template <int N>
 __device__ __forceinline__ void eo_sweep_dtbt_z(const double* f, const double* acc, double* out, int a, int b) {
   constexpr int H = N / 2;
   constexpr bool ODD = (N & 1) != 0;
-  constexpr int bT = tab_offset(N, 3), bB = tab_offset(N, 1);
+  constexpr int bT = tab_offset(N, 5), bB = tab_offset(N, 1);
   constexpr int oET = bT, oOT = bT + H * H, oMcT = bT + 2 * H * H, oMrT = oMcT + H;
   constexpr int oEB = bB, oOB = bB + H * H, oMcB = bB + 2 * H * H, oMrB = oMcB + H;
   double v[N], ac[N];
@@ -224,33 +228,33 @@ __device__ __forceinline__ void eo_sweep_dtbt_z(const double* f, const double* a
   double te[H], to[H], tmid = 0.0;  // even and odd parts of t = acc + D^T f
 #pragma unroll
   for (int i = 0; i < H; ++i) {
-    double se = 0.0, so = 0.0;
-    if constexpr (ODD) se = c_eo[oMcT + i] * v[H];
+    double od = ac[i] - ac[N - 1 - i];  // + 2 pe_i
+    if constexpr (ODD) od = fma(c_eo[oMcT + i], v[H], od);
 #pragma unroll
-    for (int j = 0; j < H; ++j) {
-      se = fma(c_eo[oET + i * H + j], e[j], se);
-      so = fma(c_eo[oOT + i * H + j], o[j], so);
-    }
-    te[i] = fma(2.0, so, ac[i] + ac[N - 1 - i]);
-    to[i] = fma(2.0, se, ac[i] - ac[N - 1 - i]);
+    for (int j = 0; j < H; ++j) od = fma(c_eo[oET + i * H + j], e[j], od);
+    double ev = ac[i] + ac[N - 1 - i];  // + 2 po_i
+#pragma unroll
+    for (int j = 0; j < H; ++j) ev = fma(c_eo[oOT + i * H + j], o[j], ev);
+    te[i] = ev;
+    to[i] = od;
   }
   if constexpr (ODD) {  // middle of D^T f: the middle diagonal of D^T is zero
-    double sm = 0.0;
+    double sm = ac[H];
 #pragma unroll
     for (int j = 0; j < H; ++j) sm = fma(c_eo[oMrT + j], o[j], sm);
-    tmid = ac[H] + sm;
+    tmid = sm;
   }
 #pragma unroll
   for (int i = 0; i < H; ++i) {  // B^T (centrosymmetric) on t
-    double se = 0.0, so = 0.0;
+    double se = 0.0;
     if constexpr (ODD) se = c_eo[oMcB + i] * tmid;
 #pragma unroll
-    for (int j = 0; j < H; ++j) {
-      se = fma(c_eo[oEB + i * H + j], te[j], se);
-      so = fma(c_eo[oOB + i * H + j], to[j], so);
-    }
-    out[at<N, 2>(a, b, i)] = se + so;
-    out[at<N, 2>(a, b, N - 1 - i)] = se - so;
+    for (int j = 0; j < H; ++j) se = fma(c_eo[oEB + i * H + j], te[j], se);
+    double lo = se;
+#pragma unroll
+    for (int j = 0; j < H; ++j) lo = fma(c_eo[oOB + i * H + j], to[j], lo);
+    out[at<N, 2>(a, b, i)] = lo;
+    out[at<N, 2>(a, b, N - 1 - i)] = fma(2.0, se, -lo);
   }
   if constexpr (ODD) {
     double sm = c_eo[oMrB + H] * tmid;
@@ -405,7 +409,7 @@ cudaError_t launch(const HexApplyArgs& a, GridBudget budget, cudaStream_t s) {
 std::mutex g_mutex;
 bool g_ready[64] = {false};
 
-// Split tables of B, B^T, D, D^T for n = 5..9 into this unit's constant bank.
+// Split tables of B, B^T, D, D^T and the two doubled variants for n = 5..9 into this unit's constant bank.
 inline cudaError_t upload_tables() {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -424,18 +428,20 @@ inline cudaError_t upload_tables() {
     for (int mat = 0; mat < kMats; ++mat) {
       auto S = [&](int i, int j) {
         const double* M = (mat < 2) ? B : D;
-        return (mat == 1 || mat == 3) ? M[j * n + i] : M[i * n + j];  // 1, 3: transposes
+        return (mat == 1 || mat == 3 || mat == 5) ? M[j * n + i] : M[i * n + j];  // 1, 3, 5: transposes
       };
-      const double scale = mat == 4 ? 2.0 : 1.0;  // matrix 4: D fed with the halves of an even-odd split
+      // matrix 4: D fed with the halves of an even-odd split (its middle input is whole); matrix 5: D^T whose
+      // mirror-pair outputs are wanted doubled (its middle output is not)
+      const double s_eo = mat >= 4 ? 2.0 : 1.0, s_mc = mat == 5 ? 2.0 : 1.0, s_mr = mat == 4 ? 2.0 : 1.0;
       double* o = tab.data() + tab_offset(n, mat);
       for (int i = 0; i < h; ++i)
         for (int j = 0; j < h; ++j) {
-          o[i * h + j] = scale * 0.5 * (S(i, j) + S(i, n - 1 - j));          // E
-          o[h * h + i * h + j] = scale * 0.5 * (S(i, j) - S(i, n - 1 - j));  // O
+          o[i * h + j] = s_eo * 0.5 * (S(i, j) + S(i, n - 1 - j));          // E
+          o[h * h + i * h + j] = s_eo * 0.5 * (S(i, j) - S(i, n - 1 - j));  // O
         }
       if (n & 1) {
-        for (int i = 0; i < h; ++i) o[2 * h * h + i] = S(i, h);            // Mc (the middle value is whole)
-        for (int j = 0; j <= h; ++j) o[2 * h * h + h + j] = scale * S(h, j); // Mr
+        for (int i = 0; i < h; ++i) o[2 * h * h + i] = s_mc * S(i, h);      // Mc
+        for (int j = 0; j <= h; ++j) o[2 * h * h + h + j] = s_mr * S(h, j); // Mr
       }
     }
   }

@@ -126,8 +126,9 @@ int hex_eo_cells_per_block(int n);
 // instructions (n = 5..9) but, with n^2 threads per cell, keeps the FP64 pipe
 // busy ~80% of the time against ~93% for the point kernel; measured on GB300
 // it wins from n = 7 (Q6: 14.15 vs 14.86 ms) and loses at n = 5, 6.
-// FP64 hex with p+1 points: the even-odd kernel from Q5 up (the autotuner picks it there on 64^3).
-inline bool hex_use_eo(int n, int nq, int prec) { return prec == MFA_PREC_FP64 && nq == n && n >= 6 && n <= 9; }
+// FP64 hex with p+1 points: the even-odd kernel from Q4 up (the autotuner picks it there on 64^3: 11% ahead of
+// the point kernel at Q4).
+inline bool hex_use_eo(int n, int nq, int prec) { return prec == MFA_PREC_FP64 && nq == n && n >= 5 && n <= 9; }
 
 // ---------------------------------------------------------------- launch configurations
 // Kernel variant (MFA_VARIANT_*) and cells per block of one apply; cb = 0 is
