@@ -982,9 +982,10 @@ int mfa_form_create(mfa_ctx* ctx, mfa_space* sp, const mfa_form_params* prm, mfa
     } else if (!rc) {
       const int ng = mfa::hex_geom_entries(kind);
       const size_t esz = prm->precision == MFA_PREC_FP64 ? 8 : (prm->precision == MFA_PREC_FP32 ? 4 : 2);
-      // FP32/BF16 blocks are padded to 16 bytes per cell: the kernel moves them with bulk copies
+      // FP32/BF16 blocks (line kernels) are padded to 16 bytes per cell, for the bulk copies, and further to
+      // spread the kernels' factor reads over the shared-memory banks; their points run with x slowest
       f->gstride = (int64_t)ng * f->nq;
-      if (prm->precision != MFA_PREC_FP64) f->gstride = (f->gstride * (int64_t)esz + 15) / 16 * 16 / (int64_t)esz;
+      if (prm->precision != MFA_PREC_FP64) f->gstride = mfa::line_geom_stride(f->nq1, ng, (int)esz);
       rc = cuda_alloc((void**)&f->d_geom, esz * f->gstride * sp->mesh->ncell, "geometric factors");
       const double c0 = kind == MFA_FORM_HELMHOLTZ ? prm->k2 : 1.0;
       if (!rc) {

@@ -87,6 +87,9 @@ int build(mfa_ctx* ctx, int n, mfa_form* const* forms, const double* const* xs, 
     std::vector<int64_t> first{0};
     for (int k : members) {
       mfa_form* f = forms[k];
+      if (g.prec != MFA_PREC_FP64 &&
+          f->gstride > mfa::line_geom_stride_max(g.n, mfa::hex_geom_entries(g.kind), g.prec == MFA_PREC_BF16 ? 2 : 4))
+        return mfa::set_error(MFA_ERR_UNSUPPORTED, "mfa_batch: factor block larger than the line kernels' stage");
       mfa::HexApplyArgs a{xs[k], ys[k], f->space->d_cell_node, f->d_geom,     nullptr,
                           f->space->mesh->ncell, ctx->d_err, f->gstride};
       items.push_back(a);

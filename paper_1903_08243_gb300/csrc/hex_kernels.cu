@@ -1,5 +1,7 @@
 // Hexahedral kernels: geometry precompute and dispatch of the sum-factorised
 // action (see hex_kernels.cuh for the algorithm).
+#include <type_traits>
+
 #include "hex_kernels.cuh"
 
 namespace mfa {
@@ -10,10 +12,7 @@ int hex_cells_per_block(int n, int nq) {
   return p <= 128 ? 256 / p : 1;  // hexk::Shape<N, NQ>::CB
 }
 
-int hex_line_cells_per_block(int n) {
-  const int l = n * n;
-  return 256 / l > 0 ? 256 / l : 1;  // hexl::LShape<N>::CB
-}
+int hex_line_cells_per_block(int n) { return line_cb_for(n, 256); }  // hexl::LShape<N>::CB
 
 int hex_geom_entries(int kind) {
   if (kind >= MFA_FORM_ELASTICITY) return 10;  // J^{-1} (row-major) and w|det J|
@@ -25,7 +24,8 @@ namespace {
 // Per Gauss point of a trilinear cell: J = sum_v X_v (grad_ref N_v)^T, then
 // G = w|det J| J^{-1} J^{-T} (6 entries) and c0 w|det J| (Sections 2.1 and
 // 4.1: the Jacobian of a bilinear/trilinear map is evaluated at every
-// quadrature point).  Computed once in FP64 and stored [cell][entry][q].
+// quadrature point).  Computed once in FP64 and stored [cell][entry][q], the
+// points x fastest for FP64 and x slowest for FP32/BF16 (the line kernels).
 template <typename TG>
 __device__ __forceinline__ void store_geo(TG* p, double v);
 template <>
@@ -46,6 +46,8 @@ __global__ void hex_geometry_kernel(const __grid_constant__ HexTables tb, int nq
     const int64_t cell = gid / pq;
     const int q = (int)(gid - cell * pq);
     const int qi = q % nq1, qj = (q / nq1) % nq1, qk = q / (nq1 * nq1);
+    // FP32/BF16 blocks feed the line kernels, whose pointwise step runs on x-lines: x is their slowest index
+    const int qw = std::is_same<TG, double>::value ? q : qj + nq1 * (qk + nq1 * qi);
     const double xi[3] = {tb.x1[qi], tb.x1[qj], tb.x1[qk]};
     const double w = tb.w1[qi] * tb.w1[qj] * tb.w1[qk];
     double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
@@ -69,7 +71,7 @@ __global__ void hex_geometry_kernel(const __grid_constant__ HexTables tb, int nq
     const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
     if (!(det != 0.0) || !isfinite(det)) {
       atomicOr(err, 1);
-      for (int e = 0; e < ng; ++e) store_geo(geom + cell * stride + e * pq + q, 0.0);
+      for (int e = 0; e < ng; ++e) store_geo(geom + cell * stride + e * pq + qw, 0.0);
       continue;
     }
     // inverse by the adjugate: Ji[i][j] = cof[j][i] / det
@@ -84,7 +86,7 @@ __global__ void hex_geometry_kernel(const __grid_constant__ HexTables tb, int nq
     Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
     Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
     const double wdet = w * fabs(det);
-    TG* out = geom + cell * stride + q;
+    TG* out = geom + cell * stride + qw;
     if (ng == 1) {
       store_geo(out, c0 * wdet);
       continue;

@@ -47,22 +47,21 @@ static __constant__ float c_tab[2][kTabFloats];  // [0]: FP32 tables, [1]: table
 
 constexpr int ceil32(int x) { return (x + 31) / 32 * 32; }
 
-// Cells per block for a target block size (the default targets 256 threads).
-constexpr int line_cb_for(int n, int target) { return cells_for_target(n * n, target); }
-
 // Shared-memory layout of one plane: point (x, y, z) of the batch's cell c at
 // c SC + x + SX y + SY z.  Unpadded for most n.  For n = 4 and n = 8 the lines
 // of a warp would otherwise fall on the same banks (4-way and 8-way conflicts
 // in the x sweeps, 4-way in the y sweeps: strides of 4 or 8 words with the
 // default block sizes); the padded strides bring every sweep to 1.3-way on
-// average, at 25% (n = 4) and 12.5% (n = 8) more shared memory.  For n = 6, 7
-// padding removes fewer conflicts from the sweeps than it adds to the
-// point-parallel phases, so those stay unpadded.
+// average, at 25% (n = 4) and 12.5% (n = 8) more shared memory.  For n = 7 the
+// unpadded y sweeps are 3-way (a z-plane of 49 words starts 17 banks on); with
+// a warp taking four whole rows of 7 lines (line_lanes) and z-planes of 56 words,
+// cells of 392, the x and y sweeps are free of conflicts and the z sweeps
+// conflict only where a warp spans two cells (14% more shared memory).
 template <int N>
 struct LLayout {
   static constexpr int SX = N == 8 ? 9 : N;
-  static constexpr int SY = N == 4 ? 19 : (N == 8 ? 72 : N * N);
-  static constexpr int SC = N == 4 ? 80 : (N == 8 ? 576 : N * N * N);
+  static constexpr int SY = N == 4 ? 19 : (N == 8 ? 72 : (N == 7 ? 56 : N * N));
+  static constexpr int SC = N == 4 ? 80 : (N == 8 ? 576 : (N == 7 ? 392 : N * N * N));
   static constexpr bool PADDED = SC != N * N * N;
   // plane offset of point i of the batch (cell i / n^3, local point i % n^3, x fastest)
   __host__ __device__ static constexpr int of(int i) {
@@ -78,7 +77,8 @@ struct LShape {
   static constexpr int P = N * N * N;     // points per cell
   static constexpr int PS = LLayout<N>::SC;  // floats per cell in a plane
   static constexpr int CB = CBX > 0 ? CBX : line_cb_for(N, 256);
-  static constexpr int T = ceil32(CB * L);
+  static constexpr int LANES = line_lanes(N);  // lanes of a warp that carry lines in the sweeps
+  static constexpr int T = 32 * ((CB * L + LANES - 1) / LANES);
   static constexpr int SMEM = 4 * CB * PS * 4;  // planes U, V, F0, F1 (see line_batch)
   static constexpr int K = (CB * P + T - 1) / T;  // points per thread in the point-parallel phases
 };
@@ -96,11 +96,6 @@ __device__ __forceinline__ void line_load_nodes(const int32_t* cell_node, int64_
     const int i = threadIdx.x + k * S::T;
     node[k] = i < ncb * S::P ? __ldg(cell_node + c0 * S::P + i) : -1;
   }
-}
-
-// Elements per cell of the padded factor block (16-byte multiple).
-__host__ __device__ constexpr int64_t geom_stride(int ng, int p, int esz) {
-  return ((int64_t)ng * p * esz + 15) / 16 * 16 / esz;
 }
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -171,30 +166,29 @@ __device__ __forceinline__ void sweep(const float* in, float* out, int a, int b)
   }
 }
 
-// B along z, then D along z on the values just formed (the same line, kept in
-// registers): vout = B_z u, dout = D_z B_z u.  One shared-memory read fewer
-// per point than two separate sweeps.  `dout` may alias `in` (the thread's
-// own line is read before it is written).
+// B along x, then D along x on the values just formed, for the thread's x-line
+// (kept in registers in between): vout = B_x u, dout = D_x B_x u.  `dout` may
+// alias `in` (the thread's own line is read before it is written).
 template <int N, int variant>
-__device__ __forceinline__ void sweep_bd_z(const float* in, float* vout, float* dout, int a, int b) {
+__device__ __forceinline__ void sweep_bd_x(const float* in, float* vout, float* dout, int a, int b) {
   constexpr int offB = tab_offset(N), offD = tab_offset(N) + N * N;
-  float v[N], w[N];
+  float v[N], vx[N];
 #pragma unroll
-  for (int m = 0; m < N; ++m) v[m] = in[at<N, 2>(a, b, m)];
+  for (int m = 0; m < N; ++m) v[m] = in[at<N, 0>(a, b, m)];
 #pragma unroll
   for (int r = 0; r < N; ++r) {
     float s = 0.0f;
 #pragma unroll
     for (int m = 0; m < N; ++m) s = fmaf(c_tab[variant][offB + r * N + m], v[m], s);
-    w[r] = s;
-    vout[at<N, 2>(a, b, r)] = s;
+    vx[r] = s;
+    vout[at<N, 0>(a, b, r)] = s;
   }
 #pragma unroll
   for (int r = 0; r < N; ++r) {
     float s = 0.0f;
 #pragma unroll
-    for (int m = 0; m < N; ++m) s = fmaf(c_tab[variant][offD + r * N + m], w[m], s);
-    dout[at<N, 2>(a, b, r)] = s;
+    for (int m = 0; m < N; ++m) s = fmaf(c_tab[variant][offD + r * N + m], vx[m], s);
+    dout[at<N, 0>(a, b, r)] = s;
   }
 }
 
@@ -247,11 +241,11 @@ struct LineArgs {
   int* err;
 };
 
-// One batch of CB consecutive cells.  Contractions run line-parallel (a
-// thread owns one line per direction); the phases that touch global memory
-// (gather, geometric factors, scatter) run point-parallel over the whole
-// batch, so consecutive threads read consecutive map, factor and output
-// addresses.
+// Factor blocks: per cell, `gstride` elements holding NG entries of n^3
+// points each, the points ordered with x slowest (point (x, y, z) at
+// y + n z + n^2 x).  The pointwise step runs on x-lines, so at each point of
+// the line the batch's threads read consecutive elements (one bank each from
+// the shared stage, coalesced from global memory).
 template <int PREC>
 using GeoT = typename std::conditional<PREC == MFA_PREC_BF16, __nv_bfloat16, float>::type;
 
@@ -261,6 +255,68 @@ __device__ __forceinline__ float geo_at(const void* p, int64_t i) {
   if constexpr (PREC == MFA_PREC_BF16) return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
   else if constexpr (SHARED) return static_cast<const float*>(p)[i];
   else return __ldg(static_cast<const float*>(p) + i);  // read-only path: global memory only
+}
+
+// The pointwise step on the thread's x-line, fused with D_x^T.  V and D0 hold
+// the values and the x-derivative at the line's points (sweep_bd_x); F1 and F0
+// hold the y- and z-derivatives there.  Per point, the fluxes
+// f = G (d0, d1, d2) and the value term c0 w|J| u (Helmholtz); f1 and f2 go
+// back to F1 and F0 for the transposed y and z sweeps, f0 stays in registers,
+// and V receives r = c0 w|J| u + D_x^T f0.  `gs` is the batch's factor block
+// (stage or global memory), `gc` the offset of the thread's cell in it.
+template <int N, int KIND, int PREC, bool STG, int variant>
+__device__ __forceinline__ void fused_x(const void* gs, int64_t gc, float* F0, float* F1, float* V, const float* D0,
+                                        int a, int b) {
+  constexpr int L = N * N, P = N * N * N, offD = tab_offset(N) + N * N;
+  constexpr int NG = KIND == MFA_FORM_HELMHOLTZ ? 7 : 6;
+  const int l = a + N * b;
+  float f0[N], r0[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) {
+    const int j = at<N, 0>(a, b, m);
+    const int64_t gi = gc + l + L * m;
+    float g[NG];
+#pragma unroll
+    for (int e = 0; e < NG; ++e) g[e] = geo_at<PREC, STG>(gs, gi + (int64_t)e * P);
+    const float d0 = D0[j], d1 = F1[j], d2 = F0[j];
+    f0[m] = fmaf(g[0], d0, fmaf(g[3], d1, g[4] * d2));
+    F1[j] = fmaf(g[3], d0, fmaf(g[1], d1, g[5] * d2));
+    F0[j] = fmaf(g[4], d0, fmaf(g[5], d1, g[2] * d2));
+    if constexpr (KIND == MFA_FORM_HELMHOLTZ) r0[m] = g[NG - 1] * V[j];
+    else r0[m] = 0.0f;
+  }
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    float s = r0[r];
+#pragma unroll
+    for (int m = 0; m < N; ++m) s = fmaf(c_tab[variant][offD + m * N + r], f0[m], s);
+    V[at<N, 0>(a, b, r)] = s;
+  }
+}
+
+// Mass: B along x, the weight w|J| at each point of the line, and B^T along x
+// in one pass over the thread's x-line (in registers).
+template <int N, int PREC, bool STG, int variant>
+__device__ __forceinline__ void fused_x_mass(const float* in, float* out, const void* gs, int64_t gc, int a, int b) {
+  constexpr int L = N * N, offB = tab_offset(N);
+  const int l = a + N * b;
+  float v[N], u[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) v[m] = in[at<N, 0>(a, b, m)];
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    float s = 0.0f;
+#pragma unroll
+    for (int m = 0; m < N; ++m) s = fmaf(c_tab[variant][offB + r * N + m], v[m], s);
+    u[r] = s * geo_at<PREC, STG>(gs, gc + l + L * r);
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    float s = 0.0f;
+#pragma unroll
+    for (int r = 0; r < N; ++r) s = fmaf(c_tab[variant][offB + r * N + k], u[r], s);
+    out[at<N, 0>(a, b, k)] = s;
+  }
 }
 
 // Shared staging of one batch's factors, and the barrier state.
@@ -298,56 +354,65 @@ __device__ __forceinline__ void line_load_x(const void* xp, const int32_t (&node
 }
 
 // One batch of CB consecutive cells.  Contractions run line-parallel (a
-// thread owns one line per direction); the phases that touch global memory
-// (gather, scatter) run point-parallel over the whole batch, so consecutive
-// threads read consecutive map and output addresses; the factors come from
-// the bulk-copied stage.  `next` >= 0: batch (of `an`) to prefetch afterwards.
-// `xin` holds x at this thread's points of this batch (requested during the
-// previous batch); once the forward sweeps are done, the next batch's values
-// are requested into it through `node_next`, so that they arrive while this
-// batch finishes and the gather never waits on global memory.
+// thread owns one line per direction; warps carry line_lanes(n) lines); the
+// gather and the scatter run point-parallel over the whole batch, so
+// consecutive threads read consecutive map and output addresses.  The sweep
+// order ends the forward pass along x: B_z, B_y, then B_x and D_x on the
+// thread's x-line in one pass, D_y and D_z from the values; the
+// pointwise step and D_x^T run on the same x-line (fused_x), then D_y^T,
+// D_z^T with B_z^T (sweep_dtbt_z), B_y^T and B_x^T.  The factors come from the
+// bulk-copied stage (STG) or straight from global memory.  `next` >= 0: batch
+// (of `an`) to prefetch afterwards.  `xin` holds x at this thread's points of
+// this batch (requested during the previous batch); once the forward sweeps
+// are done, the next batch's values are requested into it through
+// `node_next`, so that they arrive while this batch finishes and the gather
+// never waits on global memory.
 template <int N, int KIND, int PREC, typename TX, bool STG = staged<PREC>(), int CBX = 0>
 __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, float* smem, Stage& st,
                                            const LineArgs* an, int64_t next, const int32_t (&node)[LShape<N, CBX>::K],
                                            const int32_t (&node_next)[LShape<N, CBX>::K],
                                            float (&xin)[LShape<N, CBX>::K]) {
   using S = LShape<N, CBX>;
-  constexpr int L = S::L, P = S::P, CB = S::CB, T = S::T, K = S::K, NG = geom_entries<KIND>();
+  constexpr int L = S::L, CB = S::CB, T = S::T, K = S::K;
   constexpr int variant = PREC == MFA_PREC_BF16 ? 1 : 0;
   const int t = threadIdx.x;
-  const int cl = t / L, l = t - cl * L;
+  const int lane = t & 31;
+  const int line = (t >> 5) * S::LANES + lane;  // the batch's lines, cell by cell
+  const int cl = line / L, l = line - cl * L;
   const int la = l % N, lb = l / N;
   const int64_t c0 = batch * CB;
   const int ncb = (int)(a.count - c0 < CB ? a.count - c0 : CB);  // cells in this batch
-  const bool valid = cl < ncb;
+  const bool valid = lane < S::LANES && cl < ncb;
   constexpr int PS = S::PS;
   using Y = LLayout<N>;
-  // Four planes of CB cells (PS floats each, layout LLayout): U (gathered input, then the z-derivative and
-  // its flux, then the B^T results), V (values at the Gauss points, then the test-side accumulation), F0 and
-  // F1 (x- and y-derivatives and their fluxes).
+  // Four planes of CB cells (PS floats each, layout LLayout): U (gathered input, then B_y's output, then the
+  // x-derivative, then the B^T results), V (values at the Gauss points, then the test-side accumulation), F0 and F1 (z- and
+  // y-derivatives and their fluxes).  A thread without a line of this batch works on no plane.
   float* U0 = smem;
-  float* U = U0 + cl * PS;
-  float* V = U + CB * PS;
-  float* F0 = V + CB * PS;
-  float* F1 = F0 + CB * PS;
+  float* V0 = U0 + CB * PS;
+  float* F00 = V0 + CB * PS;
+  float* F10 = F00 + CB * PS;
+  const int cp = valid ? cl : 0;
+  float* U = U0 + cp * PS;
+  float* V = V0 + cp * PS;
+  float* F0 = F00 + cp * PS;
+  float* F1 = F10 + cp * PS;
 
   // gather, point-parallel: point i of the batch is local point i % P of cell c0 + i / P
 #pragma unroll
   for (int k = 0; k < K; ++k)
     if (node[k] >= 0) U0[Y::of(t + k * T)] = xin[k];
   __syncthreads();
-  if (valid) sweep<N, 0, 0, false, false, variant>(U, V, la, lb);  // B in x
+  if (valid) sweep<N, 2, 0, false, false, variant>(U, V, la, lb);  // B in z
   __syncthreads();
   if (valid) sweep<N, 1, 0, false, false, variant>(V, U, la, lb);  // B in y
   __syncthreads();
-  if constexpr (KIND == MFA_FORM_MASS) {
-    if (valid) sweep<N, 2, 0, false, false, variant>(U, V, la, lb);  // B in z: values at the Gauss points
-  } else {
-    if (valid) sweep_bd_z<N, variant>(U, V, U, la, lb);  // B in z (values, into V), D in z (into U's plane)
+  if constexpr (KIND != MFA_FORM_MASS) {
+    if (valid) sweep_bd_x<N, variant>(U, V, U, la, lb);  // B in x (values, into V), D in x (into U's plane)
     __syncthreads();
     if (valid) {
-      sweep<N, 0, 1, false, false, variant>(V, F0, la, lb);  // D in x
       sweep<N, 1, 1, false, false, variant>(V, F1, la, lb);  // D in y
+      sweep<N, 2, 1, false, false, variant>(V, F0, la, lb);  // D in z
     }
   }
   // the next batch's x: its nodes were requested at the start of this batch and have arrived by now
@@ -364,63 +429,50 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
   if constexpr (STG) {
     if (*st.abort) return false;
   }
-  float* V0 = U0 + CB * PS;
   const void* gs = STG ? static_cast<const void*>(st.buf)
-                                  : static_cast<const void*>(static_cast<const GeoT<PREC>*>(a.geom) + c0 * a.gstride);
-  const int64_t gsd = a.gstride;
+                       : static_cast<const void*>(static_cast<const GeoT<PREC>*>(a.geom) + c0 * a.gstride);
+  const int64_t gc = (int64_t)cp * a.gstride;
   if constexpr (KIND == MFA_FORM_MASS) {
-    for (int i = t; i < ncb * P; i += T) {
-      const int c = i / P, q = i - c * P, j = Y::of(i);
-      V0[j] *= geo_at<PREC, STG>(gs, c * gsd + q);
-    }
+    if (valid) fused_x_mass<N, PREC, STG, variant>(U, V, gs, gc, la, lb);  // B_x, w|J|, B_x^T: into V
   } else {
-    float* G0 = V0 + CB * PS;
-    float* G1 = G0 + CB * PS;
-    for (int i = t; i < ncb * P; i += T) {
-      const int c = i / P, q = i - c * P, j = Y::of(i);
-      const int64_t gb = c * gsd + q;
-      float g[NG];
-#pragma unroll
-      for (int e = 0; e < NG; ++e) g[e] = geo_at<PREC, STG>(gs, gb + (int64_t)e * P);
-      const float d0 = G0[j], d1 = G1[j], d2 = U0[j];
-      G0[j] = fmaf(g[0], d0, fmaf(g[3], d1, g[4] * d2));
-      G1[j] = fmaf(g[3], d0, fmaf(g[1], d1, g[5] * d2));
-      U0[j] = fmaf(g[4], d0, fmaf(g[5], d1, g[2] * d2));
-      if constexpr (KIND == MFA_FORM_HELMHOLTZ) V0[j] *= g[6];
-      else V0[j] = 0.0f;
-    }
+    if (valid) fused_x<N, KIND, PREC, STG, variant>(gs, gc, F0, F1, V, U, la, lb);  // r = c0 w|J| u + D_x^T f0
   }
   __syncthreads();
   // the stage is free: start the next batch's factors now
   if (t == 0 && next >= 0) issue_factors<N, KIND, PREC, STG, CBX>(*an, next, st);
+  float* R0;  // plane of the result
   if constexpr (KIND != MFA_FORM_MASS) {
-    if (valid) sweep<N, 0, 1, true, true, variant>(F0, V, la, lb);  // r = c0 w|J| u + D_x^T f0
-    __syncthreads();
     if (valid) sweep<N, 1, 1, true, true, variant>(F1, V, la, lb);  // + D_y^T f1
     __syncthreads();
-    if (valid) sweep_dtbt_z<N, variant>(U, V, U, la, lb);           // B^T in z of (r + D_z^T f2)
+    if (valid) sweep_dtbt_z<N, variant>(F0, V, U, la, lb);          // B^T in z of (r + D_z^T f2)
+    __syncthreads();
+    if (valid) sweep<N, 1, 0, true, false, variant>(U, V, la, lb);  // B^T in y
+    __syncthreads();
+    if (valid) sweep<N, 0, 0, true, false, variant>(V, U, la, lb);  // B^T in x
+    R0 = U0;
   } else {
-    if (valid) sweep<N, 2, 0, true, false, variant>(V, U, la, lb);  // B^T in z
+    if (valid) sweep<N, 1, 0, true, false, variant>(V, U, la, lb);  // B^T in y
+    __syncthreads();
+    if (valid) sweep<N, 2, 0, true, false, variant>(U, V, la, lb);  // B^T in z
+    R0 = V0;
   }
-  __syncthreads();
-  if (valid) sweep<N, 1, 0, true, false, variant>(U, V, la, lb);  // B^T in y
-  __syncthreads();
-  if (valid) sweep<N, 0, 0, true, false, variant>(V, U, la, lb);  // B^T in x
   __syncthreads();
   // scatter-add, point-parallel
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     if (node[k] < 0) continue;
-    if constexpr (sizeof(TX) == 8) add_y(static_cast<double*>(a.y), node[k], U0[Y::of(t + k * T)]);
-    else add_y(static_cast<float*>(a.y), node[k], U0[Y::of(t + k * T)]);
+    if constexpr (sizeof(TX) == 8) add_y(static_cast<double*>(a.y), node[k], R0[Y::of(t + k * T)]);
+    else add_y(static_cast<float*>(a.y), node[k], R0[Y::of(t + k * T)]);
   }
   __syncthreads();
   return true;
 }
 
+// The stage holds CB factor blocks of the largest stride line_geom_stride may choose (the launchers refuse a
+// larger one).
 template <int N, int PREC, int CBX = 0>
 __host__ __device__ constexpr int stage_bytes(int ng) {
-  return LShape<N, CBX>::CB * (int)geom_stride(ng, LShape<N, CBX>::P, PREC == MFA_PREC_BF16 ? 2 : 4) *
+  return LShape<N, CBX>::CB * (int)line_geom_stride_max(N, ng, PREC == MFA_PREC_BF16 ? 2 : 4) *
          (PREC == MFA_PREC_BF16 ? 2 : 4);
 }
 
@@ -472,8 +524,9 @@ __global__ void __launch_bounds__(LShape<N, CBX>::T) line_apply_kernel(const Lin
   }
 }
 
-// The grouped launches have no tuner: FP32 groups read their factors straight from global memory, which the
-// 64-operator batch measured faster (11.8 against 12.8 ms per step); BF16 groups stage them.
+// The grouped launches have no tuner: FP32 groups read their factors straight from global memory (coalesced on
+// x-lines; the 64-operator batch measured that faster than staging, whose FP32 blocks cost occupancy); BF16
+// groups stage them.
 template <int PREC>
 __host__ __device__ constexpr bool group_staged() {
   return PREC == MFA_PREC_BF16;
@@ -532,6 +585,9 @@ cudaError_t launch_line(const LineArgs& a, GridBudget budget, cudaStream_t s) {
   using S = LShape<N, CBX>;
   constexpr int smem = line_smem<N, KIND, PREC, STG, CBX>();
   auto kern = line_apply_kernel<N, KIND, PREC, TX, STG, CBX>;
+  if (a.gstride < (int64_t)(N * N * N) * geom_entries<KIND>() ||
+      a.gstride > line_geom_stride_max(N, geom_entries<KIND>(), PREC == MFA_PREC_BF16 ? 2 : 4))
+    return cudaErrorInvalidValue;
   static int bps = -1;
   if (bps < 0) bps = occupancy(kern, S::T, smem);
   const int64_t nbatch = (a.count + S::CB - 1) / S::CB;

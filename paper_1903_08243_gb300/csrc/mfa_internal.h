@@ -143,6 +143,25 @@ struct LaunchConfig {
 };
 // Cells per block of a kernel with `per_cell` threads per cell for a target block size.
 constexpr int cells_for_target(int per_cell, int target) { return target / per_cell > 0 ? target / per_cell : 1; }
+// Line kernels (FP32/BF16 hex): lanes of a warp that carry lines in the sweeps.  For n = 7 a warp takes four
+// whole rows of 7 lines (28 lanes): with the padded plane layout that makes the sweeps in all three directions
+// free of bank conflicts.  Other n use all 32 lanes on consecutive lines.
+__host__ __device__ constexpr int line_lanes(int n) { return n == 7 ? 28 : 32; }
+// Cells per block of the line kernels for a target block size (a multiple of 32 threads).
+__host__ __device__ constexpr int line_cb_for(int n, int target) {
+  return (target / 32) * line_lanes(n) / (n * n) > 0 ? (target / 32) * line_lanes(n) / (n * n) : 1;
+}
+// Elements per cell of an FP32/BF16 factor block (ng entries of n^3 points, x the slowest point index): the
+// smallest multiple of 16 bytes (line_geom_stride_base), plus up to kLineGeomPadMax further 16-byte units,
+// chosen to spread the line kernels' factor reads over the most shared-memory banks.
+constexpr int kLineGeomPadMax = 8;
+__host__ __device__ constexpr int64_t line_geom_stride_base(int n, int ng, int esz) {
+  return ((int64_t)ng * n * n * n * esz + 15) / 16 * 16 / esz;
+}
+__host__ __device__ constexpr int64_t line_geom_stride_max(int n, int ng, int esz) {
+  return line_geom_stride_base(n, ng, esz) + kLineGeomPadMax * 16 / esz;
+}
+int64_t line_geom_stride(int n, int ng, int esz);
 int hex_default_variant(int n, int nq, int prec);
 // Compiled cells-per-block choices, the default first; return the count (<= 4).
 int hex_point_cb_options(int n, int nq, int* out);
