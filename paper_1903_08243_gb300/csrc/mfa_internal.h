@@ -199,6 +199,7 @@ struct TetTables {
   double alpha[10 * 3];           // [a][e]
   double beta[10 * 9];            // [a][e][f]
   double mvec[10];                // sum_q w_q phi_a(xi_q)
+  double wmom[13];                // sum_q w_q (1, xi_f, xi_f xi_g): [0], [1 + f], [4 + 3 f + g]
 };
 
 struct TetApplyArgs {

@@ -179,6 +179,13 @@ __global__ void __launch_bounds__(128) tet_apply_kernel(const __grid_constant__ 
 // instead of 120), mapped back once per cell.  The body force term is
 // -b |det J| sum_q w_q phi_a(xi_q).  Same quadrature and physics as
 // tet_apply_kernel; only the order of the sums changes.
+//
+// Neo-Hookean residual: P = mu F + s cof(F), s = (lambda ln J - mu) / J.
+// F = I + G0 + sum_f xi_f G_f is linear in xi, so the moments of mu F are
+// mu |det J| (W0 F0 + sum_f W1_f G_f) for K0 and
+// mu |det J| (W1_f F0 + sum_g W2_fg G_g) for K_f, with F0 = I + G0 and the
+// rule's weight moments W0 = sum_q w_q, W1_f = sum_q w_q xi_f,
+// W2_fg = sum_q w_q xi_f xi_g: the point loop keeps only s cof(F).
 template <int KIND, int LAW, int SC>
 __global__ void __launch_bounds__(128) tet_moment_kernel(const __grid_constant__ TetTables tb, const TetApplyArgs a) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < a.count;
@@ -256,8 +263,56 @@ __global__ void __launch_bounds__(128) tet_moment_kernel(const __grid_constant__
 #pragma unroll
         for (int j = 0; j < 3; ++j) K1[f][c][j] = 0.0;
     bool ok = true;
+    constexpr bool kSplitNH = KIND == MFA_FORM_HYPER_RES && LAW != MFA_LAW_SVK;
+    if constexpr (kSplitNH) {
+      G0[0][0] += 1.0;  // F0 = I + G0
+      G0[1][1] += 1.0;
+      G0[2][2] += 1.0;
 #pragma unroll 1
-    for (int q = 0; q < tb.nq; ++q) {
+      for (int q = 0; q < tb.nq; ++q) {
+        const double x0 = tb.pts[3 * q], x1 = tb.pts[3 * q + 1], x2 = tb.pts[3 * q + 2];
+        double F[3][3], cf[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) F[c][j] = fma(x2, Gf[2][c][j], fma(x1, Gf[1][c][j], fma(x0, Gf[0][c][j], G0[c][j])));
+        const double Jq = det3(F, cf);
+        if (!(Jq > 0.0)) {
+          ok = false;
+          continue;
+        }
+        const double t = tb.w[q] * adet * ((a.lambda * log(Jq) - a.mu) / Jq);
+        const double t0 = t * x0, t1 = t * x1, t2 = t * x2;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            K0[c][j] = fma(t, cf[c][j], K0[c][j]);
+            K1[0][c][j] = fma(t0, cf[c][j], K1[0][c][j]);
+            K1[1][c][j] = fma(t1, cf[c][j], K1[1][c][j]);
+            K1[2][c][j] = fma(t2, cf[c][j], K1[2][c][j]);
+          }
+      }
+      const double ma = a.mu * adet;
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          double s0 = tb.wmom[0] * G0[c][j];
+#pragma unroll
+          for (int g = 0; g < 3; ++g) s0 = fma(tb.wmom[1 + g], Gf[g][c][j], s0);
+          K0[c][j] = fma(ma, s0, K0[c][j]);
+#pragma unroll
+          for (int f = 0; f < 3; ++f) {
+            double sf = tb.wmom[1 + f] * G0[c][j];
+#pragma unroll
+            for (int g = 0; g < 3; ++g) sf = fma(tb.wmom[4 + 3 * f + g], Gf[g][c][j], sf);
+            K1[f][c][j] = fma(ma, sf, K1[f][c][j]);
+          }
+        }
+    }
+#pragma unroll 1
+    for (int q = 0; q < (kSplitNH ? 0 : tb.nq); ++q) {
       const double x0 = tb.pts[3 * q], x1 = tb.pts[3 * q + 1], x2 = tb.pts[3 * q + 2];
       const double wd = tb.w[q] * adet;
       double gu[3][3], gc[3][3], f1[3][3];
