@@ -44,10 +44,15 @@ __global__ void hex_geometry_kernel(const __grid_constant__ HexTables tb, int nq
   for (int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gid < total;
        gid += (int64_t)gridDim.x * blockDim.x) {
     const int64_t cell = gid / pq;
-    const int q = (int)(gid - cell * pq);
-    const int qi = q % nq1, qj = (q / nq1) % nq1, qk = q / (nq1 * nq1);
-    // FP32/BF16 blocks feed the line kernels, whose pointwise step runs on x-lines: x is their slowest index
-    const int qw = std::is_same<TG, double>::value ? q : qj + nq1 * (qk + nq1 * qi);
+    // point qw of the stored block (consecutive threads write consecutive elements): FP64 blocks order the
+    // points x fastest, FP32/BF16 blocks (the line kernels', whose pointwise step runs on x-lines) x slowest
+    const int qw = (int)(gid - cell * pq);
+    int qi, qj, qk;
+    if (std::is_same<TG, double>::value) {
+      qi = qw % nq1, qj = (qw / nq1) % nq1, qk = qw / (nq1 * nq1);
+    } else {
+      qj = qw % nq1, qk = (qw / nq1) % nq1, qi = qw / (nq1 * nq1);
+    }
     const double xi[3] = {tb.x1[qi], tb.x1[qj], tb.x1[qk]};
     const double w = tb.w1[qi] * tb.w1[qj] * tb.w1[qk];
     double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};

@@ -71,6 +71,14 @@ struct LLayout {
   }
 };
 
+// n >= 8: the scatter reads its node indices again (from L2) instead of holding them in registers through the
+// batch, which lets those kernels reach four blocks per SM; below that the registers are there and the reload
+// would only add its latency before the scatter.
+template <int N>
+__host__ __device__ constexpr bool line_reload_nodes() {
+  return N >= 8;
+}
+
 template <int N, int CBX = 0>
 struct LShape {
   static constexpr int L = N * N;         // lines per cell and direction
@@ -369,7 +377,8 @@ __device__ __forceinline__ void line_load_x(const void* xp, const int32_t (&node
 // never waits on global memory.
 template <int N, int KIND, int PREC, typename TX, bool STG = staged<PREC>(), int CBX = 0>
 __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, float* smem, Stage& st,
-                                           const LineArgs* an, int64_t next, const int32_t (&node)[LShape<N, CBX>::K],
+                                           const LineArgs* an, int64_t next,
+                                           const int32_t (&node)[line_reload_nodes<N>() ? 1 : LShape<N, CBX>::K],
                                            const int32_t (&node_next)[LShape<N, CBX>::K],
                                            float (&xin)[LShape<N, CBX>::K]) {
   using S = LShape<N, CBX>;
@@ -401,7 +410,7 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
   // gather, point-parallel: point i of the batch is local point i % P of cell c0 + i / P
 #pragma unroll
   for (int k = 0; k < K; ++k)
-    if (node[k] >= 0) U0[Y::of(t + k * T)] = xin[k];
+    if (t + k * T < ncb * S::P) U0[Y::of(t + k * T)] = xin[k];
   __syncthreads();
   if (valid) sweep<N, 2, 0, false, false, variant>(U, V, la, lb);  // B in z
   __syncthreads();
@@ -441,6 +450,11 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
   // the stage is free: start the next batch's factors now
   if (t == 0 && next >= 0) issue_factors<N, KIND, PREC, STG, CBX>(*an, next, st);
   float* R0;  // plane of the result
+  int32_t snode[K];  // nodes of this thread's points, for the scatter
+  if constexpr (!line_reload_nodes<N>()) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) snode[k] = node[k];
+  }
   if constexpr (KIND != MFA_FORM_MASS) {
     if (valid) sweep<N, 1, 1, true, true, variant>(F1, V, la, lb);  // + D_y^T f1
     __syncthreads();
@@ -448,11 +462,13 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
     __syncthreads();
     if (valid) sweep<N, 1, 0, true, false, variant>(U, V, la, lb);  // B^T in y
     __syncthreads();
+    if constexpr (line_reload_nodes<N>()) line_load_nodes<N, CBX>(a.cell_node, a.count, batch, snode);
     if (valid) sweep<N, 0, 0, true, false, variant>(V, U, la, lb);  // B^T in x
     R0 = U0;
   } else {
     if (valid) sweep<N, 1, 0, true, false, variant>(V, U, la, lb);  // B^T in y
     __syncthreads();
+    if constexpr (line_reload_nodes<N>()) line_load_nodes<N, CBX>(a.cell_node, a.count, batch, snode);
     if (valid) sweep<N, 2, 0, true, false, variant>(U, V, la, lb);  // B^T in z
     R0 = V0;
   }
@@ -460,9 +476,9 @@ __device__ __forceinline__ bool line_batch(const LineArgs& a, int64_t batch, flo
   // scatter-add, point-parallel
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    if (node[k] < 0) continue;
-    if constexpr (sizeof(TX) == 8) add_y(static_cast<double*>(a.y), node[k], R0[Y::of(t + k * T)]);
-    else add_y(static_cast<float*>(a.y), node[k], R0[Y::of(t + k * T)]);
+    if (snode[k] < 0) continue;
+    if constexpr (sizeof(TX) == 8) add_y(static_cast<double*>(a.y), snode[k], R0[Y::of(t + k * T)]);
+    else add_y(static_cast<float*>(a.y), snode[k], R0[Y::of(t + k * T)]);
   }
   __syncthreads();
   return true;
@@ -487,6 +503,19 @@ __host__ __device__ constexpr int line_smem() {
   return STG ? stage_offset<N, CBX>() + stage_bytes<N, PREC, CBX>(geom_entries<KIND>()) + 16 : LShape<N, CBX>::SMEM;
 }
 
+// Blocks per SM that shared memory and the thread count allow, at most 4: the register budget of the grouped
+// launches' __launch_bounds__, so that registers do not cut their occupancy below it (4 blocks of 256 threads:
+// 64 registers; the 64-operator FP32 batch ran 12% faster with it, its Q7/Q8 groups going from 3 to 4 blocks
+// per SM).  The single-operator kernel has no such bound: there it measured 1-10% slower on Q3-Q6, whose
+// registers did not limit occupancy.
+template <int N, int KIND, int PREC, bool STG = staged<PREC>(), int CBX = 0>
+__host__ __device__ constexpr int line_min_blocks() {
+  constexpr int by_smem = (228 * 1024) / (line_smem<N, KIND, PREC, STG, CBX>() + 1024);
+  constexpr int by_threads = 2048 / LShape<N, CBX>::T;
+  constexpr int m = by_smem < by_threads ? by_smem : by_threads;
+  return m < 1 ? 1 : (m > 4 ? 4 : m);
+}
+
 template <int N, int KIND, int PREC, bool STG = staged<PREC>(), int CBX = 0>
 __device__ __forceinline__ void stage_setup(float* smem, Stage& st, int* abort) {
   st.buf = reinterpret_cast<unsigned char*>(smem) + stage_offset<N, CBX>();
@@ -509,7 +538,7 @@ __global__ void __launch_bounds__(LShape<N, CBX>::T) line_apply_kernel(const Lin
   using S = LShape<N, CBX>;
   const int64_t nbatch = (a.count + S::CB - 1) / S::CB;
   if ((int64_t)blockIdx.x < nbatch && threadIdx.x == 0) issue_factors<N, KIND, PREC, STG, CBX>(a, blockIdx.x, st);
-  int32_t node[S::K], nodes_next[S::K];
+  int32_t node[line_reload_nodes<N>() ? 1 : S::K], nodes_next[S::K];
   float xin[S::K];
   if ((int64_t)blockIdx.x < nbatch) {
     line_load_nodes<N, CBX>(a.cell_node, a.count, blockIdx.x, nodes_next);
@@ -517,8 +546,10 @@ __global__ void __launch_bounds__(LShape<N, CBX>::T) line_apply_kernel(const Lin
   }
   for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
     const int64_t next = batch + gridDim.x < nbatch ? batch + gridDim.x : -1;
+    if constexpr (!line_reload_nodes<N>()) {
 #pragma unroll
-    for (int k = 0; k < S::K; ++k) node[k] = nodes_next[k];
+      for (int k = 0; k < S::K; ++k) node[k] = nodes_next[k];
+    }
     if (next >= 0) line_load_nodes<N, CBX>(a.cell_node, a.count, next, nodes_next);
     if (!line_batch<N, KIND, PREC, TX, STG, CBX>(a, batch, smem_l, st, &a, next, node, nodes_next, xin)) return;
   }
@@ -533,7 +564,8 @@ __host__ __device__ constexpr bool group_staged() {
 }
 
 template <int N, int KIND, int PREC>
-__global__ void __launch_bounds__(LShape<N>::T) line_group_kernel(const HexApplyArgs* __restrict__ items,
+__global__ void __launch_bounds__(LShape<N>::T, (line_min_blocks<N, KIND, PREC, group_staged<PREC>()>()))
+    line_group_kernel(const HexApplyArgs* __restrict__ items,
                                                                   const int64_t* __restrict__ first, int nitems) {
   extern __shared__ __align__(128) float smem_l[];
   __shared__ int abort_flag;
@@ -546,7 +578,7 @@ __global__ void __launch_bounds__(LShape<N>::T) line_group_kernel(const HexApply
     return LineArgs{h.x, h.y, h.cell_node, h.geom, h.count, h.geom_stride, h.err};
   };
   constexpr int K = LShape<N>::K;
-  int32_t node[K], nodes_next[K];
+  int32_t node[line_reload_nodes<N>() ? 1 : K], nodes_next[K];
   float xin[K];
   int k = 0;
   if ((int64_t)blockIdx.x < total) {
@@ -564,8 +596,10 @@ __global__ void __launch_bounds__(LShape<N>::T) line_group_kernel(const HexApply
     while (kn + 1 < nitems && gn >= first[kn + 1]) ++kn;
     const LineArgs an = args_of(kn < nitems ? kn : k);
     const int64_t next = gn < total ? gn - first[kn] : -1;
+    if constexpr (!line_reload_nodes<N>()) {
 #pragma unroll
-    for (int j = 0; j < K; ++j) node[j] = nodes_next[j];
+      for (int j = 0; j < K; ++j) node[j] = nodes_next[j];
+    }
     if (next >= 0) line_load_nodes<N, 0>(an.cell_node, an.count, next, nodes_next);
     if (!line_batch<N, KIND, PREC, double, STG>(a, gb - first[k], smem_l, st, &an, next, node, nodes_next, xin))
       return;
