@@ -16,11 +16,11 @@
 // mbarrier), issued for the next batch as soon as the current one has
 // consumed its factors, so the copy overlaps the transposed sweeps, the
 // scatter and the next gather.  Each cell's factor block is padded to 16
-// bytes for the copy.  Waits are bounded: on timeout the kernel sets error
-// bit 4 and every thread leaves.  FP32 stages its factors the same way by
-// default; the form that reads them straight from global memory
-// (point-parallel, coalesced; MFA_VARIANT_LINE) is compiled for both
-// precisions, and the autotuner takes it where it is faster.
+// bytes for the copy (and further, see line_geom_stride).  Waits are bounded:
+// on timeout the kernel sets error bit 4 and every thread leaves.  FP32
+// stages its factors the same way by default; the form that reads them
+// straight from global memory (on x-lines, coalesced; MFA_VARIANT_LINE) is
+// compiled for both precisions, and the autotuner takes it where it is faster.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -92,7 +92,8 @@ struct LShape {
 };
 
 // Node of each of this thread's points of batch `batch` (-1 past the batch's end): requested a batch
-// ahead, so the gather and the scatter wait on one load instead of two.
+// ahead, so the gather waits on one load instead of two (and for n < 8 the
+// scatter reuses them; line_reload_nodes).
 template <int N, int CBX>
 __device__ __forceinline__ void line_load_nodes(const int32_t* cell_node, int64_t count, int64_t batch,
                                                 int32_t (&node)[LShape<N, CBX>::K]) {
